@@ -1,0 +1,471 @@
+"""Benchmark: one step = every property check, the scan, the stable partition (with
+its InvFiltPart check) and a scatter/gather of the payload, on the large plain
+workload: int32 index arrays of n = 2^28 and int64 arrays of n = 2^27 (random
+permutation, nondecreasing prefix sum, planted-violation variants), and a partition
+of 2^28 int32 keys with a float32 payload under Bernoulli predicates p = 0.5 and
+p = 0.01. All inputs are seeded synthetic data; every input is larger than L2.
+
+value = algorithmic HBM bytes of the whole step / step time (GB/s), summed over
+ranks (replicas: each rank runs the same step on its own GPU). Per-op times come
+from CUDA events on the launching stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--small]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+I64MIN, I64MAX = -(2**63), 2**63 - 1
+METRIC = "HBM GB/s & fraction of GB300 peak for property checks + partition; batched/bwd vs plain"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ workload
+
+def make_ops(n32, n64, small=False):
+    """The op list of one step: (name, kind, input names, algorithmic bytes)."""
+    ops = []
+    for tag, n, es in (("i32", n32, 4), ("i64", n64, 8)):
+        ops += [
+            (f"range_perm_{tag}", "range", (f"perm_{tag}",), es * n),
+            (f"range_oor_{tag}", "range", (f"oor_{tag}",), es * n),
+            (f"mono_le_{tag}", "mono", (f"mono_{tag}",), es * n),
+            (f"mono_brk_{tag}", "mono", (f"brk_{tag}",), es * n),
+            (f"inj_perm_{tag}", "inj_fixed", (f"perm_{tag}",), es * n),
+            (f"inj_dup_{tag}", "inj_inf", (f"dup_{tag}",), es * n),
+            (f"bij_perm_{tag}", "bij", (f"perm_{tag}",), es * n),
+            (f"bij_dup_{tag}", "bij", (f"dup_{tag}",), es * n),
+        ]
+    n = n32
+    ops += [
+        ("scan_i32", "scan", ("steps_i32",), 8 * n),
+        ("partition_p50", "partition", ("keys", "payload"), 16 * n),
+        ("partition_p01", "partition01", ("keys", "payload"), 16 * n),
+        ("filtpart_p50", "filtpart", ("keys",), 8 * n),
+        ("scatter_payload", "scatter", ("perm_i32", "payload"), 12 * n),
+        ("gather_payload", "gather", ("perm_i32", "payload"), 12 * n),
+    ]
+    return ops
+
+
+def host_inputs(n32, n64):
+    """Seeded inputs built on the host with NumPy (used by the CPU baseline and e2e)."""
+    s = synth.seed_for(1)
+    d = {}
+    for tag, n, dt in (("i32", n32, np.int32), ("i64", n64, np.int64)):
+        perm = synth.permutation(n, s + 1, dt)
+        mono = synth.monotone(n, s + 2, dt)
+        d[f"perm_{tag}"] = perm
+        d[f"mono_{tag}"] = mono
+        d[f"oor_{tag}"] = synth.plant_value(perm, s + 3, n)[0]
+        d[f"dup_{tag}"] = synth.plant_duplicate(perm, s + 4)[0]
+        d[f"brk_{tag}"] = synth.plant_order_break(mono, s + 5)[0]
+    d["steps_i32"] = np.random.default_rng(s + 6).integers(0, 4, size=n32).astype(np.int32)
+    d["keys"] = synth.keys_uniform(n32, s + 7)
+    d["payload"] = synth.payload_f32(n32, s + 8)
+    return d
+
+
+def device_inputs(n32, n64, dev):
+    """The same recipe drawn on the device with torch's generator (large sizes)."""
+    import torch
+    s = synth.seed_for(1)
+    d = {}
+    for tag, n, dt in (("i32", n32, torch.int32), ("i64", n64, torch.int64)):
+        perm = synth.t_permutation(n, s + 1, dev, dt)
+        mono = synth.t_monotone(n, s + 2, dev, dt)
+        d[f"perm_{tag}"] = perm
+        d[f"mono_{tag}"] = mono
+        d[f"oor_{tag}"] = synth.t_plant_value(perm, s + 3, n)[0]
+        d[f"dup_{tag}"] = synth.t_plant_duplicate(perm, s + 4)[0]
+        d[f"brk_{tag}"] = synth.t_plant_order_break(mono, s + 5)[0]
+    g = torch.Generator(device=dev)
+    g.manual_seed(s + 6)
+    d["steps_i32"] = torch.randint(0, 4, (n32,), generator=g, device=dev, dtype=torch.int32)
+    d["keys"] = synth.t_keys_uniform(n32, s + 7, dev)
+    d["payload"] = synth.t_payload_f32(n32, s + 8, dev)
+    return d
+
+
+class Runner:
+    """Runs the step's ops through the library with preallocated outputs/workspaces."""
+
+    def __init__(self, ixp, inp, n32, n64, dev):
+        import torch
+        self.ixp, self.inp, self.n32, self.n64, self.dev = ixp, inp, n32, n64, dev
+        self.torch = torch
+        n = n32
+        big = max(ixp.workspace_size("inj", 0, n, 4 * n + 4096), ixp.workspace_size("inj", 1, n64, 4 * n64 + 4096),
+                  ixp.workspace_size("partition", 0, n, 0), ixp.workspace_size("scan", 0, n, 0))
+        self.ws = torch.empty(big, dtype=torch.uint8, device=dev)
+        self.verdicts = torch.zeros((64, 6), dtype=torch.int64, device=dev)
+        self.idx = torch.empty(n, dtype=torch.int32, device=dev)
+        self.idx01 = torch.empty(n, dtype=torch.int32, device=dev)
+        self.pay_out = torch.empty(n, dtype=torch.float32, device=dev)
+        self.scan_out = torch.empty(n, dtype=torch.int32, device=dev)
+        self.tot = torch.empty(1, dtype=torch.int32, device=dev)
+        self.status = torch.zeros(4, dtype=torch.int32, device=dev)
+        self.num_true = torch.empty(2, dtype=torch.int64, device=dev)
+        self.scat = torch.empty(n, dtype=torch.float32, device=dev)
+        self.gath = torch.empty(n, dtype=torch.float32, device=dev)
+        self.p50 = synth.bernoulli_threshold(0.5)
+        self.p01 = synth.bernoulli_threshold(0.01)
+
+    def run(self, i, name, kind, names):
+        ixp, inp, ws, v = self.ixp, self.inp, self.ws, self.verdicts[i]
+        x = inp[names[0]]
+        n = x.numel()
+        if kind == "range":
+            ixp.check_range(x, 0, n - 1, out=v, ws=ws)
+        elif kind == "mono":
+            ixp.check_mono(x, "le", out=v, ws=ws)
+        elif kind == "inj_fixed":
+            ixp.check_inj(x, 0, n - 1, out=v, ws=ws)
+        elif kind == "inj_inf":
+            ixp.check_inj(x, I64MIN, I64MAX, span=4 * n + 4096, out=v, ws=ws)
+        elif kind == "bij":
+            ixp.check_bij(x, I64MIN, I64MAX, 0, n - 1, out=v, ws=ws)
+        elif kind == "scan":
+            ixp.scan(x, out=self.scan_out, totals=self.tot, status=self.status[0:1], ws=ws)
+        elif kind == "partition":
+            ixp.partition(x, ("lt", 0, self.p50), payload=inp["payload"], want_keys=False, out=self.idx,
+                          out_payload=self.pay_out, num_true=self.num_true[0:1], status=self.status[1:2], ws=ws)
+        elif kind == "partition01":
+            ixp.partition(x, ("lt", 0, self.p01), payload=inp["payload"], want_keys=False, out=self.idx01,
+                          out_payload=self.pay_out, num_true=self.num_true[1:2], status=self.status[2:3], ws=ws)
+        elif kind == "filtpart":
+            ixp.check_filtpart(self.idx, x, part=("lt", 0, self.p50), out=v, ws=ws)
+        elif kind == "scatter":
+            ixp.scatter(self.scat, x, inp["payload"])
+        elif kind == "gather":
+            ixp.gather(inp["payload"], x, out=self.gath, status=self.status[3:4])
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- CPU baseline
+
+SAMPLE_N32, SAMPLE_N64 = 1 << 24, 1 << 23
+
+
+def oracle_step(inp, ops):
+    """One pass of the op mix through the oracle; returns the algorithmic bytes."""
+    import oracle
+    p50, p01 = synth.bernoulli_threshold(0.5), synth.bernoulli_threshold(0.01)
+    total_bytes = 0
+    idx50 = None
+    if True:
+        for name, kind, names, nbytes in ops:
+            x = inp[names[0]]
+            n = x.shape[0]
+            if kind == "range":
+                oracle.check_range(x, 0, n - 1)
+            elif kind == "mono":
+                oracle.check_mono(x, "le")
+            elif kind == "inj_fixed":
+                oracle.check_inj(x, 0, n - 1)
+            elif kind == "inj_inf":
+                oracle.check_inj(x)
+            elif kind == "bij":
+                oracle.check_bij(x, I64MIN, I64MAX, 0, n - 1)
+            elif kind == "scan":
+                oracle.scan(x)
+            elif kind == "partition":
+                idx50 = oracle.partition(x, ("lt", 0, p50), payload=inp["payload"], want_keys=False)["indices"]
+            elif kind == "partition01":
+                oracle.partition(x, ("lt", 0, p01), payload=inp["payload"], want_keys=False)
+            elif kind == "filtpart":
+                oracle.check_filtpart(idx50, x, part=("lt", 0, p50))
+            elif kind == "scatter":
+                oracle.scatter(np.zeros_like(inp["payload"]), x, inp["payload"])
+            elif kind == "gather":
+                oracle.gather(inp["payload"], x)
+            total_bytes += nbytes
+    return total_bytes
+
+
+def cpu_baseline(steps=4):
+    """The oracle, as it stands, on a bounded sample of the same op mix."""
+    inp = host_inputs(SAMPLE_N32, SAMPLE_N64)
+    ops = make_ops(SAMPLE_N32, SAMPLE_N64)
+    t0 = time.perf_counter()
+    total = sum(oracle_step(inp, ops) for _ in range(steps))
+    dt = time.perf_counter() - t0
+    return {"value": round(total / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} pass(es) of the step's op mix at n=2^24 (int32) / 2^23 (int64) = 1/16 of the "
+                      f"workload, {dt:.1f} s, single-threaded C oracle"}
+
+
+# ---------------------------------------------------------------------- main
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    inp = host_inputs(SAMPLE_N32, SAMPLE_N64)
+    ops = make_ops(SAMPLE_N32, SAMPLE_N64)
+    for _ in range(args.warmup):
+        oracle_step(inp, ops)
+    t0 = time.perf_counter()
+    total = sum(oracle_step(inp, ops) for _ in range(args.steps))
+    dt = time.perf_counter() - t0
+    cb = {"value": round(total / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+          "sample": "each step = one pass of the op mix at n=2^24 (int32) / 2^23 (int64) = 1/16 of the workload"}
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 1),
+            "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64 (index), f32 payload",
+            "data": "synthetic", "config": {"workload": "plain-large (oracle sample)", "n_i32": SAMPLE_N32,
+                                            "n_i64": SAMPLE_N64},
+            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--small", action="store_true", help="2^26 / 2^25 elements (profiling; still above L2)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ops", default="", help="comma-separated subset of op names (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2506_23058_gb300 as ixp
+    ixp.load()
+
+    n32, n64 = (1 << 26, 1 << 25) if args.small else (1 << 28, 1 << 27)
+    ops = make_ops(n32, n64)
+    if args.ops:
+        keep = set(args.ops.split(","))
+        ops = [o for o in ops if o[0] in keep]
+    inp = device_inputs(n32, n64, dev)
+    R = Runner(ixp, inp, n32, n64, dev)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    def step(events=None):
+        for i, (name, kind, names, _) in enumerate(ops):
+            if events is not None:
+                events[i][0].record(stream)
+            R.run(i, name, kind, names)
+            if events is not None:
+                events[i][1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = ixp.load().ixp_kernel_launches()
+
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in ops]
+          for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    clocks.start()
+    time.sleep(0.5)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = ixp.load().ixp_kernel_launches() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    step_bytes = sum(o[3] for o in ops)
+    value = world * step_bytes * args.steps / (total_ms / 1e3) / 1e9
+
+    # per-op times (mean over timed steps)
+    per_op = {}
+    for i, (name, kind, names, nbytes) in enumerate(ops):
+        ts = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
+        m = sum(ts) / len(ts)
+        per_op[name] = {"ms": round(m, 4), "alg_bytes": nbytes, "gbs": round(nbytes / (m / 1e3) / 1e9, 1)}
+    peak, peak_src = peaks()
+    dom = max(per_op, key=lambda k: per_op[k]["ms"])
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        traffic = json.load(open(tf)).get(dom)
+    roofline = {"bound": "hbm", "op": dom, "achieved": per_op[dom]["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": round(per_op[dom]["gbs"] / peak, 4), "traffic": traffic, "peak_source": peak_src}
+    for k in per_op:
+        per_op[k]["frac"] = round(per_op[k]["gbs"] / peak, 4)
+
+    # verdict sanity (outside the timed region)
+    vd = R.verdicts.cpu().tolist()
+    checks = {}
+    for i, (name, kind, _, _) in enumerate(ops):
+        if kind in ("range", "mono", "inj_fixed", "inj_inf", "bij", "filtpart"):
+            w = vd[i]
+            lo = w[0] & 0xFFFFFFFF
+            checks[name] = {"ok": lo - (1 << 32) if lo >= (1 << 31) else lo, "index": w[1],
+                            "status": w[5] & 0xFFFFFFFF}
+
+    e2e = None
+    if not args.no_e2e and not args.ops:
+        e2e = run_e2e(ixp, R, ops, inp, dev, args, step_bytes)
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32/int64 (index), f32 payload", "data": "synthetic",
+            "config": {"workload": "plain-large: i32 n=2^28, i64 n=2^27, partition 2^28 keys + f32 payload "
+                                   "(p=0.5, 0.01)" if not args.small else "plain-small: i32 n=2^26, i64 n=2^25",
+                       "n_i32": n32, "n_i64": n64, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (129 MB); no flush"},
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "ops": per_op,
+            "verdicts": checks}
+    if e2e is not None:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu and not args.ops:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(ixp, R, ops, inp, dev, args, step_bytes):
+    """Same step through the public API from pinned host buffers: H2D of every input
+    and D2H of the verdicts and the partition outputs inside the timed region."""
+    import torch
+    names = sorted({nm for o in ops for nm in o[2]})
+    host = {k: torch.empty(inp[k].shape, dtype=inp[k].dtype, pin_memory=True) for k in names}
+    for k in names:
+        host[k].copy_(inp[k])
+    out_host = {"verdicts": torch.empty_like(R.verdicts, device="cpu").pin_memory(),
+                "idx": torch.empty(R.idx.shape, dtype=R.idx.dtype, pin_memory=True),
+                "pay": torch.empty(R.pay_out.shape, dtype=R.pay_out.dtype, pin_memory=True),
+                "num_true": torch.empty(2, dtype=torch.int64, pin_memory=True)}
+    h2d = sum(host[k].numel() * host[k].element_size() for k in names)
+    d2h = sum(v.numel() * v.element_size() for v in out_host.values())
+    stream = torch.cuda.current_stream()
+    steps = max(1, min(args.steps, 3))
+
+    def one():
+        for k in names:
+            inp[k].copy_(host[k], non_blocking=True)
+        for i, (name, kind, nm, _) in enumerate(ops):
+            R.run(i, name, kind, nm)
+        out_host["verdicts"].copy_(R.verdicts, non_blocking=True)
+        out_host["idx"].copy_(R.idx, non_blocking=True)
+        out_host["pay"].copy_(R.pay_out, non_blocking=True)
+        out_host["num_true"].copy_(R.num_true, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"value": round(step_bytes / (ms / 1e3) / 1e9, 1), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": steps}
+
+
+if __name__ == "__main__":
+    main()

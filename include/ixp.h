@@ -1,0 +1,252 @@
+/*
+ * ixp.h - C ABI of the GB300 (sm_103a) library for the index-array properties and
+ * the scan/scatter combinators of "Verifying Properties of Index Arrays in a
+ * Purely-Functional Data-Parallel Language" (arXiv 2506.23058).
+ *
+ * The paper proves these properties at compile time; this library decides them at
+ * run time on concrete int32/int64 arrays in GPU memory, and provides the data-
+ * parallel programs that build and use such arrays (scan, scatter, gather, stable
+ * partition, flag arrays from shape arrays).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Pointers named d_* or described as "device" are CUDA device pointers. All
+ *    arrays are contiguous, naturally aligned for their element type, and owned by
+ *    the caller. The library never allocates device memory; scratch space comes
+ *    from a caller-supplied workspace of at least ixp_workspace_size(...) bytes,
+ *    256-byte aligned, which the call may overwrite.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream). Results (verdicts, totals, status words) are written to
+ *    device memory, so the calls can be captured in CUDA graphs. Inputs must not be
+ *    modified, and outputs/workspace not read, until the stream reaches that point.
+ *  - The return value reports host-side validation and launch errors only. A
+ *    property that does not hold is not an error: the call returns IXP_OK and the
+ *    verdict says ok = 0. Device-side failures (a bitmap span above capacity, a
+ *    bounded wait that gave up, an out-of-bounds gather index) are reported in the
+ *    verdict's or call's device status word.
+ *  - Index types: IXP_I32 (int32_t) or IXP_I64 (int64_t). n is an element count.
+ *  - Segments (the paper's segmented shape (e^m, k, e_k), Sec. 2.3): `offsets` is a
+ *    device int64_t[nseg + 1] with offsets[0] = 0, offsets[nseg] = n and
+ *    offsets nondecreasing; empty segments are allowed. {NULL, 0} means one flat
+ *    segment [0, n). Invalid offsets give unspecified results but every memory
+ *    access stays inside [0, n).
+ */
+#ifndef IXP_H
+#define IXP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ixp_stream; /* identical to cudaStream_t */
+
+/* ---- return / status codes ------------------------------------------------ */
+#define IXP_OK 0
+#define IXP_E_INVAL (-1)     /* bad argument: null pointer, n < 0, lo > hi, Img outside Rcd, ... */
+#define IXP_E_DTYPE (-2)     /* unsupported element type */
+#define IXP_E_SPAN (-3)      /* value span larger than the workspace bitmap (device status) */
+#define IXP_E_WORKSPACE (-4) /* workspace missing, misaligned or too small */
+#define IXP_E_CUDA (-5)      /* a CUDA launch or memset failed */
+#define IXP_E_TIMEOUT (-6)   /* a bounded device wait gave up (device status) */
+#define IXP_E_OOB (-7)       /* gather index outside the source (device status) */
+
+typedef enum { IXP_I32 = 0, IXP_I64 = 1 } ixp_itype;
+
+/* Monotonic^op (Sec. 2.3, Fig. 5): op in {<=, <, >=, >}. */
+typedef enum { IXP_LE = 0, IXP_LT = 1, IXP_GE = 2, IXP_GT = 3 } ixp_cmp;
+
+/* Verdict kinds. */
+enum {
+    IXP_V_NONE = 0,
+    IXP_V_OUT_OF_RANGE = 1, /* Range: index = first i with X[i] outside [lo, hi] */
+    IXP_V_ORDER = 2,        /* Mono: index = later index j of the first failing pair */
+    IXP_V_DUPLICATE = 3,    /* Inj/Bij: index = smallest i whose value repeats */
+    IXP_V_OUT_OF_IMAGE = 4, /* Bij: index = first i with X[i] in Rcd but outside Img */
+    IXP_V_MISSING = 5,      /* Bij: value = smallest image value no element takes */
+    IXP_V_WRONG_DEST = 6    /* FiltPart: index = first i with a wrong destination */
+};
+
+/* Verdict of a property check, written to device memory (48 bytes).
+ * ok = 1 holds, 0 violated, -1 undecided (status != IXP_OK). The meaning of
+ * index/value/aux0/aux1 is given at each check. */
+typedef struct {
+    int32_t ok;
+    int32_t kind;
+    int64_t index;
+    int64_t value;
+    int64_t aux0;
+    int64_t aux1;
+    int32_t status;
+    int32_t reserved;
+} ixp_verdict;
+
+/* Element predicate, the p of partition2 (Fig. 2) and the p^f / p^p of FiltPart
+ * (Fig. 5), evaluated on keys[i] (or flags[i]):
+ *   IXP_P_TRUE    always true (the "\_ -> true" of the paper)
+ *   IXP_P_MOD_EQ  floored (keys[i] mod a) == b, a > 0
+ *   IXP_P_LT      keys[i] < b (signed)
+ *   IXP_P_FLAGS   flags[i] != 0, flags a device uint8_t[n] */
+enum { IXP_P_TRUE = 0, IXP_P_MOD_EQ = 1, IXP_P_LT = 2, IXP_P_FLAGS = 3 };
+typedef struct {
+    int32_t kind;
+    int32_t a;
+    int64_t b;
+    const uint8_t *flags;
+} ixp_pred;
+
+typedef struct {
+    const int64_t *offsets; /* device int64_t[nseg + 1] or NULL */
+    int64_t nseg;
+} ixp_segs;
+
+/* ---- workspace ------------------------------------------------------------- */
+enum {
+    IXP_OP_RANGE = 0,
+    IXP_OP_MONO = 1,
+    IXP_OP_INJ = 2,      /* extra = largest value span to support (bitmap bits) */
+    IXP_OP_BIJ = 3,      /* extra = |Img| (bitmap bits) */
+    IXP_OP_FILTPART = 4, /* extra = nseg */
+    IXP_OP_SCAN = 5,     /* extra = nseg */
+    IXP_OP_PARTITION = 6,/* extra = nseg */
+    IXP_OP_FLAGS = 7     /* n = m (number of segments) */
+};
+
+/* Bytes of workspace that call `op` needs for n elements of type itype and the
+ * op-specific `extra` above. Returns 0 for an unknown op. */
+size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra);
+
+/* Human-readable name of a return/status code. */
+const char *ixp_strerror(int code);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int ixp_version(void);
+
+/* Number of this library's kernels that have run on the current device since the
+ * library was loaded (each kernel counts itself once, from its first block). Reads
+ * device memory: call it after synchronizing. 0 when no device is present. */
+unsigned long long ixp_kernel_launches(void);
+
+/* ---- property checks ------------------------------------------------------- */
+
+/* Range X (lb, ub)  [Sec. 2.3, Fig. 5]: for all 0 <= i < n, lo <= X[i] <= hi.
+ * Closed bounds; INT64_MIN / INT64_MAX stand for -inf / +inf. lo > hi is
+ * IXP_E_INVAL. Verdict: index = first i outside the bounds, value = X[i],
+ * aux0 = min X, aux1 = max X (INT64_MAX / INT64_MIN when n = 0). */
+int ixp_check_range(const void *x, int itype, int64_t n, int64_t lo, int64_t hi, ixp_verdict *d_verdict,
+                    void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* Monotonic^op X  [Sec. 2.3, Fig. 5]: for all i < j (inside one segment when
+ * segmented), X[i] op X[j]; tested on adjacent pairs, which is equivalent for a
+ * transitive op. Verdict: index = j of the first failing pair (X[j-1], X[j]),
+ * value = X[j], aux0 = X[j-1]. d_seg_ok (nullable, device uint8_t[nseg]) gets 1/0
+ * per segment. */
+int ixp_check_mono(const void *x, int itype, int64_t n, int cmp, ixp_segs segs, ixp_verdict *d_verdict,
+                   uint8_t *d_seg_ok, void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* Inj X Rcd  [Sec. 2.3, Fig. 5]: no two positions whose values lie in
+ * Rcd = [rcd_lo, rcd_hi] hold the same value. Decided with a bitmap over the value
+ * span: [rcd_lo, rcd_hi] when that is finite and fits, else [min, max] of the
+ * in-Rcd values (one extra pass). A span above the workspace capacity (set by
+ * `extra` in ixp_workspace_size) gives verdict status IXP_E_SPAN. Verdict on a
+ * violation: index = smallest i whose value occurs again, value = X[i],
+ * aux0 = smallest j > i with X[j] = X[i]. */
+int ixp_check_inj(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, ixp_verdict *d_verdict,
+                  void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* Bij X Rcd Img  [Sec. 2.3, Fig. 5; rule BijF1, Sec. 3.2]: Inj X Rcd and the set
+ * of in-Rcd values equals Img = [img_lo, img_hi], which must lie inside Rcd.
+ * Verdict: the smaller of (first i with X[i] in Rcd outside Img -> OUT_OF_IMAGE)
+ * and (smallest i with X[i] in Img repeated -> DUPLICATE); otherwise, if some
+ * image value is not taken, MISSING with value = the smallest such value and
+ * index = -1. aux0 = number of elements with values in Img, aux1 = |Img|. */
+int ixp_check_bij(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, int64_t img_lo,
+                  int64_t img_hi, ixp_verdict *d_verdict, void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* InvFiltPart Z (p^f, p^p)  [Sec. 2.3, Fig. 5 and the InvFiltPart prose]: Z is the
+ * scatter-index array that turns X into its filter-partition, i.e. for each
+ * segment k, the elements kept by `filt` go, stably, trues of `part` first, to
+ * consecutive positions after all kept elements of segments < k, and every
+ * dropped element's Z lies outside [0, N) (N = number of kept elements), so
+ * scatter ignores it. Verdict: index = first i with a wrong destination,
+ * value = Z[i], aux0 = N, aux1 = the expected destination (-1 if dropped).
+ * keys may be NULL when both predicates are TRUE or FLAGS. */
+int ixp_check_filtpart(const void *z, int ztype, int64_t n, const void *keys, int ktype, ixp_pred filt,
+                       ixp_pred part, ixp_segs segs, ixp_verdict *d_verdict, void *ws, size_t ws_bytes,
+                       ixp_stream stream);
+
+/* ---- combinators ----------------------------------------------------------- */
+
+/* scan (+) 0  [Sec. 2.1]: out[i] = sum_{j<i} in[j] (exclusive) or sum_{j<=i} in[j]
+ * (inclusive), restarting at each segment start. Sums wrap in the output type
+ * (two's complement). Types: i32->i32, i32->i64, i64->i64. d_totals (nullable,
+ * device, output type) gets the sum of each segment (one entry when flat).
+ * d_status (nullable, device int32) gets IXP_OK or IXP_E_TIMEOUT. */
+int ixp_scan(const void *in, int in_type, void *out, int out_type, int64_t n, int inclusive, ixp_segs segs,
+             void *d_totals, int32_t *d_status, void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* Stable two-way partition, partition2 of Fig. 2 (flat) and partition2L of Sec. 6
+ * (segmented): out_indices[i] = the scatter destination of element i, which is
+ * e_k + (number of trues before i in its segment) when pred(i) holds and
+ * e_k + T_k + (number of falses before i in its segment) otherwise, T_k being the
+ * segment's number of trues. d_num_true (device int64_t[max(1, nseg)]) gets T_k.
+ * out_keys / out_payload (nullable) receive keys / payload rows scattered to their
+ * destinations (payload rows are row_bytes bytes, a multiple of 4, at most 64).
+ * keys may be NULL for a FLAGS or TRUE predicate. d_status as for ixp_scan. */
+int ixp_partition(const void *keys, int ktype, int64_t n, ixp_pred pred, const void *payload, int32_t row_bytes,
+                  void *out_indices, int out_type, void *out_keys, void *out_payload, int64_t *d_num_true,
+                  ixp_segs segs, int32_t *d_status, void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* scatter dst is vs  [Sec. 2.1]: for each i, if 0 <= idx[i] < dst_len then row
+ * dst[idx[i]] := vals[i] (mode IXP_SCATTER_ASSIGN) or += vals[i] (IXP_SCATTER_ADD,
+ * float32 rows accumulated with float32 atomics, or float64 rows with float64
+ * atomics). Out-of-bounds indices are ignored. ASSIGN is deterministic only when
+ * the in-bounds indices are injective (check with ixp_check_inj). Rows are
+ * row_elems elements of elem_bytes (4 or 8) bytes. */
+enum { IXP_SCATTER_ASSIGN = 0, IXP_SCATTER_ADD = 1 };
+int ixp_scatter(void *dst, int64_t dst_len, const void *idx, int itype, const void *vals, int64_t n,
+                int32_t row_elems, int32_t elem_bytes, int32_t mode, ixp_stream stream);
+
+/* Additive scatter of float32 rows accumulated in float64: acc[idx[i]] += vals[i]
+ * for in-bounds idx[i], acc a device double[dst_len * row_elems] the caller zeroes
+ * (or pre-loads). Same-target updates inside a warp are combined before the
+ * atomic. */
+int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const void *idx, int itype, const float *vals,
+                               int64_t n, int32_t row_elems, ixp_stream stream);
+
+/* Rounds a float64 accumulator to float32 (out[i] = (float)acc[i], count elements). */
+int ixp_f64_to_f32(float *out, const double *acc, int64_t count, ixp_stream stream);
+
+/* gather: out[i] = src[idx[i]] (rows of row_elems * elem_bytes bytes). An index
+ * outside [0, src_len) zero-fills its row and sets *d_status = IXP_E_OOB
+ * (d_status nullable; it is not cleared, so zero it first). */
+int ixp_gather(void *out, const void *src, int64_t src_len, const void *idx, int itype, int64_t n,
+               int32_t row_elems, int32_t elem_bytes, int32_t *d_status, ixp_stream stream);
+
+/* mkSgmDescr shape xs  [Sec. 2.1, Fig. 2 right]: out (length sum(shape)) is zero
+ * except out[e_k] = xs[k] (1 when xs is NULL) for every non-empty segment k, with
+ * e_k the exclusive scan of shape; empty segments write nothing. shape is a device
+ * int64_t[m] of non-negative sizes (Range shape (0, inf)); a negative size sets
+ * *d_status = IXP_E_INVAL. d_offsets (nullable, device int64_t[m + 1]) gets e_0..e_m.
+ * out_len must equal sum(shape), which the caller knows or reads from d_offsets of a
+ * first call with out = NULL and out_len = 0 (then only the offsets are written). */
+int ixp_flags_from_shape(const int64_t *shape, int64_t m, const int64_t *xs, void *out, int out_type,
+                         int64_t out_len, int64_t *d_offsets, int32_t *d_status, void *ws, size_t ws_bytes,
+                         ixp_stream stream);
+
+/* ---- testing hook ------------------------------------------------------------ */
+
+/* Sets the bound on every device-side wait of later calls in this process (number
+ * of polls; <= 0 restores the default of 1048576, or the value of the environment
+ * variable IXP_DEBUG_SPIN_LIMIT) and names one look-back tile that never
+ * publishes its value (-1: none). Tests use it to make a wait run out and check
+ * that the call reports IXP_E_TIMEOUT instead of hanging. */
+int ixp_debug_set_wait(long long spin_limit, long long skip_tile);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IXP_H */

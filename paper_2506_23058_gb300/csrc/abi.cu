@@ -1,0 +1,79 @@
+// abi.cu - workspace sizing, error strings, version, launch-shape helpers.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace ixp {
+
+size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg);  // scan.cu
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+// Enough 256-thread blocks for `per_thread` items per thread, capped at 8 resident
+// blocks per SM (2048 threads), at least one block.
+int stream_grid(int64_t work_items, int per_thread) {
+    int64_t per_block = (int64_t)STREAM_THREADS * std::max(1, per_thread);
+    int64_t blocks = (work_items + per_block - 1) / per_block;
+    int64_t cap = (int64_t)num_sms() * 8;
+    return (int)std::max<int64_t>(1, std::min(blocks, cap));
+}
+
+}  // namespace ixp
+
+using namespace ixp;
+
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra) {
+    if (n < 0) n = 0;
+    const int es = itype == IXP_I64 ? 8 : 4;
+    switch (op) {
+        case IXP_OP_RANGE:
+        case IXP_OP_MONO: return HDR_BYTES;
+        case IXP_OP_INJ:
+        case IXP_OP_BIJ: {
+            int64_t span = extra > 0 ? extra : n;
+            size_t words = (size_t)((span + 31) / 32);
+            return HDR_BYTES + round256(2 * words * 4 + 256);
+        }
+        case IXP_OP_SCAN: return tiled_ws_bytes(n, 16 / es, extra);
+        case IXP_OP_PARTITION:
+        case IXP_OP_FILTPART: return tiled_ws_bytes(n, 16 / es, extra);
+        case IXP_OP_FLAGS: return tiled_ws_bytes(n, 2, 0);
+        default: return 0;
+    }
+}
+
+extern "C" const char *ixp_strerror(int code) {
+    switch (code) {
+        case IXP_OK: return "ok";
+        case IXP_E_INVAL: return "invalid argument";
+        case IXP_E_DTYPE: return "unsupported element type";
+        case IXP_E_SPAN: return "value span exceeds the workspace bitmap";
+        case IXP_E_WORKSPACE: return "workspace missing, misaligned or too small";
+        case IXP_E_CUDA: return "CUDA launch failed";
+        case IXP_E_TIMEOUT: return "bounded device wait gave up";
+        case IXP_E_OOB: return "index out of bounds";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int ixp_version(void) { return 100; }
+
+extern "C" unsigned long long ixp_tu_kernels_checks(void);
+extern "C" unsigned long long ixp_tu_kernels_scan(void);
+extern "C" unsigned long long ixp_tu_kernels_scatter(void);
+
+extern "C" unsigned long long ixp_kernel_launches(void) {
+    return ixp_tu_kernels_checks() + ixp_tu_kernels_scan() + ixp_tu_kernels_scatter();
+}

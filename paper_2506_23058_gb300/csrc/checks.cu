@@ -1,0 +1,674 @@
+// checks.cu - runtime checks of the paper's index-array properties (Sec. 2.3,
+// Fig. 5): Range, Monotonic, Inj and Bij on int32/int64 arrays.
+//
+// Range and flat Mono are single streaming passes (4 or 8 bytes per element, HBM
+// bound). Inj and Bij set one bit per in-codomain element in a bitmap over the value
+// span with an L2 atomicOr whose return value flags a collision (rule BijF1 of
+// Sec. 3.2 counts the same way: Inj plus |Img| in-image elements); the bitmap for a
+// 2^28 span is 32 MiB and stays L2 resident. When a collision was seen, two more
+// passes recover the exact witness (smallest repeated index and its partner); they
+// exit at once otherwise.
+#include "common.cuh"
+
+namespace ixp {
+
+// ============================================================== Range
+template <typename T>
+__global__ void __launch_bounds__(STREAM_THREADS) range_kernel(const T *__restrict__ x, int64_t n, int64_t lo,
+                                                               int64_t hi, Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    using VT = typename Vec<T>::type;
+    constexpr int V = Vec<T>::N;
+    Split<T> s(x, n);
+    int64_t mn = INT64_MAX, mx = INT64_MIN, bad = INT64_MAX;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto visit = [&](int64_t i, int64_t xi) {
+        mn = xi < mn ? xi : mn;
+        mx = xi > mx ? xi : mx;
+        if ((xi < lo) | (xi > hi)) bad = i < bad ? i : bad;
+    };
+    for (int64_t i = tid; i < s.head; i += stride) visit(i, ld1(x, i));
+    for (int64_t i = s.tail0 + tid; i < n; i += stride) visit(i, ld1(x, i));
+    const VT *xv = reinterpret_cast<const VT *>(x + s.head);
+    int64_t v = tid;
+    for (; v + 3 * stride < s.nvec; v += 4 * stride) {
+        VT a[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int64_t e[V];
+            unpack(a[u], e);
+#pragma unroll
+            for (int k = 0; k < V; k++) visit(s.head + (v + u * stride) * V + k, e[k]);
+        }
+    }
+    for (; v < s.nvec; v += stride) {
+        int64_t e[V];
+        unpack(ldv(xv + v), e);
+#pragma unroll
+        for (int k = 0; k < V; k++) visit(s.head + v * V + k, e[k]);
+    }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    unsigned long long r;
+    r = block_max_u64(enc_min(mn), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_min, r);
+    r = block_max_u64(enc_max(mx), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_max, r);
+    r = block_max_u64(bad == INT64_MAX ? 0ull : enc_first(bad), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+}
+
+template <typename T>
+__global__ void range_finalize(const T *x, int64_t n, const Hdr *h, ixp_verdict *out) {
+    IXP_KERNEL_ENTRY();
+    ixp_verdict v;
+    int64_t bad = h->k_first ? dec_first(h->k_first) : -1;
+    v.status = h->status;
+    v.ok = v.status ? -1 : (bad < 0 ? 1 : 0);
+    v.kind = bad < 0 ? IXP_V_NONE : IXP_V_OUT_OF_RANGE;
+    v.index = bad;
+    v.value = bad < 0 ? 0 : (int64_t)x[bad];
+    v.aux0 = dec_min(h->k_min);
+    v.aux1 = dec_max(h->k_max);
+    v.reserved = 0;
+    *out = v;
+}
+
+// ======================================================= Monotonic (flat)
+__device__ __forceinline__ bool cmp_ok(int c, int64_t a, int64_t b) {
+    switch (c) {
+        case IXP_LE: return a <= b;
+        case IXP_LT: return a < b;
+        case IXP_GE: return a >= b;
+        default: return a > b;
+    }
+}
+
+// Grid-stride over 16-byte vectors with a warp-uniform loop: lane l holds vector
+// wbase + l, so the element before its vector is lane l-1's last element (one
+// shuffle); lane 0 reads it from memory.
+template <typename T, int C>
+__global__ void __launch_bounds__(STREAM_THREADS) mono_kernel(const T *__restrict__ x, int64_t n, Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    using VT = typename Vec<T>::type;
+    constexpr int V = Vec<T>::N;
+    Split<T> s(x, n);
+    int64_t bad = INT64_MAX;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    // scalar head and tail pairs (j >= 1)
+    for (int64_t j = tid; j < s.head; j += stride)
+        if (j >= 1 && !cmp_ok(C, ld1(x, j - 1), ld1(x, j))) bad = j < bad ? j : bad;
+    for (int64_t j = s.tail0 + tid; j < n; j += stride)
+        if (j >= 1 && !cmp_ok(C, ld1(x, j - 1), ld1(x, j))) bad = j < bad ? j : bad;
+    const VT *xv = reinterpret_cast<const VT *>(x + s.head);
+    const int64_t wtid = tid - lane;  // warp's first thread
+    for (int64_t wb = wtid; wb < s.nvec; wb += 4 * stride) {
+        VT a[4];
+        int64_t prevm[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int64_t vv = wb + u * stride + lane;
+            if (vv < s.nvec) a[u] = ldv(xv + vv);
+            int64_t p = s.head + (wb + u * stride) * V;  // first element of lane 0's vector
+            prevm[u] = (lane == 0 && p >= 1 && wb + u * stride < s.nvec) ? ld1(x, p - 1) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int64_t vv = wb + u * stride + lane;
+            int64_t e[V];
+            if (vv < s.nvec) unpack(a[u], e);
+            else {
+#pragma unroll
+                for (int k = 0; k < V; k++) e[k] = 0;
+            }
+            int64_t prev = __shfl_up_sync(FULL, e[V - 1], 1);
+            if (lane == 0) prev = prevm[u];
+            if (vv < s.nvec) {
+                int64_t j0 = s.head + vv * V;
+                if (j0 >= 1 && !cmp_ok(C, prev, e[0])) bad = j0 < bad ? j0 : bad;
+#pragma unroll
+                for (int k = 1; k < V; k++)
+                    if (!cmp_ok(C, e[k - 1], e[k])) bad = (j0 + k) < bad ? (j0 + k) : bad;
+            }
+        }
+    }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    unsigned long long r = block_max_u64(bad == INT64_MAX ? 0ull : enc_first(bad), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+}
+
+// =================================================== Monotonic (segmented)
+// One 4096-element tile per block iteration. Segment heads inside the tile are
+// marked in a shared bitmap (binary search for the first offset >= tile start,
+// then a walk); the pair (j-1, j) is tested only when j is not a head.
+constexpr int MONO_SEG_TILE = 4096;
+
+__device__ __forceinline__ int64_t lower_bound_off(const int64_t *off, int64_t nseg, int64_t key) {
+    // first k in [0, nseg] with off[k] >= key (nseg+1 if none)
+    int64_t lo = 0, hi = nseg + 1;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t segment_of(const int64_t *off, int64_t nseg, int64_t i) {
+    // last k in [0, nseg) with off[k] <= i
+    int64_t lo = 0, hi = nseg;  // answer in [0, nseg-1]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(STREAM_THREADS) mono_seg_kernel(const T *__restrict__ x, int64_t n, int c,
+                                                                  const int64_t *__restrict__ off, int64_t nseg,
+                                                                  uint8_t *seg_ok, Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    __shared__ unsigned heads[MONO_SEG_TILE / 32];
+    __shared__ int64_t s_k;
+    int64_t bad = INT64_MAX;
+    const int64_t ntiles = (n + MONO_SEG_TILE - 1) / MONO_SEG_TILE;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t t0 = t * MONO_SEG_TILE;
+        const int64_t t1 = min(n, t0 + MONO_SEG_TILE);
+        for (int w = threadIdx.x; w < MONO_SEG_TILE / 32; w += blockDim.x) heads[w] = 0;
+        if (threadIdx.x == 0) s_k = lower_bound_off(off, nseg, t0);
+        __syncthreads();
+        for (int64_t k = s_k + threadIdx.x; k <= nseg; k += blockDim.x) {
+            int64_t o = __ldg(off + k);
+            if (o >= t1) break;
+            if (o >= t0) atomicOr(&heads[(o - t0) >> 5], 1u << ((o - t0) & 31));
+        }
+        __syncthreads();
+        for (int64_t j = t0 + threadIdx.x; j < t1; j += blockDim.x) {
+            if (j == 0) continue;
+            int64_t r = j - t0;
+            if (heads[r >> 5] & (1u << (r & 31))) continue;
+            int64_t a = ld1(x, j - 1), b = ld1(x, j);
+            if (!cmp_ok(c, a, b)) {
+                bad = j < bad ? j : bad;
+                if (seg_ok) seg_ok[segment_of(off, nseg, j)] = 0;
+            }
+        }
+        __syncthreads();
+    }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    unsigned long long r = block_max_u64(bad == INT64_MAX ? 0ull : enc_first(bad), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+}
+
+template <typename T>
+__global__ void mono_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
+    IXP_KERNEL_ENTRY();
+    ixp_verdict v;
+    int64_t j = h->k_first ? dec_first(h->k_first) : -1;
+    v.status = h->status;
+    v.ok = v.status ? -1 : (j < 0 ? 1 : 0);
+    v.kind = j < 0 ? IXP_V_NONE : IXP_V_ORDER;
+    v.index = j;
+    v.value = j < 0 ? 0 : (int64_t)x[j];
+    v.aux0 = j < 1 ? 0 : (int64_t)x[j - 1];
+    v.aux1 = 0;
+    v.reserved = 0;
+    *out = v;
+}
+
+// ================================================================ Inj / Bij
+// Min/max of the in-codomain values (needed when Rcd is unbounded).
+template <typename T>
+__global__ void __launch_bounds__(STREAM_THREADS) minmax_in_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
+                                                                   int64_t rhi, Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    using VT = typename Vec<T>::type;
+    constexpr int V = Vec<T>::N;
+    Split<T> s(x, n);
+    int64_t mn = INT64_MAX, mx = INT64_MIN;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto visit = [&](int64_t xi) {
+        if (xi >= rlo && xi <= rhi) {
+            mn = xi < mn ? xi : mn;
+            mx = xi > mx ? xi : mx;
+        }
+    };
+    for (int64_t i = tid; i < s.head; i += stride) visit(ld1(x, i));
+    for (int64_t i = s.tail0 + tid; i < n; i += stride) visit(ld1(x, i));
+    const VT *xv = reinterpret_cast<const VT *>(x + s.head);
+    int64_t v = tid;
+    for (; v + 3 * stride < s.nvec; v += 4 * stride) {
+        VT a[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int64_t e[V];
+            unpack(a[u], e);
+#pragma unroll
+            for (int k = 0; k < V; k++) visit(e[k]);
+        }
+    }
+    for (; v < s.nvec; v += stride) {
+        int64_t e[V];
+        unpack(ldv(xv + v), e);
+#pragma unroll
+        for (int k = 0; k < V; k++) visit(e[k]);
+    }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    unsigned long long r = block_max_u64(enc_min(mn), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_min, r);
+    r = block_max_u64(enc_max(mx), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_max, r);
+}
+
+// Fix the bitmap's base and span, check it against the capacity, clear the words
+// the call will use. Fixed range: base = lo, span = hi - lo + 1. Otherwise the
+// range comes from minmax_in_kernel (span 0 when nothing is in range).
+__global__ void bitmap_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, unsigned long long cap_bits,
+                                    unsigned *bm, unsigned *dup) {
+    IXP_KERNEL_ENTRY();
+    unsigned long long base, span;
+    if (fixed) {
+        base = (unsigned long long)lo;
+        span = (unsigned long long)hi - (unsigned long long)lo + 1ull;
+    } else {
+        int64_t mn = dec_min(h->k_min), mx = dec_max(h->k_max);
+        if (mn > mx) {
+            base = 0;
+            span = 0;
+        } else {
+            base = (unsigned long long)mn;
+            span = (unsigned long long)mx - (unsigned long long)mn + 1ull;
+        }
+    }
+    // span == 0 after the +1 means the full 2^64 range
+    bool too_big = (fixed || span != 0) ? (span > cap_bits || (span == 0 && fixed)) : false;
+    if (too_big) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, IXP_E_SPAN);
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        h->base = base;
+        h->span = span;
+    }
+    const unsigned long long words = (span + 31) / 32;
+    for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < words;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        bm[w] = 0u;
+        dup[w] = 0u;
+    }
+}
+
+// Mark pass. For each element with a value in [mlo, mhi] (Rcd for Inj, Img for
+// Bij): atomicOr its bit; a bit already set means a repeat, which is recorded in
+// the second bitmap. For Bij, values in Rcd but outside Img are out of image.
+template <typename T, bool BIJ>
+__global__ void __launch_bounds__(STREAM_THREADS) mark_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
+                                                              int64_t rhi, int64_t mlo, int64_t mhi, Hdr *h,
+                                                              unsigned *__restrict__ bm, unsigned *__restrict__ dup) {
+    IXP_KERNEL_ENTRY();
+    if (h->status) return;
+    using VT = typename Vec<T>::type;
+    constexpr int V = Vec<T>::N;
+    const unsigned long long base = h->base, span = h->span;
+    Split<T> s(x, n);
+    unsigned long long cnt = 0;
+    unsigned anydup = 0;
+    int64_t ooi = INT64_MAX;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    auto visit = [&](int64_t i, int64_t xi) {
+        if (xi < rlo || xi > rhi) return;
+        if (BIJ && (xi < mlo || xi > mhi)) {
+            ooi = i < ooi ? i : ooi;
+            return;
+        }
+        unsigned long long b = (unsigned long long)xi - base;
+        if (b >= span) return;  // cannot happen for a consistent header; keeps writes in bounds
+        unsigned bit = 1u << (b & 31);
+        unsigned old = atomicOr(bm + (b >> 5), bit);
+        if (old & bit) {
+            atomicOr(dup + (b >> 5), bit);
+            anydup = 1;
+        }
+        cnt++;
+    };
+    for (int64_t i = tid; i < s.head; i += stride) visit(i, ld1(x, i));
+    for (int64_t i = s.tail0 + tid; i < n; i += stride) visit(i, ld1(x, i));
+    const VT *xv = reinterpret_cast<const VT *>(x + s.head);
+    int64_t v = tid;
+    for (; v + 3 * stride < s.nvec; v += 4 * stride) {
+        VT a[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int64_t e[V];
+            unpack(a[u], e);
+#pragma unroll
+            for (int k = 0; k < V; k++) visit(s.head + (v + u * stride) * V + k, e[k]);
+        }
+    }
+    for (; v < s.nvec; v += stride) {
+        int64_t e[V];
+        unpack(ldv(xv + v), e);
+#pragma unroll
+        for (int k = 0; k < V; k++) visit(s.head + v * V + k, e[k]);
+    }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    unsigned long long r = block_sum_u64(cnt, sm);
+    if (threadIdx.x == 0 && r) atomicAdd(&h->cnt0, r);
+    if (__syncthreads_or(anydup) && threadIdx.x == 0) atomicOr(&h->flag, 1u);
+    if (BIJ) {
+        r = block_max_u64(ooi == INT64_MAX ? 0ull : enc_first(ooi), sm);
+        if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+    }
+}
+
+// Smallest index whose value (in [mlo, mhi]) has its bit in the repeat bitmap.
+// Runs only when the mark pass saw a repeat.
+template <typename T>
+__global__ void __launch_bounds__(STREAM_THREADS) first_dup_kernel(const T *__restrict__ x, int64_t n, int64_t mlo,
+                                                                   int64_t mhi, Hdr *h,
+                                                                   const unsigned *__restrict__ dup,
+                                                                   unsigned long long *slot) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || !h->flag) return;
+    const unsigned long long base = h->base, span = h->span;
+    int64_t best = INT64_MAX;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += stride) {
+        int64_t xi = ld1(x, i);
+        if (xi < mlo || xi > mhi) continue;
+        unsigned long long b = (unsigned long long)xi - base;
+        if (b >= span) continue;
+        if (__ldg(dup + (b >> 5)) & (1u << (b & 31))) {
+            best = i;  // the first hit of this thread is its smallest index
+            break;
+        }
+    }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    unsigned long long r = block_max_u64(best == INT64_MAX ? 0ull : enc_first(best), sm);
+    if (threadIdx.x == 0) atomic_max_u64(slot, r);
+}
+
+// Partner of the first repeated index i*: the smallest j > i* with x[j] = x[i*].
+template <typename T>
+__global__ void __launch_bounds__(STREAM_THREADS) partner_kernel(const T *__restrict__ x, int64_t n, Hdr *h,
+                                                                 const unsigned long long *slot) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || !h->flag || !*slot) return;
+    const int64_t i0 = dec_first(*slot);
+    const int64_t v0 = ld1(x, i0);
+    int64_t best = INT64_MAX;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = i0 + 1 + tid; j < n; j += stride)
+        if (ld1(x, j) == v0) {
+            best = j;
+            break;
+        }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    unsigned long long r = block_max_u64(best == INT64_MAX ? 0ull : enc_first(best), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_aux, r);
+}
+
+template <typename T>
+__global__ void inj_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
+    IXP_KERNEL_ENTRY();
+    ixp_verdict v;
+    v.status = h->status;
+    int64_t i = (h->flag && h->k_first) ? dec_first(h->k_first) : -1;
+    v.ok = v.status ? -1 : (i < 0 ? 1 : 0);
+    v.kind = (v.status || i < 0) ? IXP_V_NONE : IXP_V_DUPLICATE;
+    v.index = v.status ? -1 : i;
+    v.value = (v.status || i < 0) ? 0 : (int64_t)x[i];
+    v.aux0 = (v.status || i < 0 || !h->k_aux) ? -1 : dec_first(h->k_aux);
+    v.aux1 = 0;
+    v.reserved = 0;
+    *out = v;
+}
+
+// Bij "missing" value: when nothing is out of image and nothing repeats but fewer
+// than |Img| elements hit the image, the smallest clear bit is the first value no
+// element takes.
+__global__ void __launch_bounds__(STREAM_THREADS) missing_kernel(Hdr *h, const unsigned *__restrict__ bm) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->flag || h->k_first) return;
+    const unsigned long long span = h->span;
+    if (h->cnt0 >= span) return;
+    const unsigned long long words = (span + 31) / 32;
+    unsigned long long best = ~0ull;
+    for (unsigned long long w = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; w < words;
+         w += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned z = ~bm[w];
+        if (w == words - 1 && (span & 31)) z &= (1u << (span & 31)) - 1u;
+        if (z) {
+            best = w * 32 + (__ffs(z) - 1);
+            break;
+        }
+    }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    unsigned long long r = block_max_u64(best == ~0ull ? 0ull : enc_first((int64_t)best), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_aux, r);
+}
+
+template <typename T>
+__global__ void bij_finalize(const T *x, const Hdr *h, ixp_verdict *out, int64_t img_lo, int64_t img_size) {
+    IXP_KERNEL_ENTRY();
+    ixp_verdict v;
+    v.status = h->status;
+    v.reserved = 0;
+    v.aux0 = (int64_t)h->cnt0;
+    v.aux1 = img_size;
+    int64_t ooi = h->k_first ? dec_first(h->k_first) : -1;
+    int64_t dupi = (h->flag && h->k_first2) ? dec_first(h->k_first2) : -1;
+    if (v.status) {
+        v.ok = -1;
+        v.kind = IXP_V_NONE;
+        v.index = -1;
+        v.value = 0;
+    } else if (ooi >= 0 && (dupi < 0 || ooi < dupi)) {
+        v.ok = 0;
+        v.kind = IXP_V_OUT_OF_IMAGE;
+        v.index = ooi;
+        v.value = (int64_t)x[ooi];
+    } else if (dupi >= 0) {
+        v.ok = 0;
+        v.kind = IXP_V_DUPLICATE;
+        v.index = dupi;
+        v.value = (int64_t)x[dupi];
+    } else if ((int64_t)h->cnt0 < img_size) {
+        v.ok = 0;
+        v.kind = IXP_V_MISSING;
+        v.index = -1;
+        v.value = img_lo + (h->k_aux ? dec_first(h->k_aux) : 0);
+    } else {
+        v.ok = 1;
+        v.kind = IXP_V_NONE;
+        v.index = -1;
+        v.value = 0;
+    }
+    *out = v;
+}
+
+// ================================================================ host side
+
+static bool aligned_to(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static int launch_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+static int check_ws(void *ws, size_t ws_bytes, size_t need) {
+    if (!ws || !aligned_to(ws, 256) || ws_bytes < need) return IXP_E_WORKSPACE;
+    return IXP_OK;
+}
+
+static int elem_size(int t) { return t == IXP_I32 ? 4 : 8; }
+
+}  // namespace ixp
+
+using namespace ixp;
+
+extern "C" int ixp_check_range(const void *x, int itype, int64_t n, int64_t lo, int64_t hi, ixp_verdict *d_verdict,
+                               void *ws, size_t ws_bytes, ixp_stream stream) {
+    if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
+    if (n < 0 || lo > hi || !d_verdict || (n > 0 && (!x || !aligned_to(x, elem_size(itype))))) return IXP_E_INVAL;
+    int rc = check_ws(ws, ws_bytes, ixp_workspace_size(IXP_OP_RANGE, itype, n, 0));
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Hdr *h = (Hdr *)ws;
+    if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    int grid = stream_grid((n + 3) / 4);
+    if (itype == IXP_I32) {
+        if (n > 0) range_kernel<int32_t><<<grid, STREAM_THREADS, 0, st>>>((const int32_t *)x, n, lo, hi, h);
+        range_finalize<int32_t><<<1, 1, 0, st>>>((const int32_t *)x, n, h, d_verdict);
+    } else {
+        if (n > 0) range_kernel<int64_t><<<grid, STREAM_THREADS, 0, st>>>((const int64_t *)x, n, lo, hi, h);
+        range_finalize<int64_t><<<1, 1, 0, st>>>((const int64_t *)x, n, h, d_verdict);
+    }
+    return launch_status();
+}
+
+template <typename T>
+static void launch_mono(const T *x, int64_t n, int cmp, int grid, Hdr *h, cudaStream_t st) {
+    switch (cmp) {
+        case IXP_LE: mono_kernel<T, IXP_LE><<<grid, STREAM_THREADS, 0, st>>>(x, n, h); break;
+        case IXP_LT: mono_kernel<T, IXP_LT><<<grid, STREAM_THREADS, 0, st>>>(x, n, h); break;
+        case IXP_GE: mono_kernel<T, IXP_GE><<<grid, STREAM_THREADS, 0, st>>>(x, n, h); break;
+        default: mono_kernel<T, IXP_GT><<<grid, STREAM_THREADS, 0, st>>>(x, n, h); break;
+    }
+}
+
+extern "C" int ixp_check_mono(const void *x, int itype, int64_t n, int cmp, ixp_segs segs, ixp_verdict *d_verdict,
+                              uint8_t *d_seg_ok, void *ws, size_t ws_bytes, ixp_stream stream) {
+    if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
+    if (n < 0 || cmp < 0 || cmp > 3 || !d_verdict || (n > 0 && (!x || !aligned_to(x, elem_size(itype)))))
+        return IXP_E_INVAL;
+    const bool seg = segs.offsets != nullptr;
+    if ((seg && segs.nseg < 1) || (!seg && (segs.nseg != 0 || d_seg_ok))) return IXP_E_INVAL;
+    int rc = check_ws(ws, ws_bytes, ixp_workspace_size(IXP_OP_MONO, itype, n, segs.nseg));
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Hdr *h = (Hdr *)ws;
+    if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (seg && d_seg_ok && cudaMemsetAsync(d_seg_ok, 1, (size_t)segs.nseg, st) != cudaSuccess) return IXP_E_CUDA;
+    if (n > 1) {
+        if (!seg) {
+            int grid = stream_grid((n + 3) / 4);
+            if (itype == IXP_I32) launch_mono((const int32_t *)x, n, cmp, grid, h, st);
+            else launch_mono((const int64_t *)x, n, cmp, grid, h, st);
+        } else {
+            int64_t tiles = (n + MONO_SEG_TILE - 1) / MONO_SEG_TILE;
+            int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 8);
+            if (itype == IXP_I32)
+                mono_seg_kernel<int32_t><<<grid, STREAM_THREADS, 0, st>>>((const int32_t *)x, n, cmp, segs.offsets,
+                                                                          segs.nseg, d_seg_ok, h);
+            else
+                mono_seg_kernel<int64_t><<<grid, STREAM_THREADS, 0, st>>>((const int64_t *)x, n, cmp, segs.offsets,
+                                                                          segs.nseg, d_seg_ok, h);
+        }
+    }
+    if (itype == IXP_I32) mono_finalize<int32_t><<<1, 1, 0, st>>>((const int32_t *)x, h, d_verdict);
+    else mono_finalize<int64_t><<<1, 1, 0, st>>>((const int64_t *)x, h, d_verdict);
+    return launch_status();
+}
+
+namespace ixp {
+// Bitmap capacity (bits) that a workspace of ws_bytes holds: two bitmaps after the header.
+static unsigned long long bitmap_capacity(size_t ws_bytes) {
+    if (ws_bytes < HDR_BYTES) return 0;
+    return (unsigned long long)((ws_bytes - HDR_BYTES) / 8) * 32ull;
+}
+
+template <typename T>
+static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bool bij, int64_t ilo, int64_t ihi,
+                             Hdr *h, unsigned *bm, unsigned *dup, unsigned long long cap, ixp_verdict *out,
+                             cudaStream_t st) {
+    const int grid = stream_grid((n + 3) / 4);
+    const int sgrid = num_sms() * 4;
+    if (bij) {
+        bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, 1, ilo, ihi, cap, bm, dup);
+        if (n > 0) {
+            mark_kernel<T, true><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, ilo, ihi, h, bm, dup);
+            first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, &h->k_first2);
+        }
+        missing_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, bm);
+        bij_finalize<T><<<1, 1, 0, st>>>(x, h, out, ilo, (int64_t)((unsigned long long)ihi - (unsigned long long)ilo + 1));
+        return;
+    }
+    // Inj: a finite Rcd that fits the bitmap is used as is; otherwise find [min, max].
+    const unsigned long long rspan = (unsigned long long)rhi - (unsigned long long)rlo + 1ull;
+    const bool fixed = rspan != 0 && rspan <= cap && rspan <= 4ull * (unsigned long long)n + 4096ull;
+    if (!fixed && n > 0) minmax_in_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h);
+    bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, fixed ? 1 : 0, rlo, rhi, cap, bm, dup);
+    if (n > 0) {
+        mark_kernel<T, false><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, rlo, rhi, h, bm, dup);
+        first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, dup, &h->k_first);
+        partner_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, h, &h->k_first);
+    }
+    inj_finalize<T><<<1, 1, 0, st>>>(x, h, out);
+}
+}  // namespace ixp
+
+extern "C" int ixp_check_inj(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi,
+                             ixp_verdict *d_verdict, void *ws, size_t ws_bytes, ixp_stream stream) {
+    if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
+    if (n < 0 || rcd_lo > rcd_hi || !d_verdict || (n > 0 && (!x || !aligned_to(x, elem_size(itype)))))
+        return IXP_E_INVAL;
+    int rc = check_ws(ws, ws_bytes, HDR_BYTES + 256);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Hdr *h = (Hdr *)ws;
+    const unsigned long long cap = bitmap_capacity(ws_bytes);
+    unsigned *bm = (unsigned *)((char *)ws + HDR_BYTES);
+    unsigned *dup = bm + cap / 32;
+    if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (itype == IXP_I32)
+        run_bitmap_check((const int32_t *)x, n, rcd_lo, rcd_hi, false, 0, 0, h, bm, dup, cap, d_verdict, st);
+    else
+        run_bitmap_check((const int64_t *)x, n, rcd_lo, rcd_hi, false, 0, 0, h, bm, dup, cap, d_verdict, st);
+    return launch_status();
+}
+
+extern "C" int ixp_check_bij(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, int64_t img_lo,
+                             int64_t img_hi, ixp_verdict *d_verdict, void *ws, size_t ws_bytes, ixp_stream stream) {
+    if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
+    if (n < 0 || rcd_lo > rcd_hi || img_lo > img_hi || img_lo < rcd_lo || img_hi > rcd_hi || !d_verdict ||
+        (n > 0 && (!x || !aligned_to(x, elem_size(itype)))))
+        return IXP_E_INVAL;
+    const unsigned long long isize = (unsigned long long)img_hi - (unsigned long long)img_lo + 1ull;
+    if (isize == 0 || isize > (1ull << 40)) return IXP_E_INVAL;
+    const unsigned long long cap = bitmap_capacity(ws_bytes);
+    int rc = check_ws(ws, ws_bytes, HDR_BYTES + 256);
+    if (rc) return rc;
+    if (isize > cap) return IXP_E_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    Hdr *h = (Hdr *)ws;
+    unsigned *bm = (unsigned *)((char *)ws + HDR_BYTES);
+    unsigned *dup = bm + cap / 32;
+    if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (itype == IXP_I32)
+        run_bitmap_check((const int32_t *)x, n, rcd_lo, rcd_hi, true, img_lo, img_hi, h, bm, dup, cap, d_verdict, st);
+    else
+        run_bitmap_check((const int64_t *)x, n, rcd_lo, rcd_hi, true, img_lo, img_hi, h, bm, dup, cap, d_verdict, st);
+    return launch_status();
+}
+
+extern "C" unsigned long long ixp_tu_kernels_checks(void) {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, ixp::tu_kernel_count, sizeof(v)) != cudaSuccess) return 0;
+    return v;
+}

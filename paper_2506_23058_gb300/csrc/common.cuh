@@ -1,0 +1,176 @@
+// common.cuh - device helpers shared by the library's kernels (not by the oracle).
+//
+// Layout rules used throughout:
+//  * Streaming kernels read 16-byte vectors (int4 / longlong2) in a grid-stride loop
+//    unrolled four deep, so each SM keeps ~128 KB of loads in flight; the elements
+//    before the first 16-byte boundary and after the last whole vector are handled
+//    one by one.
+//  * Reductions go warp shuffle -> shared memory -> one global atomic per block.
+//  * Every call zeroes a 256-byte header at the start of its workspace. All header
+//    slots start at 0 and are only raised with unsigned 64-bit atomicMax, so minima,
+//    maxima and "first index" slots are stored under order-preserving encodings:
+//        first index i : ~i          (0 = none; decodes to -1)
+//        minimum  x    : ~(x ^ SIGN) (0 decodes to INT64_MAX)
+//        maximum  x    :  x ^ SIGN   (0 decodes to INT64_MIN)
+//  * Every spin-wait is bounded; giving up sets the header's status to
+//    IXP_E_TIMEOUT and the kernel carries on without the missing value.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ixp.h"
+
+namespace ixp {
+
+constexpr uint64_t SIGN = 0x8000000000000000ull;
+constexpr unsigned FULL = 0xffffffffu;
+
+__host__ __device__ inline uint64_t enc_first(int64_t i) { return ~(uint64_t)i; }
+__host__ __device__ inline int64_t dec_first(uint64_t k) { return (int64_t)~k; }
+__host__ __device__ inline uint64_t enc_min(int64_t x) { return ~((uint64_t)x ^ SIGN); }
+__host__ __device__ inline int64_t dec_min(uint64_t k) { return (int64_t)(~k ^ SIGN); }
+__host__ __device__ inline uint64_t enc_max(int64_t x) { return (uint64_t)x ^ SIGN; }
+__host__ __device__ inline int64_t dec_max(uint64_t k) { return (int64_t)(k ^ SIGN); }
+
+// Workspace header (256 bytes, zeroed by the host at the start of every call).
+struct Hdr {
+    unsigned long long k_min;     // enc_min of the minimum
+    unsigned long long k_max;     // enc_max of the maximum
+    unsigned long long k_first;   // enc_first of the first violating index
+    unsigned long long k_first2;  // enc_first of a second candidate (Bij: duplicate)
+    unsigned long long k_aux;     // enc_first of a partner / missing value offset
+    unsigned long long cnt0;      // counters
+    unsigned long long cnt1;
+    unsigned long long base;      // bitmap base value (as uint64)
+    unsigned long long span;      // bitmap span in bits
+    unsigned int tile_ctr;        // dynamic tile ticket
+    unsigned int flag;            // "a duplicate was seen"
+    int status;                   // IXP_OK or a device-side error
+    int pad0;
+    unsigned long long total;     // scan / partition total
+    unsigned long long spare[20];
+};
+static_assert(sizeof(Hdr) == 256, "header must be 256 bytes");
+
+constexpr size_t HDR_BYTES = 256;
+
+// ------------------------------------------------------------------ loads
+
+template <typename T> struct Vec;
+template <> struct Vec<int32_t> { using type = int4; static constexpr int N = 4; };
+template <> struct Vec<int64_t> { using type = longlong2; static constexpr int N = 2; };
+
+__device__ __forceinline__ int4 ldv(const int4 *p) { return __ldcs(p); }
+__device__ __forceinline__ longlong2 ldv(const longlong2 *p) { return __ldcs(p); }
+
+__device__ __forceinline__ void unpack(const int4 &v, int64_t (&e)[4]) { e[0] = v.x; e[1] = v.y; e[2] = v.z; e[3] = v.w; }
+__device__ __forceinline__ void unpack(const longlong2 &v, int64_t (&e)[2]) { e[0] = v.x; e[1] = v.y; }
+
+// Split [0, n) of an array at p into a scalar head (up to the first 16-byte
+// boundary), a run of whole 16-byte vectors, and a scalar tail.
+template <typename T> struct Split {
+    int64_t head;   // number of leading scalar elements
+    int64_t nvec;   // number of vectors after the head
+    int64_t tail0;  // first tail element
+    __device__ __forceinline__ Split(const T *p, int64_t n) {
+        constexpr int V = Vec<T>::N;
+        uintptr_t a = reinterpret_cast<uintptr_t>(p);
+        head = (int64_t)(((16 - (a & 15)) & 15) / sizeof(T));
+        if (head > n) head = n;
+        nvec = (n - head) / V;
+        tail0 = head + nvec * V;
+    }
+};
+
+// ------------------------------------------------------------ reductions
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long w = __shfl_xor_sync(FULL, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Block-wide max of `v` (all threads call); result valid in thread 0.
+// `sm` must hold blockDim.x / 32 entries.
+__device__ __forceinline__ unsigned long long block_max_u64(unsigned long long v, unsigned long long *sm) {
+    v = warp_max_u64(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+    if (w == 0) {
+        r = l < (int)(blockDim.x >> 5) ? sm[l] : 0ull;
+        r = warp_max_u64(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, unsigned long long *sm) {
+    v = warp_sum_u64(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sm[w] = v;
+    __syncthreads();
+    unsigned long long r = 0;
+    if (w == 0) {
+        r = l < (int)(blockDim.x >> 5) ? sm[l] : 0ull;
+        r = warp_sum_u64(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ void atomic_max_u64(unsigned long long *p, unsigned long long v) {
+    if (v) atomicMax(p, v);
+}
+
+// ------------------------------------------------------- memory ordering
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void set_status(Hdr *h, int code) { atomicCAS(&h->status, 0, code); }
+
+// ------------------------------------------------------------ element load
+
+template <typename T> __device__ __forceinline__ int64_t ld1(const T *p, int64_t i) { return (int64_t)__ldg(p + i); }
+
+__device__ __forceinline__ int64_t load_index(const void *p, int t, int64_t i) {
+    return t == IXP_I32 ? (int64_t)__ldg((const int32_t *)p + i) : (int64_t)__ldg((const int64_t *)p + i);
+}
+
+// Kernel-execution counter: every kernel's first block bumps its translation
+// unit's counter once, so the host can read how many kernels actually ran.
+static __device__ unsigned long long tu_kernel_count;
+#define IXP_KERNEL_ENTRY()                                                  \
+    do {                                                                    \
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tu_kernel_count, 1ull); \
+    } while (0)
+
+// Launch shape for grid-stride streaming kernels: 8 blocks of 256 threads per SM.
+constexpr int STREAM_THREADS = 256;
+int stream_grid(int64_t work_items, int per_thread = 4);
+int num_sms();
+
+}  // namespace ixp

@@ -1,0 +1,1032 @@
+// scan.cu - scan (Sec. 2.1), stable two-way partition (partition2, Fig. 2;
+// partition2L, Sec. 6), the InvFiltPart check (Sec. 2.3, Fig. 5) and mkSgmDescr
+// (Fig. 2, right).
+//
+// Tiles. A block of 256 threads owns one tile of 1024 16-byte vectors (4096 int32
+// or 2048 int64 elements) in a warp-striped layout: warp w, sub-chunk u, lane l
+// holds vector q = (4w + u) * 32 + l, so every load and store instruction of a warp
+// touches 512 contiguous bytes.
+//
+// Single-pass scan. Tiles take ids from an atomic ticket (so a tile only waits on
+// tiles that are already running), publish their aggregate, and warp 0 looks back
+// over up to 32 predecessors at a time (decoupled look-back: Merrill & Garland,
+// "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016). Segmented
+// sums use the pair operator (f1, v1) + (f2, v2) = (f1 | f2, f2 ? v2 : v1 + v2) of
+// the paper's sgmSum; a predecessor whose aggregate holds a segment head ends the
+// look-back as an inclusive prefix would. Every wait is bounded.
+//
+// Partition / InvFiltPart. Pass 1 counts kept and kept-true elements per tile,
+// turns the counts into exclusive tile prefixes with the same look-back, and
+// records the prefix at every segment start. Pass 2 re-reads the tile, ranks each
+// element inside the tile with warp scans, and writes destinations (partition) or
+// compares them with Z (check). The design moves 20 bytes per element for a
+// partition of int32 keys with a 4-byte payload (16 algorithmic), because the false
+// elements' destinations need the total count of trues before anything is written.
+#include <algorithm>
+#include <cstdlib>
+
+#include "common.cuh"
+
+namespace ixp {
+
+constexpr int TB = 256;  // threads per tile
+constexpr int SUB = 4;   // vectors per thread per tile
+
+struct Wait {
+    long long spin_limit;  // polls before a wait gives up
+    long long skip_tile;   // testing hook: this tile never publishes (-1: none)
+};
+
+static Wait g_wait = {-1, -1};
+
+static Wait wait_config() {
+    if (g_wait.spin_limit < 0) {
+        const char *e = std::getenv("IXP_DEBUG_SPIN_LIMIT");
+        long long v = e ? std::atoll(e) : 0;
+        g_wait.spin_limit = v > 0 ? v : (1ll << 20);
+    }
+    return g_wait;
+}
+
+struct Lookback {
+    unsigned *flag;            // 0 empty, 1 aggregate, 2 inclusive; bit 2: aggregate holds a segment head
+    unsigned long long *agg;   // tile aggregate
+    unsigned long long *incl;  // inclusive prefix through this tile
+};
+
+struct SP {
+    unsigned f;
+    unsigned long long v;
+};
+__device__ __forceinline__ SP sp_op(SP a, SP b) { return SP{a.f | b.f, b.f ? b.v : a.v + b.v}; }
+__device__ __forceinline__ SP shfl_up_sp(SP a, int d) {
+    return SP{__shfl_up_sync(FULL, a.f, d), __shfl_up_sync(FULL, a.v, d)};
+}
+__device__ __forceinline__ SP shfl_down_sp(SP a, int d) {
+    return SP{__shfl_down_sync(FULL, a.f, d), __shfl_down_sync(FULL, a.v, d)};
+}
+__device__ __forceinline__ SP shfl_sp(SP a, int src) { return SP{__shfl_sync(FULL, a.f, src), __shfl_sync(FULL, a.v, src)}; }
+
+// Called by all 32 lanes of one warp. Publishes `agg` for tile t, waits for the
+// predecessors and returns the exclusive prefix of tile t (same value in every lane).
+__device__ SP lookback(const Lookback L, int64_t t, SP agg, Hdr *h, Wait wt) {
+    const int lane = threadIdx.x & 31;
+    const bool publish = t != wt.skip_tile;
+    if (t == 0) {
+        if (lane == 0 && publish) {
+            L.incl[0] = agg.v;
+            st_release_u32(L.flag, 2u | (agg.f << 2));
+        }
+        return SP{0u, 0ull};
+    }
+    if (lane == 0 && publish) {
+        L.agg[t] = agg.v;
+        st_release_u32(L.flag + t, 1u | (agg.f << 2));
+    }
+    SP excl{0u, 0ull};
+    int64_t top = t - 1;
+    long long spins = 0;
+    bool gave_up = false;
+    while (true) {
+        const int64_t j = top - lane;
+        unsigned f = j >= 0 ? ld_acquire_u32(L.flag + j) : 2u;
+        bool virt = j < 0;
+        while (__any_sync(FULL, (f & 3u) == 0u)) {
+            if ((f & 3u) == 0u) f = ld_acquire_u32(L.flag + j);
+            if (++spins > wt.spin_limit) {
+                if ((f & 3u) == 0u) {
+                    f = 2u;
+                    virt = true;
+                    gave_up = true;
+                }
+            } else if (spins > 32) {
+                __nanosleep(64);
+            }
+        }
+        const unsigned stop = __ballot_sync(FULL, (f & 3u) == 2u || (f & 4u));
+        const int L0 = stop ? __ffs(stop) - 1 : 32;
+        SP mine{0u, 0ull};
+        if (lane < L0) {
+            mine = SP{0u, ld_relaxed_u64(L.agg + j)};
+        } else if (lane == L0) {
+            unsigned long long v = 0;
+            if (!virt) v = (f & 3u) == 2u ? ld_relaxed_u64(L.incl + j) : ld_relaxed_u64(L.agg + j);
+            mine = SP{1u, v};
+        }
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            SP o = shfl_down_sp(mine, d);
+            if (lane + d < 32) mine = sp_op(o, mine);
+        }
+        excl = sp_op(shfl_sp(mine, 0), excl);
+        if (L0 < 32) break;
+        top -= 32;
+    }
+    if (gave_up && lane == 0) set_status(h, IXP_E_TIMEOUT);
+    if (lane == 0 && publish) {
+        L.incl[t] = sp_op(excl, agg).v;
+        st_release_u32(L.flag + t, 2u | (agg.f << 2));
+    }
+    return excl;
+}
+
+// ------------------------------------------------------------ segment heads
+
+__device__ __forceinline__ int64_t lb_off(const int64_t *off, int64_t nseg, int64_t key) {
+    int64_t lo = 0, hi = nseg + 1;  // first k in [0, nseg] with off[k] >= key
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t seg_of(const int64_t *off, int64_t nseg, int64_t i) {
+    int64_t lo = 0, hi = nseg;  // last k in [0, nseg) with off[k] <= i
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Mark positions off[k] in [t0, t1) in a shared bitmap of TILE bits.
+template <int TILE>
+__device__ __forceinline__ void mark_heads(unsigned *heads, const int64_t *off, int64_t nseg, int64_t t0, int64_t t1,
+                                           int64_t *s_k) {
+    for (int w = threadIdx.x; w < TILE / 32; w += blockDim.x) heads[w] = 0u;
+    if (threadIdx.x == 0) *s_k = lb_off(off, nseg, t0);
+    __syncthreads();
+    for (int64_t k = *s_k + threadIdx.x; k < nseg; k += blockDim.x) {
+        int64_t o = __ldg(off + k);
+        if (o >= t1) break;
+        if (o >= t0) atomicOr(&heads[(o - t0) >> 5], 1u << ((o - t0) & 31));
+    }
+    __syncthreads();
+}
+
+// ============================================================== scan kernel
+
+template <typename TI, typename TO, bool SEG>
+__global__ void __launch_bounds__(TB) scan_kernel(const TI *__restrict__ in, TO *__restrict__ out, int64_t n,
+                                                  int inclusive, const int64_t *__restrict__ off, int64_t nseg,
+                                                  Lookback L, Hdr *h, Wait wt, TO *total_out, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(TI);
+    constexpr int TILE = TB * SUB * V;
+    __shared__ int64_t s_tile, s_k;
+    __shared__ unsigned heads[SEG ? TILE / 32 : 1];
+    __shared__ SP s_warp[TB / 32];
+    if (threadIdx.x == 0) s_tile = atomicAdd(&h->tile_ctr, 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    if (SEG) mark_heads<TILE>(heads, off, nseg, t0, t1, &s_k);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+
+    unsigned long long a[SUB][V];
+    unsigned hb[SUB];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t q = (int64_t)((w * SUB + u) * 32 + l);
+        const int64_t p0 = t0 + q * V;
+        if (vec_ok && p0 + V <= n) {
+            if (V == 4) {
+                int4 v = __ldcs(reinterpret_cast<const int4 *>(in + p0));
+                a[u][0] = (unsigned long long)(int64_t)v.x;
+                a[u][1 % V] = (unsigned long long)(int64_t)v.y;
+                a[u][2 % V] = (unsigned long long)(int64_t)v.z;
+                a[u][3 % V] = (unsigned long long)(int64_t)v.w;
+            } else {
+                longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(in + p0));
+                a[u][0] = (unsigned long long)v.x;
+                a[u][1 % V] = (unsigned long long)v.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++) a[u][k] = (p0 + k < n) ? (unsigned long long)(int64_t)in[p0 + k] : 0ull;
+        }
+        hb[u] = 0;
+        if (SEG) {
+#pragma unroll
+            for (int k = 0; k < V; k++) {
+                int r = (int)(q * V + k);
+                if (heads[r >> 5] & (1u << (r & 31))) hb[u] |= 1u << k;
+            }
+        }
+    }
+    // warp-level scan, sub-chunk by sub-chunk
+    SP carry{0u, 0ull};
+    SP lane_pre[SUB];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        SP x{0u, 0ull};
+#pragma unroll
+        for (int k = 0; k < V; k++) x = sp_op(x, SP{(hb[u] >> k) & 1u, a[u][k]});
+        SP y = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            SP o = shfl_up_sp(y, d);
+            if (l >= d) y = sp_op(o, y);
+        }
+        SP ex = shfl_up_sp(y, 1);
+        if (l == 0) ex = SP{0u, 0ull};
+        lane_pre[u] = sp_op(carry, ex);
+        carry = sp_op(carry, shfl_sp(y, 31));
+    }
+    if (l == 0) s_warp[w] = carry;
+    __syncthreads();
+    if (w == 0) {
+        SP wt8 = l < TB / 32 ? s_warp[l] : SP{0u, 0ull};
+        SP y = wt8;
+#pragma unroll
+        for (int d = 1; d < TB / 32; d <<= 1) {
+            SP o = shfl_up_sp(y, d);
+            if (l >= d) y = sp_op(o, y);
+        }
+        SP ex = shfl_up_sp(y, 1);
+        if (l == 0) ex = SP{0u, 0ull};
+        SP tile_agg = shfl_sp(y, TB / 32 - 1);
+        SP tile_ex = lookback(L, t, tile_agg, h, wt);
+        __syncwarp();
+        if (l < TB / 32) s_warp[l] = sp_op(tile_ex, ex);
+        if (l == 0 && total_out && t1 == n) *total_out = (TO)sp_op(tile_ex, tile_agg).v;
+    }
+    __syncthreads();
+    const SP pre = s_warp[w];
+    constexpr int VO = 16 / sizeof(TO);
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        SP run = sp_op(pre, lane_pre[u]);
+        TO o[V];
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            run = sp_op(run, SP{(hb[u] >> k) & 1u, a[u][k]});
+            o[k] = (TO)(inclusive ? run.v : run.v - a[u][k]);
+        }
+        if (vec_ok && p0 + V <= n) {
+#pragma unroll
+            for (int c = 0; c < V; c += VO) {
+                if (VO == 4) {
+                    int4 s;
+                    s.x = (int)o[c];
+                    s.y = (int)o[(c + 1) % V];
+                    s.z = (int)o[(c + 2) % V];
+                    s.w = (int)o[(c + 3) % V];
+                    __stcs(reinterpret_cast<int4 *>(out + p0 + c), s);
+                } else {
+                    longlong2 s;
+                    s.x = (long long)o[c];
+                    s.y = (long long)o[(c + 1) % V];
+                    __stcs(reinterpret_cast<longlong2 *>(out + p0 + c), s);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (p0 + k < n) out[p0 + k] = o[k];
+        }
+    }
+}
+
+// Segment totals after a segmented scan: tot[k] = inclusive value at the segment's
+// last element, 0 for an empty segment.
+template <typename TI, typename TO>
+__global__ void seg_totals_kernel(const TI *in, const TO *out, const int64_t *off, int64_t nseg, int64_t n,
+                                  int inclusive, TO *tot) {
+    IXP_KERNEL_ENTRY();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nseg; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = off[k], b = off[k + 1];
+        if (b < a || a < 0 || b > n) b = a;  // invalid offsets: keep accesses in bounds
+        if (b > a) {
+            unsigned long long v = (unsigned long long)(int64_t)out[b - 1];
+            if (!inclusive) v += (unsigned long long)(int64_t)in[b - 1];
+            tot[k] = (TO)v;
+        } else {
+            tot[k] = (TO)0;
+        }
+    }
+}
+
+// ========================================================= predicate counts
+
+struct DPred {
+    int kind;
+    int a;
+    long long b;
+    const uint8_t *flags;
+};
+
+__device__ __forceinline__ bool pred_eval(const DPred &p, int64_t key, int64_t i) {
+    switch (p.kind) {
+        case IXP_P_TRUE: return true;
+        case IXP_P_MOD_EQ: {
+            int64_t r = key % (int64_t)p.a;
+            if (r < 0) r += p.a;
+            return r == p.b;
+        }
+        case IXP_P_LT: return key < p.b;
+        default: return __ldg(p.flags + i) != 0;
+    }
+}
+
+// Loads the V keys of one vector slot (keys may be NULL: zeros).
+template <typename KT, int V>
+__device__ __forceinline__ void load_keys(const KT *keys, int64_t p0, int64_t n, int vec_ok, int64_t (&kv)[V]) {
+    if (!keys) {
+#pragma unroll
+        for (int k = 0; k < V; k++) kv[k] = 0;
+        return;
+    }
+    if (vec_ok && p0 + V <= n) {
+        if (sizeof(KT) == 4) {
+            int4 v = __ldcs(reinterpret_cast<const int4 *>(keys + p0));
+            kv[0] = v.x;
+            kv[1 % V] = v.y;
+            kv[2 % V] = v.z;
+            kv[3 % V] = v.w;
+        } else {
+            longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(keys + p0));
+            kv[0] = v.x;
+            kv[1 % V] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k++) kv[k] = (p0 + k < n) ? (int64_t)keys[p0 + k] : 0;
+    }
+}
+
+// In-tile exclusive counts. Inputs: per sub-chunk u, V-bit masks kt (kept and
+// true) and kk (kept). Output: per u, the packed exclusive count (kk << 16 | kt)
+// of the elements before this thread's vector in the tile, and the tile total.
+template <int V>
+__device__ __forceinline__ unsigned tile_counts(const unsigned (&kt)[SUB], const unsigned (&kk)[SUB],
+                                                unsigned (&pre)[SUB], unsigned *s_warp_u32) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned carry = 0, lp[SUB];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        unsigned x = (unsigned)__popc(kt[u]) | ((unsigned)__popc(kk[u]) << 16);
+        unsigned y = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            unsigned o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y += o;
+        }
+        lp[u] = carry + y - x;
+        carry += __shfl_sync(FULL, y, 31);
+    }
+    if (l == 0) s_warp_u32[w] = carry;
+    __syncthreads();
+    unsigned wpre = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < TB / 32; i++) {
+        unsigned c = s_warp_u32[i];
+        if (i < w) wpre += c;
+        tot += c;
+    }
+#pragma unroll
+    for (int u = 0; u < SUB; u++) pre[u] = wpre + lp[u];
+    __syncthreads();
+    return tot;
+}
+
+__device__ __forceinline__ unsigned long long widen(unsigned packed) {
+    return (unsigned long long)(packed & 0xffffu) | ((unsigned long long)(packed >> 16) << 32);
+}
+
+// Pass 1: per-tile counts -> look-back -> exclusive tile prefixes (packed
+// kept << 32 | kept_true), the grand total in h->total, and the prefix at every
+// segment start in seg_cnt[k] (k = 0..nseg).
+template <typename KT, bool SEG>
+__global__ void __launch_bounds__(TB) count_kernel(const KT *__restrict__ keys, int64_t n, DPred filt, DPred part,
+                                                   const int64_t *__restrict__ off, int64_t nseg, Lookback L,
+                                                   unsigned long long *tile_prefix, unsigned long long *seg_cnt,
+                                                   Hdr *h, Wait wt, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int TILE = TB * SUB * V;
+    __shared__ int64_t s_tile, s_k;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ unsigned s_cnt[SEG ? TILE + 1 : 1];
+    __shared__ unsigned long long s_pre;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&h->tile_ctr, 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned kt[SUB], kk[SUB];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        int64_t kv[V];
+        load_keys<KT, V>(keys, p0, n, vec_ok, kv);
+        kt[u] = kk[u] = 0;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            if (p0 + k < n && pred_eval(filt, kv[k], p0 + k)) {
+                kk[u] |= 1u << k;
+                if (pred_eval(part, kv[k], p0 + k)) kt[u] |= 1u << k;
+            }
+        }
+    }
+    unsigned pre[SUB];
+    const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
+    if (w == 0) {
+        SP ex = lookback(L, t, SP{0u, widen(tot)}, h, wt);
+        if (l == 0) {
+            tile_prefix[t] = ex.v;
+            s_pre = ex.v;
+            if (t1 == n) h->total = ex.v + widen(tot);
+        }
+    }
+    if (SEG) {
+#pragma unroll
+        for (int u = 0; u < SUB; u++) {
+            const int r0 = ((w * SUB + u) * 32 + l) * V;
+#pragma unroll
+            for (int k = 0; k < V; k++) {
+                unsigned below = (1u << k) - 1u;
+                s_cnt[r0 + k] = pre[u] + (unsigned)__popc(kt[u] & below) + ((unsigned)__popc(kk[u] & below) << 16);
+            }
+        }
+        if (threadIdx.x == 0) {
+            s_cnt[TILE] = tot;
+            s_k = lb_off(off, nseg, t0);
+        }
+        __syncthreads();
+        const unsigned long long base = s_pre;
+        const int64_t hi = (t1 == n) ? n : t1 - 1;  // the last tile also owns position n
+        for (int64_t k = s_k + threadIdx.x; k <= nseg; k += blockDim.x) {
+            int64_t o = __ldg(off + k);
+            if (o > hi) break;
+            if (o >= t0) seg_cnt[k] = base + widen(s_cnt[(o - t0) < TILE ? (o - t0) : TILE]);
+        }
+    }
+}
+
+// In-tile segment ids: element position r in the tile belongs to segment
+// k0 + rel[r] where k0 is the segment of the tile's first element.
+template <int V>
+__device__ __forceinline__ void tile_segments(const int64_t *off, int64_t nseg, int64_t t0, int64_t t1, int *s_rel,
+                                              int64_t *s_k0, int (&rel)[SUB][V]) {
+    constexpr int TILE = TB * SUB * V;
+    for (int r = threadIdx.x; r < TILE; r += blockDim.x) s_rel[r] = 0;
+    if (threadIdx.x == 0) *s_k0 = seg_of(off, nseg, t0);
+    __syncthreads();
+    const int64_t k0 = *s_k0;
+    for (int64_t k = k0 + 1 + threadIdx.x; k < nseg; k += blockDim.x) {
+        int64_t o = __ldg(off + k);
+        if (o >= t1) break;
+        if (o > t0) atomicMax(&s_rel[o - t0], (int)(k - k0));
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __shared__ int s_wmax[TB / 32];
+    int carry = 0;
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int r0 = ((w * SUB + u) * 32 + l) * V;
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            m = max(m, s_rel[r0 + k]);
+            rel[u][k] = m;  // running max inside the vector
+        }
+        int y = m;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            int o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y = max(y, o);
+        }
+        int ex = __shfl_up_sync(FULL, y, 1);
+        if (l == 0) ex = 0;
+        ex = max(ex, carry);
+#pragma unroll
+        for (int k = 0; k < V; k++) rel[u][k] = max(rel[u][k], ex);
+        carry = max(carry, __shfl_sync(FULL, y, 31));
+    }
+    if (l == 0) s_wmax[w] = carry;
+    __syncthreads();
+    int wpre = 0;
+    for (int i = 0; i < w; i++) wpre = max(wpre, s_wmax[i]);
+#pragma unroll
+    for (int u = 0; u < SUB; u++)
+#pragma unroll
+        for (int k = 0; k < V; k++) rel[u][k] = max(rel[u][k], wpre);
+    __syncthreads();
+}
+
+// Pass 2 of the partition: destinations, and the scattered keys/payload.
+template <typename KT, typename OT, bool SEG>
+__global__ void __launch_bounds__(TB) partition_write_kernel(
+    const KT *__restrict__ keys, int64_t n, DPred pred, const uint32_t *__restrict__ payload, int row_words,
+    OT *__restrict__ out_idx, KT *__restrict__ out_keys, uint32_t *__restrict__ out_payload,
+    const int64_t *__restrict__ off, int64_t nseg, const unsigned long long *__restrict__ tile_prefix,
+    const unsigned long long *__restrict__ seg_cnt, const Hdr *h, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int TILE = TB * SUB * V;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ int s_rel[SEG ? TILE : 1];
+    __shared__ int64_t s_k0;
+    const int64_t t = blockIdx.x;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned kt[SUB], kk[SUB];
+    int64_t kv[SUB][V];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        load_keys<KT, V>(keys, p0, n, vec_ok, kv[u]);
+        kt[u] = kk[u] = 0;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            if (p0 + k < n) {
+                kk[u] |= 1u << k;
+                if (pred_eval(pred, kv[u][k], p0 + k)) kt[u] |= 1u << k;
+            }
+        }
+    }
+    unsigned pre[SUB];
+    tile_counts<V>(kt, kk, pre, s_w);
+    int rel[SUB][V];
+    if (SEG) tile_segments<V>(off, nseg, t0, t1, s_rel, &s_k0, rel);
+    const unsigned long long tp = tile_prefix[t];
+    const int64_t T = (int64_t)(h->total & 0xffffffffull);
+    const int64_t tile_ct = (int64_t)(tp & 0xffffffffull);
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        OT dst[V];
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            const int64_t i = p0 + k;
+            const unsigned below = (1u << k) - 1u;
+            const int64_t ct = tile_ct + (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & below);  // trues before i
+            const bool c = (kt[u] >> k) & 1u;
+            int64_t d;
+            if (!SEG) {
+                d = c ? ct : T + (i - ct);
+            } else {
+                const int64_t sk = s_k0 + rel[u][k];
+                const int64_t ek = __ldg(off + sk);
+                const int64_t ctk = (int64_t)(__ldg(seg_cnt + sk) & 0xffffffffull);
+                const int64_t tk = (int64_t)(__ldg(seg_cnt + sk + 1) & 0xffffffffull) - ctk;
+                const int64_t tb = ct - ctk;  // trues before i in its segment
+                d = c ? ek + tb : ek + tk + (i - ek) - tb;
+            }
+            dst[k] = (OT)d;
+            if (i < n && d >= 0 && d < n) {  // d is outside [0, n) only for invalid offsets
+                if (out_keys) out_keys[d] = (KT)kv[u][k];
+                if (out_payload)
+                    for (int c2 = 0; c2 < row_words; c2++) out_payload[d * row_words + c2] = payload[i * row_words + c2];
+            }
+        }
+        if (vec_ok && p0 + V <= n && sizeof(OT) * V >= 16) {
+            if (sizeof(OT) == 4) {
+                int4 s;
+                s.x = (int)dst[0];
+                s.y = (int)dst[1 % V];
+                s.z = (int)dst[2 % V];
+                s.w = (int)dst[3 % V];
+                __stcs(reinterpret_cast<int4 *>(out_idx + p0), s);
+            } else {
+#pragma unroll
+                for (int c = 0; c < V; c += 2) {
+                    longlong2 s;
+                    s.x = (long long)dst[c];
+                    s.y = (long long)dst[(c + 1) % V];
+                    __stcs(reinterpret_cast<longlong2 *>(out_idx + p0 + c), s);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (p0 + k < n) out_idx[p0 + k] = dst[k];
+        }
+    }
+}
+
+__global__ void num_true_kernel(const unsigned long long *seg_cnt, const Hdr *h, int64_t nseg, int64_t *num_true) {
+    IXP_KERNEL_ENTRY();
+    if (nseg == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) num_true[0] = (int64_t)(h->total & 0xffffffffull);
+        return;
+    }
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nseg; k += (int64_t)gridDim.x * blockDim.x)
+        num_true[k] = (int64_t)(seg_cnt[k + 1] & 0xffffffffull) - (int64_t)(seg_cnt[k] & 0xffffffffull);
+}
+
+// Pass 2 of the InvFiltPart check: compare Z with the expected destinations.
+// With `witness` set, only the tile holding the first mismatch runs (grid of 1)
+// and it stores that element's expected destination (+1, 0 for dropped) in k_aux.
+template <typename KT, typename ZT, bool SEG>
+__global__ void __launch_bounds__(TB) filtpart_cmp_kernel(
+    const ZT *__restrict__ z, int64_t n, const KT *__restrict__ keys, DPred filt, DPred part,
+    const int64_t *__restrict__ off, int64_t nseg, const unsigned long long *__restrict__ tile_prefix,
+    const unsigned long long *__restrict__ seg_cnt, Hdr *h, int vec_ok, int witness) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int TILE = TB * SUB * V;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ int s_rel[SEG ? TILE : 1];
+    __shared__ int64_t s_k0;
+    int64_t t = blockIdx.x;
+    int64_t target = -1;
+    if (witness) {
+        if (!h->k_first || h->status) return;
+        target = dec_first(h->k_first);
+        t = target / TILE;
+    }
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned kt[SUB], kk[SUB];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        int64_t kv[V];
+        load_keys<KT, V>(keys, p0, n, vec_ok, kv);
+        kt[u] = kk[u] = 0;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            if (p0 + k < n && pred_eval(filt, kv[k], p0 + k)) {
+                kk[u] |= 1u << k;
+                if (pred_eval(part, kv[k], p0 + k)) kt[u] |= 1u << k;
+            }
+        }
+    }
+    unsigned pre[SUB];
+    tile_counts<V>(kt, kk, pre, s_w);
+    int rel[SUB][V];
+    if (SEG) tile_segments<V>(off, nseg, t0, t1, s_rel, &s_k0, rel);
+    const unsigned long long tp = tile_prefix[t];
+    const int64_t Ntot = (int64_t)(h->total >> 32);
+    const int64_t Ttot = (int64_t)(h->total & 0xffffffffull);
+    int64_t bad = INT64_MAX;
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            const int64_t i = p0 + k;
+            if (i >= n) continue;
+            const unsigned below = (1u << k) - 1u;
+            const int64_t ct = (int64_t)(tp & 0xffffffffull) + (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & below);
+            const int64_t ck = (int64_t)(tp >> 32) + (int64_t)(pre[u] >> 16) + __popc(kk[u] & below);
+            const bool kept = (kk[u] >> k) & 1u, c = (kt[u] >> k) & 1u;
+            int64_t ref = -1;
+            if (kept) {
+                int64_t Fk = 0, ctk = 0, ckk = 0, tk = Ttot;
+                if (SEG) {
+                    const int64_t sk = s_k0 + rel[u][k];
+                    const unsigned long long a0 = __ldg(seg_cnt + sk), a1 = __ldg(seg_cnt + sk + 1);
+                    ctk = (int64_t)(a0 & 0xffffffffull);
+                    ckk = (int64_t)(a0 >> 32);
+                    Fk = ckk;
+                    tk = (int64_t)(a1 & 0xffffffffull) - ctk;
+                }
+                const int64_t tb = ct - ctk, kb = ck - ckk;  // trues / kept before i in its segment
+                ref = c ? Fk + tb : Fk + tk + (kb - tb);
+            }
+            const int64_t zi = (int64_t)z[i];
+            const bool wrong = kept ? (zi != ref) : (zi >= 0 && zi < Ntot);
+            if (wrong) bad = i < bad ? i : bad;
+            if (witness && i == target) h->cnt1 = (unsigned long long)(ref + 1);
+        }
+    }
+    if (witness) return;
+    __shared__ unsigned long long sm[TB / 32];
+    unsigned long long r = block_max_u64(bad == INT64_MAX ? 0ull : enc_first(bad), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+}
+
+template <typename ZT>
+__global__ void filtpart_finalize(const ZT *z, const Hdr *h, ixp_verdict *out) {
+    IXP_KERNEL_ENTRY();
+    ixp_verdict v;
+    v.status = h->status;
+    v.reserved = 0;
+    const int64_t i = h->k_first ? dec_first(h->k_first) : -1;
+    v.ok = v.status ? -1 : (i < 0 ? 1 : 0);
+    v.kind = (v.status || i < 0) ? IXP_V_NONE : IXP_V_WRONG_DEST;
+    v.index = v.status ? -1 : i;
+    v.value = (v.status || i < 0) ? 0 : (int64_t)z[i];
+    v.aux0 = (int64_t)(h->total >> 32);
+    v.aux1 = (v.status || i < 0) ? 0 : (int64_t)h->cnt1 - 1;
+    *out = v;
+}
+
+// ============================================================== mkSgmDescr
+
+__global__ void shape_check_kernel(const int64_t *shape, int64_t m, int32_t *status) {
+    IXP_KERNEL_ENTRY();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x)
+        if (shape[k] < 0) atomicCAS(status, 0, IXP_E_INVAL);
+}
+
+template <typename OT>
+__global__ void flags_scatter_kernel(const int64_t *shape, const int64_t *xs, const int64_t *offs, int64_t m,
+                                     OT *out, int64_t out_len, const int32_t *status) {
+    IXP_KERNEL_ENTRY();
+    if (*status) return;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t e = offs[k];
+        if (shape[k] > 0 && e >= 0 && e < out_len) out[e] = (OT)(xs ? xs[k] : 1);
+    }
+}
+
+__global__ void status_copy_kernel(const Hdr *h, int32_t *d_status) {
+    IXP_KERNEL_ENTRY();
+    if (h->status) atomicCAS(d_status, 0, h->status);
+}
+
+// ================================================================ host side
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static int launch_status() { return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA; }
+
+static int64_t ntiles_for(int64_t n, int V) { return (n + (int64_t)TB * SUB * V - 1) / ((int64_t)TB * SUB * V); }
+
+// Workspace layout for the tiled passes (all offsets 256-aligned):
+//   header | flags u32[T] | agg u64[T] | incl u64[T] | tile_prefix u64[T] | seg_cnt u64[nseg+1]
+struct TileWs {
+    Hdr *h;
+    Lookback L;
+    unsigned long long *tile_prefix;
+    unsigned long long *seg_cnt;
+    size_t bytes;
+};
+
+static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static TileWs tile_ws(void *ws, int64_t ntiles, int64_t nseg) {
+    TileWs r;
+    char *p = (char *)ws;
+    size_t o = HDR_BYTES;
+    r.h = (Hdr *)p;
+    r.L.flag = (unsigned *)(p + o);
+    o += up256((size_t)ntiles * 4);
+    r.L.agg = (unsigned long long *)(p + o);
+    o += up256((size_t)ntiles * 8);
+    r.L.incl = (unsigned long long *)(p + o);
+    o += up256((size_t)ntiles * 8);
+    r.tile_prefix = (unsigned long long *)(p + o);
+    o += up256((size_t)ntiles * 8);
+    r.seg_cnt = (unsigned long long *)(p + o);
+    o += up256((size_t)(nseg + 1) * 8);
+    r.bytes = o;
+    return r;
+}
+
+size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg) {
+    int64_t nt = ntiles_for(n, V);
+    return tile_ws(nullptr, nt, nseg < 0 ? 0 : nseg).bytes;
+}
+
+static int ws_ok(void *ws, size_t have, size_t need) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || have < need) return IXP_E_WORKSPACE;
+    return IXP_OK;
+}
+
+static DPred dpred(const ixp_pred &p) { return DPred{p.kind, p.a, (long long)p.b, p.flags}; }
+
+static bool pred_ok(const ixp_pred &p, bool have_keys) {
+    switch (p.kind) {
+        case IXP_P_TRUE: return true;
+        case IXP_P_MOD_EQ: return have_keys && p.a > 0;
+        case IXP_P_LT: return have_keys;
+        case IXP_P_FLAGS: return p.flags != nullptr;
+        default: return false;
+    }
+}
+
+template <typename TI, typename TO>
+static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs segs, TO *tot, int32_t *d_status,
+                    void *ws, size_t ws_bytes, cudaStream_t st, bool keep_status = false) {
+    constexpr int V = 16 / sizeof(TI);
+    const bool seg = segs.offsets != nullptr;
+    const int64_t nt = ntiles_for(n, V);
+    TileWs W = tile_ws(ws, nt, seg ? segs.nseg : 0);
+    int rc = ws_ok(ws, ws_bytes, W.bytes);
+    if (rc) return rc;
+    if (cudaMemsetAsync(ws, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (nt > 0 && cudaMemsetAsync(W.L.flag, 0, (size_t)nt * 4, st) != cudaSuccess) return IXP_E_CUDA;
+    if (d_status && !keep_status && cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return IXP_E_CUDA;
+    if (!seg && tot && n == 0 && cudaMemsetAsync(tot, 0, sizeof(TO), st) != cudaSuccess) return IXP_E_CUDA;
+    const int vec = aligned16(in) && aligned16(out);
+    const Wait wt = wait_config();
+    if (nt > 0) {
+        if (seg)
+            scan_kernel<TI, TO, true><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, segs.offsets, segs.nseg,
+                                                                  W.L, W.h, wt, nullptr, vec);
+        else
+            scan_kernel<TI, TO, false><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, nullptr, 0, W.L, W.h, wt,
+                                                                   tot, vec);
+    }
+    if (seg && tot && segs.nseg > 0) {
+        int g = (int)std::min<int64_t>((segs.nseg + 255) / 256, 4096);
+        seg_totals_kernel<TI, TO><<<g, 256, 0, st>>>(in, out, segs.offsets, segs.nseg, n, inclusive, tot);
+    }
+    if (d_status) status_copy_kernel<<<1, 1, 0, st>>>(W.h, d_status);
+    return launch_status();
+}
+
+template <typename KT>
+static int run_counts(const KT *keys, int64_t n, DPred filt, DPred part, ixp_segs segs, TileWs &W, int64_t nt,
+                      int vec, cudaStream_t st) {
+    const bool seg = segs.offsets != nullptr;
+    if (cudaMemsetAsync(W.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (nt > 0 && cudaMemsetAsync(W.L.flag, 0, (size_t)nt * 4, st) != cudaSuccess) return IXP_E_CUDA;
+    if (seg && cudaMemsetAsync(W.seg_cnt, 0, (size_t)(segs.nseg + 1) * 8, st) != cudaSuccess) return IXP_E_CUDA;
+    const Wait wt = wait_config();
+    if (nt > 0) {
+        if (seg)
+            count_kernel<KT, true><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, segs.offsets, segs.nseg, W.L,
+                                                               W.tile_prefix, W.seg_cnt, W.h, wt, vec);
+        else
+            count_kernel<KT, false><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, nullptr, 0, W.L, W.tile_prefix,
+                                                                nullptr, W.h, wt, vec);
+    }
+    return IXP_OK;
+}
+
+template <typename KT, typename OT>
+static int run_partition(const KT *keys, int64_t n, ixp_pred pred, const void *payload, int row_bytes, OT *out_idx,
+                         KT *out_keys, void *out_payload, int64_t *num_true, ixp_segs segs, int32_t *d_status,
+                         void *ws, size_t ws_bytes, cudaStream_t st) {
+    constexpr int V = 16 / sizeof(KT);
+    const bool seg = segs.offsets != nullptr;
+    const int64_t nt = ntiles_for(n, V);
+    TileWs W = tile_ws(ws, nt, seg ? segs.nseg : 0);
+    int rc = ws_ok(ws, ws_bytes, W.bytes);
+    if (rc) return rc;
+    const int vec = (keys == nullptr || aligned16(keys)) && aligned16(out_idx);
+    const DPred all{IXP_P_TRUE, 0, 0, nullptr};
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return IXP_E_CUDA;
+    rc = run_counts<KT>(keys, n, all, dpred(pred), segs, W, nt, vec, st);
+    if (rc) return rc;
+    if (nt > 0) {
+        if (seg)
+            partition_write_kernel<KT, OT, true><<<(unsigned)nt, TB, 0, st>>>(
+                keys, n, dpred(pred), (const uint32_t *)payload, row_bytes / 4, out_idx, out_keys,
+                (uint32_t *)out_payload, segs.offsets, segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec);
+        else
+            partition_write_kernel<KT, OT, false><<<(unsigned)nt, TB, 0, st>>>(
+                keys, n, dpred(pred), (const uint32_t *)payload, row_bytes / 4, out_idx, out_keys,
+                (uint32_t *)out_payload, nullptr, 0, W.tile_prefix, nullptr, W.h, vec);
+    }
+    const int64_t ns = seg ? segs.nseg : 0;
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>((ns + 255) / 256, 4096));
+    num_true_kernel<<<g, 256, 0, st>>>(W.seg_cnt, W.h, ns, num_true);
+    if (d_status) status_copy_kernel<<<1, 1, 0, st>>>(W.h, d_status);
+    return launch_status();
+}
+
+template <typename KT, typename ZT>
+static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, ixp_pred part, ixp_segs segs,
+                        ixp_verdict *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+    constexpr int V = 16 / sizeof(KT);
+    const bool seg = segs.offsets != nullptr;
+    const int64_t nt = ntiles_for(n, V);
+    TileWs W = tile_ws(ws, nt, seg ? segs.nseg : 0);
+    int rc = ws_ok(ws, ws_bytes, W.bytes);
+    if (rc) return rc;
+    const int vec = keys == nullptr || aligned16(keys);
+    rc = run_counts<KT>(keys, n, dpred(filt), dpred(part), segs, W, nt, vec, st);
+    if (rc) return rc;
+    if (nt > 0) {
+        if (seg) {
+            filtpart_cmp_kernel<KT, ZT, true><<<(unsigned)nt, TB, 0, st>>>(
+                z, n, keys, dpred(filt), dpred(part), segs.offsets, segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec, 0);
+            filtpart_cmp_kernel<KT, ZT, true><<<1, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), segs.offsets,
+                                                               segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec, 1);
+        } else {
+            filtpart_cmp_kernel<KT, ZT, false><<<(unsigned)nt, TB, 0, st>>>(
+                z, n, keys, dpred(filt), dpred(part), nullptr, 0, W.tile_prefix, nullptr, W.h, vec, 0);
+            filtpart_cmp_kernel<KT, ZT, false><<<1, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), nullptr, 0,
+                                                                W.tile_prefix, nullptr, W.h, vec, 1);
+        }
+    }
+    filtpart_finalize<ZT><<<1, 1, 0, st>>>(z, W.h, out);
+    return launch_status();
+}
+
+}  // namespace ixp
+
+using namespace ixp;
+
+extern "C" int ixp_scan(const void *in, int in_type, void *out, int out_type, int64_t n, int inclusive, ixp_segs segs,
+                        void *d_totals, int32_t *d_status, void *ws, size_t ws_bytes, ixp_stream stream) {
+    if ((in_type != IXP_I32 && in_type != IXP_I64) || (out_type != IXP_I32 && out_type != IXP_I64) ||
+        (in_type == IXP_I64 && out_type == IXP_I32))
+        return IXP_E_DTYPE;
+    if (n < 0 || (n > 0 && (!in || !out))) return IXP_E_INVAL;
+    if ((segs.offsets && segs.nseg < 1) || (!segs.offsets && segs.nseg != 0)) return IXP_E_INVAL;
+    const int es = in_type == IXP_I32 ? 4 : 8, eo = out_type == IXP_I32 ? 4 : 8;
+    if ((reinterpret_cast<uintptr_t>(in) % es) || (reinterpret_cast<uintptr_t>(out) % eo)) return IXP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (in_type == IXP_I32 && out_type == IXP_I32)
+        return run_scan((const int32_t *)in, (int32_t *)out, n, inclusive, segs, (int32_t *)d_totals, d_status, ws,
+                        ws_bytes, st);
+    if (in_type == IXP_I32)
+        return run_scan((const int32_t *)in, (int64_t *)out, n, inclusive, segs, (int64_t *)d_totals, d_status, ws,
+                        ws_bytes, st);
+    return run_scan((const int64_t *)in, (int64_t *)out, n, inclusive, segs, (int64_t *)d_totals, d_status, ws,
+                    ws_bytes, st);
+}
+
+extern "C" int ixp_partition(const void *keys, int ktype, int64_t n, ixp_pred pred, const void *payload,
+                             int32_t row_bytes, void *out_indices, int out_type, void *out_keys, void *out_payload,
+                             int64_t *d_num_true, ixp_segs segs, int32_t *d_status, void *ws, size_t ws_bytes,
+                             ixp_stream stream) {
+    if ((keys && ktype != IXP_I32 && ktype != IXP_I64) || (out_type != IXP_I32 && out_type != IXP_I64))
+        return IXP_E_DTYPE;
+    if (n < 0 || n >= (1ll << 32) || (n > 0 && !out_indices) || !d_num_true || !pred_ok(pred, keys != nullptr))
+        return IXP_E_INVAL;
+    if (out_type == IXP_I32 && n > INT32_MAX) return IXP_E_INVAL;
+    if ((out_keys && !keys) || (out_payload && (!payload || row_bytes <= 0 || row_bytes % 4 || row_bytes > 64)))
+        return IXP_E_INVAL;
+    if ((segs.offsets && segs.nseg < 1) || (!segs.offsets && segs.nseg != 0)) return IXP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool k64 = keys && ktype == IXP_I64;
+    if (!k64) {
+        if (out_type == IXP_I32)
+            return run_partition((const int32_t *)keys, n, pred, payload, row_bytes, (int32_t *)out_indices,
+                                 (int32_t *)out_keys, out_payload, d_num_true, segs, d_status, ws, ws_bytes, st);
+        return run_partition((const int32_t *)keys, n, pred, payload, row_bytes, (int64_t *)out_indices,
+                             (int32_t *)out_keys, out_payload, d_num_true, segs, d_status, ws, ws_bytes, st);
+    }
+    if (out_type == IXP_I32)
+        return run_partition((const int64_t *)keys, n, pred, payload, row_bytes, (int32_t *)out_indices,
+                             (int64_t *)out_keys, out_payload, d_num_true, segs, d_status, ws, ws_bytes, st);
+    return run_partition((const int64_t *)keys, n, pred, payload, row_bytes, (int64_t *)out_indices,
+                         (int64_t *)out_keys, out_payload, d_num_true, segs, d_status, ws, ws_bytes, st);
+}
+
+extern "C" int ixp_check_filtpart(const void *z, int ztype, int64_t n, const void *keys, int ktype, ixp_pred filt,
+                                  ixp_pred part, ixp_segs segs, ixp_verdict *d_verdict, void *ws, size_t ws_bytes,
+                                  ixp_stream stream) {
+    if ((ztype != IXP_I32 && ztype != IXP_I64) || (keys && ktype != IXP_I32 && ktype != IXP_I64)) return IXP_E_DTYPE;
+    if (n < 0 || n >= (1ll << 32) || (n > 0 && !z) || !d_verdict) return IXP_E_INVAL;
+    if (!pred_ok(filt, keys != nullptr) || !pred_ok(part, keys != nullptr)) return IXP_E_INVAL;
+    if ((segs.offsets && segs.nseg < 1) || (!segs.offsets && segs.nseg != 0)) return IXP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool k64 = keys && ktype == IXP_I64;
+    if (!k64) {
+        if (ztype == IXP_I32)
+            return run_filtpart((const int32_t *)z, n, (const int32_t *)keys, filt, part, segs, d_verdict, ws, ws_bytes,
+                                st);
+        return run_filtpart((const int64_t *)z, n, (const int32_t *)keys, filt, part, segs, d_verdict, ws, ws_bytes,
+                            st);
+    }
+    if (ztype == IXP_I32)
+        return run_filtpart((const int32_t *)z, n, (const int64_t *)keys, filt, part, segs, d_verdict, ws, ws_bytes,
+                            st);
+    return run_filtpart((const int64_t *)z, n, (const int64_t *)keys, filt, part, segs, d_verdict, ws, ws_bytes, st);
+}
+
+extern "C" int ixp_flags_from_shape(const int64_t *shape, int64_t m, const int64_t *xs, void *out, int out_type,
+                                    int64_t out_len, int64_t *d_offsets, int32_t *d_status, void *ws, size_t ws_bytes,
+                                    ixp_stream stream) {
+    if (out_type != IXP_I32 && out_type != IXP_I64) return IXP_E_DTYPE;
+    if (m < 0 || (m > 0 && !shape) || out_len < 0 || (out_len > 0 && !out) || !d_offsets || !d_status)
+        return IXP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    // scan workspace first, then nothing else is needed (offsets live in d_offsets)
+    if (cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return IXP_E_CUDA;
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, 4096));
+    if (m > 0) shape_check_kernel<<<g, 256, 0, st>>>(shape, m, d_status);
+    const ixp_segs flat{nullptr, 0};
+    int rc = run_scan(shape, d_offsets, m, 0, flat, d_offsets + m, d_status, ws, ws_bytes, st, true);
+    if (rc) return rc;
+    if (out_len > 0) {
+        const size_t es = out_type == IXP_I32 ? 4 : 8;
+        if (cudaMemsetAsync(out, 0, (size_t)out_len * es, st) != cudaSuccess) return IXP_E_CUDA;
+        if (m > 0) {
+            if (out_type == IXP_I32)
+                flags_scatter_kernel<int32_t><<<g, 256, 0, st>>>(shape, xs, d_offsets, m, (int32_t *)out, out_len,
+                                                                 d_status);
+            else
+                flags_scatter_kernel<int64_t><<<g, 256, 0, st>>>(shape, xs, d_offsets, m, (int64_t *)out, out_len,
+                                                                 d_status);
+        }
+    }
+    return launch_status();
+}
+
+extern "C" int ixp_debug_set_wait(long long spin_limit, long long skip_tile) {
+    ixp::g_wait.spin_limit = spin_limit > 0 ? spin_limit : (1ll << 20);
+    ixp::g_wait.skip_tile = skip_tile;
+    return IXP_OK;
+}
+
+extern "C" unsigned long long ixp_tu_kernels_scan(void) {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, ixp::tu_kernel_count, sizeof(v)) != cudaSuccess) return 0;
+    return v;
+}

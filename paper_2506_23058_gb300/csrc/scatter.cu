@@ -1,0 +1,215 @@
+// scatter.cu - scatter and gather of payload rows (Sec. 2.1: scatter ignores
+// indices outside the destination), the additive scatter used as the adjoint of
+// gather, and the float64 -> float32 rounding of its accumulator.
+//
+// One thread moves one row. Rows whose size is a multiple of 16 bytes (with
+// 16-byte aligned bases) move as int4 vectors, so an [n x 8] float32 payload row is
+// one 32-byte sector per access.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace ixp {
+
+template <typename IT>
+__global__ void __launch_bounds__(STREAM_THREADS) scatter_rows_kernel(char *__restrict__ dst, int64_t dst_len,
+                                                                      const IT *__restrict__ idx,
+                                                                      const char *__restrict__ vals, int64_t n,
+                                                                      int row_bytes, int vec16) {
+    IXP_KERNEL_ENTRY();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t d = (int64_t)__ldg(idx + i);
+        if (d < 0 || d >= dst_len) continue;
+        if (vec16) {
+            const int4 *s = reinterpret_cast<const int4 *>(vals + i * row_bytes);
+            int4 *t = reinterpret_cast<int4 *>(dst + d * row_bytes);
+            for (int c = 0; c < row_bytes / 16; c++) t[c] = __ldcs(s + c);
+        } else {
+            const uint32_t *s = reinterpret_cast<const uint32_t *>(vals + i * row_bytes);
+            uint32_t *t = reinterpret_cast<uint32_t *>(dst + d * row_bytes);
+            for (int c = 0; c < row_bytes / 4; c++) t[c] = s[c];
+        }
+    }
+}
+
+template <typename IT, typename FT>
+__global__ void __launch_bounds__(STREAM_THREADS) scatter_add_kernel(FT *__restrict__ dst, int64_t dst_len,
+                                                                     const IT *__restrict__ idx,
+                                                                     const FT *__restrict__ vals, int64_t n,
+                                                                     int row_elems) {
+    IXP_KERNEL_ENTRY();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t d = (int64_t)__ldg(idx + i);
+        if (d < 0 || d >= dst_len) continue;
+        for (int c = 0; c < row_elems; c++) atomicAdd(dst + d * row_elems + c, vals[i * row_elems + c]);
+    }
+}
+
+// Additive scatter of float32 rows into a float64 accumulator. Lanes of a warp
+// that hit the same target are found with match_any; each such group is summed
+// with a masked shuffle tree (in float64) and its lowest lane issues the atomics,
+// so a hot target costs one atomic per warp instead of one per element.
+template <typename IT>
+__global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double *__restrict__ acc, int64_t dst_len,
+                                                                         const IT *__restrict__ idx,
+                                                                         const float *__restrict__ vals, int64_t n,
+                                                                         int row_elems) {
+    IXP_KERNEL_ENTRY();
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (int64_t base = tid - lane; base < n; base += stride) {
+        const int64_t i = base + lane;
+        const bool live = i < n;
+        int64_t d = live ? (int64_t)__ldg(idx + i) : -1;
+        if (d < 0 || d >= dst_len) d = -1;
+        const unsigned peers = __match_any_sync(FULL, (unsigned long long)d);
+        const bool single = __popc(peers) == 1;
+        if (d >= 0 && single)
+            for (int c = 0; c < row_elems; c++) atomicAdd(acc + d * row_elems + c, (double)vals[i * row_elems + c]);
+        // groups of two or more lanes: one leader per group
+        unsigned todo = __ballot_sync(FULL, !single && d >= 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            const int64_t key = __shfl_sync(FULL, d, src);
+            const unsigned grp = __ballot_sync(FULL, d == key);
+            todo &= ~grp;
+            for (int c = 0; c < row_elems; c++) {
+                double v = (d == key) ? (double)vals[i * row_elems + c] : 0.0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+                if (lane == src) atomicAdd(acc + key * row_elems + c, v);
+            }
+        }
+    }
+}
+
+__global__ void f64_to_f32_kernel(float *__restrict__ out, const double *__restrict__ acc, int64_t count) {
+    IXP_KERNEL_ENTRY();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += stride) out[i] = (float)acc[i];
+}
+
+template <typename IT>
+__global__ void __launch_bounds__(STREAM_THREADS) gather_rows_kernel(char *__restrict__ out,
+                                                                     const char *__restrict__ src, int64_t src_len,
+                                                                     const IT *__restrict__ idx, int64_t n,
+                                                                     int row_bytes, int vec16, int32_t *status) {
+    IXP_KERNEL_ENTRY();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t s = (int64_t)__ldg(idx + i);
+        const bool ok = s >= 0 && s < src_len;
+        if (!ok && status) atomicCAS(status, 0, IXP_E_OOB);
+        if (vec16) {
+            int4 *t = reinterpret_cast<int4 *>(out + i * row_bytes);
+            const int4 *f = reinterpret_cast<const int4 *>(src + (ok ? s : 0) * row_bytes);
+            for (int c = 0; c < row_bytes / 16; c++) __stcs(t + c, ok ? __ldg(f + c) : make_int4(0, 0, 0, 0));
+        } else {
+            uint32_t *t = reinterpret_cast<uint32_t *>(out + i * row_bytes);
+            const uint32_t *f = reinterpret_cast<const uint32_t *>(src + (ok ? s : 0) * row_bytes);
+            for (int c = 0; c < row_bytes / 4; c++) t[c] = ok ? __ldg(f + c) : 0u;
+        }
+    }
+}
+
+static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+static int row_grid(int64_t n) { return stream_grid(n, 1); }
+
+}  // namespace ixp
+
+using namespace ixp;
+
+extern "C" int ixp_scatter(void *dst, int64_t dst_len, const void *idx, int itype, const void *vals, int64_t n,
+                           int32_t row_elems, int32_t elem_bytes, int32_t mode, ixp_stream stream) {
+    if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
+    if (elem_bytes != 4 && elem_bytes != 8) return IXP_E_DTYPE;
+    if (n < 0 || dst_len < 0 || row_elems <= 0 || row_elems > 64 || (n > 0 && (!idx || !vals)) ||
+        (dst_len > 0 && !dst) || (mode != IXP_SCATTER_ASSIGN && mode != IXP_SCATTER_ADD))
+        return IXP_E_INVAL;
+    if (!al(idx, itype == IXP_I32 ? 4 : 8) || !al(vals, elem_bytes) || !al(dst, elem_bytes)) return IXP_E_INVAL;
+    if (n == 0) return IXP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int rb = row_elems * elem_bytes;
+    const int g = row_grid(n);
+    if (mode == IXP_SCATTER_ASSIGN) {
+        const int v16 = (rb % 16 == 0) && al(dst, 16) && al(vals, 16);
+        if (itype == IXP_I32)
+            scatter_rows_kernel<int32_t><<<g, STREAM_THREADS, 0, st>>>((char *)dst, dst_len, (const int32_t *)idx,
+                                                                       (const char *)vals, n, rb, v16);
+        else
+            scatter_rows_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>((char *)dst, dst_len, (const int64_t *)idx,
+                                                                       (const char *)vals, n, rb, v16);
+    } else if (elem_bytes == 4) {
+        if (itype == IXP_I32)
+            scatter_add_kernel<int32_t, float><<<g, STREAM_THREADS, 0, st>>>((float *)dst, dst_len, (const int32_t *)idx,
+                                                                             (const float *)vals, n, row_elems);
+        else
+            scatter_add_kernel<int64_t, float><<<g, STREAM_THREADS, 0, st>>>((float *)dst, dst_len, (const int64_t *)idx,
+                                                                             (const float *)vals, n, row_elems);
+    } else {
+        if (itype == IXP_I32)
+            scatter_add_kernel<int32_t, double><<<g, STREAM_THREADS, 0, st>>>(
+                (double *)dst, dst_len, (const int32_t *)idx, (const double *)vals, n, row_elems);
+        else
+            scatter_add_kernel<int64_t, double><<<g, STREAM_THREADS, 0, st>>>(
+                (double *)dst, dst_len, (const int64_t *)idx, (const double *)vals, n, row_elems);
+    }
+    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+extern "C" int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const void *idx, int itype, const float *vals,
+                                          int64_t n, int32_t row_elems, ixp_stream stream) {
+    if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
+    if (n < 0 || dst_len < 0 || row_elems <= 0 || row_elems > 64 || (n > 0 && (!idx || !vals)) || (dst_len > 0 && !acc))
+        return IXP_E_INVAL;
+    if (!al(idx, itype == IXP_I32 ? 4 : 8) || !al(vals, 4) || !al(acc, 8)) return IXP_E_INVAL;
+    if (n == 0) return IXP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int g = row_grid(n);
+    if (itype == IXP_I32)
+        scatter_add_f64_kernel<int32_t><<<g, STREAM_THREADS, 0, st>>>(acc, dst_len, (const int32_t *)idx, vals, n,
+                                                                      row_elems);
+    else
+        scatter_add_f64_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>(acc, dst_len, (const int64_t *)idx, vals, n,
+                                                                      row_elems);
+    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+extern "C" int ixp_f64_to_f32(float *out, const double *acc, int64_t count, ixp_stream stream) {
+    if (count < 0 || (count > 0 && (!out || !acc))) return IXP_E_INVAL;
+    if (count == 0) return IXP_OK;
+    f64_to_f32_kernel<<<stream_grid(count, 4), STREAM_THREADS, 0, (cudaStream_t)stream>>>(out, acc, count);
+    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+extern "C" int ixp_gather(void *out, const void *src, int64_t src_len, const void *idx, int itype, int64_t n,
+                          int32_t row_elems, int32_t elem_bytes, int32_t *d_status, ixp_stream stream) {
+    if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
+    if (elem_bytes != 4 && elem_bytes != 8) return IXP_E_DTYPE;
+    if (n < 0 || src_len < 0 || row_elems <= 0 || row_elems > 64 || (n > 0 && (!idx || !out)) ||
+        (src_len > 0 && !src))
+        return IXP_E_INVAL;
+    if (!al(idx, itype == IXP_I32 ? 4 : 8) || !al(out, elem_bytes) || !al(src, elem_bytes)) return IXP_E_INVAL;
+    if (n == 0) return IXP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int rb = row_elems * elem_bytes;
+    const int v16 = (rb % 16 == 0) && al(out, 16) && al(src, 16);
+    const int g = row_grid(n);
+    if (itype == IXP_I32)
+        gather_rows_kernel<int32_t><<<g, STREAM_THREADS, 0, st>>>((char *)out, (const char *)src, src_len,
+                                                                  (const int32_t *)idx, n, rb, v16, d_status);
+    else
+        gather_rows_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>((char *)out, (const char *)src, src_len,
+                                                                  (const int64_t *)idx, n, rb, v16, d_status);
+    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+extern "C" unsigned long long ixp_tu_kernels_scatter(void) {
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, ixp::tu_kernel_count, sizeof(v)) != cudaSuccess) return 0;
+    return v;
+}

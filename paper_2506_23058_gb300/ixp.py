@@ -1,0 +1,360 @@
+"""Python binding of the C ABI in include/ixp.h (ctypes; argument marshalling only).
+
+Every function here takes torch CUDA tensors, passes their device pointers, sizes
+and the current CUDA stream to the library, and returns device tensors. All work
+runs in the library's kernels; if the library cannot be loaded the call raises.
+torch supplies device memory (workspaces come from its caching allocator) and
+streams, nothing else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import torch
+
+from . import build as _build
+
+I64MIN = -(2**63)
+I64MAX = 2**63 - 1
+
+KINDS = ["none", "out_of_range", "order", "duplicate", "out_of_image", "missing", "wrong_dest"]
+CMPS = {"le": 0, "lt": 1, "ge": 2, "gt": 3}
+PREDS = {"true": 0, "mod_eq": 1, "lt": 2, "flags": 3}
+OPS = {"range": 0, "mono": 1, "inj": 2, "bij": 3, "filtpart": 4, "scan": 5, "partition": 6, "flags": 7}
+ERRORS = {0: "ok", -1: "invalid argument", -2: "unsupported element type", -3: "value span exceeds the workspace",
+          -4: "workspace too small", -5: "CUDA launch failed", -6: "bounded device wait gave up",
+          -7: "index out of bounds"}
+
+
+class IxpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Pred(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("a", C.c_int32), ("b", C.c_int64), ("flags", C.c_void_p)]
+
+
+class Segs(C.Structure):
+    _fields_ = [("offsets", C.c_void_p), ("nseg", C.c_int64)]
+
+
+_P = C.c_void_p
+_I = C.c_int
+_L = C.c_int64
+_Z = C.c_size_t
+
+_SIGS = {
+    "ixp_workspace_size": (_Z, [_I, _I, _L, _L]),
+    "ixp_strerror": (C.c_char_p, [_I]),
+    "ixp_version": (_I, []),
+    "ixp_check_range": (_I, [_P, _I, _L, _L, _L, _P, _P, _Z, _P]),
+    "ixp_check_mono": (_I, [_P, _I, _L, _I, Segs, _P, _P, _P, _Z, _P]),
+    "ixp_check_inj": (_I, [_P, _I, _L, _L, _L, _P, _P, _Z, _P]),
+    "ixp_check_bij": (_I, [_P, _I, _L, _L, _L, _L, _L, _P, _P, _Z, _P]),
+    "ixp_check_filtpart": (_I, [_P, _I, _L, _P, _I, Pred, Pred, Segs, _P, _P, _Z, _P]),
+    "ixp_scan": (_I, [_P, _I, _P, _I, _L, _I, Segs, _P, _P, _P, _Z, _P]),
+    "ixp_partition": (_I, [_P, _I, _L, Pred, _P, C.c_int32, _P, _I, _P, _P, _P, Segs, _P, _P, _Z, _P]),
+    "ixp_scatter": (_I, [_P, _L, _P, _I, _P, _L, C.c_int32, C.c_int32, C.c_int32, _P]),
+    "ixp_scatter_add_f32_to_f64": (_I, [_P, _L, _P, _I, _P, _L, C.c_int32, _P]),
+    "ixp_f64_to_f32": (_I, [_P, _P, _L, _P]),
+    "ixp_gather": (_I, [_P, _P, _L, _P, _I, _L, C.c_int32, C.c_int32, _P, _P]),
+    "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
+    "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
+    "ixp_kernel_launches": (C.c_ulonglong, []),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads libixp.so (building it first if asked). Raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library {path} is missing or stale; call paper_2506_23058_gb300.build.build()")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ck(code: int, what: str):
+    if code != 0:
+        raise IxpError(code, what)
+
+
+def _itype(t: torch.Tensor) -> int:
+    if t.dtype == torch.int32:
+        return 0
+    if t.dtype == torch.int64:
+        return 1
+    raise IxpError(-2, f"index arrays are int32 or int64, not {t.dtype}")
+
+
+def _dev(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _segs(offsets):
+    if offsets is None:
+        return Segs(None, 0)
+    return Segs(_dev(offsets, "offsets"), offsets.numel() - 1)
+
+
+def make_pred(kind="true", a=0, b=0, flags=None) -> Pred:
+    """Predicate: 'true', 'mod_eq' (floored key mod a == b), 'lt' (key < b), 'flags' (flags[i] != 0)."""
+    if isinstance(kind, Pred):
+        return kind
+    if isinstance(kind, (tuple, list)):
+        return make_pred(*kind)
+    fp = None
+    if kind == "flags":
+        if flags is None or flags.dtype != torch.uint8:
+            raise ValueError("flags predicate needs a uint8 CUDA tensor")
+        fp = _dev(flags, "flags")
+    return Pred(PREDS[kind], int(a), int(b), fp)
+
+
+def workspace_size(op: str, itype: int, n: int, extra: int = 0) -> int:
+    return int(load().ixp_workspace_size(OPS[op], itype, n, extra))
+
+
+_WS_CACHE: dict = {}
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A reusable uint8 device buffer of at least nbytes (one per device and stream)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    key = (dev, torch.cuda.current_stream(dev).cuda_stream)
+    buf = _WS_CACHE.get(key)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        _WS_CACHE[key] = buf
+    return buf
+
+
+@dataclass
+class Verdict:
+    """A verdict in device memory (48 bytes). `.get()` copies it to the host."""
+    buf: torch.Tensor  # int64[6]
+
+    def get(self) -> dict:
+        w = self.buf.cpu().tolist()
+        lo, hi = w[0] & 0xFFFFFFFF, (w[0] >> 32) & 0xFFFFFFFF
+        ok = lo - (1 << 32) if lo >= (1 << 31) else lo
+        st = w[5] & 0xFFFFFFFF
+        st = st - (1 << 32) if st >= (1 << 31) else st
+        return {"ok": ok, "kind": KINDS[hi] if hi < len(KINDS) else hi, "index": w[1], "value": w[2],
+                "aux0": w[3], "aux1": w[4], "status": st}
+
+
+def _verdict_buf(device, out=None):
+    return out if out is not None else torch.empty(6, dtype=torch.int64, device=device)
+
+
+# ------------------------------------------------------------------- checks
+
+def check_range(x, lo=I64MIN, hi=I64MAX, *, out=None, ws=None, stream=None) -> Verdict:
+    v = _verdict_buf(x.device, out)
+    need = workspace_size("range", _itype(x), x.numel())
+    ws = ws if ws is not None else workspace(need, x.device)
+    _ck(load().ixp_check_range(_dev(x, "x"), _itype(x), x.numel(), lo, hi, v.data_ptr(), ws.data_ptr(),
+                               ws.numel(), _stream(stream)), "check_range")
+    return Verdict(v)
+
+
+def check_mono(x, cmp="le", offsets=None, *, seg_ok=None, out=None, ws=None, stream=None) -> Verdict:
+    v = _verdict_buf(x.device, out)
+    segs = _segs(offsets)
+    need = workspace_size("mono", _itype(x), x.numel(), segs.nseg)
+    ws = ws if ws is not None else workspace(need, x.device)
+    so = None if seg_ok is None else _dev(seg_ok, "seg_ok")
+    _ck(load().ixp_check_mono(_dev(x, "x"), _itype(x), x.numel(), CMPS[cmp], segs, v.data_ptr(), so, ws.data_ptr(),
+                              ws.numel(), _stream(stream)), "check_mono")
+    return Verdict(v)
+
+
+def check_inj(x, rcd_lo=I64MIN, rcd_hi=I64MAX, *, span=None, out=None, ws=None, stream=None) -> Verdict:
+    """`span`: the largest value span the bitmap must cover. Default: the Rcd width when
+    it is at most 4n + 4096, else 4n + 4096 (a wider actual span reports IXP_E_SPAN)."""
+    v = _verdict_buf(x.device, out)
+    n = x.numel()
+    if span is None:
+        span = 4 * n + 4096
+        if rcd_hi - rcd_lo + 1 <= span:
+            span = rcd_hi - rcd_lo + 1
+    need = workspace_size("inj", _itype(x), n, max(1, span))
+    ws = ws if ws is not None else workspace(need, x.device)
+    _ck(load().ixp_check_inj(_dev(x, "x"), _itype(x), n, rcd_lo, rcd_hi, v.data_ptr(), ws.data_ptr(), ws.numel(),
+                             _stream(stream)), "check_inj")
+    return Verdict(v)
+
+
+def check_bij(x, rcd_lo, rcd_hi, img_lo, img_hi, *, out=None, ws=None, stream=None) -> Verdict:
+    v = _verdict_buf(x.device, out)
+    need = workspace_size("bij", _itype(x), x.numel(), img_hi - img_lo + 1)
+    ws = ws if ws is not None else workspace(need, x.device)
+    _ck(load().ixp_check_bij(_dev(x, "x"), _itype(x), x.numel(), rcd_lo, rcd_hi, img_lo, img_hi, v.data_ptr(),
+                             ws.data_ptr(), ws.numel(), _stream(stream)), "check_bij")
+    return Verdict(v)
+
+
+def check_filtpart(z, keys=None, filt="true", part="true", offsets=None, *, out=None, ws=None, stream=None) -> Verdict:
+    v = _verdict_buf(z.device, out)
+    segs = _segs(offsets)
+    kt = _itype(keys) if keys is not None else 0
+    need = workspace_size("filtpart", kt, z.numel(), segs.nseg)
+    ws = ws if ws is not None else workspace(need, z.device)
+    kp = None if keys is None else _dev(keys, "keys")
+    _ck(load().ixp_check_filtpart(_dev(z, "z"), _itype(z), z.numel(), kp, kt, make_pred(filt), make_pred(part), segs,
+                                  v.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "check_filtpart")
+    return Verdict(v)
+
+
+# ---------------------------------------------------------------- combinators
+
+def scan(x, out_dtype=None, inclusive=False, offsets=None, *, out=None, totals=None, status=None, ws=None,
+         stream=None):
+    """Returns (out, totals, status) as device tensors."""
+    out_dtype = out_dtype or x.dtype
+    n = x.numel()
+    out = out if out is not None else torch.empty(n, dtype=out_dtype, device=x.device)
+    segs = _segs(offsets)
+    if totals is None:
+        totals = torch.empty(max(1, segs.nseg), dtype=out_dtype, device=x.device)
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=x.device)
+    need = workspace_size("scan", _itype(x), n, segs.nseg)
+    ws = ws if ws is not None else workspace(need, x.device)
+    _ck(load().ixp_scan(_dev(x, "x"), _itype(x), out.data_ptr(), _itype(out), n, int(inclusive), segs,
+                        totals.data_ptr(), status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "scan")
+    return out, totals, status
+
+
+def partition(keys, pred, payload=None, out_dtype=torch.int32, offsets=None, *, want_keys=True, n=None, out=None,
+              out_keys=None, out_payload=None, num_true=None, status=None, ws=None, stream=None):
+    """Stable two-way partition. Returns dict(indices, num_true, keys_out, payload_out, status)."""
+    p = make_pred(pred)
+    if keys is not None:
+        n = keys.numel()
+        device = keys.device
+    else:
+        device = pred[3].device if isinstance(pred, (tuple, list)) else torch.device("cuda")
+    segs = _segs(offsets)
+    out = out if out is not None else torch.empty(n, dtype=out_dtype, device=device)
+    if want_keys and keys is not None and out_keys is None:
+        out_keys = torch.empty_like(keys)
+    if payload is not None and out_payload is None:
+        out_payload = torch.empty_like(payload)
+    num_true = num_true if num_true is not None else torch.empty(max(1, segs.nseg), dtype=torch.int64, device=device)
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=device)
+    kt = _itype(keys) if keys is not None else 0
+    need = workspace_size("partition", kt, n, segs.nseg)
+    ws = ws if ws is not None else workspace(need, device)
+    row_bytes = 0
+    if payload is not None:
+        row_bytes = payload.element_size()
+        for d in payload.shape[1:]:
+            row_bytes *= d
+    _ck(load().ixp_partition(None if keys is None else _dev(keys, "keys"), kt, n, p,
+                             None if payload is None else _dev(payload, "payload"), row_bytes, out.data_ptr(),
+                             _itype(out), None if out_keys is None or not want_keys else out_keys.data_ptr(),
+                             None if out_payload is None else out_payload.data_ptr(), num_true.data_ptr(), segs,
+                             status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "partition")
+    return {"indices": out, "num_true": num_true, "keys_out": out_keys if want_keys else None,
+            "payload_out": out_payload, "status": status}
+
+
+def _rows(t: torch.Tensor, n: int):
+    per = 1
+    for d in t.shape[1:]:
+        per *= d
+    return per, t.element_size()
+
+
+def scatter(dst, idx, vals, mode="assign", *, stream=None):
+    """In place: dst[idx[i]] = vals[i] (or += for mode='add'); out-of-bounds indices are ignored."""
+    n = idx.numel()
+    row_elems, eb = _rows(vals, n)
+    _ck(load().ixp_scatter(_dev(dst, "dst"), dst.shape[0], _dev(idx, "idx"), _itype(idx), _dev(vals, "vals"), n,
+                           row_elems, eb, 0 if mode == "assign" else 1, _stream(stream)), "scatter")
+    return dst
+
+
+def scatter_add_f64(acc, idx, vals, *, stream=None):
+    """In place: acc (float64) [idx[i]] += vals[i] (float32 rows)."""
+    n = idx.numel()
+    row_elems = _rows(vals, n)[0]
+    _ck(load().ixp_scatter_add_f32_to_f64(_dev(acc, "acc"), acc.shape[0], _dev(idx, "idx"), _itype(idx),
+                                          _dev(vals, "vals"), n, row_elems, _stream(stream)), "scatter_add_f64")
+    return acc
+
+
+def f64_to_f32(acc, out=None, *, stream=None):
+    out = out if out is not None else torch.empty(acc.shape, dtype=torch.float32, device=acc.device)
+    _ck(load().ixp_f64_to_f32(_dev(out, "out"), _dev(acc, "acc"), acc.numel(), _stream(stream)), "f64_to_f32")
+    return out
+
+
+def gather(src, idx, *, out=None, status=None, stream=None):
+    """out[i] = src[idx[i]]; an out-of-range index zero-fills its row and sets status to -7."""
+    n = idx.numel()
+    shape = (n,) + tuple(src.shape[1:])
+    out = out if out is not None else torch.empty(shape, dtype=src.dtype, device=src.device)
+    row_elems = 1
+    for s in src.shape[1:]:
+        row_elems *= s
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=src.device)
+    _ck(load().ixp_gather(_dev(out, "out"), _dev(src, "src"), src.shape[0], _dev(idx, "idx"), _itype(idx), n,
+                          row_elems, src.element_size(), status.data_ptr(), _stream(stream)), "gather")
+    return out, status
+
+
+def flags_from_shape(shape, xs=None, out_dtype=torch.int64, out_len=None, *, stream=None):
+    """mkSgmDescr. Returns (flags, offsets, status). out_len=None reads sum(shape) (one sync)."""
+    m = shape.numel()
+    offs = torch.empty(m + 1, dtype=torch.int64, device=shape.device)
+    status = torch.zeros(1, dtype=torch.int32, device=shape.device)
+    need = workspace_size("flags", 1, m)
+    ws = workspace(need, shape.device)
+    xp = None if xs is None else _dev(xs, "xs")
+    if out_len is None:
+        _ck(load().ixp_flags_from_shape(_dev(shape, "shape"), m, xp, None, 1, 0, offs.data_ptr(), status.data_ptr(),
+                                        ws.data_ptr(), ws.numel(), _stream(stream)), "flags_from_shape")
+        out_len = int(offs[m].item()) if m else 0
+        if status.item() != 0:
+            raise IxpError(int(status.item()), "flags_from_shape")
+    out = torch.empty(out_len, dtype=out_dtype, device=shape.device)
+    _ck(load().ixp_flags_from_shape(_dev(shape, "shape"), m, xp, out.data_ptr() if out_len else None,
+                                    0 if out_dtype == torch.int32 else 1, out_len, offs.data_ptr(),
+                                    status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)),
+        "flags_from_shape")
+    return out, offs, status
+
+
+def debug_set_wait(spin_limit: int, skip_tile: int = -1):
+    """Testing hook: bound on device waits (polls) and a tile that never publishes."""
+    _ck(load().ixp_debug_set_wait(spin_limit, skip_tile), "debug_set_wait")

@@ -1,0 +1,391 @@
+"""GPU path vs the CPU oracle, element by element, on seeded inputs of sizes that
+span several tiles and ragged tails (tiles are 4096 int32 / 2048 int64 elements,
+grid-stride vectors 16 bytes). Verdicts, indices and moved bytes are bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+I64MIN, I64MAX = oracle.INT64_MIN, oracle.INT64_MAX
+SIZES = [0, 1, 2, 3, 31, 32, 33, 1023, 2047, 2048, 2049, 4095, 4096, 4097, 12289, 65536, 100003]
+
+
+@pytest.fixture(scope="module")
+def ixp():
+    import paper_2506_23058_gb300 as m
+    m.load()
+    return m
+
+
+@pytest.fixture(scope="module")
+def dev():
+    return torch.device("cuda:0")
+
+
+def T(a, dev):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
+def same(g, o, what=""):
+    g = g.get()
+    assert g["status"] == 0, (what, g)
+    assert bool(g["ok"]) == o["ok"], (what, g, o)
+    for f in ("kind", "index", "value", "aux0", "aux1"):
+        assert g[f] == o[f], (what, f, g, o)
+
+
+def arrays(n, dtype, seed):
+    out = {"identity": synth.identity(n, dtype), "perm": synth.permutation(n, seed, dtype),
+           "mono": synth.monotone(n, seed, dtype)}
+    if n >= 2:
+        out["dup"] = synth.plant_duplicate(out["perm"], seed)[0]
+        out["oor"] = synth.plant_value(out["perm"], seed, n)[0]
+        out["neg"] = synth.plant_value(out["perm"], seed + 1, -1)[0]
+        out["brk"] = synth.plant_order_break(out["mono"], seed)[0]
+    return out
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("n", SIZES)
+def test_range(ixp, dev, n, dtype):
+    for name, a in arrays(n, dtype, 100 + n).items():
+        for lo, hi in [(0, max(0, n - 1)), (I64MIN, I64MAX), (1, max(1, n - 2)), (I64MIN, 0)]:
+            same(ixp.check_range(T(a, dev), lo, hi), oracle.check_range(a, lo, hi), (name, n, lo, hi))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_range_unaligned_views_and_planted_edges(ixp, dev, dtype):
+    n = 20000
+    base = synth.permutation(n + 8, 7, dtype)
+    for off in range(4):
+        a = base[off:off + n]
+        same(ixp.check_range(T(base, dev)[off:off + n], 0, n + 7), oracle.check_range(a, 0, n + 7))
+    for p in [0, 1, 4095, 4096, 4097, n - 1]:
+        a = synth.identity(n, dtype)
+        a[p] = -5
+        same(ixp.check_range(T(a, dev), 0, n - 1), oracle.check_range(a, 0, n - 1), p)
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("n", SIZES)
+def test_mono_flat(ixp, dev, n, dtype):
+    for name, a in arrays(n, dtype, 200 + n).items():
+        for c in ["le", "lt", "ge", "gt"]:
+            same(ixp.check_mono(T(a, dev), c), oracle.check_mono(a, c), (name, n, c))
+        r = a[::-1].copy()
+        for c in ["ge", "gt"]:
+            same(ixp.check_mono(T(r, dev), c), oracle.check_mono(r, c), (name, n, c, "rev"))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_mono_unaligned_and_edges(ixp, dev, dtype):
+    n = 30000
+    base = synth.identity(n + 8, dtype)
+    for p in [1, 2, 3, 4, 5, 127, 128, 129, 4096, 8191, 8192, n - 1]:
+        a = base.copy()
+        a[p] = a[p - 1] - 1
+        t = T(a, dev)
+        for off in range(4):
+            same(ixp.check_mono(t[off:off + n], "lt"), oracle.check_mono(a[off:off + n], "lt"), (p, off))
+
+
+def random_offsets(rng, n, m, p_empty=0.2):
+    cuts = np.sort(rng.integers(0, n + 1, size=m - 1))
+    off = np.concatenate([[0], cuts, [n]]).astype(np.int64)
+    return off
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("n,m", [(0, 1), (1, 1), (100, 7), (5000, 3), (5000, 900), (70000, 50), (70000, 20000)])
+def test_mono_segmented(ixp, dev, n, m, dtype):
+    rng = np.random.default_rng(n + m)
+    off = random_offsets(rng, n, m)
+    # sorted within each segment, resets at segment starts
+    a = np.concatenate([np.sort(rng.integers(0, 1000, size=off[k + 1] - off[k])) for k in range(m)]).astype(dtype) \
+        if n else np.zeros(0, dtype)
+    for trial in range(3):
+        b = a.copy()
+        if trial and n > 2:
+            for p in rng.integers(1, n, size=trial * 3):
+                b[p] = b[p - 1] - 1
+        for c in ["le", "lt"]:
+            so = torch.zeros(m, dtype=torch.uint8, device=dev)
+            g = ixp.check_mono(T(b, dev), c, T(off, dev), seg_ok=so)
+            o, oso = oracle.check_mono(b, c, off, seg_ok=True)
+            same(g, o, (n, m, c, trial))
+            assert np.array_equal(so.cpu().numpy(), oso[:m])
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("n", SIZES)
+def test_inj(ixp, dev, n, dtype):
+    for name, a in arrays(n, dtype, 300 + n).items():
+        for lo, hi in [(I64MIN, I64MAX), (0, max(0, n - 1)), (0, n // 2), (5, 5)]:
+            same(ixp.check_inj(T(a, dev), lo, hi), oracle.check_inj(a, lo, hi), (name, n, lo, hi))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_inj_many_duplicates_and_edges(ixp, dev, dtype):
+    rng = np.random.default_rng(5)
+    for n in [10, 1000, 50000]:
+        a = rng.integers(0, n // 2 + 1, size=n).astype(dtype)
+        same(ixp.check_inj(T(a, dev)), oracle.check_inj(a), n)
+        same(ixp.check_inj(T(a, dev), 3, n // 4), oracle.check_inj(a, 3, n // 4), n)
+    n = 40000
+    for p, q in [(0, 1), (0, n - 1), (n - 2, n - 1), (4095, 4096), (17, 30000)]:
+        a = synth.permutation(n, 11, dtype)
+        a[q] = a[p]
+        same(ixp.check_inj(T(a, dev)), oracle.check_inj(a), (p, q))
+
+
+def test_inj_wide_values_and_span_limit(ixp, dev):
+    rng = np.random.default_rng(9)
+    n = 5000
+    a = (rng.permutation(n).astype(np.int64) * 3 - 7000)
+    same(ixp.check_inj(T(a, dev)), oracle.check_inj(a))
+    a[100] = a[4000]
+    same(ixp.check_inj(T(a, dev)), oracle.check_inj(a))
+    # values spread over 2^40: the bitmap cannot hold the span -> device status IXP_E_SPAN
+    b = rng.integers(0, 2**40, size=n).astype(np.int64)
+    g = ixp.check_inj(T(b, dev)).get()
+    assert g["status"] == -3 and g["ok"] == -1
+    # restricting Rcd to a small window makes it decidable again
+    same(ixp.check_inj(T(b, dev), 0, 2**20), oracle.check_inj(b, 0, 2**20))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("n", [1, 2, 33, 4097, 65536, 100003])
+def test_bij(ixp, dev, n, dtype):
+    seed = 400 + n
+    perm = synth.permutation(n, seed, dtype)
+    cases = {"perm": perm}
+    if n >= 2:
+        cases["dup"] = synth.plant_duplicate(perm, seed)[0]
+        cases["oor"] = synth.plant_value(perm, seed, n)[0]
+        cases["neg"] = synth.plant_value(perm, seed, -1)[0]
+        cases["gap"] = synth.plant_value(perm, seed, n + 5)[0]
+    for name, a in cases.items():
+        for rlo, rhi, ilo, ihi in [(I64MIN, I64MAX, 0, n - 1), (0, n - 1, 0, n - 1), (-1, n + 10, 0, n - 1),
+                                   (0, n + 2, 0, n + 2)]:
+            same(ixp.check_bij(T(a, dev), rlo, rhi, ilo, ihi), oracle.check_bij(a, rlo, rhi, ilo, ihi),
+                 (name, n, rlo, rhi, ilo, ihi))
+
+
+@pytest.mark.parametrize("it,ot", [(np.int32, np.int32), (np.int32, np.int64), (np.int64, np.int64)])
+@pytest.mark.parametrize("n", SIZES + [300000])
+def test_scan_flat(ixp, dev, n, it, ot):
+    rng = np.random.default_rng(n)
+    info = np.iinfo(it)
+    for lo, hi in [(0, 4), (info.min // 4, info.max // 4)]:
+        a = rng.integers(lo, hi, size=n).astype(it)
+        for inc in (False, True):
+            out, tot, st = ixp.scan(T(a, dev), getattr(torch, np.dtype(ot).name), inclusive=inc)
+            o, otot = oracle.scan(a, ot, inclusive=inc)
+            assert st.item() == 0
+            assert np.array_equal(out.cpu().numpy(), o), (n, inc)
+            assert int(tot[0].item()) == int(otot[0])
+
+
+@pytest.mark.parametrize("it,ot", [(np.int32, np.int32), (np.int32, np.int64), (np.int64, np.int64)])
+@pytest.mark.parametrize("n,m", [(1, 1), (100, 7), (5000, 3), (5000, 2000), (70000, 50), (70000, 30000)])
+def test_scan_segmented(ixp, dev, n, m, it, ot):
+    rng = np.random.default_rng(n * 7 + m)
+    off = random_offsets(rng, n, m)
+    a = rng.integers(-50, 100, size=n).astype(it)
+    for inc in (False, True):
+        out, tot, st = ixp.scan(T(a, dev), getattr(torch, np.dtype(ot).name), inclusive=inc, offsets=T(off, dev))
+        o, otot = oracle.scan(a, ot, inclusive=inc, offsets=off)
+        assert st.item() == 0
+        assert np.array_equal(out.cpu().numpy(), o), (n, m, inc)
+        assert np.array_equal(tot.cpu().numpy(), otot[:m])
+
+
+def test_scan_unaligned(ixp, dev):
+    a = np.arange(50001, dtype=np.int32) % 7
+    t = T(a, dev)
+    for off in range(4):
+        out = torch.empty(50001, dtype=torch.int64, device=dev)
+        r, _, _ = ixp.scan(t[off:], torch.int64, out=out[off:], totals=torch.empty(1, dtype=torch.int64, device=dev))
+        assert np.array_equal(r.cpu().numpy(), oracle.scan(a[off:], np.int64)[0])
+
+
+def test_scan_timeout_is_reported(ixp, dev):
+    # a tile that never publishes makes its successors' bounded waits run out
+    n = 4096 * 12 + 5
+    a = np.ones(n, np.int32)
+    try:
+        ixp.debug_set_wait(2000, 3)
+        _, _, st = ixp.scan(T(a, dev))
+        torch.cuda.synchronize()
+        assert st.item() == -6
+    finally:
+        ixp.debug_set_wait(0, -1)
+    _, _, st = ixp.scan(T(a, dev))
+    assert st.item() == 0
+
+
+PREDS = [("mod_eq", 3, 0), ("lt", 0, 0), ("lt", 0, synth.bernoulli_threshold(0.01)), ("mod_eq", 5, 2)]
+
+
+@pytest.mark.parametrize("kt", [np.int32, np.int64])
+@pytest.mark.parametrize("ot", [np.int32, np.int64])
+@pytest.mark.parametrize("n", [0, 1, 5, 2048, 4097, 65536, 100003])
+def test_partition_flat(ixp, dev, n, kt, ot):
+    keys = synth.keys_uniform(n, 500 + n).astype(kt)
+    pay = synth.payload_f32(n, 600 + n)
+    for p in PREDS:
+        r = ixp.partition(T(keys, dev), p, payload=T(pay, dev), out_dtype=getattr(torch, np.dtype(ot).name))
+        o = oracle.partition(keys, p, payload=pay, out_dtype=ot)
+        assert r["status"].item() == 0
+        assert np.array_equal(r["indices"].cpu().numpy(), o["indices"]), (n, p)
+        assert int(r["num_true"][0].item()) == int(o["num_true"][0])
+        assert np.array_equal(r["keys_out"].cpu().numpy(), o["keys_out"])
+        assert np.array_equal(r["payload_out"].cpu().numpy().view(np.uint32), o["payload_out"].view(np.uint32))
+
+
+def test_partition_flags_and_wide_rows(ixp, dev):
+    n = 30001
+    fl = synth.flags_bernoulli(n, 3, 0.3)
+    pay = synth.payload_f32(n, 4, cols=8)
+    r = ixp.partition(None, ("flags", 0, 0, T(fl, dev)), payload=T(pay, dev), n=n)
+    o = oracle.partition(None, ("flags", 0, 0, fl), payload=pay)
+    assert np.array_equal(r["indices"].cpu().numpy(), o["indices"])
+    assert np.array_equal(r["payload_out"].cpu().numpy(), o["payload_out"])
+
+
+@pytest.mark.parametrize("kt", [np.int32, np.int64])
+@pytest.mark.parametrize("n,m", [(1, 1), (100, 7), (5000, 3), (5000, 2000), (70000, 50), (70000, 30000)])
+def test_partition_segmented(ixp, dev, n, m, kt):
+    rng = np.random.default_rng(n + 3 * m)
+    off = random_offsets(rng, n, m)
+    keys = synth.keys_uniform(n, n + m).astype(kt)
+    pay = synth.payload_f32(n, n + m + 1)
+    p = ("lt", 0, synth.bernoulli_threshold(0.3))
+    r = ixp.partition(T(keys, dev), p, payload=T(pay, dev), offsets=T(off, dev))
+    o = oracle.partition(keys, p, payload=pay, offsets=off)
+    assert np.array_equal(r["indices"].cpu().numpy(), o["indices"])
+    assert np.array_equal(r["num_true"].cpu().numpy(), o["num_true"][:m])
+    assert np.array_equal(r["keys_out"].cpu().numpy(), o["keys_out"])
+    assert np.array_equal(r["payload_out"].cpu().numpy(), o["payload_out"])
+
+
+@pytest.mark.parametrize("zt", [np.int32, np.int64])
+@pytest.mark.parametrize("n", [1, 6, 4097, 65536, 100003])
+def test_filtpart(ixp, dev, n, zt):
+    rng = np.random.default_rng(n)
+    keys = synth.keys_uniform(n, 700 + n)
+    part = ("mod_eq", 3, 0)
+    z = oracle.partition(keys, part, out_dtype=zt)["indices"]
+    cases = {"ok": z.copy()}
+    if n >= 2:
+        s = z.copy()
+        a, b = rng.integers(0, n, size=2)
+        s[a], s[b] = s[b], s[a]
+        cases["swap"] = s
+        s = z.copy()
+        s[n - 1] += 1
+        cases["last"] = s
+    for name, zz in cases.items():
+        same(ixp.check_filtpart(T(zz, dev), T(keys, dev), part=part), oracle.check_filtpart(zz, keys, part=part),
+             (name, n))
+
+
+@pytest.mark.parametrize("n,m", [(100, 1), (5000, 40), (70000, 30000)])
+def test_filtpart_filter_and_segments(ixp, dev, n, m):
+    rng = np.random.default_rng(n + m)
+    off = random_offsets(rng, n, m)
+    keys = synth.keys_uniform(n, n).astype(np.int64)
+    flags = synth.flags_bernoulli(n, n + 1, 0.7)
+    fl_o = ("flags", 0, 0, flags)
+    fl_g = ("flags", 0, 0, T(flags, dev))
+    part = ("lt", 0, synth.bernoulli_threshold(0.4))
+    # reference destinations from the oracle's definition; dropped elements -> -1
+    cls = (keys >= part[2]).astype(np.uint8)
+    ref = np.full(n, -1, np.int64)
+    pos = 0
+    for k in range(m):
+        idx = [i for i in range(off[k], off[k + 1]) if flags[i]]
+        for i in sorted(idx, key=lambda i: cls[i]):
+            ref[i] = pos
+            pos += 1
+    for trial in range(3):
+        z = ref.copy()
+        if trial == 1:
+            z[rng.integers(0, n)] += 1
+        if trial == 2:
+            d = np.flatnonzero(ref < 0)
+            if len(d):
+                z[d[len(d) // 2]] = 0
+        g = ixp.check_filtpart(T(z, dev), T(keys, dev), filt=fl_g, part=part, offsets=T(off, dev))
+        o = oracle.check_filtpart(z, keys, filt=fl_o, part=part, offsets=off)
+        same(g, o, (n, m, trial))
+
+
+@pytest.mark.parametrize("it", [np.int32, np.int64])
+@pytest.mark.parametrize("cols,fdt", [(1, np.float32), (8, np.float32), (3, np.float32), (2, np.float64)])
+def test_scatter_gather(ixp, dev, it, cols, fdt):
+    rng = np.random.default_rng(cols)
+    n, m = 50003, 40000
+    vals = rng.standard_normal((n, cols)).astype(fdt)
+    idx = (rng.permutation(n) - 5000).astype(it)  # injective, some out of bounds on both sides
+    dst = np.zeros((m, cols), fdt)
+    g = ixp.scatter(T(dst, dev), T(idx, dev), T(vals, dev))
+    assert np.array_equal(g.cpu().numpy(), oracle.scatter(dst, idx, vals))
+    gi = np.clip(idx, 0, m - 1).astype(it)
+    out, st = ixp.gather(g, T(gi, dev))
+    assert st.item() == 0 and np.array_equal(out.cpu().numpy(), oracle.gather(g.cpu().numpy(), gi)[0])
+    out, st = ixp.gather(g, T(idx, dev))
+    o, oob = oracle.gather(g.cpu().numpy(), idx)
+    assert st.item() == -7 and oob and np.array_equal(out.cpu().numpy(), o)
+
+
+def test_scatter_add_f64_zipf(ixp, dev):
+    n, m, cols = 200000, 1024, 8
+    idx = synth.zipf_ranks(n, m, 1.1, 77)
+    vals = synth.payload_f32(n, 78, cols=cols)
+    acc = torch.zeros((m, cols), dtype=torch.float64, device=dev)
+    ixp.scatter_add_f64(acc, T(idx, dev), T(vals, dev))
+    ref = oracle.scatter_add_f64(m, idx, vals)
+    absum = oracle.scatter_add_f64(m, idx, np.abs(vals))
+    err = np.abs(acc.cpu().numpy() - ref)
+    assert np.all(err <= 1e-10 * absum + 1e-300)
+    f32 = ixp.f64_to_f32(acc).cpu().numpy()
+    assert np.array_equal(f32, ref.astype(np.float32)) or np.all(np.abs(f32 - ref) <= 1e-6 * np.maximum(absum, 1e-30))
+
+
+@pytest.mark.parametrize("m", [0, 1, 5, 1000, 40000])
+@pytest.mark.parametrize("ot", [np.int32, np.int64])
+def test_flags_from_shape(ixp, dev, m, ot):
+    rng = np.random.default_rng(m)
+    shape = synth.shapes_with_empties(m, m + 1, 9)
+    xs = rng.integers(1, 1000, size=m).astype(np.int64)
+    for x in (xs, None):
+        out, offs, st = ixp.flags_from_shape(T(shape, dev), None if x is None else T(x, dev),
+                                             out_dtype=getattr(torch, np.dtype(ot).name))
+        o, ooff = oracle.flags_from_shape(shape, x, out_dtype=ot)
+        assert st.item() == 0
+        assert np.array_equal(out.cpu().numpy(), o)
+        assert np.array_equal(offs.cpu().numpy(), ooff)
+
+
+def test_flags_from_shape_paper_example(ixp, dev):
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "mksgmdescr_example.json")))
+    out, _, _ = ixp.flags_from_shape(T(np.array(g["shape"], np.int64), dev), T(np.array(g["xs"], np.int64), dev))
+    assert out.cpu().tolist() == g["result"]
+
+
+def test_partition_paper_demo(ixp, dev):
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "partition2_demo.json")))
+    r = ixp.partition(T(np.array(g["xs"], np.int32), dev), ("lt", 0, 5))
+    assert r["indices"].cpu().tolist() == g["indices"]
+    assert r["keys_out"].cpu().tolist() == g["ys"]
+    assert r["num_true"].item() == g["num_true"]
