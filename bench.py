@@ -58,15 +58,21 @@ def make_ops(n32, n64, small=False):
             (f"bij_dup_{tag}", "bij", (f"dup_{tag}",), es * n),
         ]
     n = n32
+    nr = n32 // 4  # rows of the [n/4 x 8] float32 payload moved by scatter / gather
     ops += [
         ("scan_i32", "scan", ("steps_i32",), 8 * n),
         ("partition_p50", "partition", ("keys", "payload"), 16 * n),
         ("partition_p01", "partition01", ("keys", "payload"), 16 * n),
         ("filtpart_p50", "filtpart", ("keys",), 8 * n),
-        ("scatter_payload", "scatter", ("perm_i32", "payload"), 12 * n),
-        ("gather_payload", "gather", ("perm_i32", "payload"), 12 * n),
+        ("scatter_rows8", "scatter", ("perm_rows", "payload8"), 68 * nr),
+        ("gather_rows8", "gather", ("perm_rows", "payload8"), 68 * nr),
+        ("flags_from_shape", "flags", ("shape",), None),
     ]
     return ops
+
+
+def flags_bytes(m, total):
+    return 8 * m + 8 * (m + 1) + 4 * total
 
 
 def host_inputs(n32, n64):
@@ -84,6 +90,9 @@ def host_inputs(n32, n64):
     d["steps_i32"] = np.random.default_rng(s + 6).integers(0, 4, size=n32).astype(np.int32)
     d["keys"] = synth.keys_uniform(n32, s + 7)
     d["payload"] = synth.payload_f32(n32, s + 8)
+    d["perm_rows"] = synth.permutation(n32 // 4, s + 9, np.int32)
+    d["payload8"] = synth.payload_f32(n32 // 4, s + 10, cols=8)
+    d["shape"] = synth.shapes_log_uniform(4096, s + 11, cap_total=n32)
     return d
 
 
@@ -105,6 +114,9 @@ def device_inputs(n32, n64, dev):
     d["steps_i32"] = torch.randint(0, 4, (n32,), generator=g, device=dev, dtype=torch.int32)
     d["keys"] = synth.t_keys_uniform(n32, s + 7, dev)
     d["payload"] = synth.t_payload_f32(n32, s + 8, dev)
+    d["perm_rows"] = synth.t_permutation(n32 // 4, s + 9, dev, torch.int32)
+    d["payload8"] = synth.t_payload_f32(n32 // 4, s + 10, dev, cols=8)
+    d["shape"] = torch.from_numpy(synth.shapes_log_uniform(4096, s + 11, cap_total=n32)).to(dev)
     return d
 
 
@@ -127,8 +139,11 @@ class Runner:
         self.tot = torch.empty(1, dtype=torch.int32, device=dev)
         self.status = torch.zeros(4, dtype=torch.int32, device=dev)
         self.num_true = torch.empty(2, dtype=torch.int64, device=dev)
-        self.scat = torch.empty(n, dtype=torch.float32, device=dev)
-        self.gath = torch.empty(n, dtype=torch.float32, device=dev)
+        self.scat = torch.empty((n // 4, 8), dtype=torch.float32, device=dev)
+        self.gath = torch.empty((n // 4, 8), dtype=torch.float32, device=dev)
+        self.shape_total = int(inp["shape"].sum().item())
+        self.flags = torch.empty(self.shape_total, dtype=torch.int32, device=dev)
+        self.offs = torch.empty(inp["shape"].numel() + 1, dtype=torch.int64, device=dev)
         self.p50 = synth.bernoulli_threshold(0.5)
         self.p01 = synth.bernoulli_threshold(0.01)
 
@@ -157,9 +172,12 @@ class Runner:
         elif kind == "filtpart":
             ixp.check_filtpart(self.idx, x, part=("lt", 0, self.p50), out=v, ws=ws)
         elif kind == "scatter":
-            ixp.scatter(self.scat, x, inp["payload"])
+            ixp.scatter(self.scat, x, inp["payload8"])
         elif kind == "gather":
-            ixp.gather(inp["payload"], x, out=self.gath, status=self.status[3:4])
+            ixp.gather(inp["payload8"], x, out=self.gath, status=self.status[3:4])
+        elif kind == "flags":
+            ixp.flags_from_shape(x, None, out_len=self.shape_total, out=self.flags, offsets=self.offs,
+                                 status=self.status[3:4], ws=ws)
 
 
 # ------------------------------------------------------------------- clocks
@@ -248,9 +266,12 @@ def oracle_step(inp, ops):
             elif kind == "filtpart":
                 oracle.check_filtpart(idx50, x, part=("lt", 0, p50))
             elif kind == "scatter":
-                oracle.scatter(np.zeros_like(inp["payload"]), x, inp["payload"])
+                oracle.scatter(np.zeros_like(inp["payload8"]), x, inp["payload8"])
             elif kind == "gather":
-                oracle.gather(inp["payload"], x)
+                oracle.gather(inp["payload8"], x)
+            elif kind == "flags":
+                out, _ = oracle.flags_from_shape(x, out_dtype=np.int32)
+                nbytes = flags_bytes(x.shape[0], out.shape[0])
             total_bytes += nbytes
     return total_bytes
 
@@ -332,6 +353,7 @@ def main():
         ops = [o for o in ops if o[0] in keep]
     inp = device_inputs(n32, n64, dev)
     R = Runner(ixp, inp, n32, n64, dev)
+    ops = [(a, b, c, d if d is not None else flags_bytes(inp["shape"].numel(), R.shape_total)) for a, b, c, d in ops]
     stream = torch.cuda.current_stream()
     torch.cuda.synchronize()
 

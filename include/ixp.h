@@ -152,7 +152,7 @@ int ixp_check_mono(const void *x, int itype, int64_t n, int cmp, ixp_segs segs, 
  * in-Rcd values (one extra pass). A span above the workspace capacity (set by
  * `extra` in ixp_workspace_size) gives verdict status IXP_E_SPAN. Verdict on a
  * violation: index = smallest i whose value occurs again, value = X[i],
- * aux0 = smallest j > i with X[j] = X[i]. */
+ * aux0 = smallest j > i with X[j] = X[i] (0 when the property holds). */
 int ixp_check_inj(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, ixp_verdict *d_verdict,
                   void *ws, size_t ws_bytes, ixp_stream stream);
 
@@ -161,7 +161,8 @@ int ixp_check_inj(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t r
  * Verdict: the smaller of (first i with X[i] in Rcd outside Img -> OUT_OF_IMAGE)
  * and (smallest i with X[i] in Img repeated -> DUPLICATE); otherwise, if some
  * image value is not taken, MISSING with value = the smallest such value and
- * index = -1. aux0 = number of elements with values in Img, aux1 = |Img|. */
+ * index = -1. aux0 = number of elements with values in Img, aux1 = |Img|
+ * (reported whether or not the property holds). */
 int ixp_check_bij(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, int64_t img_lo,
                   int64_t img_hi, ixp_verdict *d_verdict, void *ws, size_t ws_bytes, ixp_stream stream);
 

@@ -332,7 +332,7 @@ int ixo_check_inj(const void *x, int t, int64_t n, int64_t rlo, int64_t rhi, con
  *   - otherwise, the smallest v in Img_k that no element takes  -> MISSING
  * seg_img != 0 selects Img_k = [e_k, e_{k+1} - 1]; otherwise Img_k = [ilo, ihi].
  * aux0 = number of elements with values in Img_k, aux1 = |Img_k| (for the
- * reported segment). */
+ * reported segment; summed over all segments when the property holds). */
 int ixo_check_bij(const void *x, int t, int64_t n, int64_t rlo, int64_t rhi, int64_t ilo, int64_t ihi,
                   int seg_img, const int64_t *off, int64_t nseg, ixo_verdict *v, uint8_t *seg_ok)
 {
@@ -345,6 +345,7 @@ int ixo_check_bij(const void *x, int t, int64_t n, int64_t rlo, int64_t rhi, int
     if (!seg_img && (ilo > ihi || ilo < rlo || ihi > rhi || (uint64_t)ihi - (uint64_t)ilo >= ((uint64_t)1 << 40)))
         return IXO_E_INVAL;
     verdict_ok(v);
+    int64_t sum_in = 0, sum_size = 0;
     for (int64_t k = 0; k < seg_count(off, nseg); k++) {
         int64_t a = seg_lo(off, k), b = seg_hi(off, k, n);
         int64_t lo = seg_img ? a : ilo, hi = seg_img ? b - 1 : ihi;
@@ -367,6 +368,8 @@ int ixo_check_bij(const void *x, int t, int64_t n, int64_t rlo, int64_t rhi, int
         if (rc)
             return rc;
         int64_t size = hi - lo + 1; /* 0 for an empty segment with seg_img */
+        sum_in += in_img;
+        sum_size += size;
         int sok = 1;
         if (bad_img >= 0 || di >= 0) {
             sok = 0;
@@ -410,6 +413,10 @@ int ixo_check_bij(const void *x, int t, int64_t n, int64_t rlo, int64_t rhi, int
         }
         if (seg_ok)
             seg_ok[k] = (uint8_t)sok;
+    }
+    if (v->ok) {
+        v->aux0 = sum_in;
+        v->aux1 = sum_size;
     }
     return IXO_OK;
 }

@@ -19,12 +19,13 @@ int num_sms() {
     return cached[dev];
 }
 
-// Enough 256-thread blocks for `per_thread` items per thread, capped at 8 resident
-// blocks per SM (2048 threads), at least one block.
+// Enough 256-thread blocks for `per_thread` items per thread, capped at one wave
+// of 4 resident blocks per SM (the streaming kernels are built for 4 blocks/SM,
+// 64 registers per thread), at least one block.
 int stream_grid(int64_t work_items, int per_thread) {
     int64_t per_block = (int64_t)STREAM_THREADS * std::max(1, per_thread);
     int64_t blocks = (work_items + per_block - 1) / per_block;
-    int64_t cap = (int64_t)num_sms() * 8;
+    int64_t cap = (int64_t)num_sms() * 4;
     return (int)std::max<int64_t>(1, std::min(blocks, cap));
 }
 

@@ -8,28 +8,65 @@
 // 2^28 span is 32 MiB and stays L2 resident. When a collision was seen, two more
 // passes recover the exact witness (smallest repeated index and its partner); they
 // exit at once otherwise.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ixp {
 
 // ============================================================== Range
+// Bounds are clamped to the element type on the host (lo_t, hi_t), so the loop
+// compares in the native width; per 16-byte vector only the vector's min and max
+// are tested, and the first bad index is located only inside a failing vector.
+template <typename T> struct Lim;
+template <> struct Lim<int32_t> { static constexpr int32_t lo = INT32_MIN, hi = INT32_MAX; };
+template <> struct Lim<int64_t> { static constexpr int64_t lo = INT64_MIN, hi = INT64_MAX; };
+
 template <typename T>
-__global__ void __launch_bounds__(STREAM_THREADS) range_kernel(const T *__restrict__ x, int64_t n, int64_t lo,
-                                                               int64_t hi, Hdr *h) {
+__global__ void __launch_bounds__(STREAM_THREADS, 4) range_kernel(const T *__restrict__ x, int64_t n, T lo, T hi,
+                                                               Hdr *h) {
     IXP_KERNEL_ENTRY();
     using VT = typename Vec<T>::type;
     constexpr int V = Vec<T>::N;
     Split<T> s(x, n);
-    int64_t mn = INT64_MAX, mx = INT64_MIN, bad = INT64_MAX;
+    T mn = Lim<T>::hi, mx = Lim<T>::lo;
+    int64_t bad = INT64_MAX;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    auto visit = [&](int64_t i, int64_t xi) {
+    auto one = [&](int64_t i, T xi) {
         mn = xi < mn ? xi : mn;
         mx = xi > mx ? xi : mx;
         if ((xi < lo) | (xi > hi)) bad = i < bad ? i : bad;
     };
-    for (int64_t i = tid; i < s.head; i += stride) visit(i, ld1(x, i));
-    for (int64_t i = s.tail0 + tid; i < n; i += stride) visit(i, ld1(x, i));
+    auto vec = [&](int64_t i0, const VT &a) {
+        T e[V];
+        if (V == 4) {
+            const int4 &q = reinterpret_cast<const int4 &>(a);
+            e[0] = (T)q.x;
+            e[1 % V] = (T)q.y;
+            e[2 % V] = (T)q.z;
+            e[3 % V] = (T)q.w;
+        } else {
+            const longlong2 &q = reinterpret_cast<const longlong2 &>(a);
+            e[0] = (T)q.x;
+            e[1 % V] = (T)q.y;
+        }
+        T vmin = e[0], vmax = e[0];
+#pragma unroll
+        for (int k = 1; k < V; k++) {
+            vmin = e[k] < vmin ? e[k] : vmin;
+            vmax = e[k] > vmax ? e[k] : vmax;
+        }
+        mn = vmin < mn ? vmin : mn;
+        mx = vmax > mx ? vmax : mx;
+        if ((vmin < lo) | (vmax > hi)) {
+#pragma unroll
+            for (int k = V - 1; k >= 0; k--)
+                if ((e[k] < lo) | (e[k] > hi)) bad = (i0 + k) < bad ? (i0 + k) : bad;
+        }
+    };
+    for (int64_t i = tid; i < s.head; i += stride) one(i, x[i]);
+    for (int64_t i = s.tail0 + tid; i < n; i += stride) one(i, x[i]);
     const VT *xv = reinterpret_cast<const VT *>(x + s.head);
     int64_t v = tid;
     for (; v + 3 * stride < s.nvec; v += 4 * stride) {
@@ -37,34 +74,25 @@ __global__ void __launch_bounds__(STREAM_THREADS) range_kernel(const T *__restri
 #pragma unroll
         for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            int64_t e[V];
-            unpack(a[u], e);
-#pragma unroll
-            for (int k = 0; k < V; k++) visit(s.head + (v + u * stride) * V + k, e[k]);
-        }
+        for (int u = 0; u < 4; u++) vec(s.head + (v + u * stride) * V, a[u]);
     }
-    for (; v < s.nvec; v += stride) {
-        int64_t e[V];
-        unpack(ldv(xv + v), e);
-#pragma unroll
-        for (int k = 0; k < V; k++) visit(s.head + v * V + k, e[k]);
-    }
+    for (; v < s.nvec; v += stride) vec(s.head + v * V, ldv(xv + v));
     __shared__ unsigned long long sm[STREAM_THREADS / 32];
     unsigned long long r;
-    r = block_max_u64(enc_min(mn), sm);
-    if (threadIdx.x == 0) atomic_max_u64(&h->k_min, r);
-    r = block_max_u64(enc_max(mx), sm);
+    r = block_max_u64(enc_min((int64_t)mn), sm);
+    if (threadIdx.x == 0 && mn <= mx) atomic_max_u64(&h->k_min, r);
+    r = block_max_u64(enc_max((int64_t)mx), sm);
     if (threadIdx.x == 0) atomic_max_u64(&h->k_max, r);
     r = block_max_u64(bad == INT64_MAX ? 0ull : enc_first(bad), sm);
     if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
 }
 
 template <typename T>
-__global__ void range_finalize(const T *x, int64_t n, const Hdr *h, ixp_verdict *out) {
+__global__ void range_finalize(const T *x, int64_t n, const Hdr *h, ixp_verdict *out, int all_bad) {
     IXP_KERNEL_ENTRY();
     ixp_verdict v;
     int64_t bad = h->k_first ? dec_first(h->k_first) : -1;
+    if (all_bad && n > 0) bad = 0;
     v.status = h->status;
     v.ok = v.status ? -1 : (bad < 0 ? 1 : 0);
     v.kind = bad < 0 ? IXP_V_NONE : IXP_V_OUT_OF_RANGE;
@@ -90,7 +118,15 @@ __device__ __forceinline__ bool cmp_ok(int c, int64_t a, int64_t b) {
 // wbase + l, so the element before its vector is lane l-1's last element (one
 // shuffle); lane 0 reads it from memory.
 template <typename T, int C>
-__global__ void __launch_bounds__(STREAM_THREADS) mono_kernel(const T *__restrict__ x, int64_t n, Hdr *h) {
+__device__ __forceinline__ bool cmp_t(T a, T b) {
+    if (C == IXP_LE) return a <= b;
+    if (C == IXP_LT) return a < b;
+    if (C == IXP_GE) return a >= b;
+    return a > b;
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(STREAM_THREADS, 4) mono_kernel(const T *__restrict__ x, int64_t n, Hdr *h) {
     IXP_KERNEL_ENTRY();
     using VT = typename Vec<T>::type;
     constexpr int V = Vec<T>::N;
@@ -101,38 +137,50 @@ __global__ void __launch_bounds__(STREAM_THREADS) mono_kernel(const T *__restric
     const int lane = threadIdx.x & 31;
     // scalar head and tail pairs (j >= 1)
     for (int64_t j = tid; j < s.head; j += stride)
-        if (j >= 1 && !cmp_ok(C, ld1(x, j - 1), ld1(x, j))) bad = j < bad ? j : bad;
+        if (j >= 1 && !cmp_t<T, C>(x[j - 1], x[j])) bad = j < bad ? j : bad;
     for (int64_t j = s.tail0 + tid; j < n; j += stride)
-        if (j >= 1 && !cmp_ok(C, ld1(x, j - 1), ld1(x, j))) bad = j < bad ? j : bad;
+        if (j >= 1 && !cmp_t<T, C>(x[j - 1], x[j])) bad = j < bad ? j : bad;
     const VT *xv = reinterpret_cast<const VT *>(x + s.head);
     const int64_t wtid = tid - lane;  // warp's first thread
     for (int64_t wb = wtid; wb < s.nvec; wb += 4 * stride) {
         VT a[4];
-        int64_t prevm[4];
+        T prevm[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            int64_t vv = wb + u * stride + lane;
+            const int64_t vv = wb + u * stride + lane;
             if (vv < s.nvec) a[u] = ldv(xv + vv);
-            int64_t p = s.head + (wb + u * stride) * V;  // first element of lane 0's vector
-            prevm[u] = (lane == 0 && p >= 1 && wb + u * stride < s.nvec) ? ld1(x, p - 1) : 0;
+            const int64_t p = s.head + (wb + u * stride) * V;  // first element of lane 0's vector
+            prevm[u] = (lane == 0 && p >= 1 && wb + u * stride < s.nvec) ? x[p - 1] : (T)0;
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-            int64_t vv = wb + u * stride + lane;
-            int64_t e[V];
-            if (vv < s.nvec) unpack(a[u], e);
-            else {
-#pragma unroll
-                for (int k = 0; k < V; k++) e[k] = 0;
+            const int64_t vv = wb + u * stride + lane;
+            const bool live = vv < s.nvec;
+            T e[V];
+            if (V == 4) {
+                const int4 &q = reinterpret_cast<const int4 &>(a[u]);
+                e[0] = (T)q.x;
+                e[1 % V] = (T)q.y;
+                e[2 % V] = (T)q.z;
+                e[3 % V] = (T)q.w;
+            } else {
+                const longlong2 &q = reinterpret_cast<const longlong2 &>(a[u]);
+                e[0] = (T)q.x;
+                e[1 % V] = (T)q.y;
             }
-            int64_t prev = __shfl_up_sync(FULL, e[V - 1], 1);
+            T prev = __shfl_up_sync(FULL, e[V - 1], 1);
             if (lane == 0) prev = prevm[u];
-            if (vv < s.nvec) {
-                int64_t j0 = s.head + vv * V;
-                if (j0 >= 1 && !cmp_ok(C, prev, e[0])) bad = j0 < bad ? j0 : bad;
+            if (live) {
+                const int64_t j0 = s.head + vv * V;
+                bool fail = j0 >= 1 && !cmp_t<T, C>(prev, e[0]);
 #pragma unroll
-                for (int k = 1; k < V; k++)
-                    if (!cmp_ok(C, e[k - 1], e[k])) bad = (j0 + k) < bad ? (j0 + k) : bad;
+                for (int k = 1; k < V; k++) fail |= !cmp_t<T, C>(e[k - 1], e[k]);
+                if (fail) {
+                    if (j0 >= 1 && !cmp_t<T, C>(prev, e[0])) bad = j0 < bad ? j0 : bad;
+#pragma unroll
+                    for (int k = 1; k < V; k++)
+                        if (!cmp_t<T, C>(e[k - 1], e[k])) bad = (j0 + k) < bad ? (j0 + k) : bad;
+                }
             }
         }
     }
@@ -226,7 +274,7 @@ __global__ void mono_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
 // ================================================================ Inj / Bij
 // Min/max of the in-codomain values (needed when Rcd is unbounded).
 template <typename T>
-__global__ void __launch_bounds__(STREAM_THREADS) minmax_in_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
+__global__ void __launch_bounds__(STREAM_THREADS, 4) minmax_in_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
                                                                    int64_t rhi, Hdr *h) {
     IXP_KERNEL_ENTRY();
     using VT = typename Vec<T>::type;
@@ -312,7 +360,7 @@ __global__ void bitmap_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, u
 // Bij): atomicOr its bit; a bit already set means a repeat, which is recorded in
 // the second bitmap. For Bij, values in Rcd but outside Img are out of image.
 template <typename T, bool BIJ>
-__global__ void __launch_bounds__(STREAM_THREADS) mark_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
+__global__ void __launch_bounds__(STREAM_THREADS, 4) mark_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
                                                               int64_t rhi, int64_t mlo, int64_t mhi, Hdr *h,
                                                               unsigned *__restrict__ bm, unsigned *__restrict__ dup) {
     IXP_KERNEL_ENTRY();
@@ -433,7 +481,7 @@ __global__ void inj_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
     v.kind = (v.status || i < 0) ? IXP_V_NONE : IXP_V_DUPLICATE;
     v.index = v.status ? -1 : i;
     v.value = (v.status || i < 0) ? 0 : (int64_t)x[i];
-    v.aux0 = (v.status || i < 0 || !h->k_aux) ? -1 : dec_first(h->k_aux);
+    v.aux0 = (v.status || i < 0) ? 0 : (h->k_aux ? dec_first(h->k_aux) : -1);
     v.aux1 = 0;
     v.reserved = 0;
     *out = v;
@@ -533,11 +581,14 @@ extern "C" int ixp_check_range(const void *x, int itype, int64_t n, int64_t lo, 
     if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
     int grid = stream_grid((n + 3) / 4);
     if (itype == IXP_I32) {
-        if (n > 0) range_kernel<int32_t><<<grid, STREAM_THREADS, 0, st>>>((const int32_t *)x, n, lo, hi, h);
-        range_finalize<int32_t><<<1, 1, 0, st>>>((const int32_t *)x, n, h, d_verdict);
+        // every int32 value violates when the bounds miss the int32 range entirely
+        const int all_bad = lo > (int64_t)INT32_MAX || hi < (int64_t)INT32_MIN;
+        const int32_t lo32 = (int32_t)std::max<int64_t>(lo, INT32_MIN), hi32 = (int32_t)std::min<int64_t>(hi, INT32_MAX);
+        if (n > 0) range_kernel<int32_t><<<grid, STREAM_THREADS, 0, st>>>((const int32_t *)x, n, lo32, hi32, h);
+        range_finalize<int32_t><<<1, 1, 0, st>>>((const int32_t *)x, n, h, d_verdict, all_bad);
     } else {
         if (n > 0) range_kernel<int64_t><<<grid, STREAM_THREADS, 0, st>>>((const int64_t *)x, n, lo, hi, h);
-        range_finalize<int64_t><<<1, 1, 0, st>>>((const int64_t *)x, n, h, d_verdict);
+        range_finalize<int64_t><<<1, 1, 0, st>>>((const int64_t *)x, n, h, d_verdict, 0);
     }
     return launch_status();
 }

@@ -24,6 +24,7 @@
 // elements' destinations need the total count of trues before anything is written.
 #include <algorithm>
 #include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -48,11 +49,25 @@ static Wait wait_config() {
     return g_wait;
 }
 
+// One 16-byte status word per tile: {value, flag}, written and read with single
+// 16-byte accesses so that one load returns a consistent pair. flag: 0 empty,
+// 1 aggregate, 2 inclusive prefix; bit 2: the aggregate holds a segment head.
 struct Lookback {
-    unsigned *flag;            // 0 empty, 1 aggregate, 2 inclusive; bit 2: aggregate holds a segment head
-    unsigned long long *agg;   // tile aggregate
-    unsigned long long *incl;  // inclusive prefix through this tile
+    ulonglong2 *st;
 };
+
+__device__ __forceinline__ void publish_status(ulonglong2 *p, unsigned long long value, unsigned long long flag) {
+    asm volatile("st.global.cg.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(value), "l"(flag) : "memory");
+}
+__device__ __forceinline__ ulonglong2 read_status(const ulonglong2 *p) {
+    ulonglong2 v;
+    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+    return v;
+}
+
+// Look-back window: each lane reads LB_PER_LANE consecutive predecessors, so one
+// round trip covers 32 * LB_PER_LANE tiles.
+constexpr int LB_PER_LANE = 4;
 
 struct SP {
     unsigned f;
@@ -69,50 +84,63 @@ __device__ __forceinline__ SP shfl_sp(SP a, int src) { return SP{__shfl_sync(FUL
 
 // Called by all 32 lanes of one warp. Publishes `agg` for tile t, waits for the
 // predecessors and returns the exclusive prefix of tile t (same value in every lane).
+// Lane l reads tiles top - 4l - 0..3 (nearest first); the window is combined in
+// order with the segmented-sum operator and the walk stops at the nearest tile
+// whose inclusive prefix is known or whose aggregate holds a segment head.
 __device__ SP lookback(const Lookback L, int64_t t, SP agg, Hdr *h, Wait wt) {
     const int lane = threadIdx.x & 31;
     const bool publish = t != wt.skip_tile;
     if (t == 0) {
-        if (lane == 0 && publish) {
-            L.incl[0] = agg.v;
-            st_release_u32(L.flag, 2u | (agg.f << 2));
-        }
+        if (lane == 0 && publish) publish_status(L.st, agg.v, 2ull | ((unsigned long long)agg.f << 2));
         return SP{0u, 0ull};
     }
-    if (lane == 0 && publish) {
-        L.agg[t] = agg.v;
-        st_release_u32(L.flag + t, 1u | (agg.f << 2));
-    }
+    if (lane == 0 && publish) publish_status(L.st + t, agg.v, 1ull | ((unsigned long long)agg.f << 2));
     SP excl{0u, 0ull};
     int64_t top = t - 1;
     long long spins = 0;
     bool gave_up = false;
     while (true) {
-        const int64_t j = top - lane;
-        unsigned f = j >= 0 ? ld_acquire_u32(L.flag + j) : 2u;
-        bool virt = j < 0;
-        while (__any_sync(FULL, (f & 3u) == 0u)) {
-            if ((f & 3u) == 0u) f = ld_acquire_u32(L.flag + j);
+        ulonglong2 w[LB_PER_LANE];
+#pragma unroll
+        for (int q = 0; q < LB_PER_LANE; q++) {
+            const int64_t j = top - (int64_t)lane * LB_PER_LANE - q;
+            w[q] = j >= 0 ? read_status(L.st + j) : make_ulonglong2(0ull, 2ull);
+        }
+        while (true) {
+            bool pending = false;
+#pragma unroll
+            for (int q = 0; q < LB_PER_LANE; q++) pending |= (w[q].y & 3ull) == 0ull;
+            if (!__any_sync(FULL, pending)) break;
             if (++spins > wt.spin_limit) {
-                if ((f & 3u) == 0u) {
-                    f = 2u;
-                    virt = true;
-                    gave_up = true;
-                }
-            } else if (spins > 32) {
-                __nanosleep(64);
+#pragma unroll
+                for (int q = 0; q < LB_PER_LANE; q++)
+                    if ((w[q].y & 3ull) == 0ull) {
+                        w[q] = make_ulonglong2(0ull, 2ull);
+                        gave_up = true;
+                    }
+                break;
+            }
+            if (spins > 16) __nanosleep(32);
+#pragma unroll
+            for (int q = 0; q < LB_PER_LANE; q++) {
+                const int64_t j = top - (int64_t)lane * LB_PER_LANE - q;
+                if ((w[q].y & 3ull) == 0ull) w[q] = read_status(L.st + j);
             }
         }
-        const unsigned stop = __ballot_sync(FULL, (f & 3u) == 2u || (f & 4u));
-        const int L0 = stop ? __ffs(stop) - 1 : 32;
+        // combine this lane's tiles (farthest first), cutting at the nearest stopper
         SP mine{0u, 0ull};
-        if (lane < L0) {
-            mine = SP{0u, ld_relaxed_u64(L.agg + j)};
-        } else if (lane == L0) {
-            unsigned long long v = 0;
-            if (!virt) v = (f & 3u) == 2u ? ld_relaxed_u64(L.incl + j) : ld_relaxed_u64(L.agg + j);
-            mine = SP{1u, v};
+        bool stop_here = false;
+#pragma unroll
+        for (int q = 0; q < LB_PER_LANE; q++) {
+            if (stop_here) continue;
+            const bool stopper = (w[q].y & 3ull) == 2ull || (w[q].y & 4ull);
+            SP e{stopper ? 1u : 0u, w[q].x};
+            mine = sp_op(e, mine);  // tile q is earlier than tiles 0..q-1
+            stop_here = stopper;
         }
+        const unsigned stop = __ballot_sync(FULL, stop_here);
+        const int L0 = stop ? __ffs(stop) - 1 : 32;
+        if (lane > L0) mine = SP{0u, 0ull};
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             SP o = shfl_down_sp(mine, d);
@@ -120,13 +148,72 @@ __device__ SP lookback(const Lookback L, int64_t t, SP agg, Hdr *h, Wait wt) {
         }
         excl = sp_op(shfl_sp(mine, 0), excl);
         if (L0 < 32) break;
-        top -= 32;
+        top -= 32 * LB_PER_LANE;
     }
     if (gave_up && lane == 0) set_status(h, IXP_E_TIMEOUT);
-    if (lane == 0 && publish) {
-        L.incl[t] = sp_op(excl, agg).v;
-        st_release_u32(L.flag + t, 2u | (agg.f << 2));
+    if (lane == 0 && publish) publish_status(L.st + t, sp_op(excl, agg).v, 2ull | ((unsigned long long)agg.f << 2));
+    return excl;
+}
+
+// Plain-sum form of the look-back (no segment flags): the same protocol with
+// addition; the window is reduced with a butterfly since order does not matter.
+__device__ unsigned long long lookback_sum(const Lookback L, int64_t t, unsigned long long agg, Hdr *h, Wait wt) {
+    const int lane = threadIdx.x & 31;
+    const bool publish = t != wt.skip_tile;
+    if (t == 0) {
+        if (lane == 0 && publish) publish_status(L.st, agg, 2ull);
+        return 0ull;
     }
+    if (lane == 0 && publish) publish_status(L.st + t, agg, 1ull);
+    unsigned long long excl = 0;
+    int64_t top = t - 1;
+    long long spins = 0;
+    bool gave_up = false;
+    while (true) {
+        ulonglong2 w[LB_PER_LANE];
+#pragma unroll
+        for (int q = 0; q < LB_PER_LANE; q++) {
+            const int64_t j = top - (int64_t)lane * LB_PER_LANE - q;
+            w[q] = j >= 0 ? read_status(L.st + j) : make_ulonglong2(0ull, 2ull);
+        }
+        while (true) {
+            bool pending = false;
+#pragma unroll
+            for (int q = 0; q < LB_PER_LANE; q++) pending |= w[q].y == 0ull;
+            if (!__any_sync(FULL, pending)) break;
+            if (++spins > wt.spin_limit) {
+#pragma unroll
+                for (int q = 0; q < LB_PER_LANE; q++)
+                    if (w[q].y == 0ull) {
+                        w[q] = make_ulonglong2(0ull, 2ull);
+                        gave_up = true;
+                    }
+                break;
+            }
+            if (spins > 16) __nanosleep(32);
+#pragma unroll
+            for (int q = 0; q < LB_PER_LANE; q++) {
+                const int64_t j = top - (int64_t)lane * LB_PER_LANE - q;
+                if (w[q].y == 0ull) w[q] = read_status(L.st + j);
+            }
+        }
+        unsigned long long mine = 0;
+        bool stop_here = false;
+#pragma unroll
+        for (int q = 0; q < LB_PER_LANE; q++) {
+            if (stop_here) continue;
+            mine += w[q].x;
+            stop_here = w[q].y == 2ull;
+        }
+        const unsigned stop = __ballot_sync(FULL, stop_here);
+        const int L0 = stop ? __ffs(stop) - 1 : 32;
+        if (lane > L0) mine = 0;
+        excl += warp_sum_u64(mine);
+        if (L0 < 32) break;
+        top -= 32 * LB_PER_LANE;
+    }
+    if (gave_up && lane == 0) set_status(h, IXP_E_TIMEOUT);
+    if (lane == 0 && publish) publish_status(L.st + t, excl + agg, 2ull);
     return excl;
 }
 
@@ -292,6 +379,113 @@ __global__ void __launch_bounds__(TB) scan_kernel(const TI *__restrict__ in, TO 
     }
 }
 
+// Flat scan: plain sums in the output width (32-bit accumulators for int32
+// outputs), four 16-byte vectors per thread, at least four blocks per SM.
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(TB, 4) scan_flat_kernel(const TI *__restrict__ in, TO *__restrict__ out, int64_t n,
+                                                          int inclusive, Lookback L, Hdr *h, Wait wt, TO *total_out,
+                                                          int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(TI);
+    constexpr int TILE = TB * SUB * V;
+    using ACC = typename std::conditional<sizeof(TO) == 4, uint32_t, unsigned long long>::type;
+    __shared__ int64_t s_tile;
+    __shared__ ACC s_warp[TB / 32];
+    if (threadIdx.x == 0) s_tile = atomicAdd(&h->tile_ctr, 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int64_t t0 = t * TILE;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    ACC a[SUB][V];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        if (vec_ok && p0 + V <= n) {
+            if (V == 4) {
+                int4 v = __ldcs(reinterpret_cast<const int4 *>(in + p0));
+                a[u][0] = (ACC)(int64_t)v.x;
+                a[u][1 % V] = (ACC)(int64_t)v.y;
+                a[u][2 % V] = (ACC)(int64_t)v.z;
+                a[u][3 % V] = (ACC)(int64_t)v.w;
+            } else {
+                longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(in + p0));
+                a[u][0] = (ACC)v.x;
+                a[u][1 % V] = (ACC)v.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++) a[u][k] = (p0 + k < n) ? (ACC)(int64_t)in[p0 + k] : (ACC)0;
+        }
+    }
+    ACC carry = 0, lane_pre[SUB];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        ACC x = 0;
+#pragma unroll
+        for (int k = 0; k < V; k++) x += a[u][k];
+        ACC y = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            ACC o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y += o;
+        }
+        lane_pre[u] = carry + y - x;
+        carry += __shfl_sync(FULL, y, 31);
+    }
+    if (l == 0) s_warp[w] = carry;
+    __syncthreads();
+    if (w == 0) {
+        const ACC x = l < TB / 32 ? s_warp[l] : (ACC)0;
+        ACC y = x;
+#pragma unroll
+        for (int d = 1; d < TB / 32; d <<= 1) {
+            ACC o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y += o;
+        }
+        const ACC tile_agg = __shfl_sync(FULL, y, TB / 32 - 1);
+        const unsigned long long tile_ex = lookback_sum(L, t, (unsigned long long)tile_agg, h, wt);
+        __syncwarp();
+        if (l < TB / 32) s_warp[l] = (ACC)tile_ex + (y - x);
+        if (l == 0 && total_out && t0 + TILE >= n) *total_out = (TO)(tile_ex + (unsigned long long)tile_agg);
+    }
+    __syncthreads();
+    const ACC pre = s_warp[w];
+    constexpr int VO = 16 / sizeof(TO);
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        ACC run = pre + lane_pre[u];
+        TO o[V];
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            run += a[u][k];
+            o[k] = (TO)(inclusive ? run : run - a[u][k]);
+        }
+        if (vec_ok && p0 + V <= n) {
+#pragma unroll
+            for (int c = 0; c < V; c += VO) {
+                if (VO == 4) {
+                    int4 st4;
+                    st4.x = (int)o[c];
+                    st4.y = (int)o[(c + 1) % V];
+                    st4.z = (int)o[(c + 2) % V];
+                    st4.w = (int)o[(c + 3) % V];
+                    __stcs(reinterpret_cast<int4 *>(out + p0 + c), st4);
+                } else {
+                    longlong2 st2;
+                    st2.x = (long long)o[c];
+                    st2.y = (long long)o[(c + 1) % V];
+                    __stcs(reinterpret_cast<longlong2 *>(out + p0 + c), st2);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (p0 + k < n) out[p0 + k] = o[k];
+        }
+    }
+}
+
 // Segment totals after a segmented scan: tot[k] = inclusive value at the segment's
 // last element, 0 for an empty segment.
 template <typename TI, typename TO>
@@ -359,6 +553,46 @@ __device__ __forceinline__ void load_keys(const KT *keys, int64_t p0, int64_t n,
     }
 }
 
+// Loads V consecutive elements of type T at p0 (vector loads when aligned and
+// in range, guarded scalar loads otherwise; missing elements read as 0).
+template <typename T, int V>
+__device__ __forceinline__ void load_vec(const T *p, int64_t p0, int64_t n, int vec_ok, T (&o)[V]) {
+    constexpr int BYTES = (int)sizeof(T) * V;
+    if (vec_ok && p0 + V <= n) {
+        if (BYTES == 16 && sizeof(T) == 4) {
+            int4 v = __ldcs(reinterpret_cast<const int4 *>(p + p0));
+            o[0] = (T)v.x;
+            o[1 % V] = (T)v.y;
+            o[2 % V] = (T)v.z;
+            o[3 % V] = (T)v.w;
+            return;
+        }
+        if (BYTES == 16 && sizeof(T) == 8) {
+            longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(p + p0));
+            o[0] = (T)v.x;
+            o[1 % V] = (T)v.y;
+            return;
+        }
+        if (BYTES == 32) {
+            longlong2 a = __ldcs(reinterpret_cast<const longlong2 *>(p + p0));
+            longlong2 b = __ldcs(reinterpret_cast<const longlong2 *>(p + p0) + 1);
+            o[0] = (T)a.x;
+            o[1 % V] = (T)a.y;
+            o[2 % V] = (T)b.x;
+            o[3 % V] = (T)b.y;
+            return;
+        }
+        if (BYTES == 8) {
+            int2 v = __ldcs(reinterpret_cast<const int2 *>(p + p0));
+            o[0] = (T)v.x;
+            o[1 % V] = (T)v.y;
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < V; k++) o[k] = (p0 + k < n) ? p[p0 + k] : (T)0;
+}
+
 // In-tile exclusive counts. Inputs: per sub-chunk u, V-bit masks kt (kept and
 // true) and kk (kept). Output: per u, the packed exclusive count (kk << 16 | kt)
 // of the elements before this thread's vector in the tile, and the tile total.
@@ -402,7 +636,7 @@ __device__ __forceinline__ unsigned long long widen(unsigned packed) {
 // kept << 32 | kept_true), the grand total in h->total, and the prefix at every
 // segment start in seg_cnt[k] (k = 0..nseg).
 template <typename KT, bool SEG>
-__global__ void __launch_bounds__(TB) count_kernel(const KT *__restrict__ keys, int64_t n, DPred filt, DPred part,
+__global__ void __launch_bounds__(TB, 4) count_kernel(const KT *__restrict__ keys, int64_t n, DPred filt, DPred part,
                                                    const int64_t *__restrict__ off, int64_t nseg, Lookback L,
                                                    unsigned long long *tile_prefix, unsigned long long *seg_cnt,
                                                    Hdr *h, Wait wt, int vec_ok) {
@@ -436,11 +670,11 @@ __global__ void __launch_bounds__(TB) count_kernel(const KT *__restrict__ keys, 
     unsigned pre[SUB];
     const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
     if (w == 0) {
-        SP ex = lookback(L, t, SP{0u, widen(tot)}, h, wt);
+        const unsigned long long ex = lookback_sum(L, t, widen(tot), h, wt);
         if (l == 0) {
-            tile_prefix[t] = ex.v;
-            s_pre = ex.v;
-            if (t1 == n) h->total = ex.v + widen(tot);
+            tile_prefix[t] = ex;
+            s_pre = ex;
+            if (t1 == n) h->total = ex + widen(tot);
         }
     }
     if (SEG) {
@@ -611,6 +845,216 @@ __global__ void __launch_bounds__(TB) partition_write_kernel(
     }
 }
 
+// Flat partition, pass 2, for payload rows of one 32-bit word: the tile's trues
+// land in one contiguous run [tp, tp + T_tile) and its falses in another, so the
+// keys and payload are first placed in tile order in shared memory and then
+// written out as two coalesced runs.
+template <typename KT, typename OT>
+__global__ void __launch_bounds__(TB, 4) partition_flat_kernel(
+    const KT *__restrict__ keys, int64_t n, DPred pred, const uint32_t *__restrict__ payload, OT *__restrict__ out_idx,
+    KT *__restrict__ out_keys, uint32_t *__restrict__ out_payload, const unsigned long long *__restrict__ tile_prefix,
+    const Hdr *h, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int TILE = TB * SUB * V;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ uint32_t s_pay[TILE];
+    __shared__ KT s_key[TILE];
+    const int64_t t = blockIdx.x;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned kt[SUB], kk[SUB];
+    KT kv[SUB][V];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        if (keys) load_vec<KT, V>(keys, p0, n, vec_ok, kv[u]);
+        else {
+#pragma unroll
+            for (int k = 0; k < V; k++) kv[u][k] = (KT)0;
+        }
+        kt[u] = kk[u] = 0;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            if (p0 + k < n) {
+                kk[u] |= 1u << k;
+                if (pred_eval(pred, (int64_t)kv[u][k], p0 + k)) kt[u] |= 1u << k;
+            }
+        }
+    }
+    unsigned pre[SUB];
+    const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
+    const int64_t tile_T = (int64_t)(tot & 0xffffu);
+    const int64_t tp = (int64_t)(tile_prefix[t] & 0xffffffffull);
+    const int64_t T = (int64_t)(h->total & 0xffffffffull);
+    const int64_t fbase = T + (t0 - tp);  // destination of the tile's first false
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        OT dst[V];
+        uint32_t pv[V];
+        if (out_payload) {
+            if (vec_ok && p0 + V <= n && V == 4) {
+                uint4 q = __ldcs(reinterpret_cast<const uint4 *>(payload + p0));
+                pv[0] = q.x;
+                pv[1 % V] = q.y;
+                pv[2 % V] = q.z;
+                pv[3 % V] = q.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; k++) pv[k] = (p0 + k < n) ? payload[p0 + k] : 0u;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            const int64_t r = (int64_t)((w * SUB + u) * 32 + l) * V + k;  // position in the tile
+            const int64_t lt = (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & ((1u << k) - 1u));
+            const bool c = (kt[u] >> k) & 1u;
+            const int64_t slot = c ? lt : tile_T + (r - lt);
+            dst[k] = (OT)(c ? tp + lt : fbase + (r - lt));
+            if (p0 + k < n) {
+                if (out_payload) s_pay[slot] = pv[k];
+                if (out_keys) s_key[slot] = (KT)kv[u][k];
+            }
+        }
+        if (vec_ok && p0 + V <= n && sizeof(OT) * V >= 16) {
+            if (sizeof(OT) == 4) {
+                int4 s4;
+                s4.x = (int)dst[0];
+                s4.y = (int)dst[1 % V];
+                s4.z = (int)dst[2 % V];
+                s4.w = (int)dst[3 % V];
+                __stcs(reinterpret_cast<int4 *>(out_idx + p0), s4);
+            } else {
+#pragma unroll
+                for (int c = 0; c < V; c += 2) {
+                    longlong2 s2;
+                    s2.x = (long long)dst[c];
+                    s2.y = (long long)dst[(c + 1) % V];
+                    __stcs(reinterpret_cast<longlong2 *>(out_idx + p0 + c), s2);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (p0 + k < n) out_idx[p0 + k] = dst[k];
+        }
+    }
+    if (!out_payload && !out_keys) return;
+    __syncthreads();
+    const int tile_n = (int)(t1 - t0);
+    for (int r = threadIdx.x; r < tile_n; r += TB) {
+        const int64_t d = r < tile_T ? tp + r : fbase + (r - tile_T);
+        if (d < 0 || d >= n) continue;  // only for an inconsistent header
+        if (out_payload) __stcs(out_payload + d, s_pay[r]);
+        if (out_keys) out_keys[d] = s_key[r];
+    }
+}
+
+// Flat InvFiltPart check in one pass (8 bytes per int32 element when it holds).
+// The kept/kept-true counts before each element come from the look-back. A kept
+// true element must hold exactly its rank; for kept false elements the quantity
+// Z[i] - (kept falses before i) must equal T (the total of kept trues), which is
+// only known at the end, so its minimum and maximum are reduced; a dropped element
+// must lie outside [0, N), so the smallest non-negative dropped Z is reduced. When
+// anything fails, an exact second pass finds the first wrong index.
+template <typename KT, typename ZT>
+__global__ void __launch_bounds__(TB, 4) filtpart_fast_kernel(const ZT *__restrict__ z, int64_t n,
+                                                              const KT *__restrict__ keys, DPred filt, DPred part,
+                                                              Lookback L, unsigned long long *tile_prefix, Hdr *h,
+                                                              Wait wt, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int TILE = TB * SUB * V;
+    __shared__ int64_t s_tile;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ unsigned long long s_pre;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&h->tile_ctr, 1u);
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned kt[SUB], kk[SUB];
+    ZT zv[SUB][V];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        int64_t kv[V];
+        load_keys<KT, V>(keys, p0, n, vec_ok, kv);
+        load_vec<ZT, V>(z, p0, n, vec_ok, zv[u]);
+        kt[u] = kk[u] = 0;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            if (p0 + k < n && pred_eval(filt, kv[k], p0 + k)) {
+                kk[u] |= 1u << k;
+                if (pred_eval(part, kv[k], p0 + k)) kt[u] |= 1u << k;
+            }
+        }
+    }
+    unsigned pre[SUB];
+    const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
+    if (w == 0) {
+        const unsigned long long ex = lookback_sum(L, t, widen(tot), h, wt);
+        if (l == 0) {
+            tile_prefix[t] = ex;
+            s_pre = ex;
+            if (t1 == n) h->total = ex + widen(tot);
+        }
+    }
+    __syncthreads();
+    const int64_t ct0 = (int64_t)(s_pre & 0xffffffffull), ck0 = (int64_t)(s_pre >> 32);
+    int64_t bad = INT64_MAX, qmin = INT64_MAX, qmax = INT64_MIN, dmin = INT64_MAX;
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            const int64_t i = p0 + k;
+            if (i >= n) continue;
+            const unsigned below = (1u << k) - 1u;
+            const int64_t ct = ct0 + (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & below);
+            const int64_t ck = ck0 + (int64_t)(pre[u] >> 16) + __popc(kk[u] & below);
+            const int64_t zi = (int64_t)zv[u][k];
+            if ((kk[u] >> k) & 1u) {
+                if ((kt[u] >> k) & 1u) {
+                    if (zi != ct) bad = i < bad ? i : bad;
+                } else {
+                    const int64_t q = zi - (ck - ct);
+                    qmin = q < qmin ? q : qmin;
+                    qmax = q > qmax ? q : qmax;
+                }
+            } else if (zi >= 0) {
+                dmin = zi < dmin ? zi : dmin;
+            }
+        }
+    }
+    __shared__ unsigned long long sm[TB / 32];
+    unsigned long long r = block_max_u64(bad == INT64_MAX ? 0ull : enc_first(bad), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+    r = block_max_u64(enc_min(qmin), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_min, r);
+    r = block_max_u64(enc_max(qmax), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_max, r);
+    r = block_max_u64(enc_min(dmin), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first2, r);
+}
+
+// Decides whether the one-pass result proves the property; if not, clears the
+// candidate index and raises the flag that enables the exact pass.
+__global__ void filtpart_decide_kernel(Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    if (h->status) return;
+    const int64_t T = (int64_t)(h->total & 0xffffffffull), N = (int64_t)(h->total >> 32);
+    const bool has_false = h->k_max != 0;  // enc_max(INT64_MIN) == 0 means no kept false element
+    const int64_t qmin = dec_min(h->k_min), qmax = dec_max(h->k_max);
+    const int64_t dmin = dec_min(h->k_first2);
+    const bool ok = h->k_first == 0 && (!has_false || (qmin == T && qmax == T)) && dmin >= N;
+    if (!ok) {
+        h->k_first = 0;
+        h->flag = 1u;
+    }
+}
+
 __global__ void num_true_kernel(const unsigned long long *seg_cnt, const Hdr *h, int64_t nseg, int64_t *num_true) {
     IXP_KERNEL_ENTRY();
     if (nseg == 0) {
@@ -625,16 +1069,17 @@ __global__ void num_true_kernel(const unsigned long long *seg_cnt, const Hdr *h,
 // With `witness` set, only the tile holding the first mismatch runs (grid of 1)
 // and it stores that element's expected destination (+1, 0 for dropped) in k_aux.
 template <typename KT, typename ZT, bool SEG>
-__global__ void __launch_bounds__(TB) filtpart_cmp_kernel(
+__global__ void __launch_bounds__(TB, 4) filtpart_cmp_kernel(
     const ZT *__restrict__ z, int64_t n, const KT *__restrict__ keys, DPred filt, DPred part,
     const int64_t *__restrict__ off, int64_t nseg, const unsigned long long *__restrict__ tile_prefix,
-    const unsigned long long *__restrict__ seg_cnt, Hdr *h, int vec_ok, int witness) {
+    const unsigned long long *__restrict__ seg_cnt, Hdr *h, int vec_ok, int witness, int need_flag) {
     IXP_KERNEL_ENTRY();
     constexpr int V = 16 / sizeof(KT);
     constexpr int TILE = TB * SUB * V;
     __shared__ unsigned s_w[TB / 32];
     __shared__ int s_rel[SEG ? TILE : 1];
     __shared__ int64_t s_k0;
+    if (need_flag && !h->flag) return;
     int64_t t = blockIdx.x;
     int64_t target = -1;
     if (witness) {
@@ -753,7 +1198,7 @@ static int launch_status() { return cudaGetLastError() == cudaSuccess ? IXP_OK :
 static int64_t ntiles_for(int64_t n, int V) { return (n + (int64_t)TB * SUB * V - 1) / ((int64_t)TB * SUB * V); }
 
 // Workspace layout for the tiled passes (all offsets 256-aligned):
-//   header | flags u32[T] | agg u64[T] | incl u64[T] | tile_prefix u64[T] | seg_cnt u64[nseg+1]
+//   header | status {u64, u64}[T] | tile_prefix u64[T] | seg_cnt u64[nseg+1]
 struct TileWs {
     Hdr *h;
     Lookback L;
@@ -769,12 +1214,8 @@ static TileWs tile_ws(void *ws, int64_t ntiles, int64_t nseg) {
     char *p = (char *)ws;
     size_t o = HDR_BYTES;
     r.h = (Hdr *)p;
-    r.L.flag = (unsigned *)(p + o);
-    o += up256((size_t)ntiles * 4);
-    r.L.agg = (unsigned long long *)(p + o);
-    o += up256((size_t)ntiles * 8);
-    r.L.incl = (unsigned long long *)(p + o);
-    o += up256((size_t)ntiles * 8);
+    r.L.st = (ulonglong2 *)(p + o);
+    o += up256((size_t)ntiles * 16);
     r.tile_prefix = (unsigned long long *)(p + o);
     o += up256((size_t)ntiles * 8);
     r.seg_cnt = (unsigned long long *)(p + o);
@@ -815,7 +1256,7 @@ static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs se
     int rc = ws_ok(ws, ws_bytes, W.bytes);
     if (rc) return rc;
     if (cudaMemsetAsync(ws, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
-    if (nt > 0 && cudaMemsetAsync(W.L.flag, 0, (size_t)nt * 4, st) != cudaSuccess) return IXP_E_CUDA;
+    if (nt > 0 && cudaMemsetAsync(W.L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;
     if (d_status && !keep_status && cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return IXP_E_CUDA;
     if (!seg && tot && n == 0 && cudaMemsetAsync(tot, 0, sizeof(TO), st) != cudaSuccess) return IXP_E_CUDA;
     const int vec = aligned16(in) && aligned16(out);
@@ -825,8 +1266,7 @@ static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs se
             scan_kernel<TI, TO, true><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, segs.offsets, segs.nseg,
                                                                   W.L, W.h, wt, nullptr, vec);
         else
-            scan_kernel<TI, TO, false><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, nullptr, 0, W.L, W.h, wt,
-                                                                   tot, vec);
+            scan_flat_kernel<TI, TO><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, W.L, W.h, wt, tot, vec);
     }
     if (seg && tot && segs.nseg > 0) {
         int g = (int)std::min<int64_t>((segs.nseg + 255) / 256, 4096);
@@ -841,7 +1281,7 @@ static int run_counts(const KT *keys, int64_t n, DPred filt, DPred part, ixp_seg
                       int vec, cudaStream_t st) {
     const bool seg = segs.offsets != nullptr;
     if (cudaMemsetAsync(W.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
-    if (nt > 0 && cudaMemsetAsync(W.L.flag, 0, (size_t)nt * 4, st) != cudaSuccess) return IXP_E_CUDA;
+    if (nt > 0 && cudaMemsetAsync(W.L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;
     if (seg && cudaMemsetAsync(W.seg_cnt, 0, (size_t)(segs.nseg + 1) * 8, st) != cudaSuccess) return IXP_E_CUDA;
     const Wait wt = wait_config();
     if (nt > 0) {
@@ -870,7 +1310,11 @@ static int run_partition(const KT *keys, int64_t n, ixp_pred pred, const void *p
     if (d_status && cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return IXP_E_CUDA;
     rc = run_counts<KT>(keys, n, all, dpred(pred), segs, W, nt, vec, st);
     if (rc) return rc;
-    if (nt > 0) {
+    if (nt > 0 && !seg && (!out_payload || row_bytes == 4)) {
+        partition_flat_kernel<KT, OT><<<(unsigned)nt, TB, 0, st>>>(keys, n, dpred(pred), (const uint32_t *)payload,
+                                                                  out_idx, out_keys, (uint32_t *)out_payload,
+                                                                  W.tile_prefix, W.h, vec && aligned16(payload));
+    } else if (nt > 0) {
         if (seg)
             partition_write_kernel<KT, OT, true><<<(unsigned)nt, TB, 0, st>>>(
                 keys, n, dpred(pred), (const uint32_t *)payload, row_bytes / 4, out_idx, out_keys,
@@ -897,20 +1341,28 @@ static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, i
     int rc = ws_ok(ws, ws_bytes, W.bytes);
     if (rc) return rc;
     const int vec = keys == nullptr || aligned16(keys);
+    if (!seg) {
+        if (cudaMemsetAsync(W.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+        if (nt > 0 && cudaMemsetAsync(W.L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;
+        if (nt > 0) {
+            filtpart_fast_kernel<KT, ZT><<<(unsigned)nt, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), W.L,
+                                                                     W.tile_prefix, W.h, wait_config(), vec);
+            filtpart_decide_kernel<<<1, 1, 0, st>>>(W.h);
+            filtpart_cmp_kernel<KT, ZT, false><<<(unsigned)nt, TB, 0, st>>>(
+                z, n, keys, dpred(filt), dpred(part), nullptr, 0, W.tile_prefix, nullptr, W.h, vec, 0, 1);
+            filtpart_cmp_kernel<KT, ZT, false><<<1, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), nullptr, 0,
+                                                                W.tile_prefix, nullptr, W.h, vec, 1, 1);
+        }
+        filtpart_finalize<ZT><<<1, 1, 0, st>>>(z, W.h, out);
+        return launch_status();
+    }
     rc = run_counts<KT>(keys, n, dpred(filt), dpred(part), segs, W, nt, vec, st);
     if (rc) return rc;
     if (nt > 0) {
-        if (seg) {
-            filtpart_cmp_kernel<KT, ZT, true><<<(unsigned)nt, TB, 0, st>>>(
-                z, n, keys, dpred(filt), dpred(part), segs.offsets, segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec, 0);
-            filtpart_cmp_kernel<KT, ZT, true><<<1, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), segs.offsets,
-                                                               segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec, 1);
-        } else {
-            filtpart_cmp_kernel<KT, ZT, false><<<(unsigned)nt, TB, 0, st>>>(
-                z, n, keys, dpred(filt), dpred(part), nullptr, 0, W.tile_prefix, nullptr, W.h, vec, 0);
-            filtpart_cmp_kernel<KT, ZT, false><<<1, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), nullptr, 0,
-                                                                W.tile_prefix, nullptr, W.h, vec, 1);
-        }
+        filtpart_cmp_kernel<KT, ZT, true><<<(unsigned)nt, TB, 0, st>>>(
+            z, n, keys, dpred(filt), dpred(part), segs.offsets, segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec, 0, 0);
+        filtpart_cmp_kernel<KT, ZT, true><<<1, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), segs.offsets,
+                                                           segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec, 1, 0);
     }
     filtpart_finalize<ZT><<<1, 1, 0, st>>>(z, W.h, out);
     return launch_status();
@@ -946,7 +1398,7 @@ extern "C" int ixp_partition(const void *keys, int ktype, int64_t n, ixp_pred pr
                              ixp_stream stream) {
     if ((keys && ktype != IXP_I32 && ktype != IXP_I64) || (out_type != IXP_I32 && out_type != IXP_I64))
         return IXP_E_DTYPE;
-    if (n < 0 || n >= (1ll << 32) || (n > 0 && !out_indices) || !d_num_true || !pred_ok(pred, keys != nullptr))
+    if (n < 0 || n >= (1ll << 32) || (n > 0 && !out_indices) || !d_num_true || !pred_ok(pred, keys != nullptr || n == 0))
         return IXP_E_INVAL;
     if (out_type == IXP_I32 && n > INT32_MAX) return IXP_E_INVAL;
     if ((out_keys && !keys) || (out_payload && (!payload || row_bytes <= 0 || row_bytes % 4 || row_bytes > 64)))
@@ -973,7 +1425,7 @@ extern "C" int ixp_check_filtpart(const void *z, int ztype, int64_t n, const voi
                                   ixp_stream stream) {
     if ((ztype != IXP_I32 && ztype != IXP_I64) || (keys && ktype != IXP_I32 && ktype != IXP_I64)) return IXP_E_DTYPE;
     if (n < 0 || n >= (1ll << 32) || (n > 0 && !z) || !d_verdict) return IXP_E_INVAL;
-    if (!pred_ok(filt, keys != nullptr) || !pred_ok(part, keys != nullptr)) return IXP_E_INVAL;
+    if (!pred_ok(filt, keys != nullptr || n == 0) || !pred_ok(part, keys != nullptr || n == 0)) return IXP_E_INVAL;
     if ((segs.offsets && segs.nseg < 1) || (!segs.offsets && segs.nseg != 0)) return IXP_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const bool k64 = keys && ktype == IXP_I64;

@@ -11,6 +11,10 @@
 
 namespace ixp {
 
+// Rows move as 16-byte chunks when the row size is a multiple of 16 (vec16); each
+// thread keeps RU rows in flight (indices first, then all row loads, then stores).
+constexpr int RU = 4;
+
 template <typename IT>
 __global__ void __launch_bounds__(STREAM_THREADS) scatter_rows_kernel(char *__restrict__ dst, int64_t dst_len,
                                                                       const IT *__restrict__ idx,
@@ -18,18 +22,41 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_rows_kernel(char *__re
                                                                       int row_bytes, int vec16) {
     IXP_KERNEL_ENTRY();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (vec16 && row_bytes <= 64) {
+        const int nc = row_bytes / 16;
+        for (int64_t i0 = tid; i0 < n; i0 += RU * stride) {
+            int64_t d[RU];
+            int4 v[RU][4];
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                const int64_t i = i0 + u * stride;
+                d[u] = i < n ? (int64_t)__ldcs(idx + i) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                const int64_t i = i0 + u * stride;
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (c < nc && i < n) v[u][c] = __ldcs(reinterpret_cast<const int4 *>(vals + i * row_bytes) + c);
+            }
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                if (d[u] < 0 || d[u] >= dst_len) continue;
+                int4 *t = reinterpret_cast<int4 *>(dst + d[u] * row_bytes);
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (c < nc) __stcs(t + c, v[u][c]);
+            }
+        }
+        return;
+    }
+    for (int64_t i = tid; i < n; i += stride) {
         const int64_t d = (int64_t)__ldg(idx + i);
         if (d < 0 || d >= dst_len) continue;
-        if (vec16) {
-            const int4 *s = reinterpret_cast<const int4 *>(vals + i * row_bytes);
-            int4 *t = reinterpret_cast<int4 *>(dst + d * row_bytes);
-            for (int c = 0; c < row_bytes / 16; c++) t[c] = __ldcs(s + c);
-        } else {
-            const uint32_t *s = reinterpret_cast<const uint32_t *>(vals + i * row_bytes);
-            uint32_t *t = reinterpret_cast<uint32_t *>(dst + d * row_bytes);
-            for (int c = 0; c < row_bytes / 4; c++) t[c] = s[c];
-        }
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(vals + i * row_bytes);
+        uint32_t *t = reinterpret_cast<uint32_t *>(dst + d * row_bytes);
+        for (int c = 0; c < row_bytes / 4; c++) t[c] = src[c];
     }
 }
 
@@ -99,20 +126,49 @@ __global__ void __launch_bounds__(STREAM_THREADS) gather_rows_kernel(char *__res
                                                                      int row_bytes, int vec16, int32_t *status) {
     IXP_KERNEL_ENTRY();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-        const int64_t s = (int64_t)__ldg(idx + i);
-        const bool ok = s >= 0 && s < src_len;
-        if (!ok && status) atomicCAS(status, 0, IXP_E_OOB);
-        if (vec16) {
-            int4 *t = reinterpret_cast<int4 *>(out + i * row_bytes);
-            const int4 *f = reinterpret_cast<const int4 *>(src + (ok ? s : 0) * row_bytes);
-            for (int c = 0; c < row_bytes / 16; c++) __stcs(t + c, ok ? __ldg(f + c) : make_int4(0, 0, 0, 0));
-        } else {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool any_oob = false;
+    if (vec16 && row_bytes <= 64) {
+        const int nc = row_bytes / 16;
+        for (int64_t i0 = tid; i0 < n; i0 += RU * stride) {
+            int64_t s[RU];
+            int4 v[RU][4];
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                const int64_t i = i0 + u * stride;
+                s[u] = i < n ? (int64_t)__ldcs(idx + i) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                const int64_t i = i0 + u * stride;
+                const bool ok = s[u] >= 0 && s[u] < src_len;
+                if (i < n && !ok) any_oob = true;
+                const int4 *f = reinterpret_cast<const int4 *>(src + (ok ? s[u] : 0) * row_bytes);
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (c < nc) v[u][c] = (ok && i < n) ? __ldg(f + c) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                const int64_t i = i0 + u * stride;
+                if (i >= n) continue;
+                int4 *t = reinterpret_cast<int4 *>(out + i * row_bytes);
+#pragma unroll
+                for (int c = 0; c < 4; c++)
+                    if (c < nc) __stcs(t + c, v[u][c]);
+            }
+        }
+    } else {
+        for (int64_t i = tid; i < n; i += stride) {
+            const int64_t s = (int64_t)__ldg(idx + i);
+            const bool ok = s >= 0 && s < src_len;
+            if (!ok) any_oob = true;
             uint32_t *t = reinterpret_cast<uint32_t *>(out + i * row_bytes);
             const uint32_t *f = reinterpret_cast<const uint32_t *>(src + (ok ? s : 0) * row_bytes);
             for (int c = 0; c < row_bytes / 4; c++) t[c] = ok ? __ldg(f + c) : 0u;
         }
     }
+    if (any_oob && status) atomicCAS(status, 0, IXP_E_OOB);
 }
 
 static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }

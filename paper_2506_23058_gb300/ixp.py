@@ -333,13 +333,14 @@ def gather(src, idx, *, out=None, status=None, stream=None):
     return out, status
 
 
-def flags_from_shape(shape, xs=None, out_dtype=torch.int64, out_len=None, *, stream=None):
+def flags_from_shape(shape, xs=None, out_dtype=torch.int64, out_len=None, *, out=None, offsets=None, status=None,
+                     ws=None, stream=None):
     """mkSgmDescr. Returns (flags, offsets, status). out_len=None reads sum(shape) (one sync)."""
     m = shape.numel()
-    offs = torch.empty(m + 1, dtype=torch.int64, device=shape.device)
-    status = torch.zeros(1, dtype=torch.int32, device=shape.device)
+    offs = offsets if offsets is not None else torch.empty(m + 1, dtype=torch.int64, device=shape.device)
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=shape.device)
     need = workspace_size("flags", 1, m)
-    ws = workspace(need, shape.device)
+    ws = ws if ws is not None else workspace(need, shape.device)
     xp = None if xs is None else _dev(xs, "xs")
     if out_len is None:
         _ck(load().ixp_flags_from_shape(_dev(shape, "shape"), m, xp, None, 1, 0, offs.data_ptr(), status.data_ptr(),
@@ -347,11 +348,11 @@ def flags_from_shape(shape, xs=None, out_dtype=torch.int64, out_len=None, *, str
         out_len = int(offs[m].item()) if m else 0
         if status.item() != 0:
             raise IxpError(int(status.item()), "flags_from_shape")
-    out = torch.empty(out_len, dtype=out_dtype, device=shape.device)
+    if out is None:
+        out = torch.empty(out_len, dtype=out_dtype, device=shape.device)
     _ck(load().ixp_flags_from_shape(_dev(shape, "shape"), m, xp, out.data_ptr() if out_len else None,
-                                    0 if out_dtype == torch.int32 else 1, out_len, offs.data_ptr(),
-                                    status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)),
-        "flags_from_shape")
+                                    _itype(out), out_len, offs.data_ptr(), status.data_ptr(), ws.data_ptr(),
+                                    ws.numel(), _stream(stream)), "flags_from_shape")
     return out, offs, status
 
 

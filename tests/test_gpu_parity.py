@@ -135,7 +135,7 @@ def test_inj_many_duplicates_and_edges(ixp, dev, dtype):
     for n in [10, 1000, 50000]:
         a = rng.integers(0, n // 2 + 1, size=n).astype(dtype)
         same(ixp.check_inj(T(a, dev)), oracle.check_inj(a), n)
-        same(ixp.check_inj(T(a, dev), 3, n // 4), oracle.check_inj(a, 3, n // 4), n)
+        same(ixp.check_inj(T(a, dev), 3, max(3, n // 4)), oracle.check_inj(a, 3, max(3, n // 4)), n)
     n = 40000
     for p, q in [(0, 1), (0, n - 1), (n - 2, n - 1), (4095, 4096), (17, 30000)]:
         a = synth.permutation(n, 11, dtype)
