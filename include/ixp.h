@@ -237,6 +237,32 @@ int ixp_flags_from_shape(const int64_t *shape, int64_t m, const int64_t *xs, voi
                          int64_t out_len, int64_t *d_offsets, int32_t *d_status, void *ws, size_t ws_bytes,
                          ixp_stream stream);
 
+/* ---- allocation-free scan -------------------------------------------------------- */
+
+/* ixp_scan for callers that cannot allocate device memory at all: a host runtime
+ * whose device memory is fully planned before it starts, a process with a fixed
+ * device-memory budget, or code on a path where a cudaMalloc (which can
+ * synchronize the device) is not allowed. The paper has no counterpart; this is
+ * a library convenience. It computes exactly what ixp_scan computes for a flat
+ * array (segs = {NULL, 0}), but takes no workspace: its scratch (a 256-byte header
+ * and 16 bytes per tile of 4096 int32 or 2048 int64 inputs) is a fixed array of
+ * 262,400 bytes inside this library, which every GPU that loads the library holds
+ * until the process exits. n above ixp_scan_noalloc_max_n(in_type) (2^26 for int32
+ * input, 2^25 for int64) is rejected with IXP_E_INVAL; so are the argument errors
+ * of ixp_scan. The call allocates nothing: it clears the part of the array it
+ * uses with cudaMemsetAsync, then launches the scan.
+ *  - The first call on each device looks up the array's device address (with that
+ *    device current) and remembers it; make that first call before any stream
+ *    capture. A failed lookup returns IXP_E_CUDA.
+ *  - Every call on a device shares the one array. Calls whose work overlaps on the
+ *    GPU (different streams, or concurrent graph branches) race on it and give
+ *    wrong results; order them on one stream or with events. */
+int ixp_scan_noalloc(const void *in, int in_type, void *out, int out_type, int64_t n, int inclusive,
+                     void *d_totals, int32_t *d_status, ixp_stream stream);
+
+/* Largest n that ixp_scan_noalloc accepts for the given input type. */
+int64_t ixp_scan_noalloc_max_n(int in_type);
+
 /* ---- testing hook ------------------------------------------------------------ */
 
 /* Sets the bound on every device-side wait of later calls in this process (number

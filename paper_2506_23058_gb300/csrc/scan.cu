@@ -24,6 +24,7 @@
 // elements' destinations need the total count of trues before anything is written.
 #include <algorithm>
 #include <cstdlib>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -1469,6 +1470,78 @@ extern "C" int ixp_flags_from_shape(const int64_t *shape, int64_t m, const int64
         }
     }
     return launch_status();
+}
+
+// ---------------------------------------------------------------- no-alloc scan
+// A flat scan whose scratch (the call header and one 16-byte look-back status per
+// tile) lives in a fixed array in this library's own device memory instead of a
+// caller-provided workspace. The array is reached from host code only through the
+// address cudaGetSymbolAddress returns for the current device; the symbol itself is
+// a host-side stand-in.
+constexpr int64_t NOALLOC_MAX_TILES = 16384;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HDR_BYTES + NOALLOC_MAX_TILES * 16];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[256] = {};
+
+// First call on a device: look up the array's device address with that device
+// current and remember it. Returns nullptr on failure.
+void *noalloc_scratch_for_current_device() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return nullptr;
+        g_noalloc_addr[dev] = p;
+    }
+    return g_noalloc_addr[dev];
+}
+
+template <typename TI, typename TO>
+int run_scan_noalloc(const TI *in, TO *out, int64_t n, int inclusive, TO *tot, int32_t *d_status, cudaStream_t st) {
+    constexpr int V = 16 / sizeof(TI);
+    const int64_t nt = ntiles_for(n, V);
+    if (nt > NOALLOC_MAX_TILES) return IXP_E_INVAL;
+    void *base = noalloc_scratch_for_current_device();
+    if (!base) return IXP_E_CUDA;
+    Hdr *h = (Hdr *)base;
+    Lookback L;
+    L.st = (ulonglong2 *)((char *)base + HDR_BYTES);
+    // the array keeps the previous call's contents: clear the header and the statuses used
+    if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (nt > 0 && cudaMemsetAsync(L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return IXP_E_CUDA;
+    if (tot && n == 0 && cudaMemsetAsync(tot, 0, sizeof(TO), st) != cudaSuccess) return IXP_E_CUDA;
+    const int vec = aligned16(in) && aligned16(out);
+    if (nt > 0)
+        scan_flat_kernel<TI, TO><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, L, h, wait_config(), tot, vec);
+    if (d_status) status_copy_kernel<<<1, 1, 0, st>>>(h, d_status);
+    return launch_status();
+}
+}  // namespace
+
+extern "C" int64_t ixp_scan_noalloc_max_n(int in_type) {
+    const int V = in_type == IXP_I64 ? 2 : 4;
+    return NOALLOC_MAX_TILES * (int64_t)TB * SUB * V;
+}
+
+extern "C" int ixp_scan_noalloc(const void *in, int in_type, void *out, int out_type, int64_t n, int inclusive,
+                                void *d_totals, int32_t *d_status, ixp_stream stream) {
+    if ((in_type != IXP_I32 && in_type != IXP_I64) || (out_type != IXP_I32 && out_type != IXP_I64) ||
+        (in_type == IXP_I64 && out_type == IXP_I32))
+        return IXP_E_DTYPE;
+    if (n < 0 || (n > 0 && (!in || !out))) return IXP_E_INVAL;
+    if (n > ixp_scan_noalloc_max_n(in_type)) return IXP_E_INVAL;
+    const int es = in_type == IXP_I32 ? 4 : 8, eo = out_type == IXP_I32 ? 4 : 8;
+    if ((reinterpret_cast<uintptr_t>(in) % es) || (reinterpret_cast<uintptr_t>(out) % eo)) return IXP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (in_type == IXP_I32 && out_type == IXP_I32)
+        return run_scan_noalloc((const int32_t *)in, (int32_t *)out, n, inclusive, (int32_t *)d_totals, d_status, st);
+    if (in_type == IXP_I32)
+        return run_scan_noalloc((const int32_t *)in, (int64_t *)out, n, inclusive, (int64_t *)d_totals, d_status, st);
+    return run_scan_noalloc((const int64_t *)in, (int64_t *)out, n, inclusive, (int64_t *)d_totals, d_status, st);
 }
 
 extern "C" int ixp_debug_set_wait(long long spin_limit, long long skip_tile) {
