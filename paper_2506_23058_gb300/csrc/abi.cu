@@ -6,6 +6,7 @@
 namespace ixp {
 
 size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg);  // scan.cu
+size_t bk_prefix_bytes(int64_t n);                       // checks.cu
 
 int num_sms() {
     static int cached[64] = {0};
@@ -43,9 +44,12 @@ extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra
         case IXP_OP_MONO: return HDR_BYTES;
         case IXP_OP_INJ:
         case IXP_OP_BIJ: {
+            // large inputs also get the bucket pool (about 5 bytes per element)
             int64_t span = extra > 0 ? extra : n;
+            if (span < (1 << 21)) span = 1 << 21;
             size_t words = (size_t)((span + 31) / 32);
-            return HDR_BYTES + round256(2 * words * 4 + 256);
+            size_t prefix = n >= (1 << 18) ? bk_prefix_bytes(n) : HDR_BYTES;
+            return prefix + round256(2 * words * 4 + 256);
         }
         case IXP_OP_SCAN: return tiled_ws_bytes(n, 16 / es, extra);
         case IXP_OP_PARTITION:

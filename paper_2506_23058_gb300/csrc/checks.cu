@@ -550,6 +550,293 @@ __global__ void bij_finalize(const T *x, const Hdr *h, ixp_verdict *out, int64_t
     *out = v;
 }
 
+// ============================================== Inj / Bij, value-bucketed path
+// For large spans the bitmap is split into B buckets of W = 2^lw consecutive
+// values. Pass 1 reads X once and writes each in-range value's offset (rel mod W)
+// into its bucket's region of a pool: a block sorts its tile by bucket in shared
+// memory (a counting sort), reserves space with one atomicAdd per bucket, and writes
+// contiguous runs. Pass 2 gives each bucket one block with a W-bit shared-memory
+// bitmap and sets one bit per stored offset; the atomicOr's return value flags a
+// repeat, which is recorded in the global repeat bitmap for the witness passes.
+// A bucket that receives more values than its pool region holds sends the excess
+// through L2 atomics on the global mark bitmap (pass 1), and pass 2 merges those
+// bits before it sets its own, so skewed inputs stay exact.
+constexpr int BK_TILE = 8192;
+constexpr int BK_THREADS = 256;
+constexpr unsigned BK_MAX = 4096;
+constexpr unsigned BK_INVALID = 0xffffffffu;
+
+struct BucketCfg {
+    unsigned lw;                // log2 of the bucket width W (values per bucket)
+    unsigned bmax;              // bucket count the launch shapes are sized for
+    unsigned long long pool;    // pool capacity in entries
+};
+
+__global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, unsigned long long cap_bits,
+                                    BucketCfg cfg, unsigned *cursors, unsigned *marks, unsigned *dup) {
+    IXP_KERNEL_ENTRY();
+    unsigned long long base = 0, span = 0;
+    bool too_big = false;
+    if (fixed) {
+        base = (unsigned long long)lo;
+        span = (unsigned long long)hi - (unsigned long long)lo + 1ull;
+        too_big = span == 0 || span > cap_bits;
+    } else {
+        const int64_t mn = dec_min(h->k_min), mx = dec_max(h->k_max);
+        if (mn <= mx) {
+            const unsigned long long d = (unsigned long long)mx - (unsigned long long)mn;
+            too_big = d >= cap_bits;
+            base = (unsigned long long)mn;
+            span = d + 1ull;
+        }
+    }
+    const unsigned long long nb = too_big ? 0ull : (span + (1ull << cfg.lw) - 1ull) >> cfg.lw;
+    if (too_big || nb > cfg.bmax) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, IXP_E_SPAN);
+        return;
+    }
+    const unsigned long long cap = nb ? (cfg.pool / nb) & ~3ull : 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        h->base = base;
+        h->span = span;
+        h->spare[0] = nb;
+        h->spare[1] = cap;
+    }
+    const unsigned long long words = (span + 31) / 32;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long w = tid; w < words; w += stride) {
+        marks[w] = 0u;
+        dup[w] = 0u;
+    }
+    for (unsigned long long b = tid; b < nb; b += stride) cursors[b] = 0u;
+}
+
+template <typename T, bool BIJ>
+__global__ void __launch_bounds__(BK_THREADS, 2) bucket_scatter_kernel(
+    const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, int64_t mlo, int64_t mhi, Hdr *h, BucketCfg cfg,
+    unsigned *__restrict__ cursors, unsigned *__restrict__ pool, unsigned *__restrict__ marks,
+    unsigned *__restrict__ dup, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    if (h->status) return;
+    constexpr int V = Vec<T>::N;
+    constexpr int NV = BK_TILE / V / BK_THREADS;  // 16-byte vectors per thread per tile
+    extern __shared__ unsigned bk_smem[];
+    unsigned *s_sorted = bk_smem;              // BK_TILE
+    unsigned *s_cnt = s_sorted + BK_TILE;      // bmax
+    unsigned *s_start = s_cnt + cfg.bmax;      // bmax
+    unsigned *s_gpos = s_start + cfg.bmax;     // bmax
+    __shared__ unsigned s_wsum[BK_THREADS / 32];
+    __shared__ unsigned s_total;
+    const unsigned long long base = h->base, span = h->span;
+    const unsigned nb = (unsigned)h->spare[0];
+    const unsigned long long cap = h->spare[1];
+    const unsigned lw = cfg.lw;
+    const unsigned long long wmask = (1ull << lw) - 1ull;
+    const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    unsigned long long valid = 0;  // kept by thread 0 only
+    unsigned anydup = 0;
+    int64_t ooi = INT64_MAX;
+    const unsigned per = (nb + BK_THREADS - 1) / BK_THREADS;  // bucket-count scan entries per thread
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t t0 = tile * BK_TILE;
+        for (unsigned b = tid; b < nb; b += BK_THREADS) s_cnt[b] = 0u;
+        // A: all loads first, then classify into (bucket << lw | offset), kept in registers
+        T e[NV][V];
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+            const int64_t p0 = t0 + (int64_t)(j * BK_THREADS + tid) * V;
+            if (vec_ok && p0 + V <= n) {
+                if (V == 4) {
+                    int4 v = __ldcs(reinterpret_cast<const int4 *>(x + p0));
+                    e[j][0] = (T)v.x;
+                    e[j][1 % V] = (T)v.y;
+                    e[j][2 % V] = (T)v.z;
+                    e[j][3 % V] = (T)v.w;
+                } else {
+                    longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(x + p0));
+                    e[j][0] = (T)v.x;
+                    e[j][1 % V] = (T)v.y;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < V; c++) e[j][c] = (p0 + c < n) ? x[p0 + c] : (T)0;
+            }
+        }
+        __syncthreads();  // s_cnt zeroed
+        unsigned st[NV][V];
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+            const int64_t p0 = t0 + (int64_t)(j * BK_THREADS + tid) * V;
+#pragma unroll
+            for (int c = 0; c < V; c++) {
+                const int64_t xi = (int64_t)e[j][c];
+                unsigned sv = BK_INVALID;
+                if (p0 + c < n && xi >= rlo && xi <= rhi) {
+                    if (BIJ && (xi < mlo || xi > mhi)) {
+                        ooi = (p0 + c) < ooi ? (p0 + c) : ooi;
+                    } else {
+                        const unsigned long long rel = (unsigned long long)xi - base;
+                        if (rel < span) {
+                            const unsigned b = (unsigned)(rel >> lw);
+                            atomicAdd(&s_cnt[b], 1u);
+                            sv = (b << lw) | (unsigned)(rel & wmask);
+                        }
+                    }
+                }
+                st[j][c] = sv;
+            }
+        }
+        __syncthreads();
+        // B: exclusive scan of the bucket counts, then reserve pool space per bucket
+        {
+            unsigned loc = 0;
+            const unsigned b0 = tid * per;
+            for (unsigned k = 0; k < per; k++)
+                if (b0 + k < nb) loc += s_cnt[b0 + k];
+            unsigned y = loc;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned o = __shfl_up_sync(FULL, y, d);
+                if (lane >= d) y += o;
+            }
+            if (lane == 31) s_wsum[wid] = y;
+            __syncthreads();
+            unsigned wpre = 0, tot = 0;
+#pragma unroll
+            for (int i = 0; i < BK_THREADS / 32; i++) {
+                wpre += i < wid ? s_wsum[i] : 0u;
+                tot += s_wsum[i];
+            }
+            unsigned run = wpre + y - loc;
+            for (unsigned k = 0; k < per; k++)
+                if (b0 + k < nb) {
+                    const unsigned c = s_cnt[b0 + k];
+                    s_start[b0 + k] = run;
+                    s_gpos[b0 + k] = c ? atomicAdd(&cursors[b0 + k], c) : 0u;
+                    s_cnt[b0 + k] = 0u;
+                    run += c;
+                }
+            if (tid == 0) s_total = tot;
+        }
+        __syncthreads();
+        // C: counting-sort the tile by bucket (from registers)
+#pragma unroll
+        for (int j = 0; j < NV; j++)
+#pragma unroll
+            for (int c = 0; c < V; c++) {
+                const unsigned v = st[j][c];
+                if (v != BK_INVALID) {
+                    const unsigned b = v >> lw;
+                    s_sorted[s_start[b] + atomicAdd(&s_cnt[b], 1u)] = v;
+                }
+            }
+        __syncthreads();
+        // D: write contiguous runs into the pool; overflow goes through L2 atomics
+        const unsigned total = s_total;
+        if (tid == 0) valid += total;
+        for (unsigned p = tid; p < total; p += BK_THREADS) {
+            const unsigned v = s_sorted[p];
+            const unsigned b = v >> lw;
+            const unsigned long long q = (unsigned long long)s_gpos[b] + (p - s_start[b]);
+            if (q < cap) {
+                __stcs(pool + (unsigned long long)b * cap + q, (unsigned)(v & wmask));
+            } else {
+                const unsigned long long rel = ((unsigned long long)b << lw) | (v & wmask);
+                const unsigned bit = 1u << (rel & 31);
+                const unsigned old = atomicOr(marks + (rel >> 5), bit);
+                if (old & bit) {
+                    atomicOr(dup + (rel >> 5), bit);
+                    anydup = 1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    __shared__ unsigned long long sm[BK_THREADS / 32];
+    if (tid == 0 && valid) atomicAdd(&h->cnt0, valid);
+    unsigned long long r;
+    if (__syncthreads_or(anydup) && tid == 0) atomicOr(&h->flag, 1u);
+    if (BIJ) {
+        r = block_max_u64(ooi == INT64_MAX ? 0ull : enc_first(ooi), sm);
+        if (tid == 0) atomic_max_u64(&h->k_first, r);
+    }
+}
+
+// Pass 2: one block per bucket, a W-bit bitmap in shared memory.
+__global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, BucketCfg cfg,
+                                                                  const unsigned *__restrict__ cursors,
+                                                                  const unsigned *__restrict__ pool,
+                                                                  const unsigned *__restrict__ marks,
+                                                                  unsigned *__restrict__ dup, int bij) {
+    IXP_KERNEL_ENTRY();
+    extern __shared__ unsigned s_bm[];
+    const unsigned nb = (unsigned)h->spare[0];
+    const unsigned b = blockIdx.x;
+    if (h->status || b >= nb) return;
+    const unsigned long long cap = h->spare[1], span = h->span;
+    const unsigned lw = cfg.lw;
+    const unsigned words = (1u << lw) / 32;
+    const unsigned long long lo_rel = (unsigned long long)b << lw;
+    const unsigned long long range = min(1ull << lw, span - lo_rel);  // values this bucket covers
+    const unsigned cnt = cursors[b];
+    const unsigned long long stored = min((unsigned long long)cnt, cap);
+    const bool overflowed = cnt > cap;
+    for (unsigned w = threadIdx.x; w < words; w += blockDim.x)
+        s_bm[w] = (overflowed && (lo_rel >> 5) + w < (span + 31) / 32) ? marks[(lo_rel >> 5) + w] : 0u;
+    __syncthreads();
+    unsigned anydup = 0;
+    const unsigned *src = pool + (unsigned long long)b * cap;
+    const unsigned long long nv = stored / 4;
+    constexpr int U = 8;  // 16-byte loads in flight per thread
+    for (unsigned long long q0 = threadIdx.x; q0 < nv; q0 += (unsigned long long)U * blockDim.x) {
+        uint4 o4[U];
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+            const unsigned long long q = q0 + (unsigned long long)j * blockDim.x;
+            o4[j] = q < nv ? __ldcs(reinterpret_cast<const uint4 *>(src) + q) : make_uint4(~0u, ~0u, ~0u, ~0u);
+        }
+#pragma unroll
+        for (int j = 0; j < U; j++) {
+            const unsigned o[4] = {o4[j].x, o4[j].y, o4[j].z, o4[j].w};
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                if (o[c] == ~0u) continue;  // beyond this thread's share
+                const unsigned bit = 1u << (o[c] & 31);
+                if (atomicOr(&s_bm[o[c] >> 5], bit) & bit) {
+                    atomicOr(dup + ((lo_rel + o[c]) >> 5), 1u << ((lo_rel + o[c]) & 31));
+                    anydup = 1;
+                }
+            }
+        }
+    }
+    for (unsigned long long q = nv * 4 + threadIdx.x; q < stored; q += blockDim.x) {
+        const unsigned off = src[q];
+        const unsigned bit = 1u << (off & 31);
+        if (atomicOr(&s_bm[off >> 5], bit) & bit) {
+            atomicOr(dup + ((lo_rel + off) >> 5), 1u << ((lo_rel + off) & 31));
+            anydup = 1;
+        }
+    }
+    if (__syncthreads_or(anydup) && threadIdx.x == 0) atomicOr(&h->flag, 1u);
+    if (bij && (unsigned long long)cnt < range) {
+        // smallest value of this bucket that no element takes
+        unsigned long long best = ~0ull;
+        for (unsigned w = threadIdx.x; w < (range + 31) / 32; w += blockDim.x) {
+            unsigned z = ~s_bm[w];
+            if ((unsigned long long)(w + 1) * 32 > range) z &= (1u << (range & 31)) - 1u;
+            if (z) {
+                best = lo_rel + (unsigned long long)w * 32 + (__ffs(z) - 1);
+                break;
+            }
+        }
+        __shared__ unsigned long long sm[BK_THREADS / 32];
+        unsigned long long r = block_max_u64(best == ~0ull ? 0ull : enc_first((int64_t)best), sm);
+        if (threadIdx.x == 0) atomic_max_u64(&h->k_aux, r);
+    }
+}
+
 // ================================================================ host side
 
 static bool aligned_to(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -638,25 +925,99 @@ extern "C" int ixp_check_mono(const void *x, int itype, int64_t n, int cmp, ixp_
 }
 
 namespace ixp {
-// Bitmap capacity (bits) that a workspace of ws_bytes holds: two bitmaps after the header.
-static unsigned long long bitmap_capacity(size_t ws_bytes) {
-    if (ws_bytes < HDR_BYTES) return 0;
-    return (unsigned long long)((ws_bytes - HDR_BYTES) / 8) * 32ull;
+// Workspace layouts for Inj/Bij. Small inputs: header | marks | repeats (two bitmaps).
+// Large inputs (n >= BK_MIN_N): header | bucket cursors | pool | marks | repeats.
+constexpr int64_t BK_MIN_N = 1 << 18;
+constexpr unsigned long long BK_MIN_SPAN = 1ull << 21;
+
+static size_t rnd256(size_t b) { return (b + 255) & ~(size_t)255; }
+static unsigned long long bk_pool_entries(int64_t n) {
+    return ((unsigned long long)n + (unsigned long long)n / 4 + 4ull * BK_MAX + 3ull) & ~3ull;
+}
+size_t bk_prefix_bytes(int64_t n) { return HDR_BYTES + rnd256(BK_MAX * 4) + rnd256(bk_pool_entries(n) * 4); }
+
+struct BitmapWs {
+    Hdr *h;
+    unsigned *cursors, *pool, *bm, *dup;
+    unsigned long long cap;  // bits per bitmap
+    bool buckets;            // bucketed layout available
+};
+
+static BitmapWs bitmap_ws(void *ws, size_t ws_bytes, int64_t n) {
+    BitmapWs w{};
+    char *p = (char *)ws;
+    w.h = (Hdr *)p;
+    w.buckets = n >= BK_MIN_N && ws_bytes >= bk_prefix_bytes(n) + 2 * (BK_MIN_SPAN / 8);
+    size_t off = HDR_BYTES;
+    if (w.buckets) {
+        w.cursors = (unsigned *)(p + HDR_BYTES);
+        w.pool = (unsigned *)(p + HDR_BYTES + rnd256(BK_MAX * 4));
+        off = bk_prefix_bytes(n);
+    }
+    w.cap = ws_bytes > off ? (unsigned long long)((ws_bytes - off) / 8) * 32ull : 0ull;
+    w.bm = (unsigned *)(p + off);
+    w.dup = w.bm + w.cap / 32;
+    return w;
+}
+
+// Bucket width: about two buckets per SM, between 2^14 and 2^19 values (a 64 KB
+// shared bitmap), widened to 2^20 if the bucket count would exceed BK_MAX.
+static bool bucket_config(unsigned long long span, unsigned long long pool, BucketCfg *cfg) {
+    unsigned long long target = span / (2ull * (unsigned long long)num_sms());
+    unsigned lw = 14;
+    while (lw < 19 && (1ull << (lw + 1)) <= target) lw++;
+    unsigned long long bmax = (span + (1ull << lw) - 1) >> lw;
+    if (bmax > BK_MAX) {
+        lw = 20;
+        bmax = (span + (1ull << lw) - 1) >> lw;
+    }
+    if (bmax > BK_MAX) return false;
+    cfg->lw = lw;
+    cfg->bmax = (unsigned)bmax;
+    cfg->pool = pool;
+    return true;
+}
+
+template <typename T, bool BIJ>
+static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int64_t mlo, int64_t mhi, int fixed,
+                           int64_t flo, int64_t fhi, const BitmapWs &w, const BucketCfg &cfg, cudaStream_t st) {
+    const int sgrid = num_sms() * 4;
+    bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, w.cursors, w.bm, w.dup);
+    const size_t s1 = (size_t)(BK_TILE + 3 * cfg.bmax) * 4;
+    cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (BK_TILE + 3 * BK_MAX) * 4);
+    const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
+    const int g1 = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 2);
+    const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+    bucket_scatter_kernel<T, BIJ><<<g1, BK_THREADS, s1, st>>>(x, n, rlo, rhi, mlo, mhi, w.h, cfg, w.cursors, w.pool,
+                                                             w.bm, w.dup, vec);
+    cudaFuncSetAttribute(bucket_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << 20) / 8);
+    bucket_check_kernel<<<cfg.bmax, BK_THREADS, (1u << cfg.lw) / 8, st>>>(w.h, cfg, w.cursors, w.pool, w.bm, w.dup,
+                                                                         BIJ ? 1 : 0);
 }
 
 template <typename T>
 static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bool bij, int64_t ilo, int64_t ihi,
-                             Hdr *h, unsigned *bm, unsigned *dup, unsigned long long cap, ixp_verdict *out,
-                             cudaStream_t st) {
+                             const BitmapWs &w, ixp_verdict *out, cudaStream_t st) {
+    Hdr *h = w.h;
+    unsigned *bm = w.bm, *dup = w.dup;
+    const unsigned long long cap = w.cap;
     const int grid = stream_grid((n + 3) / 4);
     const int sgrid = num_sms() * 4;
+    BucketCfg cfg{};
     if (bij) {
-        bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, 1, ilo, ihi, cap, bm, dup);
-        if (n > 0) {
-            mark_kernel<T, true><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, ilo, ihi, h, bm, dup);
+        const unsigned long long isize = (unsigned long long)ihi - (unsigned long long)ilo + 1ull;
+        if (w.buckets && isize >= BK_MIN_SPAN && bucket_config(isize, bk_pool_entries(n), &cfg)) {
+            launch_buckets<T, true>(x, n, rlo, rhi, ilo, ihi, 1, ilo, ihi, w, cfg, st);
             first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, &h->k_first2);
+        } else {
+            bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, 1, ilo, ihi, cap, bm, dup);
+            if (n > 0) {
+                mark_kernel<T, true><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, ilo, ihi, h, bm, dup);
+                first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, &h->k_first2);
+            }
+            missing_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, bm);
         }
-        missing_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, bm);
         bij_finalize<T><<<1, 1, 0, st>>>(x, h, out, ilo, (int64_t)((unsigned long long)ihi - (unsigned long long)ilo + 1));
         return;
     }
@@ -664,9 +1025,14 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
     const unsigned long long rspan = (unsigned long long)rhi - (unsigned long long)rlo + 1ull;
     const bool fixed = rspan != 0 && rspan <= cap && rspan <= 4ull * (unsigned long long)n + 4096ull;
     if (!fixed && n > 0) minmax_in_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h);
-    bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, fixed ? 1 : 0, rlo, rhi, cap, bm, dup);
+    const unsigned long long span_cap = fixed ? rspan : cap;
+    if (w.buckets && span_cap >= BK_MIN_SPAN && bucket_config(span_cap, bk_pool_entries(n), &cfg)) {
+        launch_buckets<T, false>(x, n, rlo, rhi, rlo, rhi, fixed ? 1 : 0, rlo, rhi, w, cfg, st);
+    } else {
+        bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, fixed ? 1 : 0, rlo, rhi, cap, bm, dup);
+        if (n > 0) mark_kernel<T, false><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, rlo, rhi, h, bm, dup);
+    }
     if (n > 0) {
-        mark_kernel<T, false><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, rlo, rhi, h, bm, dup);
         first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, dup, &h->k_first);
         partner_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, h, &h->k_first);
     }
@@ -682,15 +1048,12 @@ extern "C" int ixp_check_inj(const void *x, int itype, int64_t n, int64_t rcd_lo
     int rc = check_ws(ws, ws_bytes, HDR_BYTES + 256);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    Hdr *h = (Hdr *)ws;
-    const unsigned long long cap = bitmap_capacity(ws_bytes);
-    unsigned *bm = (unsigned *)((char *)ws + HDR_BYTES);
-    unsigned *dup = bm + cap / 32;
-    if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    const BitmapWs w = bitmap_ws(ws, ws_bytes, n);
+    if (cudaMemsetAsync(w.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
     if (itype == IXP_I32)
-        run_bitmap_check((const int32_t *)x, n, rcd_lo, rcd_hi, false, 0, 0, h, bm, dup, cap, d_verdict, st);
+        run_bitmap_check((const int32_t *)x, n, rcd_lo, rcd_hi, false, 0, 0, w, d_verdict, st);
     else
-        run_bitmap_check((const int64_t *)x, n, rcd_lo, rcd_hi, false, 0, 0, h, bm, dup, cap, d_verdict, st);
+        run_bitmap_check((const int64_t *)x, n, rcd_lo, rcd_hi, false, 0, 0, w, d_verdict, st);
     return launch_status();
 }
 
@@ -702,19 +1065,16 @@ extern "C" int ixp_check_bij(const void *x, int itype, int64_t n, int64_t rcd_lo
         return IXP_E_INVAL;
     const unsigned long long isize = (unsigned long long)img_hi - (unsigned long long)img_lo + 1ull;
     if (isize == 0 || isize > (1ull << 40)) return IXP_E_INVAL;
-    const unsigned long long cap = bitmap_capacity(ws_bytes);
     int rc = check_ws(ws, ws_bytes, HDR_BYTES + 256);
     if (rc) return rc;
-    if (isize > cap) return IXP_E_WORKSPACE;
+    const BitmapWs w = bitmap_ws(ws, ws_bytes, n);
+    if (isize > w.cap) return IXP_E_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
-    Hdr *h = (Hdr *)ws;
-    unsigned *bm = (unsigned *)((char *)ws + HDR_BYTES);
-    unsigned *dup = bm + cap / 32;
-    if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (cudaMemsetAsync(w.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
     if (itype == IXP_I32)
-        run_bitmap_check((const int32_t *)x, n, rcd_lo, rcd_hi, true, img_lo, img_hi, h, bm, dup, cap, d_verdict, st);
+        run_bitmap_check((const int32_t *)x, n, rcd_lo, rcd_hi, true, img_lo, img_hi, w, d_verdict, st);
     else
-        run_bitmap_check((const int64_t *)x, n, rcd_lo, rcd_hi, true, img_lo, img_hi, h, bm, dup, cap, d_verdict, st);
+        run_bitmap_check((const int64_t *)x, n, rcd_lo, rcd_hi, true, img_lo, img_hi, w, d_verdict, st);
     return launch_status();
 }
 

@@ -176,6 +176,47 @@ def test_bij(ixp, dev, n, dtype):
                  (name, n, rlo, rhi, ilo, ihi))
 
 
+# ---- large inputs take the value-bucketed Inj/Bij path (n >= 2^18, span >= 2^21)
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+@pytest.mark.parametrize("n", [1 << 18, (1 << 21) + 12345, 3_000_001])
+def test_inj_bij_bucketed(ixp, dev, n, dtype):
+    seed = 900 + n
+    perm = synth.permutation(n, seed, dtype)
+    cases = {"perm": perm, "dup": synth.plant_duplicate(perm, seed)[0], "oor": synth.plant_value(perm, seed, n)[0],
+             "neg": synth.plant_value(perm, seed, -1)[0], "far": synth.plant_value(perm, seed, 3 * n)[0]}
+    for name, a in cases.items():
+        t = T(a, dev)
+        for lo, hi in [(I64MIN, I64MAX), (0, n - 1)]:
+            same(ixp.check_inj(t, lo, hi), oracle.check_inj(a, lo, hi), (name, n, lo, hi, "inj"))
+        for rlo, rhi in [(I64MIN, I64MAX), (0, n - 1), (-1, 2 * n)]:
+            same(ixp.check_bij(t, rlo, rhi, 0, n - 1), oracle.check_bij(a, rlo, rhi, 0, n - 1), (name, n, rlo, "bij"))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_inj_bucketed_skewed_overflow(ixp, dev, dtype):
+    # most values packed into the first bucket's range of a wide span: the bucket's pool
+    # region overflows and the excess takes the L2-atomic path
+    rng = np.random.default_rng(17)
+    n = 600_000
+    dense = rng.permutation(400_000)
+    sparse = 400_000 + rng.choice(2**23, size=n - 400_000, replace=False)
+    a = rng.permutation(np.concatenate([dense, sparse])).astype(dtype)
+    same(ixp.check_inj(T(a, dev)), oracle.check_inj(a), "skew-ok")
+    same(ixp.check_inj(T(a, dev), 0, 2**23 + 400_000), oracle.check_inj(a, 0, 2**23 + 400_000), "skew-ok-fixed")
+    for p, q in [(3, 500_000), (599_999, 0), (12345, 54321)]:
+        b = a.copy()
+        b[q] = b[p]
+        same(ixp.check_inj(T(b, dev)), oracle.check_inj(b), ("skew-dup", p, q))
+    # many repeats inside the dense range
+    c = a.copy()
+    c[:200_000] = rng.integers(0, 1000, size=200_000)
+    same(ixp.check_inj(T(c, dev)), oracle.check_inj(c), "skew-many")
+    # Bij over the dense+sparse image with a gap
+    img_hi = 2**23 + 400_000 - 1
+    same(ixp.check_bij(T(a, dev), I64MIN, I64MAX, 0, img_hi), oracle.check_bij(a, I64MIN, I64MAX, 0, img_hi), "bij-gap")
+
+
 @pytest.mark.parametrize("it,ot", [(np.int32, np.int32), (np.int32, np.int64), (np.int64, np.int64)])
 @pytest.mark.parametrize("n", SIZES + [300000])
 def test_scan_flat(ixp, dev, n, it, ot):
