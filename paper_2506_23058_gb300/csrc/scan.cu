@@ -382,25 +382,25 @@ __global__ void __launch_bounds__(TB) scan_kernel(const TI *__restrict__ in, TO 
 
 // Flat scan: plain sums in the output width (32-bit accumulators for int32
 // outputs), four 16-byte vectors per thread, at least four blocks per SM.
-template <typename TI, typename TO>
-__global__ void __launch_bounds__(TB, 4) scan_flat_kernel(const TI *__restrict__ in, TO *__restrict__ out, int64_t n,
-                                                          int inclusive, Lookback L, Hdr *h, Wait wt, TO *total_out,
-                                                          int vec_ok) {
+template <typename TI, typename TO, int NT = TB, int S = SUB, int MINB = 1024 / NT>
+__global__ void __launch_bounds__(NT, MINB) scan_flat_kernel(const TI *__restrict__ in, TO *__restrict__ out,
+                                                                  int64_t n, int inclusive, Lookback L, Hdr *h, Wait wt,
+                                                                  TO *total_out, int vec_ok) {
     IXP_KERNEL_ENTRY();
     constexpr int V = 16 / sizeof(TI);
-    constexpr int TILE = TB * SUB * V;
+    constexpr int TILE = NT * S * V;
     using ACC = typename std::conditional<sizeof(TO) == 4, uint32_t, unsigned long long>::type;
     __shared__ int64_t s_tile;
-    __shared__ ACC s_warp[TB / 32];
+    __shared__ ACC s_warp[NT / 32];
     if (threadIdx.x == 0) s_tile = atomicAdd(&h->tile_ctr, 1u);
     __syncthreads();
     const int64_t t = s_tile;
     const int64_t t0 = t * TILE;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    ACC a[SUB][V];
+    ACC a[S][V];
 #pragma unroll
-    for (int u = 0; u < SUB; u++) {
-        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+    for (int u = 0; u < S; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * S + u) * 32 + l) * V;
         if (vec_ok && p0 + V <= n) {
             if (V == 4) {
                 int4 v = __ldcs(reinterpret_cast<const int4 *>(in + p0));
@@ -418,9 +418,9 @@ __global__ void __launch_bounds__(TB, 4) scan_flat_kernel(const TI *__restrict__
             for (int k = 0; k < V; k++) a[u][k] = (p0 + k < n) ? (ACC)(int64_t)in[p0 + k] : (ACC)0;
         }
     }
-    ACC carry = 0, lane_pre[SUB];
+    ACC carry = 0, lane_pre[S];
 #pragma unroll
-    for (int u = 0; u < SUB; u++) {
+    for (int u = 0; u < S; u++) {
         ACC x = 0;
 #pragma unroll
         for (int k = 0; k < V; k++) x += a[u][k];
@@ -436,25 +436,25 @@ __global__ void __launch_bounds__(TB, 4) scan_flat_kernel(const TI *__restrict__
     if (l == 0) s_warp[w] = carry;
     __syncthreads();
     if (w == 0) {
-        const ACC x = l < TB / 32 ? s_warp[l] : (ACC)0;
+        const ACC x = l < NT / 32 ? s_warp[l] : (ACC)0;
         ACC y = x;
 #pragma unroll
-        for (int d = 1; d < TB / 32; d <<= 1) {
+        for (int d = 1; d < NT / 32; d <<= 1) {
             ACC o = __shfl_up_sync(FULL, y, d);
             if (l >= d) y += o;
         }
-        const ACC tile_agg = __shfl_sync(FULL, y, TB / 32 - 1);
+        const ACC tile_agg = __shfl_sync(FULL, y, NT / 32 - 1);
         const unsigned long long tile_ex = lookback_sum(L, t, (unsigned long long)tile_agg, h, wt);
         __syncwarp();
-        if (l < TB / 32) s_warp[l] = (ACC)tile_ex + (y - x);
+        if (l < NT / 32) s_warp[l] = (ACC)tile_ex + (y - x);
         if (l == 0 && total_out && t0 + TILE >= n) *total_out = (TO)(tile_ex + (unsigned long long)tile_agg);
     }
     __syncthreads();
     const ACC pre = s_warp[w];
     constexpr int VO = 16 / sizeof(TO);
 #pragma unroll
-    for (int u = 0; u < SUB; u++) {
-        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+    for (int u = 0; u < S; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * S + u) * 32 + l) * V;
         ACC run = pre + lane_pre[u];
         TO o[V];
 #pragma unroll
@@ -485,6 +485,157 @@ __global__ void __launch_bounds__(TB, 4) scan_flat_kernel(const TI *__restrict__
                 if (p0 + k < n) out[p0 + k] = o[k];
         }
     }
+}
+
+// Flat scan with the tile staged in shared memory by TMA bulk copies: thread 0
+// takes the tile ticket and issues the copies (64 KB of input per tile), all
+// threads wait on the mbarrier, then the tile is read twice from shared memory
+// (sums, then outputs) so that few registers are live and three tiles fit per SM.
+constexpr int TMA_NT = 256;
+constexpr int TMA_TILE_BYTES = 65536;
+constexpr int TMA_CHUNK = 16384;  // bytes per bulk copy
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(TMA_NT, 3) scan_tma_kernel(const TI *__restrict__ in, TO *__restrict__ out,
+                                                             int64_t n, int inclusive, Lookback L, Hdr *h, Wait wt,
+                                                             TO *total_out) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(TI);
+    constexpr int TILE = TMA_TILE_BYTES / (int)sizeof(TI);
+    constexpr int S = TILE / V / TMA_NT;  // vectors per thread
+    using ACC = typename std::conditional<sizeof(TO) == 4, uint32_t, unsigned long long>::type;
+    extern __shared__ __align__(128) unsigned char tma_buf[];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int64_t s_tile;
+    __shared__ ACC s_warp[TMA_NT / 32];
+    __shared__ int s_ok;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        s_tile = atomicAdd(&h->tile_ctr, 1u);
+    }
+    __syncthreads();
+    const int64_t t = s_tile;
+    const int64_t t0 = t * TILE;
+    const int64_t cnt = min((int64_t)TILE, n - t0);
+    const int64_t bulk_elems = (cnt * (int64_t)sizeof(TI)) / 16 * 16 / (int64_t)sizeof(TI);
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)(bulk_elems * sizeof(TI));
+        mbar_expect_tx(&bar, bytes);
+        for (unsigned off = 0; off < bytes; off += TMA_CHUNK)
+            bulk_g2s(tma_buf + off, (const char *)(in + t0) + off, min((unsigned)TMA_CHUNK, bytes - off), &bar);
+        const bool ok = mbar_wait_bounded(&bar, 0, wt.spin_limit);
+        if (!ok) {
+            set_status(h, IXP_E_TIMEOUT);
+            mbar_wait_bounded(&bar, 0, wt.spin_limit);  // let the copies land before the block moves on
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    const TI *sv = reinterpret_cast<const TI *>(tma_buf);
+    auto elem = [&](int64_t r) -> ACC {  // element r of the tile
+        if (r < bulk_elems) return (ACC)(int64_t)sv[r];
+        return (r < cnt) ? (ACC)(int64_t)in[t0 + r] : (ACC)0;
+    };
+    // pass 1: per sub-chunk vector sums, warp scans with carry
+    ACC carry = 0, lane_pre[S];
+#pragma unroll
+    for (int u = 0; u < S; u++) {
+        const int64_t r0 = (int64_t)((w * S + u) * 32 + l) * V;
+        ACC x = 0;
+        if (r0 + V <= bulk_elems) {
+            if (V == 4) {
+                const int4 q = reinterpret_cast<const int4 *>(tma_buf)[r0 / 4];
+                x = (ACC)(int64_t)q.x + (ACC)(int64_t)q.y + (ACC)(int64_t)q.z + (ACC)(int64_t)q.w;
+            } else {
+                const longlong2 q = reinterpret_cast<const longlong2 *>(tma_buf)[r0 / 2];
+                x = (ACC)q.x + (ACC)q.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++) x += elem(r0 + k);
+        }
+        ACC y = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            ACC o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y += o;
+        }
+        lane_pre[u] = carry + y - x;
+        carry += __shfl_sync(FULL, y, 31);
+    }
+    if (l == 0) s_warp[w] = carry;
+    __syncthreads();
+    if (w == 0) {
+        const ACC x = l < TMA_NT / 32 ? s_warp[l] : (ACC)0;
+        ACC y = x;
+#pragma unroll
+        for (int d = 1; d < TMA_NT / 32; d <<= 1) {
+            ACC o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y += o;
+        }
+        const ACC tile_agg = __shfl_sync(FULL, y, TMA_NT / 32 - 1);
+        const unsigned long long tile_ex = lookback_sum(L, t, (unsigned long long)tile_agg, h, wt);
+        __syncwarp();
+        if (l < TMA_NT / 32) s_warp[l] = (ACC)tile_ex + (y - x);
+        if (l == 0 && total_out && t0 + TILE >= n) *total_out = (TO)(tile_ex + (unsigned long long)tile_agg);
+    }
+    __syncthreads();
+    // pass 2: outputs
+    const ACC pre = s_warp[w];
+    constexpr int VO = 16 / sizeof(TO);
+#pragma unroll
+    for (int u = 0; u < S; u++) {
+        const int64_t r0 = (int64_t)((w * S + u) * 32 + l) * V;
+        ACC a[V];
+        if (r0 + V <= bulk_elems) {
+            if (V == 4) {
+                const int4 q = reinterpret_cast<const int4 *>(tma_buf)[r0 / 4];
+                a[0] = (ACC)(int64_t)q.x;
+                a[1 % V] = (ACC)(int64_t)q.y;
+                a[2 % V] = (ACC)(int64_t)q.z;
+                a[3 % V] = (ACC)(int64_t)q.w;
+            } else {
+                const longlong2 q = reinterpret_cast<const longlong2 *>(tma_buf)[r0 / 2];
+                a[0] = (ACC)q.x;
+                a[1 % V] = (ACC)q.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++) a[k] = elem(r0 + k);
+        }
+        ACC run = pre + lane_pre[u];
+        TO o[V];
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            run += a[k];
+            o[k] = (TO)(inclusive ? run : run - a[k]);
+        }
+        const int64_t p0 = t0 + r0;
+        if (p0 + V <= n) {
+#pragma unroll
+            for (int c = 0; c < V; c += VO) {
+                if (VO == 4) {
+                    int4 st4;
+                    st4.x = (int)o[c];
+                    st4.y = (int)o[(c + 1) % V];
+                    st4.z = (int)o[(c + 2) % V];
+                    st4.w = (int)o[(c + 3) % V];
+                    __stcs(reinterpret_cast<int4 *>(out + p0 + c), st4);
+                } else {
+                    longlong2 st2;
+                    st2.x = (long long)o[c];
+                    st2.y = (long long)o[(c + 1) % V];
+                    __stcs(reinterpret_cast<longlong2 *>(out + p0 + c), st2);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (p0 + k < n) out[p0 + k] = o[k];
+        }
+    }
+    (void)s_ok;
 }
 
 // Segment totals after a segmented scan: tot[k] = inclusive value at the segment's
@@ -1266,7 +1417,14 @@ static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs se
         if (seg)
             scan_kernel<TI, TO, true><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, segs.offsets, segs.nseg,
                                                                   W.L, W.h, wt, nullptr, vec);
-        else
+        else if (vec) {
+            constexpr int64_t tile = TMA_TILE_BYTES / (int64_t)sizeof(TI);
+            const int64_t ntma = (n + tile - 1) / tile;
+            cudaFuncSetAttribute(scan_tma_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TMA_TILE_BYTES);
+            scan_tma_kernel<TI, TO><<<(unsigned)ntma, TMA_NT, TMA_TILE_BYTES, st>>>(in, out, n, inclusive, W.L, W.h, wt,
+                                                                                  tot);
+        } else
             scan_flat_kernel<TI, TO><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, W.L, W.h, wt, tot, vec);
     }
     if (seg && tot && segs.nseg > 0) {

@@ -255,19 +255,23 @@ def test_scan_unaligned(ixp, dev):
         assert np.array_equal(r.cpu().numpy(), oracle.scan(a[off:], np.int64)[0])
 
 
-def test_scan_timeout_is_reported(ixp, dev):
-    # a tile that never publishes makes its successors' bounded waits run out
-    n = 4096 * 12 + 5
-    a = np.ones(n, np.int32)
+@pytest.mark.parametrize("offset", [0, 1])
+def test_scan_timeout_is_reported(ixp, dev, offset):
+    # a tile that never publishes makes its successors' bounded waits run out;
+    # offset 0 takes the TMA-staged path (16384-element tiles), offset 1 the
+    # unaligned register path (4096-element tiles)
+    n = 16384 * 12 + 5
+    a = np.ones(n + offset, np.int32)
+    t = T(a, dev)[offset:]
     try:
         ixp.debug_set_wait(2000, 3)
-        _, _, st = ixp.scan(T(a, dev))
+        _, _, st = ixp.scan(t)
         torch.cuda.synchronize()
         assert st.item() == -6
     finally:
         ixp.debug_set_wait(0, -1)
-    _, _, st = ixp.scan(T(a, dev))
-    assert st.item() == 0
+    out, tot, st = ixp.scan(t)
+    assert st.item() == 0 and int(tot.item()) == n
 
 
 PREDS = [("mod_eq", 3, 0), ("lt", 0, 0), ("lt", 0, synth.bernoulli_threshold(0.01)), ("mod_eq", 5, 2)]
