@@ -220,6 +220,10 @@ int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const void *idx, in
 /* Rounds a float64 accumulator to float32 (out[i] = (float)acc[i], count elements). */
 int ixp_f64_to_f32(float *out, const double *acc, int64_t count, ixp_stream stream);
 
+/* Widens float32 to float64 (out[i] = (double)in[i]); used to pre-load a float64
+ * accumulator with a float32 destination before an additive scatter. */
+int ixp_f32_to_f64(double *out, const float *in, int64_t count, ixp_stream stream);
+
 /* gather: out[i] = src[idx[i]] (rows of row_elems * elem_bytes bytes). An index
  * outside [0, src_len) zero-fills its row and sets *d_status = IXP_E_OOB
  * (d_status nullable; it is not cleared, so zero it first). */

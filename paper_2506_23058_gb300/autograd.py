@@ -1,0 +1,137 @@
+"""Differentiable scatter, gather and partition over float payloads.
+
+Forward and backward both run the library's kernels (this module only allocates
+outputs and marshals arguments):
+
+* ``gather``   y[i] = src[idx[i]].  Adjoint: grad_src[t] = sum of grad_y[i] over
+  idx[i] = t. When the caller asserts (or has checked with ``check_inj``) that idx
+  is injective, that sum has at most one term, so the adjoint is a plain scatter
+  with no atomics. Otherwise float32 gradients accumulate in float64 and are
+  rounded once; float64 gradients use float64 atomics.
+* ``scatter``  out = dst with rows idx[i] replaced by vals[i] (indices outside
+  dst are ignored, Sec. 2.1). Requires injective in-bounds indices (the paper's
+  condition for a deterministic scatter). Adjoint: grad_vals = gather of grad_out
+  (zero for ignored indices); grad_dst = grad_out with the overwritten rows zeroed.
+* ``scatter_add``  out = dst + sum of vals rows per index. Indexing is exact and
+  needs no injectivity; adjoint: grad_vals = gather of grad_out, grad_dst = grad_out.
+* ``partition``  the payload rows moved to the stable two-way partition order
+  (partition2, Fig. 2). Adjoint: grad_payload = gather of grad_out by ``indices``
+  (every element goes to exactly one destination).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import ixp
+
+
+def _zeros(shape, dtype, device):
+    return torch.zeros(shape, dtype=dtype, device=device)
+
+
+def _scatter_add_into(grad, idx, g):
+    """grad (zeroed, float32 or float64) += rows of g grouped by idx."""
+    if g.dtype == torch.float32:
+        acc = _zeros(grad.shape, torch.float64, g.device)
+        ixp.scatter_add_f64(acc, idx, g)
+        ixp.f64_to_f32(acc, out=grad)
+    else:
+        ixp.scatter(grad, idx, g, mode="add")
+    return grad
+
+
+class GatherFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, src, idx, injective=False):
+        out, status = ixp.gather(src.contiguous(), idx)
+        ctx.save_for_backward(idx, status)
+        ctx.src_shape = src.shape
+        ctx.injective = bool(injective)
+        ctx.mark_non_differentiable(status)
+        return out, status
+
+    @staticmethod
+    def backward(ctx, g, _g_status):
+        idx, status = ctx.saved_tensors
+        g = g.contiguous()
+        grad = _zeros(ctx.src_shape, g.dtype, g.device)
+        if ctx.injective:
+            ixp.scatter(grad, idx, g)  # one term per target: no atomics
+        else:
+            _scatter_add_into(grad, idx, g)
+        return grad, None, None
+
+
+class ScatterFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, dst, idx, vals):
+        out = dst.contiguous().clone()
+        ixp.scatter(out, idx, vals.contiguous())
+        ctx.save_for_backward(idx)
+        ctx.vals_shape = vals.shape
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        (idx,) = ctx.saved_tensors
+        g = g.contiguous()
+        grad_vals, _ = ixp.gather(g, idx)  # out-of-bounds indices give zero rows
+        grad_dst = g.clone()
+        ixp.scatter(grad_dst, idx, _zeros(ctx.vals_shape, g.dtype, g.device))
+        return grad_dst, None, grad_vals
+
+
+class ScatterAddFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, dst, idx, vals):
+        dst = dst.contiguous()
+        vals = vals.contiguous()
+        if vals.dtype == torch.float32:
+            acc = ixp.f32_to_f64(dst)
+            ixp.scatter_add_f64(acc, idx, vals)
+            out = ixp.f64_to_f32(acc)
+        else:
+            out = dst.clone()
+            ixp.scatter(out, idx, vals, mode="add")
+        ctx.save_for_backward(idx)
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        (idx,) = ctx.saved_tensors
+        g = g.contiguous()
+        grad_vals, _ = ixp.gather(g, idx)
+        return g, None, grad_vals
+
+
+class PartitionFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, payload, keys, pred, offsets=None, out_dtype=torch.int32):
+        r = ixp.partition(keys, pred, payload=payload.contiguous(), out_dtype=out_dtype, offsets=offsets,
+                          want_keys=False, n=payload.shape[0])
+        ctx.save_for_backward(r["indices"])
+        ctx.mark_non_differentiable(r["indices"], r["num_true"])
+        return r["payload_out"], r["indices"], r["num_true"]
+
+    @staticmethod
+    def backward(ctx, g, _gi, _gn):
+        (indices,) = ctx.saved_tensors
+        grad, _ = ixp.gather(g.contiguous(), indices)
+        return grad, None, None, None, None
+
+
+def gather(src, idx, injective=False):
+    return GatherFn.apply(src, idx, injective)[0]
+
+
+def scatter(dst, idx, vals):
+    return ScatterFn.apply(dst, idx, vals)
+
+
+def scatter_add(dst, idx, vals):
+    return ScatterAddFn.apply(dst, idx, vals)
+
+
+def partition(payload, keys, pred, offsets=None, out_dtype=torch.int32):
+    """Returns (payload_out, indices, num_true); only payload_out carries gradients."""
+    return PartitionFn.apply(payload, keys, pred, offsets, out_dtype)

@@ -272,6 +272,11 @@ __global__ void mono_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
 }
 
 // ================================================================ Inj / Bij
+constexpr int BK_TILE = 8192;
+constexpr int BK_THREADS = 256;
+constexpr unsigned BK_MAX = 4096;
+constexpr unsigned BK_INVALID = 0xffffffffu;
+
 // Min/max of the in-codomain values (needed when Rcd is unbounded).
 template <typename T>
 __global__ void __launch_bounds__(STREAM_THREADS, 4) minmax_in_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
@@ -423,27 +428,59 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) mark_kernel(const T *__rest
 }
 
 // Smallest index whose value (in [mlo, mhi]) has its bit in the repeat bitmap.
-// Runs only when the mark pass saw a repeat.
+// Runs only when a repeat was seen. With bucket_mask (bucketed path), only values
+// whose bucket saw a repeat look the bitmap up, so the pass streams at HBM speed.
 template <typename T>
-__global__ void __launch_bounds__(STREAM_THREADS) first_dup_kernel(const T *__restrict__ x, int64_t n, int64_t mlo,
-                                                                   int64_t mhi, Hdr *h,
-                                                                   const unsigned *__restrict__ dup,
-                                                                   unsigned long long *slot) {
+__global__ void __launch_bounds__(STREAM_THREADS, 4) first_dup_kernel(const T *__restrict__ x, int64_t n, int64_t mlo,
+                                                                      int64_t mhi, Hdr *h,
+                                                                      const unsigned *__restrict__ dup,
+                                                                      const unsigned *__restrict__ bucket_mask,
+                                                                      unsigned lw, unsigned long long *slot) {
     IXP_KERNEL_ENTRY();
     if (h->status || !h->flag) return;
+    __shared__ unsigned s_mask[BK_MAX / 32];
     const unsigned long long base = h->base, span = h->span;
+    if (bucket_mask)
+        for (int w = threadIdx.x; w < (int)(BK_MAX / 32); w += blockDim.x) s_mask[w] = bucket_mask[w];
+    __syncthreads();
+    using VT = typename Vec<T>::type;
+    constexpr int V = Vec<T>::N;
+    Split<T> s(x, n);
     int64_t best = INT64_MAX;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < n; i += stride) {
-        int64_t xi = ld1(x, i);
-        if (xi < mlo || xi > mhi) continue;
-        unsigned long long b = (unsigned long long)xi - base;
-        if (b >= span) continue;
-        if (__ldg(dup + (b >> 5)) & (1u << (b & 31))) {
-            best = i;  // the first hit of this thread is its smallest index
-            break;
+    auto one = [&](int64_t i, T xv) {
+        const int64_t xi = (int64_t)xv;
+        if (xi < mlo || xi > mhi) return;
+        const unsigned long long rel = (unsigned long long)xi - base;
+        if (rel >= span) return;
+        if (bucket_mask) {
+            const unsigned b = (unsigned)(rel >> lw);
+            if (!(s_mask[b >> 5] & (1u << (b & 31)))) return;
         }
+        if (__ldg(dup + (rel >> 5)) & (1u << (rel & 31))) best = i < best ? i : best;
+    };
+    for (int64_t i = tid; i < s.head; i += stride) one(i, x[i]);
+    for (int64_t i = s.tail0 + tid; i < n; i += stride) one(i, x[i]);
+    const VT *xv = reinterpret_cast<const VT *>(x + s.head);
+    int64_t v = tid;
+    for (; v + 3 * stride < s.nvec; v += 4 * stride) {
+        VT a[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int64_t e[V];
+            unpack(a[u], e);
+#pragma unroll
+            for (int k = 0; k < V; k++) one(s.head + (v + u * stride) * V + k, (T)e[k]);
+        }
+    }
+    for (; v < s.nvec; v += stride) {
+        int64_t e[V];
+        unpack(ldv(xv + v), e);
+#pragma unroll
+        for (int k = 0; k < V; k++) one(s.head + v * V + k, (T)e[k]);
     }
     __shared__ unsigned long long sm[STREAM_THREADS / 32];
     unsigned long long r = block_max_u64(best == INT64_MAX ? 0ull : enc_first(best), sm);
@@ -452,22 +489,49 @@ __global__ void __launch_bounds__(STREAM_THREADS) first_dup_kernel(const T *__re
 
 // Partner of the first repeated index i*: the smallest j > i* with x[j] = x[i*].
 template <typename T>
-__global__ void __launch_bounds__(STREAM_THREADS) partner_kernel(const T *__restrict__ x, int64_t n, Hdr *h,
-                                                                 const unsigned long long *slot) {
+__global__ void __launch_bounds__(STREAM_THREADS, 4) partner_kernel(const T *__restrict__ x, int64_t n, Hdr *h,
+                                                                    const unsigned long long *slot) {
     IXP_KERNEL_ENTRY();
     if (h->status || !h->flag || !*slot) return;
     const int64_t i0 = dec_first(*slot);
-    const int64_t v0 = ld1(x, i0);
+    const T v0 = x[i0];
+    const int64_t start = i0 + 1;
+    using VT = typename Vec<T>::type;
+    constexpr int V = Vec<T>::N;
+    const T *xs = x + start;
+    const int64_t m = n - start;
+    Split<T> s(xs, m);
     int64_t best = INT64_MAX;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = i0 + 1 + tid; j < n; j += stride)
-        if (ld1(x, j) == v0) {
-            best = j;
-            break;
+    for (int64_t i = tid; i < s.head; i += stride)
+        if (xs[i] == v0) best = i < best ? i : best;
+    for (int64_t i = s.tail0 + tid; i < m; i += stride)
+        if (xs[i] == v0) best = i < best ? i : best;
+    const VT *xv = reinterpret_cast<const VT *>(xs + s.head);
+    int64_t v = tid;
+    for (; v + 3 * stride < s.nvec; v += 4 * stride) {
+        VT a[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            int64_t e[V];
+            unpack(a[u], e);
+#pragma unroll
+            for (int k = V - 1; k >= 0; k--)
+                if ((T)e[k] == v0) best = min(best, s.head + (v + u * stride) * V + k);
         }
+    }
+    for (; v < s.nvec; v += stride) {
+        int64_t e[V];
+        unpack(ldv(xv + v), e);
+#pragma unroll
+        for (int k = V - 1; k >= 0; k--)
+            if ((T)e[k] == v0) best = min(best, s.head + v * V + k);
+    }
     __shared__ unsigned long long sm[STREAM_THREADS / 32];
-    unsigned long long r = block_max_u64(best == INT64_MAX ? 0ull : enc_first(best), sm);
+    unsigned long long r = block_max_u64(best == INT64_MAX ? 0ull : enc_first(start + best), sm);
     if (threadIdx.x == 0) atomic_max_u64(&h->k_aux, r);
 }
 
@@ -561,10 +625,6 @@ __global__ void bij_finalize(const T *x, const Hdr *h, ixp_verdict *out, int64_t
 // A bucket that receives more values than its pool region holds sends the excess
 // through L2 atomics on the global mark bitmap (pass 1), and pass 2 merges those
 // bits before it sets its own, so skewed inputs stay exact.
-constexpr int BK_TILE = 8192;
-constexpr int BK_THREADS = 256;
-constexpr unsigned BK_MAX = 4096;
-constexpr unsigned BK_INVALID = 0xffffffffu;
 
 struct BucketCfg {
     unsigned lw;                // log2 of the bucket width W (values per bucket)
@@ -573,7 +633,8 @@ struct BucketCfg {
 };
 
 __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, unsigned long long cap_bits,
-                                    BucketCfg cfg, unsigned *cursors, unsigned *marks, unsigned *dup) {
+                                    BucketCfg cfg, unsigned *cursors, unsigned *marks, unsigned *dup,
+                                    unsigned *bucket_mask) {
     IXP_KERNEL_ENTRY();
     unsigned long long base = 0, span = 0;
     bool too_big = false;
@@ -610,13 +671,14 @@ __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, u
         dup[w] = 0u;
     }
     for (unsigned long long b = tid; b < nb; b += stride) cursors[b] = 0u;
+    for (unsigned long long w = tid; w < BK_MAX / 32; w += stride) bucket_mask[w] = 0u;
 }
 
 template <typename T, bool BIJ>
 __global__ void __launch_bounds__(BK_THREADS, 2) bucket_scatter_kernel(
     const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, int64_t mlo, int64_t mhi, Hdr *h, BucketCfg cfg,
     unsigned *__restrict__ cursors, unsigned *__restrict__ pool, unsigned *__restrict__ marks,
-    unsigned *__restrict__ dup, int vec_ok) {
+    unsigned *__restrict__ dup, unsigned *__restrict__ bucket_mask, int vec_ok) {
     IXP_KERNEL_ENTRY();
     if (h->status) return;
     constexpr int V = Vec<T>::N;
@@ -748,6 +810,7 @@ __global__ void __launch_bounds__(BK_THREADS, 2) bucket_scatter_kernel(
                 const unsigned old = atomicOr(marks + (rel >> 5), bit);
                 if (old & bit) {
                     atomicOr(dup + (rel >> 5), bit);
+                    atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
                     anydup = 1;
                 }
             }
@@ -769,7 +832,8 @@ __global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, Bucket
                                                                   const unsigned *__restrict__ cursors,
                                                                   const unsigned *__restrict__ pool,
                                                                   const unsigned *__restrict__ marks,
-                                                                  unsigned *__restrict__ dup, int bij) {
+                                                                  unsigned *__restrict__ dup,
+                                                                  unsigned *__restrict__ bucket_mask, int bij) {
     IXP_KERNEL_ENTRY();
     extern __shared__ unsigned s_bm[];
     const unsigned nb = (unsigned)h->spare[0];
@@ -819,7 +883,10 @@ __global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, Bucket
             anydup = 1;
         }
     }
-    if (__syncthreads_or(anydup) && threadIdx.x == 0) atomicOr(&h->flag, 1u);
+    if (__syncthreads_or(anydup) && threadIdx.x == 0) {
+        atomicOr(&h->flag, 1u);
+        atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
+    }
     if (bij && (unsigned long long)cnt < range) {
         // smallest value of this bucket that no element takes
         unsigned long long best = ~0ull;
@@ -934,11 +1001,13 @@ static size_t rnd256(size_t b) { return (b + 255) & ~(size_t)255; }
 static unsigned long long bk_pool_entries(int64_t n) {
     return ((unsigned long long)n + (unsigned long long)n / 4 + 4ull * BK_MAX + 3ull) & ~3ull;
 }
-size_t bk_prefix_bytes(int64_t n) { return HDR_BYTES + rnd256(BK_MAX * 4) + rnd256(bk_pool_entries(n) * 4); }
+size_t bk_prefix_bytes(int64_t n) {
+    return HDR_BYTES + rnd256(BK_MAX * 4) + rnd256(BK_MAX / 8) + rnd256(bk_pool_entries(n) * 4);
+}
 
 struct BitmapWs {
     Hdr *h;
-    unsigned *cursors, *pool, *bm, *dup;
+    unsigned *cursors, *bmask, *pool, *bm, *dup;
     unsigned long long cap;  // bits per bitmap
     bool buckets;            // bucketed layout available
 };
@@ -951,7 +1020,8 @@ static BitmapWs bitmap_ws(void *ws, size_t ws_bytes, int64_t n) {
     size_t off = HDR_BYTES;
     if (w.buckets) {
         w.cursors = (unsigned *)(p + HDR_BYTES);
-        w.pool = (unsigned *)(p + HDR_BYTES + rnd256(BK_MAX * 4));
+        w.bmask = (unsigned *)(p + HDR_BYTES + rnd256(BK_MAX * 4));
+        w.pool = (unsigned *)(p + HDR_BYTES + rnd256(BK_MAX * 4) + rnd256(BK_MAX / 8));
         off = bk_prefix_bytes(n);
     }
     w.cap = ws_bytes > off ? (unsigned long long)((ws_bytes - off) / 8) * 32ull : 0ull;
@@ -982,7 +1052,8 @@ template <typename T, bool BIJ>
 static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int64_t mlo, int64_t mhi, int fixed,
                            int64_t flo, int64_t fhi, const BitmapWs &w, const BucketCfg &cfg, cudaStream_t st) {
     const int sgrid = num_sms() * 4;
-    bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, w.cursors, w.bm, w.dup);
+    bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, w.cursors, w.bm, w.dup,
+                                                          w.bmask);
     const size_t s1 = (size_t)(BK_TILE + 3 * cfg.bmax) * 4;
     cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (BK_TILE + 3 * BK_MAX) * 4);
@@ -990,10 +1061,10 @@ static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int6
     const int g1 = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 2);
     const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
     bucket_scatter_kernel<T, BIJ><<<g1, BK_THREADS, s1, st>>>(x, n, rlo, rhi, mlo, mhi, w.h, cfg, w.cursors, w.pool,
-                                                             w.bm, w.dup, vec);
+                                                             w.bm, w.dup, w.bmask, vec);
     cudaFuncSetAttribute(bucket_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << 20) / 8);
     bucket_check_kernel<<<cfg.bmax, BK_THREADS, (1u << cfg.lw) / 8, st>>>(w.h, cfg, w.cursors, w.pool, w.bm, w.dup,
-                                                                         BIJ ? 1 : 0);
+                                                                         w.bmask, BIJ ? 1 : 0);
 }
 
 template <typename T>
@@ -1009,12 +1080,13 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
         const unsigned long long isize = (unsigned long long)ihi - (unsigned long long)ilo + 1ull;
         if (w.buckets && isize >= BK_MIN_SPAN && bucket_config(isize, bk_pool_entries(n), &cfg)) {
             launch_buckets<T, true>(x, n, rlo, rhi, ilo, ihi, 1, ilo, ihi, w, cfg, st);
-            first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, &h->k_first2);
+            first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, w.bmask, cfg.lw,
+                                                                 &h->k_first2);
         } else {
             bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, 1, ilo, ihi, cap, bm, dup);
             if (n > 0) {
                 mark_kernel<T, true><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, ilo, ihi, h, bm, dup);
-                first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, &h->k_first2);
+                first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, nullptr, 0, &h->k_first2);
             }
             missing_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, bm);
         }
@@ -1026,14 +1098,16 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
     const bool fixed = rspan != 0 && rspan <= cap && rspan <= 4ull * (unsigned long long)n + 4096ull;
     if (!fixed && n > 0) minmax_in_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h);
     const unsigned long long span_cap = fixed ? rspan : cap;
-    if (w.buckets && span_cap >= BK_MIN_SPAN && bucket_config(span_cap, bk_pool_entries(n), &cfg)) {
+    const bool bk = w.buckets && span_cap >= BK_MIN_SPAN && bucket_config(span_cap, bk_pool_entries(n), &cfg);
+    if (bk) {
         launch_buckets<T, false>(x, n, rlo, rhi, rlo, rhi, fixed ? 1 : 0, rlo, rhi, w, cfg, st);
     } else {
         bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, fixed ? 1 : 0, rlo, rhi, cap, bm, dup);
         if (n > 0) mark_kernel<T, false><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, rlo, rhi, h, bm, dup);
     }
     if (n > 0) {
-        first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, dup, &h->k_first);
+        first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, dup, bk ? w.bmask : nullptr,
+                                                             bk ? cfg.lw : 0, &h->k_first);
         partner_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, h, &h->k_first);
     }
     inj_finalize<T><<<1, 1, 0, st>>>(x, h, out);

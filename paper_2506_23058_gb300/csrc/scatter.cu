@@ -113,6 +113,12 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double 
     }
 }
 
+__global__ void f32_to_f64_kernel(double *__restrict__ out, const float *__restrict__ in, int64_t count) {
+    IXP_KERNEL_ENTRY();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += stride) out[i] = (double)in[i];
+}
+
 __global__ void f64_to_f32_kernel(float *__restrict__ out, const double *__restrict__ acc, int64_t count) {
     IXP_KERNEL_ENTRY();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -239,6 +245,13 @@ extern "C" int ixp_f64_to_f32(float *out, const double *acc, int64_t count, ixp_
     if (count < 0 || (count > 0 && (!out || !acc))) return IXP_E_INVAL;
     if (count == 0) return IXP_OK;
     f64_to_f32_kernel<<<stream_grid(count, 4), STREAM_THREADS, 0, (cudaStream_t)stream>>>(out, acc, count);
+    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+extern "C" int ixp_f32_to_f64(double *out, const float *in, int64_t count, ixp_stream stream) {
+    if (count < 0 || (count > 0 && (!out || !in))) return IXP_E_INVAL;
+    if (count == 0) return IXP_OK;
+    f32_to_f64_kernel<<<stream_grid(count, 4), STREAM_THREADS, 0, (cudaStream_t)stream>>>(out, in, count);
     return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
 }
 

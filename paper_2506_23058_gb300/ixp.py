@@ -61,6 +61,7 @@ _SIGS = {
     "ixp_scatter": (_I, [_P, _L, _P, _I, _P, _L, C.c_int32, C.c_int32, C.c_int32, _P]),
     "ixp_scatter_add_f32_to_f64": (_I, [_P, _L, _P, _I, _P, _L, C.c_int32, _P]),
     "ixp_f64_to_f32": (_I, [_P, _P, _L, _P]),
+    "ixp_f32_to_f64": (_I, [_P, _P, _L, _P]),
     "ixp_gather": (_I, [_P, _P, _L, _P, _I, _L, C.c_int32, C.c_int32, _P, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
@@ -316,6 +317,12 @@ def scatter_add_f64(acc, idx, vals, *, stream=None):
 def f64_to_f32(acc, out=None, *, stream=None):
     out = out if out is not None else torch.empty(acc.shape, dtype=torch.float32, device=acc.device)
     _ck(load().ixp_f64_to_f32(_dev(out, "out"), _dev(acc, "acc"), acc.numel(), _stream(stream)), "f64_to_f32")
+    return out
+
+
+def f32_to_f64(x, out=None, *, stream=None):
+    out = out if out is not None else torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    _ck(load().ixp_f32_to_f64(_dev(out, "out"), _dev(x, "x"), x.numel(), _stream(stream)), "f32_to_f64")
     return out
 
 
