@@ -111,7 +111,9 @@ enum {
     IXP_OP_FILTPART = 4, /* extra = nseg */
     IXP_OP_SCAN = 5,     /* extra = nseg */
     IXP_OP_PARTITION = 6,/* extra = nseg */
-    IXP_OP_FLAGS = 7     /* n = m (number of segments) */
+    IXP_OP_FLAGS = 7,    /* n = m (number of segments) */
+    IXP_OP_INJ_SEG = 8,  /* extra = nseg */
+    IXP_OP_BIJ_SEG = 9   /* extra = nseg */
 };
 
 /* Bytes of workspace that call `op` needs for n elements of type itype and the
@@ -165,6 +167,30 @@ int ixp_check_inj(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t r
  * (reported whether or not the property holds). */
 int ixp_check_bij(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, int64_t img_lo,
                   int64_t img_hi, ixp_verdict *d_verdict, void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* Inj of every segment  [Sec. 2.3, Fig. 5, read per segment]: within each segment
+ * [e_k, e_{k+1}), no two positions whose values lie in Rcd = [rcd_lo, rcd_hi] hold
+ * the same value; equal values in different segments are allowed. segs is
+ * required (nseg >= 1, nseg < 2^32). A segment that increases strictly holds at
+ * once (strict monotonicity implies injectivity); any other segment is checked
+ * exactly. Limit: a segment that does not increase strictly and whose in-Rcd values
+ * span more than 2^24 gives verdict status IXP_E_SPAN. Verdict: the first failing
+ * segment decides; index = smallest i in it whose value repeats in the segment,
+ * value = X[i], aux0 = the next j in the segment with X[j] = X[i]. d_seg_ok
+ * (nullable, device uint8_t[nseg]) gets 1/0 per segment. */
+int ixp_check_inj_seg(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, ixp_segs segs,
+                      ixp_verdict *d_verdict, uint8_t *d_seg_ok, void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* Bij X Rcd (e^m, k, e_k, Img_k) with Img_k = [e_k, e_{k+1})  [Sec. 2.3, Fig. 5]:
+ * every segment's in-Rcd values are exactly its own index range (a per-segment
+ * permutation, what a segmented partition produces). Rcd must contain [0, n).
+ * Verdict: the first failing segment decides: the smaller of its first
+ * OUT_OF_IMAGE and first DUPLICATE position, else MISSING with value = its
+ * smallest untaken image value (index -1); aux0 = that segment's in-image count,
+ * aux1 = its length (summed over all segments when the property holds).
+ * Segments longer than 2^24 give verdict status IXP_E_SPAN. */
+int ixp_check_bij_seg(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, ixp_segs segs,
+                      ixp_verdict *d_verdict, uint8_t *d_seg_ok, void *ws, size_t ws_bytes, ixp_stream stream);
 
 /* InvFiltPart Z (p^f, p^p)  [Sec. 2.3, Fig. 5 and the InvFiltPart prose]: Z is the
  * scatter-index array that turns X into its filter-partition, i.e. for each

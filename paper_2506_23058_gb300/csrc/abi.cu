@@ -7,6 +7,7 @@ namespace ixp {
 
 size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg);  // scan.cu
 size_t bk_prefix_bytes(int64_t n);                       // checks.cu
+size_t seg_ws_bytes(int64_t nseg);                       // segmented.cu
 
 int num_sms() {
     static int cached[64] = {0};
@@ -55,6 +56,8 @@ extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra
         case IXP_OP_PARTITION:
         case IXP_OP_FILTPART: return tiled_ws_bytes(n, 16 / es, extra);
         case IXP_OP_FLAGS: return tiled_ws_bytes(n, 2, 0);
+        case IXP_OP_INJ_SEG:
+        case IXP_OP_BIJ_SEG: return seg_ws_bytes(extra);
         default: return 0;
     }
 }
@@ -78,7 +81,8 @@ extern "C" int ixp_version(void) { return 100; }
 extern "C" unsigned long long ixp_tu_kernels_checks(void);
 extern "C" unsigned long long ixp_tu_kernels_scan(void);
 extern "C" unsigned long long ixp_tu_kernels_scatter(void);
+extern "C" unsigned long long ixp_tu_kernels_segmented(void);
 
 extern "C" unsigned long long ixp_kernel_launches(void) {
-    return ixp_tu_kernels_checks() + ixp_tu_kernels_scan() + ixp_tu_kernels_scatter();
+    return ixp_tu_kernels_checks() + ixp_tu_kernels_scan() + ixp_tu_kernels_scatter() + ixp_tu_kernels_segmented();
 }

@@ -22,7 +22,8 @@ I64MAX = 2**63 - 1
 KINDS = ["none", "out_of_range", "order", "duplicate", "out_of_image", "missing", "wrong_dest"]
 CMPS = {"le": 0, "lt": 1, "ge": 2, "gt": 3}
 PREDS = {"true": 0, "mod_eq": 1, "lt": 2, "flags": 3}
-OPS = {"range": 0, "mono": 1, "inj": 2, "bij": 3, "filtpart": 4, "scan": 5, "partition": 6, "flags": 7}
+OPS = {"range": 0, "mono": 1, "inj": 2, "bij": 3, "filtpart": 4, "scan": 5, "partition": 6, "flags": 7,
+       "inj_seg": 8, "bij_seg": 9}
 ERRORS = {0: "ok", -1: "invalid argument", -2: "unsupported element type", -3: "value span exceeds the workspace",
           -4: "workspace too small", -5: "CUDA launch failed", -6: "bounded device wait gave up",
           -7: "index out of bounds"}
@@ -56,6 +57,8 @@ _SIGS = {
     "ixp_check_inj": (_I, [_P, _I, _L, _L, _L, _P, _P, _Z, _P]),
     "ixp_check_bij": (_I, [_P, _I, _L, _L, _L, _L, _L, _P, _P, _Z, _P]),
     "ixp_check_filtpart": (_I, [_P, _I, _L, _P, _I, Pred, Pred, Segs, _P, _P, _Z, _P]),
+    "ixp_check_inj_seg": (_I, [_P, _I, _L, _L, _L, Segs, _P, _P, _P, _Z, _P]),
+    "ixp_check_bij_seg": (_I, [_P, _I, _L, _L, _L, Segs, _P, _P, _P, _Z, _P]),
     "ixp_scan": (_I, [_P, _I, _P, _I, _L, _I, Segs, _P, _P, _P, _Z, _P]),
     "ixp_partition": (_I, [_P, _I, _L, Pred, _P, C.c_int32, _P, _I, _P, _P, _P, Segs, _P, _P, _Z, _P]),
     "ixp_scatter": (_I, [_P, _L, _P, _I, _P, _L, C.c_int32, C.c_int32, C.c_int32, _P]),
@@ -221,6 +224,30 @@ def check_bij(x, rcd_lo, rcd_hi, img_lo, img_hi, *, out=None, ws=None, stream=No
     ws = ws if ws is not None else workspace(need, x.device)
     _ck(load().ixp_check_bij(_dev(x, "x"), _itype(x), x.numel(), rcd_lo, rcd_hi, img_lo, img_hi, v.data_ptr(),
                              ws.data_ptr(), ws.numel(), _stream(stream)), "check_bij")
+    return Verdict(v)
+
+
+def check_inj_seg(x, offsets, rcd_lo=I64MIN, rcd_hi=I64MAX, *, seg_ok=None, out=None, ws=None, stream=None):
+    """Inj of every segment [offsets[k], offsets[k+1])."""
+    v = _verdict_buf(x.device, out)
+    segs = _segs(offsets)
+    need = workspace_size("inj_seg", _itype(x), x.numel(), segs.nseg)
+    ws = ws if ws is not None else workspace(need, x.device)
+    so = None if seg_ok is None else _dev(seg_ok, "seg_ok")
+    _ck(load().ixp_check_inj_seg(_dev(x, "x"), _itype(x), x.numel(), rcd_lo, rcd_hi, segs, v.data_ptr(), so,
+                                 ws.data_ptr(), ws.numel(), _stream(stream)), "check_inj_seg")
+    return Verdict(v)
+
+
+def check_bij_seg(x, offsets, rcd_lo=I64MIN, rcd_hi=I64MAX, *, seg_ok=None, out=None, ws=None, stream=None):
+    """Bij of every segment onto its own index range [offsets[k], offsets[k+1])."""
+    v = _verdict_buf(x.device, out)
+    segs = _segs(offsets)
+    need = workspace_size("bij_seg", _itype(x), x.numel(), segs.nseg)
+    ws = ws if ws is not None else workspace(need, x.device)
+    so = None if seg_ok is None else _dev(seg_ok, "seg_ok")
+    _ck(load().ixp_check_bij_seg(_dev(x, "x"), _itype(x), x.numel(), rcd_lo, rcd_hi, segs, v.data_ptr(), so,
+                                 ws.data_ptr(), ws.numel(), _stream(stream)), "check_bij_seg")
     return Verdict(v)
 
 

@@ -217,6 +217,109 @@ def test_inj_bucketed_skewed_overflow(ixp, dev, dtype):
     same(ixp.check_bij(T(a, dev), I64MIN, I64MAX, 0, img_hi), oracle.check_bij(a, I64MIN, I64MAX, 0, img_hi), "bij-gap")
 
 
+# ---- per-segment Inj / Bij
+
+def mixed_segments(rng, m, small_max=300, big=(), empty_p=0.15):
+    """Segment lengths: mostly small (warp path), some above 256 (block path), a few big."""
+    L = rng.integers(0, small_max, size=m)
+    L[rng.random(m) < empty_p] = 0
+    for pos, ln in big:
+        L[pos] = ln
+    return synth.offsets_from_shape(L)
+
+
+def seg_perm(rng, off, dtype):
+    return np.concatenate([rng.permutation(np.arange(off[k], off[k + 1])) for k in range(len(off) - 1)]
+                          ).astype(dtype) if off[-1] else np.zeros(0, dtype)
+
+
+def seg_same(ixp, dev, x, off, g_fn, o_fn, what):
+    m = len(off) - 1
+    so = torch.full((m,), 7, dtype=torch.uint8, device=dev)
+    g = g_fn(T(x, dev), T(off, dev), seg_ok=so)
+    o, oso = o_fn(x, off)
+    same(g, o, what)
+    assert np.array_equal(so.cpu().numpy(), oso[:m]), what
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_bij_seg(ixp, dev, dtype):
+    rng = np.random.default_rng(41)
+    off = mixed_segments(rng, 2000, big=[(5, 5000), (700, 70000), (1500, 1 << 20)])
+    x = seg_perm(rng, off, dtype)
+    n = int(off[-1])
+    g_fn = lambda t, o, seg_ok: ixp.check_bij_seg(t, o, seg_ok=seg_ok)  # noqa: E731
+    o_fn = lambda a, o: oracle.check_bij(a, I64MIN, I64MAX, seg_img=True, offsets=o, seg_ok=True)  # noqa: E731
+    seg_same(ixp, dev, x, off, g_fn, o_fn, "ok")
+    nonempty = np.flatnonzero(np.diff(off) > 1)
+    for trial in range(6):
+        y = x.copy()
+        k = int(nonempty[rng.integers(0, len(nonempty))]) if trial < 4 else int(nonempty[-1 - trial])
+        a, b = int(off[k]), int(off[k + 1])
+        i, j = a + int(rng.integers(0, b - a)), a + int(rng.integers(0, b - a))
+        if trial % 3 == 0:
+            y[j] = y[i] if i != j else y[i]  # duplicate inside the segment (also a missing value)
+        elif trial % 3 == 1:
+            y[i] = (b + 3) % n  # value of another segment
+        else:
+            y[i] = n + 10  # outside Rcd [0, n+5]: ignored, leaves a missing value
+        for rlo, rhi in [(I64MIN, I64MAX), (0, n + 5)]:
+            g_fn2 = lambda t, o, seg_ok: ixp.check_bij_seg(t, o, rlo, rhi, seg_ok=seg_ok)  # noqa: E731
+            o_fn2 = lambda a_, o: oracle.check_bij(a_, rlo, rhi, seg_img=True, offsets=o, seg_ok=True)  # noqa: E731
+            seg_same(ixp, dev, y, off, g_fn2, o_fn2, (trial, k, rlo))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_inj_seg(ixp, dev, dtype):
+    rng = np.random.default_rng(43)
+    off = mixed_segments(rng, 3000, big=[(9, 4000), (1000, 50000), (2000, 300000)])
+    m = len(off) - 1
+    n = int(off[-1])
+    g_fn = lambda t, o, seg_ok: ixp.check_inj_seg(t, o, seg_ok=seg_ok)  # noqa: E731
+    o_fn = lambda a, o: oracle.check_inj(a, offsets=o, seg_ok=True)  # noqa: E731
+    # rows of sorted distinct columns (strict increase), as in CSR
+    cols = np.concatenate([np.sort(rng.choice(1 << 24, size=int(off[k + 1] - off[k]), replace=False))
+                           for k in range(m)]).astype(dtype)
+    seg_same(ixp, dev, cols, off, g_fn, o_fn, "sorted")
+    nonempty = np.flatnonzero(np.diff(off) > 2)
+    for trial in range(8):
+        y = cols.copy()
+        k = int(nonempty[rng.integers(0, len(nonempty))]) if trial < 5 else int(nonempty[-1 - trial])
+        a, b = int(off[k]), int(off[k + 1])
+        p = a + 1 + int(rng.integers(0, b - a - 1))
+        if trial % 2 == 0:
+            y[p] = y[p - 1]  # planted duplicate
+        else:
+            y[p], y[p - 1] = y[p - 1], y[p]  # order swap: still injective
+        seg_same(ixp, dev, y, off, g_fn, o_fn, (trial, k))
+    # unsorted rows with small spans (shared-memory bitmaps) and repeats across rows (allowed)
+    z = np.concatenate([rng.permutation(int(off[k + 1] - off[k])) for k in range(m)]).astype(dtype)
+    seg_same(ixp, dev, z, off, g_fn, o_fn, "perm-rows")
+    z2 = z.copy()
+    k = 2000
+    z2[int(off[k]) + 7] = z2[int(off[k]) + 100]
+    seg_same(ixp, dev, z2, off, g_fn, o_fn, "perm-rows-dup")
+    # an unsorted row whose values span more than 2^20 (global-bitmap pass)
+    z3 = z.copy()
+    a, b = int(off[1000]), int(off[1001])
+    z3[a:b] = rng.choice(1 << 23, size=b - a, replace=False)
+    seg_same(ixp, dev, z3, off, g_fn, o_fn, "wide-row")
+    z3[a + 17] = z3[b - 1]
+    seg_same(ixp, dev, z3, off, g_fn, o_fn, "wide-row-dup")
+    # Rcd restricts the check
+    g_r = lambda t, o, seg_ok: ixp.check_inj_seg(t, o, 0, 100, seg_ok=seg_ok)  # noqa: E731
+    o_r = lambda a_, o: oracle.check_inj(a_, 0, 100, offsets=o, seg_ok=True)  # noqa: E731
+    seg_same(ixp, dev, z2, off, g_r, o_r, "rcd")
+
+
+def test_inj_seg_span_limit(ixp, dev):
+    rng = np.random.default_rng(47)
+    off = np.array([0, 1000, 1300], np.int64)
+    x = np.concatenate([np.arange(1000), rng.choice(1 << 40, size=300, replace=False)]).astype(np.int64)
+    g = ixp.check_inj_seg(T(x, dev), T(off, dev)).get()
+    assert g["status"] == -3 and g["ok"] == -1
+
+
 @pytest.mark.parametrize("it,ot", [(np.int32, np.int32), (np.int32, np.int64), (np.int64, np.int64)])
 @pytest.mark.parametrize("n", SIZES + [300000])
 def test_scan_flat(ixp, dev, n, it, ot):
