@@ -267,6 +267,41 @@ int ixp_flags_from_shape(const int64_t *shape, int64_t m, const int64_t *xs, voi
                          int64_t out_len, int64_t *d_offsets, int32_t *d_status, void *ws, size_t ws_bytes,
                          ixp_stream stream);
 
+/* ---- batched pipeline over a jagged array ---------------------------------------- */
+
+/* Launch shape of ixp_batch_run (the autotuner's search space): threads per CTA
+ * (256 or 512), resident CTAs per SM (1..8), log2 of the shared bitmap in bits
+ * (10..20) and elements per thread per sweep step (4 or 8). */
+typedef struct {
+    int32_t threads;
+    int32_t ctas_per_sm;
+    int32_t smem_bits_log2;
+    int32_t chunk;
+} ixp_batch_tuning;
+
+/* Bytes of workspace ixp_batch_run needs for a tuning (NULL = defaults). */
+size_t ixp_batch_workspace_size(const ixp_batch_tuning *tuning);
+
+/* One persistent launch over the m segments of a jagged array of n = sum(shape)
+ * int32 elements [Sec. 2.1 mkSgmDescr; Sec. 6 partition2L; Sec. 2.3 Fig. 5 checks].
+ * For every segment k (e_k = shape[0] + ... + shape[k-1]):
+ *   flags[e_k..e_{k+1})   = 1 at e_k, 0 elsewhere (mkSgmDescr with xs = 1)
+ *   indices[e_k..e_{k+1}) = the stable partition destinations of the segment's
+ *                           keys under pred (trues first), d_num_true[k] = T_k
+ *   d_seg_ok[k]           = Mono< of iota inside the segment
+ *   d_seg_ok[m + k]       = Inj of chk inside the segment
+ *   d_seg_ok[2m + k]      = Bij of chk inside the segment onto [e_k, e_{k+1})
+ * d_offsets (int64[m+1]) gets e_0..e_m; d_first_bad[0..2] the first segment
+ * failing Mono / Inj / Bij (-1 if none). order (nullable) is the work list, a
+ * permutation of [0, m) (longest segments first balances the launch). pred is
+ * TRUE, MOD_EQ or LT. d_status gets IXP_E_INVAL for a negative size, a bad work
+ * list or sum(shape) != n, and IXP_E_SPAN if a segment's chk values span more
+ * than 2^21 (Inj/Bij then read 0 for that segment). */
+int ixp_batch_run(const int64_t *shape, int64_t m, const int32_t *keys, ixp_pred pred, const int32_t *chk,
+                  const int32_t *iota, int64_t n, const int32_t *order, int32_t *flags, int32_t *indices,
+                  int64_t *d_num_true, int64_t *d_offsets, uint8_t *d_seg_ok, int64_t *d_first_bad,
+                  int32_t *d_status, const ixp_batch_tuning *tuning, void *ws, size_t ws_bytes, ixp_stream stream);
+
 /* ---- allocation-free scan -------------------------------------------------------- */
 
 /* ixp_scan for callers that cannot allocate device memory at all: a host runtime

@@ -5,7 +5,7 @@ gather / partition / mkSgmDescr combinators that build and use such arrays.
 The compute path is the CUDA library built from ``csrc/`` (C ABI: include/ixp.h);
 this package only marshals torch tensors into it. There is no CPU fallback.
 """
-from . import autograd  # noqa: F401
+from . import autograd, batched, tune  # noqa: F401
 from .ixp import (I64MAX, I64MIN, IxpError, Verdict, check_bij, check_bij_seg, check_filtpart, check_inj,
                   check_inj_seg, check_mono,  # noqa: F401
                   check_range, debug_set_wait, f32_to_f64, f64_to_f32, flags_from_shape, gather, lib_path, load, make_pred,

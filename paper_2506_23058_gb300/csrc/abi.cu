@@ -82,7 +82,9 @@ extern "C" unsigned long long ixp_tu_kernels_checks(void);
 extern "C" unsigned long long ixp_tu_kernels_scan(void);
 extern "C" unsigned long long ixp_tu_kernels_scatter(void);
 extern "C" unsigned long long ixp_tu_kernels_segmented(void);
+extern "C" unsigned long long ixp_tu_kernels_batched(void);
 
 extern "C" unsigned long long ixp_kernel_launches(void) {
-    return ixp_tu_kernels_checks() + ixp_tu_kernels_scan() + ixp_tu_kernels_scatter() + ixp_tu_kernels_segmented();
+    return ixp_tu_kernels_checks() + ixp_tu_kernels_scan() + ixp_tu_kernels_scatter() + ixp_tu_kernels_segmented() +
+           ixp_tu_kernels_batched();
 }

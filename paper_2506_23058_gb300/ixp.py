@@ -43,6 +43,11 @@ class Segs(C.Structure):
     _fields_ = [("offsets", C.c_void_p), ("nseg", C.c_int64)]
 
 
+class BatchTuning(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("ctas_per_sm", C.c_int32), ("smem_bits_log2", C.c_int32),
+                ("chunk", C.c_int32)]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _L = C.c_int64
@@ -69,6 +74,8 @@ _SIGS = {
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
     "ixp_kernel_launches": (C.c_ulonglong, []),
+    "ixp_batch_workspace_size": (_Z, [_P]),
+    "ixp_batch_run": (_I, [_P, _L, _P, Pred, _P, _P, _L, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _Z, _P]),
 }
 
 _lib = None
