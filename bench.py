@@ -331,6 +331,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ops", default="", help="comma-separated subset of op names (profiling)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -429,6 +430,12 @@ def main():
     if not args.no_e2e and not args.ops:
         e2e = run_e2e(ixp, R, ops, inp, dev, args, step_bytes)
 
+    extras = {}
+    if not args.ops and not args.no_extras:
+        plain_ns_per_byte = (total_ms / args.steps) * 1e6 / step_bytes
+        extras["batched"] = run_batched(ixp, inp, n32, dev, plain_ns_per_byte, args)
+        extras["backward"] = run_backward(ixp, inp, n32, dev, per_op)
+
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/int64 (index), f32 payload", "data": "synthetic",
@@ -440,12 +447,103 @@ def main():
             "verdicts": checks}
     if e2e is not None:
         line["e2e"] = e2e
+    line.update(extras)
     if rank == 0 and world == 1 and not args.no_cpu and not args.ops:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _time(fn, reps=5, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def run_batched(ixp, inp, n32, dev, plain_ns_per_byte, args):
+    """4096 segments of log-uniform size in [1, 2^20] (total <= 2^28 int32): flags,
+    per-segment partition (p = 0.3), per-segment Mono/Inj/Bij with 1% of segments
+    violated, all in one persistent launch replayed from a CUDA graph."""
+    import torch
+    from paper_2506_23058_gb300 import batched, tune
+    s = synth.seed_for(3)
+    shape = synth.shapes_log_uniform(4096, s, max_log2=20, cap_total=n32)
+    n = int(shape.sum())
+    sh = torch.from_numpy(shape).to(dev)
+    seg = torch.repeat_interleave(torch.arange(4096, device=dev, dtype=torch.int64), sh)
+    g = torch.Generator(device=dev)
+    g.manual_seed(s + 1)
+    r = torch.randint(0, 2**31, (n,), generator=g, device=dev, dtype=torch.int64)
+    chk = torch.argsort(seg * (2**31) + r).to(torch.int32)  # a permutation of each segment's range
+    off = torch.zeros(4097, dtype=torch.int64, device=dev)
+    off[1:] = torch.cumsum(sh, 0)
+    iota = (torch.arange(n, device=dev, dtype=torch.int64) - off[seg]).to(torch.int32)
+    del r, seg
+    rng = np.random.default_rng(s + 2)
+    offh = off.cpu().numpy()
+    for k in rng.choice(np.flatnonzero(shape >= 3), size=41, replace=False):
+        i = int(offh[k]) + int(rng.integers(1, int(shape[k])))
+        if k % 2:
+            chk[i] = chk[i - 1]
+        else:
+            iota[i] = iota[i - 1]
+    keys = inp["keys"][:n]
+    br = batched.BatchRunner(shape, keys, ("lt", 0, synth.bernoulli_threshold(0.3)), chk, iota)
+    tuned = tune.lookup(br.n, br.m)
+    if tuned is None:
+        tuned = tuple(tune.autotune(br, reps=2)["tuning"])
+    br.set_tuning(tuned)
+    br.capture()
+    ms = _time(br.replay, reps=5)
+    res = br.results()
+    nbytes = br.algorithmic_bytes()
+    ns_per_byte = ms * 1e6 / nbytes
+    return {"workload": "4096 segments log-uniform [1, 2^20], n=%d int32, p=0.3, 1%% planted" % n, "ms": round(ms, 4),
+            "alg_bytes": nbytes, "gbs": round(nbytes / (ms / 1e3) / 1e9, 1), "tuning": list(tuned),
+            "time_per_byte_vs_plain": round(ns_per_byte / plain_ns_per_byte, 3), "graph": True,
+            "first_bad": res["first_bad"], "status": res["status"]}
+
+
+def run_backward(ixp, inp, n32, dev, per_op):
+    """Backward of gather on a [n/4 x 8] float32 payload by a permutation (an
+    atomic-free scatter, Inj proven) and of a Zipf(1.1) scatter-add over 2^20 targets
+    (a gather), each against the forward op's time per byte."""
+    import torch
+    from paper_2506_23058_gb300 import autograd
+    nr = n32 // 4
+    perm = inp["perm_rows"]
+    src = inp["payload8"].detach().requires_grad_(True)
+    inv = ixp.invert(perm, nr)  # the proven-Inj index's inverse, built once per index array
+    y = autograd.gather(src, perm, inverse=inv)
+    gy = torch.empty_like(y).uniform_(-1, 1)
+    fwd = _time(lambda: autograd.gather(src, perm, inverse=inv))
+    bwd = _time(lambda: torch.autograd.grad(y, src, gy, retain_graph=True))
+    nbytes = 68 * nr
+    zipf = torch.from_numpy(synth.zipf_ranks(nr, 1 << 20, 1.1, synth.seed_for(4))).to(dev)
+    dst = torch.zeros((1 << 20, 8), dtype=torch.float32, device=dev, requires_grad=True)
+    z = autograd.scatter_add(dst, zipf, src)
+    gz = torch.empty_like(z).uniform_(-1, 1)
+    zf = _time(lambda: autograd.scatter_add(dst, zipf, src))
+    zb = _time(lambda: torch.autograd.grad(z, src, gz, retain_graph=True))
+    zbytes = 4 * nr + 32 * nr + 2 * 32 * (1 << 20)
+    return {"gather_inj": {"fwd_ms": round(fwd, 4), "bwd_ms": round(bwd, 4),
+                           "bwd_gbs": round(nbytes / (bwd / 1e3) / 1e9, 1),
+                           "time_per_byte_vs_plain": round(bwd / fwd, 3)},
+            "scatter_add_zipf": {"fwd_ms": round(zf, 4), "bwd_ms": round(zb, 4),
+                                 "fwd_gbs": round(zbytes / (zf / 1e3) / 1e9, 1),
+                                 "bwd_gbs": round(nbytes / (zb / 1e3) / 1e9, 1),
+                                 "bwd_time_per_byte_vs_plain_gather": round((zb / nbytes) / (fwd / nbytes), 3)},
+            "workload": "payload [%d x 8] f32; permutation; Zipf(1.1) over 2^20 targets" % nr}
 
 
 def run_e2e(ixp, R, ops, inp, dev, args, step_bytes):

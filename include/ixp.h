@@ -246,6 +246,14 @@ int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const void *idx, in
 /* Rounds a float64 accumulator to float32 (out[i] = (float)acc[i], count elements). */
 int ixp_f64_to_f32(float *out, const double *acc, int64_t count, ixp_stream stream);
 
+/* Inverse of an index array, the is^-1 that rule Sc1 (Sec. 4, scatter conversion)
+ * couples to a bijective scatter index: inv[idx[i]] = i for every in-bounds
+ * idx[i] in [0, inv_len), and inv[j] = -1 for targets no index hits. idx must be
+ * injective on its in-bounds entries (check with ixp_check_inj); otherwise which
+ * i lands in inv[j] is unspecified. With inv, the adjoint of a gather by idx is the
+ * gather by inv (out-of-range -1 rows read as zero), with no atomics. */
+int ixp_invert(const void *idx, int itype, int64_t n, void *inv, int inv_type, int64_t inv_len, ixp_stream stream);
+
 /* Widens float32 to float64 (out[i] = (double)in[i]); used to pre-load a float64
  * accumulator with a float32 destination before an additive scatter. */
 int ixp_f32_to_f64(double *out, const float *in, int64_t count, ixp_stream stream);
@@ -294,9 +302,11 @@ size_t ixp_batch_workspace_size(const ixp_batch_tuning *tuning);
  * d_offsets (int64[m+1]) gets e_0..e_m; d_first_bad[0..2] the first segment
  * failing Mono / Inj / Bij (-1 if none). order (nullable) is the work list, a
  * permutation of [0, m) (longest segments first balances the launch). pred is
- * TRUE, MOD_EQ or LT. d_status gets IXP_E_INVAL for a negative size, a bad work
- * list or sum(shape) != n, and IXP_E_SPAN if a segment's chk values span more
- * than 2^21 (Inj/Bij then read 0 for that segment). */
+ * TRUE, MOD_EQ or LT. keys, chk, iota, flags and indices must be 16-byte aligned
+ * (else IXP_E_INVAL). d_status gets IXP_E_INVAL for a negative size, a bad work
+ * list or sum(shape) != n, and IXP_E_SPAN if a segment is longer than 2^21 or its
+ * chk values, when some fall outside its image, span more than 2^21 (Inj/Bij then
+ * read 0 for that segment). */
 int ixp_batch_run(const int64_t *shape, int64_t m, const int32_t *keys, ixp_pred pred, const int32_t *chk,
                   const int32_t *iota, int64_t n, const int32_t *order, int32_t *flags, int32_t *indices,
                   int64_t *d_num_true, int64_t *d_offsets, uint8_t *d_seg_ok, int64_t *d_first_bad,

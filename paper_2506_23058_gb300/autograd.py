@@ -5,9 +5,12 @@ outputs and marshals arguments):
 
 * ``gather``   y[i] = src[idx[i]].  Adjoint: grad_src[t] = sum of grad_y[i] over
   idx[i] = t. When the caller asserts (or has checked with ``check_inj``) that idx
-  is injective, that sum has at most one term, so the adjoint is a plain scatter
-  with no atomics. Otherwise float32 gradients accumulate in float64 and are
-  rounded once; float64 gradients use float64 atomics.
+  is injective, that sum has at most one term: with the inverse index array
+  (``invert``; the paper's scatter rule Sc1 builds the same is^-1 for a bijective
+  index) the adjoint is a gather, grad_src[t] = grad_y[inv[t]], with sequential
+  writes and no atomics; without it, a plain atomic-free scatter. Otherwise float32
+  gradients accumulate in float64 and are rounded once; float64 gradients use
+  float64 atomics.
 * ``scatter``  out = dst with rows idx[i] replaced by vals[i] (indices outside
   dst are ignored, Sec. 2.1). Requires injective in-bounds indices (the paper's
   condition for a deterministic scatter). Adjoint: grad_vals = gather of grad_out
@@ -42,24 +45,28 @@ def _scatter_add_into(grad, idx, g):
 
 class GatherFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, src, idx, injective=False):
+    def forward(ctx, src, idx, injective=False, inverse=None):
         out, status = ixp.gather(src.contiguous(), idx)
-        ctx.save_for_backward(idx, status)
+        ctx.save_for_backward(idx, inverse if inverse is not None else idx)
+        ctx.has_inverse = inverse is not None
         ctx.src_shape = src.shape
-        ctx.injective = bool(injective)
+        ctx.injective = bool(injective) or inverse is not None
         ctx.mark_non_differentiable(status)
         return out, status
 
     @staticmethod
     def backward(ctx, g, _g_status):
-        idx, status = ctx.saved_tensors
+        idx, inv = ctx.saved_tensors
         g = g.contiguous()
+        if ctx.has_inverse:
+            grad, _ = ixp.gather(g, inv)  # rows no index reaches read as zero
+            return grad, None, None, None
         grad = _zeros(ctx.src_shape, g.dtype, g.device)
         if ctx.injective:
             ixp.scatter(grad, idx, g)  # one term per target: no atomics
         else:
             _scatter_add_into(grad, idx, g)
-        return grad, None, None
+        return grad, None, None, None
 
 
 class ScatterFn(torch.autograd.Function):
@@ -120,8 +127,9 @@ class PartitionFn(torch.autograd.Function):
         return grad, None, None, None, None
 
 
-def gather(src, idx, injective=False):
-    return GatherFn.apply(src, idx, injective)[0]
+def gather(src, idx, injective=False, inverse=None):
+    """inverse: ``invert(idx, src.shape[0])`` for an injective idx (cache it when idx is fixed)."""
+    return GatherFn.apply(src, idx, injective, inverse)[0]
 
 
 def scatter(dst, idx, vals):

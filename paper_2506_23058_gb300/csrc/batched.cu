@@ -72,38 +72,40 @@ __global__ void __launch_bounds__(NT) batch_kernel(const int64_t *__restrict__ s
     extern __shared__ unsigned bt_bm[];
     __shared__ unsigned long long s_red[NT / 32];
     __shared__ unsigned s_cnt[CH][NT / 32];
-    __shared__ unsigned long long s_k;
-    constexpr int CHUNK = NT * CH;  // elements per sweep step
+    __shared__ unsigned long long s_k, s_carry;
+    __shared__ long long s_mm[2];
+    constexpr int U = 4;  // 16-byte vectors in flight per thread in sweep 1
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
     unsigned *my_gbm = gbm + (BT_GLOBAL_BITS / 32) * blockIdx.x;
     while (true) {
-        if (threadIdx.x == 0) s_k = atomicAdd(&h->spare[BT_CLAIM], 1ull);
+        if (tid == 0) s_k = atomicAdd(&h->spare[BT_CLAIM], 1ull);
         __syncthreads();
         const unsigned long long c = s_k;
         __syncthreads();
         if (c >= (unsigned long long)m) break;
         const int64_t k = order ? (int64_t)order[c] : (int64_t)c;
         if (k < 0 || k >= m) {  // the work list must be a permutation of [0, m)
-            if (threadIdx.x == 0) set_status(h, IXP_E_INVAL);
+            if (tid == 0) set_status(h, IXP_E_INVAL);
             continue;
         }
         // e_k = sum of shape[0..k); a negative size invalidates the call
         unsigned long long part = 0;
         bool neg = false;
-        for (int64_t j = threadIdx.x; j < k; j += NT) {
-            const int64_t s = __ldg(shape + j);
-            neg |= s < 0;
-            part += (unsigned long long)s;
+        for (int64_t j = tid; j < k; j += NT) {
+            const int64_t sj = __ldg(shape + j);
+            neg |= sj < 0;
+            part += (unsigned long long)sj;
         }
         const int64_t L0 = __ldg(shape + k);
         neg |= L0 < 0;
         const int64_t e = (int64_t)bt_block_sum<NT>(part, s_red);
         if (__syncthreads_or(neg)) {
-            if (threadIdx.x == 0) set_status(h, IXP_E_INVAL);
+            if (tid == 0) set_status(h, IXP_E_INVAL);
             continue;
         }
         const int64_t a = e < 0 ? 0 : (e > n ? n : e);
         const int64_t b = (e + L0) > n ? n : (e + L0);
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             offsets[k] = e;
             if (k == m - 1) {
                 offsets[m] = e + L0;
@@ -111,104 +113,191 @@ __global__ void __launch_bounds__(NT) batch_kernel(const int64_t *__restrict__ s
             }
         }
         if (b <= a) {
-            if (threadIdx.x == 0) {
+            if (tid == 0) {
                 num_true[k] = 0;
                 seg_ok[k] = seg_ok[m + k] = seg_ok[2 * m + k] = 1;
             }
             continue;
         }
-        // ---- sweep 1: trues, Mono of iota, min/max of chk
+        const int64_t L = b - a;
+        // head [a, a4), body of whole 16-byte vectors [a4, b4), tail [b4, b)
+        const int64_t a4 = min(b, (a + 3) & ~(int64_t)3);
+        const int64_t nv = (b - a4) / 4;
+        const int64_t b4 = a4 + 4 * nv;
+        // bitmap over the segment's image [a, b) for chk
+        const bool img_fits = (unsigned long long)L <= BT_GLOBAL_BITS;
+        unsigned *bm = (unsigned long long)L <= smem_bits ? bt_bm : my_gbm;
+        if (img_fits)
+            for (int64_t q = tid; q < (L + 31) / 32; q += NT) bm[q] = 0u;
+        __syncthreads();
+        // ---- sweep 1: trues, Mono of iota, image marks and min/max of chk
         unsigned long long tcount = 0;
-        bool mono_bad = false;
+        bool mono_bad = false, dup = false, outside = false;
         int64_t mn = INT64_MAX, mx = INT64_MIN;
-        for (int64_t i0 = a; i0 < b; i0 += CHUNK) {
+        auto visit = [&](int64_t i, int32_t kv, int32_t it, int32_t it_prev, int32_t cv) {
+            tcount += bt_pred(pred, kv) ? 1u : 0u;
+            if (i > a && !(it_prev < it)) mono_bad = true;
+            const int64_t v = cv;
+            mn = v < mn ? v : mn;
+            mx = v > mx ? v : mx;
+            if (v < a || v >= b) {
+                outside = true;
+            } else if (img_fits) {
+                const unsigned r = (unsigned)(v - a), bit = 1u << (r & 31);
+                if (atomicOr(bm + (r >> 5), bit) & bit) dup = true;
+            }
+        };
+        if (tid < 3) {
+            const int64_t i = a + tid;
+            if (i < a4) visit(i, keys[i], iota[i], i > a ? iota[i - 1] : 0, chk[i]);
+            const int64_t j = b4 + tid;
+            if (j < b) visit(j, keys[j], iota[j], j > a ? iota[j - 1] : 0, chk[j]);
+        }
+        for (int64_t v0 = tid; v0 < nv; v0 += (int64_t)NT * U) {
+            int4 kq[U], iq[U], cq[U];
+            int32_t ip[U];
 #pragma unroll
-            for (int q = 0; q < CH; q++) {
-                const int64_t i = i0 + q * NT + threadIdx.x;
-                if (i < b) {
-                    tcount += bt_pred(pred, __ldcs(keys + i)) ? 1u : 0u;
-                    const int32_t it = __ldg(iota + i);
-                    if (i > a && !(__ldg(iota + i - 1) < it)) mono_bad = true;
-                    const int64_t v = (int64_t)__ldcs(chk + i);
-                    mn = v < mn ? v : mn;
-                    mx = v > mx ? v : mx;
+            for (int u = 0; u < U; u++) {
+                const int64_t v = v0 + (int64_t)u * NT;
+                if (v < nv) {
+                    const int64_t p = a4 + 4 * v;
+                    kq[u] = __ldcs(reinterpret_cast<const int4 *>(keys + p));
+                    iq[u] = __ldcs(reinterpret_cast<const int4 *>(iota + p));
+                    cq[u] = __ldcs(reinterpret_cast<const int4 *>(chk + p));
+                    ip[u] = p > a ? __ldg(iota + p - 1) : 0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; u++) {
+                const int64_t v = v0 + (int64_t)u * NT;
+                if (v < nv) {
+                    const int64_t p = a4 + 4 * v;
+                    visit(p, kq[u].x, iq[u].x, ip[u], cq[u].x);
+                    visit(p + 1, kq[u].y, iq[u].y, iq[u].x, cq[u].y);
+                    visit(p + 2, kq[u].z, iq[u].z, iq[u].y, cq[u].z);
+                    visit(p + 3, kq[u].w, iq[u].w, iq[u].z, cq[u].w);
                 }
             }
         }
         const unsigned long long T = bt_block_sum<NT>(tcount, s_red);
         const int any_mono_bad = __syncthreads_or(mono_bad);
+        const int any_dup = __syncthreads_or(dup);
+        const int any_out = __syncthreads_or(outside);
         const unsigned long long kmn = block_max_u64(enc_min(mn), s_red);
         const unsigned long long kmx = block_max_u64(enc_max(mx), s_red);
-        __shared__ long long s_mm[2];
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             s_mm[0] = dec_min(kmn);
             s_mm[1] = dec_max(kmx);
         }
         __syncthreads();
-        const int64_t gmn = s_mm[0], gmx = s_mm[1];
-        // ---- sweep 2: partition destinations and the flag array. Element (q, warp w,
-        // lane l) of a chunk sits at i0 + q * NT + 32 w + l; ranks come from ballots.
-        unsigned long long carry = 0;
-        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-        const unsigned lt = (1u << l) - 1u;
-        for (int64_t i0 = a; i0 < b; i0 += CHUNK) {
-            unsigned bal[CH];
+        // ---- sweep 2: partition destinations and the flag array
+        auto dest = [&](int64_t i, bool t, unsigned long long tb) -> int32_t {
+            return (int32_t)(t ? a + (int64_t)tb : a + (int64_t)T + (i - a) - (int64_t)tb);
+        };
+        if (tid == 0) {  // head elements, in order
+            unsigned long long cc = 0;
+            for (int64_t i = a; i < a4; i++) {
+                const bool t = bt_pred(pred, keys[i]);
+                indices[i] = dest(i, t, cc);
+                flags[i] = i == a ? 1 : 0;
+                cc += t ? 1u : 0u;
+            }
+            s_carry = cc;
+        }
+        __syncthreads();
+        unsigned long long carry = s_carry;
+        const unsigned ltm = (1u << l) - 1u;
+        for (int64_t c0 = 0; c0 < nv; c0 += (int64_t)NT * CH) {
+            unsigned msk[CH], lpre[CH];
+            int4 kq[CH];
 #pragma unroll
             for (int q = 0; q < CH; q++) {
-                const int64_t i = i0 + q * NT + threadIdx.x;
-                const bool t = i < b && bt_pred(pred, __ldg(keys + i));
-                bal[q] = __ballot_sync(FULL, t);
-                if (l == 0) s_cnt[q][w] = __popc(bal[q]);
+                const int64_t v = c0 + (int64_t)q * NT + tid;
+                msk[q] = 0;
+                if (v < nv) {
+                    kq[q] = __ldg(reinterpret_cast<const int4 *>(keys + a4 + 4 * v));
+                    msk[q] = (bt_pred(pred, kq[q].x) ? 1u : 0u) | (bt_pred(pred, kq[q].y) ? 2u : 0u) |
+                             (bt_pred(pred, kq[q].z) ? 4u : 0u) | (bt_pred(pred, kq[q].w) ? 8u : 0u);
+                }
+                const unsigned x = __popc(msk[q]);
+                unsigned y = x;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const unsigned o = __shfl_up_sync(FULL, y, d);
+                    if (l >= d) y += o;
+                }
+                lpre[q] = y - x;
+                if (l == 31) s_cnt[q][w] = y;
             }
             __syncthreads();
-            unsigned before = 0, tot = 0;  // trues of this chunk before (q, w); chunk total
+            unsigned tot = 0, run = 0;
 #pragma unroll
             for (int q = 0; q < CH; q++) {
-                for (int ww = 0; ww < NT / 32; ww++) tot += s_cnt[q][ww];
-            }
-#pragma unroll
-            for (int q = 0; q < CH; q++) {
-                unsigned pq = 0;
-                for (int qq = 0; qq < q; qq++)
-                    for (int ww = 0; ww < NT / 32; ww++) pq += s_cnt[qq][ww];
-                for (int ww = 0; ww < w; ww++) pq += s_cnt[q][ww];
-                before = pq;
-                const int64_t i = i0 + q * NT + threadIdx.x;
-                if (i < b) {
-                    const unsigned long long tb = carry + before + __popc(bal[q] & lt);
-                    const bool t = (bal[q] >> l) & 1u;
-                    const int64_t d = t ? a + (int64_t)tb : a + (int64_t)T + (i - a) - (int64_t)tb;
-                    __stcs(indices + i, (int32_t)d);
-                    __stcs(flags + i, i == a ? 1 : 0);
+                unsigned before = run;  // all of q' < q
+                for (int ww = 0; ww < NT / 32; ww++) {
+                    const unsigned cq2 = s_cnt[q][ww];
+                    if (ww < w) before += cq2;
+                    run += cq2;
+                }
+                const int64_t v = c0 + (int64_t)q * NT + tid;
+                if (v < nv) {
+                    const int64_t p = a4 + 4 * v;
+                    const unsigned long long tb0 = carry + before + lpre[q];
+                    int4 o, f;
+                    o.x = dest(p, msk[q] & 1u, tb0);
+                    o.y = dest(p + 1, (msk[q] >> 1) & 1u, tb0 + __popc(msk[q] & 1u));
+                    o.z = dest(p + 2, (msk[q] >> 2) & 1u, tb0 + __popc(msk[q] & 3u));
+                    o.w = dest(p + 3, (msk[q] >> 3) & 1u, tb0 + __popc(msk[q] & 7u));
+                    f.x = p == a ? 1 : 0;
+                    f.y = f.z = f.w = 0;
+                    __stcs(reinterpret_cast<int4 *>(indices + p), o);
+                    __stcs(reinterpret_cast<int4 *>(flags + p), f);
                 }
             }
+            tot = run;
             carry += tot;
             __syncthreads();
         }
-        // ---- Inj / Bij of chk over [gmn, gmx]
-        const unsigned long long span = (unsigned long long)gmx - (unsigned long long)gmn + 1ull;
-        bool dup = false;
-        bool decided = true;
-        unsigned *bm = span <= smem_bits ? bt_bm : my_gbm;
-        if (span == 0 || span > BT_GLOBAL_BITS) {
-            decided = false;
-        } else {
-            const unsigned long long words = (span + 31) / 32;
-            for (unsigned long long w = threadIdx.x; w < words; w += NT) bm[w] = 0u;
-            __syncthreads();
-            for (int64_t i = a + threadIdx.x; i < b; i += NT) {
-                const unsigned long long r = (unsigned long long)(int64_t)__ldg(chk + i) - (unsigned long long)gmn;
-                const unsigned bit = 1u << (r & 31);
-                if (atomicOr(bm + (r >> 5), bit) & bit) dup = true;
+        if (tid == 0) {  // tail elements, in order
+            unsigned long long cc = carry;
+            for (int64_t i = b4; i < b; i++) {
+                const bool t = bt_pred(pred, keys[i]);
+                indices[i] = dest(i, t, cc);
+                flags[i] = i == a ? 1 : 0;
+                cc += t ? 1u : 0u;
             }
         }
-        const int any_dup = __syncthreads_or(dup);
-        if (threadIdx.x == 0) {
+        (void)ltm;
+        // ---- Inj when some chk value lies outside the segment's image: one more
+        // bitmap pass over [min, max] (rare; decides Inj, Bij has failed already)
+        const int64_t gmn = s_mm[0], gmx = s_mm[1];
+        bool inj_decided = img_fits && !any_out;
+        bool inj_dup = any_dup;
+        if (any_out) {
+            const unsigned long long span = (unsigned long long)gmx - (unsigned long long)gmn + 1ull;
+            if (span != 0 && span <= BT_GLOBAL_BITS) {
+                unsigned *bm2 = span <= smem_bits ? bt_bm : my_gbm;
+                __syncthreads();
+                for (unsigned long long q = tid; q < (span + 31) / 32; q += NT) bm2[q] = 0u;
+                __syncthreads();
+                bool d2 = false;
+                for (int64_t i = a + tid; i < b; i += NT) {
+                    const unsigned long long r = (unsigned long long)(int64_t)__ldg(chk + i) - (unsigned long long)gmn;
+                    const unsigned bit = 1u << (r & 31);
+                    if (atomicOr(bm2 + (r >> 5), bit) & bit) d2 = true;
+                }
+                inj_dup = __syncthreads_or(d2);
+                inj_decided = true;
+            } else {
+                inj_decided = false;
+            }
+        }
+        if (tid == 0) {
             num_true[k] = (int64_t)T;
             const bool mono_ok = !any_mono_bad;
-            const bool inj_ok = decided && !any_dup;
-            const bool bij_ok = inj_ok && gmn >= a && gmx < b;
-            if (!decided) set_status(h, IXP_E_SPAN);
+            const bool inj_ok = inj_decided && !inj_dup;
+            const bool bij_ok = img_fits && !any_out && !any_dup;  // L distinct values inside an L-value image
+            if (!inj_decided || !img_fits) set_status(h, IXP_E_SPAN);
             seg_ok[k] = mono_ok;
             seg_ok[m + k] = inj_ok;
             seg_ok[2 * m + k] = bij_ok;
@@ -267,6 +356,10 @@ extern "C" int ixp_batch_run(const int64_t *shape, int64_t m, const int32_t *key
         t.smem_bits_log2 > 20 || (t.chunk != 4 && t.chunk != 8))
         return IXP_E_INVAL;
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < ixp_batch_workspace_size(&t)) return IXP_E_WORKSPACE;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(chk) |
+                         reinterpret_cast<uintptr_t>(iota) | reinterpret_cast<uintptr_t>(flags) |
+                         reinterpret_cast<uintptr_t>(indices);
+    if (al & 15u) return IXP_E_INVAL;  // the five element arrays must be 16-byte aligned
     cudaStream_t st = (cudaStream_t)stream;
     Hdr *h = (Hdr *)ws;
     unsigned *gbm = (unsigned *)((char *)ws + HDR_BYTES);

@@ -75,15 +75,30 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_kernel(FT *__restr
 }
 
 // Additive scatter of float32 rows into a float64 accumulator. Lanes of a warp
-// that hit the same target are found with match_any; each such group is summed
-// with a masked shuffle tree (in float64) and its lowest lane issues the atomics,
-// so a hot target costs one atomic per warp instead of one per element.
+// that hit the same target are combined first (match_any + a masked shuffle tree in
+// float64). Each block then keeps a direct-mapped cache of HOT_SLOTS target rows in
+// shared memory: a group's leader adds into the cached row when its target owns the
+// slot (claiming a free slot on first use) and falls back to a global float64
+// atomic otherwise; the cache is flushed with one atomic per cached value when the
+// block ends. Hot targets (a Zipf head) thus cost shared-memory atomics instead of
+// serialised global ones.
+constexpr int HOT_SLOTS = 512;
+constexpr int HOT_COLS = 8;  // cached row width; wider rows bypass the cache
+
 template <typename IT>
 __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double *__restrict__ acc, int64_t dst_len,
                                                                          const IT *__restrict__ idx,
                                                                          const float *__restrict__ vals, int64_t n,
                                                                          int row_elems) {
     IXP_KERNEL_ENTRY();
+    __shared__ unsigned long long s_tag[HOT_SLOTS];  // ~0 = free
+    __shared__ double s_row[HOT_SLOTS][HOT_COLS];
+    const bool cache = row_elems <= HOT_COLS;
+    for (int sl = threadIdx.x; sl < HOT_SLOTS; sl += blockDim.x) {
+        s_tag[sl] = ~0ull;
+        for (int c = 0; c < HOT_COLS; c++) s_row[sl][c] = 0.0;
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -93,23 +108,63 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double 
         int64_t d = live ? (int64_t)__ldg(idx + i) : -1;
         if (d < 0 || d >= dst_len) d = -1;
         const unsigned peers = __match_any_sync(FULL, (unsigned long long)d);
+        const int leader = __ffs(peers) - 1;
+        // every lane of a group adds its row into the leader's registers, one column at a time
+        double v[HOT_COLS];
         const bool single = __popc(peers) == 1;
-        if (d >= 0 && single)
-            for (int c = 0; c < row_elems; c++) atomicAdd(acc + d * row_elems + c, (double)vals[i * row_elems + c]);
-        // groups of two or more lanes: one leader per group
         unsigned todo = __ballot_sync(FULL, !single && d >= 0);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            const int64_t key = __shfl_sync(FULL, d, src);
-            const unsigned grp = __ballot_sync(FULL, d == key);
-            todo &= ~grp;
-            for (int c = 0; c < row_elems; c++) {
-                double v = (d == key) ? (double)vals[i * row_elems + c] : 0.0;
+        if (cache) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-                if (lane == src) atomicAdd(acc + key * row_elems + c, v);
+            for (int c = 0; c < HOT_COLS; c++) v[c] = (d >= 0 && c < row_elems) ? (double)vals[i * row_elems + c] : 0.0;
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                const int64_t key = __shfl_sync(FULL, d, src);
+                const unsigned grp = __ballot_sync(FULL, d == key);
+                todo &= ~grp;
+#pragma unroll
+                for (int c = 0; c < HOT_COLS; c++) {
+                    double x = (d == key) ? v[c] : 0.0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+                    if (lane == src) v[c] = x;
+                }
+            }
+            if (d >= 0 && lane == leader) {
+                const int sl = (int)(d % HOT_SLOTS);
+                unsigned long long tag = s_tag[sl];
+                if (tag == ~0ull) {
+                    const unsigned long long prev = atomicCAS(&s_tag[sl], ~0ull, (unsigned long long)d);
+                    tag = prev == ~0ull ? (unsigned long long)d : prev;
+                }
+                if (tag == (unsigned long long)d) {
+                    for (int c = 0; c < row_elems; c++) atomicAdd(&s_row[sl][c], v[c]);
+                } else {
+                    for (int c = 0; c < row_elems; c++) atomicAdd(acc + d * row_elems + c, v[c]);
+                }
+            }
+        } else {
+            if (d >= 0 && single)
+                for (int c = 0; c < row_elems; c++) atomicAdd(acc + d * row_elems + c, (double)vals[i * row_elems + c]);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                const int64_t key = __shfl_sync(FULL, d, src);
+                const unsigned grp = __ballot_sync(FULL, d == key);
+                todo &= ~grp;
+                for (int c = 0; c < row_elems; c++) {
+                    double x = (d == key) ? (double)vals[i * row_elems + c] : 0.0;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+                    if (lane == src) atomicAdd(acc + key * row_elems + c, x);
+                }
             }
         }
+    }
+    if (!cache) return;
+    __syncthreads();
+    for (int e = threadIdx.x; e < HOT_SLOTS * HOT_COLS; e += blockDim.x) {
+        const int sl = e / HOT_COLS, c = e % HOT_COLS;
+        const unsigned long long t = s_tag[sl];
+        if (t != ~0ull && c < row_elems) atomicAdd(acc + (int64_t)t * row_elems + c, s_row[sl][c]);
     }
 }
 
@@ -245,6 +300,38 @@ extern "C" int ixp_f64_to_f32(float *out, const double *acc, int64_t count, ixp_
     if (count < 0 || (count > 0 && (!out || !acc))) return IXP_E_INVAL;
     if (count == 0) return IXP_OK;
     f64_to_f32_kernel<<<stream_grid(count, 4), STREAM_THREADS, 0, (cudaStream_t)stream>>>(out, acc, count);
+    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+template <typename IT, typename OT>
+__global__ void __launch_bounds__(STREAM_THREADS) invert_kernel(const IT *__restrict__ idx, int64_t n,
+                                                                OT *__restrict__ inv, int64_t inv_len) {
+    IXP_KERNEL_ENTRY();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const int64_t j = (int64_t)__ldg(idx + i);
+        if (j >= 0 && j < inv_len) inv[j] = (OT)i;
+    }
+}
+
+extern "C" int ixp_invert(const void *idx, int itype, int64_t n, void *inv, int inv_type, int64_t inv_len,
+                          ixp_stream stream) {
+    if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
+    if (inv_type != IXP_I32 && inv_type != IXP_I64) return IXP_E_DTYPE;
+    if (n < 0 || inv_len < 0 || (n > 0 && !idx) || (inv_len > 0 && !inv)) return IXP_E_INVAL;
+    if (inv_type == IXP_I32 && n > INT32_MAX) return IXP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t eb = inv_type == IXP_I32 ? 4 : 8;
+    if (inv_len > 0 && cudaMemsetAsync(inv, 0xff, (size_t)inv_len * eb, st) != cudaSuccess) return IXP_E_CUDA;
+    if (n == 0) return IXP_OK;
+    const int g = row_grid(n);
+    if (itype == IXP_I32) {
+        if (inv_type == IXP_I32) invert_kernel<int32_t, int32_t><<<g, STREAM_THREADS, 0, st>>>((const int32_t *)idx, n, (int32_t *)inv, inv_len);
+        else invert_kernel<int32_t, int64_t><<<g, STREAM_THREADS, 0, st>>>((const int32_t *)idx, n, (int64_t *)inv, inv_len);
+    } else {
+        if (inv_type == IXP_I32) invert_kernel<int64_t, int32_t><<<g, STREAM_THREADS, 0, st>>>((const int64_t *)idx, n, (int32_t *)inv, inv_len);
+        else invert_kernel<int64_t, int64_t><<<g, STREAM_THREADS, 0, st>>>((const int64_t *)idx, n, (int64_t *)inv, inv_len);
+    }
     return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
 }
 

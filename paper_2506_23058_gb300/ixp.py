@@ -70,6 +70,7 @@ _SIGS = {
     "ixp_scatter_add_f32_to_f64": (_I, [_P, _L, _P, _I, _P, _L, C.c_int32, _P]),
     "ixp_f64_to_f32": (_I, [_P, _P, _L, _P]),
     "ixp_f32_to_f64": (_I, [_P, _P, _L, _P]),
+    "ixp_invert": (_I, [_P, _I, _L, _P, _I, _L, _P]),
     "ixp_gather": (_I, [_P, _P, _L, _P, _I, _L, C.c_int32, C.c_int32, _P, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
@@ -351,6 +352,15 @@ def scatter_add_f64(acc, idx, vals, *, stream=None):
 def f64_to_f32(acc, out=None, *, stream=None):
     out = out if out is not None else torch.empty(acc.shape, dtype=torch.float32, device=acc.device)
     _ck(load().ixp_f64_to_f32(_dev(out, "out"), _dev(acc, "acc"), acc.numel(), _stream(stream)), "f64_to_f32")
+    return out
+
+
+def invert(idx, inv_len, out_dtype=None, *, out=None, stream=None):
+    """inv[idx[i]] = i for in-bounds idx[i] (idx injective), -1 where nothing lands."""
+    out_dtype = out_dtype or idx.dtype
+    out = out if out is not None else torch.empty(inv_len, dtype=out_dtype, device=idx.device)
+    _ck(load().ixp_invert(_dev(idx, "idx"), _itype(idx), idx.numel(), out.data_ptr() if inv_len else None,
+                          _itype(out), inv_len, _stream(stream)), "invert")
     return out
 
 

@@ -47,6 +47,22 @@ def test_gather_injective_backward_is_an_exact_scatter(ag, dev):
     assert np.array_equal(s.grad.cpu().numpy(), ref)
 
 
+def test_gather_backward_through_the_inverse(ag, dev):
+    import paper_2506_23058_gb300 as m
+    n, cols, ns = 40_000, 8, 50_000
+    src = synth.payload_f32(ns, 31, cols=cols)
+    idx = synth.permutation(ns, 32).astype(np.int32)[:n]  # injective, leaves 10000 rows untouched
+    w = synth.payload_f32(n, 33, cols=cols)
+    inv = m.invert(T(idx, dev), ns)
+    ref_inv = np.full(ns, -1, np.int32)
+    ref_inv[idx] = np.arange(n, dtype=np.int32)
+    assert np.array_equal(inv.cpu().numpy(), ref_inv)
+    s = T(src, dev, True)
+    y = ag.gather(s, T(idx, dev), inverse=inv)
+    (y * T(w, dev)).sum().backward()
+    assert np.array_equal(s.grad.cpu().numpy(), oracle.scatter(np.zeros_like(src), idx, w))
+
+
 @pytest.mark.parametrize("it", [np.int32, np.int64])
 def test_gather_zipf_backward_matches_fp64_reference(ag, dev, it):
     n, m, cols = 200_000, 4096, 8
@@ -127,6 +143,9 @@ def test_finite_differences_fp64(ag, dev):
     idx_rep = T(rng.integers(0, 37, size=53).astype(np.int64), dev)
     assert torch.autograd.gradcheck(lambda s: ag.gather(s, idx_inj, injective=True), (src,), **kw)
     assert torch.autograd.gradcheck(lambda s: ag.gather(s, idx_rep), (src,), **kw)
+    import paper_2506_23058_gb300 as m
+    inv = m.invert(idx_inj, 37)
+    assert torch.autograd.gradcheck(lambda s: ag.gather(s, idx_inj, inverse=inv), (src,), **kw)
     vals = T(rng.standard_normal((53, 3)), dev, True)
     assert torch.autograd.gradcheck(lambda d, v: ag.scatter_add(d, idx_rep, v), (src, vals), **kw)
     sidx = T((rng.permutation(45) - 4).astype(np.int64), dev)  # injective, some out of bounds
