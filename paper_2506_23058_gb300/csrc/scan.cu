@@ -666,42 +666,52 @@ struct DPred {
     const uint8_t *flags;
 };
 
-__device__ __forceinline__ bool pred_eval(const DPred &p, int64_t key, int64_t i) {
-    switch (p.kind) {
-        case IXP_P_TRUE: return true;
-        case IXP_P_MOD_EQ: {
-            int64_t r = key % (int64_t)p.a;
-            if (r < 0) r += p.a;
-            return r == p.b;
-        }
-        case IXP_P_LT: return key < p.b;
-        default: return __ldg(p.flags + i) != 0;
-    }
-}
-
-// Loads the V keys of one vector slot (keys may be NULL: zeros).
+// Predicate over the V keys of one vector slot at positions p0..p0+V-1, as a
+// V-bit mask (positions at or past n are 0). The kind is tested once per slot and
+// 32-bit keys are compared in 32-bit arithmetic: a bound outside the int32 range
+// makes LT constant, and MOD_EQ (a > 0, result in [0, a)) runs as a 32-bit
+// remainder.
 template <typename KT, int V>
-__device__ __forceinline__ void load_keys(const KT *keys, int64_t p0, int64_t n, int vec_ok, int64_t (&kv)[V]) {
-    if (!keys) {
+__device__ __forceinline__ unsigned pred_mask(const DPred &p, const KT (&kv)[V], int64_t p0, int64_t n) {
+    const unsigned valid = p0 + V <= n ? (1u << V) - 1u : (p0 >= n ? 0u : (1u << (unsigned)(n - p0)) - 1u);
+    unsigned m = 0;
+    switch (p.kind) {
+        case IXP_P_TRUE: return valid;
+        case IXP_P_LT:
+            if (sizeof(KT) == 4) {
+                if (p.b > (long long)INT32_MAX) return valid;
+                if (p.b <= (long long)INT32_MIN) return 0u;
+                const int32_t b = (int32_t)p.b;
 #pragma unroll
-        for (int k = 0; k < V; k++) kv[k] = 0;
-        return;
-    }
-    if (vec_ok && p0 + V <= n) {
-        if (sizeof(KT) == 4) {
-            int4 v = __ldcs(reinterpret_cast<const int4 *>(keys + p0));
-            kv[0] = v.x;
-            kv[1 % V] = v.y;
-            kv[2 % V] = v.z;
-            kv[3 % V] = v.w;
-        } else {
-            longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(keys + p0));
-            kv[0] = v.x;
-            kv[1 % V] = v.y;
-        }
-    } else {
+                for (int k = 0; k < V; k++) m |= (unsigned)((int32_t)kv[k] < b) << k;
+            } else {
 #pragma unroll
-        for (int k = 0; k < V; k++) kv[k] = (p0 + k < n) ? (int64_t)keys[p0 + k] : 0;
+                for (int k = 0; k < V; k++) m |= (unsigned)((int64_t)kv[k] < p.b) << k;
+            }
+            return m & valid;
+        case IXP_P_MOD_EQ:
+            if (p.b < 0 || p.b >= (long long)p.a) return 0u;
+            if (sizeof(KT) == 4) {
+                const int32_t a = p.a, b = (int32_t)p.b;
+#pragma unroll
+                for (int k = 0; k < V; k++) {
+                    int32_t r = (int32_t)kv[k] % a;
+                    r += r < 0 ? a : 0;
+                    m |= (unsigned)(r == b) << k;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < V; k++) {
+                    int64_t r = (int64_t)kv[k] % (int64_t)p.a;
+                    r += r < 0 ? (int64_t)p.a : 0;
+                    m |= (unsigned)(r == p.b) << k;
+                }
+            }
+            return m & valid;
+        default:
+#pragma unroll
+            for (int k = 0; k < V; k++) m |= (unsigned)(p0 + k < n && __ldg(p.flags + p0 + k) != 0) << k;
+            return m;
     }
 }
 
@@ -745,6 +755,17 @@ __device__ __forceinline__ void load_vec(const T *p, int64_t p0, int64_t n, int 
     for (int k = 0; k < V; k++) o[k] = (p0 + k < n) ? p[p0 + k] : (T)0;
 }
 
+// Keys of one vector slot in their own type (keys may be NULL: zeros).
+template <typename KT, int V>
+__device__ __forceinline__ void load_slot(const KT *keys, int64_t p0, int64_t n, int vec_ok, KT (&kv)[V]) {
+    if (keys) {
+        load_vec<KT, V>(keys, p0, n, vec_ok, kv);
+    } else {
+#pragma unroll
+        for (int k = 0; k < V; k++) kv[k] = (KT)0;
+    }
+}
+
 // In-tile exclusive counts. Inputs: per sub-chunk u, V-bit masks kt (kept and
 // true) and kk (kept). Output: per u, the packed exclusive count (kk << 16 | kt)
 // of the elements before this thread's vector in the tile, and the tile total.
@@ -784,73 +805,127 @@ __device__ __forceinline__ unsigned long long widen(unsigned packed) {
     return (unsigned long long)(packed & 0xffffu) | ((unsigned long long)(packed >> 16) << 32);
 }
 
-// Pass 1: per-tile counts -> look-back -> exclusive tile prefixes (packed
-// kept << 32 | kept_true), the grand total in h->total, and the prefix at every
-// segment start in seg_cnt[k] (k = 0..nseg).
+// Pass 1a: per-tile counts, streaming (no inter-tile dependency). Tile t writes its
+// packed count (kept << 32 | kept_true) to tile_prefix[t]; with segments, every
+// segment start off[k] inside the tile gets the in-tile exclusive count before it
+// in seg_cnt[k] (the tile's prefix is added by seg_fix_kernel once it is known).
 template <typename KT, bool SEG>
-__global__ void __launch_bounds__(TB, 4) count_kernel(const KT *__restrict__ keys, int64_t n, DPred filt, DPred part,
-                                                   const int64_t *__restrict__ off, int64_t nseg, Lookback L,
+__global__ void __launch_bounds__(TB, 6) count_kernel(const KT *__restrict__ keys, int64_t n, DPred filt, DPred part,
+                                                   const int64_t *__restrict__ off, int64_t nseg,
                                                    unsigned long long *tile_prefix, unsigned long long *seg_cnt,
-                                                   Hdr *h, Wait wt, int vec_ok) {
+                                                   int vec_ok) {
     IXP_KERNEL_ENTRY();
     constexpr int V = 16 / sizeof(KT);
     constexpr int TILE = TB * SUB * V;
-    __shared__ int64_t s_tile, s_k;
+    __shared__ int64_t s_k;
     __shared__ unsigned s_w[TB / 32];
-    __shared__ unsigned s_cnt[SEG ? TILE + 1 : 1];
-    __shared__ unsigned long long s_pre;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&h->tile_ctr, 1u);
-    __syncthreads();
-    const int64_t t = s_tile;
+    __shared__ unsigned s_cnt[SEG ? TILE : 1];
+    const int64_t t = blockIdx.x;
     const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     unsigned kt[SUB], kk[SUB];
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
         const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
-        int64_t kv[V];
-        load_keys<KT, V>(keys, p0, n, vec_ok, kv);
-        kt[u] = kk[u] = 0;
+        KT kv[V];
+        load_slot<KT, V>(keys, p0, n, vec_ok, kv);
+        kk[u] = pred_mask<KT, V>(filt, kv, p0, n);
+        kt[u] = kk[u] & pred_mask<KT, V>(part, kv, p0, n);
+    }
+    if (!SEG) {
+        unsigned x = 0;
 #pragma unroll
-        for (int k = 0; k < V; k++) {
-            if (p0 + k < n && pred_eval(filt, kv[k], p0 + k)) {
-                kk[u] |= 1u << k;
-                if (pred_eval(part, kv[k], p0 + k)) kt[u] |= 1u << k;
-            }
+        for (int u = 0; u < SUB; u++) x += (unsigned)__popc(kt[u]) | ((unsigned)__popc(kk[u]) << 16);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        if (l == 0) s_w[w] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned tot = 0;
+#pragma unroll
+            for (int i = 0; i < TB / 32; i++) tot += s_w[i];
+            tile_prefix[t] = widen(tot);
         }
+        return;
     }
     unsigned pre[SUB];
     const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
-    if (w == 0) {
-        const unsigned long long ex = lookback_sum(L, t, widen(tot), h, wt);
-        if (l == 0) {
-            tile_prefix[t] = ex;
-            s_pre = ex;
-            if (t1 == n) h->total = ex + widen(tot);
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int r0 = ((w * SUB + u) * 32 + l) * V;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            unsigned below = (1u << k) - 1u;
+            s_cnt[r0 + k] = pre[u] + (unsigned)__popc(kt[u] & below) + ((unsigned)__popc(kk[u] & below) << 16);
         }
     }
-    if (SEG) {
+    if (threadIdx.x == 0) {
+        tile_prefix[t] = widen(tot);
+        s_k = lb_off(off, nseg, t0);
+    }
+    __syncthreads();
+    for (int64_t k = s_k + threadIdx.x; k <= nseg; k += blockDim.x) {
+        const int64_t o = __ldg(off + k);
+        if (o >= t1) break;
+        if (o >= t0) seg_cnt[k] = widen(s_cnt[o - t0]);
+    }
+}
+
+// Pass 1b: exclusive scan of the packed tile counts in place (one block), grand
+// total to h->total.
+constexpr int TS_NT = 1024;
+constexpr int TS_PER = 8;
+__global__ void __launch_bounds__(TS_NT) tile_scan_kernel(unsigned long long *tp, int64_t nt, Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    __shared__ unsigned long long s_w[TS_NT / 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned long long carry = 0;
+    for (int64_t base = 0; base < nt; base += (int64_t)TS_NT * TS_PER) {
+        const int64_t p0 = base + (int64_t)threadIdx.x * TS_PER;
+        unsigned long long v[TS_PER], x = 0;
 #pragma unroll
-        for (int u = 0; u < SUB; u++) {
-            const int r0 = ((w * SUB + u) * 32 + l) * V;
+        for (int j = 0; j < TS_PER; j++) {
+            v[j] = p0 + j < nt ? tp[p0 + j] : 0ull;
+            x += v[j];
+        }
+        unsigned long long y = x;
 #pragma unroll
-            for (int k = 0; k < V; k++) {
-                unsigned below = (1u << k) - 1u;
-                s_cnt[r0 + k] = pre[u] + (unsigned)__popc(kt[u] & below) + ((unsigned)__popc(kk[u] & below) << 16);
-            }
+        for (int d = 1; d < 32; d <<= 1) {
+            unsigned long long o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y += o;
         }
-        if (threadIdx.x == 0) {
-            s_cnt[TILE] = tot;
-            s_k = lb_off(off, nseg, t0);
-        }
+        if (l == 31) s_w[w] = y;
         __syncthreads();
-        const unsigned long long base = s_pre;
-        const int64_t hi = (t1 == n) ? n : t1 - 1;  // the last tile also owns position n
-        for (int64_t k = s_k + threadIdx.x; k <= nseg; k += blockDim.x) {
-            int64_t o = __ldg(off + k);
-            if (o > hi) break;
-            if (o >= t0) seg_cnt[k] = base + widen(s_cnt[(o - t0) < TILE ? (o - t0) : TILE]);
+        unsigned long long wpre = 0, tot = 0;
+#pragma unroll 4
+        for (int i = 0; i < TS_NT / 32; i++) {
+            const unsigned long long c = s_w[i];
+            wpre += i < w ? c : 0ull;
+            tot += c;
         }
+        unsigned long long run = carry + wpre + y - x;
+#pragma unroll
+        for (int j = 0; j < TS_PER; j++) {
+            if (p0 + j < nt) tp[p0 + j] = run;
+            run += v[j];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) h->total = carry;
+}
+
+// Pass 1c: seg_cnt[k] = packed count before off[k] (tile prefix + in-tile part);
+// off[k] = n maps to the total. Offsets outside [0, n] leave seg_cnt[k] without
+// meaning but in bounds.
+template <int TILE>
+__global__ void seg_fix_kernel(const int64_t *__restrict__ off, int64_t nseg, int64_t n,
+                               const unsigned long long *__restrict__ tp, unsigned long long *seg_cnt, const Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= nseg; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = __ldg(off + k);
+        if (o >= n || o < 0) seg_cnt[k] = h->total;
+        else seg_cnt[k] += __ldg(tp + o / TILE);
     }
 }
 
@@ -923,19 +998,14 @@ __global__ void __launch_bounds__(TB) partition_write_kernel(
     const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     unsigned kt[SUB], kk[SUB];
-    int64_t kv[SUB][V];
+    KT kv[SUB][V];
+    const DPred all{IXP_P_TRUE, 0, 0, nullptr};
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
         const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
-        load_keys<KT, V>(keys, p0, n, vec_ok, kv[u]);
-        kt[u] = kk[u] = 0;
-#pragma unroll
-        for (int k = 0; k < V; k++) {
-            if (p0 + k < n) {
-                kk[u] |= 1u << k;
-                if (pred_eval(pred, kv[u][k], p0 + k)) kt[u] |= 1u << k;
-            }
-        }
+        load_slot<KT, V>(keys, p0, n, vec_ok, kv[u]);
+        kk[u] = pred_mask<KT, V>(all, kv[u], p0, n);
+        kt[u] = pred_mask<KT, V>(pred, kv[u], p0, n);
     }
     unsigned pre[SUB];
     tile_counts<V>(kt, kk, pre, s_w);
@@ -967,7 +1037,7 @@ __global__ void __launch_bounds__(TB) partition_write_kernel(
             }
             dst[k] = (OT)d;
             if (i < n && d >= 0 && d < n) {  // d is outside [0, n) only for invalid offsets
-                if (out_keys) out_keys[d] = (KT)kv[u][k];
+                if (out_keys) out_keys[d] = kv[u][k];
                 if (out_payload)
                     for (int c2 = 0; c2 < row_words; c2++) out_payload[d * row_words + c2] = payload[i * row_words + c2];
             }
@@ -1020,19 +1090,10 @@ __global__ void __launch_bounds__(TB, 4) partition_flat_kernel(
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
         const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
-        if (keys) load_vec<KT, V>(keys, p0, n, vec_ok, kv[u]);
-        else {
-#pragma unroll
-            for (int k = 0; k < V; k++) kv[u][k] = (KT)0;
-        }
-        kt[u] = kk[u] = 0;
-#pragma unroll
-        for (int k = 0; k < V; k++) {
-            if (p0 + k < n) {
-                kk[u] |= 1u << k;
-                if (pred_eval(pred, (int64_t)kv[u][k], p0 + k)) kt[u] |= 1u << k;
-            }
-        }
+        load_slot<KT, V>(keys, p0, n, vec_ok, kv[u]);
+        const DPred all{IXP_P_TRUE, 0, 0, nullptr};
+        kk[u] = pred_mask<KT, V>(all, kv[u], p0, n);
+        kt[u] = pred_mask<KT, V>(pred, kv[u], p0, n);
     }
     unsigned pre[SUB];
     const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
@@ -1103,108 +1164,107 @@ __global__ void __launch_bounds__(TB, 4) partition_flat_kernel(
     }
 }
 
-// Flat InvFiltPart check in one pass (8 bytes per int32 element when it holds).
-// The kept/kept-true counts before each element come from the look-back. A kept
-// true element must hold exactly its rank; for kept false elements the quantity
-// Z[i] - (kept falses before i) must equal T (the total of kept trues), which is
-// only known at the end, so its minimum and maximum are reduced; a dropped element
-// must lie outside [0, N), so the smallest non-negative dropped Z is reduced. When
-// anything fails, an exact second pass finds the first wrong index.
+// Flat InvFiltPart check, streaming pass over Z and the keys (8 bytes per int32
+// element). A kept true element at in-tile true rank r must hold P_t + r, where
+// P_t is the count of kept trues before the tile; a kept false at in-tile false
+// rank r must hold T + F_t + r (T the total of kept trues, F_t the kept falses
+// before the tile). Neither P_t, F_t nor T is known yet, so each tile records
+// whether Z - r is one constant over its kept trues (and over its kept falses) and
+// which: rec[t] = {true constant, false constant}, with FP_NONE for no such element
+// and FP_BAD when they differ or a value is below its rank. A dropped element must
+// lie outside [0, N), so the smallest non-negative dropped Z goes to h->k_first2.
+// The packed tile count goes to tile_prefix[t] for the scan that follows.
+constexpr long long FP_NONE = -1, FP_BAD = -2;
+
+__device__ __forceinline__ void fp_fold(int64_t &mn, int64_t &mx, int64_t zi, int64_t r) {
+    const int64_t q = zi < r ? (int64_t)INT64_MIN : zi - r;
+    mn = q < mn ? q : mn;
+    mx = q > mx ? q : mx;
+}
+
+__device__ __forceinline__ long long fp_rec(int64_t mn, int64_t mx) {
+    if (mn > mx) return FP_NONE;
+    return (mn == mx && mn >= 0) ? (long long)mn : FP_BAD;
+}
+
 template <typename KT, typename ZT>
-__global__ void __launch_bounds__(TB, 4) filtpart_fast_kernel(const ZT *__restrict__ z, int64_t n,
+__global__ void __launch_bounds__(TB, sizeof(ZT) > sizeof(KT) ? 3 : 4) filtpart_tile_kernel(const ZT *__restrict__ z, int64_t n,
                                                               const KT *__restrict__ keys, DPred filt, DPred part,
-                                                              Lookback L, unsigned long long *tile_prefix, Hdr *h,
-                                                              Wait wt, int vec_ok) {
+                                                              unsigned long long *tile_prefix, longlong2 *rec, Hdr *h,
+                                                              int vec_ok) {
     IXP_KERNEL_ENTRY();
     constexpr int V = 16 / sizeof(KT);
     constexpr int TILE = TB * SUB * V;
-    __shared__ int64_t s_tile;
     __shared__ unsigned s_w[TB / 32];
-    __shared__ unsigned long long s_pre;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&h->tile_ctr, 1u);
-    __syncthreads();
-    const int64_t t = s_tile;
-    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    __shared__ unsigned long long s_r[5][TB / 32];
+    const int64_t t = blockIdx.x;
+    const int64_t t0 = t * TILE;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     unsigned kt[SUB], kk[SUB];
     ZT zv[SUB][V];
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
         const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
-        int64_t kv[V];
-        load_keys<KT, V>(keys, p0, n, vec_ok, kv);
+        KT kv[V];
+        load_slot<KT, V>(keys, p0, n, vec_ok, kv);
         load_vec<ZT, V>(z, p0, n, vec_ok, zv[u]);
-        kt[u] = kk[u] = 0;
-#pragma unroll
-        for (int k = 0; k < V; k++) {
-            if (p0 + k < n && pred_eval(filt, kv[k], p0 + k)) {
-                kk[u] |= 1u << k;
-                if (pred_eval(part, kv[k], p0 + k)) kt[u] |= 1u << k;
-            }
-        }
+        kk[u] = pred_mask<KT, V>(filt, kv, p0, n);
+        kt[u] = kk[u] & pred_mask<KT, V>(part, kv, p0, n);
     }
     unsigned pre[SUB];
     const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
-    if (w == 0) {
-        const unsigned long long ex = lookback_sum(L, t, widen(tot), h, wt);
-        if (l == 0) {
-            tile_prefix[t] = ex;
-            s_pre = ex;
-            if (t1 == n) h->total = ex + widen(tot);
-        }
-    }
-    __syncthreads();
-    const int64_t ct0 = (int64_t)(s_pre & 0xffffffffull), ck0 = (int64_t)(s_pre >> 32);
-    int64_t bad = INT64_MAX, qmin = INT64_MAX, qmax = INT64_MIN, dmin = INT64_MAX;
+    int64_t tmn = INT64_MAX, tmx = INT64_MIN, fmn = INT64_MAX, fmx = INT64_MIN, dmin = INT64_MAX;
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
         const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
 #pragma unroll
         for (int k = 0; k < V; k++) {
-            const int64_t i = p0 + k;
-            if (i >= n) continue;
+            if (p0 + k >= n) continue;
             const unsigned below = (1u << k) - 1u;
-            const int64_t ct = ct0 + (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & below);
-            const int64_t ck = ck0 + (int64_t)(pre[u] >> 16) + __popc(kk[u] & below);
+            const int64_t rt = (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & below);
+            const int64_t rk = (int64_t)(pre[u] >> 16) + __popc(kk[u] & below);
             const int64_t zi = (int64_t)zv[u][k];
             if ((kk[u] >> k) & 1u) {
-                if ((kt[u] >> k) & 1u) {
-                    if (zi != ct) bad = i < bad ? i : bad;
-                } else {
-                    const int64_t q = zi - (ck - ct);
-                    qmin = q < qmin ? q : qmin;
-                    qmax = q > qmax ? q : qmax;
-                }
+                if ((kt[u] >> k) & 1u) fp_fold(tmn, tmx, zi, rt);
+                else fp_fold(fmn, fmx, zi, rk - rt);
             } else if (zi >= 0) {
                 dmin = zi < dmin ? zi : dmin;
             }
         }
     }
-    __shared__ unsigned long long sm[TB / 32];
-    unsigned long long r = block_max_u64(bad == INT64_MAX ? 0ull : enc_first(bad), sm);
-    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
-    r = block_max_u64(enc_min(qmin), sm);
-    if (threadIdx.x == 0) atomic_max_u64(&h->k_min, r);
-    r = block_max_u64(enc_max(qmax), sm);
-    if (threadIdx.x == 0) atomic_max_u64(&h->k_max, r);
-    r = block_max_u64(enc_min(dmin), sm);
-    if (threadIdx.x == 0) atomic_max_u64(&h->k_first2, r);
+    unsigned long long r[5] = {enc_min(tmn), enc_max(tmx), enc_min(fmn), enc_max(fmx), enc_min(dmin)};
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        r[j] = warp_max_u64(r[j]);
+        if (l == 0) s_r[j][w] = r[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < 5; j++)
+            for (int i = 1; i < TB / 32; i++) r[j] = s_r[j][i] > r[j] ? s_r[j][i] : r[j];
+        tile_prefix[t] = widen(tot);
+        rec[t] = make_longlong2(fp_rec(dec_min(r[0]), dec_max(r[1])), fp_rec(dec_min(r[2]), dec_max(r[3])));
+        atomic_max_u64(&h->k_first2, r[4]);
+    }
 }
 
-// Decides whether the one-pass result proves the property; if not, clears the
-// candidate index and raises the flag that enables the exact pass.
-__global__ void filtpart_decide_kernel(Hdr *h) {
+// After the tile scan: a tile passes when its recorded constants are P_t and
+// T + F_t; any failing tile, or a dropped Z inside [0, N), raises the flag that
+// enables the exact pass.
+__global__ void filtpart_decide_kernel(const unsigned long long *__restrict__ tp, const longlong2 *__restrict__ rec,
+                                       int64_t nt, Hdr *h) {
     IXP_KERNEL_ENTRY();
-    if (h->status) return;
     const int64_t T = (int64_t)(h->total & 0xffffffffull), N = (int64_t)(h->total >> 32);
-    const bool has_false = h->k_max != 0;  // enc_max(INT64_MIN) == 0 means no kept false element
-    const int64_t qmin = dec_min(h->k_min), qmax = dec_max(h->k_max);
-    const int64_t dmin = dec_min(h->k_first2);
-    const bool ok = h->k_first == 0 && (!has_false || (qmin == T && qmax == T)) && dmin >= N;
-    if (!ok) {
-        h->k_first = 0;
-        h->flag = 1u;
+    bool bad = false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) bad = dec_min(h->k_first2) < N;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt; t += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long p = __ldg(tp + t);
+        const int64_t ct = (int64_t)(p & 0xffffffffull), cf = (int64_t)(p >> 32) - ct;
+        const longlong2 r = rec[t];
+        bad |= (r.x != FP_NONE && r.x != ct) || (r.y != FP_NONE && r.y != T + cf);
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) h->flag = 1u;
 }
 
 __global__ void num_true_kernel(const unsigned long long *seg_cnt, const Hdr *h, int64_t nseg, int64_t *num_true) {
@@ -1245,16 +1305,10 @@ __global__ void __launch_bounds__(TB, 4) filtpart_cmp_kernel(
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
         const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
-        int64_t kv[V];
-        load_keys<KT, V>(keys, p0, n, vec_ok, kv);
-        kt[u] = kk[u] = 0;
-#pragma unroll
-        for (int k = 0; k < V; k++) {
-            if (p0 + k < n && pred_eval(filt, kv[k], p0 + k)) {
-                kk[u] |= 1u << k;
-                if (pred_eval(part, kv[k], p0 + k)) kt[u] |= 1u << k;
-            }
-        }
+        KT kv[V];
+        load_slot<KT, V>(keys, p0, n, vec_ok, kv);
+        kk[u] = pred_mask<KT, V>(filt, kv, p0, n);
+        kt[u] = kk[u] & pred_mask<KT, V>(part, kv, p0, n);
     }
     unsigned pre[SUB];
     tile_counts<V>(kt, kk, pre, s_w);
@@ -1438,18 +1492,21 @@ static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs se
 template <typename KT>
 static int run_counts(const KT *keys, int64_t n, DPred filt, DPred part, ixp_segs segs, TileWs &W, int64_t nt,
                       int vec, cudaStream_t st) {
+    constexpr int V = 16 / sizeof(KT);
     const bool seg = segs.offsets != nullptr;
     if (cudaMemsetAsync(W.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
-    if (nt > 0 && cudaMemsetAsync(W.L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;
-    if (seg && cudaMemsetAsync(W.seg_cnt, 0, (size_t)(segs.nseg + 1) * 8, st) != cudaSuccess) return IXP_E_CUDA;
-    const Wait wt = wait_config();
     if (nt > 0) {
         if (seg)
-            count_kernel<KT, true><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, segs.offsets, segs.nseg, W.L,
-                                                               W.tile_prefix, W.seg_cnt, W.h, wt, vec);
+            count_kernel<KT, true><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, segs.offsets, segs.nseg,
+                                                               W.tile_prefix, W.seg_cnt, vec);
         else
-            count_kernel<KT, false><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, nullptr, 0, W.L, W.tile_prefix,
-                                                                nullptr, W.h, wt, vec);
+            count_kernel<KT, false><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, nullptr, 0, W.tile_prefix,
+                                                                nullptr, vec);
+    }
+    tile_scan_kernel<<<1, TS_NT, 0, st>>>(W.tile_prefix, nt, W.h);
+    if (seg) {
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>((segs.nseg + 256) / 256, 4096));
+        seg_fix_kernel<TB * SUB * V><<<g, 256, 0, st>>>(segs.offsets, segs.nseg, n, W.tile_prefix, W.seg_cnt, W.h);
     }
     return IXP_OK;
 }
@@ -1502,11 +1559,13 @@ static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, i
     const int vec = keys == nullptr || aligned16(keys);
     if (!seg) {
         if (cudaMemsetAsync(W.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
-        if (nt > 0 && cudaMemsetAsync(W.L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;
         if (nt > 0) {
-            filtpart_fast_kernel<KT, ZT><<<(unsigned)nt, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), W.L,
-                                                                     W.tile_prefix, W.h, wait_config(), vec);
-            filtpart_decide_kernel<<<1, 1, 0, st>>>(W.h);
+            longlong2 *rec = reinterpret_cast<longlong2 *>(W.L.st);
+            filtpart_tile_kernel<KT, ZT><<<(unsigned)nt, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part),
+                                                                     W.tile_prefix, rec, W.h, vec);
+            tile_scan_kernel<<<1, TS_NT, 0, st>>>(W.tile_prefix, nt, W.h);
+            const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 1024));
+            filtpart_decide_kernel<<<g, 256, 0, st>>>(W.tile_prefix, rec, nt, W.h);
             filtpart_cmp_kernel<KT, ZT, false><<<(unsigned)nt, TB, 0, st>>>(
                 z, n, keys, dpred(filt), dpred(part), nullptr, 0, W.tile_prefix, nullptr, W.h, vec, 0, 1);
             filtpart_cmp_kernel<KT, ZT, false><<<1, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), nullptr, 0,

@@ -377,7 +377,9 @@ def test_scan_timeout_is_reported(ixp, dev, offset):
     assert st.item() == 0 and int(tot.item()) == n
 
 
-PREDS = [("mod_eq", 3, 0), ("lt", 0, 0), ("lt", 0, synth.bernoulli_threshold(0.01)), ("mod_eq", 5, 2)]
+PREDS = [("mod_eq", 3, 0), ("lt", 0, 0), ("lt", 0, synth.bernoulli_threshold(0.01)), ("mod_eq", 5, 2),
+         ("lt", 0, (1 << 31) + 5), ("lt", 0, -(1 << 31) - 7), ("lt", 0, -(1 << 31) + 1), ("mod_eq", 4, 7),
+         ("mod_eq", 7, 6), ("mod_eq", 1, 0), ("mod_eq", 3, -1)]
 
 
 @pytest.mark.parametrize("kt", [np.int32, np.int64])
@@ -441,6 +443,41 @@ def test_filtpart(ixp, dev, n, zt):
     for name, zz in cases.items():
         same(ixp.check_filtpart(T(zz, dev), T(keys, dev), part=part), oracle.check_filtpart(zz, keys, part=part),
              (name, n))
+
+
+@pytest.mark.parametrize("zt", [np.int32, np.int64])
+@pytest.mark.parametrize("n", [4097, 300001])
+def test_filtpart_flat_with_filter(ixp, dev, n, zt):
+    """Flat InvFiltPart with a filter, over many tiles: planted faults that keep
+    every tile's Z - rank constant (a whole tile shifted), a dropped Z inside
+    [0, N), negative and extreme values."""
+    rng = np.random.default_rng(n + 11)
+    keys = synth.keys_uniform(n, 900 + n).astype(np.int64)
+    flags = synth.flags_bernoulli(n, 901 + n, 0.6)
+    fl_o, fl_g = ("flags", 0, 0, flags), ("flags", 0, 0, T(flags, dev))
+    part = ("lt", 0, synth.bernoulli_threshold(0.4))
+    kept = flags != 0
+    tru = kept & (keys < part[2])
+    N, Tn = int(kept.sum()), int(tru.sum())
+    z = np.full(n, -1, np.int64)
+    z[np.flatnonzero(tru)] = np.arange(Tn)
+    z[np.flatnonzero(kept & ~tru)] = Tn + np.arange(N - Tn)
+    tile = 2048  # elements per tile for int64 keys
+    cases = {"ok": z.copy()}
+    s = z.copy(); s[~kept] = N + 3; cases["dropped_above"] = s
+    s = z.copy(); s[np.flatnonzero(~kept)[len(np.flatnonzero(~kept)) // 2]] = 0; cases["dropped_inside"] = s
+    sel = np.zeros(n, bool); sel[tile:2 * tile] = True
+    s = z.copy(); s[sel & tru] += 1; cases["tile_true_shift"] = s
+    s = z.copy(); s[sel & kept & ~tru] -= 1; cases["tile_false_shift"] = s
+    s = z.copy(); s[np.flatnonzero(tru)[-1]] = -5; cases["true_negative"] = s
+    s = z.copy(); s[np.flatnonzero(kept & ~tru)[0]] = np.iinfo(zt).min; cases["false_min"] = s
+    s = z.copy(); s[np.flatnonzero(tru)[0]] = np.iinfo(zt).max; cases["true_max"] = s
+    a, b = np.flatnonzero(kept)[[3, 10]]
+    s = z.copy(); s[a], s[b] = s[b], s[a]; cases["swap"] = s
+    for name, zz in cases.items():
+        zz = zz.astype(zt)
+        same(ixp.check_filtpart(T(zz, dev), T(keys, dev), filt=fl_g, part=part),
+             oracle.check_filtpart(zz, keys, filt=fl_o, part=part), (name, n))
 
 
 @pytest.mark.parametrize("n,m", [(100, 1), (5000, 40), (70000, 30000)])
