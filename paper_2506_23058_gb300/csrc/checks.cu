@@ -275,7 +275,6 @@ __global__ void mono_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
 constexpr int BK_TILE = 8192;
 constexpr int BK_THREADS = 256;
 constexpr unsigned BK_MAX = 4096;
-constexpr unsigned BK_INVALID = 0xffffffffu;
 
 // Min/max of the in-codomain values (needed when Rcd is unbounded).
 template <typename T>
@@ -674,41 +673,56 @@ __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, u
     for (unsigned long long w = tid; w < BK_MAX / 32; w += stride) bucket_mask[w] = 0u;
 }
 
+// Pass 1: each block takes tiles of BK_TILE elements. An element whose value lies
+// in [base, base + span) (the bitmap's range: Img for Bij, the fixed Rcd or the
+// observed [min, max] for Inj) has rel = value - base, bucket rel >> lw and offset
+// rel & (W - 1). The tile is counting-sorted by bucket in shared memory (the rank
+// within the bucket comes from the counting atomic itself) and written to the
+// per-bucket pools as contiguous runs; entries past a bucket's capacity go to the
+// global bitmap through L2 atomics instead. For Bij, elements of Rcd outside Img
+// give the first such index (k_first).
+constexpr int BS_THREADS = 512;
+constexpr int BS_PER = BK_TILE / BS_THREADS;  // elements per thread per tile
+
+__host__ __device__ constexpr size_t bs_smem_bytes(unsigned bmax) {
+    return (size_t)bmax * (8 + 4 + 4 + 4) + (size_t)BK_TILE * 4;
+}
+
 template <typename T, bool BIJ>
-__global__ void __launch_bounds__(BK_THREADS, 2) bucket_scatter_kernel(
-    const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, int64_t mlo, int64_t mhi, Hdr *h, BucketCfg cfg,
+__global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
+    const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, Hdr *h, BucketCfg cfg,
     unsigned *__restrict__ cursors, unsigned *__restrict__ pool, unsigned *__restrict__ marks,
     unsigned *__restrict__ dup, unsigned *__restrict__ bucket_mask, int vec_ok) {
     IXP_KERNEL_ENTRY();
     if (h->status) return;
     constexpr int V = Vec<T>::N;
-    constexpr int NV = BK_TILE / V / BK_THREADS;  // 16-byte vectors per thread per tile
-    extern __shared__ unsigned bk_smem[];
-    unsigned *s_sorted = bk_smem;              // BK_TILE
-    unsigned *s_cnt = s_sorted + BK_TILE;      // bmax
-    unsigned *s_start = s_cnt + cfg.bmax;      // bmax
-    unsigned *s_gpos = s_start + cfg.bmax;     // bmax
-    __shared__ unsigned s_wsum[BK_THREADS / 32];
+    constexpr int NV = BS_PER / V;  // 16-byte vectors per thread per tile
+    extern __shared__ __align__(16) unsigned char bk_raw[];
+    long long *s_dst = reinterpret_cast<long long *>(bk_raw);  // bmax: pool index of tile slot 0 for bucket b
+    unsigned *s_sorted = reinterpret_cast<unsigned *>(s_dst + cfg.bmax);  // BK_TILE
+    unsigned *s_cnt = s_sorted + BK_TILE;                                  // bmax
+    unsigned *s_start = s_cnt + cfg.bmax;                                  // bmax
+    unsigned *s_lim = s_start + cfg.bmax;                                  // bmax: slots below fit the pool
+    __shared__ unsigned s_wsum[BS_THREADS / 32];
     __shared__ unsigned s_total;
     const unsigned long long base = h->base, span = h->span;
     const unsigned nb = (unsigned)h->spare[0];
     const unsigned long long cap = h->spare[1];
     const unsigned lw = cfg.lw;
-    const unsigned long long wmask = (1ull << lw) - 1ull;
+    const unsigned wmask = (1u << lw) - 1u;
     const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned long long valid = 0;  // kept by thread 0 only
     unsigned anydup = 0;
     int64_t ooi = INT64_MAX;
-    const unsigned per = (nb + BK_THREADS - 1) / BK_THREADS;  // bucket-count scan entries per thread
+    const unsigned per = (nb + BS_THREADS - 1) / BS_THREADS;  // bucket-count scan entries per thread
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t t0 = tile * BK_TILE;
-        for (unsigned b = tid; b < nb; b += BK_THREADS) s_cnt[b] = 0u;
-        // A: all loads first, then classify into (bucket << lw | offset), kept in registers
+        for (unsigned b = tid; b < nb; b += BS_THREADS) s_cnt[b] = 0u;
         T e[NV][V];
 #pragma unroll
         for (int j = 0; j < NV; j++) {
-            const int64_t p0 = t0 + (int64_t)(j * BK_THREADS + tid) * V;
+            const int64_t p0 = t0 + (int64_t)(j * BS_THREADS + tid) * V;
             if (vec_ok && p0 + V <= n) {
                 if (V == 4) {
                     int4 v = __ldcs(reinterpret_cast<const int4 *>(x + p0));
@@ -727,31 +741,29 @@ __global__ void __launch_bounds__(BK_THREADS, 2) bucket_scatter_kernel(
             }
         }
         __syncthreads();  // s_cnt zeroed
-        unsigned st[NV][V];
+        unsigned rv[BS_PER], rk[BS_PER], vm = 0;
 #pragma unroll
         for (int j = 0; j < NV; j++) {
-            const int64_t p0 = t0 + (int64_t)(j * BK_THREADS + tid) * V;
+            const int64_t p0 = t0 + (int64_t)(j * BS_THREADS + tid) * V;
 #pragma unroll
             for (int c = 0; c < V; c++) {
+                const int q = j * V + c;
                 const int64_t xi = (int64_t)e[j][c];
-                unsigned sv = BK_INVALID;
-                if (p0 + c < n && xi >= rlo && xi <= rhi) {
-                    if (BIJ && (xi < mlo || xi > mhi)) {
+                const unsigned long long rel = (unsigned long long)xi - base;
+                rv[q] = (unsigned)rel;
+                rk[q] = 0u;
+                if (p0 + c < n) {
+                    if (rel < span) {
+                        rk[q] = atomicAdd(&s_cnt[(unsigned)rel >> lw], 1u);
+                        vm |= 1u << q;
+                    } else if (BIJ && xi >= rlo && xi <= rhi) {
                         ooi = (p0 + c) < ooi ? (p0 + c) : ooi;
-                    } else {
-                        const unsigned long long rel = (unsigned long long)xi - base;
-                        if (rel < span) {
-                            const unsigned b = (unsigned)(rel >> lw);
-                            atomicAdd(&s_cnt[b], 1u);
-                            sv = (b << lw) | (unsigned)(rel & wmask);
-                        }
                     }
                 }
-                st[j][c] = sv;
             }
         }
         __syncthreads();
-        // B: exclusive scan of the bucket counts, then reserve pool space per bucket
+        // exclusive scan of the bucket counts; reserve pool space per bucket
         {
             unsigned loc = 0;
             const unsigned b0 = tid * per;
@@ -767,49 +779,39 @@ __global__ void __launch_bounds__(BK_THREADS, 2) bucket_scatter_kernel(
             __syncthreads();
             unsigned wpre = 0, tot = 0;
 #pragma unroll
-            for (int i = 0; i < BK_THREADS / 32; i++) {
+            for (int i = 0; i < BS_THREADS / 32; i++) {
                 wpre += i < wid ? s_wsum[i] : 0u;
                 tot += s_wsum[i];
             }
             unsigned run = wpre + y - loc;
             for (unsigned k = 0; k < per; k++)
                 if (b0 + k < nb) {
-                    const unsigned c = s_cnt[b0 + k];
-                    s_start[b0 + k] = run;
-                    s_gpos[b0 + k] = c ? atomicAdd(&cursors[b0 + k], c) : 0u;
-                    s_cnt[b0 + k] = 0u;
+                    const unsigned b = b0 + k, c = s_cnt[b];
+                    const unsigned long long g = c ? atomicAdd(&cursors[b], c) : 0ull;
+                    s_start[b] = run;
+                    s_dst[b] = (long long)((unsigned long long)b * cap + g) - (long long)run;
+                    s_lim[b] = g >= cap ? run : run + (unsigned)min((unsigned long long)c, cap - g);
                     run += c;
                 }
             if (tid == 0) s_total = tot;
         }
         __syncthreads();
-        // C: counting-sort the tile by bucket (from registers)
 #pragma unroll
-        for (int j = 0; j < NV; j++)
-#pragma unroll
-            for (int c = 0; c < V; c++) {
-                const unsigned v = st[j][c];
-                if (v != BK_INVALID) {
-                    const unsigned b = v >> lw;
-                    s_sorted[s_start[b] + atomicAdd(&s_cnt[b], 1u)] = v;
-                }
-            }
+        for (int q = 0; q < BS_PER; q++)
+            if ((vm >> q) & 1u) s_sorted[s_start[rv[q] >> lw] + rk[q]] = rv[q];
         __syncthreads();
-        // D: write contiguous runs into the pool; overflow goes through L2 atomics
         const unsigned total = s_total;
         if (tid == 0) valid += total;
-        for (unsigned p = tid; p < total; p += BK_THREADS) {
+        for (unsigned p = tid; p < total; p += BS_THREADS) {
             const unsigned v = s_sorted[p];
             const unsigned b = v >> lw;
-            const unsigned long long q = (unsigned long long)s_gpos[b] + (p - s_start[b]);
-            if (q < cap) {
-                __stcs(pool + (unsigned long long)b * cap + q, (unsigned)(v & wmask));
+            if (p < s_lim[b]) {
+                __stcs(pool + (s_dst[b] + (long long)p), v & wmask);
             } else {
-                const unsigned long long rel = ((unsigned long long)b << lw) | (v & wmask);
-                const unsigned bit = 1u << (rel & 31);
-                const unsigned old = atomicOr(marks + (rel >> 5), bit);
+                const unsigned bit = 1u << (v & 31);
+                const unsigned old = atomicOr(marks + (v >> 5), bit);
                 if (old & bit) {
-                    atomicOr(dup + (rel >> 5), bit);
+                    atomicOr(dup + (v >> 5), bit);
                     atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
                     anydup = 1;
                 }
@@ -817,12 +819,11 @@ __global__ void __launch_bounds__(BK_THREADS, 2) bucket_scatter_kernel(
         }
         __syncthreads();
     }
-    __shared__ unsigned long long sm[BK_THREADS / 32];
+    __shared__ unsigned long long sm[BS_THREADS / 32];
     if (tid == 0 && valid) atomicAdd(&h->cnt0, valid);
-    unsigned long long r;
     if (__syncthreads_or(anydup) && tid == 0) atomicOr(&h->flag, 1u);
     if (BIJ) {
-        r = block_max_u64(ooi == INT64_MAX ? 0ull : enc_first(ooi), sm);
+        const unsigned long long r = block_max_u64(ooi == INT64_MAX ? 0ull : enc_first(ooi), sm);
         if (tid == 0) atomic_max_u64(&h->k_first, r);
     }
 }
@@ -1054,14 +1055,13 @@ static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int6
     const int sgrid = num_sms() * 4;
     bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, w.cursors, w.bm, w.dup,
                                                           w.bmask);
-    const size_t s1 = (size_t)(BK_TILE + 3 * cfg.bmax) * 4;
     cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (BK_TILE + 3 * BK_MAX) * 4);
+                         (int)bs_smem_bytes(BK_MAX));
     const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
-    const int g1 = (int)std::min<int64_t>(ntiles, (int64_t)num_sms() * 2);
+    const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 2));
     const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-    bucket_scatter_kernel<T, BIJ><<<g1, BK_THREADS, s1, st>>>(x, n, rlo, rhi, mlo, mhi, w.h, cfg, w.cursors, w.pool,
-                                                             w.bm, w.dup, w.bmask, vec);
+    bucket_scatter_kernel<T, BIJ><<<g1, BS_THREADS, bs_smem_bytes(cfg.bmax), st>>>(
+        x, n, rlo, rhi, w.h, cfg, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
     cudaFuncSetAttribute(bucket_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << 20) / 8);
     bucket_check_kernel<<<cfg.bmax, BK_THREADS, (1u << cfg.lw) / 8, st>>>(w.h, cfg, w.cursors, w.pool, w.bm, w.dup,
                                                                          w.bmask, BIJ ? 1 : 0);

@@ -2,9 +2,11 @@
 // indices outside the destination), the additive scatter used as the adjoint of
 // gather, and the float64 -> float32 rounding of its accumulator.
 //
-// One thread moves one row. Rows whose size is a multiple of 16 bytes (with
-// 16-byte aligned bases) move as int4 vectors, so an [n x 8] float32 payload row is
-// one 32-byte sector per access.
+// Rows whose size is a multiple of 16 bytes (with 16-byte aligned bases) move as
+// 16-byte chunks, L lanes of a warp per row (L the largest power of two <= the
+// chunk count, at most 32), so that one warp instruction touches 32 / L rows and a
+// 32-byte row is one full sector written (or read) by a lane pair. Other rows move
+// one thread per row in 4-byte words.
 #include <algorithm>
 
 #include "common.cuh"
@@ -19,38 +21,10 @@ template <typename IT>
 __global__ void __launch_bounds__(STREAM_THREADS) scatter_rows_kernel(char *__restrict__ dst, int64_t dst_len,
                                                                       const IT *__restrict__ idx,
                                                                       const char *__restrict__ vals, int64_t n,
-                                                                      int row_bytes, int vec16) {
+                                                                      int row_bytes) {
     IXP_KERNEL_ENTRY();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (vec16 && row_bytes <= 64) {
-        const int nc = row_bytes / 16;
-        for (int64_t i0 = tid; i0 < n; i0 += RU * stride) {
-            int64_t d[RU];
-            int4 v[RU][4];
-#pragma unroll
-            for (int u = 0; u < RU; u++) {
-                const int64_t i = i0 + u * stride;
-                d[u] = i < n ? (int64_t)__ldcs(idx + i) : -1;
-            }
-#pragma unroll
-            for (int u = 0; u < RU; u++) {
-                const int64_t i = i0 + u * stride;
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-                    if (c < nc && i < n) v[u][c] = __ldcs(reinterpret_cast<const int4 *>(vals + i * row_bytes) + c);
-            }
-#pragma unroll
-            for (int u = 0; u < RU; u++) {
-                if (d[u] < 0 || d[u] >= dst_len) continue;
-                int4 *t = reinterpret_cast<int4 *>(dst + d[u] * row_bytes);
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-                    if (c < nc) __stcs(t + c, v[u][c]);
-            }
-        }
-        return;
-    }
     for (int64_t i = tid; i < n; i += stride) {
         const int64_t d = (int64_t)__ldg(idx + i);
         if (d < 0 || d >= dst_len) continue;
@@ -58,6 +32,97 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_rows_kernel(char *__re
         uint32_t *t = reinterpret_cast<uint32_t *>(dst + d * row_bytes);
         for (int c = 0; c < row_bytes / 4; c++) t[c] = src[c];
     }
+}
+
+// Lane-split row move: lane j of the L lanes serving row r moves chunks j and
+// (CPL = 2) j + L of the row's nc 16-byte chunks. SCATTER: dst[idx[r]] = vals[r]
+// (indices outside [0, dst_len) ignored); gather: out[r] = src[idx[r]] (zero row
+// and an OOB status for indices outside [0, src_len)).
+template <typename IT, int L, int CPL, bool SCATTER>
+__global__ void __launch_bounds__(STREAM_THREADS, CPL == 1 ? 6 : 4)
+    rows_lanes_kernel(int4 *__restrict__ out, int64_t out_len, const IT *__restrict__ idx,
+                      const int4 *__restrict__ in, int64_t in_len, int64_t n, int nc, int32_t *status) {
+    IXP_KERNEL_ENTRY();
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int j = (int)(gt % L);
+    const int64_t r0 = gt / L;
+    const int64_t rs = (int64_t)gridDim.x * blockDim.x / L;
+    const bool two = CPL == 2 && j + L < nc;
+    bool any_oob = false;
+    for (int64_t rb = r0; rb < n; rb += RU * rs) {
+        int64_t d[RU];
+        int4 v[RU][CPL];
+#pragma unroll
+        for (int u = 0; u < RU; u++) {
+            const int64_t r = rb + u * rs;
+            d[u] = r < n ? (int64_t)__ldcs(idx + r) : -1;
+        }
+        if (SCATTER) {
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                const int64_t r = rb + u * rs;
+                if (r < n) {
+                    v[u][0] = __ldcs(in + r * nc + j);
+                    if (two) v[u][CPL - 1] = __ldcs(in + r * nc + j + L);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                if (d[u] < 0 || d[u] >= out_len) continue;
+                __stcs(out + d[u] * nc + j, v[u][0]);
+                if (two) __stcs(out + d[u] * nc + j + L, v[u][CPL - 1]);
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                const int64_t r = rb + u * rs;
+                const bool ok = d[u] >= 0 && d[u] < in_len;
+                if (r < n && !ok) any_oob = true;
+                v[u][0] = v[u][CPL - 1] = make_int4(0, 0, 0, 0);
+                if (r < n && ok) {
+                    v[u][0] = __ldg(in + d[u] * nc + j);
+                    if (two) v[u][CPL - 1] = __ldg(in + d[u] * nc + j + L);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RU; u++) {
+                const int64_t r = rb + u * rs;
+                if (r >= n) continue;
+                __stcs(out + r * nc + j, v[u][0]);
+                if (two) __stcs(out + r * nc + j + L, v[u][CPL - 1]);
+            }
+        }
+    }
+    if (!SCATTER && any_oob && status) atomicCAS(status, 0, IXP_E_OOB);
+}
+
+template <typename IT, bool SCATTER>
+static void launch_rows_lanes(int4 *out, int64_t out_len, const IT *idx, const int4 *in, int64_t in_len, int64_t n,
+                              int nc, int32_t *status, cudaStream_t st) {
+    int L = 1;
+    while (L * 2 <= nc && L < 32) L *= 2;
+    const int cpl = (nc + L - 1) / L;  // 1 or 2
+    const int64_t per_block = (int64_t)STREAM_THREADS / L * RU;
+    const int64_t cap = (int64_t)num_sms() * (cpl == 1 ? 6 : 4);
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + per_block - 1) / per_block, cap));
+#define IXP_ROWS_CASE(LL)                                                                                       \
+    case LL:                                                                                                    \
+        if (cpl == 1)                                                                                           \
+            rows_lanes_kernel<IT, LL, 1, SCATTER><<<g, STREAM_THREADS, 0, st>>>(out, out_len, idx, in, in_len, n, \
+                                                                               nc, status);                    \
+        else                                                                                                    \
+            rows_lanes_kernel<IT, LL, 2, SCATTER><<<g, STREAM_THREADS, 0, st>>>(out, out_len, idx, in, in_len, n, \
+                                                                               nc, status);                    \
+        break;
+    switch (L) {
+        IXP_ROWS_CASE(1)
+        IXP_ROWS_CASE(2)
+        IXP_ROWS_CASE(4)
+        IXP_ROWS_CASE(8)
+        IXP_ROWS_CASE(16)
+        IXP_ROWS_CASE(32)
+    }
+#undef IXP_ROWS_CASE
 }
 
 template <typename IT, typename FT>
@@ -184,50 +249,18 @@ template <typename IT>
 __global__ void __launch_bounds__(STREAM_THREADS) gather_rows_kernel(char *__restrict__ out,
                                                                      const char *__restrict__ src, int64_t src_len,
                                                                      const IT *__restrict__ idx, int64_t n,
-                                                                     int row_bytes, int vec16, int32_t *status) {
+                                                                     int row_bytes, int32_t *status) {
     IXP_KERNEL_ENTRY();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool any_oob = false;
-    if (vec16 && row_bytes <= 64) {
-        const int nc = row_bytes / 16;
-        for (int64_t i0 = tid; i0 < n; i0 += RU * stride) {
-            int64_t s[RU];
-            int4 v[RU][4];
-#pragma unroll
-            for (int u = 0; u < RU; u++) {
-                const int64_t i = i0 + u * stride;
-                s[u] = i < n ? (int64_t)__ldcs(idx + i) : 0;
-            }
-#pragma unroll
-            for (int u = 0; u < RU; u++) {
-                const int64_t i = i0 + u * stride;
-                const bool ok = s[u] >= 0 && s[u] < src_len;
-                if (i < n && !ok) any_oob = true;
-                const int4 *f = reinterpret_cast<const int4 *>(src + (ok ? s[u] : 0) * row_bytes);
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-                    if (c < nc) v[u][c] = (ok && i < n) ? __ldg(f + c) : make_int4(0, 0, 0, 0);
-            }
-#pragma unroll
-            for (int u = 0; u < RU; u++) {
-                const int64_t i = i0 + u * stride;
-                if (i >= n) continue;
-                int4 *t = reinterpret_cast<int4 *>(out + i * row_bytes);
-#pragma unroll
-                for (int c = 0; c < 4; c++)
-                    if (c < nc) __stcs(t + c, v[u][c]);
-            }
-        }
-    } else {
-        for (int64_t i = tid; i < n; i += stride) {
-            const int64_t s = (int64_t)__ldg(idx + i);
-            const bool ok = s >= 0 && s < src_len;
-            if (!ok) any_oob = true;
-            uint32_t *t = reinterpret_cast<uint32_t *>(out + i * row_bytes);
-            const uint32_t *f = reinterpret_cast<const uint32_t *>(src + (ok ? s : 0) * row_bytes);
-            for (int c = 0; c < row_bytes / 4; c++) t[c] = ok ? __ldg(f + c) : 0u;
-        }
+    for (int64_t i = tid; i < n; i += stride) {
+        const int64_t s = (int64_t)__ldg(idx + i);
+        const bool ok = s >= 0 && s < src_len;
+        if (!ok) any_oob = true;
+        uint32_t *t = reinterpret_cast<uint32_t *>(out + i * row_bytes);
+        const uint32_t *f = reinterpret_cast<const uint32_t *>(src + (ok ? s : 0) * row_bytes);
+        for (int c = 0; c < row_bytes / 4; c++) t[c] = ok ? __ldg(f + c) : 0u;
     }
     if (any_oob && status) atomicCAS(status, 0, IXP_E_OOB);
 }
@@ -254,12 +287,18 @@ extern "C" int ixp_scatter(void *dst, int64_t dst_len, const void *idx, int ityp
     const int g = row_grid(n);
     if (mode == IXP_SCATTER_ASSIGN) {
         const int v16 = (rb % 16 == 0) && al(dst, 16) && al(vals, 16);
-        if (itype == IXP_I32)
+        if (v16 && itype == IXP_I32)
+            launch_rows_lanes<int32_t, true>((int4 *)dst, dst_len, (const int32_t *)idx, (const int4 *)vals, n, n,
+                                             rb / 16, nullptr, st);
+        else if (v16)
+            launch_rows_lanes<int64_t, true>((int4 *)dst, dst_len, (const int64_t *)idx, (const int4 *)vals, n, n,
+                                             rb / 16, nullptr, st);
+        else if (itype == IXP_I32)
             scatter_rows_kernel<int32_t><<<g, STREAM_THREADS, 0, st>>>((char *)dst, dst_len, (const int32_t *)idx,
-                                                                       (const char *)vals, n, rb, v16);
+                                                                       (const char *)vals, n, rb);
         else
             scatter_rows_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>((char *)dst, dst_len, (const int64_t *)idx,
-                                                                       (const char *)vals, n, rb, v16);
+                                                                       (const char *)vals, n, rb);
     } else if (elem_bytes == 4) {
         if (itype == IXP_I32)
             scatter_add_kernel<int32_t, float><<<g, STREAM_THREADS, 0, st>>>((float *)dst, dst_len, (const int32_t *)idx,
@@ -355,12 +394,18 @@ extern "C" int ixp_gather(void *out, const void *src, int64_t src_len, const voi
     const int rb = row_elems * elem_bytes;
     const int v16 = (rb % 16 == 0) && al(out, 16) && al(src, 16);
     const int g = row_grid(n);
-    if (itype == IXP_I32)
+    if (v16 && itype == IXP_I32)
+        launch_rows_lanes<int32_t, false>((int4 *)out, n, (const int32_t *)idx, (const int4 *)src, src_len, n,
+                                          rb / 16, d_status, st);
+    else if (v16)
+        launch_rows_lanes<int64_t, false>((int4 *)out, n, (const int64_t *)idx, (const int4 *)src, src_len, n,
+                                          rb / 16, d_status, st);
+    else if (itype == IXP_I32)
         gather_rows_kernel<int32_t><<<g, STREAM_THREADS, 0, st>>>((char *)out, (const char *)src, src_len,
-                                                                  (const int32_t *)idx, n, rb, v16, d_status);
+                                                                  (const int32_t *)idx, n, rb, d_status);
     else
         gather_rows_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>((char *)out, (const char *)src, src_len,
-                                                                  (const int64_t *)idx, n, rb, v16, d_status);
+                                                                  (const int64_t *)idx, n, rb, d_status);
     return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
 }
 

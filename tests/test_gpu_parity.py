@@ -512,7 +512,9 @@ def test_filtpart_filter_and_segments(ixp, dev, n, m):
 
 
 @pytest.mark.parametrize("it", [np.int32, np.int64])
-@pytest.mark.parametrize("cols,fdt", [(1, np.float32), (8, np.float32), (3, np.float32), (2, np.float64)])
+@pytest.mark.parametrize("cols,fdt", [(1, np.float32), (8, np.float32), (3, np.float32), (2, np.float64),
+                                      (4, np.float32), (12, np.float32), (40, np.float32), (16, np.float64),
+                                      (64, np.float64), (48, np.float64)])
 def test_scatter_gather(ixp, dev, it, cols, fdt):
     rng = np.random.default_rng(cols)
     n, m = 50003, 40000
