@@ -871,48 +871,112 @@ __global__ void __launch_bounds__(TB, 6) count_kernel(const KT *__restrict__ key
     }
 }
 
-// Pass 1b: exclusive scan of the packed tile counts in place (one block), grand
-// total to h->total.
-constexpr int TS_NT = 1024;
-constexpr int TS_PER = 8;
-__global__ void __launch_bounds__(TS_NT) tile_scan_kernel(unsigned long long *tp, int64_t nt, Hdr *h) {
+// Pass 1a without segments: each block counts CT consecutive tiles with all their
+// loads issued up front (more bytes in flight per thread than one tile gives).
+constexpr int CT = 2;
+
+template <typename KT>
+__global__ void __launch_bounds__(TB, 4) count_tiles_kernel(const KT *__restrict__ keys, int64_t n, DPred filt,
+                                                         DPred part, int64_t nt, unsigned long long *tile_prefix,
+                                                         int vec_ok) {
     IXP_KERNEL_ENTRY();
-    __shared__ unsigned long long s_w[TS_NT / 32];
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int TILE = TB * SUB * V;
+    __shared__ unsigned s_w[CT][TB / 32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    unsigned long long carry = 0;
-    for (int64_t base = 0; base < nt; base += (int64_t)TS_NT * TS_PER) {
-        const int64_t p0 = base + (int64_t)threadIdx.x * TS_PER;
-        unsigned long long v[TS_PER], x = 0;
+    KT kv[CT][SUB][V];
 #pragma unroll
-        for (int j = 0; j < TS_PER; j++) {
-            v[j] = p0 + j < nt ? tp[p0 + j] : 0ull;
-            x += v[j];
+    for (int c = 0; c < CT; c++)
+#pragma unroll
+        for (int u = 0; u < SUB; u++) {
+            const int64_t p0 = ((int64_t)blockIdx.x * CT + c) * TILE + (int64_t)((w * SUB + u) * 32 + l) * V;
+            load_slot<KT, V>(keys, p0, n, vec_ok, kv[c][u]);
         }
-        unsigned long long y = x;
+#pragma unroll
+    for (int c = 0; c < CT; c++) {
+        unsigned x = 0;
+#pragma unroll
+        for (int u = 0; u < SUB; u++) {
+            const int64_t p0 = ((int64_t)blockIdx.x * CT + c) * TILE + (int64_t)((w * SUB + u) * 32 + l) * V;
+            const unsigned kk = pred_mask<KT, V>(filt, kv[c][u], p0, n);
+            const unsigned kt = kk & pred_mask<KT, V>(part, kv[c][u], p0, n);
+            x += (unsigned)__popc(kt) | ((unsigned)__popc(kk) << 16);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+        if (l == 0) s_w[c][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < CT) {
+        const int64_t t = (int64_t)blockIdx.x * CT + threadIdx.x;
+        unsigned tot = 0;
+#pragma unroll
+        for (int i = 0; i < TB / 32; i++) tot += s_w[threadIdx.x][i];
+        if (t < nt) tile_prefix[t] = widen(tot);
+    }
+}
+
+// Pass 1b: exclusive scan of the packed tile counts in place, in groups of TS_G
+// tiles: each block scans its group and writes the group total; then each block
+// adds the sum of the totals of the groups before it, and the last block writes
+// the grand total to h->total.
+constexpr int TS_G = 1024;
+
+__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long x, unsigned long long *s_w,
+                                                                  unsigned long long *total) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    unsigned long long y = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        unsigned long long o = __shfl_up_sync(FULL, y, d);
+        if (l >= d) y += o;
+    }
+    if (l == 31) s_w[w] = y;
+    __syncthreads();
+    if (w == 0) {
+        const unsigned long long v = l < nw ? s_w[l] : 0ull;
+        unsigned long long z = v;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            unsigned long long o = __shfl_up_sync(FULL, y, d);
-            if (l >= d) y += o;
+            unsigned long long o = __shfl_up_sync(FULL, z, d);
+            if (l >= d) z += o;
         }
-        if (l == 31) s_w[w] = y;
-        __syncthreads();
-        unsigned long long wpre = 0, tot = 0;
-#pragma unroll 4
-        for (int i = 0; i < TS_NT / 32; i++) {
-            const unsigned long long c = s_w[i];
-            wpre += i < w ? c : 0ull;
-            tot += c;
-        }
-        unsigned long long run = carry + wpre + y - x;
-#pragma unroll
-        for (int j = 0; j < TS_PER; j++) {
-            if (p0 + j < nt) tp[p0 + j] = run;
-            run += v[j];
-        }
-        carry += tot;
-        __syncthreads();
+        if (l < nw) s_w[l] = z - v;
+        if (l == 31) s_w[32] = z;
     }
-    if (threadIdx.x == 0) h->total = carry;
+    __syncthreads();
+    const unsigned long long r = s_w[w] + y - x;
+    *total = s_w[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(TS_G) group_scan_kernel(unsigned long long *tp, int64_t nt,
+                                                          unsigned long long *gtot) {
+    IXP_KERNEL_ENTRY();
+    __shared__ unsigned long long s_w[33];
+    const int64_t t = blockIdx.x * (int64_t)TS_G + threadIdx.x;
+    const unsigned long long x = t < nt ? tp[t] : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan_u64(x, s_w, &tot);
+    if (t < nt) tp[t] = ex;
+    if (threadIdx.x == 0) gtot[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(TS_G) group_add_kernel(unsigned long long *tp, int64_t nt,
+                                                         const unsigned long long *__restrict__ gtot, Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    __shared__ unsigned long long s_w[TS_G / 32];
+    __shared__ unsigned long long s_pre;
+    unsigned long long v = 0;
+    for (int64_t g = threadIdx.x; g < (int64_t)blockIdx.x; g += TS_G) v += gtot[g];
+    v = block_sum_u64(v, s_w);
+    if (threadIdx.x == 0) s_pre = v;
+    __syncthreads();
+    const unsigned long long pre = s_pre;
+    const int64_t t = blockIdx.x * (int64_t)TS_G + threadIdx.x;
+    if (t < nt) tp[t] += pre;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) h->total = pre + gtot[blockIdx.x];
 }
 
 // Pass 1c: seg_cnt[k] = packed count before off[k] (tile prefix + in-tile part);
@@ -1067,67 +1131,124 @@ __global__ void __launch_bounds__(TB) partition_write_kernel(
     }
 }
 
-// Flat partition, pass 2, for payload rows of one 32-bit word: the tile's trues
-// land in one contiguous run [tp, tp + T_tile) and its falses in another, so the
-// keys and payload are first placed in tile order in shared memory and then
-// written out as two coalesced runs.
-template <typename KT, typename OT>
+// Flat partition, pass 2, for payload rows of one 32-bit word. The tile's keys
+// and payload are staged in shared memory (one bulk copy each when the tile is
+// full and aligned, plain loads otherwise). The tile's trues land in one
+// contiguous run [tp, tp + T_tile) of the outputs and its falses in another, so
+// the payload (and keys) are placed in run order in shared memory, each run
+// shifted by its destination's offset within a 16-byte chunk, and written out as
+// aligned 16-byte stores with scalar stores only at the two ends of each run.
+template <typename E>
+__device__ __forceinline__ void write_run(E *__restrict__ g, const E *s, int64_t d0, int len, int sh) {
+    constexpr int C = 16 / (int)sizeof(E);
+    const int nch = (sh + len + C - 1) / C;
+    E *gb = g + (d0 - sh);  // 16-byte aligned
+    for (int k = threadIdx.x; k < nch; k += blockDim.x) {
+        const int e0 = k * C;
+        if (e0 >= sh && e0 + C <= sh + len) {
+            __stcs(reinterpret_cast<int4 *>(gb + e0), *reinterpret_cast<const int4 *>(s + e0));
+        } else {
+#pragma unroll
+            for (int c = 0; c < C; c++)
+                if (e0 + c >= sh && e0 + c < sh + len) gb[e0 + c] = s[e0 + c];
+        }
+    }
+}
+
+template <typename KT>
+__host__ __device__ constexpr int pf_tile() { return TB * SUB * (16 / (int)sizeof(KT)); }
+
+// Shared layout: keys in | payload in | payload out | keys out. Each output area
+// holds both runs, each starting on a 16-byte boundary after a shift of up to one
+// chunk, and is read in whole chunks: TILE + 16 entries cover that.
+template <typename KT>
+__host__ __device__ constexpr size_t pf_smem_bytes(bool out_keys) {
+    return (size_t)pf_tile<KT>() * sizeof(KT) + (size_t)pf_tile<KT>() * 4 + (size_t)(pf_tile<KT>() + 16) * 4 +
+           (out_keys ? (size_t)(pf_tile<KT>() + 16) * sizeof(KT) : 0);
+}
+
+template <typename KT, typename OT, bool OUT_KEYS>
 __global__ void __launch_bounds__(TB, 4) partition_flat_kernel(
     const KT *__restrict__ keys, int64_t n, DPred pred, const uint32_t *__restrict__ payload, OT *__restrict__ out_idx,
     KT *__restrict__ out_keys, uint32_t *__restrict__ out_payload, const unsigned long long *__restrict__ tile_prefix,
-    const Hdr *h, int vec_ok) {
+    Hdr *h, int vec_ok, int bulk_ok, Wait wt) {
     IXP_KERNEL_ENTRY();
     constexpr int V = 16 / sizeof(KT);
     constexpr int TILE = TB * SUB * V;
+    constexpr int CK = 16 / (int)sizeof(KT);  // keys per 16-byte chunk
+    extern __shared__ __align__(128) unsigned char pf_buf[];
+    KT *s_kin = reinterpret_cast<KT *>(pf_buf);
+    uint32_t *s_pin = reinterpret_cast<uint32_t *>(s_kin + TILE);
+    uint32_t *s_pout = s_pin + TILE;
+    KT *s_kout = reinterpret_cast<KT *>(s_pout + TILE + 16);
+    __shared__ __align__(8) unsigned long long bar;
     __shared__ unsigned s_w[TB / 32];
-    __shared__ uint32_t s_pay[TILE];
-    __shared__ KT s_key[TILE];
     const int64_t t = blockIdx.x;
     const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int cnt = (int)(t1 - t0);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (bulk_ok && cnt == TILE) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            const unsigned kb = keys ? (unsigned)(TILE * sizeof(KT)) : 0u, pb = payload ? (unsigned)(TILE * 4) : 0u;
+            mbar_expect_tx(&bar, kb + pb);
+            for (unsigned o = 0; o < kb; o += 16384u)
+                bulk_g2s((char *)s_kin + o, (const char *)(keys + t0) + o, min(16384u, kb - o), &bar);
+            for (unsigned o = 0; o < pb; o += 16384u)
+                bulk_g2s((char *)s_pin + o, (const char *)(payload + t0) + o, min(16384u, pb - o), &bar);
+            if (!mbar_wait_bounded(&bar, 0, wt.spin_limit)) {
+                set_status(h, IXP_E_TIMEOUT);
+                mbar_wait_bounded(&bar, 0, wt.spin_limit);  // let the copies land before the block moves on
+            }
+        }
+    } else {
+        for (int r = threadIdx.x; r < cnt; r += TB) {
+            if (keys) s_kin[r] = keys[t0 + r];
+            if (payload) s_pin[r] = payload[t0 + r];
+        }
+    }
+    __syncthreads();
     unsigned kt[SUB], kk[SUB];
-    KT kv[SUB][V];
+    const DPred all{IXP_P_TRUE, 0, 0, nullptr};
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
-        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
-        load_slot<KT, V>(keys, p0, n, vec_ok, kv[u]);
-        const DPred all{IXP_P_TRUE, 0, 0, nullptr};
-        kk[u] = pred_mask<KT, V>(all, kv[u], p0, n);
-        kt[u] = pred_mask<KT, V>(pred, kv[u], p0, n);
+        const int r0 = ((w * SUB + u) * 32 + l) * V;
+        const int64_t p0 = t0 + r0;
+        KT kv[V];
+        if (keys) {
+            const int4 q = *reinterpret_cast<const int4 *>(s_kin + r0);
+            memcpy(kv, &q, 16);
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++) kv[k] = (KT)0;
+        }
+        kk[u] = pred_mask<KT, V>(all, kv, p0, n);
+        kt[u] = pred_mask<KT, V>(pred, kv, p0, n);
     }
     unsigned pre[SUB];
     const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
-    const int64_t tile_T = (int64_t)(tot & 0xffffu);
+    const int tile_T = (int)(tot & 0xffffu);
     const int64_t tp = (int64_t)(tile_prefix[t] & 0xffffffffull);
     const int64_t T = (int64_t)(h->total & 0xffffffffull);
     const int64_t fbase = T + (t0 - tp);  // destination of the tile's first false
+    const int sh_t = (int)(tp & 3), sh_f = (int)(fbase & 3);
+    const int f_off = (sh_t + tile_T + 3) & ~3;  // start of the false run in s_pout (16-byte aligned)
+    const int kh_t = (int)(tp % CK), kh_f = (int)(fbase % CK);
+    const int kf_off = (kh_t + tile_T + CK - 1) / CK * CK;
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
-        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        const int r0 = ((w * SUB + u) * 32 + l) * V;
+        const int64_t p0 = t0 + r0;
         OT dst[V];
-        uint32_t pv[V];
-        if (out_payload) {
-            if (vec_ok && p0 + V <= n && V == 4) {
-                uint4 q = __ldcs(reinterpret_cast<const uint4 *>(payload + p0));
-                pv[0] = q.x;
-                pv[1 % V] = q.y;
-                pv[2 % V] = q.z;
-                pv[3 % V] = q.w;
-            } else {
-#pragma unroll
-                for (int k = 0; k < V; k++) pv[k] = (p0 + k < n) ? payload[p0 + k] : 0u;
-            }
-        }
 #pragma unroll
         for (int k = 0; k < V; k++) {
-            const int64_t r = (int64_t)((w * SUB + u) * 32 + l) * V + k;  // position in the tile
-            const int64_t lt = (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & ((1u << k) - 1u));
+            const int r = r0 + k;
+            const int lt = (int)(pre[u] & 0xffffu) + __popc(kt[u] & ((1u << k) - 1u));
             const bool c = (kt[u] >> k) & 1u;
-            const int64_t slot = c ? lt : tile_T + (r - lt);
             dst[k] = (OT)(c ? tp + lt : fbase + (r - lt));
-            if (p0 + k < n) {
-                if (out_payload) s_pay[slot] = pv[k];
-                if (out_keys) s_key[slot] = (KT)kv[u][k];
+            if (r < cnt) {
+                if (out_payload) s_pout[c ? sh_t + lt : f_off + sh_f + (r - lt)] = s_pin[r];
+                if (OUT_KEYS) s_kout[c ? kh_t + lt : kf_off + kh_f + (r - lt)] = s_kin[r];
             }
         }
         if (vec_ok && p0 + V <= n && sizeof(OT) * V >= 16) {
@@ -1153,14 +1274,19 @@ __global__ void __launch_bounds__(TB, 4) partition_flat_kernel(
                 if (p0 + k < n) out_idx[p0 + k] = dst[k];
         }
     }
-    if (!out_payload && !out_keys) return;
+    if (!out_payload && !OUT_KEYS) return;
     __syncthreads();
-    const int tile_n = (int)(t1 - t0);
-    for (int r = threadIdx.x; r < tile_n; r += TB) {
-        const int64_t d = r < tile_T ? tp + r : fbase + (r - tile_T);
-        if (d < 0 || d >= n) continue;  // only for an inconsistent header
-        if (out_payload) __stcs(out_payload + d, s_pay[r]);
-        if (out_keys) out_keys[d] = s_key[r];
+    const int tile_F = cnt - tile_T;
+    // the runs stay inside [0, n) whenever the header is consistent
+    const bool runs_ok = tp >= 0 && tp + tile_T <= n && fbase >= 0 && fbase + tile_F <= n;
+    if (!runs_ok) return;
+    if (out_payload) {
+        write_run<uint32_t>(out_payload, s_pout, tp, tile_T, sh_t);
+        write_run<uint32_t>(out_payload, s_pout + f_off, fbase, tile_F, sh_f);
+    }
+    if (OUT_KEYS) {
+        write_run<KT>(out_keys, s_kout, tp, tile_T, kh_t);
+        write_run<KT>(out_keys, s_kout + kf_off, fbase, tile_F, kh_f);
     }
 }
 
@@ -1410,6 +1536,7 @@ struct TileWs {
     Lookback L;
     unsigned long long *tile_prefix;
     unsigned long long *seg_cnt;
+    unsigned long long *gtot;  // per group of TS_G tiles
     size_t bytes;
 };
 
@@ -1426,6 +1553,8 @@ static TileWs tile_ws(void *ws, int64_t ntiles, int64_t nseg) {
     o += up256((size_t)ntiles * 8);
     r.seg_cnt = (unsigned long long *)(p + o);
     o += up256((size_t)(nseg + 1) * 8);
+    r.gtot = (unsigned long long *)(p + o);
+    o += up256((size_t)((ntiles + TS_G - 1) / TS_G + 1) * 8);
     r.bytes = o;
     return r;
 }
@@ -1489,6 +1618,15 @@ static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs se
     return launch_status();
 }
 
+// Exclusive scan of the packed tile counts (h->total gets the sum; it stays 0
+// from the header reset when there are no tiles).
+static void scan_tiles(TileWs &W, int64_t nt, cudaStream_t st) {
+    if (nt <= 0) return;
+    const unsigned ng = (unsigned)((nt + TS_G - 1) / TS_G);
+    group_scan_kernel<<<ng, TS_G, 0, st>>>(W.tile_prefix, nt, W.gtot);
+    group_add_kernel<<<ng, TS_G, 0, st>>>(W.tile_prefix, nt, W.gtot, W.h);
+}
+
 template <typename KT>
 static int run_counts(const KT *keys, int64_t n, DPred filt, DPred part, ixp_segs segs, TileWs &W, int64_t nt,
                       int vec, cudaStream_t st) {
@@ -1500,10 +1638,10 @@ static int run_counts(const KT *keys, int64_t n, DPred filt, DPred part, ixp_seg
             count_kernel<KT, true><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, segs.offsets, segs.nseg,
                                                                W.tile_prefix, W.seg_cnt, vec);
         else
-            count_kernel<KT, false><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, nullptr, 0, W.tile_prefix,
-                                                                nullptr, vec);
+            count_tiles_kernel<KT><<<(unsigned)((nt + CT - 1) / CT), TB, 0, st>>>(keys, n, filt, part, nt,
+                                                                                W.tile_prefix, vec);
     }
-    tile_scan_kernel<<<1, TS_NT, 0, st>>>(W.tile_prefix, nt, W.h);
+    scan_tiles(W, nt, st);
     if (seg) {
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((segs.nseg + 256) / 256, 4096));
         seg_fix_kernel<TB * SUB * V><<<g, 256, 0, st>>>(segs.offsets, segs.nseg, n, W.tile_prefix, W.seg_cnt, W.h);
@@ -1527,9 +1665,27 @@ static int run_partition(const KT *keys, int64_t n, ixp_pred pred, const void *p
     rc = run_counts<KT>(keys, n, all, dpred(pred), segs, W, nt, vec, st);
     if (rc) return rc;
     if (nt > 0 && !seg && (!out_payload || row_bytes == 4)) {
-        partition_flat_kernel<KT, OT><<<(unsigned)nt, TB, 0, st>>>(keys, n, dpred(pred), (const uint32_t *)payload,
-                                                                  out_idx, out_keys, (uint32_t *)out_payload,
-                                                                  W.tile_prefix, W.h, vec && aligned16(payload));
+        // 16-byte stores of the payload and key runs need 16-byte aligned outputs
+        const int vec_ok = vec && (!out_payload || aligned16(out_payload)) && (!out_keys || aligned16(out_keys));
+        const int bulk_ok = (!keys || aligned16(keys)) && (!out_payload || aligned16(payload));
+        const Wait wt = wait_config();
+        if (vec_ok && out_keys) {
+            cudaFuncSetAttribute(partition_flat_kernel<KT, OT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pf_smem_bytes<KT>(true));
+            partition_flat_kernel<KT, OT, true><<<(unsigned)nt, TB, pf_smem_bytes<KT>(true), st>>>(
+                keys, n, dpred(pred), out_payload ? (const uint32_t *)payload : nullptr, out_idx, out_keys,
+                (uint32_t *)out_payload, W.tile_prefix, W.h, vec_ok, bulk_ok, wt);
+        } else if (vec_ok) {
+            cudaFuncSetAttribute(partition_flat_kernel<KT, OT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pf_smem_bytes<KT>(false));
+            partition_flat_kernel<KT, OT, false><<<(unsigned)nt, TB, pf_smem_bytes<KT>(false), st>>>(
+                keys, n, dpred(pred), out_payload ? (const uint32_t *)payload : nullptr, out_idx, nullptr,
+                (uint32_t *)out_payload, W.tile_prefix, W.h, vec_ok, bulk_ok, wt);
+        } else {
+            partition_write_kernel<KT, OT, false><<<(unsigned)nt, TB, 0, st>>>(
+                keys, n, dpred(pred), (const uint32_t *)payload, row_bytes / 4, out_idx, out_keys,
+                (uint32_t *)out_payload, nullptr, 0, W.tile_prefix, nullptr, W.h, vec);
+        }
     } else if (nt > 0) {
         if (seg)
             partition_write_kernel<KT, OT, true><<<(unsigned)nt, TB, 0, st>>>(
@@ -1563,7 +1719,7 @@ static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, i
             longlong2 *rec = reinterpret_cast<longlong2 *>(W.L.st);
             filtpart_tile_kernel<KT, ZT><<<(unsigned)nt, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part),
                                                                      W.tile_prefix, rec, W.h, vec);
-            tile_scan_kernel<<<1, TS_NT, 0, st>>>(W.tile_prefix, nt, W.h);
+            scan_tiles(W, nt, st);
             const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 1024));
             filtpart_decide_kernel<<<g, 256, 0, st>>>(W.tile_prefix, rec, nt, W.h);
             filtpart_cmp_kernel<KT, ZT, false><<<(unsigned)nt, TB, 0, st>>>(

@@ -398,6 +398,28 @@ def test_partition_flat(ixp, dev, n, kt, ot):
         assert np.array_equal(r["payload_out"].cpu().numpy().view(np.uint32), o["payload_out"].view(np.uint32))
 
 
+@pytest.mark.parametrize("kt", [np.int32, np.int64])
+@pytest.mark.parametrize("shift", [0, 1])
+def test_partition_flat_views_and_no_keys(ixp, dev, kt, shift):
+    """Keys / payload / outputs at element offsets (unaligned bases take the
+    unstaged path) and with keys not requested."""
+    n = 3 * 4096 + 777
+    keys = synth.keys_uniform(n + 1, 41).astype(kt)
+    pay = synth.payload_f32(n + 1, 42)
+    p = ("lt", 0, synth.bernoulli_threshold(0.5))
+    kd, pd = T(keys, dev)[shift:shift + n], T(pay, dev)[shift:shift + n]
+    o = oracle.partition(keys[shift:shift + n], p, payload=pay[shift:shift + n])
+    for want in (False, True):
+        out_idx = torch.empty(n + 1, dtype=torch.int32, device=dev)[shift:shift + n]
+        out_pay = torch.empty(n + 1, dtype=torch.float32, device=dev)[shift:shift + n]
+        r = ixp.partition(kd, p, payload=pd, want_keys=want, out=out_idx, out_payload=out_pay)
+        assert r["status"].item() == 0
+        assert np.array_equal(out_idx.cpu().numpy(), o["indices"])
+        assert np.array_equal(out_pay.cpu().numpy().view(np.uint32), o["payload_out"].view(np.uint32))
+        if want:
+            assert np.array_equal(r["keys_out"].cpu().numpy(), o["keys_out"])
+
+
 def test_partition_flags_and_wide_rows(ixp, dev):
     n = 30001
     fl = synth.flags_bernoulli(n, 3, 0.3)
