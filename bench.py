@@ -427,7 +427,7 @@ def main():
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tf):
-        traffic = json.load(open(tf)).get(dom)
+        traffic = json.load(open(tf)).get("ops", {}).get(dom, {}).get("bytes")
     roofline = {"bound": "hbm", "op": dom, "kernel": OP_KERNELS.get(dom), "achieved": per_op[dom]["gbs"],
                 "peak": peak, "unit": "GB/s", "frac": round(per_op[dom]["gbs"] / peak, 4), "traffic": traffic,
                 "peak_source": peak_src}

@@ -34,6 +34,17 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_rows_kernel(char *__re
     }
 }
 
+// Read-only 16-byte load whose L2 miss fetches 64 bytes, not a whole 128-byte
+// line: rows read at random indices then cost about half the DRAM traffic (the
+// random-row rate is the same either way).
+__device__ __forceinline__ int4 ld_row_chunk(const int4 *p) {
+    int4 v;
+    asm("ld.global.nc.L2::64B.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // Lane-split row move: lane j of the L lanes serving row r moves chunks j and
 // (CPL = 2) j + L of the row's nc 16-byte chunks. SCATTER: dst[idx[r]] = vals[r]
 // (indices outside [0, dst_len) ignored); gather: out[r] = src[idx[r]] (zero row
@@ -80,8 +91,8 @@ __global__ void __launch_bounds__(STREAM_THREADS, CPL == 1 ? 6 : 4)
                 if (r < n && !ok) any_oob = true;
                 v[u][0] = v[u][CPL - 1] = make_int4(0, 0, 0, 0);
                 if (r < n && ok) {
-                    v[u][0] = __ldg(in + d[u] * nc + j);
-                    if (two) v[u][CPL - 1] = __ldg(in + d[u] * nc + j + L);
+                    v[u][0] = ld_row_chunk(in + d[u] * nc + j);
+                    if (two) v[u][CPL - 1] = ld_row_chunk(in + d[u] * nc + j + L);
                 }
             }
 #pragma unroll
