@@ -1017,7 +1017,8 @@ static BitmapWs bitmap_ws(void *ws, size_t ws_bytes, int64_t n) {
     BitmapWs w{};
     char *p = (char *)ws;
     w.h = (Hdr *)p;
-    w.buckets = n >= BK_MIN_N && ws_bytes >= bk_prefix_bytes(n) + 2 * (BK_MIN_SPAN / 8);
+    // pool positions and bucket cursors are 32-bit
+    w.buckets = n >= BK_MIN_N && bk_pool_entries(n) < (1ull << 32) && ws_bytes >= bk_prefix_bytes(n) + 2 * (BK_MIN_SPAN / 8);
     size_t off = HDR_BYTES;
     if (w.buckets) {
         w.cursors = (unsigned *)(p + HDR_BYTES);

@@ -1302,10 +1302,23 @@ __global__ void __launch_bounds__(TB, 4) partition_flat_kernel(
 // The packed tile count goes to tile_prefix[t] for the scan that follows.
 constexpr long long FP_NONE = -1, FP_BAD = -2;
 
-__device__ __forceinline__ void fp_fold(int64_t &mn, int64_t &mx, int64_t zi, int64_t r) {
-    const int64_t q = zi < r ? (int64_t)INT64_MIN : zi - r;
+// AT: the arithmetic type of the per-element bookkeeping (int32 when Z is int32
+// and n <= INT32_MAX, so every rank, Z and Z - rank fits; int64 otherwise).
+template <typename AT> struct Lim;
+template <> struct Lim<int32_t> { static constexpr int32_t lo = INT32_MIN, hi = INT32_MAX; };
+template <> struct Lim<int64_t> { static constexpr int64_t lo = INT64_MIN, hi = INT64_MAX; };
+
+template <typename AT>
+__device__ __forceinline__ void fp_fold(AT &mn, AT &mx, AT zi, AT r) {
+    const AT q = zi < r ? Lim<AT>::lo : zi - r;
     mn = q < mn ? q : mn;
     mx = q > mx ? q : mx;
+}
+
+// Widen a (min, max) pair; the empty pair (AT max, AT min) stays empty.
+template <typename AT>
+__device__ __forceinline__ int64_t fp_wide_min(AT v) {
+    return v == Lim<AT>::hi ? INT64_MAX : (int64_t)v;
 }
 
 __device__ __forceinline__ long long fp_rec(int64_t mn, int64_t mx) {
@@ -1313,7 +1326,7 @@ __device__ __forceinline__ long long fp_rec(int64_t mn, int64_t mx) {
     return (mn == mx && mn >= 0) ? (long long)mn : FP_BAD;
 }
 
-template <typename KT, typename ZT>
+template <typename KT, typename ZT, typename AT>
 __global__ void __launch_bounds__(TB, sizeof(ZT) > sizeof(KT) ? 3 : 4) filtpart_tile_kernel(const ZT *__restrict__ z, int64_t n,
                                                               const KT *__restrict__ keys, DPred filt, DPred part,
                                                               unsigned long long *tile_prefix, longlong2 *rec, Hdr *h,
@@ -1339,26 +1352,29 @@ __global__ void __launch_bounds__(TB, sizeof(ZT) > sizeof(KT) ? 3 : 4) filtpart_
     }
     unsigned pre[SUB];
     const unsigned tot = tile_counts<V>(kt, kk, pre, s_w);
-    int64_t tmn = INT64_MAX, tmx = INT64_MIN, fmn = INT64_MAX, fmx = INT64_MIN, dmin = INT64_MAX;
+    constexpr AT AMAX = Lim<AT>::hi, AMIN = Lim<AT>::lo;
+    AT tmn = AMAX, tmx = AMIN, fmn = AMAX, fmx = AMIN, dmin = AMAX;
+    const bool full = t0 + TILE <= n;
 #pragma unroll
     for (int u = 0; u < SUB; u++) {
         const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
 #pragma unroll
         for (int k = 0; k < V; k++) {
-            if (p0 + k >= n) continue;
+            if (!full && p0 + k >= n) continue;
             const unsigned below = (1u << k) - 1u;
-            const int64_t rt = (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & below);
-            const int64_t rk = (int64_t)(pre[u] >> 16) + __popc(kk[u] & below);
-            const int64_t zi = (int64_t)zv[u][k];
+            const AT rt = (AT)((pre[u] & 0xffffu) + __popc(kt[u] & below));
+            const AT rk = (AT)((pre[u] >> 16) + __popc(kk[u] & below));
+            const AT zi = (AT)zv[u][k];
             if ((kk[u] >> k) & 1u) {
-                if ((kt[u] >> k) & 1u) fp_fold(tmn, tmx, zi, rt);
-                else fp_fold(fmn, fmx, zi, rk - rt);
+                if ((kt[u] >> k) & 1u) fp_fold<AT>(tmn, tmx, zi, rt);
+                else fp_fold<AT>(fmn, fmx, zi, rk - rt);
             } else if (zi >= 0) {
                 dmin = zi < dmin ? zi : dmin;
             }
         }
     }
-    unsigned long long r[5] = {enc_min(tmn), enc_max(tmx), enc_min(fmn), enc_max(fmx), enc_min(dmin)};
+    unsigned long long r[5] = {enc_min(fp_wide_min(tmn)), enc_max((int64_t)tmx), enc_min(fp_wide_min(fmn)),
+                               enc_max((int64_t)fmx), enc_min(fp_wide_min(dmin))};
 #pragma unroll
     for (int j = 0; j < 5; j++) {
         r[j] = warp_max_u64(r[j]);
@@ -1717,8 +1733,17 @@ static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, i
         if (cudaMemsetAsync(W.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
         if (nt > 0) {
             longlong2 *rec = reinterpret_cast<longlong2 *>(W.L.st);
-            filtpart_tile_kernel<KT, ZT><<<(unsigned)nt, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part),
-                                                                     W.tile_prefix, rec, W.h, vec);
+            bool narrow = false;
+            if constexpr (sizeof(ZT) == 4) {
+                narrow = n <= INT32_MAX;
+                if (narrow)
+                    filtpart_tile_kernel<KT, ZT, int32_t><<<(unsigned)nt, TB, 0, st>>>(
+                        z, n, keys, dpred(filt), dpred(part), W.tile_prefix, rec, W.h, vec);
+            }
+            if (!narrow)
+                filtpart_tile_kernel<KT, ZT, int64_t><<<(unsigned)nt, TB, 0, st>>>(z, n, keys, dpred(filt),
+                                                                              dpred(part), W.tile_prefix, rec, W.h,
+                                                                              vec);
             scan_tiles(W, nt, st);
             const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nt + 255) / 256, 1024));
             filtpart_decide_kernel<<<g, 256, 0, st>>>(W.tile_prefix, rec, nt, W.h);
