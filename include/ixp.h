@@ -264,6 +264,23 @@ int ixp_f32_to_f64(double *out, const float *in, int64_t count, ixp_stream strea
 int ixp_gather(void *out, const void *src, int64_t src_len, const void *idx, int itype, int64_t n,
                int32_t row_elems, int32_t elem_bytes, int32_t *d_status, ixp_stream stream);
 
+/* Gather of whole segments [Sec. 2.1 gather over the flattened layout of Fig. 2]:
+ * output segment k (elements out_off[k] .. out_off[k+1] - 1) becomes a copy of
+ * source segment seg_src[k] (src_off[s] .. src_off[s+1] - 1), i.e. the gather
+ * out[j] = src[src_off[seg_src[II[j]]] + j - out_off[II[j]]] with II the mkII
+ * segment ids of the output shape, without building II or the index array. Used
+ * to move CSR rows (column indices, values) into a new row order; with the
+ * inverse segment map it is its own adjoint. out_off: device int64[m + 1],
+ * out_off[0] = 0, out_off[m] = n_out, nondecreasing; src_off: device
+ * int64[src_m + 1] with src_off[src_m] = src_len; seg_src: device int32/int64[m]
+ * in [0, src_m); elements of 4 or 8 bytes; out has n_out, src src_len elements.
+ * Offsets or a map that do not describe equal-length segments set
+ * *d_status = IXP_E_INVAL (results unspecified, every access stays in bounds;
+ * d_status nullable and not cleared). */
+int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_off, int64_t m, const void *src,
+                        int64_t src_len, const int64_t *src_off, int64_t src_m, const void *seg_src, int seg_type,
+                        int32_t elem_bytes, int32_t *d_status, ixp_stream stream);
+
 /* mkSgmDescr shape xs  [Sec. 2.1, Fig. 2 right]: out (length sum(shape)) is zero
  * except out[e_k] = xs[k] (1 when xs is NULL) for every non-empty segment k, with
  * e_k the exclusive scan of shape; empty segments write nothing. shape is a device

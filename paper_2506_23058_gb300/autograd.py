@@ -20,6 +20,9 @@ outputs and marshals arguments):
 * ``partition``  the payload rows moved to the stable two-way partition order
   (partition2, Fig. 2). Adjoint: grad_payload = gather of grad_out by ``indices``
   (every element goes to exactly one destination).
+* ``gather_segments``  whole segments (CSR rows) moved to a new segment order
+  ``seg_src``, a permutation of the segments. Adjoint: the same move with the
+  inverse permutation (each element has exactly one destination).
 """
 from __future__ import annotations
 
@@ -127,6 +130,21 @@ class PartitionFn(torch.autograd.Function):
         return grad, None, None, None, None
 
 
+class GatherSegmentsFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, src, src_off, seg_src, out_off, inv_seg):
+        out, status = ixp.gather_segments(src.contiguous(), src_off, seg_src, out_off, src.numel())
+        ctx.save_for_backward(src_off, out_off, inv_seg)
+        ctx.mark_non_differentiable(status)
+        return out, status
+
+    @staticmethod
+    def backward(ctx, g, _g_status):
+        src_off, out_off, inv_seg = ctx.saved_tensors
+        grad, _ = ixp.gather_segments(g.contiguous(), out_off, inv_seg, src_off, g.numel())
+        return grad, None, None, None, None
+
+
 def gather(src, idx, injective=False, inverse=None):
     """inverse: ``invert(idx, src.shape[0])`` for an injective idx (cache it when idx is fixed)."""
     return GatherFn.apply(src, idx, injective, inverse)[0]
@@ -138,6 +156,13 @@ def scatter(dst, idx, vals):
 
 def scatter_add(dst, idx, vals):
     return ScatterAddFn.apply(dst, idx, vals)
+
+
+def gather_segments(src, src_off, seg_src, out_off, inv_seg):
+    """Segments of src (offsets src_off) in the order seg_src (a permutation of the
+    segments; out_off the offsets of the result, inv_seg its inverse, e.g. the
+    partition ``indices`` of the rows)."""
+    return GatherSegmentsFn.apply(src, src_off, seg_src, out_off, inv_seg)[0]
 
 
 def partition(payload, keys, pred, offsets=None, out_dtype=torch.int32):

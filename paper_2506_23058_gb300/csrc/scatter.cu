@@ -276,6 +276,115 @@ __global__ void __launch_bounds__(STREAM_THREADS) gather_rows_kernel(char *__res
     if (any_oob && status) atomicCAS(status, 0, IXP_E_OOB);
 }
 
+// Gather of whole segments: output segment k (out_off[k] .. out_off[k+1]) is a
+// copy of source segment seg_src[k] (src_off[s] .. src_off[s+1]). This is the
+// gather out[j] = src[src_off[seg_src[II[j]]] + j - out_off[II[j]]] with II the
+// segment-id array of the output shape (mkII, Fig. 2), done without materialising
+// II or the index array: each block takes GS_CHUNK consecutive output elements,
+// marks the starts of the non-empty segments inside them in a shared bitmap, and
+// finds an element's segment by counting the starts at or before it.
+constexpr int GS_CHUNK = 4096;
+constexpr int GS_THREADS = 256;
+constexpr int GS_WORDS = GS_CHUNK / 32;
+
+__device__ __forceinline__ unsigned gs_heads_upto(const unsigned *s_head, const unsigned *s_pre, int e) {
+    const int w = e >> 5;
+    return s_pre[w] + __popc(s_head[w] & (0xffffffffu >> (31 - (e & 31))));
+}
+
+template <typename E, typename ST>
+__global__ void __launch_bounds__(GS_THREADS) gather_segments_kernel(E *__restrict__ out,
+                                                                     const int64_t *__restrict__ out_off,
+                                                                     const E *__restrict__ src,
+                                                                     const int64_t *__restrict__ src_off,
+                                                                     const ST *__restrict__ seg_src, int64_t m,
+                                                                     int64_t n, int64_t src_m, int64_t src_len,
+                                                                     int32_t *status) {
+    IXP_KERNEL_ENTRY();
+    __shared__ int64_t s_rel[GS_CHUNK];  // by rank among the chunk's non-empty segments: source - output start
+    __shared__ unsigned s_head[GS_WORDS];
+    __shared__ unsigned s_pre[GS_WORDS];
+    __shared__ int64_t s_k0;
+    __shared__ int s_bad;
+    const int64_t j0 = blockIdx.x * (int64_t)GS_CHUNK;
+    if (j0 >= n) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (__ldg(out_off + m) != n || __ldg(out_off) != 0) && status)
+        atomicCAS(status, 0, IXP_E_INVAL);
+    const int cnt = (int)min((int64_t)GS_CHUNK, n - j0);
+    for (int w = threadIdx.x; w < GS_WORDS; w += GS_THREADS) s_head[w] = 0u;
+    if (threadIdx.x == 0) {
+        int64_t lo = 0, hi = m;  // last k with out_off[k] <= j0: the non-empty segment holding j0
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(out_off + mid) <= j0) lo = mid;
+            else hi = mid;
+        }
+        s_k0 = lo;
+        s_bad = 0;
+    }
+    __syncthreads();
+    const int64_t k0 = s_k0;
+    for (int64_t k = k0 + 1 + threadIdx.x; k < m; k += GS_THREADS) {
+        const int64_t a = __ldg(out_off + k);
+        if (a >= j0 + cnt) break;
+        if (__ldg(out_off + k + 1) > a) atomicOr(&s_head[(a - j0) >> 5], 1u << ((a - j0) & 31));
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the per-word start counts
+        constexpr int PW = GS_WORDS / 32;
+        unsigned c[PW], run = 0;
+#pragma unroll
+        for (int i = 0; i < PW; i++) {
+            c[i] = __popc(s_head[threadIdx.x * PW + i]);
+            run += c[i];
+        }
+        unsigned y = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(FULL, y, d);
+            if ((int)threadIdx.x >= d) y += o;
+        }
+        unsigned pre = y - run;
+#pragma unroll
+        for (int i = 0; i < PW; i++) {
+            s_pre[threadIdx.x * PW + i] = pre;
+            pre += c[i];
+        }
+    }
+    __syncthreads();
+    bool bad = false;
+    for (int64_t k = k0 + threadIdx.x; k < m; k += GS_THREADS) {
+        const int64_t a = __ldg(out_off + k);
+        if (a >= j0 + cnt) break;
+        const int64_t b = __ldg(out_off + k + 1);
+        if (b <= a) continue;  // empty (or, for k0, cannot happen)
+        const int64_t s = (int64_t)__ldg(seg_src + k);
+        int64_t sa = 0;
+        if (s < 0 || s >= src_m) {
+            bad = true;
+        } else {
+            sa = __ldg(src_off + s);
+            if (__ldg(src_off + s + 1) - sa != b - a || sa < 0 || sa + (b - a) > src_len) bad = true;
+        }
+        const unsigned r = a <= j0 ? 0u : gs_heads_upto(s_head, s_pre, (int)(a - j0));
+        s_rel[r] = sa - a;
+    }
+    if (bad) atomicOr(&s_bad, 1);
+    __syncthreads();
+    if (s_bad) {
+        if (threadIdx.x == 0 && status) atomicCAS(status, 0, IXP_E_INVAL);
+        return;
+    }
+    bool oob = false;
+    for (int e = threadIdx.x; e < cnt; e += GS_THREADS) {
+        const int64_t j = j0 + e;
+        const int64_t i = j + s_rel[gs_heads_upto(s_head, s_pre, e)];
+        if (i >= 0 && i < src_len) out[j] = __ldg(src + i);
+        else oob = true;  // only with inconsistent offsets
+    }
+    if (oob && status) atomicCAS(status, 0, IXP_E_INVAL);
+}
+
 static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 static int row_grid(int64_t n) { return stream_grid(n, 1); }
@@ -417,6 +526,29 @@ extern "C" int ixp_gather(void *out, const void *src, int64_t src_len, const voi
     else
         gather_rows_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>((char *)out, (const char *)src, src_len,
                                                                   (const int64_t *)idx, n, rb, d_status);
+    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+extern "C" int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_off, int64_t m, const void *src,
+                                   int64_t src_len, const int64_t *src_off, int64_t src_m, const void *seg_src,
+                                   int seg_type, int32_t elem_bytes, int32_t *d_status, ixp_stream stream) {
+    if (seg_type != IXP_I32 && seg_type != IXP_I64) return IXP_E_DTYPE;
+    if (elem_bytes != 4 && elem_bytes != 8) return IXP_E_DTYPE;
+    if (m < 0 || src_m < 0 || n_out < 0 || src_len < 0 || !out_off || !src_off ||
+        (n_out > 0 && (m == 0 || !seg_src || !out || !src)))
+        return IXP_E_INVAL;
+    if (!al(out, elem_bytes) || !al(src, elem_bytes) || !al(seg_src, seg_type == IXP_I32 ? 4 : 8)) return IXP_E_INVAL;
+    if (n_out == 0) return IXP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned g = (unsigned)((n_out + GS_CHUNK - 1) / GS_CHUNK);
+#define IXP_GS(E, ST)                                                                                          \
+    gather_segments_kernel<E, ST><<<g, GS_THREADS, 0, st>>>((E *)out, out_off, (const E *)src, src_off,       \
+                                                            (const ST *)seg_src, m, n_out, src_m, src_len, d_status)
+    if (elem_bytes == 4 && seg_type == IXP_I32) IXP_GS(uint32_t, int32_t);
+    else if (elem_bytes == 4) IXP_GS(uint32_t, int64_t);
+    else if (seg_type == IXP_I32) IXP_GS(unsigned long long, int32_t);
+    else IXP_GS(unsigned long long, int64_t);
+#undef IXP_GS
     return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
 }
 

@@ -72,6 +72,7 @@ _SIGS = {
     "ixp_f32_to_f64": (_I, [_P, _P, _L, _P]),
     "ixp_invert": (_I, [_P, _I, _L, _P, _I, _L, _P]),
     "ixp_gather": (_I, [_P, _P, _L, _P, _I, _L, C.c_int32, C.c_int32, _P, _P]),
+    "ixp_gather_segments": (_I, [_P, _L, _P, _L, _P, _L, _P, _L, _P, _I, C.c_int32, _P, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
     "ixp_kernel_launches": (C.c_ulonglong, []),
@@ -381,6 +382,19 @@ def gather(src, idx, *, out=None, status=None, stream=None):
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=src.device)
     _ck(load().ixp_gather(_dev(out, "out"), _dev(src, "src"), src.shape[0], _dev(idx, "idx"), _itype(idx), n,
                           row_elems, src.element_size(), status.data_ptr(), _stream(stream)), "gather")
+    return out, status
+
+
+def gather_segments(src, src_off, seg_src, out_off, n_out, *, out=None, status=None, stream=None):
+    """Output segment k = source segment seg_src[k] (CSR rows moved to a new order).
+    src/out: 1-D tensors of 4- or 8-byte elements; offsets int64 [m + 1]; n_out = out_off[-1]."""
+    m = seg_src.numel()
+    out = out if out is not None else torch.empty(n_out, dtype=src.dtype, device=src.device)
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=src.device)
+    _ck(load().ixp_gather_segments(_dev(out, "out"), n_out, _dev(out_off, "out_off"), m, _dev(src, "src"),
+                                   src.numel(), _dev(src_off, "src_off"), src_off.numel() - 1,
+                                   _dev(seg_src, "seg_src"), _itype(seg_src), src.element_size(), status.data_ptr(),
+                                   _stream(stream)), "gather_segments")
     return out, status
 
 

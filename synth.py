@@ -203,6 +203,54 @@ def t_payload_f32(n: int, seed: int, device, cols: int = 1):
     return torch.rand(shape, generator=_torch_gen(seed, device), device=device, dtype=torch.float32) * 2.0 - 1.0
 
 
+def t_shapes_pareto(m: int, seed: int, device, alpha: float = 2.0, xmin: float = 1.5, max_len: int = 2**16):
+    """Device version of shapes_pareto (same law, torch's generator)."""
+    import torch
+    u = torch.rand(m, generator=_torch_gen(seed, device), device=device, dtype=torch.float64)
+    x = xmin / torch.pow(1.0 - u, 1.0 / (alpha - 1.0))
+    return torch.clamp(torch.floor(x), 1, max_len).to(torch.int64)
+
+
+def t_stratified_columns(lengths, offsets, ncols: int, seed: int):
+    """Device CSR columns: for a row of length L, element t takes a uniform column in
+    [t * s, (t + 1) * s) with s = ncols // L, so every row is sorted, unique and
+    inside [0, ncols) (a stratified sample; needs L <= ncols)."""
+    import torch
+    device = lengths.device
+    m = lengths.shape[0]
+    nnz = int(offsets[-1].item())
+    row = torch.repeat_interleave(torch.arange(m, device=device), lengths, output_size=nnz)
+    t = torch.arange(nnz, device=device, dtype=torch.int64) - offsets[:-1][row]
+    stride = (ncols // lengths)[row]
+    del row
+    u = torch.rand(nnz, generator=_torch_gen(seed, device), device=device, dtype=torch.float64)
+    jitter = torch.minimum((u * stride).to(torch.int64), stride - 1)
+    return (t * stride + jitter).to(torch.int32)
+
+
+def t_plant_rows(cols, offsets, lengths, seed: int, frac: float = 0.001):
+    """In a fraction of the rows of length >= 2, make the element at a uniform
+    position p >= 1 of the row equal its predecessor (a duplicate) or swap it with
+    its predecessor (an order break). Returns (cols, planted row ids ascending)."""
+    import torch
+    r = _rng(seed)
+    L = lengths.cpu().numpy()
+    cand = np.flatnonzero(L >= 2)
+    k = max(1, int(round(frac * L.shape[0])))
+    rows = np.sort(r.choice(cand, size=min(k, cand.shape[0]), replace=False))
+    off = offsets.cpu().numpy()
+    pos = off[rows] + 1 + (r.random(rows.shape[0]) * (L[rows] - 1)).astype(np.int64)
+    dup = r.random(rows.shape[0]) < 0.5
+    y = cols.clone()
+    p = torch.from_numpy(pos).to(cols.device)
+    prev = y[p - 1].clone()
+    cur = y[p].clone()
+    d = torch.from_numpy(dup).to(cols.device)
+    y[p] = prev
+    y[p - 1] = torch.where(d, prev, cur)
+    return y, rows
+
+
 def t_position(n: int, seed: int, lo: int = 0) -> int:
     return planted_position(n, seed, lo)
 
