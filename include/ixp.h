@@ -113,7 +113,8 @@ enum {
     IXP_OP_PARTITION = 6,/* extra = nseg */
     IXP_OP_FLAGS = 7,    /* n = m (number of segments) */
     IXP_OP_INJ_SEG = 8,  /* extra = nseg */
-    IXP_OP_BIJ_SEG = 9   /* extra = nseg */
+    IXP_OP_BIJ_SEG = 9,  /* extra = nseg */
+    IXP_OP_GATHER_SEGMENTS = 10 /* n = output elements */
 };
 
 /* Bytes of workspace that call `op` needs for n elements of type itype and the
@@ -276,10 +277,11 @@ int ixp_gather(void *out, const void *src, int64_t src_len, const void *idx, int
  * in [0, src_m); elements of 4 or 8 bytes; out has n_out, src src_len elements.
  * Offsets or a map that do not describe equal-length segments set
  * *d_status = IXP_E_INVAL (results unspecified, every access stays in bounds;
- * d_status nullable and not cleared). */
+ * d_status nullable and not cleared). Workspace: ixp_workspace_size(
+ * IXP_OP_GATHER_SEGMENTS, 0, n_out, 0) bytes, 256-byte aligned. */
 int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_off, int64_t m, const void *src,
                         int64_t src_len, const int64_t *src_off, int64_t src_m, const void *seg_src, int seg_type,
-                        int32_t elem_bytes, int32_t *d_status, ixp_stream stream);
+                        int32_t elem_bytes, int32_t *d_status, void *ws, size_t ws_bytes, ixp_stream stream);
 
 /* mkSgmDescr shape xs  [Sec. 2.1, Fig. 2 right]: out (length sum(shape)) is zero
  * except out[e_k] = xs[k] (1 when xs is NULL) for every non-empty segment k, with

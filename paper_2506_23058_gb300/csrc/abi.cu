@@ -8,6 +8,7 @@ namespace ixp {
 size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg);  // scan.cu
 size_t bk_prefix_bytes(int64_t n);                       // checks.cu
 size_t seg_ws_bytes(int64_t nseg);                       // segmented.cu
+size_t gather_segments_ws_bytes(int64_t n_out);          // scatter.cu
 
 int num_sms() {
     static int cached[64] = {0};
@@ -41,8 +42,8 @@ extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra
     if (n < 0) n = 0;
     const int es = itype == IXP_I64 ? 8 : 4;
     switch (op) {
-        case IXP_OP_RANGE:
-        case IXP_OP_MONO: return HDR_BYTES;
+        case IXP_OP_RANGE: return HDR_BYTES;
+        case IXP_OP_MONO: return HDR_BYTES + chunk_lb_bytes(n);  // the table serves the segmented form
         case IXP_OP_INJ:
         case IXP_OP_BIJ: {
             // large inputs also get the bucket pool (about 5 bytes per element)
@@ -57,7 +58,8 @@ extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra
         case IXP_OP_FILTPART: return tiled_ws_bytes(n, 16 / es, extra);
         case IXP_OP_FLAGS: return tiled_ws_bytes(n, 2, 0);
         case IXP_OP_INJ_SEG:
-        case IXP_OP_BIJ_SEG: return seg_ws_bytes(extra);
+        case IXP_OP_BIJ_SEG: return seg_ws_bytes(extra) + chunk_lb_bytes(n);
+        case IXP_OP_GATHER_SEGMENTS: return gather_segments_ws_bytes(n);
         default: return 0;
     }
 }

@@ -190,65 +190,25 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) mono_kernel(const T *__rest
 }
 
 // =================================================== Monotonic (segmented)
-// One 4096-element tile per block iteration. Segment heads inside the tile are
-// marked in a shared bitmap (binary search for the first offset >= tile start,
-// then a walk); the pair (j-1, j) is tested only when j is not a head.
-constexpr int MONO_SEG_TILE = 4096;
-
-__device__ __forceinline__ int64_t lower_bound_off(const int64_t *off, int64_t nseg, int64_t key) {
-    // first k in [0, nseg] with off[k] >= key (nseg+1 if none)
-    int64_t lo = 0, hi = nseg + 1;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if (__ldg(off + mid) < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int64_t segment_of(const int64_t *off, int64_t nseg, int64_t i) {
-    // last k in [0, nseg) with off[k] <= i
-    int64_t lo = 0, hi = nseg;  // answer in [0, nseg-1]
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (__ldg(off + mid) <= i) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
+// One SP_CHUNK-element chunk per block iteration, staged in shared memory; segment
+// heads inside the chunk are marked in a bitmap and the pair (j-1, j) is tested
+// only when j is not a head.
 template <typename T>
 __global__ void __launch_bounds__(STREAM_THREADS) mono_seg_kernel(const T *__restrict__ x, int64_t n, int c,
                                                                   const int64_t *__restrict__ off, int64_t nseg,
-                                                                  uint8_t *seg_ok, Hdr *h) {
+                                                                  const int64_t *__restrict__ lb, uint8_t *seg_ok,
+                                                                  Hdr *h) {
     IXP_KERNEL_ENTRY();
-    __shared__ unsigned heads[MONO_SEG_TILE / 32];
-    __shared__ int64_t s_k;
+    __shared__ SegPairsSmem<T> S;
     int64_t bad = INT64_MAX;
-    const int64_t ntiles = (n + MONO_SEG_TILE - 1) / MONO_SEG_TILE;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t t0 = t * MONO_SEG_TILE;
-        const int64_t t1 = min(n, t0 + MONO_SEG_TILE);
-        for (int w = threadIdx.x; w < MONO_SEG_TILE / 32; w += blockDim.x) heads[w] = 0;
-        if (threadIdx.x == 0) s_k = lower_bound_off(off, nseg, t0);
-        __syncthreads();
-        for (int64_t k = s_k + threadIdx.x; k <= nseg; k += blockDim.x) {
-            int64_t o = __ldg(off + k);
-            if (o >= t1) break;
-            if (o >= t0) atomicOr(&heads[(o - t0) >> 5], 1u << ((o - t0) & 31));
-        }
-        __syncthreads();
-        for (int64_t j = t0 + threadIdx.x; j < t1; j += blockDim.x) {
-            if (j == 0) continue;
-            int64_t r = j - t0;
-            if (heads[r >> 5] & (1u << (r & 31))) continue;
-            int64_t a = ld1(x, j - 1), b = ld1(x, j);
-            if (!cmp_ok(c, a, b)) {
+    const int64_t nchunks = (n + SP_CHUNK - 1) / SP_CHUNK;
+    for (int64_t t = blockIdx.x; t < nchunks; t += gridDim.x) {
+        seg_pairs_chunk<T>(x, n, off, nseg, t * SP_CHUNK, S, lb, [&](int64_t j, T a, T b) {
+            if (!cmp_ok(c, (int64_t)a, (int64_t)b)) {
                 bad = j < bad ? j : bad;
-                if (seg_ok) seg_ok[segment_of(off, nseg, j)] = 0;
+                if (seg_ok) seg_ok[off_segment_of(off, nseg, j)] = 0;
             }
-        }
-        __syncthreads();
+        });
     }
     __shared__ unsigned long long sm[STREAM_THREADS / 32];
     unsigned long long r = block_max_u64(bad == INT64_MAX ? 0ull : enc_first(bad), sm);
@@ -977,14 +937,18 @@ extern "C" int ixp_check_mono(const void *x, int itype, int64_t n, int cmp, ixp_
             if (itype == IXP_I32) launch_mono((const int32_t *)x, n, cmp, grid, h, st);
             else launch_mono((const int64_t *)x, n, cmp, grid, h, st);
         } else {
-            int64_t tiles = (n + MONO_SEG_TILE - 1) / MONO_SEG_TILE;
+            int64_t tiles = (n + SP_CHUNK - 1) / SP_CHUNK;
             int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 8);
+            int64_t *lb = (int64_t *)((char *)ws + HDR_BYTES);  // first segment at or after each chunk start
+            if (cudaMemsetAsync(lb, 0, (size_t)tiles * 8, st) != cudaSuccess) return IXP_E_CUDA;
+            chunk_lb_kernel<SP_CHUNK><<<stream_grid(segs.nseg + 1, 4), STREAM_THREADS, 0, st>>>(segs.offsets,
+                                                                                               segs.nseg, n, lb);
             if (itype == IXP_I32)
                 mono_seg_kernel<int32_t><<<grid, STREAM_THREADS, 0, st>>>((const int32_t *)x, n, cmp, segs.offsets,
-                                                                          segs.nseg, d_seg_ok, h);
+                                                                          segs.nseg, lb, d_seg_ok, h);
             else
                 mono_seg_kernel<int64_t><<<grid, STREAM_THREADS, 0, st>>>((const int64_t *)x, n, cmp, segs.offsets,
-                                                                          segs.nseg, d_seg_ok, h);
+                                                                          segs.nseg, lb, d_seg_ok, h);
         }
     }
     if (itype == IXP_I32) mono_finalize<int32_t><<<1, 1, 0, st>>>((const int32_t *)x, h, d_verdict);

@@ -212,6 +212,98 @@ static __device__ unsigned long long tu_kernel_count;
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&tu_kernel_count, 1ull); \
     } while (0)
 
+// ------------------------------------------------------------ segment offsets
+
+// First k in [0, nseg] with off[k] >= key (nseg + 1 if none).
+__device__ __forceinline__ int64_t off_lower_bound(const int64_t *off, int64_t nseg, int64_t key) {
+    int64_t lo = 0, hi = nseg + 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Last k in [0, nseg) with off[k] <= i: the segment holding element i.
+__device__ __forceinline__ int64_t off_segment_of(const int64_t *off, int64_t nseg, int64_t i) {
+    int64_t lo = 0, hi = nseg;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Adjacent pairs inside segments, one chunk of SP_CHUNK elements per call (all
+// threads of the block call it). The chunk x[j0 .. j0 + cnt) is staged in shared
+// memory with 16-byte loads when aligned; every segment start off[k] inside the
+// chunk is marked in a bitmap, and f(j, x[j-1], x[j]) runs for every j > 0 of the
+// chunk that is not a segment start, so pairs never cross a segment boundary.
+constexpr int SP_CHUNK = 4096;
+
+template <typename T>
+struct SegPairsSmem {
+    T x[SP_CHUNK];
+    unsigned head[SP_CHUNK / 32];
+    T prev;
+    int64_t k;
+};
+
+// lb[c] = first k in [0, nseg] with off[k] >= c * SP_CHUNK, for every chunk c, from
+// one pass over the offsets (chunks are filled by the segment whose start first
+// reaches them; a chunk nothing reaches keeps the caller's fill).
+static inline size_t chunk_lb_bytes(int64_t n) {
+    return (size_t)(((n > 0 ? n : 0) + SP_CHUNK - 1) / SP_CHUNK * 8 + 8 + 255) / 256 * 256;
+}
+
+template <int CH>
+__global__ void chunk_lb_kernel(const int64_t *__restrict__ off, int64_t nseg, int64_t n, int64_t *__restrict__ lb) {
+    IXP_KERNEL_ENTRY();
+    const int64_t nch = (n + CH - 1) / CH;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= nseg; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = k == 0 ? -1 : __ldg(off + k - 1), hi = __ldg(off + k);
+        // chunks c with lo < c * CH <= hi
+        int64_t c = lo < 0 ? 0 : lo / CH + 1;
+        for (; c < nch && c * CH <= hi; c++) lb[c] = k;
+    }
+}
+
+template <typename T, typename F>
+__device__ __forceinline__ void seg_pairs_chunk(const T *__restrict__ x, int64_t n, const int64_t *__restrict__ off,
+                                                int64_t nseg, int64_t j0, SegPairsSmem<T> &S,
+                                                const int64_t *__restrict__ lbtab, F &&f) {
+    const int cnt = (int)min((int64_t)SP_CHUNK, n - j0);
+    for (int w = threadIdx.x; w < SP_CHUNK / 32; w += blockDim.x) S.head[w] = 0u;
+    if (threadIdx.x == 0) {
+        S.prev = j0 > 0 ? x[j0 - 1] : (T)0;
+        int64_t k = lbtab ? __ldg(lbtab + j0 / SP_CHUNK) : off_lower_bound(off, nseg, j0);
+        S.k = k < 0 ? 0 : (k > nseg ? nseg : k);
+    }
+    constexpr int V = 16 / (int)sizeof(T);
+    if (cnt == SP_CHUNK && (reinterpret_cast<uintptr_t>(x + j0) & 15u) == 0) {
+        for (int v = threadIdx.x; v < SP_CHUNK / V; v += blockDim.x)
+            reinterpret_cast<int4 *>(S.x)[v] = __ldcs(reinterpret_cast<const int4 *>(x + j0) + v);
+    } else {
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) S.x[e] = x[j0 + e];
+    }
+    __syncthreads();
+    for (int64_t k = S.k + threadIdx.x; k <= nseg; k += blockDim.x) {
+        const int64_t o = __ldg(off + k);
+        if (o >= j0 + cnt) break;
+        if (o >= j0) atomicOr(&S.head[(o - j0) >> 5], 1u << ((o - j0) & 31));
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        const int64_t j = j0 + e;
+        if (j == 0 || (S.head[e >> 5] >> (e & 31)) & 1u) continue;
+        f(j, e ? S.x[e - 1] : S.prev, S.x[e]);
+    }
+    __syncthreads();
+}
+
+
 // Launch shape for grid-stride streaming kernels: 8 blocks of 256 threads per SM.
 constexpr int STREAM_THREADS = 256;
 int stream_grid(int64_t work_items, int per_thread = 4);

@@ -282,10 +282,29 @@ __global__ void __launch_bounds__(STREAM_THREADS) gather_rows_kernel(char *__res
 // segment-id array of the output shape (mkII, Fig. 2), done without materialising
 // II or the index array: each block takes GS_CHUNK consecutive output elements,
 // marks the starts of the non-empty segments inside them in a shared bitmap, and
-// finds an element's segment by counting the starts at or before it.
+// finds an element's segment by counting the starts at or before it. The segment
+// holding each chunk's first element comes from a table one pass over the
+// segments fills beforehand.
 constexpr int GS_CHUNK = 4096;
 constexpr int GS_THREADS = 256;
 constexpr int GS_WORDS = GS_CHUNK / 32;
+
+size_t gather_segments_ws_bytes(int64_t n_out) {
+    const int64_t nch = (n_out + GS_CHUNK - 1) / GS_CHUNK;
+    return (size_t)((nch + 1) * 8 + 255) / 256 * 256;
+}
+
+// k0[c] = the non-empty segment that holds element c * GS_CHUNK.
+__global__ void gs_chunk_table_kernel(const int64_t *__restrict__ out_off, int64_t m, int64_t n,
+                                      int64_t *__restrict__ k0) {
+    IXP_KERNEL_ENTRY();
+    const int64_t nch = (n + GS_CHUNK - 1) / GS_CHUNK;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = __ldg(out_off + k), b = __ldg(out_off + k + 1);
+        if (b <= a || a < 0 || b > n) continue;
+        for (int64_t c = (a + GS_CHUNK - 1) / GS_CHUNK; c < nch && c * GS_CHUNK < b; c++) k0[c] = k;
+    }
+}
 
 __device__ __forceinline__ unsigned gs_heads_upto(const unsigned *s_head, const unsigned *s_pre, int e) {
     const int w = e >> 5;
@@ -299,12 +318,12 @@ __global__ void __launch_bounds__(GS_THREADS) gather_segments_kernel(E *__restri
                                                                      const int64_t *__restrict__ src_off,
                                                                      const ST *__restrict__ seg_src, int64_t m,
                                                                      int64_t n, int64_t src_m, int64_t src_len,
+                                                                     const int64_t *__restrict__ k0tab,
                                                                      int32_t *status) {
     IXP_KERNEL_ENTRY();
     __shared__ int64_t s_rel[GS_CHUNK];  // by rank among the chunk's non-empty segments: source - output start
     __shared__ unsigned s_head[GS_WORDS];
     __shared__ unsigned s_pre[GS_WORDS];
-    __shared__ int64_t s_k0;
     __shared__ int s_bad;
     const int64_t j0 = blockIdx.x * (int64_t)GS_CHUNK;
     if (j0 >= n) return;
@@ -312,22 +331,14 @@ __global__ void __launch_bounds__(GS_THREADS) gather_segments_kernel(E *__restri
         atomicCAS(status, 0, IXP_E_INVAL);
     const int cnt = (int)min((int64_t)GS_CHUNK, n - j0);
     for (int w = threadIdx.x; w < GS_WORDS; w += GS_THREADS) s_head[w] = 0u;
-    if (threadIdx.x == 0) {
-        int64_t lo = 0, hi = m;  // last k with out_off[k] <= j0: the non-empty segment holding j0
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (__ldg(out_off + mid) <= j0) lo = mid;
-            else hi = mid;
-        }
-        s_k0 = lo;
-        s_bad = 0;
-    }
+    if (threadIdx.x == 0) s_bad = 0;
+    int64_t k0 = __ldg(k0tab + blockIdx.x);
+    k0 = k0 < 0 ? 0 : (k0 >= m ? m - 1 : k0);  // only an inconsistent table leaves it out of range
     __syncthreads();
-    const int64_t k0 = s_k0;
     for (int64_t k = k0 + 1 + threadIdx.x; k < m; k += GS_THREADS) {
         const int64_t a = __ldg(out_off + k);
         if (a >= j0 + cnt) break;
-        if (__ldg(out_off + k + 1) > a) atomicOr(&s_head[(a - j0) >> 5], 1u << ((a - j0) & 31));
+        if (a > j0 && __ldg(out_off + k + 1) > a) atomicOr(&s_head[(a - j0) >> 5], 1u << ((a - j0) & 31));
     }
     __syncthreads();
     if (threadIdx.x < 32) {  // exclusive scan of the per-word start counts
@@ -357,7 +368,7 @@ __global__ void __launch_bounds__(GS_THREADS) gather_segments_kernel(E *__restri
         const int64_t a = __ldg(out_off + k);
         if (a >= j0 + cnt) break;
         const int64_t b = __ldg(out_off + k + 1);
-        if (b <= a) continue;  // empty (or, for k0, cannot happen)
+        if (b <= a) continue;  // empty
         const int64_t s = (int64_t)__ldg(seg_src + k);
         int64_t sa = 0;
         if (s < 0 || s >= src_m) {
@@ -367,7 +378,7 @@ __global__ void __launch_bounds__(GS_THREADS) gather_segments_kernel(E *__restri
             if (__ldg(src_off + s + 1) - sa != b - a || sa < 0 || sa + (b - a) > src_len) bad = true;
         }
         const unsigned r = a <= j0 ? 0u : gs_heads_upto(s_head, s_pre, (int)(a - j0));
-        s_rel[r] = sa - a;
+        if (r < GS_CHUNK) s_rel[r] = sa - a;
     }
     if (bad) atomicOr(&s_bad, 1);
     __syncthreads();
@@ -531,7 +542,8 @@ extern "C" int ixp_gather(void *out, const void *src, int64_t src_len, const voi
 
 extern "C" int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_off, int64_t m, const void *src,
                                    int64_t src_len, const int64_t *src_off, int64_t src_m, const void *seg_src,
-                                   int seg_type, int32_t elem_bytes, int32_t *d_status, ixp_stream stream) {
+                                   int seg_type, int32_t elem_bytes, int32_t *d_status, void *ws, size_t ws_bytes,
+                                   ixp_stream stream) {
     if (seg_type != IXP_I32 && seg_type != IXP_I64) return IXP_E_DTYPE;
     if (elem_bytes != 4 && elem_bytes != 8) return IXP_E_DTYPE;
     if (m < 0 || src_m < 0 || n_out < 0 || src_len < 0 || !out_off || !src_off ||
@@ -539,11 +551,17 @@ extern "C" int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_
         return IXP_E_INVAL;
     if (!al(out, elem_bytes) || !al(src, elem_bytes) || !al(seg_src, seg_type == IXP_I32 ? 4 : 8)) return IXP_E_INVAL;
     if (n_out == 0) return IXP_OK;
+    if (!ws || !al(ws, 256) || ws_bytes < gather_segments_ws_bytes(n_out)) return IXP_E_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
+    int64_t *k0 = (int64_t *)ws;
     const unsigned g = (unsigned)((n_out + GS_CHUNK - 1) / GS_CHUNK);
+    // a chunk whose start no non-empty segment covers (inconsistent offsets) keeps -1 and is clamped
+    if (cudaMemsetAsync(k0, 0xff, (size_t)g * 8, st) != cudaSuccess) return IXP_E_CUDA;
+    gs_chunk_table_kernel<<<stream_grid(m, 4), STREAM_THREADS, 0, st>>>(out_off, m, n_out, k0);
 #define IXP_GS(E, ST)                                                                                          \
     gather_segments_kernel<E, ST><<<g, GS_THREADS, 0, st>>>((E *)out, out_off, (const E *)src, src_off,       \
-                                                            (const ST *)seg_src, m, n_out, src_m, src_len, d_status)
+                                                            (const ST *)seg_src, m, n_out, src_m, src_len, k0, \
+                                                            d_status)
     if (elem_bytes == 4 && seg_type == IXP_I32) IXP_GS(uint32_t, int32_t);
     else if (elem_bytes == 4) IXP_GS(uint32_t, int64_t);
     else if (seg_type == IXP_I32) IXP_GS(unsigned long long, int32_t);

@@ -27,10 +27,13 @@ constexpr unsigned long long SG_HUGE_BITS = 1ull << 24;  // private global bitma
 constexpr int SG_HUGE_BLOCKS = 32;
 
 // header slots used here (Hdr::spare)
-enum { SG_NLARGE = 2, SG_NHUGE = 3, SG_KIND = 4, SG_INDEX = 5, SG_VALUE = 6, SG_AUX0 = 7, SG_AUX1 = 8, SG_HCLAIM = 9 };
+enum { SG_NLARGE = 2, SG_NHUGE = 3, SG_KIND = 4, SG_INDEX = 5, SG_VALUE = 6, SG_AUX0 = 7, SG_AUX1 = 8, SG_HCLAIM = 9,
+       SG_NSLOW = 10 };
 
 struct SegWs {
     Hdr *h;
+    unsigned *slow;   // Inj: segment ids that are not strictly increasing
+    unsigned *failbm; // Inj: one bit per segment, set when it enters `slow`
     unsigned *large;  // segment ids with more than SG_SMALL elements
     unsigned *huge;   // segment ids for the global-bitmap pass
     unsigned *hbm;    // SG_HUGE_BLOCKS private bitmaps of SG_HUGE_BITS bits
@@ -49,11 +52,35 @@ __device__ __forceinline__ void seg_fail(Hdr *h, uint8_t *seg_ok, int64_t k) {
     atomicMax(&h->k_first, enc_first(k));
 }
 
+// ------------------------------------------------------------- Inj pre-pass
+// A strictly increasing segment is injective (the monotonicity argument of rule
+// InjF1, Sec. 3.2), and so is its in-Rcd part. One streaming pass over X tests
+// every in-segment adjacent pair; only the segments with a non-increasing pair are
+// listed (once each, through a per-segment bit) for the exact passes below.
+template <typename T>
+__global__ void __launch_bounds__(SG_THREADS) seg_inj_prepass_kernel(const T *__restrict__ x, int64_t n,
+                                                                     const int64_t *__restrict__ off, int64_t nseg,
+                                                                     const int64_t *__restrict__ lb, SegWs W) {
+    IXP_KERNEL_ENTRY();
+    __shared__ SegPairsSmem<T> S;
+    const int64_t nchunks = (n + SP_CHUNK - 1) / SP_CHUNK;
+    for (int64_t t = blockIdx.x; t < nchunks; t += gridDim.x) {
+        seg_pairs_chunk<T>(x, n, off, nseg, t * SP_CHUNK, S, lb, [&](int64_t j, T a, T b) {
+            if (a < b) return;
+            const int64_t k = off_segment_of(off, nseg, j);
+            const unsigned bit = 1u << (k & 31);
+            if (!(atomicOr(W.failbm + (k >> 5), bit) & bit))
+                W.slow[atomicAdd(&W.h->spare[SG_NSLOW], 1ull)] = (unsigned)k;
+        });
+    }
+}
+
 // ------------------------------------------------------------- warp pass
+// `listed`: visit only the segments of W.slow (the Inj pre-pass), else all of them.
 template <typename T, bool BIJ>
 __global__ void __launch_bounds__(SG_THREADS) seg_warp_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
                                                               int64_t rhi, const int64_t *__restrict__ off,
-                                                              int64_t nseg, uint8_t *seg_ok, SegWs W) {
+                                                              int64_t nseg, uint8_t *seg_ok, SegWs W, int listed) {
     IXP_KERNEL_ENTRY();
     __shared__ T s_val[SG_THREADS / 32][SG_SMALL];
     __shared__ unsigned s_bits[SG_THREADS / 32][SG_SMALL / 32];
@@ -62,7 +89,9 @@ __global__ void __launch_bounds__(SG_THREADS) seg_warp_kernel(const T *__restric
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     Hdr *h = W.h;
     unsigned long long cnt_all = 0;
-    for (int64_t k = gw; k < nseg; k += nw) {
+    const int64_t count = listed ? (int64_t)min((unsigned long long)nseg, h->spare[SG_NSLOW]) : nseg;
+    for (int64_t it = gw; it < count; it += nw) {
+        const int64_t k = listed ? (int64_t)W.slow[it] : it;
         int64_t a, b;
         seg_bounds(off, k, n, a, b);
         const int64_t L = b - a;
@@ -425,7 +454,8 @@ __global__ void seg_finalize(const Hdr *h, ixp_verdict *out, int bij, int64_t n)
 static size_t rnd(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t seg_ws_bytes(int64_t nseg) {
-    return HDR_BYTES + 2 * rnd((size_t)(nseg > 0 ? nseg : 1) * 4) + rnd(SG_HUGE_BLOCKS * (SG_HUGE_BITS / 8)) +
+    const size_t ns = (size_t)(nseg > 0 ? nseg : 1);
+    return HDR_BYTES + 3 * rnd(ns * 4) + rnd((ns + 31) / 32 * 4) + rnd(SG_HUGE_BLOCKS * (SG_HUGE_BITS / 8)) +
            rnd(2 * (SG_HUGE_BITS / 8));
 }
 
@@ -434,6 +464,11 @@ static SegWs seg_ws(void *ws, int64_t nseg) {
     char *p = (char *)ws;
     size_t o = HDR_BYTES;
     w.h = (Hdr *)p;
+    const size_t ns = (size_t)(nseg > 0 ? nseg : 1);
+    w.slow = (unsigned *)(p + o);
+    o += rnd(ns * 4);
+    w.failbm = (unsigned *)(p + o);
+    o += rnd((ns + 31) / 32 * 4);
     w.large = (unsigned *)(p + o);
     o += rnd((size_t)(nseg > 0 ? nseg : 1) * 4);
     w.huge = (unsigned *)(p + o);
@@ -452,7 +487,21 @@ static int run_seg(const T *x, int64_t n, int64_t rlo, int64_t rhi, ixp_segs seg
     const int sms = num_sms();
     const int64_t warps_needed = segs.nseg;
     const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>((warps_needed + 7) / 8, (int64_t)sms * 8));
-    seg_warp_kernel<T, BIJ><<<g1, SG_THREADS, 0, st>>>(x, n, rlo, rhi, segs.offsets, segs.nseg, seg_ok, W);
+    if (!BIJ) {
+        // segments the pre-pass does not list hold; the exact passes settle the listed ones
+        if (cudaMemsetAsync(W.failbm, 0, ((size_t)segs.nseg + 31) / 32 * 4, st) != cudaSuccess) return IXP_E_CUDA;
+        if (seg_ok && cudaMemsetAsync(seg_ok, 1, (size_t)segs.nseg, st) != cudaSuccess) return IXP_E_CUDA;
+        if (n > 0) {
+            const int64_t chunks = (n + SP_CHUNK - 1) / SP_CHUNK;
+            int64_t *lb = (int64_t *)((char *)ws + seg_ws_bytes(segs.nseg));
+            if (cudaMemsetAsync(lb, 0, (size_t)chunks * 8, st) != cudaSuccess) return IXP_E_CUDA;
+            chunk_lb_kernel<SP_CHUNK><<<stream_grid(segs.nseg + 1, 4), STREAM_THREADS, 0, st>>>(segs.offsets,
+                                                                                               segs.nseg, n, lb);
+            const int gp = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)sms * 8));
+            seg_inj_prepass_kernel<T><<<gp, SG_THREADS, 0, st>>>(x, n, segs.offsets, segs.nseg, lb, W);
+        }
+    }
+    seg_warp_kernel<T, BIJ><<<g1, SG_THREADS, 0, st>>>(x, n, rlo, rhi, segs.offsets, segs.nseg, seg_ok, W, BIJ ? 0 : 1);
     const size_t smem = SG_SMEM_BITS / 8;
     cudaFuncSetAttribute(seg_block_kernel<T, BIJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     seg_block_kernel<T, BIJ><<<sms, SG_THREADS, smem, st>>>(x, n, rlo, rhi, segs.offsets, seg_ok, W);
@@ -471,7 +520,8 @@ static int seg_entry(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_
         return IXP_E_INVAL;
     if (!segs.offsets || segs.nseg < 1 || segs.nseg >= (1ll << 32)) return IXP_E_INVAL;
     if (BIJ && n > 0 && (rcd_lo > 0 || rcd_hi < n - 1)) return IXP_E_INVAL;  // every Img_k must lie inside Rcd
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < seg_ws_bytes(segs.nseg)) return IXP_E_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < seg_ws_bytes(segs.nseg) + chunk_lb_bytes(n))
+        return IXP_E_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     if (itype == IXP_I32)
         return run_seg<int32_t, BIJ>((const int32_t *)x, n, rcd_lo, rcd_hi, segs, d_verdict, d_seg_ok, ws, st);

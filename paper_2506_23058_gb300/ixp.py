@@ -23,7 +23,7 @@ KINDS = ["none", "out_of_range", "order", "duplicate", "out_of_image", "missing"
 CMPS = {"le": 0, "lt": 1, "ge": 2, "gt": 3}
 PREDS = {"true": 0, "mod_eq": 1, "lt": 2, "flags": 3}
 OPS = {"range": 0, "mono": 1, "inj": 2, "bij": 3, "filtpart": 4, "scan": 5, "partition": 6, "flags": 7,
-       "inj_seg": 8, "bij_seg": 9}
+       "inj_seg": 8, "bij_seg": 9, "gather_segments": 10}
 ERRORS = {0: "ok", -1: "invalid argument", -2: "unsupported element type", -3: "value span exceeds the workspace",
           -4: "workspace too small", -5: "CUDA launch failed", -6: "bounded device wait gave up",
           -7: "index out of bounds"}
@@ -72,7 +72,7 @@ _SIGS = {
     "ixp_f32_to_f64": (_I, [_P, _P, _L, _P]),
     "ixp_invert": (_I, [_P, _I, _L, _P, _I, _L, _P]),
     "ixp_gather": (_I, [_P, _P, _L, _P, _I, _L, C.c_int32, C.c_int32, _P, _P]),
-    "ixp_gather_segments": (_I, [_P, _L, _P, _L, _P, _L, _P, _L, _P, _I, C.c_int32, _P, _P]),
+    "ixp_gather_segments": (_I, [_P, _L, _P, _L, _P, _L, _P, _L, _P, _I, C.c_int32, _P, _P, _Z, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
     "ixp_kernel_launches": (C.c_ulonglong, []),
@@ -385,16 +385,19 @@ def gather(src, idx, *, out=None, status=None, stream=None):
     return out, status
 
 
-def gather_segments(src, src_off, seg_src, out_off, n_out, *, out=None, status=None, stream=None):
+def gather_segments(src, src_off, seg_src, out_off, n_out, *, out=None, status=None, ws=None, stream=None):
     """Output segment k = source segment seg_src[k] (CSR rows moved to a new order).
     src/out: 1-D tensors of 4- or 8-byte elements; offsets int64 [m + 1]; n_out = out_off[-1]."""
     m = seg_src.numel()
     out = out if out is not None else torch.empty(n_out, dtype=src.dtype, device=src.device)
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=src.device)
+    need = workspace_size("gather_segments", 0, n_out)
+    ws = ws if ws is not None else workspace(need, src.device)
     _ck(load().ixp_gather_segments(_dev(out, "out"), n_out, _dev(out_off, "out_off"), m, _dev(src, "src"),
                                    src.numel(), _dev(src_off, "src_off"), src_off.numel() - 1,
                                    _dev(seg_src, "seg_src"), _itype(seg_src), src.element_size(), status.data_ptr(),
-                                   _stream(stream)), "gather_segments")
+                                   ws.data_ptr() if ws.numel() else None, ws.numel(), _stream(stream)),
+        "gather_segments")
     return out, status
 
 
