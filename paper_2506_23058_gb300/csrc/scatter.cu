@@ -150,14 +150,14 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_kernel(FT *__restr
     }
 }
 
-// Additive scatter of float32 rows into a float64 accumulator. Lanes of a warp
-// that hit the same target are combined first (match_any + a masked shuffle tree in
-// float64). Each block then keeps a direct-mapped cache of HOT_SLOTS target rows in
-// shared memory: a group's leader adds into the cached row when its target owns the
-// slot (claiming a free slot on first use) and falls back to a global float64
-// atomic otherwise; the cache is flushed with one atomic per cached value when the
-// block ends. Hot targets (a Zipf head) thus cost shared-memory atomics instead of
-// serialised global ones.
+// Additive scatter of float32 rows into a float64 accumulator. For rows of up to
+// HOT_COLS values each block keeps a direct-mapped cache of HOT_SLOTS target rows in
+// shared memory: a lane adds its row into the cached row when its target owns the
+// slot (claiming a free slot on first use) and falls back to global float64 atomics
+// otherwise; the cache is flushed with one atomic per cached value when the block
+// ends. Hot targets (a Zipf head) thus cost shared-memory atomics instead of
+// serialised global ones. Wider rows combine same-target lanes of a warp first
+// (match_any + a shuffle tree in float64) and add the sums globally.
 constexpr int HOT_SLOTS = 512;
 constexpr int HOT_COLS = 8;  // cached row width; wider rows bypass the cache
 
@@ -183,29 +183,11 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double 
         const bool live = i < n;
         int64_t d = live ? (int64_t)__ldg(idx + i) : -1;
         if (d < 0 || d >= dst_len) d = -1;
-        const unsigned peers = __match_any_sync(FULL, (unsigned long long)d);
-        const int leader = __ffs(peers) - 1;
-        // every lane of a group adds its row into the leader's registers, one column at a time
-        double v[HOT_COLS];
-        const bool single = __popc(peers) == 1;
-        unsigned todo = __ballot_sync(FULL, !single && d >= 0);
         if (cache) {
-#pragma unroll
-            for (int c = 0; c < HOT_COLS; c++) v[c] = (d >= 0 && c < row_elems) ? (double)vals[i * row_elems + c] : 0.0;
-            while (todo) {
-                const int src = __ffs(todo) - 1;
-                const int64_t key = __shfl_sync(FULL, d, src);
-                const unsigned grp = __ballot_sync(FULL, d == key);
-                todo &= ~grp;
-#pragma unroll
-                for (int c = 0; c < HOT_COLS; c++) {
-                    double x = (d == key) ? v[c] : 0.0;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
-                    if (lane == src) v[c] = x;
-                }
-            }
-            if (d >= 0 && lane == leader) {
+            // every lane adds its own row: into the block's shared copy of a cached target (the
+            // hardware serializes same-address shared atomics, far cheaper than combining rows
+            // across the warp first), else straight into the global accumulator
+            if (d >= 0) {
                 const int sl = (int)(d % HOT_SLOTS);
                 unsigned long long tag = s_tag[sl];
                 if (tag == ~0ull) {
@@ -213,12 +195,17 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double 
                     tag = prev == ~0ull ? (unsigned long long)d : prev;
                 }
                 if (tag == (unsigned long long)d) {
-                    for (int c = 0; c < row_elems; c++) atomicAdd(&s_row[sl][c], v[c]);
+                    for (int c = 0; c < row_elems; c++) atomicAdd(&s_row[sl][c], (double)vals[i * row_elems + c]);
                 } else {
-                    for (int c = 0; c < row_elems; c++) atomicAdd(acc + d * row_elems + c, v[c]);
+                    for (int c = 0; c < row_elems; c++) atomicAdd(acc + d * row_elems + c, (double)vals[i * row_elems + c]);
                 }
             }
         } else {
+            // wide rows: the lanes holding the same target combine their rows across the warp
+            // (one column at a time) and one of them adds the sum
+            const unsigned peers = __match_any_sync(FULL, (unsigned long long)d);
+            const bool single = __popc(peers) == 1;
+            unsigned todo = __ballot_sync(FULL, !single && d >= 0);
             if (d >= 0 && single)
                 for (int c = 0; c < row_elems; c++) atomicAdd(acc + d * row_elems + c, (double)vals[i * row_elems + c]);
             while (todo) {
