@@ -114,7 +114,8 @@ enum {
     IXP_OP_FLAGS = 7,    /* n = m (number of segments) */
     IXP_OP_INJ_SEG = 8,  /* extra = nseg */
     IXP_OP_BIJ_SEG = 9,  /* extra = nseg */
-    IXP_OP_GATHER_SEGMENTS = 10 /* n = output elements */
+    IXP_OP_GATHER_SEGMENTS = 10, /* n = output elements */
+    IXP_OP_FILTPART_CLASSES = 11 /* itype = v (classes), extra = nseg (0 when flat) */
 };
 
 /* Bytes of workspace that call `op` needs for n elements of type itype and the
@@ -204,6 +205,18 @@ int ixp_check_bij_seg(const void *x, int itype, int64_t n, int64_t rcd_lo, int64
 int ixp_check_filtpart(const void *z, int ztype, int64_t n, const void *keys, int ktype, ixp_pred filt,
                        ixp_pred part, ixp_segs segs, ixp_verdict *d_verdict, void *ws, size_t ws_bytes,
                        ixp_stream stream);
+
+/* InvFiltPart with v classes  [Sec. 2.3, FiltPart Y X (e_k, p^f, p^p_1..v)]: like
+ * ixp_check_filtpart, but the kept elements of each segment are placed stably by
+ * class, class 0 first: element i has class min(cls[i], v - 1) (the last class
+ * takes what the first v - 1 class predicates leave). cls: device uint8_t[n];
+ * 1 <= v <= 256; n < 2^32. Verdict as ixp_check_filtpart: index = first i with
+ * a wrong destination, value = Z[i], aux0 = N (kept elements), aux1 = the expected
+ * destination (-1 if dropped). Workspace: ixp_workspace_size(
+ * IXP_OP_FILTPART_CLASSES, v, n, nseg) bytes, 256-byte aligned. */
+int ixp_check_filtpart_classes(const void *z, int ztype, int64_t n, const void *keys, int ktype, ixp_pred filt,
+                               const uint8_t *cls, int32_t v, ixp_segs segs, ixp_verdict *d_verdict, void *ws,
+                               size_t ws_bytes, ixp_stream stream);
 
 /* ---- combinators ----------------------------------------------------------- */
 

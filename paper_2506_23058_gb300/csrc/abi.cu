@@ -9,6 +9,7 @@ size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg);  // scan.cu
 size_t bk_prefix_bytes(int64_t n);                       // checks.cu
 size_t seg_ws_bytes(int64_t nseg);                       // segmented.cu
 size_t gather_segments_ws_bytes(int64_t n_out);          // scatter.cu
+size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg);  // classes.cu
 
 int num_sms() {
     static int cached[64] = {0};
@@ -60,6 +61,7 @@ extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra
         case IXP_OP_INJ_SEG:
         case IXP_OP_BIJ_SEG: return seg_ws_bytes(extra) + chunk_lb_bytes(n);
         case IXP_OP_GATHER_SEGMENTS: return gather_segments_ws_bytes(n);
+        case IXP_OP_FILTPART_CLASSES: return filtpart_classes_ws_bytes(itype, n, extra);
         default: return 0;
     }
 }
@@ -85,8 +87,9 @@ extern "C" unsigned long long ixp_tu_kernels_scan(void);
 extern "C" unsigned long long ixp_tu_kernels_scatter(void);
 extern "C" unsigned long long ixp_tu_kernels_segmented(void);
 extern "C" unsigned long long ixp_tu_kernels_batched(void);
+extern "C" unsigned long long ixp_tu_kernels_classes(void);
 
 extern "C" unsigned long long ixp_kernel_launches(void) {
     return ixp_tu_kernels_checks() + ixp_tu_kernels_scan() + ixp_tu_kernels_scatter() + ixp_tu_kernels_segmented() +
-           ixp_tu_kernels_batched();
+           ixp_tu_kernels_batched() + ixp_tu_kernels_classes();
 }

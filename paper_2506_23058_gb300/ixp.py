@@ -23,7 +23,7 @@ KINDS = ["none", "out_of_range", "order", "duplicate", "out_of_image", "missing"
 CMPS = {"le": 0, "lt": 1, "ge": 2, "gt": 3}
 PREDS = {"true": 0, "mod_eq": 1, "lt": 2, "flags": 3}
 OPS = {"range": 0, "mono": 1, "inj": 2, "bij": 3, "filtpart": 4, "scan": 5, "partition": 6, "flags": 7,
-       "inj_seg": 8, "bij_seg": 9, "gather_segments": 10}
+       "inj_seg": 8, "bij_seg": 9, "gather_segments": 10, "filtpart_classes": 11}
 ERRORS = {0: "ok", -1: "invalid argument", -2: "unsupported element type", -3: "value span exceeds the workspace",
           -4: "workspace too small", -5: "CUDA launch failed", -6: "bounded device wait gave up",
           -7: "index out of bounds"}
@@ -73,6 +73,7 @@ _SIGS = {
     "ixp_invert": (_I, [_P, _I, _L, _P, _I, _L, _P]),
     "ixp_gather": (_I, [_P, _P, _L, _P, _I, _L, C.c_int32, C.c_int32, _P, _P]),
     "ixp_gather_segments": (_I, [_P, _L, _P, _L, _P, _L, _P, _L, _P, _I, C.c_int32, _P, _P, _Z, _P]),
+    "ixp_check_filtpart_classes": (_I, [_P, _I, _L, _P, _I, Pred, _P, C.c_int32, Segs, _P, _P, _Z, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
     "ixp_kernel_launches": (C.c_ulonglong, []),
@@ -260,7 +261,12 @@ def check_bij_seg(x, offsets, rcd_lo=I64MIN, rcd_hi=I64MAX, *, seg_ok=None, out=
     return Verdict(v)
 
 
-def check_filtpart(z, keys=None, filt="true", part="true", offsets=None, *, out=None, ws=None, stream=None) -> Verdict:
+def check_filtpart(z, keys=None, filt="true", part="true", offsets=None, *, cls=None, v=2, out=None, ws=None,
+                   stream=None) -> Verdict:
+    """InvFiltPart. With `cls` (uint8 per element) the kept elements are placed by
+    class min(cls, v - 1) instead of by the `part` predicate."""
+    if cls is not None:
+        return _check_filtpart_classes(z, keys, filt, cls, v, offsets, out=out, ws=ws, stream=stream)
     v = _verdict_buf(z.device, out)
     segs = _segs(offsets)
     kt = _itype(keys) if keys is not None else 0
@@ -270,6 +276,19 @@ def check_filtpart(z, keys=None, filt="true", part="true", offsets=None, *, out=
     _ck(load().ixp_check_filtpart(_dev(z, "z"), _itype(z), z.numel(), kp, kt, make_pred(filt), make_pred(part), segs,
                                   v.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "check_filtpart")
     return Verdict(v)
+
+
+def _check_filtpart_classes(z, keys, filt, cls, v, offsets, *, out=None, ws=None, stream=None) -> Verdict:
+    vb = _verdict_buf(z.device, out)
+    segs = _segs(offsets)
+    kt = _itype(keys) if keys is not None else 0
+    need = workspace_size("filtpart_classes", int(v), z.numel(), segs.nseg)
+    ws = ws if ws is not None else workspace(need, z.device)
+    kp = None if keys is None else _dev(keys, "keys")
+    _ck(load().ixp_check_filtpart_classes(_dev(z, "z"), _itype(z), z.numel(), kp, kt, make_pred(filt),
+                                          _dev(cls, "cls"), int(v), segs, vb.data_ptr(), ws.data_ptr(), ws.numel(),
+                                          _stream(stream)), "check_filtpart_classes")
+    return Verdict(vb)
 
 
 # ---------------------------------------------------------------- combinators

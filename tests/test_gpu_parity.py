@@ -598,3 +598,50 @@ def test_partition_paper_demo(ixp, dev):
     assert r["indices"].cpu().tolist() == g["indices"]
     assert r["keys_out"].cpu().tolist() == g["ys"]
     assert r["num_true"].item() == g["num_true"]
+
+
+def classes_dest(cls, v, kept, off):
+    """Destinations of the v-class filter-partition: per segment, kept elements by
+    class (min(cls, v - 1)), stably; dropped elements get -1."""
+    n = cls.shape[0]
+    z = np.full(n, -1, np.int64)
+    pos = 0
+    for k in range(off.shape[0] - 1):
+        a, b = int(off[k]), int(off[k + 1])
+        idx = np.arange(a, b)[kept[a:b]]
+        c = np.minimum(cls[idx], v - 1)
+        order = idx[np.argsort(c, kind="stable")]
+        z[order] = pos + np.arange(order.shape[0])
+        pos += order.shape[0]
+    return z
+
+
+@pytest.mark.parametrize("zt", [np.int32, np.int64])
+@pytest.mark.parametrize("v", [1, 2, 3, 7, 256])
+@pytest.mark.parametrize("n,m", [(1, 0), (4097, 0), (300001, 0), (5000, 1), (70000, 37), (20000, 3000)])
+def test_filtpart_classes(ixp, dev, n, m, v, zt):
+    """InvFiltPart with v classes, flat (m = 0) and segmented, with a filter; planted
+    faults at a class boundary, inside a class, on a dropped element."""
+    rng = np.random.default_rng(n + m + v)
+    off = np.array([0, n], np.int64) if m == 0 else random_offsets(rng, n, m)
+    keys = synth.keys_uniform(n, n + v).astype(np.int64)
+    flags = synth.flags_bernoulli(n, n + v + 1, 0.8)
+    cls = rng.integers(0, 256, size=n).astype(np.uint8)
+    kept = flags != 0
+    z = classes_dest(cls, v, kept, off)
+    z[~kept] = -1
+    cases = {"ok": z.copy()}
+    kidx = np.flatnonzero(kept)
+    if kidx.shape[0] >= 2:
+        s = z.copy(); a, b = kidx[0], kidx[-1]; s[a], s[b] = s[b], s[a]; cases["swap_ends"] = s
+        s = z.copy(); s[kidx[kidx.shape[0] // 2]] += 1; cases["off_by_one"] = s
+    if (~kept).any():
+        s = z.copy(); s[np.flatnonzero(~kept)[0]] = 0; cases["dropped_inside"] = s
+    fl_o, fl_g = ("flags", 0, 0, flags), ("flags", 0, 0, T(flags, dev))
+    offs_o = None if m == 0 else off
+    offs_g = None if m == 0 else T(off, dev)
+    for name, zz in cases.items():
+        zz = zz.astype(zt)
+        got = ixp.check_filtpart(T(zz, dev), T(keys, dev), filt=fl_g, offsets=offs_g, cls=T(cls, dev), v=v)
+        ref = oracle.check_filtpart(zz, keys, filt=fl_o, cls=cls, v=v, offsets=offs_o)
+        same(got, ref, (name, n, m, v))
