@@ -218,6 +218,18 @@ int ixp_check_filtpart_classes(const void *z, int ztype, int64_t n, const void *
                                const uint8_t *cls, int32_t v, ixp_segs segs, ixp_verdict *d_verdict, void *ws,
                                size_t ws_bytes, ixp_stream stream);
 
+/* FiltPart with v classes, index form  [Sec. 2.3; the partition3 / filter programs
+ * of the evaluation]: out_idx[i] = the destination of element i in the filtered,
+ * class-partitioned order (per segment, kept elements by class min(cls[i], v - 1),
+ * stably, after all kept elements of the segments before), or -1 for an element
+ * the filter drops; *d_kept (nullable) = N, the number of kept elements. Scattering
+ * X by out_idx (ignoring -1) builds FiltPart's Y; ixp_check_filtpart_classes
+ * accepts out_idx. Same arguments, limits and workspace as
+ * ixp_check_filtpart_classes; out_type IXP_I32 needs n <= INT32_MAX. */
+int ixp_filtpart_classes(const void *keys, int ktype, int64_t n, ixp_pred filt, const uint8_t *cls, int32_t v,
+                         ixp_segs segs, void *out_idx, int out_type, int64_t *d_kept, void *ws, size_t ws_bytes,
+                         ixp_stream stream);
+
 /* ---- combinators ----------------------------------------------------------- */
 
 /* scan (+) 0  [Sec. 2.1]: out[i] = sum_{j<i} in[j] (exclusive) or sum_{j<=i} in[j]

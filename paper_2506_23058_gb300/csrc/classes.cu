@@ -126,11 +126,14 @@ __device__ __forceinline__ unsigned cl_round_rank(int c, unsigned *s_wc) {
 }
 
 // ----------------------------------------------------------- flat: pass 3
-template <typename KT, typename ZT>
+// WRITE: store the destinations (-1 for dropped elements) to `dst` instead of
+// comparing them with Z (the v-class filter-partition itself).
+template <typename KT, typename ZT, bool WRITE>
 __global__ void __launch_bounds__(CL_THREADS) cl_check_kernel(const ZT *__restrict__ z, const KT *__restrict__ keys,
                                                               const uint8_t *__restrict__ cls, int64_t n, DPred filt,
                                                               int v, int64_t nt, const unsigned *__restrict__ cnt,
-                                                              const unsigned long long *__restrict__ base, Hdr *h) {
+                                                              const unsigned long long *__restrict__ base, Hdr *h,
+                                                              ZT *__restrict__ dst) {
     IXP_KERNEL_ENTRY();
     __shared__ unsigned s_wc[CL_WARPS][CL_MAXV];
     __shared__ unsigned long long s_off[CL_MAXV];
@@ -165,6 +168,10 @@ __global__ void __launch_bounds__(CL_THREADS) cl_check_kernel(const ZT *__restri
         if (i >= n) continue;
         const int c = cl[r];
         const int64_t ref = c >= 0 ? (int64_t)(s_off[c] + s_wc[w][c] + rk[r]) : -1;
+        if (WRITE) {
+            dst[i] = (ZT)ref;
+            continue;
+        }
         const int64_t zi = (int64_t)z[i];
         const bool wrong = c >= 0 ? zi != ref : (zi >= 0 && zi < N);
         if (wrong && i < bad) {
@@ -236,13 +243,14 @@ __global__ void __launch_bounds__(CL_G) cl_group_add_kernel(unsigned long long *
 
 // One block per segment (claimed from h->tile_ctr): class histogram, class bases,
 // then the comparison in chunks of CL_TILE with per-class counters carried over.
-template <typename KT, typename ZT>
+template <typename KT, typename ZT, bool WRITE>
 __global__ void __launch_bounds__(CL_THREADS) cl_seg_check_kernel(const ZT *__restrict__ z,
                                                                   const KT *__restrict__ keys,
                                                                   const uint8_t *__restrict__ cls, int64_t n,
                                                                   DPred filt, int v, const int64_t *__restrict__ off,
                                                                   int64_t nseg,
-                                                                  const unsigned long long *__restrict__ Fk, Hdr *h) {
+                                                                  const unsigned long long *__restrict__ Fk, Hdr *h,
+                                                                  ZT *__restrict__ dst) {
     IXP_KERNEL_ENTRY();
     __shared__ unsigned s_wc[CL_WARPS][CL_MAXV];
     __shared__ unsigned long long s_off[CL_MAXV];  // destination of the next element of each class
@@ -305,6 +313,10 @@ __global__ void __launch_bounds__(CL_THREADS) cl_seg_check_kernel(const ZT *__re
                 if (i >= b) continue;
                 const int c = cl[r];
                 const int64_t ref = c >= 0 ? (int64_t)(s_off[c] + s_wc[w][c] + rk[r]) : -1;
+                if (WRITE) {
+                    dst[i] = (ZT)ref;
+                    continue;
+                }
                 const int64_t zi = (int64_t)z[i];
                 const bool wrong = c >= 0 ? zi != ref : (zi >= 0 && zi < N);
                 if (wrong && i < bad) {
@@ -342,6 +354,11 @@ __global__ void cl_finalize(const ZT *z, const Hdr *h, ixp_verdict *out) {
     *out = v;
 }
 
+__global__ void cl_kept_kernel(const Hdr *h, int64_t *kept) {
+    IXP_KERNEL_ENTRY();
+    *kept = (int64_t)(h->total >> 32);
+}
+
 static size_t cl_round(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg) {
@@ -354,9 +371,12 @@ size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg) {
     return HDR_BYTES + std::max(flat, seg);
 }
 
+// With `write`, stores the destinations to dst instead of checking z (out unused,
+// N to *d_kept when given; dst may be null only when n == 0).
 template <typename KT, typename ZT>
 static int run_classes(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, const uint8_t *cls, int v,
-                       ixp_segs segs, ixp_verdict *out, void *ws, cudaStream_t st) {
+                       ixp_segs segs, ixp_verdict *out, void *ws, cudaStream_t st, bool write = false,
+                       ZT *dst = nullptr, int64_t *d_kept = nullptr) {
     Hdr *h = (Hdr *)ws;
     char *p = (char *)ws + HDR_BYTES;
     if (cudaMemsetAsync(h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
@@ -370,7 +390,12 @@ static int run_classes(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, co
             cl_count_kernel<KT><<<(unsigned)nt, CL_THREADS, 0, st>>>(keys, cls, n, f, v, nt, cnt);
             cl_class_scan_kernel<<<(unsigned)v, 1024, 0, st>>>(cnt, nt, tot);
             cl_base_kernel<<<1, 32, 0, st>>>(tot, v, base, h);
-            cl_check_kernel<KT, ZT><<<(unsigned)nt, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt, base, h);
+            if (write)
+                cl_check_kernel<KT, ZT, true><<<(unsigned)nt, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt,
+                                                                                 base, h, dst);
+            else
+                cl_check_kernel<KT, ZT, false><<<(unsigned)nt, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt,
+                                                                                  base, h, nullptr);
         }
     } else {
         const int64_t m = segs.nseg;
@@ -381,9 +406,18 @@ static int run_classes(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, co
         const unsigned ng = (unsigned)((m + CL_G - 1) / CL_G);
         cl_group_scan_kernel<<<ng, CL_G, 0, st>>>(kc, m, gtot);
         cl_group_add_kernel<<<ng, CL_G, 0, st>>>(kc, m, gtot, h);
-        cl_seg_check_kernel<KT, ZT><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, segs.offsets, m, kc, h);
+        if (write)
+            cl_seg_check_kernel<KT, ZT, true><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, segs.offsets, m, kc, h,
+                                                                       dst);
+        else
+            cl_seg_check_kernel<KT, ZT, false><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, segs.offsets, m, kc,
+                                                                        h, nullptr);
     }
-    cl_finalize<ZT><<<1, 1, 0, st>>>(z, h, out);
+    if (write) {
+        if (d_kept) cl_kept_kernel<<<1, 1, 0, st>>>(h, d_kept);
+    } else {
+        cl_finalize<ZT><<<1, 1, 0, st>>>(z, h, out);
+    }
     return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
 }
 
@@ -408,6 +442,27 @@ extern "C" int ixp_check_filtpart_classes(const void *z, int ztype, int64_t n, c
     if (!k64) return ztype == IXP_I32 ? IXP_CL(int32_t, int32_t) : IXP_CL(int32_t, int64_t);
     return ztype == IXP_I32 ? IXP_CL(int64_t, int32_t) : IXP_CL(int64_t, int64_t);
 #undef IXP_CL
+}
+
+extern "C" int ixp_filtpart_classes(const void *keys, int ktype, int64_t n, ixp_pred filt, const uint8_t *cls,
+                                    int32_t v, ixp_segs segs, void *out_idx, int out_type, int64_t *d_kept, void *ws,
+                                    size_t ws_bytes, ixp_stream stream) {
+    if ((out_type != IXP_I32 && out_type != IXP_I64) || (keys && ktype != IXP_I32 && ktype != IXP_I64))
+        return IXP_E_DTYPE;
+    if (n < 0 || n >= (1ll << 32) || v < 1 || v > CL_MAXV || (n > 0 && (!out_idx || !cls))) return IXP_E_INVAL;
+    if (out_type == IXP_I32 && n > INT32_MAX) return IXP_E_INVAL;
+    if (!pred_ok(filt, keys != nullptr || n == 0)) return IXP_E_INVAL;
+    if ((segs.offsets && segs.nseg < 1) || (!segs.offsets && segs.nseg != 0)) return IXP_E_INVAL;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) ||
+        ws_bytes < filtpart_classes_ws_bytes(v, n, segs.offsets ? segs.nseg : 0))
+        return IXP_E_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool k64 = keys && ktype == IXP_I64;
+#define IXP_CLW(KT, OT) \
+    run_classes<KT, OT>(nullptr, n, (const KT *)keys, filt, cls, v, segs, nullptr, ws, st, true, (OT *)out_idx, d_kept)
+    if (!k64) return out_type == IXP_I32 ? IXP_CLW(int32_t, int32_t) : IXP_CLW(int32_t, int64_t);
+    return out_type == IXP_I32 ? IXP_CLW(int64_t, int32_t) : IXP_CLW(int64_t, int64_t);
+#undef IXP_CLW
 }
 
 extern "C" unsigned long long ixp_tu_kernels_classes(void) {

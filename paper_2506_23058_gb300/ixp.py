@@ -74,6 +74,7 @@ _SIGS = {
     "ixp_gather": (_I, [_P, _P, _L, _P, _I, _L, C.c_int32, C.c_int32, _P, _P]),
     "ixp_gather_segments": (_I, [_P, _L, _P, _L, _P, _L, _P, _L, _P, _I, C.c_int32, _P, _P, _Z, _P]),
     "ixp_check_filtpart_classes": (_I, [_P, _I, _L, _P, _I, Pred, _P, C.c_int32, Segs, _P, _P, _Z, _P]),
+    "ixp_filtpart_classes": (_I, [_P, _I, _L, Pred, _P, C.c_int32, Segs, _P, _I, _P, _P, _Z, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
     "ixp_kernel_launches": (C.c_ulonglong, []),
@@ -289,6 +290,23 @@ def _check_filtpart_classes(z, keys, filt, cls, v, offsets, *, out=None, ws=None
                                           _dev(cls, "cls"), int(v), segs, vb.data_ptr(), ws.data_ptr(), ws.numel(),
                                           _stream(stream)), "check_filtpart_classes")
     return Verdict(vb)
+
+
+def filtpart_classes(cls, v, keys=None, filt="true", offsets=None, out_dtype=torch.int32, *, n=None, out=None,
+                     kept=None, ws=None, stream=None):
+    """Destinations of the filter + v-class partition (-1 for dropped elements).
+    Returns (out_idx, kept) with kept = N as a 1-element int64 device tensor."""
+    n = cls.numel() if n is None else n
+    segs = _segs(offsets)
+    out = out if out is not None else torch.empty(n, dtype=out_dtype, device=cls.device)
+    kept = kept if kept is not None else torch.empty(1, dtype=torch.int64, device=cls.device)
+    kt = _itype(keys) if keys is not None else 0
+    need = workspace_size("filtpart_classes", int(v), n, segs.nseg)
+    ws = ws if ws is not None else workspace(need, cls.device)
+    _ck(load().ixp_filtpart_classes(None if keys is None else _dev(keys, "keys"), kt, n, make_pred(filt),
+                                    _dev(cls, "cls"), int(v), segs, out.data_ptr(), _itype(out), kept.data_ptr(),
+                                    ws.data_ptr(), ws.numel(), _stream(stream)), "filtpart_classes")
+    return out, kept
 
 
 # ---------------------------------------------------------------- combinators

@@ -645,3 +645,25 @@ def test_filtpart_classes(ixp, dev, n, m, v, zt):
         got = ixp.check_filtpart(T(zz, dev), T(keys, dev), filt=fl_g, offsets=offs_g, cls=T(cls, dev), v=v)
         ref = oracle.check_filtpart(zz, keys, filt=fl_o, cls=cls, v=v, offsets=offs_o)
         same(got, ref, (name, n, m, v))
+
+
+@pytest.mark.parametrize("ot", [np.int32, np.int64])
+@pytest.mark.parametrize("v", [1, 3, 256])
+@pytest.mark.parametrize("n,m", [(0, 0), (1, 0), (300001, 0), (70000, 37), (20000, 3000)])
+def test_filtpart_classes_index_form(ixp, dev, n, m, v, ot):
+    """The filter + v-class partition's destinations (partition3 is v = 3): equal to
+    the stable per-segment class order, accepted by the oracle's InvFiltPart, and
+    dropped elements marked -1."""
+    rng = np.random.default_rng(7 * n + m + v)
+    off = np.array([0, n], np.int64) if m == 0 else random_offsets(rng, n, m)
+    keys = synth.keys_uniform(n, n + 3).astype(np.int32)
+    cls = rng.integers(0, 256, size=n).astype(np.uint8)
+    filt = ("mod_eq", 5, 2) if n else ("true", 0, 0)
+    kept = np.array([(int(k) % 5) == 2 for k in keys], bool) if n else np.zeros(0, bool)
+    ref = classes_dest(cls, v, kept, off)
+    got, nk = ixp.filtpart_classes(T(cls, dev), v, T(keys, dev), filt, None if m == 0 else T(off, dev),
+                                   out_dtype=getattr(torch, np.dtype(ot).name), n=n)
+    assert np.array_equal(got.cpu().numpy(), ref.astype(ot))
+    assert int(nk.item()) == int(kept.sum())
+    vd = oracle.check_filtpart(ref.astype(ot), keys, filt=filt, cls=cls, v=v, offsets=None if m == 0 else off)
+    assert vd["ok"]
