@@ -458,6 +458,7 @@ def main():
         plain_ns_per_byte = (total_ms / args.steps) * 1e6 / step_bytes
         extras["batched"] = run_batched(ixp, inp, n32, dev, plain_ns_per_byte, args)
         extras["backward"] = run_backward(ixp, inp, n32, dev, per_op)
+        extras["classes"] = run_classes(ixp, inp, n32, dev, plain_ns_per_byte)
         if not args.small:
             del inp, R
             torch.cuda.empty_cache()
@@ -571,6 +572,29 @@ def run_backward(ixp, inp, n32, dev, per_op):
                                  "bwd_gbs": round(nbytes / (zb / 1e3) / 1e9, 1),
                                  "bwd_time_per_byte_vs_plain_gather": round((zb / nbytes) / (fwd / nbytes), 3)},
             "workload": "payload [%d x 8] f32; permutation; Zipf(1.1) over 2^20 targets" % nr}
+
+
+def run_classes(ixp, inp, n32, dev, plain_ns_per_byte):
+    """Filter + 3-class partition (partition3 with a filter) of the 2^28 int32 keys:
+    the index form (destinations, -1 for dropped) and its InvFiltPart check."""
+    import torch
+    s = synth.seed_for(6)
+    g = torch.Generator(device=dev)
+    g.manual_seed(s)
+    cls = torch.randint(0, 3, (n32,), generator=g, device=dev, dtype=torch.uint8)
+    keys = inp["keys"]
+    filt = ("lt", 0, synth.bernoulli_threshold(0.9))
+    out = torch.empty(n32, dtype=torch.int32, device=dev)
+    kept = torch.empty(1, dtype=torch.int64, device=dev)
+    fwd = _time(lambda: ixp.filtpart_classes(cls, 3, keys, filt, out=out, kept=kept))
+    vd = ixp.check_filtpart(out, keys, filt=filt, cls=cls, v=3)
+    chk = _time(lambda: ixp.check_filtpart(out, keys, filt=filt, cls=cls, v=3, out=vd.buf))
+    nb = 9 * n32  # keys + class bytes read once, 4-byte destinations written (the check reads Z instead)
+    return {"workload": "n=%d int32 keys, filter key < p(0.9), 3 classes" % n32,
+            "partition_ms": round(fwd, 4), "partition_gbs": round(nb / (fwd / 1e3) / 1e9, 1),
+            "check_ms": round(chk, 4), "check_gbs": round(nb / (chk / 1e3) / 1e9, 1),
+            "check_ok": vd.get()["ok"], "kept": int(kept.item()),
+            "time_per_byte_vs_plain": round((fwd * 1e6 / nb) / plain_ns_per_byte, 3)}
 
 
 def run_csr(ixp, dev, plain_ns_per_byte):
