@@ -46,7 +46,10 @@ __device__ __forceinline__ int cl_class(const KT *keys, const uint8_t *cls, cons
 }
 
 // ----------------------------------------------------------- flat: pass 1
-template <typename KT>
+// VS > 0 (v <= VS): warps count classes with one ballot per class and add the
+// warp totals, instead of one shared atomic per element (few classes would
+// serialise on a few counters).
+template <typename KT, int VS>
 __global__ void __launch_bounds__(CL_THREADS) cl_count_kernel(const KT *__restrict__ keys,
                                                               const uint8_t *__restrict__ cls, int64_t n, DPred filt,
                                                               int v, int64_t nt, unsigned *__restrict__ cnt) {
@@ -55,14 +58,216 @@ __global__ void __launch_bounds__(CL_THREADS) cl_count_kernel(const KT *__restri
     for (int c = threadIdx.x; c < v; c += CL_THREADS) s_h[c] = 0u;
     __syncthreads();
     const int64_t t0 = blockIdx.x * (int64_t)CL_TILE;
-    for (int e = threadIdx.x; e < CL_TILE; e += CL_THREADS) {
-        const int64_t i = t0 + e;
-        if (i >= n) break;
-        const int c = cl_class(keys, cls, filt, v, i);
-        if (c >= 0) atomicAdd(&s_h[c], 1u);
+    if constexpr (VS > 0) {
+        unsigned wc[VS];
+#pragma unroll
+        for (int k = 0; k < VS; k++) wc[k] = 0u;
+        for (int e = threadIdx.x; e < CL_TILE; e += CL_THREADS) {  // whole warps stay in the loop
+            const int64_t i = t0 + e;
+            const int c = i < n ? cl_class(keys, cls, filt, v, i) : -1;
+#pragma unroll
+            for (int k = 0; k < VS; k++) wc[k] += __popc(__ballot_sync(FULL, c == k));
+        }
+        if ((threadIdx.x & 31) == 0)
+#pragma unroll
+            for (int k = 0; k < VS; k++)
+                if (k < v && wc[k]) atomicAdd(&s_h[k], wc[k]);
+    } else {
+        for (int e = threadIdx.x; e < CL_TILE; e += CL_THREADS) {
+            const int64_t i = t0 + e;
+            if (i >= n) break;
+            const int c = cl_class(keys, cls, filt, v, i);
+            if (c >= 0) atomicAdd(&s_h[c], 1u);
+        }
     }
     __syncthreads();
     for (int c = threadIdx.x; c < v; c += CL_THREADS) cnt[(int64_t)c * nt + blockIdx.x] = s_h[c];
+}
+
+// Classes of 4 consecutive elements at p0 (16-byte key loads, one 4-byte class
+// load when aligned and in range), packed one byte each: class + 1, or 0 for an
+// element that is dropped or past n.
+template <typename KT>
+__device__ __forceinline__ unsigned cl_load4(const KT *__restrict__ keys, const uint8_t *__restrict__ cls,
+                                             const DPred &filt, int v, int64_t p0, int64_t n, int vec_ok) {
+    KT kv[4];
+    load_slot<KT, 4>(keys, p0, n, vec_ok, kv);
+    const unsigned kept = pred_mask<KT, 4>(filt, kv, p0, n);
+    unsigned cw;
+    if (vec_ok && p0 + 4 <= n) {
+        cw = __ldg(reinterpret_cast<const unsigned *>(cls + p0));
+    } else {
+        cw = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (p0 + k < n) cw |= (unsigned)__ldg(cls + p0 + k) << (8 * k);
+    }
+    unsigned out = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int c = (int)((cw >> (8 * k)) & 0xffu);
+        const unsigned cc = (unsigned)(c < v - 1 ? c : v - 1);
+        if ((kept >> k) & 1u) out |= (cc + 1u) << (8 * k);
+    }
+    return out;
+}
+
+// Per class k < VS: how many of the 4 packed elements have class k.
+template <int VS>
+__device__ __forceinline__ void cl_count4(unsigned packed, unsigned (&ck)[VS]) {
+#pragma unroll
+    for (int k = 0; k < VS; k++) ck[k] = 0;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        const unsigned b = (packed >> (8 * e)) & 0xffu;
+#pragma unroll
+        for (int k = 0; k < VS; k++) ck[k] += b == (unsigned)(k + 1);
+    }
+}
+
+// Small v (v <= VS), pass 1: lanes take 4 consecutive elements; class counts are
+// kept per lane and reduced over the warp at the end.
+template <typename KT, int VS>
+__global__ void __launch_bounds__(CL_THREADS) cl_count4_kernel(const KT *__restrict__ keys,
+                                                               const uint8_t *__restrict__ cls, int64_t n,
+                                                               DPred filt, int v, int64_t nt, int vec_ok,
+                                                               unsigned *__restrict__ cnt) {
+    IXP_KERNEL_ENTRY();
+    __shared__ unsigned s_h[VS];
+    if (threadIdx.x < VS) s_h[threadIdx.x] = 0u;
+    __syncthreads();
+    const int64_t t0 = blockIdx.x * (int64_t)CL_TILE;
+    unsigned acc[VS];
+#pragma unroll
+    for (int k = 0; k < VS; k++) acc[k] = 0;
+#pragma unroll
+    for (int r = 0; r < CL_TILE / (4 * CL_THREADS); r++) {
+        const int64_t p0 = t0 + ((int64_t)r * CL_THREADS + threadIdx.x) * 4;
+        unsigned ck[VS];
+        cl_count4<VS>(cl_load4<KT>(keys, cls, filt, v, p0, n, vec_ok), ck);
+#pragma unroll
+        for (int k = 0; k < VS; k++) acc[k] += ck[k];
+    }
+#pragma unroll
+    for (int k = 0; k < VS; k++) {
+        const unsigned t = __reduce_add_sync(FULL, acc[k]);
+        if ((threadIdx.x & 31) == 0 && t) atomicAdd(&s_h[k], t);
+    }
+    __syncthreads();
+    if (threadIdx.x < v && threadIdx.x < VS) cnt[(int64_t)threadIdx.x * nt + blockIdx.x] = s_h[threadIdx.x];
+}
+
+// Small v, pass 3: warp w takes 512 consecutive elements as 4 rounds of 128 (4 per
+// lane). In a round, each class's lane counts are scanned across the warp; the
+// warp's running class counts stay in registers; the warps' totals are scanned in
+// shared memory; then each element's destination is its class offset in the tile
+// plus the warp, lane and in-lane ranks.
+template <typename KT, typename ZT, bool WRITE, int VS>
+__global__ void __launch_bounds__(CL_THREADS) cl_check4_kernel(const ZT *__restrict__ z, const KT *__restrict__ keys,
+                                                               const uint8_t *__restrict__ cls, int64_t n,
+                                                               DPred filt, int v, int64_t nt, int vec_ok,
+                                                               const unsigned *__restrict__ cnt,
+                                                               const unsigned long long *__restrict__ base, Hdr *h,
+                                                               ZT *__restrict__ dst) {
+    IXP_KERNEL_ENTRY();
+    constexpr int R = CL_TILE / (4 * CL_THREADS);  // rounds of 4 elements per lane
+    __shared__ unsigned s_wt[CL_WARPS][VS];
+    __shared__ unsigned long long s_off[VS];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (threadIdx.x < VS) s_off[threadIdx.x] = threadIdx.x < v ? base[threadIdx.x] + cnt[(int64_t)threadIdx.x * nt + blockIdx.x] : 0ull;
+    const int64_t wbase = blockIdx.x * (int64_t)CL_TILE + (int64_t)w * (R * 128);
+    unsigned pk[R], lr[R][VS], wc[VS];
+#pragma unroll
+    for (int k = 0; k < VS; k++) wc[k] = 0;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int64_t p0 = wbase + r * 128 + l * 4;
+        pk[r] = cl_load4<KT>(keys, cls, filt, v, p0, n, vec_ok);
+        unsigned ck[VS];
+        cl_count4<VS>(pk[r], ck);
+#pragma unroll
+        for (int k = 0; k < VS; k++) {
+            unsigned y = ck[k];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned o = __shfl_up_sync(FULL, y, d);
+                if (l >= d) y += o;
+            }
+            lr[r][k] = wc[k] + y - ck[k];
+            wc[k] += __shfl_sync(FULL, y, 31);
+        }
+    }
+    if (l == 0)
+#pragma unroll
+        for (int k = 0; k < VS; k++) s_wt[w][k] = wc[k];
+    __syncthreads();
+    if (threadIdx.x < VS) {
+        unsigned run = 0;
+        for (int ww = 0; ww < CL_WARPS; ww++) {
+            const unsigned x = s_wt[ww][threadIdx.x];
+            s_wt[ww][threadIdx.x] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    const int64_t N = (int64_t)(h->total >> 32);
+    int64_t bad = INT64_MAX, bref = 0;
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int64_t p0 = wbase + r * 128 + l * 4;
+        ZT zv[4];
+        if (!WRITE) load_vec<ZT, 4>(z, p0, n, vec_ok, zv);
+        unsigned seen[VS];
+#pragma unroll
+        for (int k = 0; k < VS; k++) seen[k] = 0;
+        ZT out4[4];
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            const unsigned b = (pk[r] >> (8 * e)) & 0xffu;
+            int64_t ref = -1;
+#pragma unroll
+            for (int k = 0; k < VS; k++)
+                if (b == (unsigned)(k + 1)) {
+                    ref = (int64_t)(s_off[k] + s_wt[w][k] + lr[r][k] + seen[k]);
+                    seen[k]++;
+                }
+            out4[e] = (ZT)ref;
+            const int64_t i = p0 + e;
+            if (!WRITE && i < n) {
+                const int64_t zi = (int64_t)zv[e];
+                const bool wrong = b ? zi != ref : (zi >= 0 && zi < N);
+                if (wrong && i < bad) {
+                    bad = i;
+                    bref = ref;
+                }
+            }
+        }
+        if (WRITE) {
+            if (vec_ok && p0 + 4 <= n) {
+                if (sizeof(ZT) == 4) {
+                    int4 q;
+                    q.x = (int)out4[0];
+                    q.y = (int)out4[1];
+                    q.z = (int)out4[2];
+                    q.w = (int)out4[3];
+                    __stcs(reinterpret_cast<int4 *>(dst + p0), q);
+                } else {
+                    longlong2 a, c;
+                    a.x = (long long)out4[0];
+                    a.y = (long long)out4[1];
+                    c.x = (long long)out4[2];
+                    c.y = (long long)out4[3];
+                    __stcs(reinterpret_cast<longlong2 *>(dst + p0), a);
+                    __stcs(reinterpret_cast<longlong2 *>(dst + p0) + 1, c);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; e++)
+                    if (p0 + e < n) dst[p0 + e] = out4[e];
+            }
+        }
+    }
+    if (bad != INT64_MAX) cl_report(h, bad, bref);
 }
 
 // ----------------------------------------------------------- flat: pass 2
@@ -125,10 +330,25 @@ __device__ __forceinline__ unsigned cl_round_rank(int c, unsigned *s_wc) {
     return r;
 }
 
+// The same with the warp's class counters in registers (v <= VS, uniform across
+// the warp): one ballot per class replaces the match.
+template <int VS>
+__device__ __forceinline__ unsigned cl_round_rank_small(int c, unsigned (&wc)[VS]) {
+    const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+    unsigned r = 0;
+#pragma unroll
+    for (int k = 0; k < VS; k++) {
+        const unsigned m = __ballot_sync(FULL, c == k);
+        if (c == k) r = wc[k] + __popc(m & lt);
+        wc[k] += __popc(m);
+    }
+    return r;
+}
+
 // ----------------------------------------------------------- flat: pass 3
 // WRITE: store the destinations (-1 for dropped elements) to `dst` instead of
 // comparing them with Z (the v-class filter-partition itself).
-template <typename KT, typename ZT, bool WRITE>
+template <typename KT, typename ZT, bool WRITE, int VS>
 __global__ void __launch_bounds__(CL_THREADS) cl_check_kernel(const ZT *__restrict__ z, const KT *__restrict__ keys,
                                                               const uint8_t *__restrict__ cls, int64_t n, DPred filt,
                                                               int v, int64_t nt, const unsigned *__restrict__ cnt,
@@ -144,11 +364,27 @@ __global__ void __launch_bounds__(CL_THREADS) cl_check_kernel(const ZT *__restri
     const int64_t t0 = blockIdx.x * (int64_t)CL_TILE + (int64_t)w * (CL_ROUNDS * 32);
     int cl[CL_ROUNDS];
     unsigned rk[CL_ROUNDS];
+    if constexpr (VS > 0) {
+        unsigned wc[VS];
 #pragma unroll
-    for (int r = 0; r < CL_ROUNDS; r++) {
-        const int64_t i = t0 + r * 32 + l;
-        cl[r] = i < n ? cl_class(keys, cls, filt, v, i) : -2;
-        rk[r] = cl_round_rank(cl[r], s_wc[w]);
+        for (int k = 0; k < VS; k++) wc[k] = 0u;
+#pragma unroll
+        for (int r = 0; r < CL_ROUNDS; r++) {
+            const int64_t i = t0 + r * 32 + l;
+            cl[r] = i < n ? cl_class(keys, cls, filt, v, i) : -2;
+            rk[r] = cl_round_rank_small<VS>(cl[r], wc);
+        }
+        if (l == 0)
+#pragma unroll
+            for (int k = 0; k < VS; k++)
+                if (k < v) s_wc[w][k] = wc[k];
+    } else {
+#pragma unroll
+        for (int r = 0; r < CL_ROUNDS; r++) {
+            const int64_t i = t0 + r * 32 + l;
+            cl[r] = i < n ? cl_class(keys, cls, filt, v, i) : -2;
+            rk[r] = cl_round_rank(cl[r], s_wc[w]);
+        }
     }
     __syncthreads();
     for (int c = threadIdx.x; c < v; c += CL_THREADS) {
@@ -387,15 +623,37 @@ static int run_classes(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, co
         unsigned long long *tot = (unsigned long long *)(p + cl_round((size_t)nt * v * 4));
         unsigned long long *base = (unsigned long long *)((char *)tot + cl_round((size_t)v * 8));
         if (nt > 0) {
-            cl_count_kernel<KT><<<(unsigned)nt, CL_THREADS, 0, st>>>(keys, cls, n, f, v, nt, cnt);
-            cl_class_scan_kernel<<<(unsigned)v, 1024, 0, st>>>(cnt, nt, tot);
-            cl_base_kernel<<<1, 32, 0, st>>>(tot, v, base, h);
-            if (write)
-                cl_check_kernel<KT, ZT, true><<<(unsigned)nt, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt,
-                                                                                 base, h, dst);
-            else
-                cl_check_kernel<KT, ZT, false><<<(unsigned)nt, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt,
-                                                                                  base, h, nullptr);
+            const unsigned g = (unsigned)nt;
+#define IXP_CL_PASSES(VS)                                                                                       \
+    cl_count_kernel<KT, VS><<<g, CL_THREADS, 0, st>>>(keys, cls, n, f, v, nt, cnt);                             \
+    cl_class_scan_kernel<<<(unsigned)v, 1024, 0, st>>>(cnt, nt, tot);                                           \
+    cl_base_kernel<<<1, 32, 0, st>>>(tot, v, base, h);                                                          \
+    if (write)                                                                                                  \
+        cl_check_kernel<KT, ZT, true, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt, base, h, dst); \
+    else                                                                                                        \
+        cl_check_kernel<KT, ZT, false, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt, base, h, nullptr)
+#define IXP_CL4_PASSES(VS)                                                                                      \
+    cl_count4_kernel<KT, VS><<<g, CL_THREADS, 0, st>>>(keys, cls, n, f, v, nt, vec, cnt);                       \
+    cl_class_scan_kernel<<<(unsigned)v, 1024, 0, st>>>(cnt, nt, tot);                                           \
+    cl_base_kernel<<<1, 32, 0, st>>>(tot, v, base, h);                                                          \
+    if (write)                                                                                                  \
+        cl_check4_kernel<KT, ZT, true, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, vec, cnt, base, h, \
+                                                                    dst);                                       \
+    else                                                                                                        \
+        cl_check4_kernel<KT, ZT, false, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, vec, cnt, base,  \
+                                                                     h, nullptr)
+            const auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+            const int vec = (!keys || al16(keys)) && (reinterpret_cast<uintptr_t>(cls) & 3u) == 0 &&
+                            (write ? (!dst || al16(dst)) : al16(z));
+            if (v <= 4) {
+                IXP_CL4_PASSES(4);
+            } else if (v <= 8) {
+                IXP_CL_PASSES(8);
+            } else {
+                IXP_CL_PASSES(0);
+            }
+#undef IXP_CL_PASSES
+#undef IXP_CL4_PASSES
         }
     } else {
         const int64_t m = segs.nseg;
