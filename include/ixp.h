@@ -319,6 +319,25 @@ int ixp_flags_from_shape(const int64_t *shape, int64_t m, const int64_t *xs, voi
                          int64_t out_len, int64_t *d_offsets, int32_t *d_status, void *ws, size_t ws_bytes,
                          ixp_stream stream);
 
+/* sgmSum  [Fig. 2 with Sec. 2.1 scan]: scan with the segmented operator
+ * (f1, v1) + (f2, v2) = (f1 or f2, f2 ? v2 : v1 + v2) over (flags[i] != 0, in[i]):
+ * a segment starts at 0 and at every i with flags[i] != 0; the inclusive form is
+ * out[i] = sum of in over [last start <= i, i], the exclusive form the same
+ * without in[i]. Types and wrap-around as ixp_scan; flags: device uint8_t[n].
+ * Workspace as ixp_scan (IXP_OP_SCAN, nseg = 0). */
+int ixp_sgm_scan(const uint8_t *flags, const void *in, int in_type, void *out, int out_type, int64_t n, int inclusive,
+                 int32_t *d_status, void *ws, size_t ws_bytes, ixp_stream stream);
+
+/* mkII  [Fig. 2 right, with the prose reading: II[j] = k for e_k <= j < e_{k+1}]:
+ * out (n = offsets[m] elements, int32 or int64) gets the segment index of every
+ * position. offsets: device int64[m + 1], offsets[0] = 0, offsets[m] = n,
+ * nondecreasing (empty segments allowed), e.g. the d_offsets of
+ * ixp_flags_from_shape. Offsets that do not end at n set *d_status = IXP_E_INVAL
+ * (d_status nullable, not cleared). Workspace: ixp_workspace_size(
+ * IXP_OP_GATHER_SEGMENTS, 0, n, 0) bytes. */
+int ixp_mkii(const int64_t *offsets, int64_t m, void *out, int out_type, int64_t n, int32_t *d_status, void *ws,
+             size_t ws_bytes, ixp_stream stream);
+
 /* ---- batched pipeline over a jagged array ---------------------------------------- */
 
 /* Launch shape of ixp_batch_run (the autotuner's search space): threads per CTA

@@ -259,9 +259,12 @@ __device__ __forceinline__ void mark_heads(unsigned *heads, const int64_t *off, 
 // ============================================================== scan kernel
 
 template <typename TI, typename TO, bool SEG>
+// SEG with `flags` set: a segment starts at every i with flags[i] != 0 (the flag
+// form of sgmSum, Fig. 2) instead of at the offsets.
 __global__ void __launch_bounds__(TB) scan_kernel(const TI *__restrict__ in, TO *__restrict__ out, int64_t n,
                                                   int inclusive, const int64_t *__restrict__ off, int64_t nseg,
-                                                  Lookback L, Hdr *h, Wait wt, TO *total_out, int vec_ok) {
+                                                  Lookback L, Hdr *h, Wait wt, TO *total_out, int vec_ok,
+                                                  const uint8_t *__restrict__ flags = nullptr) {
     IXP_KERNEL_ENTRY();
     constexpr int V = 16 / sizeof(TI);
     constexpr int TILE = TB * SUB * V;
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(TB) scan_kernel(const TI *__restrict__ in, TO 
     __syncthreads();
     const int64_t t = s_tile;
     const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
-    if (SEG) mark_heads<TILE>(heads, off, nseg, t0, t1, &s_k);
+    if (SEG && !flags) mark_heads<TILE>(heads, off, nseg, t0, t1, &s_k);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 
     unsigned long long a[SUB][V];
@@ -298,7 +301,11 @@ __global__ void __launch_bounds__(TB) scan_kernel(const TI *__restrict__ in, TO 
             for (int k = 0; k < V; k++) a[u][k] = (p0 + k < n) ? (unsigned long long)(int64_t)in[p0 + k] : 0ull;
         }
         hb[u] = 0;
-        if (SEG) {
+        if (SEG && flags) {
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (p0 + k < n && __ldg(flags + p0 + k)) hb[u] |= 1u << k;
+        } else if (SEG) {
 #pragma unroll
             for (int k = 0; k < V; k++) {
                 int r = (int)(q * V + k);
@@ -1672,6 +1679,37 @@ extern "C" int ixp_scan(const void *in, int in_type, void *out, int out_type, in
                         ws_bytes, st);
     return run_scan((const int64_t *)in, (int64_t *)out, n, inclusive, segs, (int64_t *)d_totals, d_status, ws,
                     ws_bytes, st);
+}
+
+extern "C" int ixp_sgm_scan(const uint8_t *flags, const void *in, int in_type, void *out, int out_type, int64_t n,
+                            int inclusive, int32_t *d_status, void *ws, size_t ws_bytes, ixp_stream stream) {
+    if ((in_type != IXP_I32 && in_type != IXP_I64) || (out_type != IXP_I32 && out_type != IXP_I64))
+        return IXP_E_DTYPE;
+    if (in_type == IXP_I64 && out_type == IXP_I32) return IXP_E_DTYPE;
+    if (n < 0 || (n > 0 && (!flags || !in || !out))) return IXP_E_INVAL;
+    const int es = in_type == IXP_I32 ? 4 : 8, eo = out_type == IXP_I32 ? 4 : 8;
+    if ((reinterpret_cast<uintptr_t>(in) % es) || (reinterpret_cast<uintptr_t>(out) % eo)) return IXP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int V = in_type == IXP_I32 ? 4 : 2;
+    const int64_t nt = ntiles_for(n, V);
+    TileWs W = tile_ws(ws, nt, 0);
+    int rc = ws_ok(ws, ws_bytes, W.bytes);
+    if (rc) return rc;
+    if (cudaMemsetAsync(ws, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (nt > 0 && cudaMemsetAsync(W.L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return IXP_E_CUDA;
+    const Wait wt = wait_config();
+    if (nt > 0) {
+#define IXP_SGM(TI, TO)                                                                                          \
+    scan_kernel<TI, TO, true><<<(unsigned)nt, TB, 0, st>>>((const TI *)in, (TO *)out, n, inclusive, nullptr, 0, W.L, \
+                                                           W.h, wt, nullptr, aligned16(in) && aligned16(out), flags)
+        if (in_type == IXP_I32 && out_type == IXP_I32) IXP_SGM(int32_t, int32_t);
+        else if (in_type == IXP_I32) IXP_SGM(int32_t, int64_t);
+        else IXP_SGM(int64_t, int64_t);
+#undef IXP_SGM
+    }
+    if (d_status) status_copy_kernel<<<1, 1, 0, st>>>(W.h, d_status);
+    return launch_status();
 }
 
 extern "C" int ixp_partition(const void *keys, int ktype, int64_t n, ixp_pred pred, const void *payload,

@@ -383,6 +383,66 @@ __global__ void __launch_bounds__(GS_THREADS) gather_segments_kernel(E *__restri
     if (oob && status) atomicCAS(status, 0, IXP_E_INVAL);
 }
 
+// mkII (Fig. 2): out[j] = k for out_off[k] <= j < out_off[k+1], by chunks like the
+// segment gather (the chunk's first segment from the table, the starts of the
+// non-empty segments inside it in a bitmap, and the segment of each start by its
+// rank among them).
+template <typename OT>
+__global__ void __launch_bounds__(GS_THREADS) segment_ids_kernel(OT *__restrict__ out,
+                                                                 const int64_t *__restrict__ out_off, int64_t m,
+                                                                 int64_t n, const int64_t *__restrict__ k0tab,
+                                                                 int32_t *status) {
+    IXP_KERNEL_ENTRY();
+    __shared__ int64_t s_seg[GS_CHUNK];
+    __shared__ unsigned s_head[GS_WORDS];
+    __shared__ unsigned s_pre[GS_WORDS];
+    const int64_t j0 = blockIdx.x * (int64_t)GS_CHUNK;
+    if (j0 >= n) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (__ldg(out_off + m) != n || __ldg(out_off) != 0) && status)
+        atomicCAS(status, 0, IXP_E_INVAL);
+    const int cnt = (int)min((int64_t)GS_CHUNK, n - j0);
+    for (int w = threadIdx.x; w < GS_WORDS; w += GS_THREADS) s_head[w] = 0u;
+    int64_t k0 = __ldg(k0tab + blockIdx.x);
+    k0 = k0 < 0 ? 0 : (k0 >= m ? m - 1 : k0);
+    if (threadIdx.x == 0) s_seg[0] = k0;
+    __syncthreads();
+    for (int64_t k = k0 + 1 + threadIdx.x; k < m; k += GS_THREADS) {
+        const int64_t a = __ldg(out_off + k);
+        if (a >= j0 + cnt) break;
+        if (a > j0 && __ldg(out_off + k + 1) > a) atomicOr(&s_head[(a - j0) >> 5], 1u << ((a - j0) & 31));
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        constexpr int PW = GS_WORDS / 32;
+        unsigned c[PW], run = 0;
+#pragma unroll
+        for (int i = 0; i < PW; i++) {
+            c[i] = __popc(s_head[threadIdx.x * PW + i]);
+            run += c[i];
+        }
+        unsigned y = run;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(FULL, y, d);
+            if ((int)threadIdx.x >= d) y += o;
+        }
+        unsigned pre = y - run;
+#pragma unroll
+        for (int i = 0; i < PW; i++) {
+            s_pre[threadIdx.x * PW + i] = pre;
+            pre += c[i];
+        }
+    }
+    __syncthreads();
+    for (int64_t k = k0 + 1 + threadIdx.x; k < m; k += GS_THREADS) {
+        const int64_t a = __ldg(out_off + k);
+        if (a >= j0 + cnt) break;
+        if (a > j0 && __ldg(out_off + k + 1) > a) s_seg[gs_heads_upto(s_head, s_pre, (int)(a - j0))] = k;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < cnt; e += GS_THREADS) out[j0 + e] = (OT)s_seg[gs_heads_upto(s_head, s_pre, e)];
+}
+
 static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 static int row_grid(int64_t n) { return stream_grid(n, 1); }
@@ -554,6 +614,26 @@ extern "C" int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_
     else if (seg_type == IXP_I32) IXP_GS(unsigned long long, int32_t);
     else IXP_GS(unsigned long long, int64_t);
 #undef IXP_GS
+    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+}
+
+extern "C" int ixp_mkii(const int64_t *offsets, int64_t m, void *out, int out_type, int64_t n, int32_t *d_status,
+                        void *ws, size_t ws_bytes, ixp_stream stream) {
+    if (out_type != IXP_I32 && out_type != IXP_I64) return IXP_E_DTYPE;
+    if (m < 0 || n < 0 || !offsets || (n > 0 && (m == 0 || !out))) return IXP_E_INVAL;
+    if (out_type == IXP_I32 && m > INT32_MAX) return IXP_E_INVAL;
+    if (!al(out, out_type == IXP_I32 ? 4 : 8)) return IXP_E_INVAL;
+    if (n == 0) return IXP_OK;
+    if (!ws || !al(ws, 256) || ws_bytes < gather_segments_ws_bytes(n)) return IXP_E_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t *k0 = (int64_t *)ws;
+    const unsigned g = (unsigned)((n + GS_CHUNK - 1) / GS_CHUNK);
+    if (cudaMemsetAsync(k0, 0xff, (size_t)g * 8, st) != cudaSuccess) return IXP_E_CUDA;
+    gs_chunk_table_kernel<<<stream_grid(m, 4), STREAM_THREADS, 0, st>>>(offsets, m, n, k0);
+    if (out_type == IXP_I32)
+        segment_ids_kernel<int32_t><<<g, GS_THREADS, 0, st>>>((int32_t *)out, offsets, m, n, k0, d_status);
+    else
+        segment_ids_kernel<int64_t><<<g, GS_THREADS, 0, st>>>((int64_t *)out, offsets, m, n, k0, d_status);
     return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
 }
 

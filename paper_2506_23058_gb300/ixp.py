@@ -75,6 +75,8 @@ _SIGS = {
     "ixp_gather_segments": (_I, [_P, _L, _P, _L, _P, _L, _P, _L, _P, _I, C.c_int32, _P, _P, _Z, _P]),
     "ixp_check_filtpart_classes": (_I, [_P, _I, _L, _P, _I, Pred, _P, C.c_int32, Segs, _P, _P, _Z, _P]),
     "ixp_filtpart_classes": (_I, [_P, _I, _L, Pred, _P, C.c_int32, Segs, _P, _I, _P, _P, _Z, _P]),
+    "ixp_sgm_scan": (_I, [_P, _P, _I, _P, _I, _L, _I, _P, _P, _Z, _P]),
+    "ixp_mkii": (_I, [_P, _L, _P, _I, _L, _P, _P, _Z, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
     "ixp_kernel_launches": (C.c_ulonglong, []),
@@ -435,6 +437,31 @@ def gather_segments(src, src_off, seg_src, out_off, n_out, *, out=None, status=N
                                    _dev(seg_src, "seg_src"), _itype(seg_src), src.element_size(), status.data_ptr(),
                                    ws.data_ptr() if ws.numel() else None, ws.numel(), _stream(stream)),
         "gather_segments")
+    return out, status
+
+
+def sgm_scan(flags, x, out_dtype=None, inclusive=True, *, out=None, status=None, ws=None, stream=None):
+    """sgmSum: scan that restarts at every flagged position. Returns (out, status)."""
+    out_dtype = out_dtype or x.dtype
+    n = x.numel()
+    out = out if out is not None else torch.empty(n, dtype=out_dtype, device=x.device)
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=x.device)
+    need = workspace_size("scan", _itype(x), n, 0)
+    ws = ws if ws is not None else workspace(need, x.device)
+    _ck(load().ixp_sgm_scan(_dev(flags, "flags"), _dev(x, "x"), _itype(x), out.data_ptr(), _itype(out), n,
+                            int(inclusive), status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "sgm_scan")
+    return out, status
+
+
+def mkii(offsets, n, out_dtype=torch.int32, *, out=None, status=None, ws=None, stream=None):
+    """Segment index of every position: out[j] = k for offsets[k] <= j < offsets[k+1]."""
+    m = offsets.numel() - 1
+    out = out if out is not None else torch.empty(n, dtype=out_dtype, device=offsets.device)
+    status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=offsets.device)
+    need = workspace_size("gather_segments", 0, n)
+    ws = ws if ws is not None else workspace(need, offsets.device)
+    _ck(load().ixp_mkii(_dev(offsets, "offsets"), m, out.data_ptr() if n else None, _itype(out), n, status.data_ptr(),
+                        ws.data_ptr(), ws.numel(), _stream(stream)), "mkii")
     return out, status
 
 

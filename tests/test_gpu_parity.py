@@ -667,3 +667,32 @@ def test_filtpart_classes_index_form(ixp, dev, n, m, v, ot):
     assert int(nk.item()) == int(kept.sum())
     vd = oracle.check_filtpart(ref.astype(ot), keys, filt=filt, cls=cls, v=v, offsets=None if m == 0 else off)
     assert vd["ok"]
+
+
+@pytest.mark.parametrize("it,ot", [(np.int32, np.int32), (np.int32, np.int64), (np.int64, np.int64)])
+@pytest.mark.parametrize("n", [0, 1, 33, 4097, 100003, 1 << 20])
+def test_sgm_scan_flags(ixp, dev, n, it, ot):
+    """sgmSum over a flag array, inclusive (the oracle's literal operator) and
+    exclusive (inclusive minus the element), flags at 0, sparse and dense."""
+    rng = np.random.default_rng(n + 5)
+    x = rng.integers(-1000, 1000, size=n).astype(it)
+    for p in (0.0, 0.01, 0.5):
+        fl = (rng.random(n) < p).astype(np.uint8)
+        inc, st = ixp.sgm_scan(T(fl, dev), T(x, dev), out_dtype=getattr(torch, np.dtype(ot).name), inclusive=True)
+        ref = oracle.sgm_scan(fl, x, out_dtype=ot)
+        assert st.item() == 0 and np.array_equal(inc.cpu().numpy(), ref), (n, p)
+        exc, _ = ixp.sgm_scan(T(fl, dev), T(x, dev), out_dtype=getattr(torch, np.dtype(ot).name), inclusive=False)
+        assert np.array_equal(exc.cpu().numpy(), (ref - x.astype(ot)).astype(ot)), (n, p)
+
+
+@pytest.mark.parametrize("ot", [np.int32, np.int64])
+@pytest.mark.parametrize("m,maxlen,p_empty", [(1, 5, 0.0), (1000, 40, 0.3), (20000, 300, 0.5), (300, 20000, 0.2)])
+def test_mkii(ixp, dev, m, maxlen, p_empty, ot):
+    rng = np.random.default_rng(m + maxlen)
+    shape = rng.integers(0, maxlen, size=m).astype(np.int64)
+    shape[rng.random(m) < p_empty] = 0
+    off = synth.offsets_from_shape(shape)
+    n = int(off[-1])
+    ii, st = ixp.mkii(T(off, dev), n, out_dtype=getattr(torch, np.dtype(ot).name))
+    assert st.item() == 0
+    assert np.array_equal(ii.cpu().numpy(), oracle.mkii(shape).astype(ot))
