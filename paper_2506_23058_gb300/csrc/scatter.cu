@@ -165,7 +165,7 @@ template <typename IT>
 __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double *__restrict__ acc, int64_t dst_len,
                                                                          const IT *__restrict__ idx,
                                                                          const float *__restrict__ vals, int64_t n,
-                                                                         int row_elems) {
+                                                                         int row_elems, int vec16) {
     IXP_KERNEL_ENTRY();
     __shared__ unsigned long long s_tag[HOT_SLOTS];  // ~0 = free
     __shared__ double s_row[HOT_SLOTS][HOT_COLS];
@@ -194,7 +194,15 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double 
                     const unsigned long long prev = atomicCAS(&s_tag[sl], ~0ull, (unsigned long long)d);
                     tag = prev == ~0ull ? (unsigned long long)d : prev;
                 }
-                if (tag == (unsigned long long)d) {
+                float v[HOT_COLS];
+                if (row_elems == HOT_COLS && vec16) {  // the common [n x 8] case: two 16-byte loads, unrolled adds
+                    const float4 a = __ldcs(reinterpret_cast<const float4 *>(vals + i * HOT_COLS));
+                    const float4 b = __ldcs(reinterpret_cast<const float4 *>(vals + i * HOT_COLS) + 1);
+                    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+                    double *t = tag == (unsigned long long)d ? &s_row[sl][0] : acc + d * HOT_COLS;
+#pragma unroll
+                    for (int c = 0; c < HOT_COLS; c++) atomicAdd(t + c, (double)v[c]);
+                } else if (tag == (unsigned long long)d) {
                     for (int c = 0; c < row_elems; c++) atomicAdd(&s_row[sl][c], (double)vals[i * row_elems + c]);
                 } else {
                     for (int c = 0; c < row_elems; c++) atomicAdd(acc + d * row_elems + c, (double)vals[i * row_elems + c]);
@@ -504,12 +512,13 @@ extern "C" int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const vo
     if (n == 0) return IXP_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int g = row_grid(n);
+    const int v16 = al(vals, 16);
     if (itype == IXP_I32)
         scatter_add_f64_kernel<int32_t><<<g, STREAM_THREADS, 0, st>>>(acc, dst_len, (const int32_t *)idx, vals, n,
-                                                                      row_elems);
+                                                                      row_elems, v16);
     else
         scatter_add_f64_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>(acc, dst_len, (const int64_t *)idx, vals, n,
-                                                                      row_elems);
+                                                                      row_elems, v16);
     return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
 }
 
