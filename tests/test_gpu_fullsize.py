@@ -123,3 +123,93 @@ def test_scatter_gather_full_size(ixp, dev):
     smp = rng.choice(nr, size=4096, replace=False)
     ph, sh, yh = perm.cpu().numpy(), src.cpu().numpy(), y.cpu().numpy()
     assert np.array_equal(yh[smp], sh[ph[smp]])
+
+
+def test_batched_full_size(ixp, dev):
+    """The batched workload at full size (4096 log-uniform segments, 2^28 elements)
+    from the graph-captured persistent launch: flags and offsets against the oracle's
+    mkSgmDescr, per-segment verdicts against the planted segments, num_true and
+    sampled partition destinations against the definition."""
+    from paper_2506_23058_gb300 import batched
+    s = synth.seed_for(3) + 200
+    m = 4096
+    shape = synth.shapes_log_uniform(m, s, max_log2=20, cap_total=1 << 28)
+    n = int(shape.sum())
+    off = synth.offsets_from_shape(shape)
+    sh = torch.from_numpy(shape).to(dev)
+    seg = torch.repeat_interleave(torch.arange(m, device=dev, dtype=torch.int64), sh)
+    g = torch.Generator(device=dev)
+    g.manual_seed(s + 1)
+    r = torch.randint(0, 2**31, (n,), generator=g, device=dev, dtype=torch.int64)
+    chk = torch.argsort(seg * (2**31) + r).to(torch.int32)  # a permutation of each segment's range
+    offd = torch.from_numpy(off).to(dev)
+    iota = (torch.arange(n, device=dev, dtype=torch.int64) - offd[seg]).to(torch.int32)
+    del r, seg
+    rng = np.random.default_rng(s + 2)
+    planted = np.sort(rng.choice(np.flatnonzero(shape >= 3), size=41, replace=False))
+    mono_bad, inj_bad = [], []
+    for k in planted:
+        i = int(off[k]) + int(rng.integers(1, int(shape[k])))
+        if k % 2:
+            chk[i] = chk[i - 1]
+            inj_bad.append(int(k))
+        else:
+            iota[i] = iota[i - 1]
+            mono_bad.append(int(k))
+    keys = synth.t_keys_uniform(n, s + 3, dev)
+    thr = synth.bernoulli_threshold(0.3)
+    br = batched.BatchRunner(shape, keys, ("lt", 0, thr), chk, iota)
+    br.capture()
+    br.replay()
+    torch.cuda.synchronize()
+    res = br.results()
+    assert res["status"] == 0
+    o_flags, o_off = oracle.flags_from_shape(shape, None, out_dtype=np.int32)
+    assert np.array_equal(res["offsets"].cpu().numpy(), o_off)
+    assert np.array_equal(res["flags"].cpu().numpy(), o_flags)
+    exp_mono = np.ones(m, np.uint8)
+    exp_mono[mono_bad] = 0
+    exp_inj = np.ones(m, np.uint8)
+    exp_inj[inj_bad] = 0
+    assert np.array_equal(res["mono_ok"], exp_mono)
+    assert np.array_equal(res["inj_ok"], exp_inj)
+    assert np.array_equal(res["bij_ok"], exp_inj)  # a repeat inside the segment's own range breaks Bij too
+    assert res["first_bad"] == [mono_bad[0], inj_bad[0], inj_bad[0]]
+    kh = keys.cpu().numpy()
+    c = kh < thr
+    segh = np.repeat(np.arange(m), shape)
+    T = np.bincount(segh, weights=c, minlength=m).astype(np.int64)
+    assert np.array_equal(res["num_true"].cpu().numpy(), T)
+    cs = np.cumsum(c, dtype=np.int64) - c  # trues before i overall
+    smp = np.sort(rng.choice(n, size=4096, replace=False))
+    k = segh[smp]
+    tb = cs[smp] - cs[off[k]]  # trues before i in its segment
+    exp = np.where(c[smp], off[k] + tb, off[k] + T[k] + (smp - off[k]) - tb)
+    assert np.array_equal(res["indices"].cpu().numpy()[smp].astype(np.int64), exp)
+
+
+def test_differentiation_full_size(ixp, dev):
+    """Config 4 at full size: the injective gather's gradient (through the inverse
+    index) equals the scatter of the output gradient; the Zipf(1.1) scatter-add over
+    2^20 targets against the oracle's float64 sums (relative 1e-6 of the sum of
+    magnitudes), on all targets."""
+    from paper_2506_23058_gb300 import autograd
+    nr, m = 1 << 26, 1 << 20
+    perm = synth.t_permutation(nr, synth.seed_for(4) + 1, dev, torch.int32)
+    src = synth.t_payload_f32(nr, synth.seed_for(4) + 2, dev, cols=8).requires_grad_(True)
+    inv = ixp.invert(perm, nr)
+    y = autograd.gather(src, perm, inverse=inv)
+    gy = synth.t_payload_f32(nr, synth.seed_for(4) + 3, dev, cols=8)
+    (gs,) = torch.autograd.grad(y, src, gy)
+    ref = torch.zeros_like(gs)
+    ixp.scatter(ref, perm, gy)
+    assert torch.equal(gs, ref)
+    zipf = synth.zipf_ranks(nr, m, 1.1, synth.seed_for(4) + 4)
+    vals = synth.t_payload_f32(nr, synth.seed_for(4) + 5, dev, cols=8)
+    dst = torch.zeros((m, 8), dtype=torch.float32, device=dev)
+    out = autograd.scatter_add(dst, torch.from_numpy(zipf).to(dev), vals)
+    vh = vals.cpu().numpy()
+    r64 = oracle.scatter_add_f64(m, zipf, vh)
+    a64 = oracle.scatter_add_f64(m, zipf, np.abs(vh))
+    got = out.detach().cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - r64) <= 1e-6 * np.maximum(np.abs(r64), a64) + 1e-30)
