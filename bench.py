@@ -312,6 +312,14 @@ def dist_env():
     return ws, rank, local
 
 
+def arm_config(n32, n64, small, world):
+    """The workload both arms name in their JSON line."""
+    return {"workload": "plain-small: i32 n=2^26, i64 n=2^25" if small else
+            "plain-large: i32 n=2^28, i64 n=2^27, partition 2^28 keys + f32 payload (p=0.5, 0.01)",
+            "n_i32": n32, "n_i64": n64, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (129 MB); no flush"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -324,13 +332,13 @@ def run_reference(args):
     total = sum(oracle_step(inp, ops) for _ in range(args.steps))
     dt = time.perf_counter() - t0
     cb = {"value": round(total / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-          "sample": "each step = one pass of the op mix at n=2^24 (int32) / 2^23 (int64) = 1/16 of the workload"}
+          "sample": "each step = one pass of the op mix at n=2^24 (int32) / 2^23 (int64) = 1/16 of the workload; "
+                    "value = algorithmic bytes of the sample / time"}
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GB/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 1),
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64 (index), f32 payload",
-            "data": "synthetic", "config": {"workload": "plain-large (oracle sample)", "n_i32": SAMPLE_N32,
-                                            "n_i64": SAMPLE_N64},
+            "data": "synthetic", "config": arm_config(1 << 28, 1 << 27, False, args.gpus),
             "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -467,10 +475,7 @@ def main():
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/int64 (index), f32 payload", "data": "synthetic",
-            "config": {"workload": "plain-large: i32 n=2^28, i64 n=2^27, partition 2^28 keys + f32 payload "
-                                   "(p=0.5, 0.01)" if not args.small else "plain-small: i32 n=2^26, i64 n=2^25",
-                       "n_i32": n32, "n_i64": n64, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (129 MB); no flush"},
+            "config": arm_config(n32, n64, args.small, world),
             "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "ops": per_op,
             "verdicts": checks}
     if e2e is not None:
