@@ -312,6 +312,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, device, world):
+    """The slowest rank's time (every rank gets it); the identity for one process."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(step_bytes, steps, total_ms, world):
+    """Whole-job GB/s: every replica processes step_bytes per step (weak scaling)."""
+    return world * step_bytes * steps / (total_ms / 1e3) / 1e9
+
+
 def arm_config(n32, n64, small, world):
     """The workload both arms name in their JSON line."""
     return {"workload": "plain-small: i32 n=2^26, i64 n=2^25" if small else
@@ -415,14 +430,10 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     launches = ixp.load().ixp_kernel_launches() - launches0
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), dev, world)
     ms_step = total_ms / args.steps
     step_bytes = sum(o[3] for o in ops)
-    value = world * step_bytes * args.steps / (total_ms / 1e3) / 1e9
+    value = job_value(step_bytes, args.steps, total_ms, world)
 
     # per-op times (mean over timed steps)
     per_op = {}
