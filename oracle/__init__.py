@@ -278,3 +278,29 @@ def mkii(shape):
     out = np.empty(total, dtype=np.int64)
     _check(lib().ixo_mkii(_ptr(shape), C.c_int64(shape.shape[0]), _ptr(out), C.c_int64(total)))
     return out
+
+
+def hist_min(m, idx, vals=None, init=None, dtype=np.int64):
+    """Reduce-by-index with min: H = init (default: the dtype's maximum) lowered by
+    vals[i] at idx[i] for in-bounds indices; vals None means vals[i] = i."""
+    idx = np.ascontiguousarray(idx)
+    if init is None:
+        H = np.full(m, np.iinfo(np.dtype(dtype)).max, dtype=np.dtype(dtype))
+    else:
+        H = np.array(init, dtype=np.dtype(dtype), copy=True, order="C")
+    v = None if vals is None else np.ascontiguousarray(vals, dtype=H.dtype)
+    _check(lib().ixo_hist_min(_ptr(H), _itype(H), C.c_int64(m), _ptr(idx), _itype(idx), _ptr(v),
+                              C.c_int64(idx.shape[0])))
+    return H
+
+
+def smallest_pairs(n_verts, n_es, es, is_):
+    """get_smallest_pairs of maxMatching: returns (es', is') kept in input order."""
+    es = np.ascontiguousarray(es)
+    is_ = np.ascontiguousarray(is_, dtype=es.dtype)
+    n = es.shape[0]
+    oe, oi = np.empty(n, es.dtype), np.empty(n, es.dtype)
+    cnt = C.c_int64(0)
+    _check(lib().ixo_smallest_pairs(C.c_int64(n_verts), C.c_int64(n_es), _ptr(es), _ptr(is_), _itype(es),
+                                    C.c_int64(n), _ptr(oe), _ptr(oi), C.byref(cnt)))
+    return oe[:cnt.value].copy(), oi[:cnt.value].copy()

@@ -811,3 +811,72 @@ int ixo_mkii(const int64_t *shape, int64_t m, int64_t *out, int64_t out_len)
     free(beg); free(sct1); free(sct); free(flags);
     return rc;
 }
+
+/* ------------------------------------------------------------- hist min
+ * Reduce-by-index with min, Futhark's `hist` with the min operator (Sec. 7:
+ * get_smallest_pairs of maxMatching, Fig. 9, and the reduce-by-index that the
+ * dynamic verification of scatter needs). H holds the neutral element on entry
+ * (the caller fills it); for i = 0..n-1 in order, if 0 <= idx[i] < m then
+ * H[idx[i]] = min(H[idx[i]], vals[i]). vals NULL means vals[i] = i. An index out of
+ * bounds is ignored, as scatter ignores it (Sec. 2.1). H and vals share type ht. */
+int ixo_hist_min(void *H, int ht, int64_t m, const void *idx, int it, const void *vals, int64_t n)
+{
+    if (bad_type(ht) || bad_type(it))
+        return IXO_E_DTYPE;
+    if (n < 0 || m < 0 || (n > 0 && !idx) || (m > 0 && !H))
+        return IXO_E_INVAL;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t k = get(idx, it, i);
+        if (k < 0 || k >= m)
+            continue;
+        int64_t v = vals ? get(vals, ht, i) : i;
+        if (v < get(H, ht, k))
+            put(H, ht, k, (uint64_t)v);
+    }
+    return IXO_OK;
+}
+
+/* -------------------------------------------------- get_smallest_pairs
+ * Fig. 9 (left), step by step: H = hist min n_es n_verts es is; cs[i] = (H[es[i]]
+ * == is[i]); xs = filter cs es; ys = filter cs is (filter_by keeps the flagged
+ * elements in input order, FiltPart with p^f = cs and one part). es and is share
+ * type t. Reading: the precondition Range es (0, n_verts) is half-open (es indexes
+ * H, which has n_verts bins); an es[i] outside it has no bin, the hist ignores it
+ * and cs[i] is false. out_es and out_is have room for n entries; *count gets the
+ * number kept. */
+int ixo_smallest_pairs(int64_t n_verts, int64_t n_es, const void *es, const void *is, int t, int64_t n,
+                       void *out_es, void *out_is, int64_t *count)
+{
+    if (bad_type(t))
+        return IXO_E_DTYPE;
+    if (n < 0 || n_verts < 0 || (n > 0 && (!es || !is || !out_es || !out_is)) || !count)
+        return IXO_E_INVAL;
+    void *H = malloc((size_t)(n_verts > 0 ? n_verts : 1) * 8);
+    if (!H)
+        return IXO_E_NOMEM;
+    for (int64_t k = 0; k < n_verts; k++)
+        put(H, 1, k, (uint64_t)n_es);
+    /* the hist runs in 64 bits: is values widen exactly, and n_es may exceed them */
+    int64_t *is64 = calloc((size_t)(n > 0 ? n : 1), 8);
+    if (!is64) {
+        free(H);
+        return IXO_E_NOMEM;
+    }
+    for (int64_t i = 0; i < n; i++)
+        is64[i] = get(is, t, i);
+    int rc = ixo_hist_min(H, 1, n_verts, es, t, is64, n);
+    int64_t c = 0;
+    for (int64_t i = 0; rc == IXO_OK && i < n; i++) {
+        int64_t v = get(es, t, i);
+        int keep = v >= 0 && v < n_verts && get(H, 1, v) == is64[i];
+        if (keep) {
+            put(out_es, t, c, (uint64_t)v);
+            put(out_is, t, c, (uint64_t)is64[i]);
+            c++;
+        }
+    }
+    *count = c;
+    free(is64);
+    free(H);
+    return rc;
+}

@@ -21,6 +21,10 @@ use):
   * payload             - float32 uniform in [-1, 1)
   * segment shapes      - log-uniform in [1, 2^20] (batched), Pareto rows (CSR)
   * Zipf(s) targets     - inverse-CDF draw of ranks over m targets
+  * unit floats         - float32 uniform in [0, 1) (partition2's "random floats")
+  * graph slots         - edge endpoints es uniform over [0, n_verts) (or Zipf
+                          ranks for a skewed degree law), priorities is a uniform
+                          random permutation of [0, n) (injective)
 """
 from __future__ import annotations
 
@@ -104,6 +108,19 @@ def bernoulli_threshold(p: float) -> int:
 def payload_f32(n: int, seed: int, cols: int = 1) -> np.ndarray:
     shape = (n,) if cols == 1 else (n, cols)
     return _rng(seed).uniform(-1.0, 1.0, size=shape).astype(np.float32)
+
+
+def floats_unit(n: int, seed: int) -> np.ndarray:
+    return _rng(seed).random(n, dtype=np.float32)
+
+
+def graph_slots(n: int, n_verts: int, seed: int, dtype=np.int64, zipf_s: float = 0.0):
+    """(es, is): n edge-endpoint slots over n_verts vertices and injective priorities."""
+    if zipf_s > 0.0:
+        es = zipf_ranks(n, max(n_verts, 1), zipf_s, seed).astype(dtype)
+    else:
+        es = _rng(seed).integers(0, max(n_verts, 1), size=n, dtype=np.int64).astype(dtype)
+    return es, permutation(n, seed + 1, dtype)
 
 
 def class_ids(n: int, seed: int, v: int) -> np.ndarray:
@@ -201,6 +218,20 @@ def t_payload_f32(n: int, seed: int, device, cols: int = 1):
     import torch
     shape = (n,) if cols == 1 else (n, cols)
     return torch.rand(shape, generator=_torch_gen(seed, device), device=device, dtype=torch.float32) * 2.0 - 1.0
+
+
+def t_floats_unit(n: int, seed: int, device):
+    import torch
+    return torch.rand(n, generator=_torch_gen(seed, device), device=device, dtype=torch.float32)
+
+
+def t_graph_slots(n: int, n_verts: int, seed: int, device, dtype=None):
+    """Device version of graph_slots (uniform endpoints, torch's generator)."""
+    import torch
+    dtype = dtype or torch.int64
+    es = torch.randint(0, max(n_verts, 1), (n,), generator=_torch_gen(seed, device), device=device,
+                       dtype=torch.int64).to(dtype)
+    return es, t_permutation(n, seed + 1, device, dtype)
 
 
 def t_shapes_pareto(m: int, seed: int, device, alpha: float = 2.0, xmin: float = 1.5, max_len: int = 2**16):

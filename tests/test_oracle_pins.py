@@ -420,3 +420,85 @@ def test_flags_from_shape_brute_force():
 def test_flags_from_shape_rejects_negative_shape():
     with pytest.raises(oracle.OracleError):
         oracle.flags_from_shape(np.array([1, -1, 2]))
+
+
+# ------------------------------------------------- reduce-by-index (hist) with min
+
+def test_hist_min_matches_numpy_minimum_at():
+    rng = np.random.default_rng(71)
+    for dt in (np.int32, np.int64):
+        for m in (0, 1, 7, 300):
+            n = int(rng.integers(0, 2000))
+            idx = rng.integers(-20, m + 20, size=n).astype(dt)  # out of bounds on both sides
+            vals = rng.integers(-10**6, 10**6, size=n).astype(dt)
+            init = rng.integers(-10**5, 10**6, size=m).astype(dt)
+            got = oracle.hist_min(m, idx, vals, init=init, dtype=dt)
+            ref = init.copy()
+            ok = (idx >= 0) & (idx < m)
+            np.minimum.at(ref, idx[ok].astype(np.int64), vals[ok])
+            assert got.dtype == dt and np.array_equal(got, ref)
+
+
+def test_hist_min_of_iota_is_the_first_occurrence():
+    rng = np.random.default_rng(72)
+    idx = rng.integers(0, 50, size=400).astype(np.int64)
+    H = oracle.hist_min(60, idx, init=np.full(60, 400))
+    u, first = np.unique(idx, return_index=True)
+    ref = np.full(60, 400)
+    ref[u] = first
+    assert np.array_equal(H, ref)
+
+
+def test_dynamic_scatter_check_by_hist_decides_inj():
+    """The dynamic verification of a scatter (Sec. 7): with H = hist min of iota by
+    the indices, Inj on [0, m) holds iff every in-bounds i has H[idx[i]] == i; the
+    first occurrence of the earliest repeated value is min H over the violations."""
+    rng = np.random.default_rng(73)
+    for _ in range(300):
+        m = int(rng.integers(1, 40))
+        n = int(rng.integers(0, 30))
+        idx = rng.integers(-3, m + 3, size=n).astype(np.int64)
+        H = oracle.hist_min(m, idx, init=np.full(m, n))
+        ok = (idx >= 0) & (idx < m)
+        bad = [i for i in range(n) if ok[i] and H[idx[i]] != i]
+        v = oracle.check_inj(idx, 0, m - 1)
+        assert v["ok"] == (not bad)
+        if bad:
+            i0 = min(int(H[idx[i]]) for i in bad)
+            j0 = min(i for i in bad if H[idx[i]] == i0)
+            assert (v["index"], v["aux0"], v["value"]) == (i0, j0, idx[i0])
+
+
+def _smallest_pairs_brute(nv, n_es, es, is_):
+    keep = []
+    for i in range(len(es)):
+        if not (0 <= es[i] < nv):
+            continue
+        h = min([n_es] + [int(is_[j]) for j in range(len(es)) if es[j] == es[i]])
+        if h == is_[i]:
+            keep.append(i)
+    return es[keep], is_[keep]
+
+
+def test_smallest_pairs_brute_force_and_postcondition():
+    """get_smallest_pairs (Fig. 9) against its definition written as an all-pairs
+    loop, and its postcondition: with is injective, es' and is' are injective and es'
+    holds each vertex that occurs in es exactly once."""
+    rng = np.random.default_rng(74)
+    for dt in (np.int32, np.int64):
+        for _ in range(150):
+            nv = int(rng.integers(0, 12))
+            n = int(rng.integers(0, 40))
+            es = rng.integers(-2, nv + 2, size=n).astype(dt)
+            is_ = rng.permutation(n * 2)[:n].astype(dt)  # injective
+            n_es = int(rng.integers(n, 3 * n + 1))
+            oe, oi = oracle.smallest_pairs(nv, n_es, es, is_)
+            be, bi = _smallest_pairs_brute(nv, n_es, es, is_)
+            assert oe.dtype == dt and np.array_equal(oe, be) and np.array_equal(oi, bi)
+            assert oracle.check_inj(oe)["ok"] and oracle.check_inj(oi)["ok"]
+            if n_es >= 2 * n:  # every is value is below the neutral element
+                inb = es[(es >= 0) & (es < nv)]
+                assert np.array_equal(np.sort(oe), np.unique(inb))
+    # the neutral element takes part in the min: values at or above it never win
+    oe, oi = oracle.smallest_pairs(2, 5, np.array([0, 0, 1], np.int64), np.array([7, 5, 6], np.int64))
+    assert oe.tolist() == [0] and oi.tolist() == [5]
