@@ -482,6 +482,10 @@ def main():
             del inp, R
             torch.cuda.empty_cache()
             extras["csr"] = run_csr(ixp, dev, plain_ns_per_byte)
+            torch.cuda.empty_cache()
+            extras["partition2"] = run_partition2(ixp, dev)
+            torch.cuda.empty_cache()
+            extras["smallest_pairs"] = run_matching(ixp, dev)
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
@@ -668,6 +672,86 @@ def run_csr(ixp, dev, plain_ns_per_byte):
             "bwd_ms": round(bwd, 4), "bwd_gbs": round(bbytes / (bwd / 1e3) / 1e9, 1),
             "verdicts": {"offsets_mono": vo["ok"], "seg_inj": vi["ok"], "seg_mono": vm["ok"],
                          "first_planted_row": int(planted[0])}}
+
+
+def run_partition2(ixp, dev):
+    """partition2 (Fig. 2) of float32 uniform in [0, 1) by x < 0.5 at the sizes of
+    the paper's GPU measurement (50M, 100M, 200M elements, Sec. 7), three ways:
+    dynamic (the index array materialised, its injectivity decided by
+    reduce-by-index with min, then the scatter into a zeroed destination), static
+    (the fused partition into a zeroed destination) and static without the
+    initialisation. The float compare runs on the bit patterns, which order like
+    the values for non-negative floats."""
+    import torch
+    thr = int(np.float32(0.5).view(np.int32))
+    pred = ("lt", 0, thr)
+    out = {"workload": "float32 uniform [0,1), predicate x < 0.5; dynamic = partition indices + "
+                       "reduce-by-index Inj check + zero-init + scatter"}
+    for n in (50_000_000, 100_000_000, 200_000_000):
+        x = synth.t_floats_unit(n, synth.seed_for(7) + n // 1_000_000, dev)
+        bits = x.view(torch.int32)
+        ys = torch.empty_like(x)
+        ys_bits = ys.view(torch.int32)
+        idx = torch.empty(n, dtype=torch.int32, device=dev)
+        nt = torch.empty(1, dtype=torch.int64, device=dev)
+        vd = torch.empty(6, dtype=torch.int64, device=dev)
+
+        def dynamic():
+            ixp.partition(bits, pred, out=idx, want_keys=False, num_true=nt)
+            ixp.check_inj_hist(idx, n, out=vd)
+            ys.zero_()
+            ixp.scatter(ys, idx, x)
+
+        def static():
+            ys.zero_()
+            ixp.partition(bits, pred, want_indices=False, out_keys=ys_bits, num_true=nt)
+
+        def static_noinit():
+            ixp.partition(bits, pred, want_indices=False, out_keys=ys_bits, num_true=nt)
+
+        t_dyn = _time(dynamic)
+        y_dyn = ys.clone()
+        ok = ixp.Verdict(vd).get()["ok"]
+        t_st = _time(static)
+        same = bool(torch.equal(ys, y_dyn))
+        t_no = _time(static_noinit)
+        same = same and bool(torch.equal(ys, y_dyn))
+        del y_dyn
+        out["n=%d" % n] = {"dynamic_ms": round(t_dyn, 4), "static_ms": round(t_st, 4),
+                           "static_noinit_ms": round(t_no, 4),
+                           "speedup_static": round(t_dyn / t_st, 2), "speedup_noinit": round(t_dyn / t_no, 2),
+                           "static_noinit_gelem_s": round(n / (t_no / 1e3) / 1e9, 1),
+                           "inj_ok": ok, "outputs_equal": same}
+        del x, bits, ys, ys_bits, idx
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_matching(ixp, dev):
+    """get_smallest_pairs of maxMatching (Fig. 9) on a random graph: 2^26 int64
+    edge-endpoint slots over 2^23 vertices (uniform endpoints, 8 slots per vertex),
+    injective priorities; then the paper's postcondition, Inj of both outputs,
+    checked at run time."""
+    import torch
+    n_verts, n = 1 << 23, 1 << 26
+    es, is_ = synth.t_graph_slots(n, n_verts, synth.seed_for(8), dev, torch.int64)
+    out_es, out_is = torch.empty_like(es), torch.empty_like(is_)
+    cnt = torch.empty(1, dtype=torch.int64, device=dev)
+    torch.cuda.nvtx.range_push("smallest_pairs")
+    t = _time(lambda: ixp.smallest_pairs(es, is_, n_verts, n, out_es=out_es, out_is=out_is, count=cnt))
+    torch.cuda.nvtx.range_pop()
+    c = int(cnt.item())
+    v1 = torch.empty(6, dtype=torch.int64, device=dev)
+    v2 = torch.empty(6, dtype=torch.int64, device=dev)
+    t_chk = _time(lambda: (ixp.check_inj(out_es[:c], 0, n_verts - 1, out=v1),
+                           ixp.check_inj(out_is[:c], 0, n - 1, out=v2)))
+    distinct = int(torch.unique(es).numel())
+    nbytes = 32 * n + 16 * c  # es and is read by the hist and again by the filter; kept pairs written
+    return {"workload": "%d int64 slots over %d vertices (uniform), injective priorities" % (n, n_verts),
+            "ms": round(t, 4), "alg_bytes": nbytes, "gbs": round(nbytes / (t / 1e3) / 1e9, 1),
+            "kept": c, "kept_equals_distinct_vertices": c == distinct,
+            "post_inj_check_ms": round(t_chk, 4),
+            "post_inj_ok": [ixp.Verdict(v1).get()["ok"], ixp.Verdict(v2).get()["ok"]]}
 
 
 def run_e2e(ixp, R, ops, inp, dev, args, step_bytes):

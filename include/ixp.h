@@ -115,7 +115,9 @@ enum {
     IXP_OP_INJ_SEG = 8,  /* extra = nseg */
     IXP_OP_BIJ_SEG = 9,  /* extra = nseg */
     IXP_OP_GATHER_SEGMENTS = 10, /* n = output elements */
-    IXP_OP_FILTPART_CLASSES = 11 /* itype = v (classes), extra = nseg (0 when flat) */
+    IXP_OP_FILTPART_CLASSES = 11, /* itype = v (classes), extra = nseg (0 when flat) */
+    IXP_OP_INJ_HIST = 12,         /* extra = m (bins) */
+    IXP_OP_SMALLEST_PAIRS = 13    /* extra = n_verts */
 };
 
 /* Bytes of workspace that call `op` needs for n elements of type itype and the
@@ -245,8 +247,10 @@ int ixp_scan(const void *in, int in_type, void *out, int out_type, int64_t n, in
  * e_k + (number of trues before i in its segment) when pred(i) holds and
  * e_k + T_k + (number of falses before i in its segment) otherwise, T_k being the
  * segment's number of trues. d_num_true (device int64_t[max(1, nseg)]) gets T_k.
- * out_keys / out_payload (nullable) receive keys / payload rows scattered to their
- * destinations (payload rows are row_bytes bytes, a multiple of 4, at most 64).
+ * out_indices (nullable: then the destinations are only used to place the keys
+ * and payload), out_keys / out_payload (nullable) receive keys / payload rows
+ * scattered to their destinations (payload rows are row_bytes bytes, a multiple
+ * of 4, at most 64).
  * keys may be NULL for a FLAGS or TRUE predicate. d_status as for ixp_scan. */
 int ixp_partition(const void *keys, int ktype, int64_t n, ixp_pred pred, const void *payload, int32_t row_bytes,
                   void *out_indices, int out_type, void *out_keys, void *out_payload, int64_t *d_num_true,
@@ -337,6 +341,40 @@ int ixp_sgm_scan(const uint8_t *flags, const void *in, int in_type, void *out, i
  * IXP_OP_GATHER_SEGMENTS, 0, n, 0) bytes. */
 int ixp_mkii(const int64_t *offsets, int64_t m, void *out, int out_type, int64_t n, int32_t *d_status, void *ws,
              size_t ws_bytes, ixp_stream stream);
+
+/* ---- reduce-by-index and maxMatching ------------------------------------------- */
+
+/* Reduce-by-index with min, Futhark's hist with the min operator  [Sec. 7: the
+ * hist of get_smallest_pairs, Fig. 9, and of the dynamic verification of
+ * scatter]: for every i with 0 <= idx[i] < m, H[idx[i]] = min(H[idx[i]],
+ * vals[i]); indices out of bounds are ignored, as scatter ignores them (Sec. 2.1).
+ * H: device htype[m] holding the neutral element on entry (the caller fills it).
+ * vals: device htype[n], or NULL for vals[i] = i (n - 1 must then fit htype).
+ * idx: device itype[n]. Signed comparison. The result does not depend on the
+ * order of the updates. No workspace. */
+int ixp_hist_min(void *H, int htype, int64_t m, const void *idx, int itype, const void *vals, int64_t n,
+                 ixp_stream stream);
+
+/* Inj on [0, m) decided the way a dynamic verification of scatter decides it
+ * [Sec. 7: reduce-by-index with atomic min]: H = hist min over [0, m) of
+ * iota n by x, then every i with 0 <= x[i] < m must have H[x[i]] == i. Same
+ * property and verdict as ixp_check_inj(x, itype, n, 0, m - 1, ...): index = the
+ * first occurrence of the earliest repeated value, value = x[index], aux0 = its
+ * next occurrence. n < 2^32. Workspace: ixp_workspace_size(IXP_OP_INJ_HIST,
+ * itype, n, m) bytes (4 m + 256), 256-byte aligned. */
+int ixp_check_inj_hist(const void *x, int itype, int64_t n, int64_t m, ixp_verdict *d_verdict, void *ws,
+                       size_t ws_bytes, ixp_stream stream);
+
+/* get_smallest_pairs of maxMatching  [Sec. 7, Fig. 9]: H = hist min over n_verts
+ * bins, neutral element n_es, of the priorities is by the vertices es; slot i is
+ * kept when 0 <= es[i] < n_verts and H[es[i]] == is[i]; out_es / out_is get the
+ * kept es[i] / is[i] in input order (filter_by) and *d_count their number. When
+ * is is injective both outputs are injective, the property the paper proves.
+ * es, is, out_es, out_is: device arrays of one itype (out_* need room for the kept
+ * count, at most n); d_count: device int64. Workspace: ixp_workspace_size(
+ * IXP_OP_SMALLEST_PAIRS, itype, n, n_verts) bytes, 256-byte aligned. */
+int ixp_smallest_pairs(const void *es, const void *is, int itype, int64_t n, int64_t n_verts, int64_t n_es,
+                       void *out_es, void *out_is, int64_t *d_count, void *ws, size_t ws_bytes, ixp_stream stream);
 
 /* ---- batched pipeline over a jagged array ---------------------------------------- */
 

@@ -10,6 +10,8 @@ size_t bk_prefix_bytes(int64_t n);                       // checks.cu
 size_t seg_ws_bytes(int64_t nseg);                       // segmented.cu
 size_t gather_segments_ws_bytes(int64_t n_out);          // scatter.cu
 size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg);  // classes.cu
+size_t inj_hist_ws_bytes(int64_t m);                                 // hist.cu
+size_t smallest_pairs_ws_bytes(int itype, int64_t n, int64_t n_verts);  // hist.cu
 
 int num_sms() {
     static int cached[64] = {0};
@@ -62,6 +64,8 @@ extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra
         case IXP_OP_BIJ_SEG: return seg_ws_bytes(extra) + chunk_lb_bytes(n);
         case IXP_OP_GATHER_SEGMENTS: return gather_segments_ws_bytes(n);
         case IXP_OP_FILTPART_CLASSES: return filtpart_classes_ws_bytes(itype, n, extra);
+        case IXP_OP_INJ_HIST: return inj_hist_ws_bytes(extra);
+        case IXP_OP_SMALLEST_PAIRS: return smallest_pairs_ws_bytes(itype, n, extra);
         default: return 0;
     }
 }
@@ -88,8 +92,9 @@ extern "C" unsigned long long ixp_tu_kernels_scatter(void);
 extern "C" unsigned long long ixp_tu_kernels_segmented(void);
 extern "C" unsigned long long ixp_tu_kernels_batched(void);
 extern "C" unsigned long long ixp_tu_kernels_classes(void);
+extern "C" unsigned long long ixp_tu_kernels_hist(void);
 
 extern "C" unsigned long long ixp_kernel_launches(void) {
     return ixp_tu_kernels_checks() + ixp_tu_kernels_scan() + ixp_tu_kernels_scatter() + ixp_tu_kernels_segmented() +
-           ixp_tu_kernels_batched() + ixp_tu_kernels_classes();
+           ixp_tu_kernels_batched() + ixp_tu_kernels_classes() + ixp_tu_kernels_hist();
 }

@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "preds.cuh"
+#include "tilescan.cuh"
 
 namespace ixp {
 
@@ -817,68 +818,7 @@ __global__ void __launch_bounds__(TB, 4) count_tiles_kernel(const KT *__restrict
     }
 }
 
-// Pass 1b: exclusive scan of the packed tile counts in place, in groups of TS_G
-// tiles: each block scans its group and writes the group total; then each block
-// adds the sum of the totals of the groups before it, and the last block writes
-// the grand total to h->total.
-constexpr int TS_G = 1024;
-
-__device__ __forceinline__ unsigned long long block_excl_scan_u64(unsigned long long x, unsigned long long *s_w,
-                                                                  unsigned long long *total) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    unsigned long long y = x;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        unsigned long long o = __shfl_up_sync(FULL, y, d);
-        if (l >= d) y += o;
-    }
-    if (l == 31) s_w[w] = y;
-    __syncthreads();
-    if (w == 0) {
-        const unsigned long long v = l < nw ? s_w[l] : 0ull;
-        unsigned long long z = v;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            unsigned long long o = __shfl_up_sync(FULL, z, d);
-            if (l >= d) z += o;
-        }
-        if (l < nw) s_w[l] = z - v;
-        if (l == 31) s_w[32] = z;
-    }
-    __syncthreads();
-    const unsigned long long r = s_w[w] + y - x;
-    *total = s_w[32];
-    __syncthreads();
-    return r;
-}
-
-__global__ void __launch_bounds__(TS_G) group_scan_kernel(unsigned long long *tp, int64_t nt,
-                                                          unsigned long long *gtot) {
-    IXP_KERNEL_ENTRY();
-    __shared__ unsigned long long s_w[33];
-    const int64_t t = blockIdx.x * (int64_t)TS_G + threadIdx.x;
-    const unsigned long long x = t < nt ? tp[t] : 0ull;
-    unsigned long long tot;
-    const unsigned long long ex = block_excl_scan_u64(x, s_w, &tot);
-    if (t < nt) tp[t] = ex;
-    if (threadIdx.x == 0) gtot[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(TS_G) group_add_kernel(unsigned long long *tp, int64_t nt,
-                                                         const unsigned long long *__restrict__ gtot, Hdr *h) {
-    IXP_KERNEL_ENTRY();
-    __shared__ unsigned long long s_w[TS_G / 32];
-    __shared__ unsigned long long s_pre;
-    unsigned long long v = 0;
-    for (int64_t g = threadIdx.x; g < (int64_t)blockIdx.x; g += TS_G) v += gtot[g];
-    v = block_sum_u64(v, s_w);
-    if (threadIdx.x == 0) s_pre = v;
-    __syncthreads();
-    const unsigned long long pre = s_pre;
-    const int64_t t = blockIdx.x * (int64_t)TS_G + threadIdx.x;
-    if (t < nt) tp[t] += pre;
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) h->total = pre + gtot[blockIdx.x];
-}
+// Pass 1b: the grouped scan of the packed tile counts (tilescan.cuh).
 
 // Pass 1c: seg_cnt[k] = packed count before off[k] (tile prefix + in-tile part);
 // off[k] = n maps to the total. Offsets outside [0, n] leave seg_cnt[k] without
@@ -1007,7 +947,9 @@ __global__ void __launch_bounds__(TB) partition_write_kernel(
                     for (int c2 = 0; c2 < row_words; c2++) out_payload[d * row_words + c2] = payload[i * row_words + c2];
             }
         }
-        if (vec_ok && p0 + V <= n && sizeof(OT) * V >= 16) {
+        if (!out_idx) {
+            // keys / payload only
+        } else if (vec_ok && p0 + V <= n && sizeof(OT) * V >= 16) {
             if (sizeof(OT) == 4) {
                 int4 s;
                 s.x = (int)dst[0];
@@ -1152,7 +1094,9 @@ __global__ void __launch_bounds__(TB, 4) partition_flat_kernel(
                 if (OUT_KEYS) s_kout[c ? kh_t + lt : kf_off + kh_f + (r - lt)] = s_kin[r];
             }
         }
-        if (vec_ok && p0 + V <= n && sizeof(OT) * V >= 16) {
+        if (!out_idx) {
+            // destinations used for the staged runs only
+        } else if (vec_ok && p0 + V <= n && sizeof(OT) * V >= 16) {
             if (sizeof(OT) == 4) {
                 int4 s4;
                 s4.x = (int)dst[0];
@@ -1526,12 +1470,7 @@ static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs se
 
 // Exclusive scan of the packed tile counts (h->total gets the sum; it stays 0
 // from the header reset when there are no tiles).
-static void scan_tiles(TileWs &W, int64_t nt, cudaStream_t st) {
-    if (nt <= 0) return;
-    const unsigned ng = (unsigned)((nt + TS_G - 1) / TS_G);
-    group_scan_kernel<<<ng, TS_G, 0, st>>>(W.tile_prefix, nt, W.gtot);
-    group_add_kernel<<<ng, TS_G, 0, st>>>(W.tile_prefix, nt, W.gtot, W.h);
-}
+static void scan_tiles(TileWs &W, int64_t nt, cudaStream_t st) { scan_tile_counts(W.tile_prefix, nt, W.gtot, W.h, st); }
 
 template <typename KT>
 static int run_counts(const KT *keys, int64_t n, DPred filt, DPred part, ixp_segs segs, TileWs &W, int64_t nt,
@@ -1718,7 +1657,7 @@ extern "C" int ixp_partition(const void *keys, int ktype, int64_t n, ixp_pred pr
                              ixp_stream stream) {
     if ((keys && ktype != IXP_I32 && ktype != IXP_I64) || (out_type != IXP_I32 && out_type != IXP_I64))
         return IXP_E_DTYPE;
-    if (n < 0 || n >= (1ll << 32) || (n > 0 && !out_indices) || !d_num_true || !pred_ok(pred, keys != nullptr || n == 0))
+    if (n < 0 || n >= (1ll << 32) || !d_num_true || !pred_ok(pred, keys != nullptr || n == 0))
         return IXP_E_INVAL;
     if (out_type == IXP_I32 && n > INT32_MAX) return IXP_E_INVAL;
     if ((out_keys && !keys) || (out_payload && (!payload || row_bytes <= 0 || row_bytes % 4 || row_bytes > 64)))

@@ -23,7 +23,8 @@ KINDS = ["none", "out_of_range", "order", "duplicate", "out_of_image", "missing"
 CMPS = {"le": 0, "lt": 1, "ge": 2, "gt": 3}
 PREDS = {"true": 0, "mod_eq": 1, "lt": 2, "flags": 3}
 OPS = {"range": 0, "mono": 1, "inj": 2, "bij": 3, "filtpart": 4, "scan": 5, "partition": 6, "flags": 7,
-       "inj_seg": 8, "bij_seg": 9, "gather_segments": 10, "filtpart_classes": 11}
+       "inj_seg": 8, "bij_seg": 9, "gather_segments": 10, "filtpart_classes": 11, "inj_hist": 12,
+       "smallest_pairs": 13}
 ERRORS = {0: "ok", -1: "invalid argument", -2: "unsupported element type", -3: "value span exceeds the workspace",
           -4: "workspace too small", -5: "CUDA launch failed", -6: "bounded device wait gave up",
           -7: "index out of bounds"}
@@ -78,6 +79,9 @@ _SIGS = {
     "ixp_sgm_scan": (_I, [_P, _P, _I, _P, _I, _L, _I, _P, _P, _Z, _P]),
     "ixp_mkii": (_I, [_P, _L, _P, _I, _L, _P, _P, _Z, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
+    "ixp_hist_min": (_I, [_P, _I, _L, _P, _I, _P, _L, _P]),
+    "ixp_check_inj_hist": (_I, [_P, _I, _L, _L, _P, _P, _Z, _P]),
+    "ixp_smallest_pairs": (_I, [_P, _P, _I, _L, _L, _L, _P, _P, _P, _P, _Z, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
     "ixp_kernel_launches": (C.c_ulonglong, []),
     "ixp_batch_workspace_size": (_Z, [_P]),
@@ -231,6 +235,17 @@ def check_inj(x, rcd_lo=I64MIN, rcd_hi=I64MAX, *, span=None, out=None, ws=None, 
     return Verdict(v)
 
 
+def check_inj_hist(x, m, *, out=None, ws=None, stream=None) -> Verdict:
+    """Inj on [0, m) by reduce-by-index with min (the dynamic verification of scatter);
+    same verdict as check_inj(x, 0, m - 1)."""
+    v = _verdict_buf(x.device, out)
+    need = workspace_size("inj_hist", _itype(x), x.numel(), m)
+    ws = ws if ws is not None else workspace(need, x.device)
+    _ck(load().ixp_check_inj_hist(_dev(x, "x"), _itype(x), x.numel(), m, v.data_ptr(), ws.data_ptr(), ws.numel(),
+                                  _stream(stream)), "check_inj_hist")
+    return Verdict(v)
+
+
 def check_bij(x, rcd_lo, rcd_hi, img_lo, img_hi, *, out=None, ws=None, stream=None) -> Verdict:
     v = _verdict_buf(x.device, out)
     need = workspace_size("bij", _itype(x), x.numel(), img_hi - img_lo + 1)
@@ -330,9 +345,10 @@ def scan(x, out_dtype=None, inclusive=False, offsets=None, *, out=None, totals=N
     return out, totals, status
 
 
-def partition(keys, pred, payload=None, out_dtype=torch.int32, offsets=None, *, want_keys=True, n=None, out=None,
-              out_keys=None, out_payload=None, num_true=None, status=None, ws=None, stream=None):
-    """Stable two-way partition. Returns dict(indices, num_true, keys_out, payload_out, status)."""
+def partition(keys, pred, payload=None, out_dtype=torch.int32, offsets=None, *, want_keys=True, want_indices=True,
+              n=None, out=None, out_keys=None, out_payload=None, num_true=None, status=None, ws=None, stream=None):
+    """Stable two-way partition. Returns dict(indices, num_true, keys_out, payload_out, status);
+    indices is None when want_indices is False (keys / payload moved without the index array)."""
     p = make_pred(pred)
     if keys is not None:
         n = keys.numel()
@@ -340,7 +356,10 @@ def partition(keys, pred, payload=None, out_dtype=torch.int32, offsets=None, *, 
     else:
         device = pred[3].device if isinstance(pred, (tuple, list)) else torch.device("cuda")
     segs = _segs(offsets)
-    out = out if out is not None else torch.empty(n, dtype=out_dtype, device=device)
+    if want_indices:
+        out = out if out is not None else torch.empty(n, dtype=out_dtype, device=device)
+    else:
+        out = None
     if want_keys and keys is not None and out_keys is None:
         out_keys = torch.empty_like(keys)
     if payload is not None and out_payload is None:
@@ -355,9 +374,11 @@ def partition(keys, pred, payload=None, out_dtype=torch.int32, offsets=None, *, 
         row_bytes = payload.element_size()
         for d in payload.shape[1:]:
             row_bytes *= d
+    ot = _itype(out) if out is not None else (0 if out_dtype == torch.int32 else 1)
     _ck(load().ixp_partition(None if keys is None else _dev(keys, "keys"), kt, n, p,
-                             None if payload is None else _dev(payload, "payload"), row_bytes, out.data_ptr(),
-                             _itype(out), None if out_keys is None or not want_keys else out_keys.data_ptr(),
+                             None if payload is None else _dev(payload, "payload"), row_bytes,
+                             None if out is None else out.data_ptr(), ot,
+                             None if out_keys is None or not want_keys else out_keys.data_ptr(),
                              None if out_payload is None else out_payload.data_ptr(), num_true.data_ptr(), segs,
                              status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "partition")
     return {"indices": out, "num_true": num_true, "keys_out": out_keys if want_keys else None,
@@ -451,6 +472,34 @@ def sgm_scan(flags, x, out_dtype=None, inclusive=True, *, out=None, status=None,
     _ck(load().ixp_sgm_scan(_dev(flags, "flags"), _dev(x, "x"), _itype(x), out.data_ptr(), _itype(out), n,
                             int(inclusive), status.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "sgm_scan")
     return out, status
+
+
+def hist_min(H, idx, vals=None, *, stream=None):
+    """In place: H[idx[i]] = min(H[idx[i]], vals[i]) for in-bounds idx[i] (vals None: i)."""
+    if vals is not None and vals.dtype != H.dtype:
+        raise ValueError("vals must have H's dtype")
+    _ck(load().ixp_hist_min(_dev(H, "H") if H.numel() else None, _itype(H), H.numel(),
+                            _dev(idx, "idx") if idx.numel() else None, _itype(idx),
+                            None if vals is None else _dev(vals, "vals"), idx.numel(), _stream(stream)), "hist_min")
+    return H
+
+
+def smallest_pairs(es, is_, n_verts, n_es, *, out_es=None, out_is=None, count=None, ws=None, stream=None):
+    """get_smallest_pairs of maxMatching. Returns (out_es, out_is, count): the first
+    count entries of the outputs are the kept pairs in input order (count stays on
+    the device)."""
+    if is_.dtype != es.dtype or is_.numel() != es.numel():
+        raise ValueError("es and is must have one dtype and one length")
+    n = es.numel()
+    out_es = out_es if out_es is not None else torch.empty_like(es)
+    out_is = out_is if out_is is not None else torch.empty_like(is_)
+    count = count if count is not None else torch.empty(1, dtype=torch.int64, device=es.device)
+    need = workspace_size("smallest_pairs", _itype(es), n, n_verts)
+    ws = ws if ws is not None else workspace(need, es.device)
+    _ck(load().ixp_smallest_pairs(_dev(es, "es") if n else None, _dev(is_, "is") if n else None, _itype(es), n,
+                                  n_verts, n_es, out_es.data_ptr() if n else None, out_is.data_ptr() if n else None,
+                                  count.data_ptr(), ws.data_ptr(), ws.numel(), _stream(stream)), "smallest_pairs")
+    return out_es, out_is, count
 
 
 def mkii(offsets, n, out_dtype=torch.int32, *, out=None, status=None, ws=None, stream=None):

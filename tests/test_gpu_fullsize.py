@@ -213,3 +213,49 @@ def test_differentiation_full_size(ixp, dev):
     a64 = oracle.scatter_add_f64(m, zipf, np.abs(vh))
     got = out.detach().cpu().numpy().astype(np.float64)
     assert np.all(np.abs(got - r64) <= 1e-6 * np.maximum(np.abs(r64), a64) + 1e-30)
+
+
+def test_dynamic_inj_check_full_size(ixp, dev):
+    """The reduce-by-index Inj check on the 2^28 int32 permutation (a 1 GiB bin
+    array): clean, and with a planted duplicate reported at its positions."""
+    n = 1 << 28
+    s = synth.seed_for(1) + 120
+    perm = synth.t_permutation(n, s, dev, torch.int32)
+    assert ixp.check_inj_hist(perm, n).get()["ok"] == 1
+    dup, p, q = synth.t_plant_duplicate(perm, s + 1)
+    del perm
+    v = ixp.check_inj_hist(dup, n).get()
+    assert v["ok"] == 0 and v["index"] == min(p, q) and v["aux0"] == max(p, q)
+
+
+def test_partition2_three_ways_200m(ixp, dev):
+    """partition2 of 200M float32 in [0, 1) by x < 0.5: the dynamic form (indices,
+    reduce-by-index check, scatter) and the fused static form give the oracle's
+    output bit for bit."""
+    n = 200_000_000
+    x = synth.t_floats_unit(n, synth.seed_for(7) + 200, dev)
+    bits = x.view(torch.int32)
+    pred = ("lt", 0, int(np.float32(0.5).view(np.int32)))
+    r = ixp.partition(bits, pred, want_keys=False)
+    assert ixp.check_inj_hist(r["indices"], n).get()["ok"] == 1
+    ys = torch.zeros_like(x)
+    ixp.scatter(ys, r["indices"], x)
+    st = ixp.partition(bits, pred, want_indices=False)
+    assert torch.equal(st["keys_out"], ys.view(torch.int32))
+    o = oracle.partition(bits.cpu().numpy(), pred)
+    assert int(st["num_true"][0].item()) == int(o["num_true"][0])
+    assert np.array_equal(st["keys_out"].cpu().numpy(), o["keys_out"])
+
+
+def test_smallest_pairs_full_size(ixp, dev):
+    """get_smallest_pairs on 2^26 int64 slots over 2^23 vertices against the oracle
+    on the whole arrays, and the postcondition (both outputs injective)."""
+    n_verts, n = 1 << 23, 1 << 26
+    es, is_ = synth.t_graph_slots(n, n_verts, synth.seed_for(8) + 1, dev, torch.int64)
+    ge, gi, cnt = ixp.smallest_pairs(es, is_, n_verts, n)
+    c = int(cnt.item())
+    oe, oi = oracle.smallest_pairs(n_verts, n, es.cpu().numpy(), is_.cpu().numpy())
+    assert c == oe.shape[0]
+    assert np.array_equal(ge[:c].cpu().numpy(), oe) and np.array_equal(gi[:c].cpu().numpy(), oi)
+    assert ixp.check_inj(ge[:c], 0, n_verts - 1).get()["ok"] == 1
+    assert ixp.check_inj(gi[:c], 0, n - 1).get()["ok"] == 1
