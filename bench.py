@@ -370,9 +370,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ops", default="", help="comma-separated subset of op names (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
+    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs"],
+                    help="run only this workload and print its result (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.extra:
+        import torch
+        import paper_2506_23058_gb300 as ixp
+        ixp.load()
+        dev = torch.device("cuda", 0)
+        fn = {"partition2": run_partition2, "smallest_pairs": run_matching}[args.extra]
+        print(json.dumps({"extra": args.extra, "result": fn(ixp, dev)}))
         return
 
     import torch
