@@ -643,12 +643,70 @@ __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, u
 // give the first such index (k_first).
 constexpr int BS_THREADS = 512;
 constexpr int BS_PER = BK_TILE / BS_THREADS;  // elements per thread per tile
+constexpr unsigned BS_PAD_MAX = 1024;         // most buckets for the padded-run write-out
 
-__host__ __device__ constexpr size_t bs_smem_bytes(unsigned bmax) {
-    return (size_t)bmax * (8 + 4 + 4 + 4) + (size_t)BK_TILE * 4;
+// Shared memory of pass 1. Per bucket: pool index of tile slot 0 (8 bytes), count,
+// start, limit (4 bytes each); the sorted tile (TILE entries, plus up to 3 pad
+// entries per bucket when runs are padded to 16-byte chunks); with padding, the
+// bucket of each 16-byte chunk (2 bytes).
+// Layout: sorted tile (16-byte aligned, rounded to whole chunks) | pool index of
+// slot 0 per bucket | count | start | limit | chunk -> bucket.
+__host__ __device__ constexpr unsigned bs_sorted_cap(unsigned bmax, bool pad) {
+    return pad ? (BK_TILE + 3 * bmax + 3) & ~3u : BK_TILE;
+}
+__host__ __device__ constexpr size_t bs_smem_bytes(unsigned bmax, bool pad) {
+    return (size_t)bs_sorted_cap(bmax, pad) * 4 + (size_t)bmax * (8 + 4 + 4 + 4) +
+           (pad ? (size_t)(bs_sorted_cap(bmax, pad) / 4) * 2 : 0);
 }
 
-template <typename T, bool BIJ>
+// Bucket of an element, or -1 when its value is outside [base, base + span):
+// rel = x - base in 64 bits, or in 32 bits when the caller has checked that the
+// whole range [base, base + span) lies inside the int32 range (then the unsigned
+// 32-bit difference is below span exactly for the values in range).
+template <bool R32, typename T>
+__device__ __forceinline__ bool bs_rel(T x, unsigned long long base, unsigned long long span, unsigned span_m1,
+                                       unsigned &rel) {
+    if (R32) {
+        rel = (unsigned)(int)x - (unsigned)base;
+        return rel <= span_m1;
+    } else {
+        const unsigned long long r = (unsigned long long)(int64_t)x - base;
+        rel = (unsigned)r;
+        return r < span;
+    }
+}
+
+// Pass 1 over one tile's elements already in registers: count each in-range
+// element's bucket in shared memory (the atomic's return value is its rank in the
+// bucket) and remember which were in range (vm).
+template <typename T, bool BIJ, bool R32, bool FULL>
+__device__ __forceinline__ void bs_classify(const T (&e)[BS_PER / Vec<T>::N][Vec<T>::N], int64_t t0, int64_t n,
+                                            int tid, unsigned long long base, unsigned long long span,
+                                            unsigned span_m1, unsigned lw, unsigned *s_cnt, int64_t rlo, int64_t rhi,
+                                            unsigned (&rv)[BS_PER], unsigned (&rk)[BS_PER], unsigned &vm,
+                                            int64_t &ooi) {
+    constexpr int V = Vec<T>::N;
+    constexpr int NV = BS_PER / V;
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+#pragma unroll
+        for (int c = 0; c < V; c++) {
+            const int q = j * V + c;
+            const int64_t i = t0 + (int64_t)(j * BS_THREADS + tid) * V + c;
+            unsigned rel;
+            const bool in = bs_rel<R32>(e[j][c], base, span, span_m1, rel);
+            rv[q] = rel;
+            if ((FULL || i < n) && in) {
+                rk[q] = atomicAdd(&s_cnt[rel >> lw], 1u);
+                vm |= 1u << q;
+            } else if (BIJ && (FULL || i < n) && (int64_t)e[j][c] >= rlo && (int64_t)e[j][c] <= rhi) {
+                ooi = i < ooi ? i : ooi;
+            }
+        }
+    }
+}
+
+template <typename T, bool BIJ, bool PAD>
 __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
     const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, Hdr *h, BucketCfg cfg,
     unsigned *__restrict__ cursors, unsigned *__restrict__ pool, unsigned *__restrict__ marks,
@@ -657,12 +715,15 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
     if (h->status) return;
     constexpr int V = Vec<T>::N;
     constexpr int NV = BS_PER / V;  // 16-byte vectors per thread per tile
+    constexpr unsigned SENT = ~0u;  // pad entry (pass 2 skips it)
     extern __shared__ __align__(16) unsigned char bk_raw[];
-    long long *s_dst = reinterpret_cast<long long *>(bk_raw);  // bmax: pool index of tile slot 0 for bucket b
-    unsigned *s_sorted = reinterpret_cast<unsigned *>(s_dst + cfg.bmax);  // BK_TILE
-    unsigned *s_cnt = s_sorted + BK_TILE;                                  // bmax
-    unsigned *s_start = s_cnt + cfg.bmax;                                  // bmax
-    unsigned *s_lim = s_start + cfg.bmax;                                  // bmax: slots below fit the pool
+    const unsigned bmax = cfg.bmax;
+    unsigned *s_sorted = reinterpret_cast<unsigned *>(bk_raw);              // TILE (+ 3 bmax pads)
+    long long *s_dst = reinterpret_cast<long long *>(s_sorted + bs_sorted_cap(bmax, PAD));  // pool index of slot 0
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_dst + bmax);            // bmax
+    unsigned *s_start = s_cnt + bmax;                                        // bmax
+    unsigned *s_lim = s_start + bmax;                                        // bmax: slots below fit the pool
+    unsigned short *s_cb = reinterpret_cast<unsigned short *>(s_lim + bmax);  // chunk -> bucket (PAD)
     __shared__ unsigned s_wsum[BS_THREADS / 32];
     __shared__ unsigned s_total;
     const unsigned long long base = h->base, span = h->span;
@@ -670,6 +731,10 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
     const unsigned long long cap = h->spare[1];
     const unsigned lw = cfg.lw;
     const unsigned wmask = (1u << lw) - 1u;
+    // 32-bit relative values are exact when [base, base + span) lies in the int32 range
+    const bool r32 = sizeof(T) == 4 && span >= 1 && span <= (1ull << 32) && (int64_t)base >= (int64_t)INT32_MIN &&
+                     (int64_t)base <= (int64_t)INT32_MAX && (int64_t)base + (int64_t)(span - 1) <= (int64_t)INT32_MAX;
+    const unsigned span_m1 = (unsigned)(span - 1);
     const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     unsigned long long valid = 0;  // kept by thread 0 only
@@ -678,12 +743,13 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
     const unsigned per = (nb + BS_THREADS - 1) / BS_THREADS;  // bucket-count scan entries per thread
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t t0 = tile * BK_TILE;
+        const bool full = t0 + BK_TILE <= n;
         for (unsigned b = tid; b < nb; b += BS_THREADS) s_cnt[b] = 0u;
         T e[NV][V];
 #pragma unroll
         for (int j = 0; j < NV; j++) {
             const int64_t p0 = t0 + (int64_t)(j * BS_THREADS + tid) * V;
-            if (vec_ok && p0 + V <= n) {
+            if (vec_ok && (full || p0 + V <= n)) {
                 if (V == 4) {
                     int4 v = __ldcs(reinterpret_cast<const int4 *>(x + p0));
                     e[j][0] = (T)v.x;
@@ -702,33 +768,21 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
         }
         __syncthreads();  // s_cnt zeroed
         unsigned rv[BS_PER], rk[BS_PER], vm = 0;
-#pragma unroll
-        for (int j = 0; j < NV; j++) {
-            const int64_t p0 = t0 + (int64_t)(j * BS_THREADS + tid) * V;
-#pragma unroll
-            for (int c = 0; c < V; c++) {
-                const int q = j * V + c;
-                const int64_t xi = (int64_t)e[j][c];
-                const unsigned long long rel = (unsigned long long)xi - base;
-                rv[q] = (unsigned)rel;
-                rk[q] = 0u;
-                if (p0 + c < n) {
-                    if (rel < span) {
-                        rk[q] = atomicAdd(&s_cnt[(unsigned)rel >> lw], 1u);
-                        vm |= 1u << q;
-                    } else if (BIJ && xi >= rlo && xi <= rhi) {
-                        ooi = (p0 + c) < ooi ? (p0 + c) : ooi;
-                    }
-                }
-            }
-        }
+        if (r32 && full)
+            bs_classify<T, BIJ, true, true>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm, ooi);
+        else if (full)
+            bs_classify<T, BIJ, false, true>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm,
+                                             ooi);
+        else
+            bs_classify<T, BIJ, false, false>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm,
+                                              ooi);
         __syncthreads();
-        // exclusive scan of the bucket counts; reserve pool space per bucket
+        // exclusive scan of the (padded) bucket counts; reserve pool space per bucket
         {
             unsigned loc = 0;
             const unsigned b0 = tid * per;
             for (unsigned k = 0; k < per; k++)
-                if (b0 + k < nb) loc += s_cnt[b0 + k];
+                if (b0 + k < nb) loc += PAD ? (s_cnt[b0 + k] + 3u) & ~3u : s_cnt[b0 + k];
             unsigned y = loc;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
@@ -747,40 +801,84 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
             for (unsigned k = 0; k < per; k++)
                 if (b0 + k < nb) {
                     const unsigned b = b0 + k, c = s_cnt[b];
-                    const unsigned long long g = c ? atomicAdd(&cursors[b], c) : 0ull;
+                    const unsigned cr = PAD ? (c + 3u) & ~3u : c;  // reserved entries
+                    const unsigned long long g = cr ? atomicAdd(&cursors[b], cr) : 0ull;
                     s_start[b] = run;
                     s_dst[b] = (long long)((unsigned long long)b * cap + g) - (long long)run;
-                    s_lim[b] = g >= cap ? run : run + (unsigned)min((unsigned long long)c, cap - g);
-                    run += c;
+                    s_lim[b] = g >= cap ? run : run + (unsigned)min((unsigned long long)cr, cap - g);
+                    if (PAD) {
+                        for (unsigned p = c; p < cr; p++) s_sorted[run + p] = SENT;
+                        for (unsigned p = 0; p < cr; p += 4) s_cb[(run + p) >> 2] = (unsigned short)b;
+                    }
+                    run += cr;
                 }
             if (tid == 0) s_total = tot;
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < BS_PER; q++)
-            if ((vm >> q) & 1u) s_sorted[s_start[rv[q] >> lw] + rk[q]] = rv[q];
+            if ((vm >> q) & 1u) s_sorted[s_start[rv[q] >> lw] + rk[q]] = PAD ? (rv[q] & wmask) : rv[q];
         __syncthreads();
         const unsigned total = s_total;
-        if (tid == 0) valid += total;
-        for (unsigned p = tid; p < total; p += BS_THREADS) {
-            const unsigned v = s_sorted[p];
-            const unsigned b = v >> lw;
-            if (p < s_lim[b]) {
-                __stcs(pool + (s_dst[b] + (long long)p), v & wmask);
-            } else {
-                const unsigned bit = 1u << (v & 31);
-                const unsigned old = atomicOr(marks + (v >> 5), bit);
-                if (old & bit) {
-                    atomicOr(dup + (v >> 5), bit);
-                    atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
-                    anydup = 1;
+        if (PAD) {
+            // 16-byte chunks: every chunk lies in one bucket's run and starts on a
+            // 16-byte boundary of the pool (bucket regions, cursors and runs are all
+            // multiples of four entries).
+            for (unsigned k = tid; k < total / 4; k += BS_THREADS) {
+                const unsigned b = s_cb[k];
+                const unsigned p = 4 * k;
+                const uint4 d = *reinterpret_cast<const uint4 *>(s_sorted + p);
+                const long long dst = s_dst[b] + (long long)p;
+                const unsigned lim = s_lim[b];
+                if (p + 4 <= lim) {
+                    __stcs(reinterpret_cast<uint4 *>(pool + dst), d);
+                } else {
+                    const unsigned o[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                    for (int c = 0; c < 4; c++) {
+                        if (p + c < lim) {
+                            pool[dst + c] = o[c];  // pads too: pass 2 reads every reserved slot
+                        } else if (o[c] != SENT) {
+                            const unsigned v = (b << lw) | o[c];
+                            const unsigned bit = 1u << (v & 31);
+                            const unsigned old = atomicOr(marks + (v >> 5), bit);
+                            if (old & bit) {
+                                atomicOr(dup + (v >> 5), bit);
+                                atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
+                                anydup = 1;
+                            }
+                        }
+                    }
+                }
+            }
+        } else {
+            if (tid == 0) valid += total;
+            for (unsigned p = tid; p < total; p += BS_THREADS) {
+                const unsigned v = s_sorted[p];
+                const unsigned b = v >> lw;
+                if (p < s_lim[b]) {
+                    __stcs(pool + (s_dst[b] + (long long)p), v & wmask);
+                } else {
+                    const unsigned bit = 1u << (v & 31);
+                    const unsigned old = atomicOr(marks + (v >> 5), bit);
+                    if (old & bit) {
+                        atomicOr(dup + (v >> 5), bit);
+                        atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
+                        anydup = 1;
+                    }
                 }
             }
         }
+        if (PAD) valid += __popc(vm);  // per thread; summed over the block at the end
         __syncthreads();
     }
     __shared__ unsigned long long sm[BS_THREADS / 32];
-    if (tid == 0 && valid) atomicAdd(&h->cnt0, valid);
+    if (PAD) {
+        const unsigned long long tv = block_sum_u64(valid, sm);
+        if (tid == 0 && tv) atomicAdd(&h->cnt0, tv);
+    } else {
+        if (tid == 0 && valid) atomicAdd(&h->cnt0, valid);
+    }
     if (__syncthreads_or(anydup) && tid == 0) atomicOr(&h->flag, 1u);
     if (BIJ) {
         const unsigned long long r = block_max_u64(ooi == INT64_MAX ? 0ull : enc_first(ooi), sm);
@@ -838,6 +936,7 @@ __global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, Bucket
     }
     for (unsigned long long q = nv * 4 + threadIdx.x; q < stored; q += blockDim.x) {
         const unsigned off = src[q];
+        if (off == ~0u) continue;  // pad entry
         const unsigned bit = 1u << (off & 31);
         if (atomicOr(&s_bm[off >> 5], bit) & bit) {
             atomicOr(dup + ((lo_rel + off) >> 5), 1u << ((lo_rel + off) & 31));
@@ -848,8 +947,9 @@ __global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, Bucket
         atomicOr(&h->flag, 1u);
         atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
     }
-    if (bij && (unsigned long long)cnt < range) {
-        // smallest value of this bucket that no element takes
+    if (bij) {
+        // smallest value of this bucket that no element takes (the entry count
+        // cannot rule a gap out: padded runs reserve more slots than values)
         unsigned long long best = ~0ull;
         for (unsigned w = threadIdx.x; w < (range + 31) / 32; w += blockDim.x) {
             unsigned z = ~s_bm[w];
@@ -1020,13 +1120,21 @@ static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int6
     const int sgrid = num_sms() * 4;
     bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, w.cursors, w.bm, w.dup,
                                                           w.bmask);
-    cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)bs_smem_bytes(BK_MAX));
     const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
     const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 2));
     const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-    bucket_scatter_kernel<T, BIJ><<<g1, BS_THREADS, bs_smem_bytes(cfg.bmax), st>>>(
-        x, n, rlo, rhi, w.h, cfg, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
+    if (cfg.bmax <= BS_PAD_MAX && n < (1ll << 31)) {
+        // runs padded to 16-byte chunks (at least 8 elements per bucket per tile on average)
+        cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bs_smem_bytes(BS_PAD_MAX, true));
+        bucket_scatter_kernel<T, BIJ, true><<<g1, BS_THREADS, bs_smem_bytes(cfg.bmax, true), st>>>(
+            x, n, rlo, rhi, w.h, cfg, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
+    } else {
+        cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bs_smem_bytes(BK_MAX, false));
+        bucket_scatter_kernel<T, BIJ, false><<<g1, BS_THREADS, bs_smem_bytes(cfg.bmax, false), st>>>(
+            x, n, rlo, rhi, w.h, cfg, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
+    }
     cudaFuncSetAttribute(bucket_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << 20) / 8);
     bucket_check_kernel<<<cfg.bmax, BK_THREADS, (1u << cfg.lw) / 8, st>>>(w.h, cfg, w.cursors, w.pool, w.bm, w.dup,
                                                                          w.bmask, BIJ ? 1 : 0);
