@@ -1218,18 +1218,38 @@ __global__ void __launch_bounds__(TB, sizeof(ZT) > sizeof(KT) ? 3 : 4) filtpart_
             }
         }
     }
-    unsigned long long r[5] = {enc_min(fp_wide_min(tmn)), enc_max((int64_t)tmx), enc_min(fp_wide_min(fmn)),
-                               enc_max((int64_t)fmx), enc_min(fp_wide_min(dmin))};
+    if constexpr (sizeof(AT) == 4) {
+        // 32-bit bookkeeping: one warp-reduce instruction per value, then the
+        // order-preserving 64-bit encodings once per warp
+        tmn = __reduce_min_sync(FULL, tmn);
+        tmx = __reduce_max_sync(FULL, tmx);
+        fmn = __reduce_min_sync(FULL, fmn);
+        fmx = __reduce_max_sync(FULL, fmx);
+        dmin = __reduce_min_sync(FULL, dmin);
+        if (l == 0) {
+            s_r[0][w] = enc_min(fp_wide_min(tmn));
+            s_r[1][w] = enc_max((int64_t)tmx);
+            s_r[2][w] = enc_min(fp_wide_min(fmn));
+            s_r[3][w] = enc_max((int64_t)fmx);
+            s_r[4][w] = enc_min(fp_wide_min(dmin));
+        }
+    } else {
+        unsigned long long r[5] = {enc_min(fp_wide_min(tmn)), enc_max((int64_t)tmx), enc_min(fp_wide_min(fmn)),
+                                   enc_max((int64_t)fmx), enc_min(fp_wide_min(dmin))};
 #pragma unroll
-    for (int j = 0; j < 5; j++) {
-        r[j] = warp_max_u64(r[j]);
-        if (l == 0) s_r[j][w] = r[j];
+        for (int j = 0; j < 5; j++) {
+            r[j] = warp_max_u64(r[j]);
+            if (l == 0) s_r[j][w] = r[j];
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        unsigned long long r[5];
 #pragma unroll
-        for (int j = 0; j < 5; j++)
+        for (int j = 0; j < 5; j++) {
+            r[j] = s_r[j][0];
             for (int i = 1; i < TB / 32; i++) r[j] = s_r[j][i] > r[j] ? s_r[j][i] : r[j];
+        }
         tile_prefix[t] = widen(tot);
         rec[t] = make_longlong2(fp_rec(dec_min(r[0]), dec_max(r[1])), fp_rec(dec_min(r[2]), dec_max(r[3])));
         atomic_max_u64(&h->k_first2, r[4]);
