@@ -1121,7 +1121,7 @@ static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int6
     bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, w.cursors, w.bm, w.dup,
                                                           w.bmask);
     const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
-    const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 2));
+    const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 2));  // pass-1 grid
     const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
     if (cfg.bmax <= BS_PAD_MAX && n < (1ll << 31)) {
         // runs padded to 16-byte chunks (at least 8 elements per bucket per tile on average)

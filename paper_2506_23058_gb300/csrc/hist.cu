@@ -18,9 +18,13 @@
 // get_smallest_pairs: H = hist min (neutral n_es) over the vertices of the edge
 // priorities is by es; a slot is kept when its priority is its vertex's minimum;
 // both arrays are filtered by that flag, stably. The filter is two tiled passes:
-// the first computes each element's flag (one bit, stored as a bitmap word per 32
-// elements) and each tile's count, a grouped scan of the counts gives each tile's
+// the first computes each slot's flag (one bit, stored as a bitmap word per 32
+// slots) and each tile's count, a grouped scan of the counts gives each tile's
 // output offset, and the second writes the kept pairs with ranks from the bitmap.
+// (A single pass with a decoupled look-back measured slower: the tiles hold their
+// gathers in registers while they wait.) int64 priorities that all lie in
+// [0, 2^32 - 2] are reduced in a 32-bit H, half the L2 footprint of an int64 one;
+// a priority outside that range switches the call, on the device, to the 64-bit H.
 #include <algorithm>
 
 #include "common.cuh"
@@ -58,11 +62,14 @@ __device__ __forceinline__ void red_min(int64_t *p, int64_t v) {
 // H[idx[i]] = min(H[idx[i]], v_i) for 0 <= idx[i] < m, v_i = vals[i] or i (IOTA).
 // Grid-stride over groups of four elements (16-byte loads when `vec`), then the
 // elements after the last whole group one by one.
+// gate (nullable): the kernel runs only when gate->flag is set.
 template <typename IT, typename HT, bool IOTA>
 __global__ void __launch_bounds__(STREAM_THREADS) hist_min_kernel(HT *__restrict__ H, int64_t m,
                                                                   const IT *__restrict__ idx,
-                                                                  const HT *__restrict__ vals, int64_t n, int vec) {
+                                                                  const HT *__restrict__ vals, int64_t n, int vec,
+                                                                  const Hdr *gate) {
     IXP_KERNEL_ENTRY();
+    if (gate && !gate->flag) return;
     const int64_t n4 = vec ? n / 4 : 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -84,21 +91,57 @@ __global__ void __launch_bounds__(STREAM_THREADS) hist_min_kernel(HT *__restrict
 }
 
 template <typename T>
-__global__ void __launch_bounds__(STREAM_THREADS) fill_kernel(T *__restrict__ p, int64_t m, T v) {
+__global__ void __launch_bounds__(STREAM_THREADS) fill_kernel(T *__restrict__ p, int64_t m, T v, const Hdr *gate) {
     IXP_KERNEL_ENTRY();
+    if (gate && !gate->flag) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = v;
 }
 
 template <typename IT, typename HT>
-static void launch_hist(HT *H, int64_t m, const IT *idx, const HT *vals, int64_t n, cudaStream_t st) {
+static void launch_hist(HT *H, int64_t m, const IT *idx, const HT *vals, int64_t n, cudaStream_t st,
+                        const Hdr *gate = nullptr) {
     if (n <= 0) return;
     const int vec = aligned16(idx) && (vals == nullptr || aligned16(vals));
     const int g = stream_grid((n + 3) / 4, 1);
     if (vals)
-        hist_min_kernel<IT, HT, false><<<g, STREAM_THREADS, 0, st>>>(H, m, idx, vals, n, vec);
+        hist_min_kernel<IT, HT, false><<<g, STREAM_THREADS, 0, st>>>(H, m, idx, vals, n, vec, gate);
     else
-        hist_min_kernel<IT, HT, true><<<g, STREAM_THREADS, 0, st>>>(H, m, idx, nullptr, n, vec);
+        hist_min_kernel<IT, HT, true><<<g, STREAM_THREADS, 0, st>>>(H, m, idx, nullptr, n, vec, gate);
+}
+
+// The 32-bit form of the reduce-by-index for int64 priorities: H32[es[i]] =
+// min(H32[es[i]], is[i]) while is[i] lies in [0, 2^32 - 2]; a priority of an
+// in-bounds slot outside that range sets h->flag instead (the 64-bit H is then
+// built and used).
+__global__ void __launch_bounds__(STREAM_THREADS) hist_min_narrow_kernel(uint32_t *__restrict__ H, int64_t m,
+                                                                         const int64_t *__restrict__ idx,
+                                                                         const int64_t *__restrict__ vals, int64_t n,
+                                                                         int vec, Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    const int64_t n4 = vec ? n / 4 : 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool wide = false;
+    for (int64_t q = t0; q < n4; q += stride) {
+        int64_t k[4], v[4];
+        ld4<int64_t>(idx, q, k);
+        ld4<int64_t>(vals, q, v);
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            if ((uint64_t)k[c] >= (uint64_t)m) continue;
+            if ((uint64_t)v[c] > 0xfffffffeull) wide = true;
+            else red_min(H + k[c], (uint32_t)v[c]);
+        }
+    }
+    for (int64_t i = n4 * 4 + t0; i < n; i += stride) {
+        const int64_t kk = idx[i];
+        if ((uint64_t)kk >= (uint64_t)m) continue;
+        const int64_t vv = vals[i];
+        if ((uint64_t)vv > 0xfffffffeull) wide = true;
+        else red_min(H + kk, (uint32_t)vv);
+    }
+    if (__syncthreads_or(wide) && threadIdx.x == 0) atomicOr(&h->flag, 1u);
 }
 
 // ------------------------------------------------------------ dynamic Inj check
@@ -185,16 +228,17 @@ static int run_inj_hist(const IT *x, int64_t n, int64_t m, ixp_verdict *out, voi
 // ------------------------------------------------------------ get_smallest_pairs
 
 constexpr int SP_THREADS = 256;
-constexpr int SP_ROUNDS = 16;                             // 32-element rounds per warp per tile
-constexpr int SP_TILE = SP_THREADS * SP_ROUNDS;           // 4096 elements
-constexpr int SP_WARP_SPAN = 32 * SP_ROUNDS;              // 512 consecutive elements per warp
+constexpr int SP_ROUNDS = 16;                    // 32-slot rounds per warp per tile
+constexpr int SP_TILE = SP_THREADS * SP_ROUNDS;  // 4096 slots
+constexpr int SP_WARP_SPAN = 32 * SP_ROUNDS;     // 512 consecutive slots per warp
 
 struct SpWs {
     Hdr *h;
-    void *H;
+    void *H;        // n_verts entries of the index type
+    uint32_t *H32;  // n_verts entries (int64 priorities that fit 32 bits)
     unsigned long long *tile_cnt;
     unsigned long long *gtot;
-    uint32_t *keep;  // one bit per element
+    uint32_t *keep;  // one bit per slot
     size_t bytes;
 };
 
@@ -202,10 +246,13 @@ static SpWs sp_ws(void *ws, int64_t n, int64_t n_verts, int es) {
     SpWs w{};
     char *b = reinterpret_cast<char *>(ws);
     const int64_t nt = (n + SP_TILE - 1) / SP_TILE;
+    const size_t nv = (size_t)(n_verts > 0 ? n_verts : 0);
     size_t o = HDR_BYTES;
     w.h = reinterpret_cast<Hdr *>(b);
     w.H = b + o;
-    o += up256((size_t)(n_verts > 0 ? n_verts : 0) * es);
+    o += up256(nv * es);
+    w.H32 = reinterpret_cast<uint32_t *>(b + o);
+    o += es == 8 ? up256(nv * 4) : 0;
     w.tile_cnt = reinterpret_cast<unsigned long long *>(b + o);
     o += up256((size_t)(nt + 1) * 8);
     w.gtot = reinterpret_cast<unsigned long long *>(b + o);
@@ -221,19 +268,17 @@ size_t smallest_pairs_ws_bytes(int itype, int64_t n, int64_t n_verts) {
 }
 
 // Pass 1: keep[i] = (0 <= es[i] < n_verts && H[es[i]] == is[i]) as bitmap words
-// (word i / 32, bit i % 32) and the tile's count. Lane l of warp w handles
-// element t0 + 512 w + 32 r + l in round r; all rounds' loads and gathers are
-// issued before the compares.
-template <typename T>
-__global__ void __launch_bounds__(SP_THREADS) sp_flag_kernel(const T *__restrict__ es, const T *__restrict__ is,
-                                                             int64_t n, int64_t n_verts, const T *__restrict__ H,
-                                                             uint32_t *__restrict__ keep,
-                                                             unsigned long long *__restrict__ tile_cnt) {
-    IXP_KERNEL_ENTRY();
-    __shared__ unsigned s_w[SP_THREADS / 32];
+// (word i / 32, bit i % 32) and the tile's count. Lane l of warp w handles slot
+// t0 + 512 w + 32 r + l in round r; all rounds' loads and gathers are issued
+// before the compares.
+template <typename T, typename HT>
+__device__ __forceinline__ void sp_flag_tile(const T *__restrict__ es, const T *__restrict__ is, int64_t n,
+                                             int64_t n_verts, const HT *__restrict__ H, uint32_t *__restrict__ keep,
+                                             unsigned long long *__restrict__ tile_cnt, unsigned *s_w) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     const int64_t base = (int64_t)blockIdx.x * SP_TILE + (int64_t)w * SP_WARP_SPAN;
-    T e[SP_ROUNDS], hv[SP_ROUNDS];
+    T e[SP_ROUNDS];
+    HT hv[SP_ROUNDS];
 #pragma unroll
     for (int r = 0; r < SP_ROUNDS; r++) {
         const int64_t i = base + r * 32 + l;
@@ -241,13 +286,13 @@ __global__ void __launch_bounds__(SP_THREADS) sp_flag_kernel(const T *__restrict
     }
 #pragma unroll
     for (int r = 0; r < SP_ROUNDS; r++)
-        hv[r] = (uint64_t)(int64_t)e[r] < (uint64_t)n_verts ? __ldg(H + (int64_t)e[r]) : (T)0;
+        hv[r] = (uint64_t)(int64_t)e[r] < (uint64_t)n_verts ? __ldg(H + (int64_t)e[r]) : (HT)0;
     unsigned cnt = 0;
 #pragma unroll
     for (int r = 0; r < SP_ROUNDS; r++) {
         const int64_t i = base + r * 32 + l;
-        const bool in = (uint64_t)(int64_t)e[r] < (uint64_t)n_verts;  // false for i >= n (e = -1)
-        const bool k = in && __ldcs(is + i) == hv[r];
+        const bool in = (uint64_t)(int64_t)e[r] < (uint64_t)n_verts;  // false past n (e = -1)
+        const bool k = in && (int64_t)__ldcs(is + i) == (int64_t)hv[r];
         const unsigned word = __ballot_sync(FULL, k);
         if (l == 0) keep[(base + r * 32) >> 5] = word;
         cnt += __popc(word);
@@ -261,7 +306,23 @@ __global__ void __launch_bounds__(SP_THREADS) sp_flag_kernel(const T *__restrict
     }
 }
 
-// Pass 2: each kept element goes to (tile offset) + (kept before it in its tile).
+// wide: compare with H (the index type); otherwise with the 32-bit H32 unless
+// the narrow reduce-by-index flagged a priority outside its range (h->flag).
+template <typename T>
+__global__ void __launch_bounds__(SP_THREADS) sp_flag_kernel(const T *__restrict__ es, const T *__restrict__ is,
+                                                             int64_t n, int64_t n_verts, const T *__restrict__ H,
+                                                             const uint32_t *__restrict__ H32, int wide, const Hdr *h,
+                                                             uint32_t *__restrict__ keep,
+                                                             unsigned long long *__restrict__ tile_cnt) {
+    IXP_KERNEL_ENTRY();
+    __shared__ unsigned s_w[SP_THREADS / 32];
+    if (wide || h->flag)
+        sp_flag_tile<T, T>(es, is, n, n_verts, H, keep, tile_cnt, s_w);
+    else
+        sp_flag_tile<T, uint32_t>(es, is, n, n_verts, H32, keep, tile_cnt, s_w);
+}
+
+// Pass 2: each kept slot goes to (tile offset) + (kept slots before it in its tile).
 template <typename T>
 __global__ void __launch_bounds__(SP_THREADS) sp_write_kernel(const T *__restrict__ es, const T *__restrict__ is,
                                                               int64_t n, const uint32_t *__restrict__ keep,
@@ -297,18 +358,35 @@ __global__ void __launch_bounds__(SP_THREADS) sp_write_kernel(const T *__restric
 }
 
 template <typename T>
-static int run_smallest_pairs(const T *es, const T *is, int64_t n, int64_t n_verts, T neutral, T *out_es, T *out_is,
-                              int64_t *d_count, void *ws, size_t ws_bytes, cudaStream_t st) {
+static int run_smallest_pairs(const T *es, const T *is, int64_t n, int64_t n_verts, int64_t n_es, T *out_es,
+                              T *out_is, int64_t *d_count, void *ws, size_t ws_bytes, cudaStream_t st) {
     const SpWs w = sp_ws(ws, n, n_verts, (int)sizeof(T));
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || ws_bytes < w.bytes) return IXP_E_WORKSPACE;
     if (cudaMemsetAsync(w.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
     if (cudaMemsetAsync(d_count, 0, sizeof(int64_t), st) != cudaSuccess) return IXP_E_CUDA;
     if (n == 0 || n_verts == 0) return launch_status();
     T *H = reinterpret_cast<T *>(w.H);
-    fill_kernel<T><<<stream_grid(n_verts, 4), STREAM_THREADS, 0, st>>>(H, n_verts, neutral);
-    launch_hist<T, T>(H, n_verts, es, is, n, st);
+    const int gf = stream_grid(n_verts, 4);
+    int wide = 1;
+    if (sizeof(T) == 4 || n_es < 0) {
+        // int32 priorities, or a negative neutral element (below every priority a
+        // 32-bit H holds): the reduce-by-index in the index type
+        fill_kernel<T><<<gf, STREAM_THREADS, 0, st>>>(H, n_verts, (T)n_es, nullptr);
+        launch_hist<T, T>(H, n_verts, es, is, n, st);
+    } else {
+        wide = 0;
+        const uint32_t neutral = (uint32_t)std::min<int64_t>(n_es, 0xffffffffll);
+        fill_kernel<uint32_t><<<gf, STREAM_THREADS, 0, st>>>(w.H32, n_verts, neutral, nullptr);
+        const int vec = aligned16(es) && aligned16(is);
+        hist_min_narrow_kernel<<<stream_grid((n + 3) / 4, 1), STREAM_THREADS, 0, st>>>(
+            w.H32, n_verts, (const int64_t *)es, (const int64_t *)is, n, vec, w.h);
+        // only when a priority did not fit: the 64-bit H
+        fill_kernel<T><<<gf, STREAM_THREADS, 0, st>>>(H, n_verts, (T)n_es, w.h);
+        launch_hist<T, T>(H, n_verts, es, is, n, st, w.h);
+    }
     const int64_t nt = (n + SP_TILE - 1) / SP_TILE;
-    sp_flag_kernel<T><<<(unsigned)nt, SP_THREADS, 0, st>>>(es, is, n, n_verts, H, w.keep, w.tile_cnt);
+    sp_flag_kernel<T><<<(unsigned)nt, SP_THREADS, 0, st>>>(es, is, n, n_verts, H, w.H32, wide, w.h, w.keep,
+                                                           w.tile_cnt);
     scan_tile_counts(w.tile_cnt, nt, w.gtot, w.h, st);
     sp_write_kernel<T><<<(unsigned)nt, SP_THREADS, 0, st>>>(es, is, n, w.keep, w.tile_cnt, w.h, out_es, out_is,
                                                            d_count);
@@ -374,13 +452,13 @@ extern "C" int ixp_smallest_pairs(const void *es, const void *is, int itype, int
         return IXP_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     if (itype == IXP_I64)
-        return run_smallest_pairs((const int64_t *)es, (const int64_t *)is, n, n_verts, (int64_t)n_es,
-                                  (int64_t *)out_es, (int64_t *)out_is, d_count, ws, ws_bytes, st);
+        return run_smallest_pairs((const int64_t *)es, (const int64_t *)is, n, n_verts, n_es, (int64_t *)out_es,
+                                  (int64_t *)out_is, d_count, ws, ws_bytes, st);
     // int32 priorities: a neutral element above INT32_MAX acts as INT32_MAX (no
     // priority exceeds it); one below INT32_MIN is below every priority, so
     // nothing is kept.
     if (n_es < (int64_t)INT32_MIN) n = 0;
-    const int32_t neutral = (int32_t)std::min<int64_t>(n_es, INT32_MAX);
+    const int64_t neutral = std::min<int64_t>(n_es, INT32_MAX);
     return run_smallest_pairs((const int32_t *)es, (const int32_t *)is, n, n_verts, neutral, (int32_t *)out_es,
                               (int32_t *)out_is, d_count, ws, ws_bytes, st);
 }

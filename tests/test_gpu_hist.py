@@ -153,3 +153,27 @@ def test_partition_without_indices(ixp, dev, n):
     assert int(r["num_true"][0].item()) == int(o["num_true"][0]) == int((x < 0.5).sum())
     r2 = ixp.partition(T(bits, dev), pred, payload=T(pay, dev), want_keys=False, want_indices=False)
     assert np.array_equal(r2["payload_out"].cpu().numpy().view(np.uint32), o2["payload_out"].view(np.uint32))
+
+
+@pytest.mark.parametrize("n", [1, 2047, 2048, 2049, 100003])
+def test_smallest_pairs_int64_priorities_outside_32_bits(ixp, dev, n):
+    """int64 priorities reduce in a 32-bit H while they lie in [0, 2^32 - 2]; any
+    other priority of an in-range slot, or a negative neutral element, takes the
+    64-bit H. Every case against the oracle."""
+    es, is_ = synth.graph_slots(n, max(1, n // 6), 900 + n, np.int64)
+    cases = {
+        "fits": (is_, n),
+        "fits_big_neutral": (is_, 2**40),
+        "shifted": (is_ + 2**33, 2**33 + n),
+        "one_at_2^32-1": (np.where(np.arange(n) == n // 2, 2**32 - 1, is_), 2**32),
+        "negative": (is_ - n // 2, n),
+        "negative_neutral": (is_, -5),
+        "neutral_inside": (is_, n // 3),
+    }
+    for name, (pr, n_es) in cases.items():
+        pr = np.ascontiguousarray(pr, dtype=np.int64)
+        oe, oi = oracle.smallest_pairs(max(1, n // 6), n_es, es, pr)
+        ge, gi, cnt = ixp.smallest_pairs(T(es, dev), T(pr, dev), max(1, n // 6), n_es)
+        c = int(cnt.item())
+        assert c == oe.shape[0], name
+        assert np.array_equal(ge[:c].cpu().numpy(), oe) and np.array_equal(gi[:c].cpu().numpy(), oi), name
