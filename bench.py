@@ -719,12 +719,18 @@ def run_partition2(ixp, dev):
         def static_noinit():
             ixp.partition(bits, pred, want_indices=False, out_keys=ys_bits, num_true=nt)
 
+        torch.cuda.nvtx.range_push("p2_dynamic")
         t_dyn = _time(dynamic)
+        torch.cuda.nvtx.range_pop()
         y_dyn = ys.clone()
         ok = ixp.Verdict(vd).get()["ok"]
+        torch.cuda.nvtx.range_push("p2_static")
         t_st = _time(static)
+        torch.cuda.nvtx.range_pop()
         same = bool(torch.equal(ys, y_dyn))
+        torch.cuda.nvtx.range_push("p2_noinit")
         t_no = _time(static_noinit)
+        torch.cuda.nvtx.range_pop()
         same = same and bool(torch.equal(ys, y_dyn))
         del y_dyn
         out["n=%d" % n] = {"dynamic_ms": round(t_dyn, 4), "static_ms": round(t_st, 4),
