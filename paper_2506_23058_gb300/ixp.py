@@ -330,13 +330,16 @@ def filtpart_classes(cls, v, keys=None, filt="true", offsets=None, out_dtype=tor
 
 def scan(x, out_dtype=None, inclusive=False, offsets=None, *, out=None, totals=None, status=None, ws=None,
          stream=None):
-    """Returns (out, totals, status) as device tensors."""
-    out_dtype = out_dtype or x.dtype
+    """Returns (out, totals, status) as device tensors. The totals have the output's
+    dtype (the library writes them in the output type)."""
+    out_dtype = out.dtype if out is not None else (out_dtype or x.dtype)
     n = x.numel()
     out = out if out is not None else torch.empty(n, dtype=out_dtype, device=x.device)
     segs = _segs(offsets)
     if totals is None:
         totals = torch.empty(max(1, segs.nseg), dtype=out_dtype, device=x.device)
+    elif totals.dtype != out.dtype or totals.numel() < max(1, segs.nseg):
+        raise ValueError("totals must have the output's dtype and one entry per segment")
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=x.device)
     need = workspace_size("scan", _itype(x), n, segs.nseg)
     ws = ws if ws is not None else workspace(need, x.device)

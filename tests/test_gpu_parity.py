@@ -696,3 +696,15 @@ def test_mkii(ixp, dev, m, maxlen, p_empty, ot):
     ii, st = ixp.mkii(T(off, dev), n, out_dtype=getattr(torch, np.dtype(ot).name))
     assert st.item() == 0
     assert np.array_equal(ii.cpu().numpy(), oracle.mkii(shape).astype(ot))
+
+
+def test_scan_totals_take_the_output_dtype(ixp, dev):
+    """Totals are written in the output type: an int64 output given without
+    out_dtype still gets int64 totals (a sum past 2^31 does not wrap)."""
+    x = T(np.full(4099, 2**30, np.int32), dev)
+    out = torch.empty(4099, dtype=torch.int64, device=dev)
+    _, tot, st = ixp.scan(x, out=out)
+    assert st.item() == 0 and tot.dtype == torch.int64 and int(tot[0].item()) == 4099 * 2**30
+    assert int(out[-1].item()) == 4098 * 2**30
+    with pytest.raises(ValueError):
+        ixp.scan(x, out=out, totals=torch.empty(1, dtype=torch.int32, device=dev))
