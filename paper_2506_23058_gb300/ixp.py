@@ -135,6 +135,30 @@ def _dev(t: torch.Tensor, name: str):
     return t.data_ptr()
 
 
+def _need(t: torch.Tensor, name: str, n: int, dtypes=None, rows: bool = False):
+    """Checks a buffer the library reads or writes n entries (rows with rows=True) of."""
+    if dtypes is not None and t.dtype not in dtypes:
+        raise ValueError(f"{name} must be one of {dtypes}, not {t.dtype}")
+    have = (t.shape[0] if t.dim() else 1) if rows else t.numel()
+    if have < n:
+        raise ValueError(f"{name} has {have} {'rows' if rows else 'entries'}, {n} needed")
+
+
+def _row_elems(t: torch.Tensor) -> int:
+    per = 1
+    for d in t.shape[1:]:
+        per *= d
+    return per
+
+
+def _pred_flags_ok(pred, n: int):
+    p = make_pred(pred)
+    if p.kind == PREDS["flags"]:
+        fl = pred[3] if isinstance(pred, (tuple, list)) and len(pred) > 3 else None
+        if fl is not None:
+            _need(fl, "flags", n, (torch.uint8,))
+
+
 def _stream(stream):
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
@@ -194,7 +218,10 @@ class Verdict:
 
 
 def _verdict_buf(device, out=None):
-    return out if out is not None else torch.empty(6, dtype=torch.int64, device=device)
+    if out is not None:
+        _need(out, "verdict buffer", 6, (torch.int64,))
+        return out
+    return torch.empty(6, dtype=torch.int64, device=device)
 
 
 # ------------------------------------------------------------------- checks
@@ -261,6 +288,8 @@ def check_inj_seg(x, offsets, rcd_lo=I64MIN, rcd_hi=I64MAX, *, seg_ok=None, out=
     segs = _segs(offsets)
     need = workspace_size("inj_seg", _itype(x), x.numel(), segs.nseg)
     ws = ws if ws is not None else workspace(need, x.device)
+    if seg_ok is not None:
+        _need(seg_ok, "seg_ok", segs.nseg, (torch.uint8,))
     so = None if seg_ok is None else _dev(seg_ok, "seg_ok")
     _ck(load().ixp_check_inj_seg(_dev(x, "x"), _itype(x), x.numel(), rcd_lo, rcd_hi, segs, v.data_ptr(), so,
                                  ws.data_ptr(), ws.numel(), _stream(stream)), "check_inj_seg")
@@ -273,6 +302,8 @@ def check_bij_seg(x, offsets, rcd_lo=I64MIN, rcd_hi=I64MAX, *, seg_ok=None, out=
     segs = _segs(offsets)
     need = workspace_size("bij_seg", _itype(x), x.numel(), segs.nseg)
     ws = ws if ws is not None else workspace(need, x.device)
+    if seg_ok is not None:
+        _need(seg_ok, "seg_ok", segs.nseg, (torch.uint8,))
     so = None if seg_ok is None else _dev(seg_ok, "seg_ok")
     _ck(load().ixp_check_bij_seg(_dev(x, "x"), _itype(x), x.numel(), rcd_lo, rcd_hi, segs, v.data_ptr(), so,
                                  ws.data_ptr(), ws.numel(), _stream(stream)), "check_bij_seg")
@@ -287,6 +318,10 @@ def check_filtpart(z, keys=None, filt="true", part="true", offsets=None, *, cls=
         return _check_filtpart_classes(z, keys, filt, cls, v, offsets, out=out, ws=ws, stream=stream)
     v = _verdict_buf(z.device, out)
     segs = _segs(offsets)
+    if keys is not None:
+        _need(keys, "keys", z.numel())
+    _pred_flags_ok(filt, z.numel())
+    _pred_flags_ok(part, z.numel())
     kt = _itype(keys) if keys is not None else 0
     need = workspace_size("filtpart", kt, z.numel(), segs.nseg)
     ws = ws if ws is not None else workspace(need, z.device)
@@ -299,6 +334,10 @@ def check_filtpart(z, keys=None, filt="true", part="true", offsets=None, *, cls=
 def _check_filtpart_classes(z, keys, filt, cls, v, offsets, *, out=None, ws=None, stream=None) -> Verdict:
     vb = _verdict_buf(z.device, out)
     segs = _segs(offsets)
+    _need(cls, "cls", z.numel(), (torch.uint8,))
+    if keys is not None:
+        _need(keys, "keys", z.numel())
+    _pred_flags_ok(filt, z.numel())
     kt = _itype(keys) if keys is not None else 0
     need = workspace_size("filtpart_classes", int(v), z.numel(), segs.nseg)
     ws = ws if ws is not None else workspace(need, z.device)
@@ -315,8 +354,14 @@ def filtpart_classes(cls, v, keys=None, filt="true", offsets=None, out_dtype=tor
     Returns (out_idx, kept) with kept = N as a 1-element int64 device tensor."""
     n = cls.numel() if n is None else n
     segs = _segs(offsets)
+    _need(cls, "cls", n, (torch.uint8,))
+    if keys is not None:
+        _need(keys, "keys", n)
+    _pred_flags_ok(filt, n)
     out = out if out is not None else torch.empty(n, dtype=out_dtype, device=cls.device)
+    _need(out, "out", n, (torch.int32, torch.int64))
     kept = kept if kept is not None else torch.empty(1, dtype=torch.int64, device=cls.device)
+    _need(kept, "kept", 1, (torch.int64,))
     kt = _itype(keys) if keys is not None else 0
     need = workspace_size("filtpart_classes", int(v), n, segs.nseg)
     ws = ws if ws is not None else workspace(need, cls.device)
@@ -359,15 +404,25 @@ def partition(keys, pred, payload=None, out_dtype=torch.int32, offsets=None, *, 
     else:
         device = pred[3].device if isinstance(pred, (tuple, list)) else torch.device("cuda")
     segs = _segs(offsets)
+    _pred_flags_ok(pred, n)
     if want_indices:
         out = out if out is not None else torch.empty(n, dtype=out_dtype, device=device)
+        _need(out, "out", n, (torch.int32, torch.int64))
     else:
         out = None
     if want_keys and keys is not None and out_keys is None:
         out_keys = torch.empty_like(keys)
-    if payload is not None and out_payload is None:
-        out_payload = torch.empty_like(payload)
+    if want_keys and out_keys is not None:
+        _need(out_keys, "out_keys", n, (keys.dtype,))
+    if payload is not None:
+        _need(payload, "payload", n, rows=True)
+        if out_payload is None:
+            out_payload = torch.empty_like(payload)
+        _need(out_payload, "out_payload", n, (payload.dtype,), rows=True)
+        if _row_elems(out_payload) != _row_elems(payload):
+            raise ValueError("out_payload rows must match payload rows")
     num_true = num_true if num_true is not None else torch.empty(max(1, segs.nseg), dtype=torch.int64, device=device)
+    _need(num_true, "num_true", max(1, segs.nseg), (torch.int64,))
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=device)
     kt = _itype(keys) if keys is not None else 0
     need = workspace_size("partition", kt, n, segs.nseg)
@@ -399,6 +454,9 @@ def scatter(dst, idx, vals, mode="assign", *, stream=None):
     """In place: dst[idx[i]] = vals[i] (or += for mode='add'); out-of-bounds indices are ignored."""
     n = idx.numel()
     row_elems, eb = _rows(vals, n)
+    _need(vals, "vals", n, rows=True)
+    if dst.element_size() != eb or _row_elems(dst) != row_elems:
+        raise ValueError("dst rows must have the element size and width of vals rows")
     _ck(load().ixp_scatter(_dev(dst, "dst"), dst.shape[0], _dev(idx, "idx"), _itype(idx), _dev(vals, "vals"), n,
                            row_elems, eb, 0 if mode == "assign" else 1, _stream(stream)), "scatter")
     return dst
@@ -408,6 +466,10 @@ def scatter_add_f64(acc, idx, vals, *, stream=None):
     """In place: acc (float64) [idx[i]] += vals[i] (float32 rows)."""
     n = idx.numel()
     row_elems = _rows(vals, n)[0]
+    _need(vals, "vals", n, (torch.float32,), rows=True)
+    _need(acc, "acc", 0, (torch.float64,))
+    if _row_elems(acc) != row_elems:
+        raise ValueError("acc rows must have the width of vals rows")
     _ck(load().ixp_scatter_add_f32_to_f64(_dev(acc, "acc"), acc.shape[0], _dev(idx, "idx"), _itype(idx),
                                           _dev(vals, "vals"), n, row_elems, _stream(stream)), "scatter_add_f64")
     return acc
@@ -415,6 +477,7 @@ def scatter_add_f64(acc, idx, vals, *, stream=None):
 
 def f64_to_f32(acc, out=None, *, stream=None):
     out = out if out is not None else torch.empty(acc.shape, dtype=torch.float32, device=acc.device)
+    _need(out, "out", acc.numel(), (torch.float32,))
     _ck(load().ixp_f64_to_f32(_dev(out, "out"), _dev(acc, "acc"), acc.numel(), _stream(stream)), "f64_to_f32")
     return out
 
@@ -423,6 +486,7 @@ def invert(idx, inv_len, out_dtype=None, *, out=None, stream=None):
     """inv[idx[i]] = i for in-bounds idx[i] (idx injective), -1 where nothing lands."""
     out_dtype = out_dtype or idx.dtype
     out = out if out is not None else torch.empty(inv_len, dtype=out_dtype, device=idx.device)
+    _need(out, "out", inv_len, (torch.int32, torch.int64))
     _ck(load().ixp_invert(_dev(idx, "idx"), _itype(idx), idx.numel(), out.data_ptr() if inv_len else None,
                           _itype(out), inv_len, _stream(stream)), "invert")
     return out
@@ -430,6 +494,7 @@ def invert(idx, inv_len, out_dtype=None, *, out=None, stream=None):
 
 def f32_to_f64(x, out=None, *, stream=None):
     out = out if out is not None else torch.empty(x.shape, dtype=torch.float64, device=x.device)
+    _need(out, "out", x.numel(), (torch.float64,))
     _ck(load().ixp_f32_to_f64(_dev(out, "out"), _dev(x, "x"), x.numel(), _stream(stream)), "f32_to_f64")
     return out
 
@@ -439,9 +504,10 @@ def gather(src, idx, *, out=None, status=None, stream=None):
     n = idx.numel()
     shape = (n,) + tuple(src.shape[1:])
     out = out if out is not None else torch.empty(shape, dtype=src.dtype, device=src.device)
-    row_elems = 1
-    for s in src.shape[1:]:
-        row_elems *= s
+    row_elems = _row_elems(src)
+    _need(out, "out", n, (src.dtype,), rows=True)
+    if _row_elems(out) != row_elems:
+        raise ValueError("out rows must have the width of src rows")
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=src.device)
     _ck(load().ixp_gather(_dev(out, "out"), _dev(src, "src"), src.shape[0], _dev(idx, "idx"), _itype(idx), n,
                           row_elems, src.element_size(), status.data_ptr(), _stream(stream)), "gather")
@@ -452,7 +518,10 @@ def gather_segments(src, src_off, seg_src, out_off, n_out, *, out=None, status=N
     """Output segment k = source segment seg_src[k] (CSR rows moved to a new order).
     src/out: 1-D tensors of 4- or 8-byte elements; offsets int64 [m + 1]; n_out = out_off[-1]."""
     m = seg_src.numel()
+    _need(out_off, "out_off", m + 1, (torch.int64,))
+    _need(src_off, "src_off", 1, (torch.int64,))
     out = out if out is not None else torch.empty(n_out, dtype=src.dtype, device=src.device)
+    _need(out, "out", n_out, (src.dtype,))
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=src.device)
     need = workspace_size("gather_segments", 0, n_out)
     ws = ws if ws is not None else workspace(need, src.device)
@@ -481,6 +550,8 @@ def hist_min(H, idx, vals=None, *, stream=None):
     """In place: H[idx[i]] = min(H[idx[i]], vals[i]) for in-bounds idx[i] (vals None: i)."""
     if vals is not None and vals.dtype != H.dtype:
         raise ValueError("vals must have H's dtype")
+    if vals is not None:
+        _need(vals, "vals", idx.numel())
     _ck(load().ixp_hist_min(_dev(H, "H") if H.numel() else None, _itype(H), H.numel(),
                             _dev(idx, "idx") if idx.numel() else None, _itype(idx),
                             None if vals is None else _dev(vals, "vals"), idx.numel(), _stream(stream)), "hist_min")
@@ -496,7 +567,10 @@ def smallest_pairs(es, is_, n_verts, n_es, *, out_es=None, out_is=None, count=No
     n = es.numel()
     out_es = out_es if out_es is not None else torch.empty_like(es)
     out_is = out_is if out_is is not None else torch.empty_like(is_)
+    _need(out_es, "out_es", n, (es.dtype,))  # room for every slot: the kept count is known on the device only
+    _need(out_is, "out_is", n, (es.dtype,))
     count = count if count is not None else torch.empty(1, dtype=torch.int64, device=es.device)
+    _need(count, "count", 1, (torch.int64,))
     need = workspace_size("smallest_pairs", _itype(es), n, n_verts)
     ws = ws if ws is not None else workspace(need, es.device)
     _ck(load().ixp_smallest_pairs(_dev(es, "es") if n else None, _dev(is_, "is") if n else None, _itype(es), n,
@@ -508,7 +582,9 @@ def smallest_pairs(es, is_, n_verts, n_es, *, out_es=None, out_is=None, count=No
 def mkii(offsets, n, out_dtype=torch.int32, *, out=None, status=None, ws=None, stream=None):
     """Segment index of every position: out[j] = k for offsets[k] <= j < offsets[k+1]."""
     m = offsets.numel() - 1
+    _need(offsets, "offsets", 1, (torch.int64,))
     out = out if out is not None else torch.empty(n, dtype=out_dtype, device=offsets.device)
+    _need(out, "out", n, (torch.int32, torch.int64))
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=offsets.device)
     need = workspace_size("gather_segments", 0, n)
     ws = ws if ws is not None else workspace(need, offsets.device)
