@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+from ctypes import c_void_p as C_void
 import os
 import statistics
 import subprocess
@@ -370,6 +371,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ops", default="", help="comma-separated subset of op names (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
+    ap.add_argument("--no-ceilings", action="store_true", help="skip the hardware-rate microbenchmarks")
     ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs"],
                     help="run only this workload and print its result (profiling)")
     args = ap.parse_args()
@@ -467,6 +469,20 @@ def main():
                 "peak_source": peak_src}
     for k in per_op:
         per_op[k]["frac"] = round(per_op[k]["gbs"] / peak, 4)
+    ceilings = None
+    if not args.no_ceilings:
+        ceilings = measure_ceilings(ixp, dev)
+        rows = n32 // 4  # rows of 8 float32 in the scatter / gather workload
+        if dom in ("scatter_rows8", "gather_rows8"):
+            ach = rows / (per_op[dom]["ms"] / 1e3) / 1e9
+            roofline["ceiling"] = {"kind": "random 32-byte rows (measured with a read-only kernel)",
+                                   "rate": ceilings["random_32B_rows_g_per_s"], "achieved": round(ach, 2),
+                                   "unit": "G rows/s", "frac": round(ach / ceilings["random_32B_rows_g_per_s"], 3)}
+        for k in per_op:
+            if k.startswith(("inj_", "bij_")):
+                n_el = n32 if k.endswith("i32") else n64
+                r = n_el / (per_op[k]["ms"] / 1e3) / 1e9
+                per_op[k]["frac_of_l2_atomic_or"] = round(r / ceilings["l2_atomic_or_return_g_per_s"], 3)
 
     # verdict sanity (outside the timed region)
     vd = R.verdicts.cpu().tolist()
@@ -501,7 +517,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32/int64 (index), f32 payload", "data": "synthetic",
             "config": arm_config(n32, n64, args.small, world),
-            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "ops": per_op,
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clk, "ops": per_op, "ceilings": ceilings,
             "verdicts": checks}
     if e2e is not None:
         line["e2e"] = e2e
@@ -682,6 +698,54 @@ def run_csr(ixp, dev, plain_ns_per_byte):
             "bwd_ms": round(bwd, 4), "bwd_gbs": round(bbytes / (bwd / 1e3) / 1e9, 1),
             "verdicts": {"offsets_mono": vo["ok"], "seg_inj": vi["ok"], "seg_mono": vm["ok"],
                          "first_planted_row": int(planted[0])}}
+
+
+def measure_ceilings(ixp, dev, reps=3):
+    """Hardware rates that bound the kernels, from the library's minimal kernels
+    (outside the timed region): L2 atomic OR on a 2^28-bit (32 MiB) bitmap with the
+    old word returned and fire-and-forget, 2^28 random positions; random 32-byte
+    row reads, 2^26 rows of a 2 GiB array; a streaming read of 2 GiB."""
+    import torch
+    lib = ixp.load()
+    st = torch.cuda.current_stream()
+    sp = C_void(st.cuda_stream)
+    sink = torch.empty(lib.ixp_sink_words(), dtype=torch.int32, device=dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.seed_for(9))
+
+    def t_of(fn):
+        for _ in range(2):
+            assert fn() == 0
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    n = bits = 1 << 28
+    pos = torch.randint(-(2**31), 2**31, (n,), generator=g, device=dev, dtype=torch.int32)
+    bm = torch.zeros(bits // 32, dtype=torch.int32, device=dev)
+    ms_ret = t_of(lambda: lib.ixp_ceiling_atomic_or(bm.data_ptr(), bits, pos.data_ptr(), n, 1, sink.data_ptr(), sp))
+    ms_red = t_of(lambda: lib.ixp_ceiling_atomic_or(bm.data_ptr(), bits, pos.data_ptr(), n, 0, sink.data_ptr(), sp))
+    del pos, bm
+    nrows = 1 << 26
+    rows = torch.zeros(nrows * 8, dtype=torch.int32, device=dev)
+    idx = torch.randint(-(2**31), 2**31, (nrows,), generator=g, device=dev, dtype=torch.int32)
+    ms_rows = t_of(lambda: lib.ixp_ceiling_random_rows(rows.data_ptr(), nrows, idx.data_ptr(), nrows, sink.data_ptr(),
+                                                       sp))
+    nbytes = rows.numel() * 4
+    ms_read = t_of(lambda: lib.ixp_ceiling_stream_read(rows.data_ptr(), nbytes, sink.data_ptr(), sp))
+    del rows, idx
+    torch.cuda.empty_cache()
+    return {"l2_atomic_or_return_g_per_s": round(n / ms_ret / 1e6, 1),
+            "l2_atomic_or_no_return_g_per_s": round(n / ms_red / 1e6, 1),
+            "random_32B_rows_g_per_s": round(nrows / ms_rows / 1e6, 2),
+            "stream_read_gbs": round(nbytes / ms_read / 1e6, 1),
+            "how": "library microbenchmark kernels (ceilings.cu), CUDA events, 3 reps after 2 warm-up; "
+                   "32 MiB bitmap, 2^28 random bits; 2^26 random 32-byte rows of 2 GiB; 2 GiB streamed"}
 
 
 def run_partition2(ixp, dev):

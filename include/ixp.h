@@ -376,6 +376,32 @@ int ixp_check_inj_hist(const void *x, int itype, int64_t n, int64_t m, ixp_verdi
 int ixp_smallest_pairs(const void *es, const void *is, int itype, int64_t n, int64_t n_verts, int64_t n_es,
                        void *out_es, void *out_is, int64_t *d_count, void *ws, size_t ws_bytes, ixp_stream stream);
 
+/* ---- hardware-rate microbenchmarks ------------------------------------------------ */
+
+/* The rates that bound the kernels above, measured with minimal kernels so that a
+ * kernel's time can be read against the rate it needs (the paper has no
+ * counterpart; these serve the roofline report). Each writes one checksum word per
+ * block or warp into d_sink (device uint32_t[ixp_sink_words()]) so that nothing is
+ * optimised away; the checksums carry no meaning. */
+int ixp_sink_words(void);
+
+/* L2 atomic OR: for each i, bit pos[i] & (bits - 1) of the device bitmap (bits a
+ * power of two, bits / 32 words) is set with atomicOr; with_return != 0 folds the
+ * returned old word (what a bitmap duplicate test needs), 0 leaves it unused (a
+ * fire-and-forget reduction). pos: device uint32_t[n], 16-byte aligned, n a
+ * multiple of 4. */
+int ixp_ceiling_atomic_or(unsigned *bitmap, int64_t bits, const unsigned *pos, int64_t n, int with_return,
+                          unsigned *d_sink, ixp_stream stream);
+
+/* Random 32-byte rows: item i reads row idx[i] & (nrows - 1) of rows (device,
+ * 16-byte aligned, nrows a power of two up to 2^32, 32 bytes per row). idx: device
+ * uint32_t[n], 16-byte aligned, n a multiple of 4. */
+int ixp_ceiling_random_rows(const void *rows, int64_t nrows, const unsigned *idx, int64_t n, unsigned *d_sink,
+                            ixp_stream stream);
+
+/* Streaming read of bytes (a multiple of 16) from src (16-byte aligned). */
+int ixp_ceiling_stream_read(const void *src, int64_t bytes, unsigned *d_sink, ixp_stream stream);
+
 /* ---- batched pipeline over a jagged array ---------------------------------------- */
 
 /* Launch shape of ixp_batch_run (the autotuner's search space): threads per CTA

@@ -93,8 +93,10 @@ extern "C" unsigned long long ixp_tu_kernels_segmented(void);
 extern "C" unsigned long long ixp_tu_kernels_batched(void);
 extern "C" unsigned long long ixp_tu_kernels_classes(void);
 extern "C" unsigned long long ixp_tu_kernels_hist(void);
+extern "C" unsigned long long ixp_tu_kernels_ceilings(void);
 
 extern "C" unsigned long long ixp_kernel_launches(void) {
     return ixp_tu_kernels_checks() + ixp_tu_kernels_scan() + ixp_tu_kernels_scatter() + ixp_tu_kernels_segmented() +
-           ixp_tu_kernels_batched() + ixp_tu_kernels_classes() + ixp_tu_kernels_hist();
+           ixp_tu_kernels_batched() + ixp_tu_kernels_classes() + ixp_tu_kernels_hist() +
+           ixp_tu_kernels_ceilings();
 }

@@ -82,6 +82,10 @@ _SIGS = {
     "ixp_hist_min": (_I, [_P, _I, _L, _P, _I, _P, _L, _P]),
     "ixp_check_inj_hist": (_I, [_P, _I, _L, _L, _P, _P, _Z, _P]),
     "ixp_smallest_pairs": (_I, [_P, _P, _I, _L, _L, _L, _P, _P, _P, _P, _Z, _P]),
+    "ixp_sink_words": (_I, []),
+    "ixp_ceiling_atomic_or": (_I, [_P, _L, _P, _L, _I, _P, _P]),
+    "ixp_ceiling_random_rows": (_I, [_P, _L, _P, _L, _P, _P]),
+    "ixp_ceiling_stream_read": (_I, [_P, _L, _P, _P]),
     "ixp_debug_set_wait": (_I, [C.c_longlong, C.c_longlong]),
     "ixp_kernel_launches": (C.c_ulonglong, []),
     "ixp_batch_workspace_size": (_Z, [_P]),

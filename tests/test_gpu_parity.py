@@ -708,3 +708,24 @@ def test_scan_totals_take_the_output_dtype(ixp, dev):
     assert int(out[-1].item()) == 4098 * 2**30
     with pytest.raises(ValueError):
         ixp.scan(x, out=out, totals=torch.empty(1, dtype=torch.int32, device=dev))
+
+
+def test_ceiling_microbenchmarks_run_and_check_arguments(ixp, dev):
+    """The rate microbenchmarks run (a bitmap OR with and without the returned word
+    sets exactly the requested bits) and reject sizes that are not powers of two."""
+    import ctypes
+    lib = ixp.load()
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    sink = torch.empty(lib.ixp_sink_words(), dtype=torch.int32, device=dev)
+    pos = T(np.array([3, 35, 64 + 3, 1 << 20, 7, 3, 9, 1023], dtype=np.uint32).view(np.int32), dev)
+    for ret in (0, 1):
+        bm = torch.zeros(32, dtype=torch.int32, device=dev)  # 1024 bits
+        assert lib.ixp_ceiling_atomic_or(bm.data_ptr(), 1024, pos.data_ptr(), 8, ret, sink.data_ptr(), s) == 0
+        bits = np.unpackbits(bm.cpu().numpy().view(np.uint8), bitorder="little")
+        assert sorted(np.flatnonzero(bits).tolist()) == [0, 3, 7, 9, 35, 67, 1023]
+    assert lib.ixp_ceiling_atomic_or(bm.data_ptr(), 1000, pos.data_ptr(), 8, 1, sink.data_ptr(), s) != 0
+    rows = torch.zeros(64 * 8, dtype=torch.int32, device=dev)
+    assert lib.ixp_ceiling_random_rows(rows.data_ptr(), 64, pos.data_ptr(), 8, sink.data_ptr(), s) == 0
+    assert lib.ixp_ceiling_random_rows(rows.data_ptr(), 63, pos.data_ptr(), 8, sink.data_ptr(), s) != 0
+    assert lib.ixp_ceiling_stream_read(rows.data_ptr(), rows.numel() * 4, sink.data_ptr(), s) == 0
+    torch.cuda.synchronize()
