@@ -372,7 +372,7 @@ def main():
     ap.add_argument("--ops", default="", help="comma-separated subset of op names (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
     ap.add_argument("--no-ceilings", action="store_true", help="skip the hardware-rate microbenchmarks")
-    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs"],
+    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes"],
                     help="run only this workload and print its result (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -383,8 +383,14 @@ def main():
         import paper_2506_23058_gb300 as ixp
         ixp.load()
         dev = torch.device("cuda", 0)
-        fn = {"partition2": run_partition2, "smallest_pairs": run_matching}[args.extra]
-        print(json.dumps({"extra": args.extra, "result": fn(ixp, dev)}))
+        if args.extra == "classes":
+            n32 = 1 << 28
+            keys = synth.t_keys_uniform(n32, synth.seed_for(1) + 7, dev)
+            res = run_classes(ixp, {"keys": keys}, n32, dev, None)
+        else:
+            fn = {"partition2": run_partition2, "smallest_pairs": run_matching}[args.extra]
+            res = fn(ixp, dev)
+        print(json.dumps({"extra": args.extra, "result": res}))
         return
 
     import torch
@@ -640,7 +646,8 @@ def run_classes(ixp, inp, n32, dev, plain_ns_per_byte):
             "partition_ms": round(fwd, 4), "partition_gbs": round(nb / (fwd / 1e3) / 1e9, 1),
             "check_ms": round(chk, 4), "check_gbs": round(nb / (chk / 1e3) / 1e9, 1),
             "check_ok": vd.get()["ok"], "kept": int(kept.item()),
-            "time_per_byte_vs_plain": round((fwd * 1e6 / nb) / plain_ns_per_byte, 3)}
+            "time_per_byte_vs_plain": (round((fwd * 1e6 / nb) / plain_ns_per_byte, 3)
+                                       if plain_ns_per_byte else None)}
 
 
 def run_csr(ixp, dev, plain_ns_per_byte):

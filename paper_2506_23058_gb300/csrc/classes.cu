@@ -112,17 +112,16 @@ __device__ __forceinline__ unsigned cl_load4(const KT *__restrict__ keys, const 
     return out;
 }
 
-// Per class k < VS: how many of the 4 packed elements have class k.
-template <int VS>
-__device__ __forceinline__ void cl_count4(unsigned packed, unsigned (&ck)[VS]) {
-#pragma unroll
-    for (int k = 0; k < VS; k++) ck[k] = 0;
+// Per class k < 4: how many of the 4 packed elements have class k, one byte per
+// class (byte k of the result; at most 4 each).
+__device__ __forceinline__ unsigned cl_onehot4(unsigned packed) {
+    unsigned x = 0;
 #pragma unroll
     for (int e = 0; e < 4; e++) {
         const unsigned b = (packed >> (8 * e)) & 0xffu;
-#pragma unroll
-        for (int k = 0; k < VS; k++) ck[k] += b == (unsigned)(k + 1);
+        x += b ? 1u << (8 * (b - 1u)) : 0u;
     }
+    return x;
 }
 
 // Small v (v <= VS), pass 1: lanes take 4 consecutive elements; class counts are
@@ -137,20 +136,16 @@ __global__ void __launch_bounds__(CL_THREADS) cl_count4_kernel(const KT *__restr
     if (threadIdx.x < VS) s_h[threadIdx.x] = 0u;
     __syncthreads();
     const int64_t t0 = blockIdx.x * (int64_t)CL_TILE;
-    unsigned acc[VS];
-#pragma unroll
-    for (int k = 0; k < VS; k++) acc[k] = 0;
+    static_assert(VS <= 4 && CL_TILE / CL_THREADS <= 252, "byte-packed class counters");
+    unsigned acc = 0;  // byte k: class-k elements of this lane (at most CL_TILE / CL_THREADS)
 #pragma unroll
     for (int r = 0; r < CL_TILE / (4 * CL_THREADS); r++) {
         const int64_t p0 = t0 + ((int64_t)r * CL_THREADS + threadIdx.x) * 4;
-        unsigned ck[VS];
-        cl_count4<VS>(cl_load4<KT>(keys, cls, filt, v, p0, n, vec_ok), ck);
-#pragma unroll
-        for (int k = 0; k < VS; k++) acc[k] += ck[k];
+        acc += cl_onehot4(cl_load4<KT>(keys, cls, filt, v, p0, n, vec_ok));
     }
 #pragma unroll
     for (int k = 0; k < VS; k++) {
-        const unsigned t = __reduce_add_sync(FULL, acc[k]);
+        const unsigned t = __reduce_add_sync(FULL, (acc >> (8 * k)) & 0xffu);
         if ((threadIdx.x & 31) == 0 && t) atomicAdd(&s_h[k], t);
     }
     __syncthreads();
@@ -163,7 +158,7 @@ __global__ void __launch_bounds__(CL_THREADS) cl_count4_kernel(const KT *__restr
 // shared memory; then each element's destination is its class offset in the tile
 // plus the warp, lane and in-lane ranks.
 template <typename KT, typename ZT, bool WRITE, int VS>
-__global__ void __launch_bounds__(CL_THREADS) cl_check4_kernel(const ZT *__restrict__ z, const KT *__restrict__ keys,
+__global__ void __launch_bounds__(CL_THREADS, 4) cl_check4_kernel(const ZT *__restrict__ z, const KT *__restrict__ keys,
                                                                const uint8_t *__restrict__ cls, int64_t n,
                                                                DPred filt, int v, int64_t nt, int vec_ok,
                                                                const unsigned *__restrict__ cnt,
@@ -171,43 +166,41 @@ __global__ void __launch_bounds__(CL_THREADS) cl_check4_kernel(const ZT *__restr
                                                                ZT *__restrict__ dst) {
     IXP_KERNEL_ENTRY();
     constexpr int R = CL_TILE / (4 * CL_THREADS);  // rounds of 4 elements per lane
-    __shared__ unsigned s_wt[CL_WARPS][VS];
+    static_assert(VS <= 4, "byte-packed class counters");
+    __shared__ unsigned s_rt[CL_WARPS][R];                   // byte k: class-k elements of the warp's round
+    __shared__ unsigned long long s_base[CL_WARPS][R][VS];   // destination of the round's first class-k element
     __shared__ unsigned long long s_off[VS];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (threadIdx.x < VS) s_off[threadIdx.x] = threadIdx.x < v ? base[threadIdx.x] + cnt[(int64_t)threadIdx.x * nt + blockIdx.x] : 0ull;
     const int64_t wbase = blockIdx.x * (int64_t)CL_TILE + (int64_t)w * (R * 128);
-    unsigned pk[R], lr[R][VS], wc[VS];
-#pragma unroll
-    for (int k = 0; k < VS; k++) wc[k] = 0;
+    // per round: the lane's classes, and (one scan of the byte-packed counts, at
+    // most 128 per class) the class counts of the lanes below it
+    unsigned pk[R], lp[R];
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int64_t p0 = wbase + r * 128 + l * 4;
         pk[r] = cl_load4<KT>(keys, cls, filt, v, p0, n, vec_ok);
-        unsigned ck[VS];
-        cl_count4<VS>(pk[r], ck);
+        const unsigned x = cl_onehot4(pk[r]);
+        unsigned y = x;
 #pragma unroll
-        for (int k = 0; k < VS; k++) {
-            unsigned y = ck[k];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const unsigned o = __shfl_up_sync(FULL, y, d);
-                if (l >= d) y += o;
-            }
-            lr[r][k] = wc[k] + y - ck[k];
-            wc[k] += __shfl_sync(FULL, y, 31);
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y += o;
         }
+        lp[r] = y - x;
+        if (l == 31) s_rt[w][r] = y;
     }
-    if (l == 0)
-#pragma unroll
-        for (int k = 0; k < VS; k++) s_wt[w][k] = wc[k];
     __syncthreads();
+    // class k's elements lie in (warp, round) order inside the tile
     if (threadIdx.x < VS) {
-        unsigned run = 0;
-        for (int ww = 0; ww < CL_WARPS; ww++) {
-            const unsigned x = s_wt[ww][threadIdx.x];
-            s_wt[ww][threadIdx.x] = run;
-            run += x;
-        }
+        const int k = threadIdx.x;
+        unsigned long long run = s_off[k];
+        for (int ww = 0; ww < CL_WARPS; ww++)
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                s_base[ww][r][k] = run;
+                run += (s_rt[ww][r] >> (8 * k)) & 0xffu;
+            }
     }
     __syncthreads();
     const int64_t N = (int64_t)(h->total >> 32);
@@ -217,20 +210,17 @@ __global__ void __launch_bounds__(CL_THREADS) cl_check4_kernel(const ZT *__restr
         const int64_t p0 = wbase + r * 128 + l * 4;
         ZT zv[4];
         if (!WRITE) load_vec<ZT, 4>(z, p0, n, vec_ok, zv);
-        unsigned seen[VS];
-#pragma unroll
-        for (int k = 0; k < VS; k++) seen[k] = 0;
+        unsigned seen = lp[r];  // byte k: class-k elements before the next one of this lane
         ZT out4[4];
 #pragma unroll
         for (int e = 0; e < 4; e++) {
             const unsigned b = (pk[r] >> (8 * e)) & 0xffu;
             int64_t ref = -1;
-#pragma unroll
-            for (int k = 0; k < VS; k++)
-                if (b == (unsigned)(k + 1)) {
-                    ref = (int64_t)(s_off[k] + s_wt[w][k] + lr[r][k] + seen[k]);
-                    seen[k]++;
-                }
+            if (b) {
+                const unsigned sh = 8 * (b - 1u);
+                ref = (int64_t)(s_base[w][r][b - 1u] + ((seen >> sh) & 0xffu));
+                seen += 1u << sh;
+            }
             out4[e] = (ZT)ref;
             const int64_t i = p0 + e;
             if (!WRITE && i < n) {
