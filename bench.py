@@ -372,7 +372,7 @@ def main():
     ap.add_argument("--ops", default="", help="comma-separated subset of op names (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
     ap.add_argument("--no-ceilings", action="store_true", help="skip the hardware-rate microbenchmarks")
-    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes"],
+    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes", "backward"],
                     help="run only this workload and print its result (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -383,10 +383,15 @@ def main():
         import paper_2506_23058_gb300 as ixp
         ixp.load()
         dev = torch.device("cuda", 0)
+        n32 = 1 << 28
         if args.extra == "classes":
-            n32 = 1 << 28
             keys = synth.t_keys_uniform(n32, synth.seed_for(1) + 7, dev)
             res = run_classes(ixp, {"keys": keys}, n32, dev, None)
+        elif args.extra == "backward":
+            s = synth.seed_for(1)
+            inp = {"perm_rows": synth.t_permutation(n32 // 4, s + 9, dev, torch.int32),
+                   "payload8": synth.t_payload_f32(n32 // 4, s + 10, dev, cols=8)}
+            res = run_backward(ixp, inp, n32, dev, None)
         else:
             fn = {"partition2": run_partition2, "smallest_pairs": run_matching}[args.extra]
             res = fn(ixp, dev)
