@@ -39,7 +39,6 @@ int stream_grid(int64_t work_items, int per_thread) {
 
 using namespace ixp;
 
-static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra) {
     if (n < 0) n = 0;

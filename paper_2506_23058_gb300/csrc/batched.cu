@@ -384,7 +384,7 @@ extern "C" int ixp_batch_run(const int64_t *shape, int64_t m, const int32_t *key
                                  d_offsets, d_seg_ok, h, gbm, sbits, st);
     }
     batch_finalize<<<1, 1, 0, st>>>(h, d_first_bad, d_status);
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 extern "C" unsigned long long ixp_tu_kernels_batched(void) {

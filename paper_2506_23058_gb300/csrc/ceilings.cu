@@ -14,7 +14,6 @@
 
 namespace ixp {
 
-static int launch_status() { return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA; }
 
 // One bit per item: bit = pos[i] & (bits - 1) (bits a power of two), set with
 // atomicOr; with RET the old word is folded into the block's checksum.
@@ -101,7 +100,6 @@ extern "C" unsigned long long ixp_tu_kernels_ceilings(void) {
     return v;
 }
 
-static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 extern "C" int ixp_sink_words(void) { return num_sms() * 8 * (STREAM_THREADS / 32); }
 

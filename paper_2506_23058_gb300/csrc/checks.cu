@@ -967,17 +967,8 @@ __global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, Bucket
 
 // ================================================================ host side
 
-static bool aligned_to(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-static int launch_status() {
-    cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? IXP_OK : IXP_E_CUDA;
-}
 
-static int check_ws(void *ws, size_t ws_bytes, size_t need) {
-    if (!ws || !aligned_to(ws, 256) || ws_bytes < need) return IXP_E_WORKSPACE;
-    return IXP_OK;
-}
 
 static int elem_size(int t) { return t == IXP_I32 ? 4 : 8; }
 
@@ -1062,12 +1053,11 @@ namespace ixp {
 constexpr int64_t BK_MIN_N = 1 << 18;
 constexpr unsigned long long BK_MIN_SPAN = 1ull << 21;
 
-static size_t rnd256(size_t b) { return (b + 255) & ~(size_t)255; }
 static unsigned long long bk_pool_entries(int64_t n) {
     return ((unsigned long long)n + (unsigned long long)n / 4 + 4ull * BK_MAX + 3ull) & ~3ull;
 }
 size_t bk_prefix_bytes(int64_t n) {
-    return HDR_BYTES + rnd256(BK_MAX * 4) + rnd256(BK_MAX / 8) + rnd256(bk_pool_entries(n) * 4);
+    return HDR_BYTES + round256(BK_MAX * 4) + round256(BK_MAX / 8) + round256(bk_pool_entries(n) * 4);
 }
 
 struct BitmapWs {
@@ -1086,8 +1076,8 @@ static BitmapWs bitmap_ws(void *ws, size_t ws_bytes, int64_t n) {
     size_t off = HDR_BYTES;
     if (w.buckets) {
         w.cursors = (unsigned *)(p + HDR_BYTES);
-        w.bmask = (unsigned *)(p + HDR_BYTES + rnd256(BK_MAX * 4));
-        w.pool = (unsigned *)(p + HDR_BYTES + rnd256(BK_MAX * 4) + rnd256(BK_MAX / 8));
+        w.bmask = (unsigned *)(p + HDR_BYTES + round256(BK_MAX * 4));
+        w.pool = (unsigned *)(p + HDR_BYTES + round256(BK_MAX * 4) + round256(BK_MAX / 8));
         off = bk_prefix_bytes(n);
     }
     w.cap = ws_bytes > off ? (unsigned long long)((ws_bytes - off) / 8) * 32ull : 0ull;

@@ -585,15 +585,14 @@ __global__ void cl_kept_kernel(const Hdr *h, int64_t *kept) {
     *kept = (int64_t)(h->total >> 32);
 }
 
-static size_t cl_round(size_t b) { return (b + 255) & ~(size_t)255; }
 
 size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg) {
     if (v < 1) v = 1;
     if (n < 0) n = 0;
     const size_t nt = (size_t)((n + CL_TILE - 1) / CL_TILE);
-    const size_t flat = cl_round(nt * (size_t)v * 4) + 2 * cl_round((size_t)v * 8);
+    const size_t flat = round256(nt * (size_t)v * 4) + 2 * round256((size_t)v * 8);
     const size_t ns = (size_t)(nseg > 0 ? nseg : 0);
-    const size_t seg = cl_round((ns + 1) * 8) + cl_round(((ns + CL_G - 1) / CL_G + 1) * 8);
+    const size_t seg = round256((ns + 1) * 8) + round256(((ns + CL_G - 1) / CL_G + 1) * 8);
     return HDR_BYTES + std::max(flat, seg);
 }
 
@@ -610,8 +609,8 @@ static int run_classes(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, co
     if (!segs.offsets) {
         const int64_t nt = (n + CL_TILE - 1) / CL_TILE;
         unsigned *cnt = (unsigned *)p;
-        unsigned long long *tot = (unsigned long long *)(p + cl_round((size_t)nt * v * 4));
-        unsigned long long *base = (unsigned long long *)((char *)tot + cl_round((size_t)v * 8));
+        unsigned long long *tot = (unsigned long long *)(p + round256((size_t)nt * v * 4));
+        unsigned long long *base = (unsigned long long *)((char *)tot + round256((size_t)v * 8));
         if (nt > 0) {
             const unsigned g = (unsigned)nt;
 #define IXP_CL_PASSES(VS)                                                                                       \
@@ -648,7 +647,7 @@ static int run_classes(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, co
     } else {
         const int64_t m = segs.nseg;
         unsigned long long *kc = (unsigned long long *)p;
-        unsigned long long *gtot = (unsigned long long *)(p + cl_round((size_t)(m + 1) * 8));
+        unsigned long long *gtot = (unsigned long long *)(p + round256((size_t)(m + 1) * 8));
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>(m, (int64_t)num_sms() * 8));
         cl_seg_count_kernel<KT><<<g, CL_THREADS, 0, st>>>(keys, cls, n, f, v, segs.offsets, m, kc);
         const unsigned ng = (unsigned)((m + CL_G - 1) / CL_G);
@@ -666,7 +665,7 @@ static int run_classes(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, co
     } else {
         cl_finalize<ZT><<<1, 1, 0, st>>>(z, h, out);
     }
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 }  // namespace ixp

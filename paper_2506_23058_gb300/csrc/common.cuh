@@ -304,6 +304,17 @@ __device__ __forceinline__ void seg_pairs_chunk(const T *__restrict__ x, int64_t
 }
 
 
+// ------------------------------------------------------------ host helpers
+
+static inline int launch_status() { return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA; }
+static inline bool aligned_to(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+static inline bool aligned16(const void *p) { return aligned_to(p, 16); }
+static inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+// A caller workspace: present, 256-byte aligned and at least `need` bytes.
+static inline int check_ws(void *ws, size_t have, size_t need) {
+    return (!ws || !aligned_to(ws, 256) || have < need) ? IXP_E_WORKSPACE : IXP_OK;
+}
+
 // Launch shape for grid-stride streaming kernels: 8 blocks of 256 threads per SM.
 constexpr int STREAM_THREADS = 256;
 int stream_grid(int64_t work_items, int per_thread = 4);

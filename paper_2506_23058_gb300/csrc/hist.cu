@@ -32,9 +32,6 @@
 
 namespace ixp {
 
-static int launch_status() { return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA; }
-static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Four consecutive elements 4q .. 4q + 3 with 16-byte loads (p 16-byte aligned).
 template <typename T> __device__ __forceinline__ void ld4(const T *p, int64_t q, T (&v)[4]);
@@ -208,7 +205,7 @@ __global__ void inj_hist_finalize(const IT *x, const Hdr *h, ixp_verdict *out) {
     *out = v;
 }
 
-size_t inj_hist_ws_bytes(int64_t m) { return HDR_BYTES + up256((size_t)(m > 0 ? m : 0) * 4); }
+size_t inj_hist_ws_bytes(int64_t m) { return HDR_BYTES + round256((size_t)(m > 0 ? m : 0) * 4); }
 
 template <typename IT>
 static int run_inj_hist(const IT *x, int64_t n, int64_t m, ixp_verdict *out, void *ws, cudaStream_t st) {
@@ -250,15 +247,15 @@ static SpWs sp_ws(void *ws, int64_t n, int64_t n_verts, int es) {
     size_t o = HDR_BYTES;
     w.h = reinterpret_cast<Hdr *>(b);
     w.H = b + o;
-    o += up256(nv * es);
+    o += round256(nv * es);
     w.H32 = reinterpret_cast<uint32_t *>(b + o);
-    o += es == 8 ? up256(nv * 4) : 0;
+    o += es == 8 ? round256(nv * 4) : 0;
     w.tile_cnt = reinterpret_cast<unsigned long long *>(b + o);
-    o += up256((size_t)(nt + 1) * 8);
+    o += round256((size_t)(nt + 1) * 8);
     w.gtot = reinterpret_cast<unsigned long long *>(b + o);
-    o += up256((size_t)((nt + TS_G - 1) / TS_G + 1) * 8);
+    o += round256((size_t)((nt + TS_G - 1) / TS_G + 1) * 8);
     w.keep = reinterpret_cast<uint32_t *>(b + o);
-    o += up256((size_t)(nt * SP_TILE / 32) * 4);
+    o += round256((size_t)(nt * SP_TILE / 32) * 4);
     w.bytes = o;
     return w;
 }

@@ -1320,9 +1320,7 @@ __global__ void status_copy_kernel(const Hdr *h, int32_t *d_status) {
 
 // ================================================================ host side
 
-static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-static int launch_status() { return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA; }
 
 static int64_t ntiles_for(int64_t n, int V) { return (n + (int64_t)TB * SUB * V - 1) / ((int64_t)TB * SUB * V); }
 
@@ -1337,7 +1335,6 @@ struct TileWs {
     size_t bytes;
 };
 
-static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 static TileWs tile_ws(void *ws, int64_t ntiles, int64_t nseg) {
     TileWs r;
@@ -1345,13 +1342,13 @@ static TileWs tile_ws(void *ws, int64_t ntiles, int64_t nseg) {
     size_t o = HDR_BYTES;
     r.h = (Hdr *)p;
     r.L.st = (ulonglong2 *)(p + o);
-    o += up256((size_t)ntiles * 16);
+    o += round256((size_t)ntiles * 16);
     r.tile_prefix = (unsigned long long *)(p + o);
-    o += up256((size_t)ntiles * 8);
+    o += round256((size_t)ntiles * 8);
     r.seg_cnt = (unsigned long long *)(p + o);
-    o += up256((size_t)(nseg + 1) * 8);
+    o += round256((size_t)(nseg + 1) * 8);
     r.gtot = (unsigned long long *)(p + o);
-    o += up256((size_t)((ntiles + TS_G - 1) / TS_G + 1) * 8);
+    o += round256((size_t)((ntiles + TS_G - 1) / TS_G + 1) * 8);
     r.bytes = o;
     return r;
 }
@@ -1361,10 +1358,6 @@ size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg) {
     return tile_ws(nullptr, nt, nseg < 0 ? 0 : nseg).bytes;
 }
 
-static int ws_ok(void *ws, size_t have, size_t need) {
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) || have < need) return IXP_E_WORKSPACE;
-    return IXP_OK;
-}
 
 
 template <typename TI, typename TO>
@@ -1374,7 +1367,7 @@ static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs se
     const bool seg = segs.offsets != nullptr;
     const int64_t nt = ntiles_for(n, V);
     TileWs W = tile_ws(ws, nt, seg ? segs.nseg : 0);
-    int rc = ws_ok(ws, ws_bytes, W.bytes);
+    int rc = check_ws(ws, ws_bytes, W.bytes);
     if (rc) return rc;
     if (cudaMemsetAsync(ws, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
     if (nt > 0 && cudaMemsetAsync(W.L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;
@@ -1438,7 +1431,7 @@ static int run_partition(const KT *keys, int64_t n, ixp_pred pred, const void *p
     const bool seg = segs.offsets != nullptr;
     const int64_t nt = ntiles_for(n, V);
     TileWs W = tile_ws(ws, nt, seg ? segs.nseg : 0);
-    int rc = ws_ok(ws, ws_bytes, W.bytes);
+    int rc = check_ws(ws, ws_bytes, W.bytes);
     if (rc) return rc;
     const int vec = (keys == nullptr || aligned16(keys)) && aligned16(out_idx);
     const DPred all{IXP_P_TRUE, 0, 0, nullptr};
@@ -1491,7 +1484,7 @@ static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, i
     const bool seg = segs.offsets != nullptr;
     const int64_t nt = ntiles_for(n, V);
     TileWs W = tile_ws(ws, nt, seg ? segs.nseg : 0);
-    int rc = ws_ok(ws, ws_bytes, W.bytes);
+    int rc = check_ws(ws, ws_bytes, W.bytes);
     if (rc) return rc;
     const int vec = keys == nullptr || aligned16(keys);
     if (!seg) {
@@ -1568,7 +1561,7 @@ extern "C" int ixp_sgm_scan(const uint8_t *flags, const void *in, int in_type, v
     const int V = in_type == IXP_I32 ? 4 : 2;
     const int64_t nt = ntiles_for(n, V);
     TileWs W = tile_ws(ws, nt, 0);
-    int rc = ws_ok(ws, ws_bytes, W.bytes);
+    int rc = check_ws(ws, ws_bytes, W.bytes);
     if (rc) return rc;
     if (cudaMemsetAsync(ws, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
     if (nt > 0 && cudaMemsetAsync(W.L.st, 0, (size_t)nt * 16, st) != cudaSuccess) return IXP_E_CUDA;

@@ -451,7 +451,6 @@ __global__ void __launch_bounds__(GS_THREADS) segment_ids_kernel(OT *__restrict_
     for (int e = threadIdx.x; e < cnt; e += GS_THREADS) out[j0 + e] = (OT)s_seg[gs_heads_upto(s_head, s_pre, e)];
 }
 
-static bool al(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 static int row_grid(int64_t n) { return stream_grid(n, 1); }
 
@@ -466,13 +465,14 @@ extern "C" int ixp_scatter(void *dst, int64_t dst_len, const void *idx, int ityp
     if (n < 0 || dst_len < 0 || row_elems <= 0 || row_elems > 64 || (n > 0 && (!idx || !vals)) ||
         (dst_len > 0 && !dst) || (mode != IXP_SCATTER_ASSIGN && mode != IXP_SCATTER_ADD))
         return IXP_E_INVAL;
-    if (!al(idx, itype == IXP_I32 ? 4 : 8) || !al(vals, elem_bytes) || !al(dst, elem_bytes)) return IXP_E_INVAL;
+    if (!aligned_to(idx, itype == IXP_I32 ? 4 : 8) || !aligned_to(vals, elem_bytes) || !aligned_to(dst, elem_bytes))
+        return IXP_E_INVAL;
     if (n == 0) return IXP_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int rb = row_elems * elem_bytes;
     const int g = row_grid(n);
     if (mode == IXP_SCATTER_ASSIGN) {
-        const int v16 = (rb % 16 == 0) && al(dst, 16) && al(vals, 16);
+        const int v16 = (rb % 16 == 0) && aligned_to(dst, 16) && aligned_to(vals, 16);
         if (v16 && itype == IXP_I32)
             launch_rows_lanes<int32_t, true>((int4 *)dst, dst_len, (const int32_t *)idx, (const int4 *)vals, n, n,
                                              rb / 16, nullptr, st);
@@ -500,7 +500,7 @@ extern "C" int ixp_scatter(void *dst, int64_t dst_len, const void *idx, int ityp
             scatter_add_kernel<int64_t, double><<<g, STREAM_THREADS, 0, st>>>(
                 (double *)dst, dst_len, (const int64_t *)idx, (const double *)vals, n, row_elems);
     }
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 extern "C" int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const void *idx, int itype, const float *vals,
@@ -508,25 +508,25 @@ extern "C" int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const vo
     if (itype != IXP_I32 && itype != IXP_I64) return IXP_E_DTYPE;
     if (n < 0 || dst_len < 0 || row_elems <= 0 || row_elems > 64 || (n > 0 && (!idx || !vals)) || (dst_len > 0 && !acc))
         return IXP_E_INVAL;
-    if (!al(idx, itype == IXP_I32 ? 4 : 8) || !al(vals, 4) || !al(acc, 8)) return IXP_E_INVAL;
+    if (!aligned_to(idx, itype == IXP_I32 ? 4 : 8) || !aligned_to(vals, 4) || !aligned_to(acc, 8)) return IXP_E_INVAL;
     if (n == 0) return IXP_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int g = row_grid(n);
-    const int v16 = al(vals, 16);
+    const int v16 = aligned_to(vals, 16);
     if (itype == IXP_I32)
         scatter_add_f64_kernel<int32_t><<<g, STREAM_THREADS, 0, st>>>(acc, dst_len, (const int32_t *)idx, vals, n,
                                                                       row_elems, v16);
     else
         scatter_add_f64_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>(acc, dst_len, (const int64_t *)idx, vals, n,
                                                                       row_elems, v16);
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 extern "C" int ixp_f64_to_f32(float *out, const double *acc, int64_t count, ixp_stream stream) {
     if (count < 0 || (count > 0 && (!out || !acc))) return IXP_E_INVAL;
     if (count == 0) return IXP_OK;
     f64_to_f32_kernel<<<stream_grid(count, 4), STREAM_THREADS, 0, (cudaStream_t)stream>>>(out, acc, count);
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 template <typename IT, typename OT>
@@ -558,14 +558,14 @@ extern "C" int ixp_invert(const void *idx, int itype, int64_t n, void *inv, int 
         if (inv_type == IXP_I32) invert_kernel<int64_t, int32_t><<<g, STREAM_THREADS, 0, st>>>((const int64_t *)idx, n, (int32_t *)inv, inv_len);
         else invert_kernel<int64_t, int64_t><<<g, STREAM_THREADS, 0, st>>>((const int64_t *)idx, n, (int64_t *)inv, inv_len);
     }
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 extern "C" int ixp_f32_to_f64(double *out, const float *in, int64_t count, ixp_stream stream) {
     if (count < 0 || (count > 0 && (!out || !in))) return IXP_E_INVAL;
     if (count == 0) return IXP_OK;
     f32_to_f64_kernel<<<stream_grid(count, 4), STREAM_THREADS, 0, (cudaStream_t)stream>>>(out, in, count);
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 extern "C" int ixp_gather(void *out, const void *src, int64_t src_len, const void *idx, int itype, int64_t n,
@@ -575,11 +575,12 @@ extern "C" int ixp_gather(void *out, const void *src, int64_t src_len, const voi
     if (n < 0 || src_len < 0 || row_elems <= 0 || row_elems > 64 || (n > 0 && (!idx || !out)) ||
         (src_len > 0 && !src))
         return IXP_E_INVAL;
-    if (!al(idx, itype == IXP_I32 ? 4 : 8) || !al(out, elem_bytes) || !al(src, elem_bytes)) return IXP_E_INVAL;
+    if (!aligned_to(idx, itype == IXP_I32 ? 4 : 8) || !aligned_to(out, elem_bytes) || !aligned_to(src, elem_bytes))
+        return IXP_E_INVAL;
     if (n == 0) return IXP_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int rb = row_elems * elem_bytes;
-    const int v16 = (rb % 16 == 0) && al(out, 16) && al(src, 16);
+    const int v16 = (rb % 16 == 0) && aligned_to(out, 16) && aligned_to(src, 16);
     const int g = row_grid(n);
     if (v16 && itype == IXP_I32)
         launch_rows_lanes<int32_t, false>((int4 *)out, n, (const int32_t *)idx, (const int4 *)src, src_len, n,
@@ -593,7 +594,7 @@ extern "C" int ixp_gather(void *out, const void *src, int64_t src_len, const voi
     else
         gather_rows_kernel<int64_t><<<g, STREAM_THREADS, 0, st>>>((char *)out, (const char *)src, src_len,
                                                                   (const int64_t *)idx, n, rb, d_status);
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 extern "C" int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_off, int64_t m, const void *src,
@@ -605,9 +606,9 @@ extern "C" int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_
     if (m < 0 || src_m < 0 || n_out < 0 || src_len < 0 || !out_off || !src_off ||
         (n_out > 0 && (m == 0 || !seg_src || !out || !src)))
         return IXP_E_INVAL;
-    if (!al(out, elem_bytes) || !al(src, elem_bytes) || !al(seg_src, seg_type == IXP_I32 ? 4 : 8)) return IXP_E_INVAL;
+    if (!aligned_to(out, elem_bytes) || !aligned_to(src, elem_bytes) || !aligned_to(seg_src, seg_type == IXP_I32 ? 4 : 8)) return IXP_E_INVAL;
     if (n_out == 0) return IXP_OK;
-    if (!ws || !al(ws, 256) || ws_bytes < gather_segments_ws_bytes(n_out)) return IXP_E_WORKSPACE;
+    if (!ws || !aligned_to(ws, 256) || ws_bytes < gather_segments_ws_bytes(n_out)) return IXP_E_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     int64_t *k0 = (int64_t *)ws;
     const unsigned g = (unsigned)((n_out + GS_CHUNK - 1) / GS_CHUNK);
@@ -623,7 +624,7 @@ extern "C" int ixp_gather_segments(void *out, int64_t n_out, const int64_t *out_
     else if (seg_type == IXP_I32) IXP_GS(unsigned long long, int32_t);
     else IXP_GS(unsigned long long, int64_t);
 #undef IXP_GS
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 extern "C" int ixp_mkii(const int64_t *offsets, int64_t m, void *out, int out_type, int64_t n, int32_t *d_status,
@@ -631,9 +632,9 @@ extern "C" int ixp_mkii(const int64_t *offsets, int64_t m, void *out, int out_ty
     if (out_type != IXP_I32 && out_type != IXP_I64) return IXP_E_DTYPE;
     if (m < 0 || n < 0 || !offsets || (n > 0 && (m == 0 || !out))) return IXP_E_INVAL;
     if (out_type == IXP_I32 && m > INT32_MAX) return IXP_E_INVAL;
-    if (!al(out, out_type == IXP_I32 ? 4 : 8)) return IXP_E_INVAL;
+    if (!aligned_to(out, out_type == IXP_I32 ? 4 : 8)) return IXP_E_INVAL;
     if (n == 0) return IXP_OK;
-    if (!ws || !al(ws, 256) || ws_bytes < gather_segments_ws_bytes(n)) return IXP_E_WORKSPACE;
+    if (!ws || !aligned_to(ws, 256) || ws_bytes < gather_segments_ws_bytes(n)) return IXP_E_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     int64_t *k0 = (int64_t *)ws;
     const unsigned g = (unsigned)((n + GS_CHUNK - 1) / GS_CHUNK);
@@ -643,7 +644,7 @@ extern "C" int ixp_mkii(const int64_t *offsets, int64_t m, void *out, int out_ty
         segment_ids_kernel<int32_t><<<g, GS_THREADS, 0, st>>>((int32_t *)out, offsets, m, n, k0, d_status);
     else
         segment_ids_kernel<int64_t><<<g, GS_THREADS, 0, st>>>((int64_t *)out, offsets, m, n, k0, d_status);
-    return cudaGetLastError() == cudaSuccess ? IXP_OK : IXP_E_CUDA;
+    return launch_status();
 }
 
 extern "C" unsigned long long ixp_tu_kernels_scatter(void) {
