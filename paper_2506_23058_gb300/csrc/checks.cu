@@ -398,10 +398,30 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) first_dup_kernel(const T *_
     IXP_KERNEL_ENTRY();
     if (h->status || !h->flag) return;
     __shared__ unsigned s_mask[BK_MAX / 32];
+    __shared__ unsigned s_bfirst, s_blast;
     const unsigned long long base = h->base, span = h->span;
-    if (bucket_mask)
-        for (int w = threadIdx.x; w < (int)(BK_MAX / 32); w += blockDim.x) s_mask[w] = bucket_mask[w];
+    if (threadIdx.x == 0) {
+        s_bfirst = ~0u;
+        s_blast = 0u;
+    }
     __syncthreads();
+    if (bucket_mask)
+        for (int w = threadIdx.x; w < (int)(BK_MAX / 32); w += blockDim.x) {
+            const unsigned m = bucket_mask[w];
+            s_mask[w] = m;
+            if (m) {
+                atomicMin(&s_bfirst, (unsigned)w * 32u + (unsigned)(__ffs(m) - 1));
+                atomicMax(&s_blast, (unsigned)w * 32u + (unsigned)(31 - __clz(m)));
+            }
+        }
+    __syncthreads();
+    // values outside the flagged buckets' range [lo_f, lo_f + span_f) hold no repeat
+    unsigned long long lo_f = 0, span_f = span;
+    if (bucket_mask) {
+        if (s_bfirst == ~0u) return;  // no bucket flagged, no repeat to find
+        lo_f = (unsigned long long)s_bfirst << lw;
+        span_f = ((unsigned long long)(s_blast - s_bfirst) + 1ull) << lw;
+    }
     using VT = typename Vec<T>::type;
     constexpr int V = Vec<T>::N;
     Split<T> s(x, n);
@@ -410,9 +430,8 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) first_dup_kernel(const T *_
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     auto one = [&](int64_t i, T xv) {
         const int64_t xi = (int64_t)xv;
-        if (xi < mlo || xi > mhi) return;
         const unsigned long long rel = (unsigned long long)xi - base;
-        if (rel >= span) return;
+        if (rel - lo_f >= span_f || rel >= span || xi < mlo || xi > mhi) return;
         if (bucket_mask) {
             const unsigned b = (unsigned)(rel >> lw);
             if (!(s_mask[b >> 5] & (1u << (b & 31)))) return;
