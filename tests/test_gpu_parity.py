@@ -729,3 +729,25 @@ def test_ceiling_microbenchmarks_run_and_check_arguments(ixp, dev):
     assert lib.ixp_ceiling_random_rows(rows.data_ptr(), 63, pos.data_ptr(), 8, sink.data_ptr(), s) != 0
     assert lib.ixp_ceiling_stream_read(rows.data_ptr(), rows.numel() * 4, sink.data_ptr(), s) == 0
     torch.cuda.synchronize()
+
+
+def test_scatter_add_f64_fixed_point_cache_edges(ixp, dev):
+    """The shared cache keeps exact fixed-point sums at a scale sampled from each
+    block's first rows: rows far below or above that sample, zeros, a long run into
+    one target (more rows per block than the sample suggests) and wide dynamic
+    ranges must all match the float64 oracle."""
+    rng = np.random.default_rng(91)
+    n, m = 1 << 20, 512
+    idx = synth.zipf_ranks(n, m, 1.1, 92)
+    scales = np.where(rng.random(n) < 0.5, 1e-3, 1.0)
+    scales[rng.random(n) < 0.01] = 1e-30   # far below any block's sample
+    scales[n // 2:][rng.random(n - n // 2) < 0.01] = 1e12  # far above, late in the array
+    vals = (rng.uniform(-1, 1, size=(n, 8)) * scales[:, None]).astype(np.float32)
+    vals[rng.random(n) < 0.05] = 0.0
+    for idx_case in (idx, np.zeros(n, np.int32)):  # the Zipf case, then every row into target 0
+        acc = torch.zeros((m, 8), dtype=torch.float64, device=dev)
+        ixp.scatter_add_f64(acc, T(idx_case, dev), T(vals, dev))
+        ref = oracle.scatter_add_f64(m, idx_case, vals)
+        mag = oracle.scatter_add_f64(m, idx_case, np.abs(vals))
+        got = acc.cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 1e-12 * mag + 1e-300), np.max(np.abs(got - ref) / (mag + 1e-300))
