@@ -372,7 +372,7 @@ def main():
     ap.add_argument("--ops", default="", help="comma-separated subset of op names (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
     ap.add_argument("--no-ceilings", action="store_true", help="skip the hardware-rate microbenchmarks")
-    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes", "backward"],
+    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes", "backward", "segmented"],
                     help="run only this workload and print its result (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -387,6 +387,13 @@ def main():
         if args.extra == "classes":
             keys = synth.t_keys_uniform(n32, synth.seed_for(1) + 7, dev)
             res = run_classes(ixp, {"keys": keys}, n32, dev, None)
+        elif args.extra == "segmented":
+            s = synth.seed_for(1)
+            g = torch.Generator(device=dev)
+            g.manual_seed(s + 6)
+            inp = {"steps_i32": torch.randint(0, 4, (n32,), generator=g, device=dev, dtype=torch.int32),
+                   "shape": torch.from_numpy(synth.shapes_log_uniform(4096, s + 11, cap_total=n32)).to(dev)}
+            res = run_segmented(ixp, inp, n32, dev, None)
         elif args.extra == "backward":
             s = synth.seed_for(1)
             inp = {"perm_rows": synth.t_permutation(n32 // 4, s + 9, dev, torch.int32),
@@ -515,6 +522,7 @@ def main():
         extras["batched"] = run_batched(ixp, inp, n32, dev, plain_ns_per_byte, args)
         extras["backward"] = run_backward(ixp, inp, n32, dev, per_op)
         extras["classes"] = run_classes(ixp, inp, n32, dev, plain_ns_per_byte)
+        extras["segmented"] = run_segmented(ixp, inp, n32, dev, plain_ns_per_byte)
         if not args.small:
             del inp, R
             torch.cuda.empty_cache()
@@ -653,6 +661,51 @@ def run_classes(ixp, inp, n32, dev, plain_ns_per_byte):
             "check_ok": vd.get()["ok"], "kept": int(kept.item()),
             "time_per_byte_vs_plain": (round((fwd * 1e6 / nb) / plain_ns_per_byte, 3)
                                        if plain_ns_per_byte else None)}
+
+
+def run_segmented(ixp, inp, n32, dev, plain_ns_per_byte):
+    """The standalone flattening blocks of Fig. 2 over the step's 4096-segment
+    log-uniform shape (sum = the 2^28 int32 elements it covers): sgmSum, the
+    inclusive segmented scan of int32 values in [0, 4) under uint8 start flags;
+    the same scan with the segments given by their offsets (and per-segment
+    totals); and mkII, the segment index of every position from the offsets."""
+    import torch
+    shape = inp["shape"]
+    offs = torch.empty(shape.numel() + 1, dtype=torch.int64, device=dev)
+    ixp.flags_from_shape(shape, out_dtype=torch.int32, offsets=offs)
+    total = int(offs[-1].item())
+    starts = offs[:-1][shape > 0]
+    flags = torch.zeros(total, dtype=torch.uint8, device=dev)
+    flags[starts] = 1
+    x = inp["steps_i32"][:total]
+    out = torch.empty(total, dtype=torch.int32, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = ixp.workspace(ixp.workspace_size("scan", 0, total, 0), dev)
+    t_scan = _time(lambda: ixp.sgm_scan(flags, x, out=out, status=st, ws=ws))
+    m = shape.numel()
+    tots = torch.empty(m, dtype=torch.int32, device=dev)
+    ws3 = ixp.workspace(ixp.workspace_size("scan", 0, total, m), dev)
+    out2 = torch.empty(total, dtype=torch.int32, device=dev)
+    t_off = _time(lambda: ixp.scan(x, inclusive=True, offsets=offs, out=out2, totals=tots, status=st, ws=ws3))
+    ii = torch.empty(total, dtype=torch.int32, device=dev)
+    ws2 = ixp.workspace(ixp.workspace_size("gather_segments", 0, total), dev)
+    t_ii = _time(lambda: ixp.mkii(offs, total, out=ii, status=st, ws=ws2))
+    # spot checks against closed forms: the last element of each segment is its sum,
+    # and mkII is constant k on segment k
+    ends = offs[1:][shape > 0] - 1
+    seg_sum = torch.zeros(shape.numel(), dtype=torch.int64, device=dev)
+    seg_sum.index_add_(0, ii.long(), x.long())
+    ok_scan = bool(torch.equal(out[ends].long(), seg_sum[shape > 0])) and bool(torch.equal(out, out2))
+    ok_ii = bool(torch.equal(ii[starts].long(), torch.nonzero(shape > 0).flatten()))
+    nb_scan, nb_ii = 9 * total, 4 * total + 8 * offs.numel()
+    return {"workload": "%d segments log-uniform in [1, 2^20], %d int32 elements" % (shape.numel(), total),
+            "sgm_scan_ms": round(t_scan, 4), "sgm_scan_gbs": round(nb_scan / (t_scan / 1e3) / 1e9, 1),
+            "seg_scan_offsets_ms": round(t_off, 4),
+            "seg_scan_offsets_gbs": round((8 * total + 16 * m) / (t_off / 1e3) / 1e9, 1),
+            "mkii_ms": round(t_ii, 4), "mkii_gbs": round(nb_ii / (t_ii / 1e3) / 1e9, 1),
+            "checks_ok": ok_scan and ok_ii and int(st.item()) == 0,
+            "sgm_scan_time_per_byte_vs_plain": (round((t_scan * 1e6 / nb_scan) / plain_ns_per_byte, 3)
+                                                if plain_ns_per_byte else None)}
 
 
 def run_csr(ixp, dev, plain_ns_per_byte):

@@ -236,25 +236,55 @@ constexpr int BK_TILE = 8192;
 constexpr int BK_THREADS = 256;
 constexpr unsigned BK_MAX = 4096;
 
-// Min/max of the in-codomain values (needed when Rcd is unbounded).
+// Min/max of the in-codomain values (needed when Rcd is unbounded). The bounds
+// come clamped to T, so every compare is in T; a vector that lies wholly inside
+// [lo, hi] (the common case) folds its own min/max in one step. A thread that saw
+// nothing ends with mn > mx and contributes the empty encodings.
 template <typename T>
-__global__ void __launch_bounds__(STREAM_THREADS, 4) minmax_in_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
-                                                                   int64_t rhi, Hdr *h) {
+__global__ void __launch_bounds__(STREAM_THREADS, 4) minmax_in_kernel(const T *__restrict__ x, int64_t n, T lo, T hi,
+                                                                   Hdr *h) {
     IXP_KERNEL_ENTRY();
     using VT = typename Vec<T>::type;
     constexpr int V = Vec<T>::N;
     Split<T> s(x, n);
-    int64_t mn = INT64_MAX, mx = INT64_MIN;
+    T mn = Lim<T>::hi, mx = Lim<T>::lo;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    auto visit = [&](int64_t xi) {
-        if (xi >= rlo && xi <= rhi) {
+    auto one = [&](T xi) {
+        if ((xi >= lo) & (xi <= hi)) {
             mn = xi < mn ? xi : mn;
             mx = xi > mx ? xi : mx;
         }
     };
-    for (int64_t i = tid; i < s.head; i += stride) visit(ld1(x, i));
-    for (int64_t i = s.tail0 + tid; i < n; i += stride) visit(ld1(x, i));
+    auto vec = [&](const VT &a) {
+        T e[V];
+        if (V == 4) {
+            const int4 &q = reinterpret_cast<const int4 &>(a);
+            e[0] = (T)q.x;
+            e[1 % V] = (T)q.y;
+            e[2 % V] = (T)q.z;
+            e[3 % V] = (T)q.w;
+        } else {
+            const longlong2 &q = reinterpret_cast<const longlong2 &>(a);
+            e[0] = (T)q.x;
+            e[1 % V] = (T)q.y;
+        }
+        T vmin = e[0], vmax = e[0];
+#pragma unroll
+        for (int k = 1; k < V; k++) {
+            vmin = e[k] < vmin ? e[k] : vmin;
+            vmax = e[k] > vmax ? e[k] : vmax;
+        }
+        if ((vmin >= lo) & (vmax <= hi)) {
+            mn = vmin < mn ? vmin : mn;
+            mx = vmax > mx ? vmax : mx;
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++) one(e[k]);
+        }
+    };
+    for (int64_t i = tid; i < s.head; i += stride) one(x[i]);
+    for (int64_t i = s.tail0 + tid; i < n; i += stride) one(x[i]);
     const VT *xv = reinterpret_cast<const VT *>(x + s.head);
     int64_t v = tid;
     for (; v + 3 * stride < s.nvec; v += 4 * stride) {
@@ -262,23 +292,14 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) minmax_in_kernel(const T *_
 #pragma unroll
         for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            int64_t e[V];
-            unpack(a[u], e);
-#pragma unroll
-            for (int k = 0; k < V; k++) visit(e[k]);
-        }
+        for (int u = 0; u < 4; u++) vec(a[u]);
     }
-    for (; v < s.nvec; v += stride) {
-        int64_t e[V];
-        unpack(ldv(xv + v), e);
-#pragma unroll
-        for (int k = 0; k < V; k++) visit(e[k]);
-    }
+    for (; v < s.nvec; v += stride) vec(ldv(xv + v));
+    const bool seen = mn <= mx;
     __shared__ unsigned long long sm[STREAM_THREADS / 32];
-    unsigned long long r = block_max_u64(enc_min(mn), sm);
+    unsigned long long r = block_max_u64(seen ? enc_min((int64_t)mn) : enc_min(INT64_MAX), sm);
     if (threadIdx.x == 0) atomic_max_u64(&h->k_min, r);
-    r = block_max_u64(enc_max(mx), sm);
+    r = block_max_u64(seen ? enc_max((int64_t)mx) : enc_max(INT64_MIN), sm);
     if (threadIdx.x == 0) atomic_max_u64(&h->k_max, r);
 }
 
@@ -1178,7 +1199,14 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
     // Inj: a finite Rcd that fits the bitmap is used as is; otherwise find [min, max].
     const unsigned long long rspan = (unsigned long long)rhi - (unsigned long long)rlo + 1ull;
     const bool fixed = rspan != 0 && rspan <= cap && rspan <= 4ull * (unsigned long long)n + 4096ull;
-    if (!fixed && n > 0) minmax_in_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h);
+    if (!fixed && n > 0) {
+        // Rcd clamped to T's values; an empty clamp leaves lo > hi, so nothing is in range.
+        const int64_t clo = std::max<int64_t>(rlo, (int64_t)Lim<T>::lo);
+        const int64_t chi = std::min<int64_t>(rhi, (int64_t)Lim<T>::hi);
+        const bool none = clo > chi;
+        minmax_in_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, none ? Lim<T>::hi : (T)clo,
+                                                             none ? Lim<T>::lo : (T)chi, h);
+    }
     const unsigned long long span_cap = fixed ? rspan : cap;
     const bool bk = w.buckets && span_cap >= BK_MIN_SPAN && bucket_config(span_cap, bk_pool_entries(n), &cfg);
     if (bk) {

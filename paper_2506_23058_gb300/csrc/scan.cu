@@ -420,6 +420,39 @@ constexpr int TMA_NT = 256;
 constexpr int TMA_TILE_BYTES = 65536;
 constexpr int TMA_CHUNK = 16384;  // bytes per bulk copy
 
+// Thread 0 takes the tile ticket and copies the tile's whole 16-byte chunks (of a
+// TMA_TILE_BYTES tile) into buf with bulk copies; every thread returns once they
+// landed or the bounded wait gave up (IXP_E_TIMEOUT, after a second bounded wait
+// for the copies in flight). Returns the tile index; cnt = elements in the tile,
+// bulk = elements staged in buf (the rest are read from global memory).
+template <typename TI>
+__device__ __forceinline__ int64_t tma_stage_tile(const TI *in, int64_t n, unsigned char *buf,
+                                                  unsigned long long *bar, int64_t *s_tile, Hdr *h, Wait wt,
+                                                  int64_t &cnt, int64_t &bulk) {
+    constexpr int TILE = TMA_TILE_BYTES / (int)sizeof(TI);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        *s_tile = atomicAdd(&h->tile_ctr, 1u);
+    }
+    __syncthreads();
+    const int64_t t = *s_tile;
+    const int64_t t0 = t * TILE;
+    cnt = min((int64_t)TILE, n - t0);
+    bulk = (cnt * (int64_t)sizeof(TI)) / 16 * 16 / (int64_t)sizeof(TI);
+    if (threadIdx.x == 0) {
+        const unsigned bytes = (unsigned)(bulk * sizeof(TI));
+        mbar_expect_tx(bar, bytes);
+        for (unsigned o = 0; o < bytes; o += TMA_CHUNK)
+            bulk_g2s(buf + o, (const char *)(in + t0) + o, min((unsigned)TMA_CHUNK, bytes - o), bar);
+        if (!mbar_wait_bounded(bar, 0, wt.spin_limit)) {
+            set_status(h, IXP_E_TIMEOUT);
+            mbar_wait_bounded(bar, 0, wt.spin_limit);  // let the copies land before the block moves on
+        }
+    }
+    __syncthreads();
+    return t;
+}
+
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(TMA_NT, 3) scan_tma_kernel(const TI *__restrict__ in, TO *__restrict__ out,
                                                              int64_t n, int inclusive, Lookback L, Hdr *h, Wait wt,
@@ -433,30 +466,10 @@ __global__ void __launch_bounds__(TMA_NT, 3) scan_tma_kernel(const TI *__restric
     __shared__ __align__(8) unsigned long long bar;
     __shared__ int64_t s_tile;
     __shared__ ACC s_warp[TMA_NT / 32];
-    __shared__ int s_ok;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        s_tile = atomicAdd(&h->tile_ctr, 1u);
-    }
-    __syncthreads();
-    const int64_t t = s_tile;
+    int64_t cnt, bulk_elems;
+    const int64_t t = tma_stage_tile(in, n, tma_buf, &bar, &s_tile, h, wt, cnt, bulk_elems);
     const int64_t t0 = t * TILE;
-    const int64_t cnt = min((int64_t)TILE, n - t0);
-    const int64_t bulk_elems = (cnt * (int64_t)sizeof(TI)) / 16 * 16 / (int64_t)sizeof(TI);
-    if (threadIdx.x == 0) {
-        const unsigned bytes = (unsigned)(bulk_elems * sizeof(TI));
-        mbar_expect_tx(&bar, bytes);
-        for (unsigned off = 0; off < bytes; off += TMA_CHUNK)
-            bulk_g2s(tma_buf + off, (const char *)(in + t0) + off, min((unsigned)TMA_CHUNK, bytes - off), &bar);
-        const bool ok = mbar_wait_bounded(&bar, 0, wt.spin_limit);
-        if (!ok) {
-            set_status(h, IXP_E_TIMEOUT);
-            mbar_wait_bounded(&bar, 0, wt.spin_limit);  // let the copies land before the block moves on
-        }
-        s_ok = ok;
-    }
-    __syncthreads();
     const TI *sv = reinterpret_cast<const TI *>(tma_buf);
     auto elem = [&](int64_t r) -> ACC {  // element r of the tile
         if (r < bulk_elems) return (ACC)(int64_t)sv[r];
@@ -560,7 +573,178 @@ __global__ void __launch_bounds__(TMA_NT, 3) scan_tma_kernel(const TI *__restric
                 if (p0 + k < n) out[p0 + k] = o[k];
         }
     }
-    (void)s_ok;
+}
+
+// Segmented scan (sgmSum) with the tile staged as in scan_tma_kernel. The heads
+// come from a uint8 flag array (FLAGS) or from the offsets; either way they are
+// first marked in a shared bitmap of the tile. Inside a warp the segmented operator reduces to a plain scan: with x the
+// lane's local aggregate (its vector's sum after the vector's last head), y the
+// inclusive and e = y - x the exclusive plain scans over the lanes, and s the last
+// lane below l whose vector holds a head (a ballot), the values since that head
+// sum to e[l] - e[s]; with no such lane the warp's earlier carry applies.
+template <typename TI, typename TO, bool FLAGS>
+__global__ void __launch_bounds__(TMA_NT, sizeof(TO) == 4 ? 3 : 2) sgm_tma_kernel(const TI *__restrict__ in, TO *__restrict__ out,
+                                                            int64_t n, int inclusive, const uint8_t *__restrict__ flags,
+                                                            const int64_t *__restrict__ off, int64_t nseg, Lookback L,
+                                                            Hdr *h, Wait wt) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(TI);
+    constexpr int TILE = TMA_TILE_BYTES / (int)sizeof(TI);
+    constexpr int S = TILE / V / TMA_NT;  // vectors per thread
+    static_assert(S * V <= 64 && S <= 32, "head bits per thread");
+    using ACC = typename std::conditional<sizeof(TO) == 4, uint32_t, unsigned long long>::type;
+    extern __shared__ __align__(128) unsigned char tma_buf[];
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int64_t s_tile, s_k;
+    __shared__ unsigned heads[TILE / 32];
+    __shared__ ACC s_wv[TMA_NT / 32];
+    __shared__ unsigned s_wf[TMA_NT / 32];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    int64_t cnt, bulk_elems;
+    const int64_t t = tma_stage_tile(in, n, tma_buf, &bar, &s_tile, h, wt, cnt, bulk_elems);
+    const int64_t t0 = t * TILE;
+    if (FLAGS) {
+        // 16 flags per 16-byte chunk become 16 head bits (a byte compare, then a
+        // multiply that gathers the four low bits of a word); lane pairs fill one word
+        const bool f16 = (reinterpret_cast<uintptr_t>(flags) & 15) == 0;
+        for (int c = threadIdx.x; c < TILE / 16; c += TMA_NT) {
+            const int64_t p = t0 + 16 * (int64_t)c;
+            unsigned bits = 0;
+            if (f16 && p + 16 <= n) {
+                const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(flags + p));
+                const unsigned wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    bits |= ((((__vcmpne4(wd[j], 0u) & 0x01010101u) * 0x01020408u) >> 24) & 0xfu) << (4 * j);
+            } else {
+                for (int k = 0; k < 16; k++)
+                    if (p + k < n && flags[p + k]) bits |= 1u << k;
+            }
+            const unsigned hi = __shfl_down_sync(FULL, bits, 1);
+            if ((c & 1) == 0) heads[c >> 1] = bits | (hi << 16);
+        }
+        __syncthreads();
+    } else {
+        mark_heads<TILE>(heads, off, nseg, t0, t0 + cnt, &s_k);
+    }
+    const TI *sv = reinterpret_cast<const TI *>(tma_buf);
+    auto load = [&](int64_t r0, ACC (&a)[V]) {
+        if (r0 + V <= bulk_elems) {
+            if (V == 4) {
+                const int4 q = reinterpret_cast<const int4 *>(tma_buf)[r0 / 4];
+                a[0] = (ACC)(int64_t)q.x;
+                a[1 % V] = (ACC)(int64_t)q.y;
+                a[2 % V] = (ACC)(int64_t)q.z;
+                a[3 % V] = (ACC)(int64_t)q.w;
+            } else {
+                const longlong2 q = reinterpret_cast<const longlong2 *>(tma_buf)[r0 / 2];
+                a[0] = (ACC)q.x;
+                a[1 % V] = (ACC)q.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++) {
+                const int64_t r = r0 + k;
+                a[k] = r < bulk_elems ? (ACC)(int64_t)sv[r] : (r < cnt ? (ACC)(int64_t)in[t0 + r] : (ACC)0);
+            }
+        }
+    };
+    const unsigned lt_mask = (1u << l) - 1u;
+    // pass 1: head bits, local aggregates, warp scans with a segmented carry
+    unsigned long long hbits = 0;  // V head bits per vector
+    unsigned pstop = 0;            // bit u: the lane prefix of vector u holds a head
+    ACC lane_pre[S];
+    ACC cv = 0;
+    unsigned cf = 0;
+#pragma unroll
+    for (int u = 0; u < S; u++) {
+        const int64_t r0 = (int64_t)((w * S + u) * 32 + l) * V;
+        ACC a[V];
+        load(r0, a);
+        // V head bits of this vector (V divides 32, so they sit in one word)
+        const unsigned hb = (heads[(int)r0 >> 5] >> ((int)r0 & 31)) & ((1u << V) - 1u);
+        hbits |= (unsigned long long)hb << (u * V);
+        ACC x = 0;
+#pragma unroll
+        for (int k = 0; k < V; k++) x = ((hb >> k) & 1u) ? a[k] : x + a[k];
+        ACC y = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const ACC o = __shfl_up_sync(FULL, y, d);
+            if (l >= d) y += o;
+        }
+        const ACC e = y - x;
+        const unsigned fm = __ballot_sync(FULL, hb != 0u);
+        const unsigned below = fm & lt_mask;
+        const ACC e_s = __shfl_sync(FULL, e, below ? 31 - __clz(below) : 0);
+        lane_pre[u] = below ? e - e_s : cv + e;
+        pstop |= (below || cf) ? (1u << u) : 0u;
+        const ACC y_all = __shfl_sync(FULL, y, 31);
+        const ACC e_last = __shfl_sync(FULL, e, fm ? 31 - __clz(fm) : 0);
+        cv = fm ? y_all - e_last : cv + y_all;
+        cf |= fm ? 1u : 0u;
+    }
+    if (l == 0) {
+        s_wv[w] = cv;
+        s_wf[w] = cf;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const SP x = l < TMA_NT / 32 ? SP{s_wf[l], (unsigned long long)s_wv[l]} : SP{0u, 0ull};
+        SP y = x;
+#pragma unroll
+        for (int d = 1; d < TMA_NT / 32; d <<= 1) {
+            const SP o = shfl_up_sp(y, d);
+            if (l >= d) y = sp_op(o, y);
+        }
+        SP ex = shfl_up_sp(y, 1);
+        if (l == 0) ex = SP{0u, 0ull};
+        const SP tile_agg = shfl_sp(y, TMA_NT / 32 - 1);
+        const SP tile_ex = lookback(L, t, tile_agg, h, wt);
+        __syncwarp();
+        if (l < TMA_NT / 32) s_wv[l] = (ACC)sp_op(tile_ex, ex).v;
+    }
+    __syncthreads();
+    // pass 2: outputs
+    const ACC pre = s_wv[w];
+    constexpr int VO = 16 / sizeof(TO);
+#pragma unroll
+    for (int u = 0; u < S; u++) {
+        const int64_t r0 = (int64_t)((w * S + u) * 32 + l) * V;
+        ACC a[V];
+        load(r0, a);
+        const unsigned hb = (unsigned)(hbits >> (u * V));
+        ACC run = ((pstop >> u) & 1u) ? lane_pre[u] : pre + lane_pre[u];
+        TO o[V];
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            run = ((hb >> k) & 1u) ? a[k] : run + a[k];
+            o[k] = (TO)(inclusive ? run : run - a[k]);
+        }
+        const int64_t p0 = t0 + r0;
+        if (p0 + V <= n) {
+#pragma unroll
+            for (int c = 0; c < V; c += VO) {
+                if (VO == 4) {
+                    int4 st4;
+                    st4.x = (int)o[c];
+                    st4.y = (int)o[(c + 1) % V];
+                    st4.z = (int)o[(c + 2) % V];
+                    st4.w = (int)o[(c + 3) % V];
+                    __stcs(reinterpret_cast<int4 *>(out + p0 + c), st4);
+                } else {
+                    longlong2 st2;
+                    st2.x = (long long)o[c];
+                    st2.y = (long long)o[(c + 1) % V];
+                    __stcs(reinterpret_cast<longlong2 *>(out + p0 + c), st2);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (p0 + k < n) out[p0 + k] = o[k];
+        }
+    }
 }
 
 // Segment totals after a segmented scan: tot[k] = inclusive value at the segment's
@@ -1360,6 +1544,17 @@ size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg) {
 
 
 
+// Segmented scan over TMA-staged tiles (16-byte aligned input and output).
+template <typename TI, typename TO, bool FLAGS>
+static void launch_sgm_tma(const TI *in, TO *out, int64_t n, int inclusive, const uint8_t *flags, const int64_t *off,
+                           int64_t nseg, const TileWs &W, Wait wt, cudaStream_t st) {
+    constexpr int64_t tile = TMA_TILE_BYTES / (int64_t)sizeof(TI);
+    const int64_t ntma = (n + tile - 1) / tile;
+    cudaFuncSetAttribute(sgm_tma_kernel<TI, TO, FLAGS>, cudaFuncAttributeMaxDynamicSharedMemorySize, TMA_TILE_BYTES);
+    sgm_tma_kernel<TI, TO, FLAGS><<<(unsigned)ntma, TMA_NT, TMA_TILE_BYTES, st>>>(in, out, n, inclusive, flags, off,
+                                                                                nseg, W.L, W.h, wt);
+}
+
 template <typename TI, typename TO>
 static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs segs, TO *tot, int32_t *d_status,
                     void *ws, size_t ws_bytes, cudaStream_t st, bool keep_status = false) {
@@ -1376,7 +1571,9 @@ static int run_scan(const TI *in, TO *out, int64_t n, int inclusive, ixp_segs se
     const int vec = aligned16(in) && aligned16(out);
     const Wait wt = wait_config();
     if (nt > 0) {
-        if (seg)
+        if (seg && vec)
+            launch_sgm_tma<TI, TO, false>(in, out, n, inclusive, nullptr, segs.offsets, segs.nseg, W, wt, st);
+        else if (seg)
             scan_kernel<TI, TO, true><<<(unsigned)nt, TB, 0, st>>>(in, out, n, inclusive, segs.offsets, segs.nseg,
                                                                   W.L, W.h, wt, nullptr, vec);
         else if (vec) {
@@ -1568,9 +1765,15 @@ extern "C" int ixp_sgm_scan(const uint8_t *flags, const void *in, int in_type, v
     if (d_status && cudaMemsetAsync(d_status, 0, sizeof(int32_t), st) != cudaSuccess) return IXP_E_CUDA;
     const Wait wt = wait_config();
     if (nt > 0) {
-#define IXP_SGM(TI, TO)                                                                                          \
-    scan_kernel<TI, TO, true><<<(unsigned)nt, TB, 0, st>>>((const TI *)in, (TO *)out, n, inclusive, nullptr, 0, W.L, \
-                                                           W.h, wt, nullptr, aligned16(in) && aligned16(out), flags)
+        const bool vec = aligned16(in) && aligned16(out);
+#define IXP_SGM(TI, TO)                                                                                           \
+    do {                                                                                                          \
+        if (vec)                                                                                                  \
+            launch_sgm_tma<TI, TO, true>((const TI *)in, (TO *)out, n, inclusive, flags, nullptr, 0, W, wt, st);  \
+        else                                                                                                      \
+            scan_kernel<TI, TO, true><<<(unsigned)nt, TB, 0, st>>>((const TI *)in, (TO *)out, n, inclusive,       \
+                                                                   nullptr, 0, W.L, W.h, wt, nullptr, 0, flags); \
+    } while (0)
         if (in_type == IXP_I32 && out_type == IXP_I32) IXP_SGM(int32_t, int32_t);
         else if (in_type == IXP_I32) IXP_SGM(int32_t, int64_t);
         else IXP_SGM(int64_t, int64_t);

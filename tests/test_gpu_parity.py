@@ -676,13 +676,45 @@ def test_sgm_scan_flags(ixp, dev, n, it, ot):
     exclusive (inclusive minus the element), flags at 0, sparse and dense."""
     rng = np.random.default_rng(n + 5)
     x = rng.integers(-1000, 1000, size=n).astype(it)
-    for p in (0.0, 0.01, 0.5):
+    tdt = getattr(torch, np.dtype(ot).name)
+    for p in (0.0, 0.01, 0.5, 1.0):
         fl = (rng.random(n) < p).astype(np.uint8)
-        inc, st = ixp.sgm_scan(T(fl, dev), T(x, dev), out_dtype=getattr(torch, np.dtype(ot).name), inclusive=True)
+        fl[fl != 0] = rng.integers(1, 256, size=int((fl != 0).sum()))  # any nonzero byte is a head
+        inc, st = ixp.sgm_scan(T(fl, dev), T(x, dev), out_dtype=tdt, inclusive=True)
         ref = oracle.sgm_scan(fl, x, out_dtype=ot)
         assert st.item() == 0 and np.array_equal(inc.cpu().numpy(), ref), (n, p)
-        exc, _ = ixp.sgm_scan(T(fl, dev), T(x, dev), out_dtype=getattr(torch, np.dtype(ot).name), inclusive=False)
+        exc, _ = ixp.sgm_scan(T(fl, dev), T(x, dev), out_dtype=tdt, inclusive=False)
         assert np.array_equal(exc.cpu().numpy(), (ref - x.astype(ot)).astype(ot)), (n, p)
+    # flags one byte off a 16-byte boundary (aligned values), then values off it
+    fl = (rng.random(n + 1) < 0.05).astype(np.uint8)
+    ref = oracle.sgm_scan(fl[1:], x, out_dtype=ot)
+    inc, st = ixp.sgm_scan(T(fl, dev)[1:], T(x, dev), out_dtype=tdt)
+    assert st.item() == 0 and np.array_equal(inc.cpu().numpy(), ref)
+    xs = np.concatenate([np.zeros(1, it), x])
+    inc, st = ixp.sgm_scan(T(fl, dev)[1:], T(xs, dev)[1:], out_dtype=tdt)
+    assert st.item() == 0 and np.array_equal(inc.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("form", ["flags", "offsets"])
+def test_segmented_scan_timeout_is_reported(ixp, dev, form):
+    # a tile that never publishes makes its successors' bounded waits run out, in
+    # the TMA-staged segmented scan (16384 int32 elements per tile); no segment head
+    # after position 0, so every tile's look-back has to reach the skipped one
+    n = 16384 * 12 + 5
+    x = T(np.ones(n, np.int32), dev)
+    fl = torch.zeros(n, dtype=torch.uint8, device=dev)
+    fl[0] = 1
+    off = T(np.array([0, n], np.int64), dev)
+    run = (lambda: ixp.sgm_scan(fl, x)[1]) if form == "flags" else (lambda: ixp.scan(x, offsets=off)[2])
+    try:
+        ixp.debug_set_wait(2000, 3)
+        st = run()
+        torch.cuda.synchronize()
+        assert st.item() == -6
+    finally:
+        ixp.debug_set_wait(0, -1)
+    st = run()
+    assert st.item() == 0
 
 
 @pytest.mark.parametrize("ot", [np.int32, np.int64])
