@@ -384,12 +384,14 @@ def scan(x, out_dtype=None, inclusive=False, offsets=None, *, out=None, totals=N
     out_dtype = out.dtype if out is not None else (out_dtype or x.dtype)
     n = x.numel()
     out = out if out is not None else torch.empty(n, dtype=out_dtype, device=x.device)
+    _need(out, "out", n, (torch.int32, torch.int64))
     segs = _segs(offsets)
     if totals is None:
         totals = torch.empty(max(1, segs.nseg), dtype=out_dtype, device=x.device)
     elif totals.dtype != out.dtype or totals.numel() < max(1, segs.nseg):
         raise ValueError("totals must have the output's dtype and one entry per segment")
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=x.device)
+    _need(status, "status", 1, (torch.int32,))
     need = workspace_size("scan", _itype(x), n, segs.nseg)
     ws = ws if ws is not None else workspace(need, x.device)
     _ck(load().ixp_scan(_dev(x, "x"), _itype(x), out.data_ptr(), _itype(out), n, int(inclusive), segs,
@@ -428,6 +430,7 @@ def partition(keys, pred, payload=None, out_dtype=torch.int32, offsets=None, *, 
     num_true = num_true if num_true is not None else torch.empty(max(1, segs.nseg), dtype=torch.int64, device=device)
     _need(num_true, "num_true", max(1, segs.nseg), (torch.int64,))
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=device)
+    _need(status, "status", 1, (torch.int32,))
     kt = _itype(keys) if keys is not None else 0
     need = workspace_size("partition", kt, n, segs.nseg)
     ws = ws if ws is not None else workspace(need, device)
@@ -513,6 +516,7 @@ def gather(src, idx, *, out=None, status=None, stream=None):
     if _row_elems(out) != row_elems:
         raise ValueError("out rows must have the width of src rows")
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=src.device)
+    _need(status, "status", 1, (torch.int32,))
     _ck(load().ixp_gather(_dev(out, "out"), _dev(src, "src"), src.shape[0], _dev(idx, "idx"), _itype(idx), n,
                           row_elems, src.element_size(), status.data_ptr(), _stream(stream)), "gather")
     return out, status
@@ -527,6 +531,7 @@ def gather_segments(src, src_off, seg_src, out_off, n_out, *, out=None, status=N
     out = out if out is not None else torch.empty(n_out, dtype=src.dtype, device=src.device)
     _need(out, "out", n_out, (src.dtype,))
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=src.device)
+    _need(status, "status", 1, (torch.int32,))
     need = workspace_size("gather_segments", 0, n_out)
     ws = ws if ws is not None else workspace(need, src.device)
     _ck(load().ixp_gather_segments(_dev(out, "out"), n_out, _dev(out_off, "out_off"), m, _dev(src, "src"),
@@ -542,7 +547,10 @@ def sgm_scan(flags, x, out_dtype=None, inclusive=True, *, out=None, status=None,
     out_dtype = out_dtype or x.dtype
     n = x.numel()
     out = out if out is not None else torch.empty(n, dtype=out_dtype, device=x.device)
+    _need(flags, "flags", n, (torch.uint8, torch.bool))
+    _need(out, "out", n, (torch.int32, torch.int64))
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=x.device)
+    _need(status, "status", 1, (torch.int32,))
     need = workspace_size("scan", _itype(x), n, 0)
     ws = ws if ws is not None else workspace(need, x.device)
     _ck(load().ixp_sgm_scan(_dev(flags, "flags"), _dev(x, "x"), _itype(x), out.data_ptr(), _itype(out), n,
@@ -590,6 +598,7 @@ def mkii(offsets, n, out_dtype=torch.int32, *, out=None, status=None, ws=None, s
     out = out if out is not None else torch.empty(n, dtype=out_dtype, device=offsets.device)
     _need(out, "out", n, (torch.int32, torch.int64))
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=offsets.device)
+    _need(status, "status", 1, (torch.int32,))
     need = workspace_size("gather_segments", 0, n)
     ws = ws if ws is not None else workspace(need, offsets.device)
     _ck(load().ixp_mkii(_dev(offsets, "offsets"), m, out.data_ptr() if n else None, _itype(out), n, status.data_ptr(),
@@ -603,6 +612,7 @@ def flags_from_shape(shape, xs=None, out_dtype=torch.int64, out_len=None, *, out
     m = shape.numel()
     offs = offsets if offsets is not None else torch.empty(m + 1, dtype=torch.int64, device=shape.device)
     status = status if status is not None else torch.zeros(1, dtype=torch.int32, device=shape.device)
+    _need(status, "status", 1, (torch.int32,))
     need = workspace_size("flags", 1, m)
     ws = ws if ws is not None else workspace(need, shape.device)
     xp = None if xs is None else _dev(xs, "xs")

@@ -58,3 +58,27 @@ def test_scan_and_pairs_buffers(ixp):
         ixp.smallest_pairs(es, es.clone(), 4, 10, out_es=torch.empty(9, dtype=torch.int64))
     with pytest.raises(ValueError, match="vals"):
         ixp.hist_min(torch.zeros(4, dtype=torch.int64), es, torch.zeros(9, dtype=torch.int64))
+
+
+def test_sgm_scan_buffers(ixp):
+    x = torch.zeros(10, dtype=torch.int32)
+    with pytest.raises(ValueError, match="flags"):
+        ixp.sgm_scan(torch.zeros(9, dtype=torch.uint8), x)
+    with pytest.raises(ValueError, match="flags"):
+        ixp.sgm_scan(torch.zeros(10, dtype=torch.int32), x)
+    with pytest.raises(ValueError, match="out"):
+        ixp.sgm_scan(torch.zeros(10, dtype=torch.uint8), x, out=torch.empty(9, dtype=torch.int64))
+    with pytest.raises(ValueError, match="status"):
+        ixp.sgm_scan(torch.zeros(10, dtype=torch.uint8), x, status=torch.zeros(1, dtype=torch.int64))
+
+
+def test_scan_and_status_buffers(ixp):
+    x = torch.zeros(10, dtype=torch.int32)
+    with pytest.raises(ValueError, match="out"):
+        ixp.scan(x, out=torch.empty(9, dtype=torch.int32))
+    with pytest.raises(ValueError, match="status"):
+        ixp.scan(x, status=torch.zeros(0, dtype=torch.int32))
+    with pytest.raises(ValueError, match="status"):
+        ixp.mkii(torch.zeros(2, dtype=torch.int64), 0, status=torch.zeros(1, dtype=torch.int64))
+    with pytest.raises(ValueError, match="status"):
+        ixp.gather(torch.zeros(4, 2), torch.zeros(3, dtype=torch.int64), status=torch.zeros(1, dtype=torch.uint8))

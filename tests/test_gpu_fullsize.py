@@ -77,6 +77,35 @@ def test_scan_full_size(ixp, dev):
     assert np.array_equal(got, ref) and int(tot[0].item()) == int(rtot[0])
 
 
+def test_segmented_blocks_full_size(ixp, dev):
+    """sgmSum under uint8 flags, the offsets form of the segmented scan (with its
+    per-segment totals) and mkII over the 4096-segment log-uniform shape that
+    bench.py times (2^28 int32 values in [0, 4)), whole arrays against the oracle."""
+    s = synth.seed_for(1)
+    shape = synth.shapes_log_uniform(4096, s + 11, cap_total=1 << 28)
+    off = synth.offsets_from_shape(shape)
+    total = int(off[-1])
+    g = torch.Generator(device=dev)
+    g.manual_seed(s + 6)
+    x = torch.randint(0, 4, (total,), generator=g, device=dev, dtype=torch.int32)
+    fl = np.zeros(total, np.uint8)
+    fl[off[:-1][shape > 0]] = 1
+    xo = x.cpu().numpy()
+    ref_inc = oracle.sgm_scan(fl, xo)
+    got, st = ixp.sgm_scan(torch.from_numpy(fl).to(dev), x, inclusive=True)
+    assert st.item() == 0 and np.array_equal(got.cpu().numpy(), ref_inc)
+    got, st = ixp.sgm_scan(torch.from_numpy(fl).to(dev), x, inclusive=False)
+    assert st.item() == 0 and np.array_equal(got.cpu().numpy(), ref_inc - xo)
+    del got
+    ref, rtot = oracle.scan(xo, inclusive=True, offsets=off)
+    assert np.array_equal(ref, ref_inc)  # the two forms of the same segmentation agree
+    got, tot, st = ixp.scan(x, inclusive=True, offsets=torch.from_numpy(off).to(dev))
+    assert st.item() == 0 and np.array_equal(got.cpu().numpy(), ref) and np.array_equal(tot.cpu().numpy(), rtot)
+    del got, x
+    ii, st = ixp.mkii(torch.from_numpy(off).to(dev), total)
+    assert st.item() == 0 and np.array_equal(ii.cpu().numpy(), oracle.mkii(shape).astype(np.int32))
+
+
 @pytest.mark.parametrize("p", [0.5, 0.01])
 def test_partition_full_size(ixp, dev, p):
     n = 1 << 28

@@ -76,6 +76,27 @@ def test_scan_past_2_31(ixp, dev):
     assert torch.equal(out[idx], idx)
 
 
+def test_segmented_scan_past_2_31(ixp, dev):
+    # ones with segment heads at 0, 2^31 - 5 and 2^31 + 1: the inclusive value at i
+    # is i - (last head <= i) + 1, in both forms of the segmentation
+    heads = [0, (1 << 31) - 5, BIG]
+    x = torch.ones(N, dtype=torch.int32, device=dev)
+    out = torch.empty(N, dtype=torch.int64, device=dev)
+    fl = torch.zeros(N, dtype=torch.uint8, device=dev)
+    fl[torch.tensor(heads, device=dev)] = 1
+    pos = [0, 1, (1 << 31) - 6, (1 << 31) - 5, (1 << 31) - 1, 1 << 31, BIG, BIG + 1, N - 1]
+    want = torch.tensor([p - max(h for h in heads if h <= p) + 1 for p in pos], device=dev)
+    idx = torch.tensor(pos, device=dev)
+    _, st = ixp.sgm_scan(fl, x, out=out, inclusive=True)
+    assert st.item() == 0 and torch.equal(out[idx], want)
+    del fl
+    off = torch.tensor(heads + [N], dtype=torch.int64, device=dev)
+    out.fill_(-1)
+    _, tot, st = ixp.scan(x, inclusive=True, offsets=off, out=out)
+    assert st.item() == 0 and torch.equal(out[idx], want)
+    assert tot.cpu().tolist() == [(1 << 31) - 5, 6, 2]
+
+
 def test_partition_past_2_31(ixp, dev):
     x = distinct_i32(N, dev)
     thr = 0
