@@ -983,8 +983,26 @@ def run_e2e(ixp, R, ops, inp, dev, args, step_bytes):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
+
+    # this box's pinned copy rates (after the timed region): the step cannot take
+    # less than its H2D bytes at the H2D rate
+    def rate(dst, src, st):
+        with torch.cuda.stream(st):
+            dst.copy_(src, non_blocking=True)
+            a.record(st)
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            b.record(st)
+        torch.cuda.synchronize()
+        return 3 * src.numel() * src.element_size() / (a.elapsed_time(b) / 1e3) / 1e9
+
+    big = max(names, key=lambda k: host[k].numel() * host[k].element_size())
+    h2d_gbs = rate(inp[big], host[big], up[0])
+    d2h_gbs = rate(out_host["pay"], R.pay_out, down)
     return {"value": round(step_bytes / (ms / 1e3) / 1e9, 1), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3), "steps": steps,
+            "copy_rates_gbs": {"h2d": round(h2d_gbs, 1), "d2h": round(d2h_gbs, 1)},
+            "h2d_floor_ms": round(h2d / (h2d_gbs * 1e9) * 1e3, 3),
             "overlap": "H2D on 2 streams in first-use order, ops wait per input, D2H on a third stream as soon as "
                        "each output is final"}
 

@@ -420,15 +420,16 @@ constexpr int TMA_NT = 256;
 constexpr int TMA_TILE_BYTES = 65536;
 constexpr int TMA_CHUNK = 16384;  // bytes per bulk copy
 
-// Thread 0 takes the tile ticket and copies the tile's whole 16-byte chunks (of a
-// TMA_TILE_BYTES tile) into buf with bulk copies; every thread returns once they
-// landed or the bounded wait gave up (IXP_E_TIMEOUT, after a second bounded wait
-// for the copies in flight). Returns the tile index; cnt = elements in the tile,
-// bulk = elements staged in buf (the rest are read from global memory).
+// Thread 0 takes the tile ticket and starts bulk copies of the tile's whole 16-byte
+// chunks (of a TMA_TILE_BYTES tile) into buf; every thread returns with the tile
+// index (cnt = elements in the tile, bulk = elements the copies bring; the rest
+// are read from global memory). tma_wait_tile then waits for the copies (thread 0,
+// bounded: IXP_E_TIMEOUT, after a second bounded wait for the copies in flight);
+// a __syncthreads after it publishes the tile to the block.
 template <typename TI>
-__device__ __forceinline__ int64_t tma_stage_tile(const TI *in, int64_t n, unsigned char *buf,
-                                                  unsigned long long *bar, int64_t *s_tile, Hdr *h, Wait wt,
-                                                  int64_t &cnt, int64_t &bulk) {
+__device__ __forceinline__ int64_t tma_issue_tile(const TI *in, int64_t n, unsigned char *buf,
+                                                  unsigned long long *bar, int64_t *s_tile, Hdr *h, int64_t &cnt,
+                                                  int64_t &bulk) {
     constexpr int TILE = TMA_TILE_BYTES / (int)sizeof(TI);
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -444,11 +445,23 @@ __device__ __forceinline__ int64_t tma_stage_tile(const TI *in, int64_t n, unsig
         mbar_expect_tx(bar, bytes);
         for (unsigned o = 0; o < bytes; o += TMA_CHUNK)
             bulk_g2s(buf + o, (const char *)(in + t0) + o, min((unsigned)TMA_CHUNK, bytes - o), bar);
-        if (!mbar_wait_bounded(bar, 0, wt.spin_limit)) {
-            set_status(h, IXP_E_TIMEOUT);
-            mbar_wait_bounded(bar, 0, wt.spin_limit);  // let the copies land before the block moves on
-        }
     }
+    return t;
+}
+
+__device__ __forceinline__ void tma_wait_tile(unsigned long long *bar, Hdr *h, Wait wt) {
+    if (threadIdx.x == 0 && !mbar_wait_bounded(bar, 0, wt.spin_limit)) {
+        set_status(h, IXP_E_TIMEOUT);
+        mbar_wait_bounded(bar, 0, wt.spin_limit);  // let the copies land before the block moves on
+    }
+}
+
+template <typename TI>
+__device__ __forceinline__ int64_t tma_stage_tile(const TI *in, int64_t n, unsigned char *buf,
+                                                  unsigned long long *bar, int64_t *s_tile, Hdr *h, Wait wt,
+                                                  int64_t &cnt, int64_t &bulk) {
+    const int64_t t = tma_issue_tile(in, n, buf, bar, s_tile, h, cnt, bulk);
+    tma_wait_tile(bar, h, wt);
     __syncthreads();
     return t;
 }
@@ -601,18 +614,28 @@ __global__ void __launch_bounds__(TMA_NT, sizeof(TO) == 4 ? 3 : 2) sgm_tma_kerne
     __shared__ unsigned s_wf[TMA_NT / 32];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     int64_t cnt, bulk_elems;
-    const int64_t t = tma_stage_tile(in, n, tma_buf, &bar, &s_tile, h, wt, cnt, bulk_elems);
+    const int64_t t = tma_issue_tile(in, n, tma_buf, &bar, &s_tile, h, cnt, bulk_elems);
     const int64_t t0 = t * TILE;
+    // the heads are read while the tile's copies are in flight
     if (FLAGS) {
         // 16 flags per 16-byte chunk become 16 head bits (a byte compare, then a
         // multiply that gathers the four low bits of a word); lane pairs fill one word
+        constexpr int FC = TILE / 16 / TMA_NT;  // chunks per thread
         const bool f16 = (reinterpret_cast<uintptr_t>(flags) & 15) == 0;
-        for (int c = threadIdx.x; c < TILE / 16; c += TMA_NT) {
+        uint4 fq[FC];
+#pragma unroll
+        for (int i = 0; i < FC; i++) {
+            const int64_t p = t0 + 16 * (int64_t)(threadIdx.x + i * TMA_NT);
+            fq[i] = (f16 && p + 16 <= n) ? __ldcs(reinterpret_cast<const uint4 *>(flags + p)) : make_uint4(0, 0, 0, 0);
+        }
+        tma_wait_tile(&bar, h, wt);
+#pragma unroll
+        for (int i = 0; i < FC; i++) {
+            const int c = threadIdx.x + i * TMA_NT;
             const int64_t p = t0 + 16 * (int64_t)c;
             unsigned bits = 0;
             if (f16 && p + 16 <= n) {
-                const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(flags + p));
-                const unsigned wd[4] = {q.x, q.y, q.z, q.w};
+                const unsigned wd[4] = {fq[i].x, fq[i].y, fq[i].z, fq[i].w};
 #pragma unroll
                 for (int j = 0; j < 4; j++)
                     bits |= ((((__vcmpne4(wd[j], 0u) & 0x01010101u) * 0x01020408u) >> 24) & 0xfu) << (4 * j);
@@ -623,10 +646,11 @@ __global__ void __launch_bounds__(TMA_NT, sizeof(TO) == 4 ? 3 : 2) sgm_tma_kerne
             const unsigned hi = __shfl_down_sync(FULL, bits, 1);
             if ((c & 1) == 0) heads[c >> 1] = bits | (hi << 16);
         }
-        __syncthreads();
     } else {
         mark_heads<TILE>(heads, off, nseg, t0, t0 + cnt, &s_k);
+        tma_wait_tile(&bar, h, wt);
     }
+    __syncthreads();
     const TI *sv = reinterpret_cast<const TI *>(tma_buf);
     auto load = [&](int64_t r0, ACC (&a)[V]) {
         if (r0 + V <= bulk_elems) {
