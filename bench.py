@@ -373,7 +373,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
     ap.add_argument("--no-ceilings", action="store_true", help="skip the hardware-rate microbenchmarks")
     ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes", "backward", "segmented"],
-                    help="run only this workload and print its result (profiling)")
+                    help="run only this workload and print its result (profiling; --small: 2^26 elements for "
+                         "classes, backward and segmented)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -383,7 +384,7 @@ def main():
         import paper_2506_23058_gb300 as ixp
         ixp.load()
         dev = torch.device("cuda", 0)
-        n32 = 1 << 28
+        n32 = 1 << 26 if args.small else 1 << 28
         if args.extra == "classes":
             keys = synth.t_keys_uniform(n32, synth.seed_for(1) + 7, dev)
             res = run_classes(ixp, {"keys": keys}, n32, dev, None)
