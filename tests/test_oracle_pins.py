@@ -370,6 +370,23 @@ def test_sgm_scan_pieces():
         assert oracle.sgm_scan(fl, x).tolist() == ref.tolist()
 
 
+def test_mkii_matches_repeat_with_empty_segments():
+    # mkII (Fig. 2, right) is segment k repeated shape[k] times (numpy's repeat);
+    # empty segments contribute nothing, and II[j] = k exactly when
+    # offsets[k] <= j < offsets[k + 1]
+    rng = np.random.default_rng(46)
+    for _ in range(100):
+        m = int(rng.integers(1, 20))
+        shape = rng.integers(0, 6, size=m).astype(np.int64)
+        shape[rng.random(m) < 0.3] = 0
+        ii = oracle.mkii(shape)
+        assert ii.tolist() == np.repeat(np.arange(m), shape).tolist()
+        off = np.concatenate([[0], np.cumsum(shape)])
+        for j in range(int(off[-1])):
+            k = int(ii[j])
+            assert off[k] <= j < off[k + 1]
+
+
 def test_scatter_gather_library_routines():
     rng = np.random.default_rng(51)
     n, m = 500, 300
