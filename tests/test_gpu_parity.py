@@ -336,7 +336,8 @@ def test_scan_flat(ixp, dev, n, it, ot):
 
 
 @pytest.mark.parametrize("it,ot", [(np.int32, np.int32), (np.int32, np.int64), (np.int64, np.int64)])
-@pytest.mark.parametrize("n,m", [(1, 1), (100, 7), (5000, 3), (5000, 2000), (70000, 50), (70000, 30000)])
+@pytest.mark.parametrize("n,m", [(1, 1), (100, 7), (5000, 3), (5000, 2000), (70000, 50), (70000, 30000),
+                                 (300001, 3), (1 << 20, 1)])
 def test_scan_segmented(ixp, dev, n, m, it, ot):
     rng = np.random.default_rng(n * 7 + m)
     off = random_offsets(rng, n, m)
@@ -347,6 +348,19 @@ def test_scan_segmented(ixp, dev, n, m, it, ot):
         assert st.item() == 0
         assert np.array_equal(out.cpu().numpy(), o), (n, m, inc)
         assert np.array_equal(tot.cpu().numpy(), otot[:m])
+
+
+def test_scan_segmented_unaligned(ixp, dev):
+    # values and outputs off a 16-byte boundary take the register-tiled kernel
+    rng = np.random.default_rng(12)
+    n = 70001
+    off = random_offsets(rng, n, 40)
+    a = rng.integers(-50, 100, size=n + 1).astype(np.int32)
+    t = T(a, dev)
+    o, otot = oracle.scan(a[1:], np.int64, inclusive=True, offsets=off)
+    out = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    r, tot, st = ixp.scan(t[1:], torch.int64, inclusive=True, offsets=T(off, dev), out=out[1:])
+    assert st.item() == 0 and np.array_equal(r.cpu().numpy(), o) and np.array_equal(tot.cpu().numpy(), otot[:40])
 
 
 def test_scan_unaligned(ixp, dev):
