@@ -669,7 +669,9 @@ def run_segmented(ixp, inp, n32, dev, plain_ns_per_byte):
     log-uniform shape (sum = the 2^28 int32 elements it covers): sgmSum, the
     inclusive segmented scan of int32 values in [0, 4) under uint8 start flags;
     the same scan with the segments given by their offsets (and per-segment
-    totals); and mkII, the segment index of every position from the offsets."""
+    totals); mkII, the segment index of every position from the offsets; and
+    partition2L (per-segment stable partition, index form, p = 0.5) with its
+    segmented InvFiltPart check."""
     import torch
     shape = inp["shape"]
     offs = torch.empty(shape.numel() + 1, dtype=torch.int64, device=dev)
@@ -698,13 +700,23 @@ def run_segmented(ixp, inp, n32, dev, plain_ns_per_byte):
     seg_sum.index_add_(0, ii.long(), x.long())
     ok_scan = bool(torch.equal(out[ends].long(), seg_sum[shape > 0])) and bool(torch.equal(out, out2))
     ok_ii = bool(torch.equal(ii[starts].long(), torch.nonzero(shape > 0).flatten()))
+    # partition2L (per-segment stable partition, index form) and its segmented InvFiltPart check
+    part = ("lt", 0, 2)  # values uniform in [0, 4): p = 0.5
+    z = torch.empty(total, dtype=torch.int32, device=dev)
+    ntr = torch.empty(m, dtype=torch.int64, device=dev)
+    t_part = _time(lambda: ixp.partition(x, part, offsets=offs, want_keys=False, out=z, num_true=ntr, status=st))
+    vd = ixp.check_filtpart(z, x, part=part, offsets=offs)
+    t_chk = _time(lambda: ixp.check_filtpart(z, x, part=part, offsets=offs, out=vd.buf))
+    fp_ok = vd.get()["ok"] == 1
     nb_scan, nb_ii = 9 * total, 4 * total + 8 * offs.numel()
     return {"workload": "%d segments log-uniform in [1, 2^20], %d int32 elements" % (shape.numel(), total),
             "sgm_scan_ms": round(t_scan, 4), "sgm_scan_gbs": round(nb_scan / (t_scan / 1e3) / 1e9, 1),
             "seg_scan_offsets_ms": round(t_off, 4),
             "seg_scan_offsets_gbs": round((8 * total + 16 * m) / (t_off / 1e3) / 1e9, 1),
             "mkii_ms": round(t_ii, 4), "mkii_gbs": round(nb_ii / (t_ii / 1e3) / 1e9, 1),
-            "checks_ok": ok_scan and ok_ii and int(st.item()) == 0,
+            "partition_seg_ms": round(t_part, 4), "partition_seg_gbs": round(8 * total / (t_part / 1e3) / 1e9, 1),
+            "invfiltpart_seg_ms": round(t_chk, 4), "invfiltpart_seg_gbs": round(8 * total / (t_chk / 1e3) / 1e9, 1),
+            "checks_ok": ok_scan and ok_ii and fp_ok and int(st.item()) == 0,
             "sgm_scan_time_per_byte_vs_plain": (round((t_scan * 1e6 / nb_scan) / plain_ns_per_byte, 3)
                                                 if plain_ns_per_byte else None)}
 
