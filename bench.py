@@ -77,9 +77,10 @@ def make_ops(n32, n64, small=False):
 OP_KERNELS = {
     "range": "range_kernel", "mono": "mono_kernel",
     "inj": "bucket_scatter_kernel + bucket_check_kernel", "bij": "bucket_scatter_kernel + bucket_check_kernel",
-    "scan_i32": "scan_tma_kernel<int, int>", "partition_p50": "count_kernel + partition_flat_kernel<int, int, false>",
-    "partition_p01": "count_kernel + partition_flat_kernel<int, int, false>",
-    "filtpart_p50": "filtpart_tile_kernel<int, int>", "scatter_rows8": "rows_lanes_kernel<int, 2, 1, true>",
+    "scan_i32": "scan_tma_kernel<int, int>",
+    "partition_p50": "count_tiles_kernel<int> + partition_flat_kernel<int, int, false>",
+    "partition_p01": "count_tiles_kernel<int> + partition_flat_kernel<int, int, false>",
+    "filtpart_p50": "filtpart_tile_kernel<int, int, int>", "scatter_rows8": "rows_lanes_kernel<int, 2, 1, true>",
     "gather_rows8": "rows_lanes_kernel<int, 2, 1, false>", "flags_from_shape": "scan + flags_scatter_kernel",
 }
 for _tag in ("i32", "i64"):

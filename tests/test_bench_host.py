@@ -1,0 +1,44 @@
+"""bench.py's host-side bookkeeping on CPU: the algorithmic bytes each op of the
+step is credited with (the per-element figures the roofline uses), the kernel
+named for each op, the workload description and the peak it divides by."""
+import json
+import os
+
+import pytest
+
+bench = pytest.importorskip("bench")
+
+N32, N64 = 1 << 28, 1 << 27
+
+
+def test_algorithmic_bytes_per_op():
+    ops = {name: (kind, inputs, nbytes) for name, kind, inputs, nbytes in bench.make_ops(N32, N64)}
+    for tag, n, es in (("i32", N32, 4), ("i64", N64, 8)):
+        # the checks read the index array once
+        for op in ("range_perm", "range_oor", "mono_le", "mono_brk", "inj_perm", "inj_dup", "bij_perm", "bij_dup"):
+            assert ops[f"{op}_{tag}"][2] == es * n
+    assert ops["scan_i32"][2] == 8 * N32  # 4 in + 4 out
+    assert ops["partition_p50"][2] == ops["partition_p01"][2] == 16 * N32  # key + payload in and out
+    assert ops["filtpart_p50"][2] == 8 * N32  # Z + key
+    # 2^26 rows of 32 bytes by a 4-byte index: index + row read + row write
+    assert ops["scatter_rows8"][2] == ops["gather_rows8"][2] == (4 + 32 + 32) * (N32 // 4)
+    assert ops["flags_from_shape"][2] is None  # filled in from the drawn shape
+    assert bench.flags_bytes(4096, 1000) == 8 * 4096 + 8 * 4097 + 4 * 1000
+    assert len(ops) == 23
+
+
+def test_every_op_names_its_kernel():
+    for name, _, _, _ in bench.make_ops(N32, N64):
+        assert bench.OP_KERNELS.get(name), name
+
+
+def test_workload_and_peak():
+    c = bench.arm_config(N32, N64, False, 1)
+    assert c["n_i32"] == N32 and c["n_i64"] == N64 and c["parallelism"] == "replicas x1"
+    assert "larger than L2" in c["l2"]
+    peak, source = bench.peaks()
+    path = os.path.join(os.path.dirname(os.path.abspath(bench.__file__)), "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        assert source == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
+    else:
+        assert source == "fallback" and peak == 6800.0
