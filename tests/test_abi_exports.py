@@ -59,3 +59,34 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.ixp_check_range(v, 0, 10, 5, 1, v, v, 256, None) == -1      # lo > hi
     assert lib.ixp_check_range(v, 0, 10, 0, 1, v, None, 256, None) == -4   # no workspace
     assert lib.ixp_check_range(v, 0, 10, 0, 1, v, ctypes.c_void_p(512), 8, None) == -4  # too small
+
+
+def test_segmented_and_hist_arguments_rejected_on_the_host(lib):
+    v, odd = ctypes.c_void_p(256), ctypes.c_void_p(258)  # 258: not 4-byte aligned
+    I64, SZ, P = ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+    lib.ixp_sgm_scan.argtypes = [P, P, ctypes.c_int, P, ctypes.c_int, I64, ctypes.c_int, P, P, SZ, P]
+    assert lib.ixp_sgm_scan(v, v, 7, v, 0, 10, 1, None, v, 1 << 20, None) == -2    # bad input type
+    assert lib.ixp_sgm_scan(v, v, 1, v, 0, 10, 1, None, v, 1 << 20, None) == -2    # int64 into int32
+    assert lib.ixp_sgm_scan(v, v, 0, v, 0, -1, 1, None, v, 1 << 20, None) == -1    # n < 0
+    assert lib.ixp_sgm_scan(None, v, 0, v, 0, 10, 1, None, v, 1 << 20, None) == -1  # no flags
+    assert lib.ixp_sgm_scan(v, odd, 0, v, 0, 10, 1, None, v, 1 << 20, None) == -1  # misaligned values
+    assert lib.ixp_sgm_scan(v, v, 0, v, 0, 10, 1, None, v, 8, None) == -4          # workspace too small
+    lib.ixp_mkii.argtypes = [P, I64, P, ctypes.c_int, I64, P, P, SZ, P]
+    assert lib.ixp_mkii(v, 4, v, 7, 10, None, v, 1 << 20, None) == -2   # bad output type
+    assert lib.ixp_mkii(v, -1, v, 0, 10, None, v, 1 << 20, None) == -1  # m < 0
+    assert lib.ixp_mkii(v, 0, v, 0, 10, None, v, 1 << 20, None) == -1   # positions but no segment
+    assert lib.ixp_mkii(v, 4, odd, 0, 10, None, v, 1 << 20, None) == -1  # misaligned output
+    assert lib.ixp_mkii(v, 4, v, 0, 0, None, None, 0, None) == 0        # nothing to do
+    assert lib.ixp_mkii(v, 4, v, 0, 10, None, v, 8, None) == -4         # workspace too small
+    lib.ixp_hist_min.argtypes = [P, ctypes.c_int, I64, P, ctypes.c_int, P, I64, P]
+    assert lib.ixp_hist_min(v, 7, 4, v, 0, None, 10, None) == -2   # bad H type
+    assert lib.ixp_hist_min(v, 0, 4, v, 9, None, 10, None) == -2   # bad index type
+    assert lib.ixp_hist_min(v, 0, -1, v, 0, None, 10, None) == -1  # m < 0
+    assert lib.ixp_hist_min(v, 0, 4, None, 0, None, 10, None) == -1  # no indices
+    assert lib.ixp_hist_min(odd, 0, 4, v, 0, None, 10, None) == -1  # misaligned H
+    assert lib.ixp_hist_min(v, 0, 0, v, 0, None, 10, None) == 0    # empty H: nothing lands
+    lib.ixp_smallest_pairs.argtypes = [P, P, ctypes.c_int, I64, I64, I64, P, P, P, P, SZ, P]
+    assert lib.ixp_smallest_pairs(v, v, 7, 10, 4, 10, v, v, v, v, 1 << 20, None) == -2    # bad type
+    assert lib.ixp_smallest_pairs(v, v, 0, -1, 4, 10, v, v, v, v, 1 << 20, None) == -1    # n < 0
+    assert lib.ixp_smallest_pairs(v, v, 0, 10, 4, 10, v, v, None, v, 1 << 20, None) == -1  # no count
+    assert lib.ixp_smallest_pairs(v, odd, 0, 10, 4, 10, v, v, v, v, 1 << 20, None) == -1   # misaligned
