@@ -17,6 +17,7 @@ import argparse
 import json
 from ctypes import c_void_p as C_void
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -90,6 +91,54 @@ for _tag in ("i32", "i64"):
 
 def flags_bytes(m, total):
     return 8 * m + 8 * (m + 1) + 4 * total
+
+
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
+def op_elements(name, n32, n64, shape_total):
+    """Elements an op of the step processes: index entries for the checks, the scan,
+    the partition and InvFiltPart; rows for scatter / gather; output positions for
+    mkSgmDescr."""
+    if name.endswith("_i64"):
+        return n64
+    if name in ("scatter_rows8", "gather_rows8"):
+        return n32 // 4
+    if name == "flags_from_shape":
+        return shape_total
+    return n32
+
+
+def op_record(ms, nbytes, elems, peak):
+    """Per-op line: time, algorithmic bytes and their rate, elements per second, and
+    the rate as a fraction of the measured and of the nominal HBM bandwidth."""
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"ms": round(ms, 4), "alg_bytes": nbytes, "gbs": round(gbs, 1),
+            "gelem_s": round(elems / (ms / 1e3) / 1e9, 2), "frac": round(gbs / peak, 4),
+            "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
+
+
+ARM_PARTS = {"0xd0c": "Neoverse N1", "0xd40": "Neoverse V1", "0xd49": "Neoverse N2", "0xd4f": "Neoverse V2"}
+
+
+def host_info(cpuinfo="/proc/cpuinfo"):
+    """Host cores and CPU model, reported beside the oracle's timing (x86 names the
+    model; Arm gives a part number, named here for the Neoverse cores)."""
+    model = platform.machine()
+    try:
+        with open(cpuinfo) as f:
+            fields = {}
+            for line in f:
+                key, _, val = line.partition(":")
+                fields.setdefault(key.strip(), val.strip())
+        if fields.get("model name"):
+            model = fields["model name"]
+        elif fields.get("CPU part"):
+            part = fields["CPU part"].lower()
+            model = f"{platform.machine()} {ARM_PARTS.get(part, 'CPU part ' + part)}"
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
 
 
 def host_inputs(n32, n64):
@@ -302,7 +351,7 @@ def cpu_baseline(steps=4):
     dt = time.perf_counter() - t0
     return {"value": round(total / dt / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
             "sample": f"{steps} pass(es) of the step's op mix at n=2^24 (int32) / 2^23 (int64) = 1/16 of the "
-                      f"workload, {dt:.1f} s, single-threaded C oracle"}
+                      f"workload, {dt:.1f} s, single-threaded C oracle", "host": host_info()}
 
 
 # ---------------------------------------------------------------------- main
@@ -469,11 +518,11 @@ def main():
 
     # per-op times (mean over timed steps)
     per_op = {}
+    peak, peak_src = peaks()
     for i, (name, kind, names, nbytes) in enumerate(ops):
         ts = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
         m = sum(ts) / len(ts)
-        per_op[name] = {"ms": round(m, 4), "alg_bytes": nbytes, "gbs": round(nbytes / (m / 1e3) / 1e9, 1)}
-    peak, peak_src = peaks()
+        per_op[name] = op_record(m, nbytes, op_elements(name, n32, n64, R.shape_total), peak)
     # the op of the kernel with the largest share of the profiled launch list (the
     # committed profile names it), else the op with the largest time
     dom = max(per_op, key=lambda k: per_op[k]["ms"])
@@ -487,8 +536,6 @@ def main():
     roofline = {"bound": "hbm", "op": dom, "kernel": OP_KERNELS.get(dom), "achieved": per_op[dom]["gbs"],
                 "peak": peak, "unit": "GB/s", "frac": round(per_op[dom]["gbs"] / peak, 4), "traffic": traffic,
                 "peak_source": peak_src}
-    for k in per_op:
-        per_op[k]["frac"] = round(per_op[k]["gbs"] / peak, 4)
     ceilings = None
     if not args.no_ceilings:
         ceilings = measure_ceilings(ixp, dev)

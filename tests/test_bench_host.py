@@ -42,3 +42,27 @@ def test_workload_and_peak():
         assert source == "measured" and peak == float(json.load(open(path))["hbm_gbs"])
     else:
         assert source == "fallback" and peak == 6800.0
+
+
+def test_per_op_record_and_elements():
+    assert bench.op_elements("range_perm_i32", N32, N64, 7) == N32
+    assert bench.op_elements("inj_dup_i64", N32, N64, 7) == N64
+    assert bench.op_elements("scatter_rows8", N32, N64, 7) == N32 // 4
+    assert bench.op_elements("flags_from_shape", N32, N64, 7) == 7
+    r = bench.op_record(2.0, 4 * 10**9, 10**9, 8000.0)  # 4 GB and 1 G elements in 2 ms
+    assert r["gbs"] == 2000.0 and r["gelem_s"] == 500.0 and r["frac"] == 0.25
+    assert r["frac_nominal"] == round(2000.0 / bench.NOMINAL_HBM_GBS, 4)
+
+
+def test_host_info():
+    h = bench.host_info()
+    assert h["nproc"] == os.cpu_count() and isinstance(h["cpu_model"], str) and h["cpu_model"]
+
+
+def test_host_info_names_arm_parts(tmp_path):
+    f = tmp_path / "cpuinfo"
+    f.write_text("processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n\n"
+                 "processor\t: 1\nCPU part\t: 0xd4f\n")
+    assert "Neoverse V2" in bench.host_info(str(f))["cpu_model"]
+    f.write_text("processor\t: 0\nmodel name\t: Example CPU @ 2.0GHz\n")
+    assert bench.host_info(str(f))["cpu_model"] == "Example CPU @ 2.0GHz"
