@@ -3,7 +3,6 @@ needs 64 bits: the checks, the scan, the partition (int64 destinations), a gathe
 and the reduce-by-index, each against positions planted at and beyond 2^31 and
 against closed forms that hold at any size (torch's own int64 arithmetic on the
 device serves as the reference for the sampled destinations)."""
-import numpy as np
 import pytest
 
 import oracle

@@ -9,7 +9,6 @@ already run every other test.
 """
 import ctypes
 
-import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
