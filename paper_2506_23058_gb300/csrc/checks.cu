@@ -1145,8 +1145,8 @@ static bool bucket_config(unsigned long long span, unsigned long long pool, Buck
 }
 
 template <typename T, bool BIJ>
-static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int64_t mlo, int64_t mhi, int fixed,
-                           int64_t flo, int64_t fhi, const BitmapWs &w, const BucketCfg &cfg, cudaStream_t st) {
+static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int fixed, int64_t flo, int64_t fhi,
+                           const BitmapWs &w, const BucketCfg &cfg, cudaStream_t st) {
     const int sgrid = num_sms() * 4;
     bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, w.cursors, w.bm, w.dup,
                                                           w.bmask);
@@ -1182,7 +1182,7 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
     if (bij) {
         const unsigned long long isize = (unsigned long long)ihi - (unsigned long long)ilo + 1ull;
         if (w.buckets && isize >= BK_MIN_SPAN && bucket_config(isize, bk_pool_entries(n), &cfg)) {
-            launch_buckets<T, true>(x, n, rlo, rhi, ilo, ihi, 1, ilo, ihi, w, cfg, st);
+            launch_buckets<T, true>(x, n, rlo, rhi, 1, ilo, ihi, w, cfg, st);
             first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, w.bmask, cfg.lw,
                                                                  &h->k_first2);
         } else {
@@ -1210,7 +1210,7 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
     const unsigned long long span_cap = fixed ? rspan : cap;
     const bool bk = w.buckets && span_cap >= BK_MIN_SPAN && bucket_config(span_cap, bk_pool_entries(n), &cfg);
     if (bk) {
-        launch_buckets<T, false>(x, n, rlo, rhi, rlo, rhi, fixed ? 1 : 0, rlo, rhi, w, cfg, st);
+        launch_buckets<T, false>(x, n, rlo, rhi, fixed ? 1 : 0, rlo, rhi, w, cfg, st);
     } else {
         bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, fixed ? 1 : 0, rlo, rhi, cap, bm, dup);
         if (n > 0) mark_kernel<T, false><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, rlo, rhi, h, bm, dup);
