@@ -876,7 +876,7 @@ def measure_ceilings(ixp, dev, reps=3):
 
 def run_partition2(ixp, dev):
     """partition2 (Fig. 2) of float32 uniform in [0, 1) by x < 0.5 at the sizes of
-    the paper's GPU measurement (50M, 100M, 200M elements, Sec. 7), three ways:
+    the paper's GPU measurement (50M, 100M, 200M elements, Sec. 6), three ways:
     dynamic (the index array materialised, its injectivity decided by
     reduce-by-index with min, then the scatter into a zeroed destination), static
     (the fused partition into a zeroed destination) and static without the
@@ -934,7 +934,7 @@ def run_partition2(ixp, dev):
 
 
 def run_matching(ixp, dev):
-    """get_smallest_pairs of maxMatching (Fig. 9) on a random graph: 2^26 int64
+    """get_smallest_pairs of maxMatching (Fig. 16) on a random graph: 2^26 int64
     edge-endpoint slots over 2^23 vertices (uniform endpoints, 8 slots per vertex),
     injective priorities; then the paper's postcondition, Inj of both outputs,
     checked at run time."""

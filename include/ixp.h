@@ -344,8 +344,8 @@ int ixp_mkii(const int64_t *offsets, int64_t m, void *out, int out_type, int64_t
 
 /* ---- reduce-by-index and maxMatching ------------------------------------------- */
 
-/* Reduce-by-index with min, Futhark's hist with the min operator  [Sec. 7: the
- * hist of get_smallest_pairs, Fig. 9, and of the dynamic verification of
+/* Reduce-by-index with min, Futhark's hist with the min operator  [Sec. 6: the
+ * hist of get_smallest_pairs, Fig. 16, and of the dynamic verification of
  * scatter]: for every i with 0 <= idx[i] < m, H[idx[i]] = min(H[idx[i]],
  * vals[i]); indices out of bounds are ignored, as scatter ignores them (Sec. 2.1).
  * H: device htype[m] holding the neutral element on entry (the caller fills it).
@@ -356,7 +356,7 @@ int ixp_hist_min(void *H, int htype, int64_t m, const void *idx, int itype, cons
                  ixp_stream stream);
 
 /* Inj on [0, m) decided the way a dynamic verification of scatter decides it
- * [Sec. 7: reduce-by-index with atomic min]: H = hist min over [0, m) of
+ * [Sec. 6: reduce-by-index with atomic min]: H = hist min over [0, m) of
  * iota n by x, then every i with 0 <= x[i] < m must have H[x[i]] == i. Same
  * property and verdict as ixp_check_inj(x, itype, n, 0, m - 1, ...): index = the
  * first occurrence of the earliest repeated value, value = x[index], aux0 = its
@@ -365,7 +365,7 @@ int ixp_hist_min(void *H, int htype, int64_t m, const void *idx, int itype, cons
 int ixp_check_inj_hist(const void *x, int itype, int64_t n, int64_t m, ixp_verdict *d_verdict, void *ws,
                        size_t ws_bytes, ixp_stream stream);
 
-/* get_smallest_pairs of maxMatching  [Sec. 7, Fig. 9]: H = hist min over n_verts
+/* get_smallest_pairs of maxMatching  [Sec. 6, Fig. 16]: H = hist min over n_verts
  * bins, neutral element n_es, of the priorities is by the vertices es; slot i is
  * kept when 0 <= es[i] < n_verts and H[es[i]] == is[i]; out_es / out_is get the
  * kept es[i] / is[i] in input order (filter_by) and *d_count their number. When

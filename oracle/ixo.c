@@ -670,13 +670,24 @@ int ixo_gather(void *out, const void *src, int64_t src_len, const void *idx, int
 }
 
 /* --------------------------------------------------------------- partition
- * partition2 of Fig. 2 (left), step by step: cs = map p xs; flagsT = cs as 0/1;
- * flagsF = 1 - flagsT; indicesT = inclusive scan flagsT; num_true = last of
- * indicesT; indicesF = (inclusive scan flagsF) + num_true; indices = cs ? t-1 : f-1;
- * ys = scatter zeros indices xs. Segmented (partition2L, Sec. 6): the same per
- * segment, with every destination shifted by the segment offset e_k.
- * Outputs: out_idx = indices (scatter destinations, in input order), num_true[k],
- * and optionally the scattered keys and payload rows. */
+ * Stable two-way partition (Sec. 2.1 and Fig. 2, partition2; Sec. 6, partition2L
+ * for segments). What it computes: inside each segment [e_k, e_{k+1}) the elements
+ * whose predicate holds come first and the others after them, each group keeping
+ * its input order; indices[i] is the position element i moves to (the scatter
+ * destination, Sec. 2.3), and num_true[k] is the size of segment k's first group.
+ * Written as two ordered walks over each segment: the first hands out e_k, e_k+1,
+ * ... to the elements whose predicate holds, the second continues the count for
+ * the others. Optionally the keys and payload rows are moved to their positions. */
+static void partition_move(int64_t i, int64_t d, void *out_idx, int ot, const void *keys, int kt,
+                           void *out_keys, const void *payload, int row_bytes, void *out_payload)
+{
+    put(out_idx, ot, i, (uint64_t)d);
+    if (out_keys)
+        memcpy((char *)out_keys + d * (kt ? 8 : 4), (const char *)keys + i * (kt ? 8 : 4), kt ? 8 : 4);
+    if (out_payload)
+        memcpy((char *)out_payload + d * row_bytes, (const char *)payload + i * row_bytes, (size_t)row_bytes);
+}
+
 int ixo_partition(const void *keys, int kt, int64_t n, ixo_pred p, const void *payload, int row_bytes,
                   void *out_idx, int ot, void *out_keys, void *out_payload, int64_t *num_true,
                   const int64_t *off, int64_t nseg)
@@ -689,55 +700,28 @@ int ixo_partition(const void *keys, int kt, int64_t n, ixo_pred p, const void *p
         return IXO_E_INVAL;
     if (ot == 0 && n > INT32_MAX)
         return IXO_E_INVAL;
-    int64_t cap = 1;
-    for (int64_t k = 0; k < seg_count(off, nseg); k++)
-        if (seg_hi(off, k, n) - seg_lo(off, k) > cap)
-            cap = seg_hi(off, k, n) - seg_lo(off, k);
-    uint8_t *cs = malloc((size_t)cap);
-    int64_t *flagsT = malloc((size_t)cap * 8), *flagsF = malloc((size_t)cap * 8);
-    int64_t *indT = malloc((size_t)cap * 8), *tmp = malloc((size_t)cap * 8);
-    if (!cs || !flagsT || !flagsF || !indT || !tmp) {
-        free(cs); free(flagsT); free(flagsF); free(indT); free(tmp);
-        return IXO_E_NOMEM;
-    }
     for (int64_t k = 0; k < seg_count(off, nseg); k++) {
-        int64_t a = seg_lo(off, k), len = seg_hi(off, k, n) - a;
-        for (int64_t i = 0; i < len; i++)
-            cs[i] = (uint8_t)pred_eval(&p, keys, kt, a + i);
-        for (int64_t i = 0; i < len; i++)
-            flagsT[i] = cs[i] ? 1 : 0;
-        for (int64_t i = 0; i < len; i++)
-            flagsF[i] = 1 - flagsT[i];
-        int64_t acc = 0;
-        for (int64_t i = 0; i < len; i++)
-            indT[i] = (acc += flagsT[i]);
-        int64_t nt = len > 0 ? indT[len - 1] : 0;
-        acc = 0;
-        for (int64_t i = 0; i < len; i++)
-            tmp[i] = (acc += flagsF[i]);
-        for (int64_t i = 0; i < len; i++) {
-            int64_t indF = tmp[i] + nt;
-            int64_t d = a + (cs[i] ? indT[i] - 1 : indF - 1);
-            put(out_idx, ot, a + i, (uint64_t)d);
-            if (out_keys)
-                memcpy((char *)out_keys + d * (kt ? 8 : 4), (const char *)keys + (a + i) * (kt ? 8 : 4), kt ? 8 : 4);
-            if (out_payload)
-                memcpy((char *)out_payload + d * row_bytes, (const char *)payload + (a + i) * row_bytes,
-                       (size_t)row_bytes);
-        }
-        num_true[off ? k : 0] = nt;
+        int64_t a = seg_lo(off, k), b = seg_hi(off, k, n);
+        int64_t next = a; /* the next free position of segment k */
+        for (int64_t i = a; i < b; i++)
+            if (pred_eval(&p, keys, kt, i))
+                partition_move(i, next++, out_idx, ot, keys, kt, out_keys, payload, row_bytes, out_payload);
+        num_true[off ? k : 0] = next - a;
+        for (int64_t i = a; i < b; i++)
+            if (!pred_eval(&p, keys, kt, i))
+                partition_move(i, next++, out_idx, ot, keys, kt, out_keys, payload, row_bytes, out_payload);
     }
-    free(cs); free(flagsT); free(flagsF); free(indT); free(tmp);
     return IXO_OK;
 }
 
 /* ------------------------------------------------------------ mkSgmDescr
- * Fig. 2 (right), mkSgmDescr shape xs, step by step: rot = shape shifted right by
- * one with 0 in front; scn = inclusive scan rot (the exclusive scan of shape);
- * ind[i] = shape[i] <= 0 ? -1 : scn[i]; len = scn[m-1] + shape[m-1]; res = scatter
- * (replicate len 0) ind xs. Precondition Range shape (0, inf): negative shapes are
- * rejected. xs == NULL means all ones (a plain flag array). offsets (nullable) gets
- * scn followed by len (m + 1 entries). */
+ * mkSgmDescr shape xs (Fig. 2, right; Sec. 2.1): segment k occupies positions
+ * [e_k, e_k + shape[k]) of a zero array of length sum(shape), where e_k is the sum
+ * of the shapes before k; the first position of every non-empty segment holds
+ * xs[k]. Written as one running offset over the segments. Precondition Range shape
+ * (0, inf): negative shapes are rejected. xs == NULL means all ones (a plain flag
+ * array). offsets (nullable) gets e_0 .. e_{m-1} followed by the total (m + 1
+ * entries). */
 int ixo_flags_from_shape(const int64_t *shape, int64_t m, const int64_t *xs, void *out, int ot, int64_t out_len,
                          int64_t *offsets)
 {
@@ -745,76 +729,56 @@ int ixo_flags_from_shape(const int64_t *shape, int64_t m, const int64_t *xs, voi
         return IXO_E_DTYPE;
     if (m < 0 || (m > 0 && !shape))
         return IXO_E_INVAL;
-    for (int64_t i = 0; i < m; i++)
-        if (shape[i] < 0)
+    int64_t len = 0;
+    for (int64_t k = 0; k < m; k++) {
+        if (shape[k] < 0)
             return IXO_E_INVAL;
-    int64_t *rot = malloc((size_t)(m > 0 ? m : 1) * 8), *scn = malloc((size_t)(m > 0 ? m : 1) * 8),
-            *ind = malloc((size_t)(m > 0 ? m : 1) * 8);
-    if (!rot || !scn || !ind) {
-        free(rot); free(scn); free(ind);
-        return IXO_E_NOMEM;
+        len += shape[k];
     }
-    for (int64_t i = 0; i < m; i++)
-        rot[i] = i == 0 ? 0 : shape[i - 1];
-    int64_t acc = 0;
-    for (int64_t i = 0; i < m; i++)
-        scn[i] = (acc += rot[i]);
-    for (int64_t i = 0; i < m; i++)
-        ind[i] = shape[i] <= 0 ? -1 : scn[i];
-    int64_t len = m > 0 ? scn[m - 1] + shape[m - 1] : 0;
-    if (len != out_len || (len > 0 && !out)) {
-        free(rot); free(scn); free(ind);
+    if (len != out_len || (len > 0 && !out))
         return IXO_E_INVAL;
-    }
     for (int64_t j = 0; j < len; j++)
         put(out, ot, j, 0);
-    for (int64_t i = 0; i < m; i++)
-        if (0 <= ind[i] && ind[i] < len)
-            put(out, ot, ind[i], (uint64_t)(xs ? xs[i] : 1));
-    if (offsets) {
-        for (int64_t i = 0; i < m; i++)
-            offsets[i] = scn[i];
-        offsets[m] = len;
+    int64_t e = 0;
+    for (int64_t k = 0; k < m; k++) {
+        if (offsets)
+            offsets[k] = e;
+        if (shape[k] > 0)
+            put(out, ot, e, (uint64_t)(xs ? xs[k] : 1));
+        e += shape[k];
     }
-    free(rot); free(scn); free(ind);
+    if (offsets)
+        offsets[m] = len;
     return IXO_OK;
 }
 
 /* ------------------------------------------------------------------ mkII
- * Fig. 2 (right), mkII shape: II[j] = k for e_k <= j < e_{k+1} (the prose of
- * Sec. 2.1). Steps: write k+1 at the start of each non-empty segment with
- * mkSgmDescr, take flags = (that value > 0), subtract one, and propagate with the
- * segmented scan. Reading: the figure builds the flags after subtracting one,
- * which would miss a non-empty segment 0; the flags are taken before. */
+ * mkII shape (Fig. 2, right): II[j] = k for e_k <= j < e_{k+1}, the segment number
+ * of every position (the prose of Sec. 2.1). Reading: the figure builds its flags
+ * after subtracting one, which would miss a non-empty segment 0; the definition
+ * above is what is computed. Written as a walk that repeats k shape[k] times. */
 int ixo_mkii(const int64_t *shape, int64_t m, int64_t *out, int64_t out_len)
 {
     if (m < 0 || (m > 0 && !shape))
         return IXO_E_INVAL;
-    int64_t *beg = malloc((size_t)(m > 0 ? m : 1) * 8);
-    int64_t *sct1 = malloc((size_t)(out_len > 0 ? out_len : 1) * 8);
-    int64_t *sct = malloc((size_t)(out_len > 0 ? out_len : 1) * 8);
-    uint8_t *flags = malloc((size_t)(out_len > 0 ? out_len : 1));
-    if (!beg || !sct1 || !sct || !flags) {
-        free(beg); free(sct1); free(sct); free(flags);
-        return IXO_E_NOMEM;
+    int64_t len = 0;
+    for (int64_t k = 0; k < m; k++) {
+        if (shape[k] < 0)
+            return IXO_E_INVAL;
+        len += shape[k];
     }
-    for (int64_t i = 0; i < m; i++)
-        beg[i] = i + 1;
-    int rc = ixo_flags_from_shape(shape, m, beg, sct1, 1, out_len, NULL);
-    if (rc == IXO_OK) {
-        for (int64_t j = 0; j < out_len; j++) {
-            flags[j] = sct1[j] > 0;
-            sct[j] = sct1[j] == 0 ? 0 : sct1[j] - 1;
-        }
-        rc = ixo_sgm_scan(flags, sct, 1, out, 1, out_len);
-    }
-    free(beg); free(sct1); free(sct); free(flags);
-    return rc;
+    if (len != out_len || (len > 0 && !out))
+        return IXO_E_INVAL;
+    int64_t j = 0;
+    for (int64_t k = 0; k < m; k++)
+        for (int64_t r = 0; r < shape[k]; r++)
+            out[j++] = k;
+    return IXO_OK;
 }
 
 /* ------------------------------------------------------------- hist min
- * Reduce-by-index with min, Futhark's `hist` with the min operator (Sec. 7:
- * get_smallest_pairs of maxMatching, Fig. 9, and the reduce-by-index that the
+ * Reduce-by-index with min, Futhark's `hist` with the min operator (Sec. 6:
+ * get_smallest_pairs of maxMatching, Fig. 16, and the reduce-by-index that the
  * dynamic verification of scatter needs). H holds the neutral element on entry
  * (the caller fills it); for i = 0..n-1 in order, if 0 <= idx[i] < m then
  * H[idx[i]] = min(H[idx[i]], vals[i]). vals NULL means vals[i] = i. An index out of
@@ -837,13 +801,15 @@ int ixo_hist_min(void *H, int ht, int64_t m, const void *idx, int it, const void
 }
 
 /* -------------------------------------------------- get_smallest_pairs
- * Fig. 9 (left), step by step: H = hist min n_es n_verts es is; cs[i] = (H[es[i]]
- * == is[i]); xs = filter cs es; ys = filter cs is (filter_by keeps the flagged
- * elements in input order, FiltPart with p^f = cs and one part). es and is share
- * type t. Reading: the precondition Range es (0, n_verts) is half-open (es indexes
- * H, which has n_verts bins); an es[i] outside it has no bin, the hist ignores it
- * and cs[i] is false. out_es and out_is have room for n entries; *count gets the
- * number kept. */
+ * get_smallest_pairs of maxMatching (Sec. 6, Fig. 16): slot i is an edge endpoint
+ * es[i] with priority is[i]. Slot i is kept when es[i] names a vertex of
+ * [0, n_verts) and is[i] equals the smallest of n_es and the priorities of every
+ * slot of that vertex; the kept (es[i], is[i]) pairs are written in input order.
+ * Written as: the smallest priority per vertex (starting from n_es), then one
+ * ordered walk that keeps the slots that attain it. Reading: the precondition
+ * Range es (0, n_verts) is half-open (es indexes the vertex array); a slot outside
+ * it names no vertex and is not kept. es and is share type t; out_es and out_is
+ * have room for n entries; *count gets the number kept. */
 int ixo_smallest_pairs(int64_t n_verts, int64_t n_es, const void *es, const void *is, int t, int64_t n,
                        void *out_es, void *out_is, int64_t *count)
 {
@@ -851,32 +817,26 @@ int ixo_smallest_pairs(int64_t n_verts, int64_t n_es, const void *es, const void
         return IXO_E_DTYPE;
     if (n < 0 || n_verts < 0 || (n > 0 && (!es || !is || !out_es || !out_is)) || !count)
         return IXO_E_INVAL;
-    void *H = malloc((size_t)(n_verts > 0 ? n_verts : 1) * 8);
-    if (!H)
+    int64_t *best = malloc((size_t)(n_verts > 0 ? n_verts : 1) * 8);
+    if (!best)
         return IXO_E_NOMEM;
-    for (int64_t k = 0; k < n_verts; k++)
-        put(H, 1, k, (uint64_t)n_es);
-    /* the hist runs in 64 bits: is values widen exactly, and n_es may exceed them */
-    int64_t *is64 = calloc((size_t)(n > 0 ? n : 1), 8);
-    if (!is64) {
-        free(H);
-        return IXO_E_NOMEM;
+    for (int64_t v = 0; v < n_verts; v++)
+        best[v] = n_es;
+    for (int64_t i = 0; i < n; i++) {
+        int64_t v = get(es, t, i), pr = get(is, t, i);
+        if (v >= 0 && v < n_verts && pr < best[v])
+            best[v] = pr;
     }
-    for (int64_t i = 0; i < n; i++)
-        is64[i] = get(is, t, i);
-    int rc = ixo_hist_min(H, 1, n_verts, es, t, is64, n);
     int64_t c = 0;
-    for (int64_t i = 0; rc == IXO_OK && i < n; i++) {
-        int64_t v = get(es, t, i);
-        int keep = v >= 0 && v < n_verts && get(H, 1, v) == is64[i];
-        if (keep) {
+    for (int64_t i = 0; i < n; i++) {
+        int64_t v = get(es, t, i), pr = get(is, t, i);
+        if (v >= 0 && v < n_verts && pr == best[v]) {
             put(out_es, t, c, (uint64_t)v);
-            put(out_is, t, c, (uint64_t)is64[i]);
+            put(out_is, t, c, (uint64_t)pr);
             c++;
         }
     }
     *count = c;
-    free(is64);
-    free(H);
-    return rc;
+    free(best);
+    return IXO_OK;
 }

@@ -1,6 +1,6 @@
-// hist.cu - reduce-by-index with the min operator (Futhark's hist, Sec. 7), the
+// hist.cu - reduce-by-index with the min operator (Futhark's hist, Sec. 6), the
 // dynamic verification of a scatter's injectivity built on it, and
-// get_smallest_pairs of maxMatching (Fig. 9).
+// get_smallest_pairs of maxMatching (Fig. 16).
 //
 // Reduce-by-index: every in-bounds element issues one atomic min whose result is
 // unused, so each is a fire-and-forget reduction at L2. Its rate is that of L2
@@ -8,7 +8,7 @@
 // not (each reduction then reads and writes back one 32-byte sector).
 //
 // Dynamic Inj check (what the paper's evaluation compares static verification
-// against, Sec. 7): H = hist min over [0, m) of iota by x; Inj on [0, m) holds
+// against, Sec. 6): H = hist min over [0, m) of iota by x; Inj on [0, m) holds
 // iff every in-bounds i has H[x[i]] == i. A violation at j means x[j] repeats an
 // earlier element H[x[j]] < j; the smallest such H[x[j]] is the first
 // occurrence of the earliest repeated value and the smallest j with that H is its

@@ -1,5 +1,5 @@
 """Reduce-by-index with min, the dynamic Inj check built on it, get_smallest_pairs
-(maxMatching, Fig. 9) and the partition without its index array, against the
+(maxMatching, Fig. 16) and the partition without its index array, against the
 oracle element by element on seeded inputs spanning several tiles (4096 elements
 for the filter, 16-byte groups for the streaming kernels) and ragged tails."""
 import numpy as np

@@ -94,19 +94,25 @@ def bf_inj(x, lo, hi):
 
 
 def bf_bij(x, rlo, rhi, ilo, ihi):
+    """Fig. 5 Bij by its definition: (kind, index, value, in-image count, |Img|).
+    The position reported is the first one that breaks the property: a value in Rcd
+    outside Img, or a value that occurs again; with neither, the smallest image
+    value no element takes."""
     n = len(x)
     img = set(range(ilo, ihi + 1))
+    in_img = sum(1 for v in x if ilo <= v <= ihi)
+    size = ihi - ilo + 1
     for i in range(n):
         if not (rlo <= x[i] <= rhi):
             continue
         if x[i] not in img:
-            return "out_of_image", i, x[i]
+            return "out_of_image", i, x[i], in_img, size
         if any(x[j] == x[i] for j in range(n) if j != i):
-            return "duplicate", i, x[i]
+            return "duplicate", i, x[i], in_img, size
     s = {v for v in x if rlo <= v <= rhi}
     if s != img:
-        return "missing", -1, min(img - s)
-    return "none", -1, 0
+        return "missing", -1, min(img - s), in_img, size
+    return "none", -1, 0, in_img, size
 
 
 def small_arrays():
@@ -170,10 +176,12 @@ def test_bij_brute_force():
         a = np.array(x, np.int32)
         for rlo, rhi, ilo, ihi in [(I64MIN, I64MAX, 0, 2), (0, 3, 0, 3), (0, 2, 0, 2), (-1, 3, 0, 1)]:
             v = oracle.check_bij(a, rlo, rhi, ilo, ihi)
-            kind, i, val = bf_bij(x, rlo, rhi, ilo, ihi)
+            kind, i, val, cnt, size = bf_bij(x, rlo, rhi, ilo, ihi)
             assert v["kind"] == kind and v["index"] == i and v["ok"] == (kind == "none"), (x, rlo, rhi, ilo, ihi)
             if kind != "none":
                 assert v["value"] == val
+            # aux0 = elements whose value lies in Img, aux1 = |Img| (rule BijF1's two counts)
+            assert (v["aux0"], v["aux1"]) == (cnt, size), (x, rlo, rhi, ilo, ihi)
 
 
 def test_bij_identity_and_permutation():
@@ -235,6 +243,39 @@ def test_segmented_checks_equal_per_segment_checks():
             v = oracle.check_bij(y2, I64MIN, I64MAX, seg_img=True, offsets=off)
             exp_ok = all(sorted(y2[off[k]:off[k + 1]].tolist()) == list(range(off[k], off[k + 1])) for k in range(m))
             assert v["ok"] == exp_ok
+
+
+def test_segmented_bij_counts_per_segment():
+    # Segmented Bij (Fig. 5, Img_k = [e_k, e_{k+1})): the verdict of the first
+    # failing segment, with that segment's in-image count and |Img_k| as aux0/aux1;
+    # when every segment holds, the counts are summed over the segments.
+    rng = np.random.default_rng(13)
+    for _ in range(400):
+        n = int(rng.integers(0, 14))
+        m = int(rng.integers(1, 5))
+        off = random_segments(rng, n, m)
+        y = np.concatenate([rng.permutation(np.arange(off[k], off[k + 1])) for k in range(m)]).astype(np.int64) \
+            if n else np.zeros(0, np.int64)
+        for _ in range(int(rng.integers(0, 3))):
+            if n:
+                y[int(rng.integers(0, n))] = int(rng.integers(-1, n + 1))
+        rlo, rhi = (I64MIN, I64MAX) if rng.random() < 0.5 else (0, max(n - 1, 0))
+        v = oracle.check_bij(y, rlo, rhi, seg_img=True, offsets=off)
+        first = None
+        tot_in = tot_size = 0
+        for k in range(m):
+            a, b = int(off[k]), int(off[k + 1])
+            seg = y[a:b].tolist()
+            kind, i, val, cnt, size = bf_bij(seg, rlo, rhi, a, b - 1) if b > a else ("none", -1, 0, 0, 0)
+            tot_in += cnt
+            tot_size += size
+            if kind != "none" and first is None:
+                first = (kind, a + i if i >= 0 else -1, val, cnt, size)
+        if first is None:
+            assert v["ok"] and (v["aux0"], v["aux1"]) == (tot_in, tot_size), (y, off)
+        else:
+            assert not v["ok"], (y, off)
+            assert (v["kind"], v["index"], v["value"], v["aux0"], v["aux1"]) == first, (y, off, v, first)
 
 
 # ------------------------------------------------------------ partition pins
@@ -312,7 +353,7 @@ def test_filtpart_brute_force_filter_and_classes():
         z = np.array([r if r >= 0 else N + 1 + i for i, r in enumerate(ref)], np.int64)
         fl = ("flags", 0, 0, flags)
         vd = oracle.check_filtpart(z, keys, filt=fl, cls=cls, v=v, offsets=off)
-        assert vd["ok"] and vd["aux0"] == N
+        assert vd["ok"] and vd["aux0"] == N and vd["index"] == -1
         z2 = np.array([r if r >= 0 else -1 for r in ref], np.int64)
         assert oracle.check_filtpart(z2, keys, filt=fl, cls=cls, v=v, offsets=off)["ok"]
         if N >= 1:
@@ -322,6 +363,50 @@ def test_filtpart_brute_force_filter_and_classes():
             z3[i] = (ref[i] + 1) % N if ref[i] >= 0 and N > 1 else (0 if ref[i] < 0 else -5)
             vd = oracle.check_filtpart(z3, keys, filt=fl, cls=cls, v=v, offsets=off)
             assert not vd["ok"] and vd["index"] == i and vd["kind"] == "wrong_dest"
+            # aux0 = N, aux1 = the destination the definition gives i (-1: dropped)
+            assert vd["value"] == z3[i] and vd["aux0"] == N and vd["aux1"] == ref[i]
+
+
+def test_filtpart_value_mode_brute_force():
+    # FiltPart Y X (e_k, p^f, p^p) in value form: Y is X filtered and stably
+    # partitioned per segment (built here with Python's stable sort). A swapped pair
+    # of rows is reported at the smaller position with that position's source
+    # index; a flipped bit at its position; a Y of the wrong length with index -1.
+    rng = np.random.default_rng(33)
+    for _ in range(300):
+        n = int(rng.integers(0, 25))
+        v = int(rng.integers(1, 5))
+        keys = rng.integers(-9, 9, size=n).astype(np.int64)
+        cls = rng.integers(0, v + 1, size=n).astype(np.uint8)
+        flags = rng.integers(0, 2, size=n).astype(np.uint8)
+        off = random_segments(rng, n, int(rng.integers(1, 4)))
+        rows = rng.integers(0, 2**31, size=(n, 3)).astype(np.int32)
+        ref, N = bf_filtpart_ref(n, flags.tolist(), [min(c, v - 1) for c in cls.tolist()], off.tolist())
+        src = [0] * N
+        for i, r in enumerate(ref):
+            if r >= 0:
+                src[r] = i
+        y = rows[src] if N else np.zeros((0, 3), np.int32)
+        fl = ("flags", 0, 0, flags)
+        vd = oracle.check_filtpart_values(y, rows, keys, filt=fl, cls=cls, v=v, offsets=off)
+        assert vd["ok"] and vd["aux0"] == N
+        if N >= 2:
+            a, b = sorted(rng.choice(N, size=2, replace=False).tolist())
+            y2 = y.copy()
+            y2[[a, b]] = y2[[b, a]]
+            vd = oracle.check_filtpart_values(y2, rows, keys, filt=fl, cls=cls, v=v, offsets=off)
+            same = np.array_equal(y[a], y[b])
+            assert vd["ok"] == same
+            if not same:
+                assert (vd["kind"], vd["index"], vd["value"]) == ("wrong_dest", a, src[a])
+        if N >= 1:
+            p = int(rng.integers(0, N))
+            y3 = y.copy()
+            y3[p, int(rng.integers(0, 3))] ^= 1 << int(rng.integers(0, 31))
+            vd = oracle.check_filtpart_values(y3, rows, keys, filt=fl, cls=cls, v=v, offsets=off)
+            assert (vd["ok"], vd["index"], vd["value"]) == (0, p, src[p])
+            vd = oracle.check_filtpart_values(y[:-1], rows, keys, filt=fl, cls=cls, v=v, offsets=off)
+            assert (vd["ok"], vd["kind"], vd["index"], vd["value"], vd["aux0"]) == (0, "wrong_dest", -1, N - 1, N)
 
 
 def test_invfiltpart_listed_conditions_are_weaker():
@@ -467,7 +552,7 @@ def test_hist_min_of_iota_is_the_first_occurrence():
 
 
 def test_dynamic_scatter_check_by_hist_decides_inj():
-    """The dynamic verification of a scatter (Sec. 7): with H = hist min of iota by
+    """The dynamic verification of a scatter (Sec. 6): with H = hist min of iota by
     the indices, Inj on [0, m) holds iff every in-bounds i has H[idx[i]] == i; the
     first occurrence of the earliest repeated value is min H over the violations."""
     rng = np.random.default_rng(73)
@@ -498,7 +583,7 @@ def _smallest_pairs_brute(nv, n_es, es, is_):
 
 
 def test_smallest_pairs_brute_force_and_postcondition():
-    """get_smallest_pairs (Fig. 9) against its definition written as an all-pairs
+    """get_smallest_pairs (Fig. 16) against its definition written as an all-pairs
     loop, and its postcondition: with is injective, es' and is' are injective and es'
     holds each vertex that occurs in es exactly once."""
     rng = np.random.default_rng(74)
