@@ -665,10 +665,11 @@ def run_backward(ixp, inp, n32, dev, per_op):
     nr = n32 // 4
     perm = inp["perm_rows"]
     src = inp["payload8"].detach().requires_grad_(True)
-    inv = ixp.invert(perm, nr)  # the proven-Inj index's inverse, built once per index array
-    y = autograd.gather(src, perm, inverse=inv)
+    inv = ixp.invert(perm, nr)  # the index's inverse and its Inj verdict, built once per index array
+    proof = ixp.check_inj(perm, 0, nr - 1)
+    y = autograd.gather(src, perm, inverse=inv, proof=proof)
     gy = torch.empty_like(y).uniform_(-1, 1)
-    fwd = _time(lambda: autograd.gather(src, perm, inverse=inv))
+    fwd = _time(lambda: autograd.gather(src, perm, inverse=inv, proof=proof))
     bwd = _time(lambda: torch.autograd.grad(y, src, gy, retain_graph=True))
     nbytes = 68 * nr
     zipf = torch.from_numpy(synth.zipf_ranks(nr, 1 << 20, 1.1, synth.seed_for(4))).to(dev)

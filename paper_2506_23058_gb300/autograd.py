@@ -4,13 +4,17 @@ Forward and backward both run the library's kernels (this module only allocates
 outputs and marshals arguments):
 
 * ``gather``   y[i] = src[idx[i]].  Adjoint: grad_src[t] = sum of grad_y[i] over
-  idx[i] = t. When the caller asserts (or has checked with ``check_inj``) that idx
-  is injective, that sum has at most one term: with the inverse index array
-  (``invert``; the paper's scatter rule Sc1 builds the same is^-1 for a bijective
-  index) the adjoint is a gather, grad_src[t] = grad_y[inv[t]], with sequential
-  writes and no atomics; without it, a plain atomic-free scatter. Otherwise float32
-  gradients accumulate in float64 and are rounded once; float64 gradients use
-  float64 atomics.
+  idx[i] = t. When idx is injective on [0, len(src)) that sum has at most one
+  term: with the inverse index array (``invert``; the paper's scatter rule Sc1
+  builds the same is^-1 for a bijective index) the adjoint is a gather,
+  grad_src[t] = grad_y[inv[t]], with sequential writes and no atomics; without it,
+  a plain atomic-free scatter. That path is taken only on a proven Inj: asking for
+  it (``injective=True`` or an ``inverse``) runs ``check_inj(idx, 0, len(src) - 1)``
+  in the forward pass, unless the caller hands in the verdict of that same check
+  (``proof``, e.g. kept beside a cached inverse); the backward reads the verdict
+  and, when Inj does not hold, takes the general path below, so duplicate indices
+  never lose gradient terms. In the general path float32 gradients accumulate in
+  float64 and are rounded once; float64 gradients use float64 atomics.
 * ``scatter``  out = dst with rows idx[i] replaced by vals[i] (indices outside
   dst are ignored, Sec. 2.1). Requires injective in-bounds indices (the paper's
   condition for a deterministic scatter). Adjoint: grad_vals = gather of grad_out
@@ -48,12 +52,15 @@ def _scatter_add_into(grad, idx, g):
 
 class GatherFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, src, idx, injective=False, inverse=None):
+    def forward(ctx, src, idx, injective=False, inverse=None, proof=None):
         out, status = ixp.gather(src.contiguous(), idx)
-        ctx.save_for_backward(idx, inverse if inverse is not None else idx)
-        ctx.has_inverse = inverse is not None
         ctx.src_shape = src.shape
-        ctx.injective = bool(injective) or inverse is not None
+        ctx.fast = bool(injective) or inverse is not None
+        ctx.has_inverse = inverse is not None
+        if ctx.fast and proof is None:
+            proof = ixp.check_inj(idx, 0, max(src.shape[0] - 1, 0))  # device work only; read in backward
+        ctx.proof = proof
+        ctx.save_for_backward(idx, inverse if inverse is not None else idx)
         ctx.mark_non_differentiable(status)
         return out, status
 
@@ -61,15 +68,19 @@ class GatherFn(torch.autograd.Function):
     def backward(ctx, g, _g_status):
         idx, inv = ctx.saved_tensors
         g = g.contiguous()
-        if ctx.has_inverse:
+        proven = False
+        if ctx.fast:
+            v = ctx.proof.get()
+            proven = v["ok"] == 1 and v["status"] == 0
+        if proven and ctx.has_inverse:
             grad, _ = ixp.gather(g, inv)  # rows no index reaches read as zero
-            return grad, None, None, None
+            return grad, None, None, None, None
         grad = _zeros(ctx.src_shape, g.dtype, g.device)
-        if ctx.injective:
+        if proven:
             ixp.scatter(grad, idx, g)  # one term per target: no atomics
         else:
             _scatter_add_into(grad, idx, g)
-        return grad, None, None, None
+        return grad, None, None, None, None
 
 
 class ScatterFn(torch.autograd.Function):
@@ -145,9 +156,13 @@ class GatherSegmentsFn(torch.autograd.Function):
         return grad, None, None, None, None
 
 
-def gather(src, idx, injective=False, inverse=None):
-    """inverse: ``invert(idx, src.shape[0])`` for an injective idx (cache it when idx is fixed)."""
-    return GatherFn.apply(src, idx, injective, inverse)[0]
+def gather(src, idx, injective=False, inverse=None, proof=None):
+    """Differentiable gather. ``injective=True`` or ``inverse`` (``invert(idx,
+    src.shape[0])``) ask for the atomic-free adjoint, which is used only when Inj of
+    idx on [0, src.shape[0]) holds; ``proof`` is the Verdict of
+    ``check_inj(idx, 0, src.shape[0] - 1)`` when the caller already ran it (cache it
+    with the inverse when idx is fixed), else the forward pass runs that check."""
+    return GatherFn.apply(src, idx, injective, inverse, proof)[0]
 
 
 def scatter(dst, idx, vals):

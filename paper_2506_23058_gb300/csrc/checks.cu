@@ -235,6 +235,11 @@ __global__ void mono_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
 constexpr int BK_TILE = 8192;
 constexpr int BK_THREADS = 256;
 constexpr unsigned BK_MAX = 4096;
+// Header slots of the bucketed path: bucket count, pool entries per bucket, log2 of
+// the bucket width, and the launch shape the setup kernel chose for the span it
+// found (both shapes run the same two passes).
+constexpr int BK_NB = 0, BK_CAP = 1, BK_LW = 2, BK_MODE = 3;
+constexpr unsigned long long BK_STAGED = 1, BK_WIDE = 2;
 
 // Min/max of the in-codomain values (needed when Rcd is unbounded). The bounds
 // come clamped to T, so every compare is in T; a vector that lies wholly inside
@@ -407,17 +412,27 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) mark_kernel(const T *__rest
     }
 }
 
-// Smallest index whose value (in [mlo, mhi]) has its bit in the repeat bitmap.
-// Runs only when a repeat was seen. With bucket_mask (bucketed path), only values
-// whose bucket saw a repeat look the bitmap up, so the pass streams at HBM speed.
+// Witness passes (run only when a repeat was seen). Both walk X in tiles of
+// WT_VECS 16-byte vectors per block iteration, each block taking tiles in
+// increasing order (grid stride), and stop at the first tile that starts past the
+// best position found so far by any block: a skipped tile holds only larger
+// positions, so the result is exact, and on a violating input the passes read X
+// only up to about the witness instead of to the end.
+constexpr int WT_PER = 4;                          // vectors per thread per tile
+constexpr int WT_VECS = STREAM_THREADS * WT_PER;  // vectors per tile
+
+// Smallest index whose value (in [mlo, mhi]) has its bit in the repeat bitmap. With
+// bucket_mask (bucketed path), only values whose bucket saw a repeat look the
+// bitmap up.
 template <typename T>
 __global__ void __launch_bounds__(STREAM_THREADS, 4) first_dup_kernel(const T *__restrict__ x, int64_t n, int64_t mlo,
                                                                       int64_t mhi, Hdr *h,
                                                                       const unsigned *__restrict__ dup,
                                                                       const unsigned *__restrict__ bucket_mask,
-                                                                      unsigned lw, unsigned long long *slot) {
+                                                                      unsigned long long *slot) {
     IXP_KERNEL_ENTRY();
     if (h->status || !h->flag) return;
+    const unsigned lw = bucket_mask ? (unsigned)h->spare[BK_LW] : 0u;
     __shared__ unsigned s_mask[BK_MAX / 32];
     __shared__ unsigned s_bfirst, s_blast;
     const unsigned long long base = h->base, span = h->span;
@@ -447,8 +462,6 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) first_dup_kernel(const T *_
     constexpr int V = Vec<T>::N;
     Split<T> s(x, n);
     int64_t best = INT64_MAX;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     auto one = [&](int64_t i, T xv) {
         const int64_t xi = (int64_t)xv;
         const unsigned long long rel = (unsigned long long)xi - base;
@@ -459,31 +472,36 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) first_dup_kernel(const T *_
         }
         if (__ldg(dup + (rel >> 5)) & (1u << (rel & 31))) best = i < best ? i : best;
     };
-    for (int64_t i = tid; i < s.head; i += stride) one(i, x[i]);
-    for (int64_t i = s.tail0 + tid; i < n; i += stride) one(i, x[i]);
+    if (blockIdx.x == 0) {
+        for (int64_t i = threadIdx.x; i < s.head; i += blockDim.x) one(i, x[i]);
+        for (int64_t i = s.tail0 + threadIdx.x; i < n; i += blockDim.x) one(i, x[i]);
+        if (best != INT64_MAX) atomic_max_u64(slot, enc_first(best));
+    }
     const VT *xv = reinterpret_cast<const VT *>(x + s.head);
-    int64_t v = tid;
-    for (; v + 3 * stride < s.nvec; v += 4 * stride) {
-        VT a[4];
+    const int64_t ntiles = (s.nvec + WT_VECS - 1) / WT_VECS;
+    for (int64_t c = blockIdx.x; c < ntiles; c += gridDim.x) {
+        const unsigned long long cur = ld_relaxed_u64(slot);
+        if (cur && s.head + c * WT_VECS * V > dec_first(cur)) break;
+        VT a[WT_PER];
 #pragma unroll
-        for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
+        for (int u = 0; u < WT_PER; u++) {
+            const int64_t v = c * WT_VECS + u * STREAM_THREADS + threadIdx.x;
+            if (v < s.nvec) a[u] = ldv(xv + v);
+        }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < WT_PER; u++) {
+            const int64_t v = c * WT_VECS + u * STREAM_THREADS + threadIdx.x;
+            if (v >= s.nvec) continue;
             int64_t e[V];
             unpack(a[u], e);
 #pragma unroll
-            for (int k = 0; k < V; k++) one(s.head + (v + u * stride) * V + k, (T)e[k]);
+            for (int k = 0; k < V; k++) one(s.head + v * V + k, (T)e[k]);
+        }
+        if (best != INT64_MAX) {
+            atomic_max_u64(slot, enc_first(best));
+            best = INT64_MAX;
         }
     }
-    for (; v < s.nvec; v += stride) {
-        int64_t e[V];
-        unpack(ldv(xv + v), e);
-#pragma unroll
-        for (int k = 0; k < V; k++) one(s.head + v * V + k, (T)e[k]);
-    }
-    __shared__ unsigned long long sm[STREAM_THREADS / 32];
-    unsigned long long r = block_max_u64(best == INT64_MAX ? 0ull : enc_first(best), sm);
-    if (threadIdx.x == 0) atomic_max_u64(slot, r);
 }
 
 // Partner of the first repeated index i*: the smallest j > i* with x[j] = x[i*].
@@ -501,37 +519,40 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) partner_kernel(const T *__r
     const int64_t m = n - start;
     Split<T> s(xs, m);
     int64_t best = INT64_MAX;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < s.head; i += stride)
-        if (xs[i] == v0) best = i < best ? i : best;
-    for (int64_t i = s.tail0 + tid; i < m; i += stride)
-        if (xs[i] == v0) best = i < best ? i : best;
+    if (blockIdx.x == 0) {
+        for (int64_t i = threadIdx.x; i < s.head; i += blockDim.x)
+            if (xs[i] == v0) best = i < best ? i : best;
+        for (int64_t i = s.tail0 + threadIdx.x; i < m; i += blockDim.x)
+            if (xs[i] == v0) best = i < best ? i : best;
+        if (best != INT64_MAX) atomic_max_u64(&h->k_aux, enc_first(start + best));
+        best = INT64_MAX;
+    }
     const VT *xv = reinterpret_cast<const VT *>(xs + s.head);
-    int64_t v = tid;
-    for (; v + 3 * stride < s.nvec; v += 4 * stride) {
-        VT a[4];
+    const int64_t ntiles = (s.nvec + WT_VECS - 1) / WT_VECS;
+    for (int64_t c = blockIdx.x; c < ntiles; c += gridDim.x) {
+        const unsigned long long cur = ld_relaxed_u64(&h->k_aux);
+        if (cur && start + s.head + c * WT_VECS * V > dec_first(cur)) break;
+        VT a[WT_PER];
 #pragma unroll
-        for (int u = 0; u < 4; u++) a[u] = ldv(xv + v + u * stride);
+        for (int u = 0; u < WT_PER; u++) {
+            const int64_t v = c * WT_VECS + u * STREAM_THREADS + threadIdx.x;
+            if (v < s.nvec) a[u] = ldv(xv + v);
+        }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < WT_PER; u++) {
+            const int64_t v = c * WT_VECS + u * STREAM_THREADS + threadIdx.x;
+            if (v >= s.nvec) continue;
             int64_t e[V];
             unpack(a[u], e);
 #pragma unroll
             for (int k = V - 1; k >= 0; k--)
-                if ((T)e[k] == v0) best = min(best, s.head + (v + u * stride) * V + k);
+                if ((T)e[k] == v0) best = min(best, s.head + v * V + k);
+        }
+        if (best != INT64_MAX) {
+            atomic_max_u64(&h->k_aux, enc_first(start + best));
+            best = INT64_MAX;
         }
     }
-    for (; v < s.nvec; v += stride) {
-        int64_t e[V];
-        unpack(ldv(xv + v), e);
-#pragma unroll
-        for (int k = V - 1; k >= 0; k--)
-            if ((T)e[k] == v0) best = min(best, s.head + v * V + k);
-    }
-    __shared__ unsigned long long sm[STREAM_THREADS / 32];
-    unsigned long long r = block_max_u64(best == INT64_MAX ? 0ull : enc_first(start + best), sm);
-    if (threadIdx.x == 0) atomic_max_u64(&h->k_aux, r);
 }
 
 template <typename T>
@@ -631,9 +652,29 @@ struct BucketCfg {
     unsigned long long pool;    // pool capacity in entries
 };
 
+// Spans up to 2^28 take at most 512 buckets with a width picked on the device from
+// the span found ("staged" shape); wider spans, up to the host's bucket shape, the
+// host's configuration with up to BK_MAX buckets ("wide" shape).
+constexpr unsigned long long ST_MAX_SPAN = 1ull << 28;
+constexpr unsigned ST_LOGB = 9;  // at most 512 buckets: about 16 elements per bucket per tile
+constexpr unsigned ST_LW_MIN = 10;
+
+__host__ __device__ inline unsigned ceil_log2_u64(unsigned long long v) {
+    unsigned l = 0;
+    while (l < 64 && (1ull << l) < v) l++;
+    return l;
+}
+
+// Bucket width of the staged path: the smallest power of two that gives at most
+// 2^logb buckets (and at least 2^ST_LW_MIN values per bucket).
+__host__ __device__ inline unsigned staged_lw(unsigned long long span, unsigned logb) {
+    const unsigned l = ceil_log2_u64(span);
+    return l > logb + ST_LW_MIN ? l - logb : ST_LW_MIN;
+}
+
 __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, unsigned long long cap_bits,
-                                    BucketCfg cfg, unsigned *cursors, unsigned *marks, unsigned *dup,
-                                    unsigned *bucket_mask) {
+                                    BucketCfg cfg, unsigned staged_logb, unsigned *cursors, unsigned *marks,
+                                    unsigned *dup, unsigned *bucket_mask) {
     IXP_KERNEL_ENTRY();
     unsigned long long base = 0, span = 0;
     bool too_big = false;
@@ -650,8 +691,10 @@ __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, u
             span = d + 1ull;
         }
     }
-    const unsigned long long nb = too_big ? 0ull : (span + (1ull << cfg.lw) - 1ull) >> cfg.lw;
-    if (too_big || nb > cfg.bmax) {
+    const bool staged = !too_big && span <= ST_MAX_SPAN;
+    const unsigned lw = staged ? staged_lw(span, staged_logb) : cfg.lw;
+    const unsigned long long nb = too_big ? 0ull : (span + (1ull << lw) - 1ull) >> lw;
+    if (too_big || (!staged && nb > cfg.bmax)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, IXP_E_SPAN);
         return;
     }
@@ -659,8 +702,10 @@ __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, u
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         h->base = base;
         h->span = span;
-        h->spare[0] = nb;
-        h->spare[1] = cap;
+        h->spare[BK_NB] = nb;
+        h->spare[BK_CAP] = cap;
+        h->spare[BK_LW] = lw;
+        h->spare[BK_MODE] = staged ? BK_STAGED : BK_WIDE;
     }
     const unsigned long long words = (span + 31) / 32;
     const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
@@ -748,11 +793,11 @@ __device__ __forceinline__ void bs_classify(const T (&e)[BS_PER / Vec<T>::N][Vec
 
 template <typename T, bool BIJ, bool PAD>
 __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
-    const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, Hdr *h, BucketCfg cfg,
+    const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, Hdr *h, BucketCfg cfg, unsigned long long mode,
     unsigned *__restrict__ cursors, unsigned *__restrict__ pool, unsigned *__restrict__ marks,
     unsigned *__restrict__ dup, unsigned *__restrict__ bucket_mask, int vec_ok) {
     IXP_KERNEL_ENTRY();
-    if (h->status) return;
+    if (h->status || h->spare[BK_MODE] != mode) return;
     constexpr int V = Vec<T>::N;
     constexpr int NV = BS_PER / V;  // 16-byte vectors per thread per tile
     constexpr unsigned SENT = ~0u;  // pad entry (pass 2 skips it)
@@ -767,9 +812,9 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
     __shared__ unsigned s_wsum[BS_THREADS / 32];
     __shared__ unsigned s_total;
     const unsigned long long base = h->base, span = h->span;
-    const unsigned nb = (unsigned)h->spare[0];
-    const unsigned long long cap = h->spare[1];
-    const unsigned lw = cfg.lw;
+    const unsigned nb = (unsigned)h->spare[BK_NB];
+    const unsigned long long cap = h->spare[BK_CAP];
+    const unsigned lw = (unsigned)h->spare[BK_LW];
     const unsigned wmask = (1u << lw) - 1u;
     // 32-bit relative values are exact when [base, base + span) lies in the int32 range
     const bool r32 = sizeof(T) == 4 && span >= 1 && span <= (1ull << 32) && (int64_t)base >= (int64_t)INT32_MIN &&
@@ -926,8 +971,10 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
     }
 }
 
-// Pass 2: one block per bucket, a W-bit bitmap in shared memory.
-__global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, BucketCfg cfg,
+// Pass 2: one block per bucket, a W-bit bitmap in shared memory. Launched once per
+// pass-1 path (its grid and shared memory sized for that path's buckets); only the
+// launch whose path the setup kernel chose does the work.
+__global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, unsigned long long mode,
                                                                   const unsigned *__restrict__ cursors,
                                                                   const unsigned *__restrict__ pool,
                                                                   const unsigned *__restrict__ marks,
@@ -935,11 +982,11 @@ __global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, Bucket
                                                                   unsigned *__restrict__ bucket_mask, int bij) {
     IXP_KERNEL_ENTRY();
     extern __shared__ unsigned s_bm[];
-    const unsigned nb = (unsigned)h->spare[0];
+    const unsigned nb = (unsigned)h->spare[BK_NB];
     const unsigned b = blockIdx.x;
-    if (h->status || b >= nb) return;
-    const unsigned long long cap = h->spare[1], span = h->span;
-    const unsigned lw = cfg.lw;
+    if (h->status || h->spare[BK_MODE] != mode || b >= nb) return;
+    const unsigned long long cap = h->spare[BK_CAP], span = h->span;
+    const unsigned lw = (unsigned)h->spare[BK_LW];
     const unsigned words = (1u << lw) / 32;
     const unsigned long long lo_rel = (unsigned long long)b << lw;
     const unsigned long long range = min(1ull << lw, span - lo_rel);  // values this bucket covers
@@ -1093,6 +1140,7 @@ namespace ixp {
 constexpr int64_t BK_MIN_N = 1 << 18;
 constexpr unsigned long long BK_MIN_SPAN = 1ull << 21;
 
+// Pool entries of the wide path (per-bucket regions, 32-bit positions).
 static unsigned long long bk_pool_entries(int64_t n) {
     return ((unsigned long long)n + (unsigned long long)n / 4 + 4ull * BK_MAX + 3ull) & ~3ull;
 }
@@ -1144,30 +1192,49 @@ static bool bucket_config(unsigned long long span, unsigned long long pool, Buck
     return true;
 }
 
+// Pass 1 with the launch shape of one path: `shape` gives the bucket count the
+// shared memory is laid out for; the bucket width comes from the setup kernel.
 template <typename T, bool BIJ>
-static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int fixed, int64_t flo, int64_t fhi,
-                           const BitmapWs &w, const BucketCfg &cfg, cudaStream_t st) {
-    const int sgrid = num_sms() * 4;
-    bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, w.cursors, w.bm, w.dup,
-                                                          w.bmask);
+static void launch_pass1(const T *x, int64_t n, int64_t rlo, int64_t rhi, const BitmapWs &w, const BucketCfg &shape,
+                         unsigned long long mode, int vec, cudaStream_t st) {
     const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
-    const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 2));  // pass-1 grid
-    const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-    if (cfg.bmax <= BS_PAD_MAX && n < (1ll << 31)) {
+    const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 2));
+    if (shape.bmax <= BS_PAD_MAX && n < (1ll << 31)) {
         // runs padded to 16-byte chunks (at least 8 elements per bucket per tile on average)
         cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bs_smem_bytes(BS_PAD_MAX, true));
-        bucket_scatter_kernel<T, BIJ, true><<<g1, BS_THREADS, bs_smem_bytes(cfg.bmax, true), st>>>(
-            x, n, rlo, rhi, w.h, cfg, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
+        bucket_scatter_kernel<T, BIJ, true><<<g1, BS_THREADS, bs_smem_bytes(shape.bmax, true), st>>>(
+            x, n, rlo, rhi, w.h, shape, mode, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
     } else {
         cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bs_smem_bytes(BK_MAX, false));
-        bucket_scatter_kernel<T, BIJ, false><<<g1, BS_THREADS, bs_smem_bytes(cfg.bmax, false), st>>>(
-            x, n, rlo, rhi, w.h, cfg, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
+        bucket_scatter_kernel<T, BIJ, false><<<g1, BS_THREADS, bs_smem_bytes(shape.bmax, false), st>>>(
+            x, n, rlo, rhi, w.h, shape, mode, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
     }
     cudaFuncSetAttribute(bucket_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << 20) / 8);
-    bucket_check_kernel<<<cfg.bmax, BK_THREADS, (1u << cfg.lw) / 8, st>>>(w.h, cfg, w.cursors, w.pool, w.bm, w.dup,
-                                                                         w.bmask, BIJ ? 1 : 0);
+    bucket_check_kernel<<<shape.bmax, BK_THREADS, (1u << shape.lw) / 8, st>>>(w.h, mode, w.cursors, w.pool, w.bm,
+                                                                             w.dup, w.bmask, BIJ ? 1 : 0);
+}
+
+// span_cap: the largest span the setup kernel can find (the fixed range, or the
+// bitmap capacity when the range comes from the data). Spans up to 2^28 get at most
+// 512 buckets with a width picked on the device from the span found; when span_cap
+// is wider, the launch shape of the host's bucket configuration is launched too
+// and runs only if the span found is above 2^28.
+template <typename T, bool BIJ>
+static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int fixed, int64_t flo, int64_t fhi,
+                           unsigned long long span_cap, const BitmapWs &w, const BucketCfg &cfg, cudaStream_t st) {
+    const int sgrid = num_sms() * 4;
+    bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, ST_LOGB, w.cursors, w.bm,
+                                                          w.dup, w.bmask);
+    const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+    // staged shape: room for 2^ST_LOGB buckets (a narrower span found on the device
+    // gives narrower buckets, never more of them), and the widest bucket the span cap
+    // allows for the shared bitmap of pass 2
+    const unsigned long long scap = std::min<unsigned long long>(span_cap, ST_MAX_SPAN);
+    const BucketCfg sshape{staged_lw(scap, ST_LOGB), 1u << ST_LOGB, cfg.pool};
+    launch_pass1<T, BIJ>(x, n, rlo, rhi, w, sshape, BK_STAGED, vec, st);
+    if (span_cap > ST_MAX_SPAN) launch_pass1<T, BIJ>(x, n, rlo, rhi, w, cfg, BK_WIDE, vec, st);
 }
 
 template <typename T>
@@ -1182,14 +1249,13 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
     if (bij) {
         const unsigned long long isize = (unsigned long long)ihi - (unsigned long long)ilo + 1ull;
         if (w.buckets && isize >= BK_MIN_SPAN && bucket_config(isize, bk_pool_entries(n), &cfg)) {
-            launch_buckets<T, true>(x, n, rlo, rhi, 1, ilo, ihi, w, cfg, st);
-            first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, w.bmask, cfg.lw,
-                                                                 &h->k_first2);
+            launch_buckets<T, true>(x, n, rlo, rhi, 1, ilo, ihi, isize, w, cfg, st);
+            first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, w.bmask, &h->k_first2);
         } else {
             bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, 1, ilo, ihi, cap, bm, dup);
             if (n > 0) {
                 mark_kernel<T, true><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, ilo, ihi, h, bm, dup);
-                first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, nullptr, 0, &h->k_first2);
+                first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, nullptr, &h->k_first2);
             }
             missing_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, bm);
         }
@@ -1210,14 +1276,14 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
     const unsigned long long span_cap = fixed ? rspan : cap;
     const bool bk = w.buckets && span_cap >= BK_MIN_SPAN && bucket_config(span_cap, bk_pool_entries(n), &cfg);
     if (bk) {
-        launch_buckets<T, false>(x, n, rlo, rhi, fixed ? 1 : 0, rlo, rhi, w, cfg, st);
+        launch_buckets<T, false>(x, n, rlo, rhi, fixed ? 1 : 0, rlo, rhi, span_cap, w, cfg, st);
     } else {
         bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, fixed ? 1 : 0, rlo, rhi, cap, bm, dup);
         if (n > 0) mark_kernel<T, false><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, rlo, rhi, h, bm, dup);
     }
     if (n > 0) {
         first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, dup, bk ? w.bmask : nullptr,
-                                                             bk ? cfg.lw : 0, &h->k_first);
+                                                             &h->k_first);
         partner_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, h, &h->k_first);
     }
     inj_finalize<T><<<1, 1, 0, st>>>(x, h, out);

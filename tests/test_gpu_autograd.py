@@ -63,6 +63,42 @@ def test_gather_backward_through_the_inverse(ag, dev):
     assert np.array_equal(s.grad.cpu().numpy(), oracle.scatter(np.zeros_like(src), idx, w))
 
 
+@pytest.mark.parametrize("how", ["injective", "inverse"])
+def test_gather_claimed_injective_with_duplicates_keeps_every_term(ag, dev, how):
+    # idx repeats values although the caller asks for the atomic-free adjoint: the
+    # forward pass's Inj check fails, so the backward sums every term per target
+    import paper_2506_23058_gb300 as m
+    n, cols = 30_011, 8
+    idx = synth.permutation(n, 61).astype(np.int32)
+    idx[100:400] = idx[5]  # 300 more reads of one row
+    idx[7] = idx[9000]
+    src = synth.payload_f32(n, 62, cols=cols)
+    w = synth.payload_f32(n, 63, cols=cols)
+    s = T(src, dev, True)
+    ti = T(idx, dev)
+    kw = {"injective": True} if how == "injective" else {"inverse": m.invert(ti, n)}
+    y = ag.gather(s, ti, **kw)
+    (y * T(w, dev)).sum().backward()
+    ref = oracle.scatter_add_f64(n, idx, w)
+    absum = oracle.scatter_add_f64(n, idx, np.abs(w))
+    assert close_to_sum(s.grad.cpu().numpy(), ref, absum)
+
+
+def test_gather_with_a_failed_proof_keeps_every_term(ag, dev):
+    import paper_2506_23058_gb300 as m
+    n, cols = 4099, 4
+    idx = (np.arange(n) // 2).astype(np.int64)  # every row read twice
+    src = synth.payload_f32(n, 64, cols=cols)
+    w = synth.payload_f32(n, 65, cols=cols)
+    ti = T(idx, dev)
+    proof = m.check_inj(ti, 0, n - 1)
+    assert proof.get()["ok"] == 0
+    s = T(src, dev, True)
+    (ag.gather(s, ti, injective=True, proof=proof) * T(w, dev)).sum().backward()
+    ref = oracle.scatter_add_f64(n, idx, w)
+    assert close_to_sum(s.grad.cpu().numpy(), ref, oracle.scatter_add_f64(n, idx, np.abs(w)))
+
+
 @pytest.mark.parametrize("it", [np.int32, np.int64])
 def test_gather_zipf_backward_matches_fp64_reference(ag, dev, it):
     n, m, cols = 200_000, 4096, 8

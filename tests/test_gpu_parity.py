@@ -217,6 +217,61 @@ def test_inj_bucketed_skewed_overflow(ixp, dev, dtype):
     same(ixp.check_bij(T(a, dev), I64MIN, I64MAX, 0, img_hi), oracle.check_bij(a, I64MIN, I64MAX, 0, img_hi), "bij-gap")
 
 
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_inj_bij_bucketed_unaligned_sorted_and_witnesses(ixp, dev, dtype):
+    # bucketed path on an unaligned view (scalar loads), on sorted values (each tile
+    # lands in one or two buckets, so runs are thousands long), and repeats whose
+    # first occurrence sits at either end of the array with the partner far away
+    n = 1_500_007
+    perm = synth.permutation(n, 77, dtype)
+    buf = np.concatenate([np.zeros(1, dtype), perm])
+    tv = T(buf, dev)[1:]
+    for lo, hi in [(I64MIN, I64MAX), (0, n - 1)]:
+        same(ixp.check_inj(tv, lo, hi), oracle.check_inj(perm, lo, hi), ("unaligned", lo))
+    same(ixp.check_bij(tv, I64MIN, I64MAX, 0, n - 1), oracle.check_bij(perm, I64MIN, I64MAX, 0, n - 1), "unaligned-bij")
+    d = perm.copy()
+    d[n - 1] = d[n - 2]
+    buf[1:] = d
+    tv = T(buf, dev)[1:]
+    same(ixp.check_inj(tv), oracle.check_inj(d), "unaligned-dup")
+    iota = np.arange(n, dtype=dtype) * 2 + 11
+    same(ixp.check_inj(T(iota, dev)), oracle.check_inj(iota), "sorted")
+    for p, q in [(0, n - 1), (n - 3, n - 1), (0, 1), (700_000, 700_001)]:
+        a = iota.copy()
+        a[q] = a[p]
+        same(ixp.check_inj(T(a, dev)), oracle.check_inj(a), ("sorted-dup", p, q))
+        b = perm.copy()
+        b[q] = b[p]
+        same(ixp.check_inj(T(b, dev), 0, n - 1), oracle.check_inj(b, 0, n - 1), ("perm-dup", p, q))
+        same(ixp.check_bij(T(b, dev), I64MIN, I64MAX, 0, n - 1), oracle.check_bij(b, I64MIN, I64MAX, 0, n - 1),
+             ("perm-dup-bij", p, q))
+    # several repeated values: the witness is the smallest first occurrence
+    c = perm.copy()
+    c[1_400_000] = c[5]
+    c[900_000] = c[200_000]
+    c[1_000_000] = c[1_200_000]
+    same(ixp.check_inj(T(c, dev)), oracle.check_inj(c), "several")
+
+
+def test_inj_bij_both_bucket_paths_launched(ixp, dev):
+    # Rcd unbounded and n > 2^26: the bitmap capacity (4n + 4096 bits) exceeds 2^28,
+    # so both pass-1 paths are launched and the span found on the device (n) picks
+    # the staged one; a planted value far out widens the span past 2^28 and picks the
+    # wide one
+    n = (1 << 26) + 5
+    perm = synth.permutation(n, 91, np.int32)
+    t = T(perm, dev)
+    same(ixp.check_inj(t), oracle.check_inj(perm), "staged")
+    same(ixp.check_bij(t, I64MIN, I64MAX, 0, n - 1), oracle.check_bij(perm, I64MIN, I64MAX, 0, n - 1), "staged-bij")
+    d, p, q = synth.plant_duplicate(perm, 92)
+    same(ixp.check_inj(T(d, dev)), oracle.check_inj(d), ("staged-dup", p, q))
+    w = perm.copy()
+    w[12345] = 3 * n + 7  # span 3n + 8 > 2^28, below the 4n + 4096 capacity
+    same(ixp.check_inj(T(w, dev)), oracle.check_inj(w), "wide")
+    w[777] = w[12345]
+    same(ixp.check_inj(T(w, dev)), oracle.check_inj(w), "wide-dup")
+
+
 # ---- per-segment Inj / Bij
 
 def mixed_segments(rng, m, small_max=300, big=(), empty_p=0.15):
