@@ -45,19 +45,26 @@ def peaks():
 
 # ------------------------------------------------------------------ workload
 
+def inj_bitmap_bytes(span):
+    """The bitmap terms of an Inj/Bij check over a value span: span / 8 bytes cleared
+    and span / 8 bytes counted (read) once."""
+    return 2 * ((span + 7) // 8)
+
+
 def make_ops(n32, n64, small=False):
     """The op list of one step: (name, kind, input names, algorithmic bytes)."""
     ops = []
     for tag, n, es in (("i32", n32, 4), ("i64", n64, 8)):
+        ij = es * n + inj_bitmap_bytes(n)  # the value span of these arrays is n
         ops += [
             (f"range_perm_{tag}", "range", (f"perm_{tag}",), es * n),
             (f"range_oor_{tag}", "range", (f"oor_{tag}",), es * n),
             (f"mono_le_{tag}", "mono", (f"mono_{tag}",), es * n),
             (f"mono_brk_{tag}", "mono", (f"brk_{tag}",), es * n),
-            (f"inj_perm_{tag}", "inj_fixed", (f"perm_{tag}",), es * n),
-            (f"inj_dup_{tag}", "inj_inf", (f"dup_{tag}",), es * n),
-            (f"bij_perm_{tag}", "bij", (f"perm_{tag}",), es * n),
-            (f"bij_dup_{tag}", "bij", (f"dup_{tag}",), es * n),
+            (f"inj_perm_{tag}", "inj_fixed", (f"perm_{tag}",), ij),
+            (f"inj_dup_{tag}", "inj_inf", (f"dup_{tag}",), ij),
+            (f"bij_perm_{tag}", "bij", (f"perm_{tag}",), ij),
+            (f"bij_dup_{tag}", "bij", (f"dup_{tag}",), ij),
         ]
     n = n32
     nr = n32 // 4  # rows of the [n/4 x 8] float32 payload moved by scatter / gather
@@ -107,6 +114,31 @@ def op_elements(name, n32, n64, shape_total):
     if name == "flags_from_shape":
         return shape_total
     return n32
+
+
+FAMILIES = {"inj_bij": ("inj_", "bij_"), "range_mono": ("range_", "mono_")}
+
+
+def roofline_of(per_op, peak, peak_src, traffic_file=None):
+    """The roofline object of the op with the largest time in this run, and one entry
+    per op family (the ops' summed algorithmic bytes over their summed time).
+    traffic = DRAM bytes per launch from the committed ncu summary when it holds
+    that op's kernels as they are now, else None."""
+    dom = max(per_op, key=lambda k: per_op[k]["ms"])
+    traffic = None
+    tf = traffic_file or os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        traffic = json.load(open(tf)).get("ops", {}).get(dom, {}).get("bytes")
+    fam = {}
+    for f, prefixes in FAMILIES.items():
+        ks = [k for k in per_op if k.startswith(prefixes)]
+        if ks:
+            ms = sum(per_op[k]["ms"] for k in ks)
+            gb = sum(per_op[k]["alg_bytes"] for k in ks) / (ms / 1e3) / 1e9
+            fam[f] = {"ops": len(ks), "ms": round(ms, 4), "gbs": round(gb, 1), "frac": round(gb / peak, 4)}
+    return {"bound": "hbm", "op": dom, "kernel": OP_KERNELS.get(dom), "achieved": per_op[dom]["gbs"],
+            "peak": peak, "unit": "GB/s", "frac": round(per_op[dom]["gbs"] / peak, 4), "traffic": traffic,
+            "peak_source": peak_src, "families": fam}
 
 
 def op_record(ms, nbytes, elems, peak):
@@ -523,19 +555,7 @@ def main():
         ts = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
         m = sum(ts) / len(ts)
         per_op[name] = op_record(m, nbytes, op_elements(name, n32, n64, R.shape_total), peak)
-    # the op of the kernel with the largest share of the profiled launch list (the
-    # committed profile names it), else the op with the largest time
-    dom = max(per_op, key=lambda k: per_op[k]["ms"])
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tf):
-        prof = json.load(open(tf))
-        if prof.get("dominant_op") in per_op:
-            dom = prof["dominant_op"]
-        traffic = prof.get("ops", {}).get(dom, {}).get("bytes")
-    roofline = {"bound": "hbm", "op": dom, "kernel": OP_KERNELS.get(dom), "achieved": per_op[dom]["gbs"],
-                "peak": peak, "unit": "GB/s", "frac": round(per_op[dom]["gbs"] / peak, 4), "traffic": traffic,
-                "peak_source": peak_src}
+    roofline = roofline_of(per_op, peak, peak_src)
     ceilings = None
     if not args.no_ceilings:
         ceilings = measure_ceilings(ixp, dev)

@@ -117,7 +117,8 @@ enum {
     IXP_OP_GATHER_SEGMENTS = 10, /* n = output elements */
     IXP_OP_FILTPART_CLASSES = 11, /* itype = v (classes), extra = nseg (0 when flat) */
     IXP_OP_INJ_HIST = 12,         /* extra = m (bins) */
-    IXP_OP_SMALLEST_PAIRS = 13    /* extra = n_verts */
+    IXP_OP_SMALLEST_PAIRS = 13,   /* extra = n_verts */
+    IXP_OP_FILTPART_VALUES = 14   /* itype = v with a class array, 0 with a predicate; extra = nseg */
 };
 
 /* Bytes of workspace that call `op` needs for n elements of type itype and the
@@ -220,6 +221,24 @@ int ixp_check_filtpart_classes(const void *z, int ztype, int64_t n, const void *
                                const uint8_t *cls, int32_t v, ixp_segs segs, ixp_verdict *d_verdict, void *ws,
                                size_t ws_bytes, ixp_stream stream);
 
+/* FiltPart, value form  [Sec. 2.3, FiltPart Y X (e_k, p^f, p^p_1..v)]: Y (ny rows of
+ * row_bytes bytes, device) equals X (n rows, device) filtered by `filt` and
+ * partitioned stably per segment, bitwise, and has length N (the number of kept
+ * rows). The order is that of ixp_check_filtpart (cls == NULL, v = 2: trues of
+ * `part` first) or of ixp_check_filtpart_classes (cls: uint8_t[n], 1 <= v <= 256,
+ * class min(cls[i], v - 1)). Verdict: ok when Y matches; otherwise kind
+ * IXP_V_WRONG_DEST with index = the first position of Y that differs and value =
+ * the index in X of the row that belongs there, or, when ny != N, index = -1 and
+ * value = ny; aux0 = N. row_bytes: a positive multiple of 4; X and Y 4-byte
+ * aligned; n < 2^32. keys may be NULL when the predicates are TRUE or FLAGS; with
+ * n = 0 every array may be NULL, and v != 2 then selects the class form.
+ * Workspace: ixp_workspace_size(IXP_OP_FILTPART_VALUES, cls ? v : 0, n, nseg)
+ * bytes, 256-byte aligned. */
+int ixp_check_filtpart_values(const void *y, int64_t ny, const void *x, int64_t n, int32_t row_bytes,
+                              const void *keys, int ktype, ixp_pred filt, ixp_pred part, const uint8_t *cls,
+                              int32_t v, ixp_segs segs, ixp_verdict *d_verdict, void *ws, size_t ws_bytes,
+                              ixp_stream stream);
+
 /* FiltPart with v classes, index form  [Sec. 2.3; the partition3 / filter programs
  * of the evaluation]: out_idx[i] = the destination of element i in the filtered,
  * class-partitioned order (per segment, kept elements by class min(cls[i], v - 1),
@@ -268,8 +287,13 @@ int ixp_scatter(void *dst, int64_t dst_len, const void *idx, int itype, const vo
 
 /* Additive scatter of float32 rows accumulated in float64: acc[idx[i]] += vals[i]
  * for in-bounds idx[i], acc a device double[dst_len * row_elems] the caller zeroes
- * (or pre-loads). Same-target updates inside a warp are combined before the
- * atomic. */
+ * (or pre-loads). Each block first sums its rows into a shared-memory cache of
+ * target rows held as exact 64-bit fixed-point values (native integer atomics,
+ * one float64 rounding per cached row when the block ends); rows that miss the
+ * cache, and values the fixed-point scale cannot hold exactly, are added with
+ * float64 atomics. Every addition into acc rounds once in float64 (a cached
+ * partial sum is exact before its rounding); the order of the additions is not
+ * fixed, so the low bits can differ from run to run. */
 int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const void *idx, int itype, const float *vals,
                                int64_t n, int32_t row_elems, ixp_stream stream);
 
@@ -456,6 +480,9 @@ int ixp_batch_run(const int64_t *shape, int64_t m, const int32_t *keys, ixp_pred
  *  - The first call on each device looks up the array's device address (with that
  *    device current) and remembers it; make that first call before any stream
  *    capture. A failed lookup returns IXP_E_CUDA.
+ *  - The array used is the current device's, so `stream` must belong to the
+ *    current device (or be a default-stream handle); a stream of another device
+ *    is rejected with IXP_E_INVAL.
  *  - Every call on a device shares the one array. Calls whose work overlaps on the
  *    GPU (different streams, or concurrent graph branches) race on it and give
  *    wrong results; order them on one stream or with events. */

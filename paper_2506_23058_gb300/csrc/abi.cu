@@ -10,6 +10,7 @@ size_t bk_prefix_bytes(int64_t n);                       // checks.cu
 size_t seg_ws_bytes(int64_t nseg);                       // segmented.cu
 size_t gather_segments_ws_bytes(int64_t n_out);          // scatter.cu
 size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg);  // classes.cu
+size_t filtpart_values_ws_bytes(int v, int64_t n, int64_t nseg);   // scan.cu
 size_t inj_hist_ws_bytes(int64_t m);                                 // hist.cu
 size_t smallest_pairs_ws_bytes(int itype, int64_t n, int64_t n_verts);  // hist.cu
 
@@ -65,6 +66,7 @@ extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra
         case IXP_OP_FILTPART_CLASSES: return filtpart_classes_ws_bytes(itype, n, extra);
         case IXP_OP_INJ_HIST: return inj_hist_ws_bytes(extra);
         case IXP_OP_SMALLEST_PAIRS: return smallest_pairs_ws_bytes(itype, n, extra);
+        case IXP_OP_FILTPART_VALUES: return filtpart_values_ws_bytes(itype, n, extra);
         default: return 0;
     }
 }

@@ -3,11 +3,15 @@
 //
 // Range and flat Mono are single streaming passes (4 or 8 bytes per element, HBM
 // bound). Inj and Bij set one bit per in-codomain element in a bitmap over the value
-// span with an L2 atomicOr whose return value flags a collision (rule BijF1 of
-// Sec. 3.2 counts the same way: Inj plus |Img| in-image elements); the bitmap for a
-// 2^28 span is 32 MiB and stays L2 resident. When a collision was seen, two more
-// passes recover the exact witness (smallest repeated index and its partner); they
-// exit at once otherwise.
+// span; a bit found already set is a repeat (rule BijF1 of Sec. 3.2 counts the same
+// way: Inj plus |Img| in-image elements). Small inputs set the bits with L2
+// atomicOr on one global bitmap. Large inputs (n >= 2^18, span >= 2^21) first sort
+// each tile's values by bucket (a range of 2^lw values) into per-bucket pools, then
+// give every bucket one block with its part of the bitmap in shared memory, where
+// the atomicOr's return value flags the repeat. When a repeat was seen, two more
+// passes recover the exact witness (smallest repeated index and its partner),
+// reading X in index order only up to about the witness; they exit at once
+// otherwise.
 #include <algorithm>
 
 #include "common.cuh"

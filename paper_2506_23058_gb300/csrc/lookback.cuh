@@ -1,7 +1,7 @@
 // lookback.cuh - the decoupled look-back of a single-pass tile scan (Merrill &
 // Garland, "Single-pass Parallel Prefix Scan with Decoupled Look-back", 2016):
-// one 16-byte status word per tile, read and written with single 16-byte
-// accesses, and the plain-sum look-back over it. Every wait is bounded by the
+// one 16-byte status word per tile (two flagged 64-bit halves, see below), and
+// the plain-sum look-back over it. Every wait is bounded by the
 // process-wide Wait configuration; a wait that gives up records IXP_E_TIMEOUT.
 #pragma once
 
@@ -18,19 +18,32 @@ struct Wait {
 // testing hook that names a tile that never publishes.
 Wait wait_config();
 
-// One 16-byte status word per tile: {value, flag}, written and read with single
-// 16-byte accesses so that one load returns a consistent pair. flag: 0 empty,
-// 1 aggregate, 2 inclusive prefix; bit 2: the aggregate holds a segment head.
+// One 16-byte status word per tile: a 64-bit value and a flag (0 empty, 1
+// aggregate, 2 inclusive prefix; bit 2: the aggregate holds a segment head). The
+// value is split into two 32-bit halves and each 64-bit half of the word carries
+// the flag in its upper 32 bits. Both halves are written and read as relaxed
+// gpu-scope 64-bit accesses (each single-copy atomic); the PTX memory model does
+// not make the 16-byte pair atomic as a whole, so a load may combine halves from
+// two different writes of the word. Such a mix has two different flags (the word
+// goes 0 -> 1 -> 2, each state written once), and read_status reports it as not
+// ready, so a flagged value is never assembled from two writes.
 struct Lookback {
     ulonglong2 *st;
 };
 
 __device__ __forceinline__ void publish_status(ulonglong2 *p, unsigned long long value, unsigned long long flag) {
-    asm volatile("st.global.cg.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(value), "l"(flag) : "memory");
+    const unsigned long long lo = (value & 0xffffffffull) | (flag << 32);
+    const unsigned long long hi = (value >> 32) | (flag << 32);
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(lo), "l"(hi) : "memory");
 }
+// .x = the value, .y = the flag (0 while the two halves disagree)
 __device__ __forceinline__ ulonglong2 read_status(const ulonglong2 *p) {
+    unsigned long long lo, hi;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(lo), "=l"(hi) : "l"(p) : "memory");
+    const unsigned long long f = lo >> 32;
     ulonglong2 v;
-    asm volatile("ld.global.cg.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
+    v.x = (lo & 0xffffffffull) | (hi << 32);
+    v.y = f == (hi >> 32) ? f : 0ull;
     return v;
 }
 

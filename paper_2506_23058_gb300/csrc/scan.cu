@@ -1486,6 +1486,134 @@ __global__ void __launch_bounds__(TB, 4) filtpart_cmp_kernel(
     if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
 }
 
+// FiltPart value form: for every kept element i with expected destination
+// ref(i) (as in filtpart_cmp_kernel) and ref(i) < ny, compare row X[i] with row
+// Y[ref(i)] word by word; the smallest differing position and its source index are
+// kept packed as (ref << 32) | i (n < 2^32), so one atomic max of the encoding
+// keeps the lexicographically smallest pair.
+template <typename KT, bool SEG>
+__global__ void __launch_bounds__(TB, 4) filtpart_val_kernel(
+    const uint32_t *__restrict__ y, int64_t ny, const uint32_t *__restrict__ x, int row_words, int64_t n,
+    const KT *__restrict__ keys, DPred filt, DPred part, const int64_t *__restrict__ off, int64_t nseg,
+    const unsigned long long *__restrict__ tile_prefix, const unsigned long long *__restrict__ seg_cnt, Hdr *h,
+    int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int TILE = TB * SUB * V;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ int s_rel[SEG ? TILE : 1];
+    __shared__ int64_t s_k0;
+    const int64_t t = blockIdx.x;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned kt[SUB], kk[SUB];
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+        KT kv[V];
+        load_slot<KT, V>(keys, p0, n, vec_ok, kv);
+        kk[u] = pred_mask<KT, V>(filt, kv, p0, n);
+        kt[u] = kk[u] & pred_mask<KT, V>(part, kv, p0, n);
+    }
+    unsigned pre[SUB];
+    tile_counts<V>(kt, kk, pre, s_w);
+    int rel[SUB][V];
+    if (SEG) tile_segments<V>(off, nseg, t0, t1, s_rel, &s_k0, rel);
+    const unsigned long long tp = tile_prefix[t];
+    const int64_t Ttot = (int64_t)(h->total & 0xffffffffull);
+    unsigned long long bad = ~0ull;
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = t0 + (int64_t)((w * SUB + u) * 32 + l) * V;
+#pragma unroll
+        for (int k = 0; k < V; k++) {
+            const int64_t i = p0 + k;
+            if (i >= n || !((kk[u] >> k) & 1u)) continue;
+            const unsigned below = (1u << k) - 1u;
+            const int64_t ct = (int64_t)(tp & 0xffffffffull) + (int64_t)(pre[u] & 0xffffu) + __popc(kt[u] & below);
+            const int64_t ck = (int64_t)(tp >> 32) + (int64_t)(pre[u] >> 16) + __popc(kk[u] & below);
+            const bool c = (kt[u] >> k) & 1u;
+            int64_t Fk = 0, ctk = 0, ckk = 0, tk = Ttot;
+            if (SEG) {
+                const int64_t sk = s_k0 + rel[u][k];
+                const unsigned long long a0 = __ldg(seg_cnt + sk), a1 = __ldg(seg_cnt + sk + 1);
+                ctk = (int64_t)(a0 & 0xffffffffull);
+                ckk = (int64_t)(a0 >> 32);
+                Fk = ckk;
+                tk = (int64_t)(a1 & 0xffffffffull) - ctk;
+            }
+            const int64_t tb = ct - ctk, kb = ck - ckk;  // trues / kept before i in its segment
+            const int64_t ref = c ? Fk + tb : Fk + tk + (kb - tb);
+            if (ref >= ny) continue;
+            bool differ = false;
+            for (int j = 0; j < row_words; j++)
+                differ |= __ldg(x + i * row_words + j) != __ldg(y + ref * row_words + j);
+            if (differ) {
+                const unsigned long long pk = ((unsigned long long)ref << 32) | (unsigned long long)i;
+                bad = pk < bad ? pk : bad;
+            }
+        }
+    }
+    __shared__ unsigned long long sm[TB / 32];
+    const unsigned long long r = block_max_u64(bad == ~0ull ? 0ull : enc_first((int64_t)bad), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+}
+
+// Class form of the value check: the destinations come from the class kernels
+// (dest[i] >= 0 for kept i, -1 for dropped ones); compare as above.
+__global__ void __launch_bounds__(256) filtpart_val_rows_kernel(const uint32_t *__restrict__ y, int64_t ny,
+                                                                const uint32_t *__restrict__ x, int row_words,
+                                                                int64_t n, const int64_t *__restrict__ dest, Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    unsigned long long bad = ~0ull;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ref = __ldg(dest + i);
+        if (ref < 0 || ref >= ny) continue;
+        bool differ = false;
+        for (int j = 0; j < row_words; j++)
+            differ |= __ldg(x + i * row_words + j) != __ldg(y + ref * row_words + j);
+        if (differ) {
+            const unsigned long long pk = ((unsigned long long)ref << 32) | (unsigned long long)i;
+            bad = pk < bad ? pk : bad;
+        }
+    }
+    __shared__ unsigned long long sm[256 / 32];
+    const unsigned long long r = block_max_u64(bad == ~0ull ? 0ull : enc_first((int64_t)bad), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+}
+
+// Verdict of the value form. N = the kept count (the tile totals' upper half, or
+// *kept for the class form); a Y whose length is not N is reported as such
+// (index -1, value = ny); otherwise the smallest differing position of Y (index)
+// and its source element (value).
+__global__ void filtpart_val_finalize(const Hdr *h, const int64_t *kept, int64_t ny, ixp_verdict *out) {
+    IXP_KERNEL_ENTRY();
+    ixp_verdict v;
+    v.status = h->status;
+    v.reserved = 0;
+    const int64_t N = kept ? *kept : (int64_t)(h->total >> 32);
+    v.aux0 = N;
+    v.aux1 = 0;
+    v.ok = 1;
+    v.kind = IXP_V_NONE;
+    v.index = -1;
+    v.value = 0;
+    if (v.status) {
+        v.ok = -1;
+    } else if (ny != N) {
+        v.ok = 0;
+        v.kind = IXP_V_WRONG_DEST;
+        v.value = ny;
+    } else if (h->k_first) {
+        const unsigned long long pk = (unsigned long long)dec_first(h->k_first);
+        v.ok = 0;
+        v.kind = IXP_V_WRONG_DEST;
+        v.index = (int64_t)(pk >> 32);
+        v.value = (int64_t)(pk & 0xffffffffull);
+    }
+    *out = v;
+}
+
 template <typename ZT>
 __global__ void filtpart_finalize(const ZT *z, const Hdr *h, ixp_verdict *out) {
     IXP_KERNEL_ENTRY();
@@ -1746,9 +1874,99 @@ static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, i
     return launch_status();
 }
 
+// Workspace of the value form: the predicate form uses the tiled layout (sized for
+// int64 keys, which have the most tiles); the class form adds the destinations
+// (int64 per element) and the kept count to the class kernels' workspace.
+size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg);  // classes.cu
+size_t filtpart_values_ws_bytes(int v, int64_t n, int64_t nseg) {
+    if (v <= 0) return tiled_ws_bytes(n, 2, nseg);
+    return filtpart_classes_ws_bytes(v, n, nseg) + round256((size_t)(n > 0 ? n : 0) * 8) + 256;
+}
+
+template <typename KT>
+static int run_filtpart_values(const uint32_t *y, int64_t ny, const uint32_t *x, int row_words, int64_t n,
+                               const KT *keys, ixp_pred filt, ixp_pred part, ixp_segs segs, ixp_verdict *out,
+                               void *ws, size_t ws_bytes, cudaStream_t st) {
+    constexpr int V = 16 / sizeof(KT);
+    const bool seg = segs.offsets != nullptr;
+    const int64_t nt = ntiles_for(n, V);
+    TileWs W = tile_ws(ws, nt, seg ? segs.nseg : 0);
+    int rc = check_ws(ws, ws_bytes, W.bytes);
+    if (rc) return rc;
+    const int vec = keys == nullptr || aligned16(keys);
+    rc = run_counts<KT>(keys, n, dpred(filt), dpred(part), segs, W, nt, vec, st);
+    if (rc) return rc;
+    if (nt > 0) {
+        if (seg)
+            filtpart_val_kernel<KT, true><<<(unsigned)nt, TB, 0, st>>>(y, ny, x, row_words, n, keys, dpred(filt),
+                                                                      dpred(part), segs.offsets, segs.nseg,
+                                                                      W.tile_prefix, W.seg_cnt, W.h, vec);
+        else
+            filtpart_val_kernel<KT, false><<<(unsigned)nt, TB, 0, st>>>(y, ny, x, row_words, n, keys, dpred(filt),
+                                                                       dpred(part), nullptr, 0, W.tile_prefix,
+                                                                       nullptr, W.h, vec);
+    }
+    filtpart_val_finalize<<<1, 1, 0, st>>>(W.h, nullptr, ny, out);
+    return launch_status();
+}
+
+static int run_filtpart_values_classes(const uint32_t *y, int64_t ny, const uint32_t *x, int row_words, int64_t n,
+                                       const void *keys, int ktype, ixp_pred filt, const uint8_t *cls, int v,
+                                       ixp_segs segs, ixp_verdict *out, void *ws, size_t ws_bytes, cudaStream_t st) {
+    const size_t cb = filtpart_classes_ws_bytes(v, n, segs.offsets ? segs.nseg : 0);
+    int rc = check_ws(ws, ws_bytes, filtpart_values_ws_bytes(v, n, segs.offsets ? segs.nseg : 0));
+    if (rc) return rc;
+    // layout: the class kernels' workspace | destinations (int64 per element) | kept count
+    int64_t *dest = (int64_t *)((char *)ws + cb);
+    int64_t *kept = (int64_t *)((char *)ws + cb + round256((size_t)(n > 0 ? n : 0) * 8));
+    rc = ixp_filtpart_classes(keys, ktype, n, filt, cls, v, segs, n > 0 ? dest : nullptr, IXP_I64, kept, ws, cb,
+                              (ixp_stream)st);
+    if (rc) return rc;
+    // the class kernels are done with their workspace (same stream): its start holds the header now
+    Hdr *hh = (Hdr *)ws;
+    if (cudaMemsetAsync(hh, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+    if (n > 0) {
+        const int g = stream_grid(n, 1);
+        filtpart_val_rows_kernel<<<g, 256, 0, st>>>(y, ny, x, row_words, n, dest, hh);
+    }
+    filtpart_val_finalize<<<1, 1, 0, st>>>(hh, kept, ny, out);
+    return launch_status();
+}
+
 }  // namespace ixp
 
 using namespace ixp;
+
+extern "C" int ixp_check_filtpart_values(const void *y, int64_t ny, const void *x, int64_t n, int32_t row_bytes,
+                                         const void *keys, int ktype, ixp_pred filt, ixp_pred part,
+                                         const uint8_t *cls, int32_t v, ixp_segs segs, ixp_verdict *d_verdict,
+                                         void *ws, size_t ws_bytes, ixp_stream stream) {
+    if (keys && ktype != IXP_I32 && ktype != IXP_I64) return IXP_E_DTYPE;
+    if (n < 0 || ny < 0 || row_bytes <= 0 || row_bytes % 4 || !d_verdict || n >= (1ll << 32)) return IXP_E_INVAL;
+    if ((n > 0 && !x) || (ny > 0 && !y) || !aligned_to(x, 4) || !aligned_to(y, 4)) return IXP_E_INVAL;
+    if ((segs.offsets && segs.nseg < 1) || (!segs.offsets && segs.nseg != 0)) return IXP_E_INVAL;
+    // the class form: a class array, or, for an empty input (whose arrays may be
+    // NULL), any v other than the predicate form's 2
+    const bool classes = cls != nullptr || (n == 0 && v != 2);
+    if (classes ? (v < 1 || v > 256) : v != 2) return IXP_E_INVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {  // N = 0: only the length of Y can be wrong
+        const int rc = check_ws(ws, ws_bytes, HDR_BYTES);
+        if (rc) return rc;
+        if (cudaMemsetAsync(ws, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
+        filtpart_val_finalize<<<1, 1, 0, st>>>((const Hdr *)ws, nullptr, ny, d_verdict);
+        return launch_status();
+    }
+    const uint32_t *yw = (const uint32_t *)y, *xw = (const uint32_t *)x;
+    const int words = row_bytes / 4;
+    if (classes) return run_filtpart_values_classes(yw, ny, xw, words, n, keys, ktype, filt, cls, v, segs, d_verdict, ws,
+                                                ws_bytes, st);
+    if (!keys || ktype == IXP_I32)
+        return run_filtpart_values(yw, ny, xw, words, n, (const int32_t *)keys, filt, part, segs, d_verdict, ws,
+                                   ws_bytes, st);
+    return run_filtpart_values(yw, ny, xw, words, n, (const int64_t *)keys, filt, part, segs, d_verdict, ws, ws_bytes,
+                               st);
+}
 
 extern "C" int ixp_scan(const void *in, int in_type, void *out, int out_type, int64_t n, int inclusive, ixp_segs segs,
                         void *d_totals, int32_t *d_status, void *ws, size_t ws_bytes, ixp_stream stream) {
@@ -1951,6 +2169,13 @@ extern "C" int ixp_scan_noalloc(const void *in, int in_type, void *out, int out_
     const int es = in_type == IXP_I32 ? 4 : 8, eo = out_type == IXP_I32 ? 4 : 8;
     if ((reinterpret_cast<uintptr_t>(in) % es) || (reinterpret_cast<uintptr_t>(out) % eo)) return IXP_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    // the array's address is per device: the stream must belong to the current one
+    // (the legacy and per-thread default stream handles always do)
+    if (reinterpret_cast<uintptr_t>(st) > 2) {
+        int cur = -1, sdev = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(st, &sdev) != cudaSuccess) return IXP_E_CUDA;
+        if (sdev != cur) return IXP_E_INVAL;
+    }
     if (in_type == IXP_I32 && out_type == IXP_I32)
         return run_scan_noalloc((const int32_t *)in, (int32_t *)out, n, inclusive, (int32_t *)d_totals, d_status, st);
     if (in_type == IXP_I32)

@@ -9,6 +9,7 @@ streams, nothing else.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 from dataclasses import dataclass
 
@@ -24,7 +25,7 @@ CMPS = {"le": 0, "lt": 1, "ge": 2, "gt": 3}
 PREDS = {"true": 0, "mod_eq": 1, "lt": 2, "flags": 3}
 OPS = {"range": 0, "mono": 1, "inj": 2, "bij": 3, "filtpart": 4, "scan": 5, "partition": 6, "flags": 7,
        "inj_seg": 8, "bij_seg": 9, "gather_segments": 10, "filtpart_classes": 11, "inj_hist": 12,
-       "smallest_pairs": 13}
+       "smallest_pairs": 13, "filtpart_values": 14}
 ERRORS = {0: "ok", -1: "invalid argument", -2: "unsupported element type", -3: "value span exceeds the workspace",
           -4: "workspace too small", -5: "CUDA launch failed", -6: "bounded device wait gave up",
           -7: "index out of bounds"}
@@ -76,6 +77,8 @@ _SIGS = {
     "ixp_gather_segments": (_I, [_P, _L, _P, _L, _P, _L, _P, _L, _P, _I, C.c_int32, _P, _P, _Z, _P]),
     "ixp_check_filtpart_classes": (_I, [_P, _I, _L, _P, _I, Pred, _P, C.c_int32, Segs, _P, _P, _Z, _P]),
     "ixp_filtpart_classes": (_I, [_P, _I, _L, Pred, _P, C.c_int32, Segs, _P, _I, _P, _P, _Z, _P]),
+    "ixp_check_filtpart_values": (_I, [_P, _L, _P, _L, C.c_int32, _P, _I, Pred, Pred, _P, C.c_int32, Segs, _P, _P,
+                                       _Z, _P]),
     "ixp_sgm_scan": (_I, [_P, _P, _I, _P, _I, _L, _I, _P, _P, _Z, _P]),
     "ixp_mkii": (_I, [_P, _L, _P, _I, _L, _P, _P, _Z, _P]),
     "ixp_flags_from_shape": (_I, [_P, _L, _P, _P, _I, _L, _P, _P, _P, _Z, _P]),
@@ -373,6 +376,39 @@ def filtpart_classes(cls, v, keys=None, filt="true", offsets=None, out_dtype=tor
                                     _dev(cls, "cls"), int(v), segs, out.data_ptr(), _itype(out), kept.data_ptr(),
                                     ws.data_ptr(), ws.numel(), _stream(stream)), "filtpart_classes")
     return out, kept
+
+
+def check_filtpart_values(y, x, keys=None, filt="true", part="true", offsets=None, *, cls=None, v=2, out=None,
+                          ws=None, stream=None) -> Verdict:
+    """FiltPart in value form: Y (rows) equals X filtered and stably partitioned (by
+    `part`, or by class min(cls, v - 1) when `cls` is given), bitwise, with length N."""
+    vb = _verdict_buf(x.device, out)
+    n, ny = x.shape[0], y.shape[0]
+    segs = _segs(offsets)
+    if x.dtype != y.dtype or tuple(x.shape[1:]) != tuple(y.shape[1:]):
+        raise ValueError("y rows must have the type and shape of x rows")
+    row_bytes = x.element_size() * math.prod(x.shape[1:])
+    if row_bytes % 4:
+        raise ValueError("rows must be a multiple of 4 bytes")
+    for t, nm in ((x, "x"), (y, "y")):
+        if not t.is_contiguous():
+            raise ValueError(f"{nm} must be contiguous")
+    if keys is not None:
+        _need(keys, "keys", n)
+    _pred_flags_ok(filt, n)
+    if cls is not None:
+        _need(cls, "cls", n, (torch.uint8,))
+    else:
+        _pred_flags_ok(part, n)
+    kt = _itype(keys) if keys is not None else 0
+    need = workspace_size("filtpart_values", int(v) if cls is not None else 0, n, segs.nseg)
+    ws = ws if ws is not None else workspace(need, x.device)
+    _ck(load().ixp_check_filtpart_values(y.data_ptr() if ny else None, ny, x.data_ptr() if n else None, n,
+                                         row_bytes, None if keys is None else _dev(keys, "keys"), kt,
+                                         make_pred(filt), make_pred(part),
+                                         None if cls is None else _dev(cls, "cls"), int(v), segs, vb.data_ptr(),
+                                         ws.data_ptr(), ws.numel(), _stream(stream)), "check_filtpart_values")
+    return Verdict(vb)
 
 
 # ---------------------------------------------------------------- combinators

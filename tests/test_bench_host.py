@@ -15,8 +15,11 @@ def test_algorithmic_bytes_per_op():
     ops = {name: (kind, inputs, nbytes) for name, kind, inputs, nbytes in bench.make_ops(N32, N64)}
     for tag, n, es in (("i32", N32, 4), ("i64", N64, 8)):
         # the checks read the index array once
-        for op in ("range_perm", "range_oor", "mono_le", "mono_brk", "inj_perm", "inj_dup", "bij_perm", "bij_dup"):
+        for op in ("range_perm", "range_oor", "mono_le", "mono_brk"):
             assert ops[f"{op}_{tag}"][2] == es * n
+        # Inj / Bij also clear and count a bitmap of span bits (span = n here)
+        for op in ("inj_perm", "inj_dup", "bij_perm", "bij_dup"):
+            assert ops[f"{op}_{tag}"][2] == es * n + 2 * (n // 8)
     assert ops["scan_i32"][2] == 8 * N32  # 4 in + 4 out
     assert ops["partition_p50"][2] == ops["partition_p01"][2] == 16 * N32  # key + payload in and out
     assert ops["filtpart_p50"][2] == 8 * N32  # Z + key
@@ -66,3 +69,22 @@ def test_host_info_names_arm_parts(tmp_path):
     assert "Neoverse V2" in bench.host_info(str(f))["cpu_model"]
     f.write_text("processor\t: 0\nmodel name\t: Example CPU @ 2.0GHz\n")
     assert bench.host_info(str(f))["cpu_model"] == "Example CPU @ 2.0GHz"
+
+
+def test_roofline_takes_the_slowest_op_and_reports_families(tmp_path):
+    peak = 8000.0
+    per_op = {"range_perm_i32": bench.op_record(0.2, 4 * 10**9 // 5, 1, peak),
+              "inj_perm_i32": bench.op_record(1.0, 10**9, 1, peak),
+              "bij_dup_i32": bench.op_record(3.0, 10**9, 1, peak),
+              "scatter_rows8": bench.op_record(2.0, 4 * 10**9, 1, peak)}
+    tf = tmp_path / "traffic.json"
+    tf.write_text(json.dumps({"ops": {"bij_dup_i32": {"bytes": 1234}}}))
+    r = bench.roofline_of(per_op, peak, "measured", traffic_file=str(tf))
+    assert r["op"] == "bij_dup_i32" and r["traffic"] == 1234 and r["achieved"] == per_op["bij_dup_i32"]["gbs"]
+    assert r["frac"] == round(per_op["bij_dup_i32"]["gbs"] / peak, 4)
+    fam = r["families"]["inj_bij"]
+    assert fam["ops"] == 2 and fam["ms"] == 4.0 and fam["gbs"] == 500.0 and fam["frac"] == 0.0625
+    assert r["families"]["range_mono"]["ops"] == 1
+    # no summary for the op: traffic unknown
+    r = bench.roofline_of(per_op, peak, "measured", traffic_file=str(tmp_path / "none.json"))
+    assert r["traffic"] is None

@@ -82,3 +82,17 @@ def test_scan_and_status_buffers(ixp):
         ixp.mkii(torch.zeros(2, dtype=torch.int64), 0, status=torch.zeros(1, dtype=torch.int64))
     with pytest.raises(ValueError, match="status"):
         ixp.gather(torch.zeros(4, 2), torch.zeros(3, dtype=torch.int64), status=torch.zeros(1, dtype=torch.uint8))
+
+
+def test_filtpart_values_buffers(ixp):
+    x = torch.zeros(10, 3, dtype=torch.int32)
+    with pytest.raises(ValueError, match="type and shape"):
+        ixp.check_filtpart_values(torch.zeros(10, 4, dtype=torch.int32), x)
+    with pytest.raises(ValueError, match="type and shape"):
+        ixp.check_filtpart_values(torch.zeros(10, 3, dtype=torch.float32), x)
+    with pytest.raises(ValueError, match="multiple of 4"):
+        ixp.check_filtpart_values(torch.zeros(10, 3, dtype=torch.uint8), torch.zeros(10, 3, dtype=torch.uint8))
+    with pytest.raises(ValueError, match="keys"):
+        ixp.check_filtpart_values(x, x, keys=torch.zeros(9, dtype=torch.int32))
+    with pytest.raises(ValueError, match="cls"):
+        ixp.check_filtpart_values(x, x, cls=torch.zeros(10, dtype=torch.int32), v=3)

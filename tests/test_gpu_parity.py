@@ -716,6 +716,64 @@ def test_filtpart_classes(ixp, dev, n, m, v, zt):
         same(got, ref, (name, n, m, v))
 
 
+def filtpart_order(kept, cls, off):
+    """Source index of every position of FiltPart's Y: per segment, the kept
+    elements stably by class (a library stable sort)."""
+    n = kept.shape[0]
+    seg = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    idx = np.flatnonzero(kept)
+    return idx[np.lexsort((idx, cls[idx], seg[idx]))] if n else np.zeros(0, np.int64)
+
+
+@pytest.mark.parametrize("form", ["pred", "classes"])
+@pytest.mark.parametrize("cols,dt", [(0, np.float32), (3, np.int32), (8, np.float32)])
+@pytest.mark.parametrize("n,m", [(0, 0), (1, 0), (65553, 0), (300001, 0), (70000, 37)])
+def test_filtpart_values(ixp, dev, n, m, cols, dt, form):
+    """FiltPart in value form against the oracle: the right Y, two rows swapped, one
+    bit flipped, a Y one row short and one row long; flat and segmented, with a
+    filter, by a predicate (v = 2) or by classes (v = 3)."""
+    rng = np.random.default_rng(n + m + cols)
+    off = np.array([0, n], np.int64) if m == 0 else random_offsets(rng, n, m)
+    keys = synth.keys_uniform(n, n + 3).astype(np.int32)
+    flags = synth.flags_bernoulli(n, n + 4, 0.7)
+    thr = synth.bernoulli_threshold(0.4)
+    shape = (n,) if cols == 0 else (n, cols)
+    x = (rng.standard_normal(shape).astype(dt) if dt == np.float32 else
+         rng.integers(-2**31, 2**31, size=shape).astype(dt))
+    kept = flags != 0
+    if form == "pred":
+        cls = (keys >= thr).astype(np.uint8)  # class 0 = part true
+        v = 2
+    else:
+        cls = rng.integers(0, 4, size=n).astype(np.uint8)
+        v = 3
+    order = filtpart_order(kept, np.minimum(cls, v - 1), off)
+    y = x[order]
+    cases = {"ok": y}
+    N = order.shape[0]
+    if N >= 2:
+        a, b = 0, N - 1
+        s2 = y.copy(); s2[[a, b]] = s2[[b, a]]; cases["swap"] = s2
+        s3 = y.copy().view(np.int32); s3.reshape(N, -1)[N // 2, 0] ^= 1 << 3; cases["bit"] = s3.view(dt)
+    if N >= 1:
+        cases["short"] = y[:-1].copy()
+    cases["long"] = np.concatenate([y, x[:1] if n else np.zeros((1,) + shape[1:], dt)])
+    fl_o, fl_g = ("flags", 0, 0, flags), ("flags", 0, 0, T(flags, dev))
+    offs_o = None if m == 0 else off
+    offs_g = None if m == 0 else T(off, dev)
+    for name, yy in cases.items():
+        yy = np.ascontiguousarray(yy)
+        if form == "pred":
+            got = ixp.check_filtpart_values(T(yy, dev), T(x, dev), T(keys, dev), filt=fl_g, part=("lt", 0, thr),
+                                            offsets=offs_g)
+            ref = oracle.check_filtpart_values(yy, x, keys, filt=fl_o, part=("lt", 0, thr), offsets=offs_o)
+        else:
+            got = ixp.check_filtpart_values(T(yy, dev), T(x, dev), T(keys, dev), filt=fl_g, offsets=offs_g,
+                                            cls=T(cls, dev), v=v)
+            ref = oracle.check_filtpart_values(yy, x, keys, filt=fl_o, cls=cls, v=v, offsets=offs_o)
+        same(got, ref, (name, n, m, cols, form))
+
+
 @pytest.mark.parametrize("ot", [np.int32, np.int64])
 @pytest.mark.parametrize("v", [1, 3, 256])
 @pytest.mark.parametrize("n,m", [(0, 0), (1, 0), (300001, 0), (70000, 37), (20000, 3000)])
