@@ -454,7 +454,8 @@ def main():
     ap.add_argument("--ops", default="", help="comma-separated subset of op names (profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
     ap.add_argument("--no-ceilings", action="store_true", help="skip the hardware-rate microbenchmarks")
-    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes", "backward", "segmented"],
+    ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes", "backward", "segmented",
+                                                     "any_span"],
                     help="run only this workload and print its result (profiling; --small: 2^26 elements for "
                          "classes, backward and segmented)")
     args = ap.parse_args()
@@ -483,7 +484,7 @@ def main():
                    "payload8": synth.t_payload_f32(n32 // 4, s + 10, dev, cols=8)}
             res = run_backward(ixp, inp, n32, dev, None)
         else:
-            fn = {"partition2": run_partition2, "smallest_pairs": run_matching}[args.extra]
+            fn = {"partition2": run_partition2, "smallest_pairs": run_matching, "any_span": run_any_span}[args.extra]
             res = fn(ixp, dev)
         print(json.dumps({"extra": args.extra, "result": res}))
         return
@@ -600,6 +601,8 @@ def main():
             extras["partition2"] = run_partition2(ixp, dev)
             torch.cuda.empty_cache()
             extras["smallest_pairs"] = run_matching(ixp, dev)
+            torch.cuda.empty_cache()
+            extras["any_span"] = run_any_span(ixp, dev)
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
@@ -979,6 +982,35 @@ def run_matching(ixp, dev):
             "kept": c, "kept_equals_distinct_vertices": c == distinct,
             "post_inj_check_ms": round(t_chk, 4),
             "post_inj_ok": [ixp.Verdict(v1).get()["ok"], ixp.Verdict(v2).get()["ok"]]}
+
+
+def run_any_span(ixp, dev):
+    """Inj over a span no bitmap covers: 2^27 int64 ids spread over [0, 2^62)
+    (distinct: a permutation in the high bits, random low bits), decided by the hash
+    set; clean and with a planted repeat (verdicts checked against the planted pair)."""
+    import torch
+    n = 1 << 27
+    s = synth.seed_for(1) + 130
+    perm = synth.t_permutation(n, s, dev, torch.int64)
+    g = torch.Generator(device=dev)
+    g.manual_seed(s + 1)
+    ids = (perm << 35) | torch.randint(0, 1 << 35, (n,), generator=g, device=dev, dtype=torch.int64)
+    del perm
+    dup, p, q = synth.t_plant_duplicate(ids, s + 2)
+    need = ixp.workspace_size("inj", 1, n, -1)
+    ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    v1 = torch.empty(6, dtype=torch.int64, device=dev)
+    v2 = torch.empty(6, dtype=torch.int64, device=dev)
+    t_ok = _time(lambda: ixp.check_inj(ids, out=v1, ws=ws))
+    t_dup = _time(lambda: ixp.check_inj(dup, out=v2, ws=ws))
+    a, b = ixp.Verdict(v1).get(), ixp.Verdict(v2).get()
+    nbytes = 8 * n
+    return {"workload": "Inj of %d int64 ids over [0, 2^62) (hash set)" % n,
+            "ms": round(t_ok, 4), "gbs": round(nbytes / (t_ok / 1e3) / 1e9, 1),
+            "gelem_s": round(n / (t_ok / 1e3) / 1e9, 2), "dup_ms": round(t_dup, 4),
+            "ok": a["ok"] == 1 and a["status"] == 0,
+            "dup_found": b["ok"] == 0 and b["index"] == min(p, q) and b["aux0"] == max(p, q),
+            "workspace_bytes": need}
 
 
 def run_e2e(ixp, R, ops, inp, dev, args, step_bytes):

@@ -106,7 +106,7 @@ typedef struct {
 enum {
     IXP_OP_RANGE = 0,
     IXP_OP_MONO = 1,
-    IXP_OP_INJ = 2,      /* extra = largest value span to support (bitmap bits) */
+    IXP_OP_INJ = 2,      /* extra = largest value span to support (bitmap bits); < 0: any span */
     IXP_OP_BIJ = 3,      /* extra = |Img| (bitmap bits) */
     IXP_OP_FILTPART = 4, /* extra = nseg */
     IXP_OP_SCAN = 5,     /* extra = nseg */
@@ -156,10 +156,12 @@ int ixp_check_mono(const void *x, int itype, int64_t n, int cmp, ixp_segs segs, 
 /* Inj X Rcd  [Sec. 2.3, Fig. 5]: no two positions whose values lie in
  * Rcd = [rcd_lo, rcd_hi] hold the same value. Decided with a bitmap over the value
  * span: [rcd_lo, rcd_hi] when that is finite and fits, else [min, max] of the
- * in-Rcd values (one extra pass). A span above the workspace capacity (set by
- * `extra` in ixp_workspace_size) gives verdict status IXP_E_SPAN. Verdict on a
- * violation: index = smallest i whose value occurs again, value = X[i],
- * aux0 = smallest j > i with X[j] = X[i] (0 when the property holds). */
+ * in-Rcd values (one extra pass). A span wider than the workspace bitmaps is
+ * decided with a hash set of the in-Rcd values instead when the workspace holds
+ * one (ixp_workspace_size(IXP_OP_INJ, itype, n, extra < 0): any span, n < 2^32 - 1);
+ * without it such a span gives verdict status IXP_E_SPAN. Verdict on a violation:
+ * index = smallest i whose value occurs again, value = X[i], aux0 = smallest j > i
+ * with X[j] = X[i] (0 when the property holds). */
 int ixp_check_inj(const void *x, int itype, int64_t n, int64_t rcd_lo, int64_t rcd_hi, ixp_verdict *d_verdict,
                   void *ws, size_t ws_bytes, ixp_stream stream);
 

@@ -7,6 +7,7 @@ namespace ixp {
 
 size_t tiled_ws_bytes(int64_t n, int V, int64_t nseg);  // scan.cu
 size_t bk_prefix_bytes(int64_t n);                       // checks.cu
+size_t inj_any_span_ws_bytes(int64_t n);                 // checks.cu
 size_t seg_ws_bytes(int64_t nseg);                       // segmented.cu
 size_t gather_segments_ws_bytes(int64_t n_out);          // scatter.cu
 size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg);  // classes.cu
@@ -48,6 +49,8 @@ extern "C" size_t ixp_workspace_size(int op, int itype, int64_t n, int64_t extra
         case IXP_OP_RANGE: return HDR_BYTES;
         case IXP_OP_MONO: return HDR_BYTES + chunk_lb_bytes(n);  // the table serves the segmented form
         case IXP_OP_INJ:
+            if (extra < 0) return inj_any_span_ws_bytes(n);  // bitmaps + the hash set for any span
+            [[fallthrough]];
         case IXP_OP_BIJ: {
             // large inputs also get the bucket pool (about 5 bytes per element)
             int64_t span = extra > 0 ? extra : n;

@@ -243,7 +243,9 @@ constexpr unsigned BK_MAX = 4096;
 // the bucket width, and the launch shape the setup kernel chose for the span it
 // found (both shapes run the same two passes).
 constexpr int BK_NB = 0, BK_CAP = 1, BK_LW = 2, BK_MODE = 3;
-constexpr unsigned long long BK_STAGED = 1, BK_WIDE = 2;
+constexpr unsigned long long BK_STAGED = 1, BK_WIDE = 2, BK_HASH = 3;
+// header slots of the hash-set path: the pair of the value -1, the smallest pair
+constexpr int HS_NEG1 = 4, HS_PAIR = 5;
 
 // Min/max of the in-codomain values (needed when Rcd is unbounded). The bounds
 // come clamped to T, so every compare is in T; a vector that lies wholly inside
@@ -316,26 +318,26 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) minmax_in_kernel(const T *_
 // the call will use. Fixed range: base = lo, span = hi - lo + 1. Otherwise the
 // range comes from minmax_in_kernel (span 0 when nothing is in range).
 __global__ void bitmap_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, unsigned long long cap_bits,
-                                    unsigned *bm, unsigned *dup) {
+                                    unsigned *bm, unsigned *dup, int hash_ok) {
     IXP_KERNEL_ENTRY();
     unsigned long long base, span;
+    bool empty = false;  // nothing in range
     if (fixed) {
         base = (unsigned long long)lo;
         span = (unsigned long long)hi - (unsigned long long)lo + 1ull;
     } else {
         int64_t mn = dec_min(h->k_min), mx = dec_max(h->k_max);
-        if (mn > mx) {
-            base = 0;
-            span = 0;
-        } else {
-            base = (unsigned long long)mn;
-            span = (unsigned long long)mx - (unsigned long long)mn + 1ull;
-        }
+        empty = mn > mx;
+        base = empty ? 0ull : (unsigned long long)mn;
+        span = empty ? 0ull : (unsigned long long)mx - (unsigned long long)mn + 1ull;
     }
     // span == 0 after the +1 means the full 2^64 range
-    bool too_big = (fixed || span != 0) ? (span > cap_bits || (span == 0 && fixed)) : false;
+    const bool too_big = !empty && (span == 0 || span > cap_bits);
     if (too_big) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, IXP_E_SPAN);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (hash_ok) h->spare[BK_MODE] = BK_HASH;  // decided by the hash-set pass instead
+            else set_status(h, IXP_E_SPAN);
+        }
         return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -575,6 +577,115 @@ __global__ void inj_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
     *out = v;
 }
 
+// ====================================================== Inj, any value span
+// When the span of the in-range values is wider than the workspace bitmap (int64
+// ids, hashes, a range that covers most of the type), Inj is decided with an
+// open-addressing hash set in the workspace: 2^k >= 2n slots of {key, first, second}
+// (16 bytes, zeroed per call). Element i with value v in Rcd probes from slot
+// mix(v) (the SplitMix64 finalizer, Steele, Lea and Flood 2014) and claims the
+// first slot that is empty (key 0) or holds v (the key is v + 1, so that 0 marks an
+// empty slot; v = -1 keeps its pair in the header instead). In the slot, first
+// and second keep the two smallest positions of v, stored as ~i so that the
+// atomic maximum keeps the minimum and 0 means none: first takes ~i, and second
+// the smaller encoding of the old first and ~i, which leaves second = the second
+// smallest position once every copy is in. A value with a second position is a
+// repeat; the witness (reading 14) is the pair (first, second) with the smallest
+// first, found by one sweep over the slots. n < 2^32 - 1 (32-bit positions).
+struct HashSlot {
+    unsigned long long key;
+    unsigned first, second;
+};
+static_assert(sizeof(HashSlot) == 16, "hash slot must be 16 bytes");
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ void hash_keep(unsigned *first, unsigned *second, unsigned enc) {
+    const unsigned o = atomicMax(first, enc);
+    if (o) atomicMax(second, min(o, enc));  // o = 0: no earlier copy, min(o, enc) = 0 changes nothing
+}
+
+template <typename T>
+__global__ void __launch_bounds__(STREAM_THREADS, 4) hash_insert_kernel(const T *__restrict__ x, int64_t n,
+                                                                        int64_t rlo, int64_t rhi, Hdr *h,
+                                                                        HashSlot *__restrict__ tab,
+                                                                        unsigned long long mask) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != BK_HASH) return;
+    unsigned *nfirst = reinterpret_cast<unsigned *>(&h->spare[HS_NEG1]);  // the pair of v = -1
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += stride) {
+        const int64_t v = (int64_t)__ldcs(x + i);
+        if (v < rlo || v > rhi) continue;
+        const unsigned enc = ~(unsigned)i;
+        if (v == -1) {
+            hash_keep(nfirst, nfirst + 1, enc);
+            continue;
+        }
+        const unsigned long long key = (unsigned long long)v + 1ull;
+        unsigned long long s = mix64((unsigned long long)v) & mask;
+        for (unsigned long long probe = 0; probe <= mask; probe++) {  // the table is never full: ends
+            const unsigned long long old = atomicCAS(&tab[s].key, 0ull, key);
+            if (old == 0ull || old == key) {
+                hash_keep(&tab[s].first, &tab[s].second, enc);
+                break;
+            }
+            s = (s + 1) & mask;
+        }
+    }
+}
+
+// The hash set starts empty: zeroed only when the setup kernel chose the hash path.
+__global__ void __launch_bounds__(STREAM_THREADS) hash_clear_kernel(const Hdr *h, HashSlot *__restrict__ tab,
+                                                                    unsigned long long slots) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != BK_HASH) return;
+    ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tab);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < slots;
+         k += (unsigned long long)gridDim.x * blockDim.x)
+        __stcs(t2 + k, make_ulonglong2(0ull, 0ull));
+}
+
+// The smallest (first, second) pair over the slots with a second position, packed
+// as first << 32 | second and kept with one atomic maximum of its encoding.
+__global__ void __launch_bounds__(STREAM_THREADS) hash_witness_kernel(Hdr *h, const HashSlot *__restrict__ tab,
+                                                                      unsigned long long slots) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != BK_HASH) return;
+    unsigned long long best = ~0ull;
+    auto take = [&](unsigned f, unsigned sc) {
+        if (!sc) return;
+        const unsigned long long pk = ((unsigned long long)~f << 32) | (unsigned long long)~sc;
+        best = pk < best ? pk : best;
+    };
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned *nf = reinterpret_cast<const unsigned *>(&h->spare[HS_NEG1]);
+        take(nf[0], nf[1]);
+    }
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < slots;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const HashSlot e = tab[k];
+        if (e.key) take(e.first, e.second);
+    }
+    __shared__ unsigned long long sm[STREAM_THREADS / 32];
+    const unsigned long long r = block_max_u64(best == ~0ull ? 0ull : ~best, sm);
+    if (threadIdx.x == 0 && r) atomicMax(&h->spare[HS_PAIR], r);
+}
+
+// Hash mode's verdict fields: index = first, aux0 = second (the first repeat).
+__global__ void hash_result_kernel(Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != BK_HASH || !h->spare[HS_PAIR]) return;
+    const unsigned long long pk = ~h->spare[HS_PAIR];
+    h->flag = 1u;
+    h->k_first = enc_first((int64_t)(pk >> 32));
+    h->k_aux = enc_first((int64_t)(pk & 0xffffffffull));
+}
+
 // Bij "missing" value: when nothing is out of image and nothing repeats but fewer
 // than |Img| elements hit the image, the smallest clear bit is the first value no
 // element takes.
@@ -678,7 +789,7 @@ __host__ __device__ inline unsigned staged_lw(unsigned long long span, unsigned 
 
 __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, unsigned long long cap_bits,
                                     BucketCfg cfg, unsigned staged_logb, unsigned *cursors, unsigned *marks,
-                                    unsigned *dup, unsigned *bucket_mask) {
+                                    unsigned *dup, unsigned *bucket_mask, int hash_ok) {
     IXP_KERNEL_ENTRY();
     unsigned long long base = 0, span = 0;
     bool too_big = false;
@@ -699,7 +810,10 @@ __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, u
     const unsigned lw = staged ? staged_lw(span, staged_logb) : cfg.lw;
     const unsigned long long nb = too_big ? 0ull : (span + (1ull << lw) - 1ull) >> lw;
     if (too_big || (!staged && nb > cfg.bmax)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) set_status(h, IXP_E_SPAN);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (hash_ok) h->spare[BK_MODE] = BK_HASH;  // decided by the hash-set pass instead
+            else set_status(h, IXP_E_SPAN);
+        }
         return;
     }
     const unsigned long long cap = nb ? (cfg.pool / nb) & ~3ull : 0ull;
@@ -1157,9 +1271,23 @@ struct BitmapWs {
     unsigned *cursors, *bmask, *pool, *bm, *dup;
     unsigned long long cap;  // bits per bitmap
     bool buckets;            // bucketed layout available
+    HashSlot *tab;           // hash set for spans wider than the bitmaps (nullptr: none)
+    unsigned long long slots;
 };
 
-static BitmapWs bitmap_ws(void *ws, size_t ws_bytes, int64_t n) {
+// Hash-set slots for n elements: the power of two at least 2n (at least 2).
+unsigned long long inj_hash_slots(int64_t n) {
+    unsigned long long c = 2;
+    while (c < 2ull * (unsigned long long)(n > 0 ? n : 0)) c <<= 1;
+    return c;
+}
+// Bitmap bits of the any-span workspace: the default span capacity 4n + 4096, at
+// least the 2^21 bits every Inj workspace gets (as ixp_workspace_size sizes them).
+static unsigned long long inj_default_span(int64_t n) {
+    return std::max<unsigned long long>(4ull * (unsigned long long)(n > 0 ? n : 0) + 4096ull, BK_MIN_SPAN);
+}
+
+static BitmapWs bitmap_ws(void *ws, size_t ws_bytes, int64_t n, bool allow_hash) {
     BitmapWs w{};
     char *p = (char *)ws;
     w.h = (Hdr *)p;
@@ -1172,10 +1300,27 @@ static BitmapWs bitmap_ws(void *ws, size_t ws_bytes, int64_t n) {
         w.pool = (unsigned *)(p + HDR_BYTES + round256(BK_MAX * 4) + round256(BK_MAX / 8));
         off = bk_prefix_bytes(n);
     }
-    w.cap = ws_bytes > off ? (unsigned long long)((ws_bytes - off) / 8) * 32ull : 0ull;
+    // the hash set sits at the end of the workspace when the workspace also leaves
+    // the any-span bitmaps (two of inj_default_span bits) before it; a workspace
+    // sized for a given span (no hash set) is smaller than that
+    size_t end = ws_bytes;
+    const size_t hb = round256(inj_hash_slots(n) * sizeof(HashSlot));
+    const size_t bmin = 2 * round256((inj_default_span(n) + 31) / 32 * 4);
+    if (allow_hash && n < (int64_t)UINT32_MAX && ws_bytes >= off + bmin + hb) {
+        end = (ws_bytes - hb) & ~(size_t)255;
+        w.tab = (HashSlot *)(p + end);
+        w.slots = inj_hash_slots(n);
+    }
+    w.cap = end > off ? (unsigned long long)((end - off) / 8) * 32ull : 0ull;
     w.bm = (unsigned *)(p + off);
     w.dup = w.bm + w.cap / 32;
     return w;
+}
+
+size_t inj_any_span_ws_bytes(int64_t n) {
+    const size_t prefix = n >= BK_MIN_N ? bk_prefix_bytes(n) : HDR_BYTES;
+    return prefix + 2 * round256((inj_default_span(n) + 31) / 32 * 4) + round256(inj_hash_slots(n) * sizeof(HashSlot)) +
+           256;
 }
 
 // Bucket width: about two buckets per SM, between 2^14 and 2^19 values (a 64 KB
@@ -1230,7 +1375,7 @@ static void launch_buckets(const T *x, int64_t n, int64_t rlo, int64_t rhi, int 
                            unsigned long long span_cap, const BitmapWs &w, const BucketCfg &cfg, cudaStream_t st) {
     const int sgrid = num_sms() * 4;
     bucket_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(w.h, fixed, flo, fhi, w.cap, cfg, ST_LOGB, w.cursors, w.bm,
-                                                          w.dup, w.bmask);
+                                                          w.dup, w.bmask, w.tab != nullptr);
     const int vec = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
     // staged shape: room for 2^ST_LOGB buckets (a narrower span found on the device
     // gives narrower buckets, never more of them), and the widest bucket the span cap
@@ -1256,7 +1401,7 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
             launch_buckets<T, true>(x, n, rlo, rhi, 1, ilo, ihi, isize, w, cfg, st);
             first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, w.bmask, &h->k_first2);
         } else {
-            bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, 1, ilo, ihi, cap, bm, dup);
+            bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, 1, ilo, ihi, cap, bm, dup, 0);
             if (n > 0) {
                 mark_kernel<T, true><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, ilo, ihi, h, bm, dup);
                 first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, ilo, ihi, h, dup, nullptr, &h->k_first2);
@@ -1282,13 +1427,20 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
     if (bk) {
         launch_buckets<T, false>(x, n, rlo, rhi, fixed ? 1 : 0, rlo, rhi, span_cap, w, cfg, st);
     } else {
-        bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, fixed ? 1 : 0, rlo, rhi, cap, bm, dup);
+        bitmap_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, fixed ? 1 : 0, rlo, rhi, cap, bm, dup,
+                                                              w.tab != nullptr);
         if (n > 0) mark_kernel<T, false><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, rlo, rhi, h, bm, dup);
     }
     if (n > 0) {
         first_dup_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, dup, bk ? w.bmask : nullptr,
                                                              &h->k_first);
         partner_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, h, &h->k_first);
+    }
+    if (w.tab && n > 0) {  // spans wider than the bitmaps: the hash set decides (the kernels exit otherwise)
+        hash_clear_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, w.tab, w.slots);
+        hash_insert_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, w.tab, w.slots - 1);
+        hash_witness_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, w.tab, w.slots);
+        hash_result_kernel<<<1, 1, 0, st>>>(h);
     }
     inj_finalize<T><<<1, 1, 0, st>>>(x, h, out);
 }
@@ -1302,7 +1454,7 @@ extern "C" int ixp_check_inj(const void *x, int itype, int64_t n, int64_t rcd_lo
     int rc = check_ws(ws, ws_bytes, HDR_BYTES + 256);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const BitmapWs w = bitmap_ws(ws, ws_bytes, n);
+    const BitmapWs w = bitmap_ws(ws, ws_bytes, n, true);
     if (cudaMemsetAsync(w.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
     if (itype == IXP_I32)
         run_bitmap_check((const int32_t *)x, n, rcd_lo, rcd_hi, false, 0, 0, w, d_verdict, st);
@@ -1321,7 +1473,7 @@ extern "C" int ixp_check_bij(const void *x, int itype, int64_t n, int64_t rcd_lo
     if (isize == 0 || isize > (1ull << 40)) return IXP_E_INVAL;
     int rc = check_ws(ws, ws_bytes, HDR_BYTES + 256);
     if (rc) return rc;
-    const BitmapWs w = bitmap_ws(ws, ws_bytes, n);
+    const BitmapWs w = bitmap_ws(ws, ws_bytes, n, false);
     if (isize > w.cap) return IXP_E_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemsetAsync(w.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;

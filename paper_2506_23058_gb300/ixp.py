@@ -253,17 +253,28 @@ def check_mono(x, cmp="le", offsets=None, *, seg_ok=None, out=None, ws=None, str
     return Verdict(v)
 
 
+HASH_SET_MAX_BYTES = 1 << 34  # the default workspace holds a hash set up to this size
+
+
 def check_inj(x, rcd_lo=I64MIN, rcd_hi=I64MAX, *, span=None, out=None, ws=None, stream=None) -> Verdict:
-    """`span`: the largest value span the bitmap must cover. Default: the Rcd width when
-    it is at most 4n + 4096, else 4n + 4096 (a wider actual span reports IXP_E_SPAN)."""
+    """`span`: the largest value span the bitmap must cover (a wider span found in the
+    data reports IXP_E_SPAN). Default: the Rcd width when it is at most 4n + 4096;
+    otherwise any span: bitmaps for 4n + 4096 bits plus a hash set of 16 bytes per
+    slot (the power of two >= 2n slots) that decides wider spans, while that set
+    stays within HASH_SET_MAX_BYTES (n <= 2^29), else 4n + 4096 bits."""
     v = _verdict_buf(x.device, out)
     n = x.numel()
+    extra = span
     if span is None:
-        span = 4 * n + 4096
-        if rcd_hi - rcd_lo + 1 <= span:
-            span = rcd_hi - rcd_lo + 1
-    need = workspace_size("inj", _itype(x), n, max(1, span))
-    ws = ws if ws is not None else workspace(need, x.device)
+        extra = 4 * n + 4096
+        if rcd_hi - rcd_lo + 1 <= extra:
+            extra = rcd_hi - rcd_lo + 1
+        elif 16 * max(2, 1 << max(0, (2 * n - 1).bit_length())) <= HASH_SET_MAX_BYTES:
+            extra = -1
+    need = workspace_size("inj", _itype(x), n, extra if extra < 0 else max(1, extra))
+    # exactly the bytes asked for: the library reads its capacities (and whether a
+    # hash set is there) from the size it is given
+    ws = ws if ws is not None else workspace(need, x.device)[:need]
     _ck(load().ixp_check_inj(_dev(x, "x"), _itype(x), n, rcd_lo, rcd_hi, v.data_ptr(), ws.data_ptr(), ws.numel(),
                              _stream(stream)), "check_inj")
     return Verdict(v)

@@ -64,6 +64,26 @@ def test_checks_full_size(ixp, dev, tag, n, dt):
     assert (o["kind"], o["index"], o["value"]) == (v["kind"], v["index"], v["value"])
 
 
+def test_inj_any_span_full_size(ixp, dev):
+    """Inj of 2^27 int64 ids spread over [0, 2^62) (distinct by construction: a
+    permutation in the high bits), decided by the hash set: it holds, and a planted
+    repeat is reported as the pair (min, max) of its positions."""
+    n = 1 << 27
+    s = synth.seed_for(1) + 130
+    perm = synth.t_permutation(n, s, dev, torch.int64)
+    g = torch.Generator(device=dev)
+    g.manual_seed(s + 1)
+    low = torch.randint(0, 1 << 35, (n,), generator=g, device=dev, dtype=torch.int64)
+    ids = (perm << 35) | low
+    del perm, low
+    v = ixp.check_inj(ids).get()
+    assert v["status"] == 0 and v["ok"] == 1
+    dup, p, q = synth.t_plant_duplicate(ids, s + 2)
+    v = ixp.check_inj(dup).get()
+    assert v["status"] == 0 and v["ok"] == 0
+    assert v["index"] == min(p, q) and v["aux0"] == max(p, q) and v["value"] == int(dup[min(p, q)].item())
+
+
 def test_scan_full_size(ixp, dev):
     n = 1 << 28
     g = torch.Generator(device=dev)

@@ -150,12 +150,56 @@ def test_inj_wide_values_and_span_limit(ixp, dev):
     same(ixp.check_inj(T(a, dev)), oracle.check_inj(a))
     a[100] = a[4000]
     same(ixp.check_inj(T(a, dev)), oracle.check_inj(a))
-    # values spread over 2^40: the bitmap cannot hold the span -> device status IXP_E_SPAN
+    # values spread over 2^40: with a bitmap-only workspace the span is too wide
     b = rng.integers(0, 2**40, size=n).astype(np.int64)
-    g = ixp.check_inj(T(b, dev)).get()
+    g = ixp.check_inj(T(b, dev), span=4 * n + 4096).get()
     assert g["status"] == -3 and g["ok"] == -1
-    # restricting Rcd to a small window makes it decidable again
+    # the default workspace holds the hash set, which decides it
+    same(ixp.check_inj(T(b, dev)), oracle.check_inj(b))
+    # restricting Rcd to a small window makes it a bitmap check again
     same(ixp.check_inj(T(b, dev), 0, 2**20), oracle.check_inj(b, 0, 2**20))
+
+
+def spread_ids(n, seed, bits=62):
+    """Distinct int64 values spread over [0, 2^bits): a permutation in the high bits,
+    random low bits."""
+    rng = np.random.default_rng(seed)
+    hb = max(1, int(n - 1).bit_length())
+    low = bits - hb
+    return (rng.permutation(n).astype(np.int64) << low) | rng.integers(0, 1 << low, size=n, dtype=np.int64)
+
+
+@pytest.mark.parametrize("n", [2, 4097, 1 << 20, 3_000_001])
+def test_inj_any_span_hash_set(ixp, dev, n):
+    """Inj over spans no bitmap covers: int64 ids over [0, 2^62), planted repeats
+    (first position at either end, several repeated values), a restricted Rcd, int32
+    values over the whole type, and the whole int64 range."""
+    x = spread_ids(n, n)
+    same(ixp.check_inj(T(x, dev)), oracle.check_inj(x), ("ids", n))
+    for p, q in [(0, n - 1), (n - 2, n - 1), (n // 3, n // 2)]:
+        if p == q:
+            continue
+        d = x.copy()
+        d[q] = d[p]
+        same(ixp.check_inj(T(d, dev)), oracle.check_inj(d), ("ids-dup", n, p, q))
+    if n >= 8:
+        d = x.copy()
+        d[n - 1] = d[3]
+        d[n // 2] = d[n // 4]
+        d[7] = -1
+        d[n - 3] = -1  # the value -1 keeps its pair in the header
+        same(ixp.check_inj(T(d, dev)), oracle.check_inj(d), ("ids-several", n))
+        lo, hi = int(np.sort(x)[n // 4]), int(np.sort(x)[3 * n // 4])
+        same(ixp.check_inj(T(d, dev), lo, hi), oracle.check_inj(d, lo, hi), ("ids-rcd", n))
+    rng = np.random.default_rng(n + 1)
+    w = rng.integers(-2**31, 2**31, size=n, dtype=np.int64).astype(np.int32)
+    same(ixp.check_inj(T(w, dev)), oracle.check_inj(w), ("int32-wide", n))
+    e = x.copy()
+    e[0] = I64MIN
+    e[n - 1] = I64MAX  # the span is all 2^64 values
+    same(ixp.check_inj(T(e, dev)), oracle.check_inj(e), ("full-range", n))
+    e[n // 2] = I64MAX
+    same(ixp.check_inj(T(e, dev)), oracle.check_inj(e), ("full-range-dup", n))
 
 
 @pytest.mark.parametrize("dtype", [np.int32, np.int64])
