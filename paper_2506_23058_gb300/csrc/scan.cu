@@ -1380,6 +1380,113 @@ __global__ void __launch_bounds__(TB, sizeof(ZT) > sizeof(KT) ? 3 : 4) filtpart_
     }
 }
 
+// The same tile pass for the common form (int32 keys and Z, filter TRUE, predicate
+// key < b, 16-byte aligned inputs, n <= INT32_MAX), written for few instructions
+// per element: a thread takes 16 consecutive elements of the tile (four 16-byte
+// loads), so one warp scan of the threads' counts gives every rank, which then runs
+// as a counter over the thread's elements; Z - rank is taken modulo 2^32,
+// which is exact here because Z and every expected destination lie in the int32
+// range (Z - rank equals the tile constant modulo 2^32 only when Z is the expected
+// destination), so no element needs a separate negative guard; the folds are
+// branch-free min / max updates. Records the same rec[t], tile_prefix[t] and
+// dropped-element minimum (none: every element is kept) as filtpart_tile_kernel.
+__global__ void __launch_bounds__(TB, 4) filtpart_tile_lt_kernel(const int32_t *__restrict__ z, int64_t n,
+                                                                const int32_t *__restrict__ keys, int32_t b,
+                                                                unsigned long long *tile_prefix, longlong2 *rec) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 4;
+    constexpr int PER = SUB * V;  // consecutive elements per thread
+    constexpr int TILE = TB * PER;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ int s_r[4][TB / 32];
+    const int64_t t = blockIdx.x;
+    const int64_t t0 = t * TILE;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int64_t e0 = t0 + (int64_t)threadIdx.x * PER;  // this thread's first element
+    int zz[PER];
+    unsigned kt = 0, kk;
+    if (e0 + PER <= n) {
+#pragma unroll
+        for (int u = 0; u < SUB; u++) {
+            const int4 kv = __ldcs(reinterpret_cast<const int4 *>(keys + e0) + u);
+            const int4 zq = __ldcs(reinterpret_cast<const int4 *>(z + e0) + u);
+            kt |= ((unsigned)(kv.x < b) | (unsigned)(kv.y < b) << 1 | (unsigned)(kv.z < b) << 2 |
+                   (unsigned)(kv.w < b) << 3) << (u * V);
+            zz[u * V] = zq.x;
+            zz[u * V + 1] = zq.y;
+            zz[u * V + 2] = zq.z;
+            zz[u * V + 3] = zq.w;
+        }
+        kk = (1u << PER) - 1u;
+    } else {
+        const int c = e0 < n ? (int)(n - e0) : 0;
+#pragma unroll
+        for (int k = 0; k < PER; k++) {
+            const bool in = k < c;
+            zz[k] = in ? z[e0 + k] : 0;
+            kt |= (unsigned)(in && keys[e0 + k] < b) << k;
+        }
+        kk = (1u << c) - 1u;
+    }
+    // this thread's trues and kept before it in the tile: one warp scan, then the warps
+    const unsigned x = (unsigned)__popc(kt) | ((unsigned)__popc(kk) << 16);
+    unsigned y = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned o = __shfl_up_sync(FULL, y, d);
+        if (l >= d) y += o;
+    }
+    if (l == 31) s_w[w] = y;
+    __syncthreads();
+    unsigned wpre = 0, tot = 0;
+#pragma unroll
+    for (int i = 0; i < TB / 32; i++) {
+        const unsigned c = s_w[i];
+        wpre += i < w ? c : 0u;
+        tot += c;
+    }
+    const unsigned pre = wpre + y - x;
+    unsigned rt = pre & 0xffffu, rk = pre >> 16;
+    int tmn = INT32_MAX, tmx = INT32_MIN, fmn = INT32_MAX, fmx = INT32_MIN;
+#pragma unroll
+    for (int k = 0; k < PER; k++) {
+        const bool kept = (kk >> k) & 1u;
+        const bool tr = (kt >> k) & 1u;
+        const int q = (int)((unsigned)zz[k] - (tr ? rt : rk - rt));
+        tmn = (kept && tr) ? min(tmn, q) : tmn;
+        tmx = (kept && tr) ? max(tmx, q) : tmx;
+        fmn = (kept && !tr) ? min(fmn, q) : fmn;
+        fmx = (kept && !tr) ? max(fmx, q) : fmx;
+        rt += tr ? 1u : 0u;
+        rk += kept ? 1u : 0u;
+    }
+    tmn = __reduce_min_sync(FULL, tmn);
+    tmx = __reduce_max_sync(FULL, tmx);
+    fmn = __reduce_min_sync(FULL, fmn);
+    fmx = __reduce_max_sync(FULL, fmx);
+    if (l == 0) {
+        s_r[0][w] = tmn;
+        s_r[1][w] = tmx;
+        s_r[2][w] = fmn;
+        s_r[3][w] = fmx;
+    }
+    __syncthreads();
+    if (w == 0) {
+        int a = l < TB / 32 ? s_r[0][l] : INT32_MAX, c = l < TB / 32 ? s_r[1][l] : INT32_MIN;
+        int d = l < TB / 32 ? s_r[2][l] : INT32_MAX, e = l < TB / 32 ? s_r[3][l] : INT32_MIN;
+        a = __reduce_min_sync(FULL, a);
+        c = __reduce_max_sync(FULL, c);
+        d = __reduce_min_sync(FULL, d);
+        e = __reduce_max_sync(FULL, e);
+        if (l == 0) {
+            tile_prefix[t] = widen(tot);
+            // (INT32_MAX, INT32_MIN): no element of the class
+            rec[t] = make_longlong2(a > c ? FP_NONE : (a == c && a >= 0 ? (long long)a : FP_BAD),
+                                    d > e ? FP_NONE : (d == e && d >= 0 ? (long long)d : FP_BAD));
+        }
+    }
+}
+
 // After the tile scan: a tile passes when its recorded constants are P_t and
 // T + F_t; any failing tile, or a dropped Z inside [0, N), raises the flag that
 // enables the exact pass.
@@ -1841,11 +1948,22 @@ static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, i
         if (nt > 0) {
             longlong2 *rec = reinterpret_cast<longlong2 *>(W.L.st);
             bool narrow = false;
+            if constexpr (sizeof(ZT) == 4 && sizeof(KT) == 4) {
+                // the common form: filter TRUE, predicate key < b, aligned int32 arrays
+                if (n <= INT32_MAX && filt.kind == IXP_P_TRUE && part.kind == IXP_P_LT && keys && aligned16(keys) &&
+                    aligned16(z) && part.b > (long long)INT32_MIN && part.b <= (long long)INT32_MAX) {
+                    narrow = true;
+                    filtpart_tile_lt_kernel<<<(unsigned)nt, TB, 0, st>>>((const int32_t *)z, n,
+                                                                         (const int32_t *)keys, (int32_t)part.b,
+                                                                         W.tile_prefix, rec);
+                }
+            }
             if constexpr (sizeof(ZT) == 4) {
-                narrow = n <= INT32_MAX;
-                if (narrow)
+                if (!narrow && n <= INT32_MAX) {
+                    narrow = true;
                     filtpart_tile_kernel<KT, ZT, int32_t><<<(unsigned)nt, TB, 0, st>>>(
                         z, n, keys, dpred(filt), dpred(part), W.tile_prefix, rec, W.h, vec);
+                }
             }
             if (!narrow)
                 filtpart_tile_kernel<KT, ZT, int64_t><<<(unsigned)nt, TB, 0, st>>>(z, n, keys, dpred(filt),

@@ -559,6 +559,30 @@ def test_partition_segmented(ixp, dev, n, m, kt):
     assert np.array_equal(r["payload_out"].cpu().numpy(), o["payload_out"])
 
 
+@pytest.mark.parametrize("p", [0.5, 0.01, 0.999])
+@pytest.mark.parametrize("n", [1, 5, 4096, 4099, 65536 * 3 + 7, 1_000_003])
+def test_filtpart_lt_int32(ixp, dev, n, p):
+    """InvFiltPart of a partition by key < b (int32 keys and Z, no filter: the form
+    of the partition's own index array) against the oracle: correct, two entries
+    swapped, an entry off by one, negative entries and entries that wrap around
+    modulo 2^32 (Z - rank computed in 32 bits), a wrong last entry of a ragged tail."""
+    rng = np.random.default_rng(n + int(p * 1000))
+    keys = synth.keys_uniform(n, 710 + n)
+    part = ("lt", 0, synth.bernoulli_threshold(p))
+    z = oracle.partition(keys, part, out_dtype=np.int32)["indices"]
+    cases = {"ok": z.copy()}
+    if n >= 2:
+        s = z.copy(); a, b = rng.integers(0, n, size=2); s[a], s[b] = s[b], s[a]; cases["swap"] = s
+        s = z.copy(); s[n // 2] += 1; cases["plus1"] = s
+        s = z.copy(); s[n // 3] = -1; cases["neg"] = s
+        s = z.copy(); s[n // 4] = np.int32(int(s[n // 4]) - 2**31); cases["wrap"] = s
+        s = z.copy(); s[rng.integers(0, n)] = np.iinfo(np.int32).min; cases["min"] = s
+        s = z.copy(); s[n - 1] = n; cases["last"] = s
+    for name, zz in cases.items():
+        same(ixp.check_filtpart(T(zz, dev), T(keys, dev), part=part), oracle.check_filtpart(zz, keys, part=part),
+             (name, n, p))
+
+
 @pytest.mark.parametrize("zt", [np.int32, np.int64])
 @pytest.mark.parametrize("n", [1, 6, 4097, 65536, 100003])
 def test_filtpart(ixp, dev, n, zt):
