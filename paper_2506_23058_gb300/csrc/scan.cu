@@ -1010,6 +1010,370 @@ __device__ __forceinline__ void tile_segments(const int64_t *off, int64_t nseg, 
     __syncthreads();
 }
 
+// =========================================== segmented tiles, consecutive layout
+// The segmented count, partition and InvFiltPart passes with the element layout of
+// the flat InvFiltPart kernel: thread j of a tile takes the SUB * V consecutive
+// elements t0 + j * SUB * V ..., so one warp scan of the threads' packed counts
+// gives every rank and ranks run as counters over the thread's elements. The
+// segment starts that fall in the tile are listed in shared memory (positions in
+// increasing order; an empty segment repeats its position); a thread finds the
+// segment of its first element by a binary search of the list and then walks it,
+// loading a segment's counts only when the walk reaches its start. The tile sizes
+// and the tile_prefix / seg_cnt layouts are those of the other segmented kernels.
+constexpr int SG_MAXS = 4096;  // listed starts per tile; a tile with more walks the offsets in memory
+
+struct SegList {
+    int64_t ks;  // segment index of the list's first entry
+    int ns;      // entries listed (-1: more than SG_MAXS)
+};
+
+// Lists the starts off[k] in [t0, t1) (all threads call it); lb = the first k with
+// off[k] >= t0, from the per-tile table.
+__device__ __forceinline__ SegList seg_list(const int64_t *__restrict__ off, int64_t nseg, int64_t t0, int64_t t1,
+                                            int64_t lb, int *s_start, int64_t *s_ks, int *s_ns) {
+    if (threadIdx.x == 0) {
+        *s_ks = lb;
+        *s_ns = 0;
+    }
+    __syncthreads();
+    const int64_t ks = *s_ks;
+    for (int64_t k = ks + threadIdx.x; k < nseg; k += blockDim.x) {
+        const int64_t o = __ldg(off + k);
+        if (o >= t1) break;
+        const int64_t j = k - ks;
+        if (j < SG_MAXS) s_start[j] = (int)(o - t0);
+        atomicMax(s_ns, j < SG_MAXS ? (int)(j + 1) : SG_MAXS + 1);
+    }
+    __syncthreads();
+    SegList L;
+    L.ks = ks;
+    L.ns = *s_ns > SG_MAXS ? -1 : *s_ns;
+    return L;
+}
+
+// Segment walker of one thread: k = the segment of the current element (the last k
+// with off[k] <= i), and the counts of segment k.
+struct SegWalk {
+    int64_t k;      // current segment
+    int next;       // index in the tile's list of the next start not yet passed
+    int64_t ek;     // off[k]
+    int64_t ctk;    // trues before the segment (global, kept and true)
+    int64_t ckk;    // kept before the segment
+    int64_t tk;     // kept trues in the segment
+};
+
+__device__ __forceinline__ void seg_load(SegWalk &W, const int64_t *__restrict__ off, int64_t nseg,
+                                         const unsigned long long *__restrict__ seg_cnt) {
+    const int64_t k = W.k < 0 ? 0 : (W.k >= nseg ? nseg - 1 : W.k);  // stays in bounds for invalid offsets
+    const unsigned long long a0 = __ldg(seg_cnt + k), a1 = __ldg(seg_cnt + k + 1);
+    W.ek = __ldg(off + k);
+    W.ctk = (int64_t)(a0 & 0xffffffffull);
+    W.ckk = (int64_t)(a0 >> 32);
+    W.tk = (int64_t)(a1 & 0xffffffffull) - W.ctk;
+}
+
+// Starts the walk at in-tile position r0.
+__device__ __forceinline__ void seg_begin(SegWalk &W, const SegList &L, const int *s_start, int r0, int64_t t0,
+                                          const int64_t *__restrict__ off, int64_t nseg,
+                                          const unsigned long long *__restrict__ seg_cnt) {
+    if (L.ns >= 0) {
+        int lo = 0, hi = L.ns;  // number of listed starts <= r0
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_start[mid] <= r0) lo = mid + 1;
+            else hi = mid;
+        }
+        W.next = lo;
+        W.k = L.ks - 1 + lo;
+    } else {
+        W.next = 0;
+        W.k = seg_of(off, nseg, t0 + r0);
+    }
+    seg_load(W, off, nseg, seg_cnt);
+}
+
+// Moves the walk to in-tile position r (increasing).
+__device__ __forceinline__ void seg_step(SegWalk &W, const SegList &L, const int *s_start, int r, int64_t t0,
+                                         const int64_t *__restrict__ off, int64_t nseg,
+                                         const unsigned long long *__restrict__ seg_cnt) {
+    bool moved = false;
+    if (L.ns >= 0) {
+        while (W.next < L.ns && s_start[W.next] <= r) {
+            W.next++;
+            W.k++;
+            moved = true;
+        }
+    } else {
+        while (W.k + 1 < nseg && __ldg(off + W.k + 1) <= t0 + r) {
+            W.k++;
+            moved = true;
+        }
+    }
+    if (moved) seg_load(W, off, nseg, seg_cnt);
+}
+
+// Masks of this thread's PER consecutive elements at e0 (bit j = element e0 + j).
+template <typename KT>
+__device__ __forceinline__ void seg_masks(const KT *__restrict__ keys, int64_t e0, int64_t n, int vec_ok, DPred filt,
+                                          DPred part, unsigned &kk, unsigned &kt, KT (&kv)[SUB][16 / sizeof(KT)]) {
+    constexpr int V = 16 / sizeof(KT);
+    kk = 0;
+    kt = 0;
+#pragma unroll
+    for (int u = 0; u < SUB; u++) {
+        const int64_t p0 = e0 + u * V;
+        load_slot<KT, V>(keys, p0, n, vec_ok, kv[u]);
+        const unsigned mk = pred_mask<KT, V>(filt, kv[u], p0, n);
+        kk |= mk << (u * V);
+        kt |= (mk & pred_mask<KT, V>(part, kv[u], p0, n)) << (u * V);
+    }
+}
+
+// Packed in-tile exclusive count (kept << 16 | kept true) of this thread's first
+// element, and the tile total, from one warp scan and the warp totals.
+__device__ __forceinline__ unsigned seg_thread_prefix(unsigned x, unsigned *s_w, unsigned &tot) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned y = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned o = __shfl_up_sync(FULL, y, d);
+        if (l >= d) y += o;
+    }
+    if (l == 31) s_w[w] = y;
+    __syncthreads();
+    unsigned wpre = 0;
+    tot = 0;
+#pragma unroll
+    for (int i = 0; i < TB / 32; i++) {
+        const unsigned c = s_w[i];
+        wpre += i < w ? c : 0u;
+        tot += c;
+    }
+    return wpre + y - x;
+}
+
+// Pass 1 with segments (consecutive layout): tile counts, and for every segment
+// start in the tile its in-tile exclusive count (seg_fix_kernel adds the prefix).
+template <typename KT>
+__global__ void __launch_bounds__(TB, 4) count_seg_kernel(const KT *__restrict__ keys, int64_t n, DPred filt,
+                                                       DPred part, const int64_t *__restrict__ off, int64_t nseg,
+                                                       const int64_t *__restrict__ tile_lb,
+                                                       unsigned long long *tile_prefix, unsigned long long *seg_cnt,
+                                                       int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int PER = SUB * V;
+    constexpr int TILE = TB * PER;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ unsigned s_pre[TB], s_kt[TB], s_kk[TB];
+    const int64_t t = blockIdx.x;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int64_t e0 = t0 + (int64_t)threadIdx.x * PER;
+    unsigned kk, kt;
+    KT kv[SUB][V];
+    seg_masks<KT>(keys, e0, n, vec_ok, filt, part, kk, kt, kv);
+    unsigned tot;
+    const unsigned pre = seg_thread_prefix((unsigned)__popc(kt) | ((unsigned)__popc(kk) << 16), s_w, tot);
+    s_pre[threadIdx.x] = pre;
+    s_kt[threadIdx.x] = kt;
+    s_kk[threadIdx.x] = kk;
+    if (threadIdx.x == 0) tile_prefix[t] = widen(tot);
+    const int64_t ks = __ldg(tile_lb + t);
+    __syncthreads();
+    for (int64_t k = ks + threadIdx.x; k <= nseg; k += blockDim.x) {
+        const int64_t o = __ldg(off + k);
+        if (o >= t1) break;
+        if (o >= t0) {
+            const int r = (int)(o - t0), j = r / PER;
+            const unsigned below = (1u << (r % PER)) - 1u;
+            const unsigned c = s_pre[j] + (unsigned)__popc(s_kt[j] & below) + ((unsigned)__popc(s_kk[j] & below) << 16);
+            seg_cnt[k] = widen(c);
+        }
+    }
+}
+
+// Per-segment bases of the walk: within segment k, an element's destination is
+// bt + (kept trues before it, over the whole array) when it is a kept true, and
+// bf + (kept falses before it) when it is a kept false: bt = F_k - C_k and
+// bf = F_k + T_k - (F_k - C_k) = T_k + C_k, with F_k the kept elements and C_k
+// the kept trues before the segment, T_k the segment's kept trues (partition2L
+// keeps everything, so F_k = e_k there).
+template <typename AT>
+__device__ __forceinline__ void seg_bases(const SegWalk &W, AT &bt, AT &bf) {
+    bt = (AT)(W.ckk - W.ctk);
+    bf = (AT)(W.tk + W.ctk);
+}
+
+// Next listed start position after the walk's current one (INT_MAX: none).
+__device__ __forceinline__ int seg_next_pos(const SegWalk &W, const SegList &L, const int *s_start,
+                                            const int64_t *__restrict__ off, int64_t nseg, int64_t t0) {
+    if (L.ns >= 0) return W.next < L.ns ? s_start[W.next] : INT_MAX;
+    if (W.k + 1 >= nseg) return INT_MAX;
+    const int64_t o = __ldg(off + W.k + 1) - t0;
+    return o > (int64_t)INT_MAX ? INT_MAX : (int)(o < 0 ? 0 : o);
+}
+
+// Pass 2 of partition2L (consecutive layout): destinations (index form), and the
+// keys / payload rows moved to them. AT: the arithmetic type of the running
+// counts and destinations (int32 when n <= INT32_MAX).
+template <typename KT, typename OT, typename AT>
+__global__ void __launch_bounds__(TB, 4) partition_seg_kernel(
+    const KT *__restrict__ keys, int64_t n, DPred pred, const uint32_t *__restrict__ payload, int row_words,
+    OT *__restrict__ out_idx, KT *__restrict__ out_keys, uint32_t *__restrict__ out_payload,
+    const int64_t *__restrict__ off, int64_t nseg, const int64_t *__restrict__ tile_lb,
+    const unsigned long long *__restrict__ tile_prefix, const unsigned long long *__restrict__ seg_cnt, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int PER = SUB * V;
+    constexpr int TILE = TB * PER;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ int s_start[SG_MAXS];
+    __shared__ int64_t s_ks;
+    __shared__ int s_ns;
+    const int64_t t = blockIdx.x;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int64_t e0 = t0 + (int64_t)threadIdx.x * PER;
+    const DPred all{IXP_P_TRUE, 0, 0, nullptr};
+    unsigned kk, kt;
+    KT kv[SUB][V];
+    seg_masks<KT>(keys, e0, n, vec_ok, all, pred, kk, kt, kv);
+    unsigned tot;
+    const unsigned pre = seg_thread_prefix((unsigned)__popc(kt) | ((unsigned)__popc(kk) << 16), s_w, tot);
+    const SegList L = seg_list(off, nseg, t0, t1, __ldg(tile_lb + t), s_start, &s_ks, &s_ns);
+    const unsigned long long tp = tile_prefix[t];
+    AT ct = (AT)((tp & 0xffffffffull) + (pre & 0xffffu));                                  // trues before
+    AT cf = (AT)(((tp >> 32) - (tp & 0xffffffffull)) + ((pre >> 16) - (pre & 0xffffu)));  // falses before
+    const int r0 = (int)threadIdx.x * PER;
+    SegWalk W;
+    AT bt = 0, bf = 0;
+    int nxt = INT_MAX;
+    if (e0 < n) {
+        seg_begin(W, L, s_start, r0, t0, off, nseg, seg_cnt);
+        seg_bases<AT>(W, bt, bf);
+        nxt = seg_next_pos(W, L, s_start, off, nseg, t0);
+    }
+    const bool moves = out_keys || out_payload;
+    OT dst[PER];
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const bool c = (kt >> j) & 1u;
+        if (r0 + j >= nxt && e0 + j < n) {  // a segment starts here: move the walk
+            seg_step(W, L, s_start, r0 + j, t0, off, nseg, seg_cnt);
+            seg_bases<AT>(W, bt, bf);
+            nxt = seg_next_pos(W, L, s_start, off, nseg, t0);
+        }
+        const AT d = c ? bt + ct : bf + cf;
+        dst[j] = (OT)d;
+        ct += c ? 1 : 0;
+        cf += c ? 0 : 1;
+        if (moves && e0 + j < n && d >= 0 && (int64_t)d < n) {  // d is outside [0, n) only for invalid offsets
+            const int64_t i = e0 + j;
+            if (out_keys) out_keys[d] = kv[j / V][j % V];
+            if (out_payload)
+                for (int c2 = 0; c2 < row_words; c2++) out_payload[(int64_t)d * row_words + c2] = payload[i * row_words + c2];
+        }
+    }
+    if (out_idx) {
+        if (vec_ok && e0 + PER <= n) {
+            if (sizeof(OT) == 4) {
+#pragma unroll
+                for (int u = 0; u < PER / 4; u++)
+                    __stcs(reinterpret_cast<int4 *>(out_idx + e0) + u,
+                           make_int4((int)dst[4 * u], (int)dst[4 * u + 1], (int)dst[4 * u + 2], (int)dst[4 * u + 3]));
+            } else {
+#pragma unroll
+                for (int u = 0; u < PER / 2; u++)
+                    __stcs(reinterpret_cast<longlong2 *>(out_idx + e0) + u,
+                           make_longlong2((long long)dst[2 * u], (long long)dst[2 * u + 1]));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < PER; j++)
+                if (e0 + j < n) out_idx[e0 + j] = dst[j];
+        }
+    }
+}
+
+// Segmented InvFiltPart check, pass 2 (consecutive layout): the smallest i whose Z
+// is not its expected destination (kept) or lies inside [0, N) (dropped).
+template <typename KT, typename ZT, typename AT>
+__global__ void __launch_bounds__(TB, 4) filtpart_seg_kernel(
+    const ZT *__restrict__ z, int64_t n, const KT *__restrict__ keys, DPred filt, DPred part,
+    const int64_t *__restrict__ off, int64_t nseg, const int64_t *__restrict__ tile_lb,
+    const unsigned long long *__restrict__ tile_prefix, const unsigned long long *__restrict__ seg_cnt, Hdr *h,
+    int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    constexpr int V = 16 / sizeof(KT);
+    constexpr int PER = SUB * V;
+    constexpr int TILE = TB * PER;
+    __shared__ unsigned s_w[TB / 32];
+    __shared__ int s_start[SG_MAXS];
+    __shared__ int64_t s_ks;
+    __shared__ int s_ns;
+    const int64_t t = blockIdx.x;
+    const int64_t t0 = t * TILE, t1 = min(n, t0 + TILE);
+    const int64_t e0 = t0 + (int64_t)threadIdx.x * PER;
+    unsigned kk, kt;
+    KT kv[SUB][V];
+    seg_masks<KT>(keys, e0, n, vec_ok, filt, part, kk, kt, kv);
+    ZT zz[PER];
+    const bool zvec = vec_ok && e0 + PER <= n && (reinterpret_cast<uintptr_t>(z + e0) & 15u) == 0;
+    if (zvec) {
+#pragma unroll
+        for (int u = 0; u < PER * (int)sizeof(ZT) / 16; u++) {
+            if constexpr (sizeof(ZT) == 4) {
+                const int4 q = __ldcs(reinterpret_cast<const int4 *>(z + e0) + u);
+                zz[4 * u] = q.x;
+                zz[4 * u + 1] = q.y;
+                zz[4 * u + 2] = q.z;
+                zz[4 * u + 3] = q.w;
+            } else {
+                const longlong2 q = __ldcs(reinterpret_cast<const longlong2 *>(z + e0) + u);
+                zz[2 * u] = q.x;
+                zz[2 * u + 1] = q.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < PER; j++) zz[j] = e0 + j < n ? z[e0 + j] : (ZT)0;
+    }
+    unsigned tot;
+    const unsigned pre = seg_thread_prefix((unsigned)__popc(kt) | ((unsigned)__popc(kk) << 16), s_w, tot);
+    const SegList L = seg_list(off, nseg, t0, t1, __ldg(tile_lb + t), s_start, &s_ks, &s_ns);
+    const unsigned long long tp = tile_prefix[t];
+    AT ct = (AT)((tp & 0xffffffffull) + (pre & 0xffffu));                                  // kept trues before
+    AT cf = (AT)(((tp >> 32) - (tp & 0xffffffffull)) + ((pre >> 16) - (pre & 0xffffu)));  // kept falses before
+    const int64_t Ntot = (int64_t)(h->total >> 32);
+    const int r0 = (int)threadIdx.x * PER;
+    SegWalk W;
+    AT bt = 0, bf = 0;
+    int nxt = INT_MAX;
+    if (e0 < n) {
+        seg_begin(W, L, s_start, r0, t0, off, nseg, seg_cnt);
+        seg_bases<AT>(W, bt, bf);
+        nxt = seg_next_pos(W, L, s_start, off, nseg, t0);
+    }
+    int bad = INT_MAX;  // position in the thread's run
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const bool kept = (kk >> j) & 1u, c = (kt >> j) & 1u;
+        if (r0 + j >= nxt && e0 + j < n) {  // a segment starts here: move the walk
+            seg_step(W, L, s_start, r0 + j, t0, off, nseg, seg_cnt);
+            seg_bases<AT>(W, bt, bf);
+            nxt = seg_next_pos(W, L, s_start, off, nseg, t0);
+        }
+        const AT ref = c ? bt + ct : bf + cf;
+        const int64_t zi = (int64_t)zz[j];
+        const bool wrong = kept ? zi != (int64_t)ref : (zi >= 0 && zi < Ntot);
+        if (wrong && e0 + j < n) bad = min(bad, j);
+        ct += c ? 1 : 0;
+        cf += (kept && !c) ? 1 : 0;
+    }
+    __shared__ unsigned long long sm[TB / 32];
+    const unsigned long long r = block_max_u64(bad == INT_MAX ? 0ull : enc_first(e0 + bad), sm);
+    if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+}
+
 // Pass 2 of the partition: destinations, and the scattered keys/payload.
 template <typename KT, typename OT, bool SEG>
 __global__ void __launch_bounds__(TB) partition_write_kernel(
@@ -1775,6 +2139,7 @@ struct TileWs {
     unsigned long long *tile_prefix;
     unsigned long long *seg_cnt;
     unsigned long long *gtot;  // per group of TS_G tiles
+    int64_t *tile_lb;          // per tile: first k with off[k] >= the tile's first element
     size_t bytes;
 };
 
@@ -1792,6 +2157,8 @@ static TileWs tile_ws(void *ws, int64_t ntiles, int64_t nseg) {
     o += round256((size_t)(nseg + 1) * 8);
     r.gtot = (unsigned long long *)(p + o);
     o += round256((size_t)((ntiles + TS_G - 1) / TS_G + 1) * 8);
+    r.tile_lb = (int64_t *)(p + o);
+    o += nseg > 0 ? round256((size_t)(ntiles + 1) * 8) : 0;
     r.bytes = o;
     return r;
 }
@@ -1864,9 +2231,15 @@ static int run_counts(const KT *keys, int64_t n, DPred filt, DPred part, ixp_seg
     const bool seg = segs.offsets != nullptr;
     if (cudaMemsetAsync(W.h, 0, HDR_BYTES, st) != cudaSuccess) return IXP_E_CUDA;
     if (nt > 0) {
-        if (seg)
-            count_kernel<KT, true><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, segs.offsets, segs.nseg,
-                                                               W.tile_prefix, W.seg_cnt, vec);
+        if (seg) {
+            // first segment index per tile, from one pass over the offsets (0 fills
+            // what invalid offsets leave unset)
+            if (cudaMemsetAsync(W.tile_lb, 0, (size_t)(nt + 1) * 8, st) != cudaSuccess) return IXP_E_CUDA;
+            const int g = (int)std::max<int64_t>(1, std::min<int64_t>((segs.nseg + 256) / 256, 4096));
+            chunk_lb_kernel<TB * SUB * V><<<g, 256, 0, st>>>(segs.offsets, segs.nseg, n, W.tile_lb);
+            count_seg_kernel<KT><<<(unsigned)nt, TB, 0, st>>>(keys, n, filt, part, segs.offsets, segs.nseg,
+                                                             W.tile_lb, W.tile_prefix, W.seg_cnt, vec);
+        }
         else
             count_tiles_kernel<KT><<<(unsigned)((nt + CT - 1) / CT), TB, 0, st>>>(keys, n, filt, part, nt,
                                                                                 W.tile_prefix, vec);
@@ -1918,9 +2291,17 @@ static int run_partition(const KT *keys, int64_t n, ixp_pred pred, const void *p
         }
     } else if (nt > 0) {
         if (seg)
-            partition_write_kernel<KT, OT, true><<<(unsigned)nt, TB, 0, st>>>(
-                keys, n, dpred(pred), (const uint32_t *)payload, row_bytes / 4, out_idx, out_keys,
-                (uint32_t *)out_payload, segs.offsets, segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec);
+        {
+            const int v2 = vec && (!out_idx || aligned16(out_idx));
+            if (n <= INT32_MAX)
+                partition_seg_kernel<KT, OT, int32_t><<<(unsigned)nt, TB, 0, st>>>(
+                    keys, n, dpred(pred), (const uint32_t *)payload, row_bytes / 4, out_idx, out_keys,
+                    (uint32_t *)out_payload, segs.offsets, segs.nseg, W.tile_lb, W.tile_prefix, W.seg_cnt, v2);
+            else
+                partition_seg_kernel<KT, OT, int64_t><<<(unsigned)nt, TB, 0, st>>>(
+                    keys, n, dpred(pred), (const uint32_t *)payload, row_bytes / 4, out_idx, out_keys,
+                    (uint32_t *)out_payload, segs.offsets, segs.nseg, W.tile_lb, W.tile_prefix, W.seg_cnt, v2);
+        }
         else
             partition_write_kernel<KT, OT, false><<<(unsigned)nt, TB, 0, st>>>(
                 keys, n, dpred(pred), (const uint32_t *)payload, row_bytes / 4, out_idx, out_keys,
@@ -1983,8 +2364,14 @@ static int run_filtpart(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, i
     rc = run_counts<KT>(keys, n, dpred(filt), dpred(part), segs, W, nt, vec, st);
     if (rc) return rc;
     if (nt > 0) {
-        filtpart_cmp_kernel<KT, ZT, true><<<(unsigned)nt, TB, 0, st>>>(
-            z, n, keys, dpred(filt), dpred(part), segs.offsets, segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec, 0, 0);
+        if (n <= INT32_MAX)
+            filtpart_seg_kernel<KT, ZT, int32_t><<<(unsigned)nt, TB, 0, st>>>(
+                z, n, keys, dpred(filt), dpred(part), segs.offsets, segs.nseg, W.tile_lb, W.tile_prefix, W.seg_cnt,
+                W.h, vec);
+        else
+            filtpart_seg_kernel<KT, ZT, int64_t><<<(unsigned)nt, TB, 0, st>>>(
+                z, n, keys, dpred(filt), dpred(part), segs.offsets, segs.nseg, W.tile_lb, W.tile_prefix, W.seg_cnt,
+                W.h, vec);
         filtpart_cmp_kernel<KT, ZT, true><<<1, TB, 0, st>>>(z, n, keys, dpred(filt), dpred(part), segs.offsets,
                                                            segs.nseg, W.tile_prefix, W.seg_cnt, W.h, vec, 1, 0);
     }

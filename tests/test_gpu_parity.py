@@ -559,6 +559,46 @@ def test_partition_segmented(ixp, dev, n, m, kt):
     assert np.array_equal(r["payload_out"].cpu().numpy(), o["payload_out"])
 
 
+def crowded_offsets(rng, n):
+    """Segments that stress the per-tile lists of segment starts: a run of size-1
+    segments, 10000 empty segments at one position (more starts than a tile holds),
+    empty segments at 0 and at n, and a few long segments."""
+    cuts = [0, 0, 0]
+    cuts += list(range(1, 3000))                        # size-1 segments
+    cuts += [5000] * 10000                              # empty segments at one position
+    cuts += sorted(rng.integers(5001, n, size=40).tolist())
+    cuts += [n, n]
+    return np.array(cuts + [n], np.int64)
+
+
+@pytest.mark.parametrize("kt", [np.int32, np.int64])
+def test_partition_and_filtpart_crowded_segments(ixp, dev, kt):
+    n = 200_003
+    rng = np.random.default_rng(77)
+    off = crowded_offsets(rng, n)
+    m = off.shape[0] - 1
+    keys = synth.keys_uniform(n, 78).astype(kt)
+    pay = synth.payload_f32(n, 79)
+    p = ("lt", 0, synth.bernoulli_threshold(0.4))
+    r = ixp.partition(T(keys, dev), p, payload=T(pay, dev), offsets=T(off, dev))
+    o = oracle.partition(keys, p, payload=pay, offsets=off)
+    assert np.array_equal(r["indices"].cpu().numpy(), o["indices"])
+    assert np.array_equal(r["num_true"].cpu().numpy(), o["num_true"][:m])
+    assert np.array_equal(r["keys_out"].cpu().numpy(), o["keys_out"])
+    assert np.array_equal(r["payload_out"].cpu().numpy(), o["payload_out"])
+    z = o["indices"].astype(np.int64)
+    for trial in range(4):
+        zz = z.copy()
+        if trial == 1:
+            zz[4999] += 1
+        if trial == 2:
+            zz[5000], zz[5001] = zz[5001], zz[5000]
+        if trial == 3:
+            zz[1500] = -3
+        g = ixp.check_filtpart(T(zz, dev), T(keys, dev), part=p, offsets=T(off, dev))
+        same(g, oracle.check_filtpart(zz, keys, part=p, offsets=off), ("crowded", trial))
+
+
 @pytest.mark.parametrize("p", [0.5, 0.01, 0.999])
 @pytest.mark.parametrize("n", [1, 5, 4096, 4099, 65536 * 3 + 7, 1_000_003])
 def test_filtpart_lt_int32(ixp, dev, n, p):
