@@ -455,7 +455,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and backward forms")
     ap.add_argument("--no-ceilings", action="store_true", help="skip the hardware-rate microbenchmarks")
     ap.add_argument("--extra", default="", choices=["", "partition2", "smallest_pairs", "classes", "backward", "segmented",
-                                                     "any_span"],
+                                                     "any_span", "batched"],
                     help="run only this workload and print its result (profiling; --small: 2^26 elements for "
                          "classes, backward and segmented)")
     args = ap.parse_args()
@@ -471,6 +471,9 @@ def main():
         if args.extra == "classes":
             keys = synth.t_keys_uniform(n32, synth.seed_for(1) + 7, dev)
             res = run_classes(ixp, {"keys": keys}, n32, dev, None)
+        elif args.extra == "batched":
+            keys = synth.t_keys_uniform(n32, synth.seed_for(1) + 7, dev)
+            res = run_batched(ixp, {"keys": keys}, n32, dev, None, args)
         elif args.extra == "segmented":
             s = synth.seed_for(1)
             g = torch.Generator(device=dev)
@@ -675,7 +678,8 @@ def run_batched(ixp, inp, n32, dev, plain_ns_per_byte, args):
     ns_per_byte = ms * 1e6 / nbytes
     return {"workload": "4096 segments log-uniform [1, 2^20], n=%d int32, p=0.3, 1%% planted" % n, "ms": round(ms, 4),
             "alg_bytes": nbytes, "gbs": round(nbytes / (ms / 1e3) / 1e9, 1), "tuning": list(tuned),
-            "time_per_byte_vs_plain": round(ns_per_byte / plain_ns_per_byte, 3), "graph": True,
+            "time_per_byte_vs_plain": round(ns_per_byte / plain_ns_per_byte, 3) if plain_ns_per_byte else None,
+            "graph": True,
             "first_bad": res["first_bad"], "status": res["status"]}
 
 

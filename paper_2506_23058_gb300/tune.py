@@ -14,8 +14,11 @@ import torch
 
 from . import build as _build
 
-CANDIDATES = [(t, c, s, ch) for t in (256, 512) for c in (1, 2, 3, 4) for s in (14, 16, 18) for ch in (4, 8)
-              if not (t == 512 and c > 2)]
+# shared bitmaps up to 2^20 bits (128 KB) let every segment of up to 2^20 elements
+# be checked in shared memory; a launch shape is kept only while its CTAs' bitmaps
+# fit in 200 KB of one SM's shared memory
+CANDIDATES = [(t, c, s, ch) for t in (256, 512) for c in (1, 2, 3, 4) for s in (14, 16, 18, 19, 20) for ch in (4, 8)
+              if not (t == 512 and c > 2) and (1 << s) // 8 * c <= 200 * 1024]
 
 
 def cache_path() -> str:

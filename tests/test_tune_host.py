@@ -44,10 +44,13 @@ def tune(monkeypatch, tmp_path):
     return m
 
 
-def test_candidates_respect_the_thread_limit(tune):
+def test_candidates_respect_the_thread_and_shared_memory_limits(tune):
     assert len(tune.CANDIDATES) == len(set(tune.CANDIDATES))
     for t, c, s, ch in tune.CANDIDATES:
-        assert t * c <= 1024 and t in (256, 512) and ch in (4, 8) and s in (14, 16, 18)
+        assert t * c <= 1024 and t in (256, 512) and ch in (4, 8) and 14 <= s <= 20
+        assert (1 << s) // 8 * c <= 200 * 1024  # the CTAs' shared bitmaps fit one SM
+    # a 2^20-element segment can be checked in shared memory by some candidate
+    assert any(s == 20 for _, _, s, _ in tune.CANDIDATES)
 
 
 def test_fastest_candidate_is_kept_and_cached(tune):
