@@ -564,6 +564,7 @@ def main():
     if not args.no_ceilings:
         ceilings = measure_ceilings(ixp, dev)
         rows = n32 // 4  # rows of 8 float32 in the scatter / gather workload
+        dom = roofline["op"]
         if dom in ("scatter_rows8", "gather_rows8"):
             ach = rows / (per_op[dom]["ms"] / 1e3) / 1e9
             roofline["ceiling"] = {"kind": "random 32-byte rows (measured with a read-only kernel)",

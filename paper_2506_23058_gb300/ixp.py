@@ -254,20 +254,22 @@ def check_mono(x, cmp="le", offsets=None, *, seg_ok=None, out=None, ws=None, str
 
 
 HASH_SET_MAX_BYTES = 1 << 34  # the default workspace holds a hash set up to this size
+RCD_BITMAP_MAX_BITS = 1 << 30  # a finite Rcd up to this width gets a bitmap over all of it
 
 
 def check_inj(x, rcd_lo=I64MIN, rcd_hi=I64MAX, *, span=None, out=None, ws=None, stream=None) -> Verdict:
     """`span`: the largest value span the bitmap must cover (a wider span found in the
-    data reports IXP_E_SPAN). Default: the Rcd width when it is at most 4n + 4096;
-    otherwise any span: bitmaps for 4n + 4096 bits plus a hash set of 16 bytes per
-    slot (the power of two >= 2n slots) that decides wider spans, while that set
-    stays within HASH_SET_MAX_BYTES (n <= 2^29), else 4n + 4096 bits."""
+    data reports IXP_E_SPAN). Default: the Rcd width when it is at most
+    max(4n + 4096, RCD_BITMAP_MAX_BITS); otherwise any span: bitmaps for 4n + 4096
+    bits plus a hash set of 16 bytes per slot (the power of two >= 2n slots) that
+    decides wider spans, while that set stays within HASH_SET_MAX_BYTES
+    (n <= 2^29), else 4n + 4096 bits."""
     v = _verdict_buf(x.device, out)
     n = x.numel()
     extra = span
     if span is None:
         extra = 4 * n + 4096
-        if rcd_hi - rcd_lo + 1 <= extra:
+        if rcd_hi - rcd_lo + 1 <= max(extra, RCD_BITMAP_MAX_BITS):
             extra = rcd_hi - rcd_lo + 1
         elif 16 * max(2, 1 << max(0, (2 * n - 1).bit_length())) <= HASH_SET_MAX_BYTES:
             extra = -1
