@@ -7,10 +7,16 @@
 // The destination of a kept element i of segment k and class h is
 //     F_k + (kept elements of segment k with class < h) + (class-h elements of
 //     segment k before i),
-// and a dropped element's Z must lie outside [0, N). Flat arrays use three tiled
-// passes (per-tile class histograms; a scan of each class over the tiles with the
-// class bases; the comparison, where an element's rank inside its tile comes from
-// the lanes of its warp with the same class and per-warp class counters).
+// and a dropped element's Z must lie outside [0, N). Flat arrays with v <= 4 use
+// tiles of 4096 elements, 16 consecutive ones per thread: the check is one pass
+// that records, per tile and class, the constant Z - (rank in the tile), then a
+// pass that scans the tile counts and compares each constant with its class
+// prefix, and an element-by-element pass over the first failing tile only; the
+// partition counts the tiles, scans the counts and writes. Flat arrays with more
+// classes use three tiled passes (per-tile class histograms; a scan of each class
+// over the tiles with the class bases; the comparison, where an element's rank
+// inside its tile comes from the lanes of its warp with the same class and
+// per-warp class counters).
 // Segmented arrays give each segment to one block (claimed from a counter): its
 // class histogram, the class bases, then the comparison chunk by chunk with class
 // counters carried from chunk to chunk; F_k comes from a scan of the per-segment
@@ -18,6 +24,8 @@
 // into one word (i << 32 | expected + 1) whose smallest value wins, so no
 // separate witness pass is needed.
 #include <algorithm>
+#include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 #include "preds.cuh"
@@ -84,180 +92,636 @@ __global__ void __launch_bounds__(CL_THREADS) cl_count_kernel(const KT *__restri
     for (int c = threadIdx.x; c < v; c += CL_THREADS) cnt[(int64_t)c * nt + blockIdx.x] = s_h[c];
 }
 
-// Classes of 4 consecutive elements at p0 (16-byte key loads, one 4-byte class
-// load when aligned and in range), packed one byte each: class + 1, or 0 for an
-// element that is dropped or past n.
-template <typename KT>
-__device__ __forceinline__ unsigned cl_load4(const KT *__restrict__ keys, const uint8_t *__restrict__ cls,
-                                             const DPred &filt, int v, int64_t p0, int64_t n, int vec_ok) {
-    KT kv[4];
-    load_slot<KT, 4>(keys, p0, n, vec_ok, kv);
-    const unsigned kept = pred_mask<KT, 4>(filt, kv, p0, n);
-    unsigned cw;
-    if (vec_ok && p0 + 4 <= n) {
-        cw = __ldg(reinterpret_cast<const unsigned *>(cls + p0));
-    } else {
-        cw = 0;
-#pragma unroll
-        for (int k = 0; k < 4; k++)
-            if (p0 + k < n) cw |= (unsigned)__ldg(cls + p0 + k) << (8 * k);
-    }
-    unsigned out = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        const int c = (int)((cw >> (8 * k)) & 0xffu);
-        const unsigned cc = (unsigned)(c < v - 1 ? c : v - 1);
-        if ((kept >> k) & 1u) out |= (cc + 1u) << (8 * k);
-    }
-    return out;
+// ----------------------------------------------------------- flat, v <= 4
+// A thread takes the CL_PER consecutive elements of its tile slot (one 16-byte
+// class load, 16-byte key and Z loads), so one block scan of the threads' class
+// counts gives every element's rank, which then runs as a per-class counter.
+//
+// The check needs one pass over Z: for a kept element of class k at tile rank r,
+// Z - r must be the same constant C_k(t) for every class-k element of tile t, and
+// C_k(t) must equal base_k + (class-k elements of the tiles before t). The tile
+// pass records C_k(t) (or "several values") and each tile's class counts; a
+// decide pass scans the counts and compares; only the first failing tile (which
+// holds the first wrong element, since a tile whose constants all match and whose
+// dropped elements lie outside [0, N) has no wrong element) is revisited element
+// by element. The per-tile counts are also summed per range of tiles (atomic adds
+// into one counter pair per range), so the decide pass gets every range's prefix
+// without a second kernel.
+constexpr int CL_PER = CL_TILE / CL_THREADS;  // consecutive elements per thread
+static_assert(CL_PER == 16, "16 four-bit class codes per thread fill one 64-bit word");
+constexpr long long CL_NONE = LLONG_MIN;      // no element of the class in the tile
+constexpr long long CL_BAD = LLONG_MIN + 1;   // the class's Z - rank is not one constant
+constexpr int CL_MAX_RANGES = 1024;
+
+struct ClRec {
+    long long c[4];
+};
+
+// Tiles per decide thread so that at most CL_MAX_RANGES ranges of
+// CL_THREADS * tpt tiles cover the array.
+static inline int cl_tpt(int64_t nt) {
+    const int64_t per = (int64_t)CL_THREADS * CL_MAX_RANGES;
+    return (int)std::max<int64_t>(1, (nt + per - 1) / per);
 }
 
-// Per class k < 4: how many of the 4 packed elements have class k, one byte per
-// class (byte k of the result; at most 4 each).
-__device__ __forceinline__ unsigned cl_onehot4(unsigned packed) {
-    unsigned x = 0;
+struct Cl16Ws {
+    ulonglong2 *rs;               // per range: class counts (c0 | c1 << 32, c2 | c3 << 32)
+    unsigned long long *tcnt;     // per tile: class counts, 16 bits each
+    ClRec *rec;                   // per tile: C_k(t)
+    unsigned long long *dmin;     // per tile: smallest dropped Z, as uint64 (negative: huge)
+    ulonglong2 *pre;              // per tile: first destination of each class (32 bits each)
+    unsigned long long *codes;    // per thread slot of a tile: its 16 class codes (the partition's pass 1)
+    int tpt;
+    int64_t nr;                   // ranges
+    size_t clear;                 // bytes after the header that must start zeroed (the range counters)
+    size_t bytes;                 // bytes after the header
+};
+
+// Layout after the header: range counters | tile counts | records | dropped minima |
+// first destinations | class codes. With ws null only the sizes are filled in.
+static Cl16Ws cl16_ws(void *ws, int64_t n) {
+    const int64_t nt = (n + CL_TILE - 1) / CL_TILE;
+    Cl16Ws W;
+    W.tpt = cl_tpt(nt);
+    const int64_t R = (int64_t)W.tpt * CL_THREADS;
+    W.nr = (nt + R - 1) / R;
+    const size_t o_rs = 0, o_tc = o_rs + round256((size_t)W.nr * 16), o_rec = o_tc + round256((size_t)nt * 8),
+                 o_dm = o_rec + round256((size_t)nt * sizeof(ClRec)), o_pre = o_dm + round256((size_t)nt * 8);
+    const size_t o_cd = o_pre + round256((size_t)nt * 16);
+    W.clear = o_tc;
+    W.bytes = o_cd + round256((size_t)nt * CL_THREADS * 8);
+    char *p = ws ? (char *)ws + HDR_BYTES : nullptr;
+    W.rs = p ? (ulonglong2 *)(p + o_rs) : nullptr;
+    W.tcnt = p ? (unsigned long long *)(p + o_tc) : nullptr;
+    W.rec = p ? (ClRec *)(p + o_rec) : nullptr;
+    W.dmin = p ? (unsigned long long *)(p + o_dm) : nullptr;
+    W.pre = p ? (ulonglong2 *)(p + o_pre) : nullptr;
+    W.codes = p ? (unsigned long long *)(p + o_cd) : nullptr;
+    return W;
+}
+
+// Class codes of the thread's CL_PER elements from e0: four bits each, class + 1,
+// or 0 for an element that is dropped or past n. `full`: all in range and every
+// array 16-byte aligned. Four class bytes are clamped to v - 1 at once: with
+// d = (c | 0x80 per byte) - (v - 1 per byte) (no borrow crosses a byte), byte i
+// of (d | c) has its top bit set exactly when c_i >= v - 1.
+// The filter over the thread's CL_PER keys from e0, as a 16-bit mask (positions
+// at or past n are 0): one dispatch on the predicate kind for all of them.
+template <typename KT>
+__device__ __forceinline__ unsigned cl_kept16(const KT *__restrict__ keys, const DPred &filt, int64_t e0, int64_t n,
+                                              bool full) {
+    const unsigned valid = full || e0 + CL_PER <= n ? 0xffffu : (e0 >= n ? 0u : (1u << (unsigned)(n - e0)) - 1u);
+    if (filt.kind == IXP_P_TRUE) return valid;
+    if (filt.kind == IXP_P_FLAGS) {
+        unsigned m = 0;
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-        const unsigned b = (packed >> (8 * e)) & 0xffu;
-        x += b ? 1u << (8 * (b - 1u)) : 0u;
+        for (int e = 0; e < CL_PER; e++) m |= (unsigned)(((valid >> e) & 1u) && __ldg(filt.flags + e0 + e) != 0) << e;
+        return m;
     }
+    KT kv[CL_PER];
+#pragma unroll
+    for (int g = 0; g < CL_PER / 4; g++) {
+        KT k4[4];
+        load_slot<KT, 4>(keys, e0 + 4 * g, n, full ? 1 : 0, k4);
+#pragma unroll
+        for (int k = 0; k < 4; k++) kv[4 * g + k] = k4[k];
+    }
+    unsigned m = 0;
+    if (filt.kind == IXP_P_LT) {
+        if (sizeof(KT) == 4) {
+            if (filt.b > (long long)INT32_MAX) return valid;
+            if (filt.b <= (long long)INT32_MIN) return 0u;
+            const int32_t b = (int32_t)filt.b;
+#pragma unroll
+            for (int e = 0; e < CL_PER; e++) m |= (unsigned)((int32_t)kv[e] < b) << e;
+        } else {
+#pragma unroll
+            for (int e = 0; e < CL_PER; e++) m |= (unsigned)((int64_t)kv[e] < filt.b) << e;
+        }
+        return m & valid;
+    }
+    // MOD_EQ (floored remainder in [0, a))
+    if (filt.b < 0 || filt.b >= (long long)filt.a) return 0u;
+#pragma unroll
+    for (int e = 0; e < CL_PER; e++) {
+        if (sizeof(KT) == 4) {
+            int32_t r = (int32_t)kv[e] % filt.a;
+            r += r < 0 ? filt.a : 0;
+            m |= (unsigned)(r == (int32_t)filt.b) << e;
+        } else {
+            int64_t r = (int64_t)kv[e] % (int64_t)filt.a;
+            r += r < 0 ? (int64_t)filt.a : 0;
+            m |= (unsigned)(r == filt.b) << e;
+        }
+    }
+    return m & valid;
+}
+
+template <typename KT>
+__device__ __forceinline__ unsigned long long cl_codes16(const KT *__restrict__ keys, const uint8_t *__restrict__ cls,
+                                                         const DPred &filt, int v, int64_t e0, int64_t n, bool full) {
+    unsigned cw[4];
+    if (full) {
+        const uint4 c4 = __ldcs(reinterpret_cast<const uint4 *>(cls + e0));
+        cw[0] = c4.x;
+        cw[1] = c4.y;
+        cw[2] = c4.z;
+        cw[3] = c4.w;
+    } else {
+#pragma unroll
+        for (int g = 0; g < 4; g++) {
+            cw[g] = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (e0 + 4 * g + k < n) cw[g] |= (unsigned)cls[e0 + 4 * g + k] << (8 * k);
+        }
+    }
+    const unsigned kept = cl_kept16<KT>(keys, filt, e0, n, full);
+    const unsigned top4 = (unsigned)(v - 1) * 0x01010101u;
+    unsigned long long codes = 0;
+#pragma unroll
+    for (int g = 0; g < 4; g++) {
+        const unsigned kept4 = (kept >> (4 * g)) & 15u;
+        const unsigned c = cw[g];
+        const unsigned ge = (((c | 0x80808080u) - top4) | c) & 0x80808080u;
+        const unsigned gm = (ge >> 7) * 0xffu;                              // 0xff where c_i >= v - 1
+        const unsigned km = ((kept4 * 0x204081u) & 0x01010101u) * 0xffu;    // 0xff where kept
+        const unsigned b = (((c & ~gm) | (top4 & gm)) + 0x01010101u) & km;  // class + 1, or 0
+        const unsigned x = b | (b >> 4);
+        codes |= (unsigned long long)((x & 0xffu) | ((x >> 8) & 0xff00u)) << (16 * g);
+    }
+    return codes;
+}
+
+// Class counts of 16 codes (four-bit fields equal to k + 1), as lo = c0 | c1 << 16
+// and hi = c2 | c3 << 16; eq[k] gets bit 4e set when element e has class k.
+__device__ __forceinline__ void cl_count_codes(unsigned long long codes, unsigned &lo, unsigned &hi,
+                                               unsigned long long (&eq)[4]) {
+    constexpr unsigned long long ONES = 0x1111111111111111ull;
+    unsigned c[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const unsigned long long t = codes ^ (ONES * (unsigned long long)(k + 1));  // zero nibble: class k
+        unsigned long long u = t | (t >> 1);
+        u |= u >> 2;  // bit 0 of each nibble: the OR of its four bits
+        eq[k] = ~u & ONES;
+        c[k] = (unsigned)__popcll(eq[k]);
+    }
+    lo = c[0] | (c[1] << 16);
+    hi = c[2] | (c[3] << 16);
+}
+__device__ __forceinline__ void cl_count_codes(unsigned long long codes, unsigned &lo, unsigned &hi) {
+    unsigned long long eq[4];
+    cl_count_codes(codes, lo, hi, eq);
+}
+
+// In-thread class ranks: nibble e of the result is the number of elements before e
+// in the thread with e's class (0 for a dropped element). eq[k] * 0x1111...10
+// puts in nibble e the count of class-k elements before e (at most 15, so no
+// nibble carries), and eq[k] * 15 masks it to the class-k positions.
+template <int VS>
+__device__ __forceinline__ unsigned long long cl_ranks16(const unsigned long long (&eq)[4]) {
+    unsigned long long x = 0;
+#pragma unroll
+    for (int k = 0; k < VS; k++) x |= (eq[k] * 0x1111111111111110ull) & (eq[k] * 0xfull);
     return x;
 }
 
-// Small v (v <= VS), pass 1: lanes take 4 consecutive elements; class counts are
-// kept per lane and reduced over the warp at the end.
-template <typename KT, int VS>
-__global__ void __launch_bounds__(CL_THREADS) cl_count4_kernel(const KT *__restrict__ keys,
-                                                               const uint8_t *__restrict__ cls, int64_t n,
-                                                               DPred filt, int v, int64_t nt, int vec_ok,
-                                                               unsigned *__restrict__ cnt) {
-    IXP_KERNEL_ENTRY();
-    __shared__ unsigned s_h[VS];
-    if (threadIdx.x < VS) s_h[threadIdx.x] = 0u;
-    __syncthreads();
-    const int64_t t0 = blockIdx.x * (int64_t)CL_TILE;
-    static_assert(VS <= 4 && CL_TILE / CL_THREADS <= 252, "byte-packed class counters");
-    unsigned acc = 0;  // byte k: class-k elements of this lane (at most CL_TILE / CL_THREADS)
+// Exclusive block scan of the threads' packed class counts (16-bit fields; a tile
+// has at most CL_TILE elements of a class); the tile totals go to tlo / thi.
+__device__ __forceinline__ void cl_block_scan16(unsigned &lo, unsigned &hi, uint2 *s_w, unsigned &tlo,
+                                                unsigned &thi) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned ylo = lo, yhi = hi;
 #pragma unroll
-    for (int r = 0; r < CL_TILE / (4 * CL_THREADS); r++) {
-        const int64_t p0 = t0 + ((int64_t)r * CL_THREADS + threadIdx.x) * 4;
-        acc += cl_onehot4(cl_load4<KT>(keys, cls, filt, v, p0, n, vec_ok));
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned a = __shfl_up_sync(FULL, ylo, d), b = __shfl_up_sync(FULL, yhi, d);
+        if (l >= d) {
+            ylo += a;
+            yhi += b;
+        }
     }
-#pragma unroll
-    for (int k = 0; k < VS; k++) {
-        const unsigned t = __reduce_add_sync(FULL, (acc >> (8 * k)) & 0xffu);
-        if ((threadIdx.x & 31) == 0 && t) atomicAdd(&s_h[k], t);
-    }
+    if (l == 31) s_w[w] = make_uint2(ylo, yhi);
     __syncthreads();
-    if (threadIdx.x < v && threadIdx.x < VS) cnt[(int64_t)threadIdx.x * nt + blockIdx.x] = s_h[threadIdx.x];
+    unsigned plo = 0, phi = 0;
+    tlo = 0;
+    thi = 0;
+#pragma unroll
+    for (int i = 0; i < CL_WARPS; i++) {
+        const uint2 s = s_w[i];
+        plo += i < w ? s.x : 0u;
+        phi += i < w ? s.y : 0u;
+        tlo += s.x;
+        thi += s.y;
+    }
+    lo = plo + ylo - lo;
+    hi = phi + yhi - hi;
 }
 
-// Small v, pass 3: warp w takes 512 consecutive elements as 4 rounds of 128 (4 per
-// lane). In a round, each class's lane counts are scanned across the warp; the
-// warp's running class counts stay in registers; the warps' totals are scanned in
-// shared memory; then each element's destination is its class offset in the tile
-// plus the warp, lane and in-lane ranks.
-template <typename KT, typename ZT, bool WRITE, int VS>
-__global__ void __launch_bounds__(CL_THREADS, 4) cl_check4_kernel(const ZT *__restrict__ z, const KT *__restrict__ keys,
-                                                               const uint8_t *__restrict__ cls, int64_t n,
-                                                               DPred filt, int v, int64_t nt, int vec_ok,
-                                                               const unsigned *__restrict__ cnt,
-                                                               const unsigned long long *__restrict__ base, Hdr *h,
-                                                               ZT *__restrict__ dst) {
+// Widens 16-bit packed tile counts (c0 | c1 << 16 | c2 << 32 | c3 << 48) to two
+// words of 32-bit fields.
+__device__ __forceinline__ ulonglong2 cl_widen(unsigned long long c) {
+    return make_ulonglong2((c & 0xffffull) | (((c >> 16) & 0xffffull) << 32),
+                           ((c >> 32) & 0xffffull) | ((c >> 48) << 32));
+}
+
+__device__ __forceinline__ void cl_add_range(ulonglong2 *rs, unsigned long long tc) {
+    const ulonglong2 w = cl_widen(tc);
+    if (w.x) atomicAdd(&rs->x, w.x);
+    if (w.y) atomicAdd(&rs->y, w.y);
+}
+
+template <typename ZT>
+__device__ __forceinline__ void cl_load_z16(const ZT *__restrict__ z, int64_t e0, int64_t n, bool full,
+                                            ZT (&zz)[CL_PER]) {
+    if (full) {
+        if constexpr (sizeof(ZT) == 4) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int4 q = __ldcs(reinterpret_cast<const int4 *>(z + e0) + u);
+                zz[4 * u] = q.x;
+                zz[4 * u + 1] = q.y;
+                zz[4 * u + 2] = q.z;
+                zz[4 * u + 3] = q.w;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const longlong2 q = __ldcs(reinterpret_cast<const longlong2 *>(z + e0) + u);
+                zz[2 * u] = q.x;
+                zz[2 * u + 1] = q.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < CL_PER; e++) zz[e] = e0 + e < n ? z[e0 + e] : (ZT)-1;  // -1: never inside [0, N)
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T cl_warp_min(T x) {
+    if constexpr (sizeof(T) == 4) {
+        return __reduce_min_sync(FULL, x);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T y = __shfl_xor_sync(FULL, x, o);
+            x = y < x ? y : x;
+        }
+        return x;
+    }
+}
+template <typename T>
+__device__ __forceinline__ T cl_warp_max(T x) {
+    if constexpr (sizeof(T) == 4) {
+        return __reduce_max_sync(FULL, x);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const T y = __shfl_xor_sync(FULL, x, o);
+            x = y > x ? y : x;
+        }
+        return x;
+    }
+}
+
+// Check, tile pass. QT is the type Z - rank is taken in: int32 (modulo 2^32) when Z
+// is int32 and n <= INT32_MAX, since then Z and every expected destination lie in
+// the int32 range and Z - rank equals a destination's constant modulo 2^32 only
+// when Z is that destination; int64 otherwise (modulo 2^64, the same argument).
+// VS: classes handled (v <= VS).
+//
+// The tile's class-k constant C_k is the Z of its first class-k element (tile rank
+// 0), read back by the one thread that holds it and shared through shared memory;
+// then an element's expected Z is C_k + its tile rank: the thread's first rank
+// for the class (block scan), looked up by class in a per-thread row of shared
+// memory, plus its in-thread class rank (cl_ranks16). Any mismatch marks the tile
+// as failing; otherwise C_k is recorded for the decide pass.
+template <typename KT, typename ZT, typename QT, int VS>
+__global__ void __launch_bounds__(CL_THREADS, sizeof(ZT) == 4 ? 4 : 3) cl_tile_kernel(const ZT *__restrict__ z, const KT *__restrict__ keys,
+                                                             const uint8_t *__restrict__ cls, int64_t n, DPred filt,
+                                                             int v, int vec_ok, int64_t R,
+                                                             unsigned long long *__restrict__ tcnt,
+                                                             ClRec *__restrict__ rec,
+                                                             unsigned long long *__restrict__ dmin,
+                                                             ulonglong2 *__restrict__ rs) {
     IXP_KERNEL_ENTRY();
-    constexpr int R = CL_TILE / (4 * CL_THREADS);  // rounds of 4 elements per lane
-    static_assert(VS <= 4, "byte-packed class counters");
-    __shared__ unsigned s_rt[CL_WARPS][R];                   // byte k: class-k elements of the warp's round
-    __shared__ unsigned long long s_base[CL_WARPS][R][VS];   // destination of the round's first class-k element
-    __shared__ unsigned long long s_off[VS];
+    using UQ = typename std::make_unsigned<QT>::type;
+    __shared__ uint2 s_w[CL_WARPS];
+    __shared__ UQ s_c[VS];
+    __shared__ UQ s_dm[CL_WARPS];
+    __shared__ unsigned s_bad;
+    __shared__ UQ s_e[VS + 1][CL_THREADS];  // row q: expected Z of the thread's first class-(q - 1) element
+    const int64_t t = blockIdx.x;
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (threadIdx.x < VS) s_off[threadIdx.x] = threadIdx.x < v ? base[threadIdx.x] + cnt[(int64_t)threadIdx.x * nt + blockIdx.x] : 0ull;
-    const int64_t wbase = blockIdx.x * (int64_t)CL_TILE + (int64_t)w * (R * 128);
-    // per round: the lane's classes, and (one scan of the byte-packed counts, at
-    // most 128 per class) the class counts of the lanes below it
-    unsigned pk[R], lp[R];
+    const int64_t e0 = t * CL_TILE + (int64_t)threadIdx.x * CL_PER;
+    const bool full = vec_ok && e0 + CL_PER <= n;
+    if (threadIdx.x == 0) s_bad = 0u;
+    const unsigned long long codes = cl_codes16<KT>(keys, cls, filt, v, e0, n, full);
+    ZT zz[CL_PER];
+    cl_load_z16<ZT>(z, e0, n, full, zz);
+    unsigned lo, hi, tlo, thi;
+    unsigned long long eq[4];
+    cl_count_codes(codes, lo, hi, eq);
+    const unsigned has = (lo & 0xffffu ? 1u : 0u) | (lo >> 16 ? 2u : 0u) | (hi & 0xffffu ? 4u : 0u) | (hi >> 16 ? 8u : 0u);
+    cl_block_scan16(lo, hi, s_w, tlo, thi);
+    const unsigned rk[4] = {lo & 0xffffu, lo >> 16, hi & 0xffffu, hi >> 16};  // tile rank of the first one
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int64_t p0 = wbase + r * 128 + l * 4;
-        pk[r] = cl_load4<KT>(keys, cls, filt, v, p0, n, vec_ok);
-        const unsigned x = cl_onehot4(pk[r]);
-        unsigned y = x;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const unsigned o = __shfl_up_sync(FULL, y, d);
-            if (l >= d) y += o;
+    for (int k = 0; k < VS; k++)
+        if (((has >> k) & 1u) && rk[k] == 0u) {  // this thread holds the tile's first class-k element
+            const int f = (__ffsll((long long)eq[k]) - 1) >> 2;
+            s_c[k] = (UQ)(QT)z[e0 + f];
         }
-        lp[r] = y - x;
-        if (l == 31) s_rt[w][r] = y;
-    }
+    const unsigned long long xr = cl_ranks16<VS>(eq);
     __syncthreads();
-    // class k's elements lie in (warp, round) order inside the tile
-    if (threadIdx.x < VS) {
-        const int k = threadIdx.x;
-        unsigned long long run = s_off[k];
-        for (int ww = 0; ww < CL_WARPS; ww++)
+    s_e[0][threadIdx.x] = 0;
 #pragma unroll
-            for (int r = 0; r < R; r++) {
-                s_base[ww][r][k] = run;
-                run += (s_rt[ww][r] >> (8 * k)) & 0xffu;
-            }
+    for (int k = 0; k < VS; k++) s_e[k + 1][threadIdx.x] = s_c[k] + (UQ)rk[k];
+    bool bad = false;
+    UQ dm = (UQ)~(UQ)0;
+#pragma unroll
+    for (int e = 0; e < CL_PER; e++) {
+        const unsigned q = (unsigned)(codes >> (4 * e)) & 15u;
+        const UQ zv = (UQ)(QT)zz[e];
+        const UQ want = s_e[q][threadIdx.x] + (UQ)((xr >> (4 * e)) & 15u);
+        bad |= q != 0u && want != zv;
+        dm = q == 0u && zv < dm ? zv : dm;
     }
+    dm = cl_warp_min<UQ>(dm);
+    if (__any_sync(FULL, bad) && l == 0) s_bad = 1u;
+    if (l == 0) s_dm[w] = dm;
+    const unsigned thas = __reduce_or_sync(FULL, has);
+    __shared__ unsigned s_has[CL_WARPS];
+    if (l == 0) s_has[w] = thas;
     __syncthreads();
-    const int64_t N = (int64_t)(h->total >> 32);
-    int64_t bad = INT64_MAX, bref = 0;
+    if (threadIdx.x == 0) {
+        unsigned all = 0;
+        for (int i = 0; i < CL_WARPS; i++) all |= s_has[i];
+        ClRec out;
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int64_t p0 = wbase + r * 128 + l * 4;
-        ZT zv[4];
-        if (!WRITE) load_vec<ZT, 4>(z, p0, n, vec_ok, zv);
-        unsigned seen = lp[r];  // byte k: class-k elements before the next one of this lane
-        ZT out4[4];
+        for (int k = 0; k < 4; k++) out.c[k] = CL_NONE;
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            const unsigned b = (pk[r] >> (8 * e)) & 0xffu;
-            int64_t ref = -1;
-            if (b) {
-                const unsigned sh = 8 * (b - 1u);
-                ref = (int64_t)(s_base[w][r][b - 1u] + ((seen >> sh) & 0xffu));
-                seen += 1u << sh;
-            }
-            out4[e] = (ZT)ref;
-            const int64_t i = p0 + e;
-            if (!WRITE && i < n) {
-                const int64_t zi = (int64_t)zv[e];
-                const bool wrong = b ? zi != ref : (zi >= 0 && zi < N);
-                if (wrong && i < bad) {
-                    bad = i;
-                    bref = ref;
-                }
-            }
+        for (int k = 0; k < VS; k++) {
+            // a negative constant is never a destination
+            const QT c = (QT)s_c[k];
+            if ((all >> k) & 1u) out.c[k] = c >= 0 && !s_bad ? (long long)c : CL_BAD;
         }
-        if (WRITE) {
-            if (vec_ok && p0 + 4 <= n) {
-                if (sizeof(ZT) == 4) {
-                    int4 q;
-                    q.x = (int)out4[0];
-                    q.y = (int)out4[1];
-                    q.z = (int)out4[2];
-                    q.w = (int)out4[3];
-                    __stcs(reinterpret_cast<int4 *>(dst + p0), q);
-                } else {
-                    longlong2 a, c;
-                    a.x = (long long)out4[0];
-                    a.y = (long long)out4[1];
-                    c.x = (long long)out4[2];
-                    c.y = (long long)out4[3];
-                    __stcs(reinterpret_cast<longlong2 *>(dst + p0), a);
-                    __stcs(reinterpret_cast<longlong2 *>(dst + p0) + 1, c);
-                }
-            } else {
+        UQ m = s_dm[0];
+        for (int i = 1; i < CL_WARPS; i++) m = s_dm[i] < m ? s_dm[i] : m;
+        const unsigned long long tc = (unsigned long long)tlo | ((unsigned long long)thi << 32);
+        tcnt[t] = tc;
+        rec[t] = out;
+        dmin[t] = (unsigned long long)m;
+        cl_add_range(rs + t / R, tc);
+    }
+}
+
+// Forward, pass 1: the tile's class counts (and its range's), and every thread's
+// class codes for the write pass (half a byte per element instead of the keys and
+// classes again).
+template <typename KT>
+__global__ void __launch_bounds__(CL_THREADS) cl_tile_count_kernel(const KT *__restrict__ keys,
+                                                                   const uint8_t *__restrict__ cls, int64_t n,
+                                                                   DPred filt, int v, int vec_ok, int64_t R,
+                                                                   unsigned long long *__restrict__ tcnt,
+                                                                   ulonglong2 *__restrict__ rs,
+                                                                   unsigned long long *__restrict__ codes_out) {
+    IXP_KERNEL_ENTRY();
+    __shared__ uint2 s_w[CL_WARPS];
+    const int64_t t = blockIdx.x;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int64_t e0 = t * CL_TILE + (int64_t)threadIdx.x * CL_PER;
+    const unsigned long long codes = cl_codes16<KT>(keys, cls, filt, v, e0, n, vec_ok && e0 + CL_PER <= n);
+    __stcs(codes_out + t * CL_THREADS + threadIdx.x, codes);
+    unsigned lo, hi;
+    cl_count_codes(codes, lo, hi);
+    lo = __reduce_add_sync(FULL, lo);  // at most 512 per field
+    hi = __reduce_add_sync(FULL, hi);
+    if (l == 0) s_w[w] = make_uint2(lo, hi);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned a = 0, b = 0;
+        for (int i = 0; i < CL_WARPS; i++) {
+            a += s_w[i].x;
+            b += s_w[i].y;
+        }
+        const unsigned long long tc = (unsigned long long)a | ((unsigned long long)b << 32);
+        tcnt[t] = tc;
+        cl_add_range(rs + t / R, tc);
+    }
+}
+
+// Block sum of two words (every thread gets it).
+__device__ __forceinline__ ulonglong2 cl_block_sum2(ulonglong2 x, ulonglong2 *s) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    x.x = warp_sum_u64(x.x);
+    x.y = warp_sum_u64(x.y);
+    __syncthreads();
+    if (l == 0) s[w] = x;
+    __syncthreads();
+    ulonglong2 r = make_ulonglong2(0ull, 0ull);
 #pragma unroll
-                for (int e = 0; e < 4; e++)
-                    if (p0 + e < n) dst[p0 + e] = out4[e];
-            }
+    for (int i = 0; i < CL_WARPS; i++) {
+        r.x += s[i].x;
+        r.y += s[i].y;
+    }
+    return r;
+}
+
+// Class bases (32-bit fields, classes 0 | 1 and 2 | 3) from the class totals, and N.
+__device__ __forceinline__ ulonglong2 cl_bases(ulonglong2 tot, unsigned long long &N) {
+    const unsigned long long t0 = tot.x & 0xffffffffull, t1 = tot.x >> 32;
+    const unsigned long long t2 = tot.y & 0xffffffffull, t3 = tot.y >> 32;
+    N = t0 + t1 + t2 + t3;
+    return make_ulonglong2(0ull | (t0 << 32), (t0 + t1) | ((t0 + t1 + t2) << 32));
+}
+
+// Decide (check) or prefix (forward) pass: block b takes range b of R = tpt *
+// CL_THREADS tiles, thread j its tiles b * R + j * tpt .. + tpt - 1. The class
+// prefix at the range's start comes from the range counters; each tile's first
+// destination per class is base_k + that prefix + the block's exclusive scan. With
+// rec, a tile whose constants or dropped Z disagree raises the first-failing-tile
+// slot; with pre, the first destinations are stored for the write pass. Block 0
+// stores N.
+__global__ void __launch_bounds__(CL_THREADS) cl_decide_kernel(const unsigned long long *__restrict__ tcnt,
+                                                               const ClRec *__restrict__ rec,
+                                                               const unsigned long long *__restrict__ dmin,
+                                                               const ulonglong2 *__restrict__ rs, int64_t nt, int tpt,
+                                                               int64_t nr, Hdr *h, ulonglong2 *__restrict__ pre) {
+    IXP_KERNEL_ENTRY();
+    __shared__ ulonglong2 s_a[CL_WARPS], s_t[CL_WARPS], s_x[CL_WARPS];
+    const int64_t b = blockIdx.x;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    ulonglong2 a = make_ulonglong2(0ull, 0ull), s = a;
+    for (int64_t j = threadIdx.x; j < nr; j += CL_THREADS) {
+        const ulonglong2 x = rs[j];
+        s.x += x.x;
+        s.y += x.y;
+        if (j < b) {
+            a.x += x.x;
+            a.y += x.y;
         }
     }
-    if (bad != INT64_MAX) cl_report(h, bad, bref);
+    a = cl_block_sum2(a, s_a);
+    s = cl_block_sum2(s, s_t);
+    unsigned long long N;
+    const ulonglong2 base = cl_bases(s, N);
+    if (b == 0 && threadIdx.x == 0) h->total = N << 32;
+    const int64_t t1 = b * (int64_t)tpt * CL_THREADS + (int64_t)threadIdx.x * tpt;
+    ulonglong2 mine = make_ulonglong2(0ull, 0ull);
+    for (int u = 0; u < tpt; u++)
+        if (t1 + u < nt) {
+            const ulonglong2 c = cl_widen(tcnt[t1 + u]);
+            mine.x += c.x;
+            mine.y += c.y;
+        }
+    // exclusive scan of the threads' sums (fields stay below 2^32: no carries)
+    ulonglong2 y = mine;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long p = __shfl_up_sync(FULL, y.x, d), q = __shfl_up_sync(FULL, y.y, d);
+        if (l >= d) {
+            y.x += p;
+            y.y += q;
+        }
+    }
+    if (l == 31) s_x[w] = y;
+    __syncthreads();
+    ulonglong2 P = make_ulonglong2(base.x + a.x + y.x - mine.x, base.y + a.y + y.y - mine.y);
+    for (int i = 0; i < w; i++) {
+        P.x += s_x[i].x;
+        P.y += s_x[i].y;
+    }
+    for (int u = 0; u < tpt; u++) {
+        const int64_t t = t1 + u;
+        if (t >= nt) break;
+        if (pre) pre[t] = P;
+        if (rec) {
+            const ClRec r = rec[t];
+            const long long want[4] = {(long long)(P.x & 0xffffffffull), (long long)(P.x >> 32),
+                                       (long long)(P.y & 0xffffffffull), (long long)(P.y >> 32)};
+            bool bad = dmin[t] < N;
+#pragma unroll
+            for (int k = 0; k < 4; k++) bad |= r.c[k] != CL_NONE && r.c[k] != want[k];
+            if (bad) atomicMax(&h->k_first2, ~(unsigned long long)t);
+        }
+        const ulonglong2 c = cl_widen(tcnt[t]);
+        P.x += c.x;
+        P.y += c.y;
+    }
+}
+
+// Check, exact pass over the first failing tile (one block; nothing to do when no
+// tile failed): every element's destination from the class prefix at the tile, and
+// the first wrong one reported.
+template <typename KT, typename ZT>
+__global__ void __launch_bounds__(CL_THREADS) cl_exact_kernel(const ZT *__restrict__ z, const KT *__restrict__ keys,
+                                                              const uint8_t *__restrict__ cls, int64_t n, DPred filt,
+                                                              int v, int vec_ok,
+                                                              const unsigned long long *__restrict__ tcnt,
+                                                              const ulonglong2 *__restrict__ rs, int tpt, int64_t nr,
+                                                              Hdr *h) {
+    IXP_KERNEL_ENTRY();
+    __shared__ ulonglong2 s_a[CL_WARPS], s_t[CL_WARPS];
+    __shared__ uint2 s_w[CL_WARPS];
+    if (h->k_first2 == 0) return;
+    const int64_t t = (int64_t)~h->k_first2;
+    const int64_t R = (int64_t)tpt * CL_THREADS, rb = t / R;
+    ulonglong2 a = make_ulonglong2(0ull, 0ull), s = a;
+    for (int64_t j = threadIdx.x; j < nr; j += CL_THREADS) {
+        const ulonglong2 x = rs[j];
+        s.x += x.x;
+        s.y += x.y;
+        if (j < rb) {
+            a.x += x.x;
+            a.y += x.y;
+        }
+    }
+    for (int64_t j = rb * R + threadIdx.x; j < t; j += CL_THREADS) {
+        const ulonglong2 c = cl_widen(tcnt[j]);
+        a.x += c.x;
+        a.y += c.y;
+    }
+    a = cl_block_sum2(a, s_a);
+    s = cl_block_sum2(s, s_t);
+    unsigned long long N;
+    const ulonglong2 base = cl_bases(s, N);
+    const unsigned long long P0 = base.x + a.x, P1 = base.y + a.y;
+    const int64_t e0 = t * CL_TILE + (int64_t)threadIdx.x * CL_PER;
+    const bool full = vec_ok && e0 + CL_PER <= n;
+    const unsigned long long codes = cl_codes16<KT>(keys, cls, filt, v, e0, n, full);
+    ZT zz[CL_PER];
+    cl_load_z16<ZT>(z, e0, n, full, zz);
+    unsigned lo, hi, tlo, thi;
+    cl_count_codes(codes, lo, hi);
+    cl_block_scan16(lo, hi, s_w, tlo, thi);
+    int64_t r[4] = {(int64_t)(P0 & 0xffffffffull) + (lo & 0xffffu), (int64_t)(P0 >> 32) + (lo >> 16),
+                    (int64_t)(P1 & 0xffffffffull) + (hi & 0xffffu), (int64_t)(P1 >> 32) + (hi >> 16)};
+    for (int e = 0; e < CL_PER; e++) {
+        const int64_t i = e0 + e;
+        if (i >= n) break;
+        const unsigned q = (unsigned)(codes >> (4 * e)) & 15u;
+        const int64_t zi = (int64_t)zz[e];
+        int64_t ref = -1;
+        if (q) ref = r[q - 1]++;
+        const bool wrong = q ? zi != ref : (zi >= 0 && zi < (int64_t)N);
+        if (wrong) {
+            cl_report(h, i, ref);
+            break;
+        }
+    }
+}
+
+// Forward, write pass, from the class codes of pass 1: each element's destination
+// (-1 for a dropped one) is its class's first destination in the thread (tile
+// prefix + block scan, looked up by class in a per-thread row of shared memory)
+// plus its in-thread class rank; 16-byte streaming stores.
+template <typename OT, int VS>
+__global__ void __launch_bounds__(CL_THREADS) cl_write_kernel(const unsigned long long *__restrict__ codes_in, int64_t n,
+                                                              int vec_ok, const ulonglong2 *__restrict__ pre,
+                                                              OT *__restrict__ dst) {
+    IXP_KERNEL_ENTRY();
+    using UT = typename std::make_unsigned<OT>::type;
+    __shared__ uint2 s_w[CL_WARPS];
+    __shared__ UT s_e[VS + 1][CL_THREADS];  // row q: first destination of class q - 1 in the thread; row 0: -1
+    const int64_t t = blockIdx.x;
+    const int64_t e0 = t * CL_TILE + (int64_t)threadIdx.x * CL_PER;
+    const bool full = vec_ok && e0 + CL_PER <= n;
+    const unsigned long long codes = __ldcs(codes_in + t * CL_THREADS + threadIdx.x);
+    unsigned lo, hi, tlo, thi;
+    unsigned long long eq[4];
+    cl_count_codes(codes, lo, hi, eq);
+    cl_block_scan16(lo, hi, s_w, tlo, thi);
+    const ulonglong2 P = pre[t];
+    const unsigned first[4] = {(unsigned)P.x + (lo & 0xffffu), (unsigned)(P.x >> 32) + (lo >> 16),
+                               (unsigned)P.y + (hi & 0xffffu), (unsigned)(P.y >> 32) + (hi >> 16)};
+    s_e[0][threadIdx.x] = (UT)~(UT)0;
+#pragma unroll
+    for (int k = 0; k < VS; k++) s_e[k + 1][threadIdx.x] = (UT)first[k];
+    const unsigned long long xr = cl_ranks16<VS>(eq);
+    OT o[CL_PER];
+#pragma unroll
+    for (int e = 0; e < CL_PER; e++) {
+        const unsigned q = (unsigned)(codes >> (4 * e)) & 15u;
+        o[e] = (OT)(s_e[q][threadIdx.x] + (UT)((xr >> (4 * e)) & 15u));  // dropped: -1 + 0
+    }
+    if (full) {
+        if constexpr (sizeof(OT) == 4) {
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                __stcs(reinterpret_cast<int4 *>(dst + e0) + u,
+                       make_int4((int)o[4 * u], (int)o[4 * u + 1], (int)o[4 * u + 2], (int)o[4 * u + 3]));
+        } else {
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                __stcs(reinterpret_cast<longlong2 *>(dst + e0) + u,
+                       make_longlong2((long long)o[2 * u], (long long)o[2 * u + 1]));
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < CL_PER; e++)
+            if (e0 + e < n) dst[e0 + e] = o[e];
+    }
 }
 
 // ----------------------------------------------------------- flat: pass 2
@@ -590,7 +1054,7 @@ size_t filtpart_classes_ws_bytes(int v, int64_t n, int64_t nseg) {
     if (v < 1) v = 1;
     if (n < 0) n = 0;
     const size_t nt = (size_t)((n + CL_TILE - 1) / CL_TILE);
-    const size_t flat = round256(nt * (size_t)v * 4) + 2 * round256((size_t)v * 8);
+    const size_t flat = v <= 4 ? cl16_ws(nullptr, n).bytes : round256(nt * (size_t)v * 4) + 2 * round256((size_t)v * 8);
     const size_t ns = (size_t)(nseg > 0 ? nseg : 0);
     const size_t seg = round256((ns + 1) * 8) + round256(((ns + CL_G - 1) / CL_G + 1) * 8);
     return HDR_BYTES + std::max(flat, seg);
@@ -621,28 +1085,55 @@ static int run_classes(const ZT *z, int64_t n, const KT *keys, ixp_pred filt, co
         cl_check_kernel<KT, ZT, true, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt, base, h, dst); \
     else                                                                                                        \
         cl_check_kernel<KT, ZT, false, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, cnt, base, h, nullptr)
-#define IXP_CL4_PASSES(VS)                                                                                      \
-    cl_count4_kernel<KT, VS><<<g, CL_THREADS, 0, st>>>(keys, cls, n, f, v, nt, vec, cnt);                       \
-    cl_class_scan_kernel<<<(unsigned)v, 1024, 0, st>>>(cnt, nt, tot);                                           \
-    cl_base_kernel<<<1, 32, 0, st>>>(tot, v, base, h);                                                          \
-    if (write)                                                                                                  \
-        cl_check4_kernel<KT, ZT, true, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, vec, cnt, base, h, \
-                                                                    dst);                                       \
-    else                                                                                                        \
-        cl_check4_kernel<KT, ZT, false, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, nt, vec, cnt, base,  \
-                                                                     h, nullptr)
             const auto al16 = [](const void *q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
-            const int vec = (!keys || al16(keys)) && (reinterpret_cast<uintptr_t>(cls) & 3u) == 0 &&
-                            (write ? (!dst || al16(dst)) : al16(z));
+            const int vec = (!keys || al16(keys)) && al16(cls) && (write ? (!dst || al16(dst)) : al16(z));
             if (v <= 4) {
-                IXP_CL4_PASSES(4);
+                const Cl16Ws W = cl16_ws(ws, n);
+                const int64_t R = (int64_t)W.tpt * CL_THREADS;
+                const unsigned gr = (unsigned)W.nr;
+                if (cudaMemsetAsync(W.rs, 0, W.clear, st) != cudaSuccess) return IXP_E_CUDA;
+                if (write) {
+                    cl_tile_count_kernel<KT><<<g, CL_THREADS, 0, st>>>(keys, cls, n, f, v, vec, R, W.tcnt, W.rs,
+                                                                       W.codes);
+                    cl_decide_kernel<<<gr, CL_THREADS, 0, st>>>(W.tcnt, nullptr, nullptr, W.rs, nt, W.tpt, W.nr, h,
+                                                                W.pre);
+                    const int dvec = !dst || (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
+                    if (v <= 2)
+                        cl_write_kernel<ZT, 2><<<g, CL_THREADS, 0, st>>>(W.codes, n, dvec, W.pre, dst);
+                    else
+                        cl_write_kernel<ZT, 4><<<g, CL_THREADS, 0, st>>>(W.codes, n, dvec, W.pre, dst);
+                } else {
+#define IXP_CL_TILE(QT, VS)                                                                                    \
+    cl_tile_kernel<KT, ZT, QT, VS><<<g, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, vec, R, W.tcnt, W.rec, W.dmin, \
+                                                             W.rs)
+                    bool narrow = false;
+                    if constexpr (sizeof(ZT) == 4) {
+                        if (n <= INT32_MAX) {
+                            narrow = true;
+                            if (v <= 2)
+                                IXP_CL_TILE(int32_t, 2);
+                            else
+                                IXP_CL_TILE(int32_t, 4);
+                        }
+                    }
+                    if (!narrow) {
+                        if (v <= 2)
+                            IXP_CL_TILE(int64_t, 2);
+                        else
+                            IXP_CL_TILE(int64_t, 4);
+                    }
+#undef IXP_CL_TILE
+                    cl_decide_kernel<<<gr, CL_THREADS, 0, st>>>(W.tcnt, W.rec, W.dmin, W.rs, nt, W.tpt, W.nr, h,
+                                                                nullptr);
+                    cl_exact_kernel<KT, ZT><<<1, CL_THREADS, 0, st>>>(z, keys, cls, n, f, v, vec, W.tcnt, W.rs,
+                                                                      W.tpt, W.nr, h);
+                }
             } else if (v <= 8) {
                 IXP_CL_PASSES(8);
             } else {
                 IXP_CL_PASSES(0);
             }
 #undef IXP_CL_PASSES
-#undef IXP_CL4_PASSES
         }
     } else {
         const int64_t m = segs.nseg;

@@ -131,3 +131,43 @@ def test_gather_and_hist_past_2_31(ixp, dev):
     ixp.hist_min(H, idx)
     assert torch.equal(H, torch.arange(1 << 20, device=dev, dtype=torch.int64).mul(
         pow(7, -1, 1 << 20)).remainder(1 << 20))
+
+
+@pytest.mark.parametrize("n,zt", [((1 << 30) + 4097, torch.int32), (N, torch.int64)])
+def test_classes_past_2_30(ixp, dev, n, zt):
+    """The flat 3-class partition and its check past 2^30 elements, where the decide
+    pass gives each thread several tiles: the index form against per-class prefix
+    counts (torch cumsum) on sampled positions, the check accepting it, and planted
+    faults reported at the first one (int32 destinations below 2^31, int64 ones
+    past it)."""
+    v = 3
+    i = torch.arange(n, device=dev, dtype=torch.int64)
+    cls = ((i * 2654435761) >> 9).remainder(5).to(torch.uint8)  # classes 3 and 4 fold into 2
+    del i
+    out, kept = ixp.filtpart_classes(cls, v, None, "true", out_dtype=zt)
+    assert int(kept.item()) == n
+    cc = torch.clamp(cls, max=v - 1)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    late = n - 5
+    early = (1 << 29) + 3
+    smp = torch.cat([torch.randint(0, n, (4096,), generator=g, device=dev),
+                     torch.tensor([0, early, late, n - 1], device=dev)])
+    exp = torch.zeros(smp.numel(), dtype=torch.int64, device=dev)
+    base = 0
+    for k in range(v):
+        m = cc == k
+        cs = torch.cumsum(m.to(torch.int64), 0)
+        exp = torch.where(cc[smp] == k, base + cs[smp] - m[smp].to(torch.int64), exp)
+        base += int(cs[-1].item())
+        del cs, m
+    del cc
+    assert torch.equal(out[smp].to(torch.int64), exp)
+    assert ixp.check_filtpart(out, None, cls=cls, v=v).get()["ok"] == 1
+    want_late, want_early = int(out[late].item()), int(out[early].item())
+    out[late] += 1
+    r = ixp.check_filtpart(out, None, cls=cls, v=v).get()
+    assert r["ok"] == 0 and r["index"] == late and r["aux1"] == want_late and r["aux0"] == n
+    out[early] -= 1
+    r = ixp.check_filtpart(out, None, cls=cls, v=v).get()
+    assert r["ok"] == 0 and r["index"] == early and r["aux1"] == want_early

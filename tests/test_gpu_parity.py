@@ -904,6 +904,62 @@ def test_filtpart_classes_index_form(ixp, dev, n, m, v, ot):
     assert vd["ok"]
 
 
+@pytest.mark.parametrize("kt,zt", [(np.int32, np.int32), (np.int64, np.int64), (np.int32, np.int64)])
+@pytest.mark.parametrize("v", [2, 3, 4])
+@pytest.mark.parametrize("n", [4096 * 40, 4096 * 40 + 13])
+@pytest.mark.parametrize("shift", [0, 1])
+def test_filtpart_classes_tiles(ixp, dev, n, v, kt, zt, shift):
+    """The flat v-class check (v <= 4) takes one pass that records each tile's
+    Z - rank per class and revisits only the first failing tile: faults planted in
+    several tiles (the first one must be reported), a whole class of one tile moved
+    by one (every Z - rank agrees inside the tile, only the prefix disagrees), a
+    dropped element inside [0, N), a kept Z whose Z - rank wraps around, dropped Z at
+    N and below 0 (both fine), against the oracle; arrays at an element offset take
+    the unvectorised loads; the index form on the same views."""
+    rng = np.random.default_rng(n + 10 * v + shift)
+    off = np.array([0, n], np.int64)
+    keys = synth.keys_uniform(n + 1, n + v).astype(kt)
+    cls = rng.integers(0, 6, size=n + 1).astype(np.uint8)
+    thr = synth.bernoulli_threshold(0.85)
+    kept = keys[shift:shift + n] < thr
+    c = cls[shift:shift + n]
+    z = classes_dest(c, v, kept, off)
+    N = int(kept.sum())
+    kidx, didx = np.flatnonzero(kept), np.flatnonzero(~kept)
+    cc = np.minimum(c, v - 1)
+    lo = np.iinfo(zt).min
+    cases = {"ok": z.copy()}
+    s = z.copy(); s[kidx[(kidx >= 30 * 4096)][0]] += 1; s[kidx[(kidx >= 20 * 4096)][5]] -= 1
+    cases["two_tiles"] = s
+    s = z.copy(); sel = kidx[(kidx // 4096 == 11) & (cc[kidx] == v - 1)]; s[sel] += 1; s[kidx[-1]] = 0
+    cases["class_block_shifted"] = s
+    s = z.copy(); s[didx[(didx >= 5 * 4096)][0]] = N - 1; s[kidx[(kidx >= 9 * 4096)][0]] += 7
+    cases["dropped_inside_first"] = s
+    s = z.copy(); s[kidx[(kidx >= 3 * 4096)][2]] = lo
+    cases["wrapping_z"] = s
+    s = z.copy(); s[didx[0]] = N; s[didx[1]] = -5; s[didx[-1]] = lo
+    cases["dropped_outside"] = s
+    s = z.copy(); a, b = kidx[(kidx >= 17 * 4096)][:2]; s[a], s[b] = s[b], s[a]
+    cases["swap_in_tile"] = s
+    filt = ("lt", 0, thr)
+    kd = T(keys, dev)[shift:shift + n]
+    cd = T(cls, dev)[shift:shift + n]
+    for name, zz in cases.items():
+        zz = zz.astype(zt)
+        zd = torch.empty(n + 1, dtype=getattr(torch, np.dtype(zt).name), device=dev)[shift:shift + n]
+        zd.copy_(T(zz, dev))
+        got = ixp.check_filtpart(zd, kd, filt=filt, cls=cd, v=v)
+        ref = oracle.check_filtpart(zz, keys[shift:shift + n], filt=filt, cls=c, v=v)
+        same(got, ref, (name, n, v, shift))
+        if name not in ("ok", "dropped_outside"):
+            assert not ref["ok"]
+    ot = getattr(torch, np.dtype(zt).name)
+    out = torch.empty(n + 1, dtype=ot, device=dev)[shift:shift + n]
+    got, nk = ixp.filtpart_classes(cd, v, kd, filt, out_dtype=ot, out=out)
+    assert np.array_equal(got.cpu().numpy(), z.astype(zt))
+    assert int(nk.item()) == N
+
+
 @pytest.mark.parametrize("it,ot", [(np.int32, np.int32), (np.int32, np.int64), (np.int64, np.int64)])
 @pytest.mark.parametrize("n", [0, 1, 33, 4097, 100003, 1 << 20])
 def test_sgm_scan_flags(ixp, dev, n, it, ot):
