@@ -289,13 +289,14 @@ int ixp_scatter(void *dst, int64_t dst_len, const void *idx, int itype, const vo
 
 /* Additive scatter of float32 rows accumulated in float64: acc[idx[i]] += vals[i]
  * for in-bounds idx[i], acc a device double[dst_len * row_elems] the caller zeroes
- * (or pre-loads). Each block first sums its rows into a shared-memory cache of
- * target rows held as exact 64-bit fixed-point values (native integer atomics,
- * one float64 rounding per cached row when the block ends); rows that miss the
- * cache, and values the fixed-point scale cannot hold exactly, are added with
- * float64 atomics. Every addition into acc rounds once in float64 (a cached
- * partial sum is exact before its rounding); the order of the additions is not
- * fixed, so the low bits can differ from run to run. */
+ * (or pre-loads). Rows of up to 8 values go through each block's shared-memory
+ * cache of target rows held as exact 64-bit fixed-point values (native integer
+ * atomics, one float64 rounding per cached row when the block ends); rows that
+ * miss the cache, and values the fixed-point scale cannot hold exactly, are added
+ * with float64 atomics, the lanes of a row covering its columns. Every addition
+ * into acc rounds once in float64 (a cached partial sum is exact before its
+ * rounding); the order of the additions is not fixed, so the low bits can differ
+ * from run to run. */
 int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const void *idx, int itype, const float *vals,
                                int64_t n, int32_t row_elems, ixp_stream stream);
 

@@ -152,43 +152,51 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_kernel(FT *__restr
 
 // Additive scatter of float32 rows into a float64 accumulator. For rows of up to
 // HOT_COLS values each block keeps a direct-mapped cache of HOT_SLOTS target rows in
-// shared memory: a lane adds its row into the cached row when its target owns the
-// slot (claiming a free slot on first use) and falls back to global float64 atomics
-// otherwise. Hot targets (a Zipf head) thus cost shared-memory atomics instead of
-// serialised global ones. The cached rows are exact 64-bit fixed-point sums (native
-// integer atomics; float64 atomics in shared memory are far slower). The block
-// samples the largest biased exponent E of its first rows; with R <= 2^r the most
-// rows the block can take, the unit is 2^L, L = (E - 125) + r - 62. A float32 value
-// with biased exponent in [E + r - 37, E + 1] is then an integer multiple of 2^L
-// below 2^(62 - r) units, so its scaled value is exact and 2^r of them cannot
-// overflow; any other value (smaller, larger than the sample, not finite) takes the
-// float64 path, zeros are skipped. When the block ends each cached sum is rounded
-// to float64 once and added globally: at least as accurate as float64 atomics. Wider rows combine same-target
-// lanes of a warp first (match_any + a shuffle tree in float64) and add the sums
-// globally.
+// shared memory, and a warp takes 32 / CP rows per step with CP lanes per row (one
+// column each, CP = row width rounded up to a power of two): the values load as
+// coalesced column words, a row whose target owns its cache slot (claiming a free
+// slot on first use) is added into the cached row, and a row that misses is added
+// to the global accumulator with one float64 atomic per lane, the CP lanes of a row
+// hitting one contiguous row (the L2 takes such a warp's reductions about three
+// times faster than 32 scattered rows). Hot targets (a Zipf head) thus cost
+// shared-memory atomics instead of serialised global ones. The cached rows are
+// exact 64-bit fixed-point sums held as two 32-bit words (native 32-bit shared
+// atomics; the low word's wrap-arounds are carried into the high word by the adder
+// that caused them, so the pair stays exact modulo 2^64). The block samples the
+// largest biased exponent E of its first rows; with R <= 2^r the most rows the
+// block can take, the unit is 2^L, L = (E - 125) + r - 62. A float32 value with
+// biased exponent in [E + r - 37, E + 1] is then an integer multiple of 2^L below
+// 2^(62 - r) units, so its scaled value is exact and 2^r of them cannot overflow;
+// any other value (smaller, larger than the sample, not finite) takes the float64
+// path, zeros are skipped. When the block ends each cached sum is rounded to
+// float64 once and added globally: at least as accurate as float64 atomics. Wider
+// rows combine same-target lanes of a warp first (match_any + a shuffle tree in
+// float64) and add the sums globally.
 constexpr int HOT_COLS = 8;        // cached row width; wider rows bypass the cache
 constexpr int HOT_SLOTS = 1024;    // cached target rows per block (a power of two)
 constexpr int HOT_BLOCKS_PER_SM = 3;
-// shared bytes of the cache: the tags, then the fixed-point rows
+constexpr int HOT_THREADS = 512;   // three blocks of 512 threads and their caches fill an SM
+// shared bytes of the cache: the tags, then the fixed-point rows (low words, high words)
 constexpr size_t hot_smem_bytes(int slots) { return (size_t)slots * (8 + 8 * HOT_COLS); }
 
 // Float32 bits -> biased exponent (0 for zero and denormals).
 __device__ __forceinline__ int f32_bexp(float v) { return (int)((__float_as_uint(v) >> 23) & 0xffu); }
 
 template <typename IT>
-__global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double *__restrict__ acc, int64_t dst_len,
+__global__ void __launch_bounds__(HOT_THREADS, HOT_BLOCKS_PER_SM) scatter_add_f64_kernel(double *__restrict__ acc, int64_t dst_len,
                                                                          const IT *__restrict__ idx,
                                                                          const float *__restrict__ vals, int64_t n,
-                                                                         int row_elems, int vec16, int slots) {
+                                                                         int row_elems, int slots) {
     IXP_KERNEL_ENTRY();
     extern __shared__ __align__(16) unsigned long long hot_raw[];
-    unsigned long long *s_tag = hot_raw;                                              // slots; ~0 = free
-    unsigned long long(*s_fix)[HOT_COLS] = reinterpret_cast<unsigned long long(*)[HOT_COLS]>(hot_raw + slots);
+    unsigned long long *s_tag = hot_raw;  // slots; ~0 = free
+    unsigned *s_lo = reinterpret_cast<unsigned *>(hot_raw + slots);  // [slot][HOT_COLS]
+    unsigned *s_hi = s_lo + (size_t)slots * HOT_COLS;
     __shared__ int s_emax;
     const bool cache = row_elems <= HOT_COLS && slots > 0;
     for (int sl = threadIdx.x; sl < slots; sl += blockDim.x) {
         s_tag[sl] = ~0ull;
-        for (int c = 0; c < HOT_COLS; c++) s_fix[sl][c] = 0ull;
+        for (int c = 0; c < HOT_COLS; c++) s_lo[sl * HOT_COLS + c] = s_hi[sl * HOT_COLS + c] = 0u;
     }
     if (threadIdx.x == 0) s_emax = 0;
     __syncthreads();
@@ -202,52 +210,77 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double 
         atomicMax(&s_emax, e);
     }
     __syncthreads();
-    const long long rb = ((n + stride - 1) / stride) * (long long)blockDim.x;  // rows this block takes at most
-    const int r = max(1, 64 - __clzll((unsigned long long)max(rb, 2ll) - 1ull));  // 2^r >= rb
-    const int L = (s_emax - 125) + r - 62;  // fixed-point unit 2^L
-    const int eb_lo = s_emax + r - 37, eb_hi = s_emax + 1;  // biased exponents kept in the cache
-    const bool fix_ok = s_emax > 0 && s_emax < 254 && -L <= 127 && -L >= -126 && eb_lo <= eb_hi;
-    const float to_fix = fix_ok ? ldexpf(1.0f, -L) : 0.0f;  // a power of two: the scaling is exact
-    for (int64_t base = tid - lane; base < n; base += stride) {
-        const int64_t i = base + lane;
-        const bool live = i < n;
-        int64_t d = live ? (int64_t)__ldg(idx + i) : -1;
-        if (d < 0 || d >= dst_len) d = -1;
-        if (cache) {
-            // every lane adds its own row: into the block's shared copy of a cached target,
-            // else straight into the global accumulator
-            if (d >= 0) {
+    if (cache) {
+        const int lg = row_elems <= 1 ? 0 : row_elems <= 2 ? 1 : row_elems <= 4 ? 2 : 3;  // CP = 2^lg lanes a row
+        const int rpw = 32 >> lg;                                                           // rows a warp step
+        const int j = lane >> lg, c = lane & ((1 << lg) - 1);
+        const bool col = c < row_elems;
+        const int64_t wpb = blockDim.x >> 5;
+        const int64_t rstride = (int64_t)gridDim.x * wpb * rpw;  // rows per grid step
+        const long long rb = ((n + rstride - 1) / rstride) * wpb * rpw;  // rows this block takes at most
+        const int r = max(1, 64 - __clzll((unsigned long long)max(rb, 2ll) - 1ull));  // 2^r >= rb
+        const int L = (s_emax - 125) + r - 62;  // fixed-point unit 2^L
+        const int eb_lo = s_emax + r - 37, eb_hi = s_emax + 1;  // biased exponents kept in the cache
+        const bool fix_ok = s_emax > 0 && s_emax < 254 && -L <= 127 && -L >= -126 && eb_lo <= eb_hi;
+        const float to_fix = fix_ok ? ldexpf(1.0f, -L) : 0.0f;  // a power of two: the scaling is exact
+        // a lane's row target (-1 when out of bounds or past n) and its column value;
+        // software-pipelined: the next step's are in flight while this one is added
+        const auto load = [&](int64_t rw, int64_t &d, float &x) {
+            d = -1;
+            x = 0.0f;
+            if (rw >= n) return;
+            d = (int64_t)__ldg(idx + rw);
+            if (d < 0 || d >= dst_len) d = -1;
+            if (col) x = __ldcs(vals + rw * row_elems + c);
+        };
+        int64_t rw = ((int64_t)blockIdx.x * wpb + (threadIdx.x >> 5)) * rpw + j;
+        int64_t d;
+        float x;
+        load(rw, d, x);
+        for (; rw < n; rw += rstride) {
+            int64_t dn;
+            float xn;
+            load(rw + rstride, dn, xn);
+            if (d >= 0 && col) {
                 const int sl = (int)(d & (int64_t)(slots - 1));
                 unsigned long long tag = s_tag[sl];
                 if (tag == ~0ull) {
                     const unsigned long long prev = atomicCAS(&s_tag[sl], ~0ull, (unsigned long long)d);
                     tag = prev == ~0ull ? (unsigned long long)d : prev;
                 }
-                const bool hit = fix_ok && tag == (unsigned long long)d;
-                float v[HOT_COLS];
-                if (row_elems == HOT_COLS && vec16) {  // the common [n x 8] case: two 16-byte loads
-                    const float4 a4 = __ldcs(reinterpret_cast<const float4 *>(vals + i * HOT_COLS));
-                    const float4 b4 = __ldcs(reinterpret_cast<const float4 *>(vals + i * HOT_COLS) + 1);
-                    v[0] = a4.x, v[1] = a4.y, v[2] = a4.z, v[3] = a4.w, v[4] = b4.x, v[5] = b4.y, v[6] = b4.z,
-                    v[7] = b4.w;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < HOT_COLS; c++) v[c] = c < row_elems ? vals[i * row_elems + c] : 0.0f;
-                }
-#pragma unroll
-                for (int c = 0; c < HOT_COLS; c++) {
-                    if (c >= row_elems) break;
-                    const int e = f32_bexp(v[c]);
-                    if (e == 0 && v[c] == 0.0f) continue;
-                    if (hit && e >= eb_lo && e <= eb_hi) {
-                        const long long q = __float2ll_rn(v[c] * to_fix);  // exact: an integer at this scale
-                        atomicAdd(&s_fix[sl][c], (unsigned long long)q);
+                const int e = f32_bexp(x);
+                if (!(e == 0 && x == 0.0f)) {
+                    if (fix_ok && tag == (unsigned long long)d && e >= eb_lo && e <= eb_hi) {
+                        const long long q = __float2ll_rn(x * to_fix);  // exact: an integer at this scale
+                        const unsigned ql = (unsigned)(unsigned long long)q;
+                        const unsigned qh = (unsigned)((unsigned long long)q >> 32);
+                        const unsigned old = atomicAdd(&s_lo[sl * HOT_COLS + c], ql);
+                        const unsigned up = qh + (old + ql < old ? 1u : 0u);
+                        if (up) atomicAdd(&s_hi[sl * HOT_COLS + c], up);
                     } else {
-                        atomicAdd(acc + d * row_elems + c, (double)v[c]);
+                        atomicAdd(acc + d * row_elems + c, (double)x);
                     }
                 }
             }
-        } else {
+            d = dn;
+            x = xn;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < slots * HOT_COLS; e += blockDim.x) {
+            const int sl = e / HOT_COLS, cc = e % HOT_COLS;
+            const unsigned long long t = s_tag[sl];
+            const long long q = (long long)(((unsigned long long)s_hi[e] << 32) | (unsigned long long)s_lo[e]);
+            if (t != ~0ull && cc < row_elems && q != 0) atomicAdd(acc + (int64_t)t * row_elems + cc, ldexp((double)q, L));
+        }
+        return;
+    }
+    {
+        for (int64_t base = tid - lane; base < n; base += stride) {
+            const int64_t i = base + lane;
+            const bool live = i < n;
+            int64_t d = live ? (int64_t)__ldg(idx + i) : -1;
+            if (d < 0 || d >= dst_len) d = -1;
+            {
             // wide rows: the lanes holding the same target combine their rows across the warp
             // (one column at a time) and one of them adds the sum
             const unsigned peers = __match_any_sync(FULL, (unsigned long long)d);
@@ -267,15 +300,8 @@ __global__ void __launch_bounds__(STREAM_THREADS) scatter_add_f64_kernel(double 
                     if (lane == src) atomicAdd(acc + key * row_elems + c, x);
                 }
             }
+            }
         }
-    }
-    if (!cache) return;
-    __syncthreads();
-    for (int e = threadIdx.x; e < slots * HOT_COLS; e += blockDim.x) {
-        const int sl = e / HOT_COLS, c = e % HOT_COLS;
-        const unsigned long long t = s_tag[sl];
-        const long long q = (long long)s_fix[sl][c];
-        if (t != ~0ull && c < row_elems && q != 0) atomicAdd(acc + (int64_t)t * row_elems + c, ldexp((double)q, L));
     }
 }
 
@@ -551,19 +577,18 @@ extern "C" int ixp_scatter_add_f32_to_f64(double *acc, int64_t dst_len, const vo
     if (!aligned_to(idx, itype == IXP_I32 ? 4 : 8) || !aligned_to(vals, 4) || !aligned_to(acc, 8)) return IXP_E_INVAL;
     if (n == 0) return IXP_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int v16 = aligned_to(vals, 16);
     const int slots = row_elems <= HOT_COLS ? HOT_SLOTS : 0;
     const size_t smem = hot_smem_bytes(slots);
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + STREAM_THREADS - 1) / STREAM_THREADS,
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + HOT_THREADS - 1) / HOT_THREADS,
                                                                 (int64_t)num_sms() * HOT_BLOCKS_PER_SM));
     if (itype == IXP_I32) {
         cudaFuncSetAttribute(scatter_add_f64_kernel<int32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        scatter_add_f64_kernel<int32_t><<<g, STREAM_THREADS, smem, st>>>(acc, dst_len, (const int32_t *)idx, vals, n,
-                                                                         row_elems, v16, slots);
+        scatter_add_f64_kernel<int32_t><<<g, HOT_THREADS, smem, st>>>(acc, dst_len, (const int32_t *)idx, vals, n,
+                                                                      row_elems, slots);
     } else {
         cudaFuncSetAttribute(scatter_add_f64_kernel<int64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        scatter_add_f64_kernel<int64_t><<<g, STREAM_THREADS, smem, st>>>(acc, dst_len, (const int64_t *)idx, vals, n,
-                                                                         row_elems, v16, slots);
+        scatter_add_f64_kernel<int64_t><<<g, HOT_THREADS, smem, st>>>(acc, dst_len, (const int64_t *)idx, vals, n,
+                                                                      row_elems, slots);
     }
     return launch_status();
 }

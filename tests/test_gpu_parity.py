@@ -744,6 +744,28 @@ def test_scatter_add_f64_zipf(ixp, dev):
     assert np.array_equal(f32, ref.astype(np.float32)) or np.all(np.abs(f32 - ref) <= 1e-6 * np.maximum(absum, 1e-30))
 
 
+@pytest.mark.parametrize("cols", [1, 3, 8])
+@pytest.mark.parametrize("it", [np.int32, np.int64])
+def test_scatter_add_f64_cache_misses(ixp, dev, cols, it):
+    """Most targets outside every block's shared cache (Zipf over 2^18 targets, so
+    the missing rows go to the global accumulator, 8 lanes per row), with
+    out-of-bounds targets mixed in: against the float64 oracle."""
+    rng = np.random.default_rng(cols + 7)
+    n, m = 300001, 1 << 18
+    idx = synth.zipf_ranks(n, m, 1.1, 79 + cols).astype(it)
+    idx[rng.random(n) < 0.01] = -1
+    idx[rng.random(n) < 0.01] = m
+    vals = synth.payload_f32(n, 80 + cols, cols=cols)
+    vals[rng.random(n) < 0.02] = 0.0
+    acc = torch.zeros((m, cols) if cols > 1 else (m,), dtype=torch.float64, device=dev)
+    ixp.scatter_add_f64(acc, T(idx, dev), T(vals if cols > 1 else vals.reshape(n), dev))
+    keep = (idx >= 0) & (idx < m)
+    ref = oracle.scatter_add_f64(m, idx[keep], vals[keep])
+    absum = oracle.scatter_add_f64(m, idx[keep], np.abs(vals[keep]))
+    got = acc.cpu().numpy().reshape(ref.shape)
+    assert np.all(np.abs(got - ref) <= 1e-10 * absum + 1e-300)
+
+
 @pytest.mark.parametrize("m", [0, 1, 5, 1000, 40000])
 @pytest.mark.parametrize("ot", [np.int32, np.int64])
 def test_flags_from_shape(ixp, dev, m, ot):
