@@ -88,12 +88,22 @@ OP_KERNELS = {
     "scan_i32": "scan_tma_kernel<int, int>",
     "partition_p50": "count_tiles_kernel<int> + partition_flat_kernel<int, int, false>",
     "partition_p01": "count_tiles_kernel<int> + partition_flat_kernel<int, int, false>",
-    "filtpart_p50": "filtpart_tile_kernel<int, int, int>", "scatter_rows8": "rows_lanes_kernel<int, 2, 1, true>",
+    "filtpart_p50": "filtpart_tile_lt_kernel", "scatter_rows8": "rows_lanes_kernel<int, 2, 1, true>",
     "gather_rows8": "rows_lanes_kernel<int, 2, 1, false>", "flags_from_shape": "scan + flags_scatter_kernel",
 }
 for _tag in ("i32", "i64"):
     for _op in ("range_perm", "range_oor", "mono_le", "mono_brk", "inj_perm", "inj_dup", "bij_perm", "bij_dup"):
         OP_KERNELS[f"{_op}_{_tag}"] = OP_KERNELS[_op.split("_")[0]]
+
+
+def inj_design_bytes(name, n32, n64):
+    """Bytes the bucketed Inj / Bij design moves (the elements read once, a 4-byte
+    pool entry written and read back per element; the bitmaps stay in shared
+    memory), or None for the other ops."""
+    if not name.startswith(("inj_", "bij_")):
+        return None
+    es, n = (4, n32) if name.endswith("_i32") else (8, n64)
+    return (es + 8) * n
 
 
 def flags_bytes(m, total):
@@ -559,6 +569,10 @@ def main():
         ts = [ev[k][i][0].elapsed_time(ev[k][i][1]) for k in range(args.steps)]
         m = sum(ts) / len(ts)
         per_op[name] = op_record(m, nbytes, op_elements(name, n32, n64, R.shape_total), peak)
+        db = inj_design_bytes(name, n32, n64)
+        if db:
+            per_op[name]["design_bytes"] = db
+            per_op[name]["frac_design"] = round(db / (m / 1e3) / 1e9 / peak, 4)
     roofline = roofline_of(per_op, peak, peak_src)
     ceilings = None
     if not args.no_ceilings:

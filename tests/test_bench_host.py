@@ -30,6 +30,15 @@ def test_algorithmic_bytes_per_op():
     assert len(ops) == 23
 
 
+def test_inj_bij_design_traffic():
+    # the bucketed design reads the elements once and writes and reads a 4-byte pool
+    # entry per element; other ops carry no design figure
+    assert bench.inj_design_bytes("inj_perm_i32", N32, N64) == 12 * N32
+    assert bench.inj_design_bytes("bij_dup_i64", N32, N64) == 16 * N64
+    assert bench.inj_design_bytes("range_perm_i32", N32, N64) is None
+    assert bench.inj_design_bytes("scan_i32", N32, N64) is None
+
+
 def test_every_op_names_its_kernel():
     for name, _, _, _ in bench.make_ops(N32, N64):
         assert bench.OP_KERNELS.get(name), name

@@ -147,6 +147,11 @@ def test_partition_full_size(ixp, dev, p):
     ih = idx.cpu().numpy()
     exp = np.where(c[smp], before[smp], T + smp - before[smp])
     assert np.array_equal(ih[smp].astype(np.int64), exp)
+    del before
+    # the whole index array against the oracle (about a second of oracle time)
+    o = oracle.partition(kh, pred, want_keys=False)
+    assert o["num_true"][0] == T and np.array_equal(ih, o["indices"].astype(ih.dtype))
+    del o
     # the payload lands at its destination
     ph, po = pay.cpu().numpy(), r["payload_out"].cpu().numpy()
     assert np.array_equal(po[exp], ph[smp])
