@@ -78,6 +78,58 @@ __device__ __forceinline__ unsigned pred_mask(const DPred &p, const KT (&kv)[V],
     }
 }
 
+// The predicate over a thread's NS consecutive vector slots of V keys from e0 (bit
+// u * V + c = element e0 + u * V + c; positions at or past n are 0), with one
+// dispatch on the kind and one bounds mask for the whole run (NS * V <= 32).
+template <typename KT, int NS, int V>
+__device__ __forceinline__ unsigned pred_mask_run(const DPred &p, const KT (&kv)[NS][V], int64_t e0, int64_t n) {
+    constexpr int PER = NS * V;
+    static_assert(PER <= 32, "one 32-bit mask");
+    constexpr unsigned ALL = PER == 32 ? ~0u : (1u << PER) - 1u;
+    const unsigned valid = e0 + PER <= n ? ALL : (e0 >= n ? 0u : (1u << (unsigned)(n - e0)) - 1u);
+    unsigned m = 0;
+    switch (p.kind) {
+        case IXP_P_TRUE: return valid;
+        case IXP_P_LT:
+            if (sizeof(KT) == 4) {
+                if (p.b > (long long)INT32_MAX) return valid;
+                if (p.b <= (long long)INT32_MIN) return 0u;
+                const int32_t b = (int32_t)p.b;
+#pragma unroll
+                for (int u = 0; u < NS; u++)
+#pragma unroll
+                    for (int c = 0; c < V; c++) m |= (unsigned)((int32_t)kv[u][c] < b) << (u * V + c);
+            } else {
+#pragma unroll
+                for (int u = 0; u < NS; u++)
+#pragma unroll
+                    for (int c = 0; c < V; c++) m |= (unsigned)((int64_t)kv[u][c] < p.b) << (u * V + c);
+            }
+            return m & valid;
+        case IXP_P_MOD_EQ:
+            if (p.b < 0 || p.b >= (long long)p.a) return 0u;
+#pragma unroll
+            for (int u = 0; u < NS; u++)
+#pragma unroll
+                for (int c = 0; c < V; c++) {
+                    if (sizeof(KT) == 4) {
+                        int32_t r = (int32_t)kv[u][c] % p.a;
+                        r += r < 0 ? p.a : 0;
+                        m |= (unsigned)(r == (int32_t)p.b) << (u * V + c);
+                    } else {
+                        int64_t r = (int64_t)kv[u][c] % (int64_t)p.a;
+                        r += r < 0 ? (int64_t)p.a : 0;
+                        m |= (unsigned)(r == p.b) << (u * V + c);
+                    }
+                }
+            return m & valid;
+        default:
+#pragma unroll
+            for (int e = 0; e < PER; e++) m |= (unsigned)(((valid >> e) & 1u) && __ldg(p.flags + e0 + e) != 0) << e;
+            return m;
+    }
+}
+
 // Loads V consecutive elements of type T at p0 (vector loads when aligned and
 // in range, guarded scalar loads otherwise; missing elements read as 0).
 template <typename T, int V>

@@ -1122,16 +1122,10 @@ template <typename KT>
 __device__ __forceinline__ void seg_masks(const KT *__restrict__ keys, int64_t e0, int64_t n, int vec_ok, DPred filt,
                                           DPred part, unsigned &kk, unsigned &kt, KT (&kv)[SUB][16 / sizeof(KT)]) {
     constexpr int V = 16 / sizeof(KT);
-    kk = 0;
-    kt = 0;
 #pragma unroll
-    for (int u = 0; u < SUB; u++) {
-        const int64_t p0 = e0 + u * V;
-        load_slot<KT, V>(keys, p0, n, vec_ok, kv[u]);
-        const unsigned mk = pred_mask<KT, V>(filt, kv[u], p0, n);
-        kk |= mk << (u * V);
-        kt |= (mk & pred_mask<KT, V>(part, kv[u], p0, n)) << (u * V);
-    }
+    for (int u = 0; u < SUB; u++) load_slot<KT, V>(keys, e0 + u * V, n, vec_ok, kv[u]);
+    kk = pred_mask_run<KT, SUB, V>(filt, kv, e0, n);
+    kt = kk & pred_mask_run<KT, SUB, V>(part, kv, e0, n);
 }
 
 // Packed in-tile exclusive count (kept << 16 | kept true) of this thread's first
@@ -1259,6 +1253,16 @@ __global__ void __launch_bounds__(TB, 4) partition_seg_kernel(
     }
     const bool moves = out_keys || out_payload;
     OT dst[PER];
+    if (!moves && e0 + PER <= n && nxt >= r0 + PER) {
+        // no segment starts inside the run (the common case): every element is kept
+        // (partition2L has no filter), so its rank among the run's trues or falses
+        // is a popcount of the mask below it
+#pragma unroll
+        for (int j = 0; j < PER; j++) {
+            const unsigned tb = (unsigned)__popc(kt & ((1u << j) - 1u));
+            dst[j] = (OT)(((kt >> j) & 1u) ? bt + ct + (AT)tb : bf + cf + (AT)(j - tb));
+        }
+    } else
 #pragma unroll
     for (int j = 0; j < PER; j++) {
         const bool c = (kt >> j) & 1u;
@@ -1359,6 +1363,22 @@ __global__ void __launch_bounds__(TB, 4) filtpart_seg_kernel(
         nxt = seg_next_pos(W, L, s_start, off, nseg, t0);
     }
     int bad = INT_MAX;  // position in the thread's run
+    if (e0 + PER <= n && nxt >= r0 + PER) {
+        // no segment starts inside the run: ranks are popcounts of the masks below
+        // each element; the wrong elements collect in a mask
+        unsigned wm = 0;
+        const unsigned kf = kk & ~kt;
+#pragma unroll
+        for (int j = 0; j < PER; j++) {
+            const unsigned below = (1u << j) - 1u;
+            const bool c = (kt >> j) & 1u;
+            const AT ref = c ? bt + ct + (AT)__popc(kt & below) : bf + cf + (AT)__popc(kf & below);
+            const int64_t zi = (int64_t)zz[j];
+            const bool wrong = ((kk >> j) & 1u) ? zi != (int64_t)ref : (zi >= 0 && zi < Ntot);
+            wm |= (unsigned)wrong << j;
+        }
+        bad = wm ? __ffs(wm) - 1 : INT_MAX;
+    } else
 #pragma unroll
     for (int j = 0; j < PER; j++) {
         const bool kept = (kk >> j) & 1u, c = (kt >> j) & 1u;
