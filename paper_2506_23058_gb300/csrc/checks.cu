@@ -1092,7 +1092,12 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
 // Pass 2: one block per bucket, a W-bit bitmap in shared memory. Launched once per
 // pass-1 path (its grid and shared memory sized for that path's buckets); only the
 // launch whose path the setup kernel chose does the work.
-__global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, unsigned long long mode,
+//
+// NT threads a block: 256 for bitmaps up to 32 KB; 512 for 64 KB ones (two blocks
+// a SM: 512 buckets then take two waves of two buckets per SM instead of two waves
+// of three, with the same warps resident); 1024 for 128 KB (one a SM).
+template <int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 4 : (NT == 512 ? 2 : 1)) bucket_check_kernel(Hdr *h, unsigned long long mode,
                                                                   const unsigned *__restrict__ cursors,
                                                                   const unsigned *__restrict__ pool,
                                                                   const unsigned *__restrict__ marks,
@@ -1164,7 +1169,7 @@ __global__ void __launch_bounds__(BK_THREADS) bucket_check_kernel(Hdr *h, unsign
                 break;
             }
         }
-        __shared__ unsigned long long sm[BK_THREADS / 32];
+        __shared__ unsigned long long sm[NT / 32];
         unsigned long long r = block_max_u64(best == ~0ull ? 0ull : enc_first((int64_t)best), sm);
         if (threadIdx.x == 0) atomic_max_u64(&h->k_aux, r);
     }
@@ -1360,9 +1365,20 @@ static void launch_pass1(const T *x, int64_t n, int64_t rlo, int64_t rhi, const 
         bucket_scatter_kernel<T, BIJ, false><<<g1, BS_THREADS, bs_smem_bytes(shape.bmax, false), st>>>(
             x, n, rlo, rhi, w.h, shape, mode, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
     }
-    cudaFuncSetAttribute(bucket_check_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << 20) / 8);
-    bucket_check_kernel<<<shape.bmax, BK_THREADS, (1u << shape.lw) / 8, st>>>(w.h, mode, w.cursors, w.pool, w.bm,
-                                                                             w.dup, w.bmask, BIJ ? 1 : 0);
+    // shape.lw: the widest bucket this launch can be given (the device may choose a narrower one)
+    const unsigned bm_bytes = (1u << shape.lw) / 8;
+#define IXP_BK_CHECK(NT)                                                                                       \
+    cudaFuncSetAttribute(bucket_check_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (1 << 20) / 8);  \
+    bucket_check_kernel<NT><<<shape.bmax, NT, bm_bytes, st>>>(w.h, mode, w.cursors, w.pool, w.bm, w.dup, w.bmask, \
+                                                              BIJ ? 1 : 0)
+    if (bm_bytes <= 32768u) {
+        IXP_BK_CHECK(256);
+    } else if (bm_bytes <= 65536u) {
+        IXP_BK_CHECK(512);
+    } else {
+        IXP_BK_CHECK(1024);
+    }
+#undef IXP_BK_CHECK
 }
 
 // span_cap: the largest span the setup kernel can find (the fixed range, or the
