@@ -84,7 +84,7 @@ def make_ops(n32, n64, small=False):
 # of a few microseconds, or witness passes that run only on a violation).
 OP_KERNELS = {
     "range": "range_kernel", "mono": "mono_kernel",
-    "inj": "bucket_scatter_kernel + bucket_check_kernel", "bij": "bucket_scatter_kernel + bucket_check_kernel",
+    "inj": "bucket_slot_kernel + bucket_check_kernel", "bij": "bucket_slot_kernel + bucket_check_kernel",
     "scan_i32": "scan_tma_kernel<int, int>",
     "partition_p50": "count_tiles_kernel<int> + partition_flat_kernel<int, int, false>",
     "partition_p01": "count_tiles_kernel<int> + partition_flat_kernel<int, int, false>",

@@ -237,7 +237,6 @@ __global__ void mono_finalize(const T *x, const Hdr *h, ixp_verdict *out) {
 
 // ================================================================ Inj / Bij
 constexpr int BK_TILE = 8192;
-constexpr int BK_THREADS = 256;
 constexpr unsigned BK_MAX = 4096;
 // Header slots of the bucketed path: bucket count, pool entries per bucket, log2 of
 // the bucket width, and the launch shape the setup kernel chose for the span it
@@ -839,19 +838,39 @@ __global__ void bucket_setup_kernel(Hdr *h, int fixed, int64_t lo, int64_t hi, u
 // Pass 1: each block takes tiles of BK_TILE elements. An element whose value lies
 // in [base, base + span) (the bitmap's range: Img for Bij, the fixed Rcd or the
 // observed [min, max] for Inj) has rel = value - base, bucket rel >> lw and offset
-// rel & (W - 1). The tile is counting-sorted by bucket in shared memory (the rank
-// within the bucket comes from the counting atomic itself) and written to the
-// per-bucket pools as contiguous runs; entries past a bucket's capacity go to the
+// rel & (W - 1); its rank among the tile's entries of its bucket is the return
+// value of the bucket's counting atomic. Each bucket's entries are written to its
+// pool as one contiguous run; entries past a bucket's pool capacity go to the
 // global bitmap through L2 atomics instead. For Bij, elements of Rcd outside Img
 // give the first such index (k_first).
+//
+// Two kernels. bucket_slot_kernel (at most BS_SLOT_NB buckets: the staged shape)
+// stores each entry straight into a fixed row of BS_CAP slots of its bucket at its
+// rank, so a tile needs neither a block-wide scan of the bucket counts nor a lookup
+// of its bucket's start; each warp then moves the rows of its 32 buckets to the
+// pools. A tile in which some bucket gets more than BS_CAP entries (clustered or
+// repeated values) is redone from the registers by the counting sort below. That
+// counting sort (scan of the counts, entries placed in bucket order in shared
+// memory, runs written out) is all of bucket_scatter_kernel, which serves the wide
+// shape (up to BK_MAX buckets).
 constexpr int BS_THREADS = 512;
 constexpr int BS_PER = BK_TILE / BS_THREADS;  // elements per thread per tile
 constexpr unsigned BS_PAD_MAX = 1024;         // most buckets for the padded-run write-out
+constexpr unsigned BS_SLOT_NB = 512;          // buckets of the slot kernel: 16 entries per bucket per tile
+constexpr unsigned BS_CAP = 40;               // slots per bucket row (a multiple of 4: whole 16-byte chunks)
+// Row stride in words: a multiple of 4 (16-byte rows, read back as 16-byte chunks)
+// that is an odd multiple of 4, so that rows of random buckets start in 8 different
+// bank groups (the ranks stored at the same time are close to one another, and with
+// a stride of 48 words the stores fell into two groups and took twice as long). Word
+// BS_CAP of a row is a spare that takes the stores of ranks past BS_CAP.
+constexpr unsigned BS_STRIDE = BS_CAP + 4;
+static_assert(BS_STRIDE % 4 == 0 && (BS_STRIDE / 4) % 2 == 1, "16-byte rows, odd in 16-byte units");
+constexpr unsigned BS_SENT = ~0u;             // pad entry (pass 2 skips it)
 
-// Shared memory of pass 1. Per bucket: pool index of tile slot 0 (8 bytes), count,
-// start, limit (4 bytes each); the sorted tile (TILE entries, plus up to 3 pad
-// entries per bucket when runs are padded to 16-byte chunks); with padding, the
-// bucket of each 16-byte chunk (2 bytes).
+// Shared memory of the counting sort. Per bucket: pool index of tile slot 0 (8
+// bytes), count, start, limit (4 bytes each); the sorted tile (TILE entries, plus up
+// to 3 pad entries per bucket when runs are padded to 16-byte chunks); with padding,
+// the bucket of each 16-byte chunk (2 bytes).
 // Layout: sorted tile (16-byte aligned, rounded to whole chunks) | pool index of
 // slot 0 per bucket | count | start | limit | chunk -> bucket.
 __host__ __device__ constexpr unsigned bs_sorted_cap(unsigned bmax, bool pad) {
@@ -861,6 +880,15 @@ __host__ __device__ constexpr size_t bs_smem_bytes(unsigned bmax, bool pad) {
     return (size_t)bs_sorted_cap(bmax, pad) * 4 + (size_t)bmax * (8 + 4 + 4 + 4) +
            (pad ? (size_t)(bs_sorted_cap(bmax, pad) / 4) * 2 : 0);
 }
+// Shared memory of the slot kernel: the counts (BS_SLOT_NB words), then one region
+// that holds either the slot rows or the counting sort's arrays other than the
+// counts (a tile that falls back to the counting sort no longer needs its rows).
+__host__ __device__ constexpr size_t bs_slot_region_bytes() {
+    return (size_t)BS_SLOT_NB * BS_STRIDE * 4 > bs_smem_bytes(BS_SLOT_NB, true) - (size_t)BS_SLOT_NB * 4
+               ? (size_t)BS_SLOT_NB * BS_STRIDE * 4
+               : bs_smem_bytes(BS_SLOT_NB, true) - (size_t)BS_SLOT_NB * 4;
+}
+__host__ __device__ constexpr size_t bs_slot_smem_bytes() { return (size_t)BS_SLOT_NB * 4 + bs_slot_region_bytes(); }
 
 // Bucket of an element, or -1 when its value is outside [base, base + span):
 // rel = x - base in 64 bits, or in 32 bits when the caller has checked that the
@@ -909,6 +937,185 @@ __device__ __forceinline__ void bs_classify(const T (&e)[BS_PER / Vec<T>::N][Vec
     }
 }
 
+// Loads one tile's elements (16-byte vectors when the array is 16-byte aligned,
+// zeros past n).
+template <typename T>
+__device__ __forceinline__ void bs_load(const T *__restrict__ x, int64_t t0, int64_t n, bool full, int vec_ok, int tid,
+                                        T (&e)[BS_PER / Vec<T>::N][Vec<T>::N]) {
+    constexpr int V = Vec<T>::N;
+    constexpr int NV = BS_PER / V;
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+        const int64_t p0 = t0 + (int64_t)(j * BS_THREADS + tid) * V;
+        if (vec_ok && (full || p0 + V <= n)) {
+            if (V == 4) {
+                int4 v = __ldcs(reinterpret_cast<const int4 *>(x + p0));
+                e[j][0] = (T)v.x;
+                e[j][1 % V] = (T)v.y;
+                e[j][2 % V] = (T)v.z;
+                e[j][3 % V] = (T)v.w;
+            } else {
+                longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(x + p0));
+                e[j][0] = (T)v.x;
+                e[j][1 % V] = (T)v.y;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < V; c++) e[j][c] = (p0 + c < n) ? x[p0 + c] : (T)0;
+        }
+    }
+}
+
+// An entry that does not fit its bucket's pool region: its bit goes straight into
+// the global mark bitmap (pass 2 merges it), a bit already set is a repeat.
+__device__ __forceinline__ void bs_spill(unsigned v, unsigned b, unsigned *marks, unsigned *dup, unsigned *bucket_mask,
+                                         unsigned &anydup) {
+    const unsigned bit = 1u << (v & 31);
+    const unsigned old = atomicOr(marks + (v >> 5), bit);
+    if (old & bit) {
+        atomicOr(dup + (v >> 5), bit);
+        atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
+        anydup = 1;
+    }
+}
+
+// Shared arrays of the counting sort.
+struct BsSort {
+    unsigned *cnt;         // nb: entries per bucket (filled by bs_classify)
+    unsigned *sorted;      // the tile in bucket order (+ pads)
+    long long *dst;        // pool index of tile slot 0, per bucket
+    unsigned *start;       // first tile slot, per bucket
+    unsigned *lim;         // tile slots below this fit the pool, per bucket
+    unsigned short *cb;    // bucket of each 16-byte chunk (PAD)
+    unsigned *wsum;        // BS_THREADS / 32
+    unsigned *total;       // 1
+};
+
+// The counting sort of one tile whose ranks are counted (s.cnt, rk): exclusive scan
+// of the (padded) bucket counts, pool space reserved per bucket with one atomicAdd
+// each, entries placed in bucket order, runs written out. PAD: runs padded to whole
+// 16-byte chunks written as 16-byte stores (every chunk lies in one bucket's run and
+// starts on a 16-byte boundary of the pool: bucket regions, cursors and runs are all
+// multiples of four entries); otherwise entries keep their bucket in the sorted tile
+// and are stored one by one. Contains two block barriers; returns before the sorted
+// tile has been read by every thread.
+template <bool PAD>
+__device__ __forceinline__ void bs_sort_tile(const BsSort &s, const unsigned (&rv)[BS_PER],
+                                             const unsigned (&rk)[BS_PER], unsigned vm, unsigned nb, unsigned lw,
+                                             unsigned long long cap, unsigned *__restrict__ cursors,
+                                             unsigned *__restrict__ pool, unsigned *__restrict__ marks,
+                                             unsigned *__restrict__ dup, unsigned *__restrict__ bucket_mask,
+                                             unsigned &anydup) {
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned wmask = (1u << lw) - 1u;
+    const unsigned per = (nb + BS_THREADS - 1) / BS_THREADS;  // bucket-count scan entries per thread
+    {
+        unsigned loc = 0;
+        const unsigned b0 = tid * per;
+        for (unsigned k = 0; k < per; k++)
+            if (b0 + k < nb) loc += PAD ? (s.cnt[b0 + k] + 3u) & ~3u : s.cnt[b0 + k];
+        unsigned y = loc;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            unsigned o = __shfl_up_sync(FULL, y, d);
+            if (lane >= d) y += o;
+        }
+        if (lane == 31) s.wsum[wid] = y;
+        __syncthreads();
+        unsigned wpre = 0, tot = 0;
+#pragma unroll
+        for (int i = 0; i < BS_THREADS / 32; i++) {
+            wpre += i < wid ? s.wsum[i] : 0u;
+            tot += s.wsum[i];
+        }
+        unsigned run = wpre + y - loc;
+        for (unsigned k = 0; k < per; k++)
+            if (b0 + k < nb) {
+                const unsigned b = b0 + k, c = s.cnt[b];
+                const unsigned cr = PAD ? (c + 3u) & ~3u : c;  // reserved entries
+                const unsigned long long g = cr ? atomicAdd(&cursors[b], cr) : 0ull;
+                s.start[b] = run;
+                s.dst[b] = (long long)((unsigned long long)b * cap + g) - (long long)run;
+                s.lim[b] = g >= cap ? run : run + (unsigned)min((unsigned long long)cr, cap - g);
+                if (PAD) {
+                    for (unsigned p = c; p < cr; p++) s.sorted[run + p] = BS_SENT;
+                    for (unsigned p = 0; p < cr; p += 4) s.cb[(run + p) >> 2] = (unsigned short)b;
+                }
+                run += cr;
+            }
+        if (tid == 0) *s.total = tot;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < BS_PER; q++)
+        if ((vm >> q) & 1u) s.sorted[s.start[rv[q] >> lw] + rk[q]] = PAD ? (rv[q] & wmask) : rv[q];
+    __syncthreads();
+    const unsigned total = *s.total;
+    if (PAD) {
+        for (unsigned k = tid; k < total / 4; k += BS_THREADS) {
+            const unsigned b = s.cb[k];
+            const unsigned p = 4 * k;
+            const uint4 d = *reinterpret_cast<const uint4 *>(s.sorted + p);
+            const long long dst = s.dst[b] + (long long)p;
+            const unsigned lim = s.lim[b];
+            if (p + 4 <= lim) {
+                __stcs(reinterpret_cast<uint4 *>(pool + dst), d);
+            } else {
+                const unsigned o[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+                for (int c = 0; c < 4; c++) {
+                    if (p + c < lim) pool[dst + c] = o[c];  // pads too: pass 2 reads every reserved slot
+                    else if (o[c] != BS_SENT) bs_spill((b << lw) | o[c], b, marks, dup, bucket_mask, anydup);
+                }
+            }
+        }
+    } else {
+        for (unsigned p = tid; p < total; p += BS_THREADS) {
+            const unsigned v = s.sorted[p];
+            const unsigned b = v >> lw;
+            if (p < s.lim[b]) __stcs(pool + (s.dst[b] + (long long)p), v & wmask);
+            else bs_spill(v, b, marks, dup, bucket_mask, anydup);
+        }
+    }
+}
+
+// Per-block results of pass 1: in-range count, whether a spilled entry repeated,
+// and (Bij) the first element of Rcd outside Img.
+template <bool BIJ>
+__device__ __forceinline__ void bs_finish(Hdr *h, unsigned long long valid, unsigned anydup, int64_t ooi) {
+    __shared__ unsigned long long sm[BS_THREADS / 32];
+    const unsigned long long tv = block_sum_u64(valid, sm);
+    if (threadIdx.x == 0 && tv) atomicAdd(&h->cnt0, tv);
+    if (__syncthreads_or(anydup) && threadIdx.x == 0) atomicOr(&h->flag, 1u);
+    if (BIJ) {
+        const unsigned long long r = block_max_u64(ooi == INT64_MAX ? 0ull : enc_first(ooi), sm);
+        if (threadIdx.x == 0) atomic_max_u64(&h->k_first, r);
+    }
+}
+
+// Whether [base, base + span) lies in the int32 range, so that 32-bit relative
+// values are exact.
+template <typename T>
+__device__ __forceinline__ bool bs_r32(unsigned long long base, unsigned long long span) {
+    return sizeof(T) == 4 && span >= 1 && span <= (1ull << 32) && (int64_t)base >= (int64_t)INT32_MIN &&
+           (int64_t)base <= (int64_t)INT32_MAX && (int64_t)base + (int64_t)(span - 1) <= (int64_t)INT32_MAX;
+}
+
+template <typename T, bool BIJ>
+__device__ __forceinline__ void bs_classify_tile(const T (&e)[BS_PER / Vec<T>::N][Vec<T>::N], bool r32, bool full,
+                                                 int64_t t0, int64_t n, unsigned long long base,
+                                                 unsigned long long span, unsigned span_m1, unsigned lw,
+                                                 unsigned *s_cnt, int64_t rlo, int64_t rhi, unsigned (&rv)[BS_PER],
+                                                 unsigned (&rk)[BS_PER], unsigned &vm, int64_t &ooi) {
+    const int tid = threadIdx.x;
+    if (r32 && full)
+        bs_classify<T, BIJ, true, true>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm, ooi);
+    else if (full)
+        bs_classify<T, BIJ, false, true>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm, ooi);
+    else
+        bs_classify<T, BIJ, false, false>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm, ooi);
+}
+
 template <typename T, bool BIJ, bool PAD>
 __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
     const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, Hdr *h, BucketCfg cfg, unsigned long long mode,
@@ -917,176 +1124,212 @@ __global__ void __launch_bounds__(BS_THREADS, 2) bucket_scatter_kernel(
     IXP_KERNEL_ENTRY();
     if (h->status || h->spare[BK_MODE] != mode) return;
     constexpr int V = Vec<T>::N;
-    constexpr int NV = BS_PER / V;  // 16-byte vectors per thread per tile
-    constexpr unsigned SENT = ~0u;  // pad entry (pass 2 skips it)
     extern __shared__ __align__(16) unsigned char bk_raw[];
-    const unsigned bmax = cfg.bmax;
-    unsigned *s_sorted = reinterpret_cast<unsigned *>(bk_raw);              // TILE (+ 3 bmax pads)
-    long long *s_dst = reinterpret_cast<long long *>(s_sorted + bs_sorted_cap(bmax, PAD));  // pool index of slot 0
-    unsigned *s_cnt = reinterpret_cast<unsigned *>(s_dst + bmax);            // bmax
-    unsigned *s_start = s_cnt + bmax;                                        // bmax
-    unsigned *s_lim = s_start + bmax;                                        // bmax: slots below fit the pool
-    unsigned short *s_cb = reinterpret_cast<unsigned short *>(s_lim + bmax);  // chunk -> bucket (PAD)
     __shared__ unsigned s_wsum[BS_THREADS / 32];
     __shared__ unsigned s_total;
+    const unsigned bmax = cfg.bmax;
+    BsSort s;
+    s.sorted = reinterpret_cast<unsigned *>(bk_raw);
+    s.dst = reinterpret_cast<long long *>(s.sorted + bs_sorted_cap(bmax, PAD));
+    s.cnt = reinterpret_cast<unsigned *>(s.dst + bmax);
+    s.start = s.cnt + bmax;
+    s.lim = s.start + bmax;
+    s.cb = reinterpret_cast<unsigned short *>(s.lim + bmax);
+    s.wsum = s_wsum;
+    s.total = &s_total;
     const unsigned long long base = h->base, span = h->span;
     const unsigned nb = (unsigned)h->spare[BK_NB];
     const unsigned long long cap = h->spare[BK_CAP];
     const unsigned lw = (unsigned)h->spare[BK_LW];
-    const unsigned wmask = (1u << lw) - 1u;
-    // 32-bit relative values are exact when [base, base + span) lies in the int32 range
-    const bool r32 = sizeof(T) == 4 && span >= 1 && span <= (1ull << 32) && (int64_t)base >= (int64_t)INT32_MIN &&
-                     (int64_t)base <= (int64_t)INT32_MAX && (int64_t)base + (int64_t)(span - 1) <= (int64_t)INT32_MAX;
+    const bool r32 = bs_r32<T>(base, span);
     const unsigned span_m1 = (unsigned)(span - 1);
     const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    unsigned long long valid = 0;  // kept by thread 0 only
+    const int tid = threadIdx.x;
+    unsigned long long valid = 0;
     unsigned anydup = 0;
     int64_t ooi = INT64_MAX;
-    const unsigned per = (nb + BS_THREADS - 1) / BS_THREADS;  // bucket-count scan entries per thread
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t t0 = tile * BK_TILE;
         const bool full = t0 + BK_TILE <= n;
-        for (unsigned b = tid; b < nb; b += BS_THREADS) s_cnt[b] = 0u;
-        T e[NV][V];
-#pragma unroll
-        for (int j = 0; j < NV; j++) {
-            const int64_t p0 = t0 + (int64_t)(j * BS_THREADS + tid) * V;
-            if (vec_ok && (full || p0 + V <= n)) {
-                if (V == 4) {
-                    int4 v = __ldcs(reinterpret_cast<const int4 *>(x + p0));
-                    e[j][0] = (T)v.x;
-                    e[j][1 % V] = (T)v.y;
-                    e[j][2 % V] = (T)v.z;
-                    e[j][3 % V] = (T)v.w;
-                } else {
-                    longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(x + p0));
-                    e[j][0] = (T)v.x;
-                    e[j][1 % V] = (T)v.y;
-                }
-            } else {
-#pragma unroll
-                for (int c = 0; c < V; c++) e[j][c] = (p0 + c < n) ? x[p0 + c] : (T)0;
-            }
-        }
-        __syncthreads();  // s_cnt zeroed
+        for (unsigned b = tid; b < nb; b += BS_THREADS) s.cnt[b] = 0u;
+        T e[BS_PER / V][V];
+        bs_load<T>(x, t0, n, full, vec_ok, tid, e);
+        __syncthreads();  // counts zeroed
         unsigned rv[BS_PER], rk[BS_PER], vm = 0;
-        if (r32 && full)
-            bs_classify<T, BIJ, true, true>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm, ooi);
-        else if (full)
-            bs_classify<T, BIJ, false, true>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm,
-                                             ooi);
-        else
-            bs_classify<T, BIJ, false, false>(e, t0, n, tid, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm,
-                                              ooi);
+        bs_classify_tile<T, BIJ>(e, r32, full, t0, n, base, span, span_m1, lw, s.cnt, rlo, rhi, rv, rk, vm, ooi);
         __syncthreads();
-        // exclusive scan of the (padded) bucket counts; reserve pool space per bucket
-        {
-            unsigned loc = 0;
-            const unsigned b0 = tid * per;
-            for (unsigned k = 0; k < per; k++)
-                if (b0 + k < nb) loc += PAD ? (s_cnt[b0 + k] + 3u) & ~3u : s_cnt[b0 + k];
-            unsigned y = loc;
+        bs_sort_tile<PAD>(s, rv, rk, vm, nb, lw, cap, cursors, pool, marks, dup, bucket_mask, anydup);
+        valid += __popc(vm);
+        __syncthreads();
+    }
+    bs_finish<BIJ>(h, valid, anydup, ooi);
+}
+
+// The slot kernel (staged shape, nb <= BS_SLOT_NB, n < 2^31). Per tile: classify
+// (ranks from the counting atomics) and store each entry at slot row (bucket) x
+// BS_STRIDE + rank. Unless a bucket overflowed its row, warp w moves the rows of buckets 32w ..
+// 32w + 31: lane l reserves bucket 32w + l's run (its count rounded up to whole
+// 16-byte chunks, the pad entries BS_SENT) with one atomicAdd, a warp scan of the
+// chunk counts lays the 32 runs end to end, and lane j of round i moves chunk 32i + j
+// of that sequence, finding its bucket from a bitmap of the runs' first chunks and
+// the bucket's run from a per-warp table (one entry per non-empty bucket).
+constexpr int BS_MAPW = 16;  // map words per warp: at least (32 x BS_CAP / 4) / 32
+static_assert(32 * (BS_CAP / 4) <= 32 * BS_MAPW && 32 * (BS_CAP / 4) < 1024 && BS_CAP < 64,
+              "run table packing: first chunk in 10 bits, count and limit in 6 and 8 bits");
+template <typename T, bool BIJ>
+__global__ void __launch_bounds__(BS_THREADS, 2) bucket_slot_kernel(
+    const T *__restrict__ x, int64_t n, int64_t rlo, int64_t rhi, Hdr *h, unsigned long long mode,
+    unsigned *__restrict__ cursors, unsigned *__restrict__ pool, unsigned *__restrict__ marks,
+    unsigned *__restrict__ dup, unsigned *__restrict__ bucket_mask, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != mode) return;
+    constexpr int V = Vec<T>::N;
+    extern __shared__ __align__(16) unsigned char bk_raw[];
+    __shared__ unsigned s_wsum[BS_THREADS / 32];
+    __shared__ unsigned s_total;
+    __shared__ unsigned s_map[BS_THREADS / 32][BS_MAPW];  // first chunks of the warp's runs
+    __shared__ uint2 s_tab[BS_THREADS / 32][32];          // per non-empty bucket: reserved slot, packed run
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(bk_raw);
+    unsigned *s_slot = s_cnt + BS_SLOT_NB;  // BS_SLOT_NB rows of BS_STRIDE words
+    const unsigned long long base = h->base, span = h->span;
+    const unsigned nb = (unsigned)h->spare[BK_NB];
+    const unsigned cap = (unsigned)h->spare[BK_CAP];  // pool entries (and so positions) are below 2^32
+    const unsigned lw = (unsigned)h->spare[BK_LW];
+    const unsigned wmask = (1u << lw) - 1u;
+    const bool r32 = bs_r32<T>(base, span);
+    const unsigned span_m1 = (unsigned)(span - 1);
+    const unsigned ntiles = (unsigned)((n + BK_TILE - 1) / BK_TILE);  // n < 2^31
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned lane_le = lane == 31 ? FULL : (2u << lane) - 1u;
+    unsigned valid = 0;  // in-range entries this thread saw (n < 2^31)
+    unsigned anydup = 0;
+    int64_t ooi = INT64_MAX;
+    for (unsigned b = tid; b < BS_SLOT_NB; b += BS_THREADS) s_cnt[b] = 0u;
+    __syncthreads();
+    for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t t0 = (int64_t)tile * BK_TILE;
+        const bool full = t0 + BK_TILE <= n;
+        T e[BS_PER / V][V];
+        bs_load<T>(x, t0, n, full, vec_ok, tid, e);
+        unsigned rv[BS_PER], rk[BS_PER], vm = 0, ovf = 0;
+        // the common case, every element of the thread's share in range: no branch
+        // per element (a rank past BS_CAP stores into the row's spare word)
+        // (int64: the test first, rv after it, so that the 64-bit values die as rv fills)
+        constexpr bool KEEP = sizeof(T) == 4;
+        // (not for int64 Bij, where both forms inline would spill registers)
+        bool all_in = full && !(BIJ && sizeof(T) == 8);
+        if (all_in) {
+#pragma unroll
+            for (int j = 0; j < BS_PER / V; j++)
+#pragma unroll
+                for (int c = 0; c < V; c++) {
+                    unsigned rel;
+                    all_in &= r32 ? bs_rel<true>(e[j][c], base, span, span_m1, rel)
+                                  : bs_rel<false>(e[j][c], base, span, span_m1, rel);
+                    if (KEEP) rv[j * V + c] = rel;
+                }
+        }
+        if (all_in) {
+            if (!KEEP)
+#pragma unroll
+                for (int j = 0; j < BS_PER / V; j++)
+#pragma unroll
+                    for (int c = 0; c < V; c++) rv[j * V + c] = (unsigned)((unsigned long long)(int64_t)e[j][c] - base);
+#pragma unroll
+            for (int q = 0; q < BS_PER; q++) rk[q] = atomicAdd(&s_cnt[rv[q] >> lw], 1u);
+#pragma unroll
+            for (int q = 0; q < BS_PER; q++) {
+                s_slot[(rv[q] >> lw) * BS_STRIDE + min(rk[q], BS_CAP)] = rv[q] & wmask;
+                ovf |= rk[q] >= BS_CAP;
+            }
+            vm = (1u << BS_PER) - 1u;
+        } else {
+            bs_classify_tile<T, BIJ>(e, r32, full, t0, n, base, span, span_m1, lw, s_cnt, rlo, rhi, rv, rk, vm, ooi);
+#pragma unroll
+            for (int q = 0; q < BS_PER; q++)
+                if ((vm >> q) & 1u) {
+                    if (rk[q] < BS_CAP) s_slot[(rv[q] >> lw) * BS_STRIDE + rk[q]] = rv[q] & wmask;
+                    else ovf = 1;
+                }
+        }
+        valid += __popc(vm);
+        if (__syncthreads_or(ovf)) {
+            // count again (the ranks were not kept) and sort the tile instead
+            for (unsigned b = tid; b < BS_SLOT_NB; b += BS_THREADS) s_cnt[b] = 0u;
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < BS_PER; q++)
+                if ((vm >> q) & 1u) rk[q] = atomicAdd(&s_cnt[rv[q] >> lw], 1u);
+            __syncthreads();
+            BsSort s;  // the counting sort's arrays overlay the rows
+            s.cnt = s_cnt;
+            s.sorted = s_slot;
+            s.dst = reinterpret_cast<long long *>(s.sorted + bs_sorted_cap(BS_SLOT_NB, true));
+            s.start = reinterpret_cast<unsigned *>(s.dst + BS_SLOT_NB);
+            s.lim = s.start + BS_SLOT_NB;
+            s.cb = reinterpret_cast<unsigned short *>(s.lim + BS_SLOT_NB);
+            s.wsum = s_wsum;
+            s.total = &s_total;
+            bs_sort_tile<true>(s, rv, rk, vm, nb, lw, cap, cursors, pool, marks, dup, bucket_mask, anydup);
+            // every thread is past the scan, the last reader of the counts
+            for (unsigned b = tid; b < BS_SLOT_NB; b += BS_THREADS) s_cnt[b] = 0u;
+        } else {
+            const unsigned bl = wid * 32 + lane;
+            unsigned c = 0;
+            if (bl < nb) {
+                c = s_cnt[bl];
+                s_cnt[bl] = 0u;
+            }
+            const unsigned cr = (c + 3u) & ~3u;  // reserved entries, c <= BS_CAP
+            const unsigned g = cr ? atomicAdd(&cursors[bl], cr) : 0u;
+            const unsigned lim = g >= cap ? 0u : min(cr, cap - g);
+            const unsigned nch = cr >> 2;
+            unsigned sc = nch;
 #pragma unroll
             for (int d = 1; d < 32; d <<= 1) {
-                unsigned o = __shfl_up_sync(FULL, y, d);
-                if (lane >= d) y += o;
+                const unsigned o = __shfl_up_sync(FULL, sc, d);
+                if (lane >= d) sc += o;
             }
-            if (lane == 31) s_wsum[wid] = y;
-            __syncthreads();
-            unsigned wpre = 0, tot = 0;
-#pragma unroll
-            for (int i = 0; i < BS_THREADS / 32; i++) {
-                wpre += i < wid ? s_wsum[i] : 0u;
-                tot += s_wsum[i];
+            const unsigned first = sc - nch, nchunks = __shfl_sync(FULL, sc, 31);
+            const unsigned nz = __ballot_sync(FULL, nch != 0);
+            if (lane < BS_MAPW) s_map[wid][lane] = 0u;
+            __syncwarp();
+            if (nch) {
+                atomicOr(&s_map[wid][first >> 5], 1u << (first & 31));
+                s_tab[wid][__popc(nz & (lane_le >> 1))] =
+                    make_uint2(g, first | (c << 10) | (lim << 16) | ((unsigned)lane << 24));
             }
-            unsigned run = wpre + y - loc;
-            for (unsigned k = 0; k < per; k++)
-                if (b0 + k < nb) {
-                    const unsigned b = b0 + k, c = s_cnt[b];
-                    const unsigned cr = PAD ? (c + 3u) & ~3u : c;  // reserved entries
-                    const unsigned long long g = cr ? atomicAdd(&cursors[b], cr) : 0ull;
-                    s_start[b] = run;
-                    s_dst[b] = (long long)((unsigned long long)b * cap + g) - (long long)run;
-                    s_lim[b] = g >= cap ? run : run + (unsigned)min((unsigned long long)cr, cap - g);
-                    if (PAD) {
-                        for (unsigned p = c; p < cr; p++) s_sorted[run + p] = SENT;
-                        for (unsigned p = 0; p < cr; p += 4) s_cb[(run + p) >> 2] = (unsigned short)b;
-                    }
-                    run += cr;
-                }
-            if (tid == 0) s_total = tot;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < BS_PER; q++)
-            if ((vm >> q) & 1u) s_sorted[s_start[rv[q] >> lw] + rk[q]] = PAD ? (rv[q] & wmask) : rv[q];
-        __syncthreads();
-        const unsigned total = s_total;
-        if (PAD) {
-            // 16-byte chunks: every chunk lies in one bucket's run and starts on a
-            // 16-byte boundary of the pool (bucket regions, cursors and runs are all
-            // multiples of four entries).
-            for (unsigned k = tid; k < total / 4; k += BS_THREADS) {
-                const unsigned b = s_cb[k];
-                const unsigned p = 4 * k;
-                const uint4 d = *reinterpret_cast<const uint4 *>(s_sorted + p);
-                const long long dst = s_dst[b] + (long long)p;
-                const unsigned lim = s_lim[b];
-                if (p + 4 <= lim) {
-                    __stcs(reinterpret_cast<uint4 *>(pool + dst), d);
+            __syncwarp();
+            unsigned before = 0;  // runs that start in earlier map words
+#pragma unroll 1
+            for (unsigned i = 0; 32 * i < nchunks; i++) {
+                const unsigned word = s_map[wid][i];
+                const unsigned r = before + __popc(word & lane_le) - 1u;  // this chunk's run
+                before += __popc(word);
+                const unsigned k = 32 * i + lane;
+                if (k >= nchunks) continue;
+                const uint2 tv = s_tab[wid][r];
+                const unsigned cb = (tv.y >> 10) & 63u, limb = (tv.y >> 16) & 255u;
+                const unsigned b = wid * 32 + (tv.y >> 24);
+                const unsigned p = 4 * (k - (tv.y & 1023u));
+                const uint4 d = *reinterpret_cast<const uint4 *>(s_slot + b * BS_STRIDE + p);
+                const unsigned o[4] = {p < cb ? d.x : BS_SENT, p + 1 < cb ? d.y : BS_SENT, p + 2 < cb ? d.z : BS_SENT,
+                                       p + 3 < cb ? d.w : BS_SENT};
+                const unsigned long long dst = (unsigned long long)b * cap + tv.x + p;
+                if (p + 4 <= limb) {
+                    __stcs(reinterpret_cast<uint4 *>(pool + dst), make_uint4(o[0], o[1], o[2], o[3]));
                 } else {
-                    const unsigned o[4] = {d.x, d.y, d.z, d.w};
 #pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        if (p + c < lim) {
-                            pool[dst + c] = o[c];  // pads too: pass 2 reads every reserved slot
-                        } else if (o[c] != SENT) {
-                            const unsigned v = (b << lw) | o[c];
-                            const unsigned bit = 1u << (v & 31);
-                            const unsigned old = atomicOr(marks + (v >> 5), bit);
-                            if (old & bit) {
-                                atomicOr(dup + (v >> 5), bit);
-                                atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
-                                anydup = 1;
-                            }
-                        }
-                    }
-                }
-            }
-        } else {
-            if (tid == 0) valid += total;
-            for (unsigned p = tid; p < total; p += BS_THREADS) {
-                const unsigned v = s_sorted[p];
-                const unsigned b = v >> lw;
-                if (p < s_lim[b]) {
-                    __stcs(pool + (s_dst[b] + (long long)p), v & wmask);
-                } else {
-                    const unsigned bit = 1u << (v & 31);
-                    const unsigned old = atomicOr(marks + (v >> 5), bit);
-                    if (old & bit) {
-                        atomicOr(dup + (v >> 5), bit);
-                        atomicOr(bucket_mask + (b >> 5), 1u << (b & 31));
-                        anydup = 1;
+                    for (int j = 0; j < 4; j++) {
+                        if (p + j < limb) pool[dst + j] = o[j];  // pads too: pass 2 reads every reserved slot
+                        else if (o[j] != BS_SENT) bs_spill((b << lw) | o[j], b, marks, dup, bucket_mask, anydup);
                     }
                 }
             }
         }
-        if (PAD) valid += __popc(vm);  // per thread; summed over the block at the end
-        __syncthreads();
+        __syncthreads();  // rows (or the sorted tile) read, counts zeroed
     }
-    __shared__ unsigned long long sm[BS_THREADS / 32];
-    if (PAD) {
-        const unsigned long long tv = block_sum_u64(valid, sm);
-        if (tid == 0 && tv) atomicAdd(&h->cnt0, tv);
-    } else {
-        if (tid == 0 && valid) atomicAdd(&h->cnt0, valid);
-    }
-    if (__syncthreads_or(anydup) && tid == 0) atomicOr(&h->flag, 1u);
-    if (BIJ) {
-        const unsigned long long r = block_max_u64(ooi == INT64_MAX ? 0ull : enc_first(ooi), sm);
-        if (tid == 0) atomic_max_u64(&h->k_first, r);
-    }
+    bs_finish<BIJ>(h, (unsigned long long)valid, anydup, ooi);
 }
 
 // Pass 2: one block per bucket, a W-bit bitmap in shared memory. Launched once per
@@ -1353,7 +1596,13 @@ static void launch_pass1(const T *x, int64_t n, int64_t rlo, int64_t rhi, const 
                          unsigned long long mode, int vec, cudaStream_t st) {
     const int64_t ntiles = (n + BK_TILE - 1) / BK_TILE;
     const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 2));
-    if (shape.bmax <= BS_PAD_MAX && n < (1ll << 31)) {
+    if (shape.bmax <= BS_SLOT_NB && n < (1ll << 31)) {
+        // fixed slot rows per bucket (16 elements per bucket per tile on average)
+        cudaFuncSetAttribute(bucket_slot_kernel<T, BIJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bs_slot_smem_bytes());
+        bucket_slot_kernel<T, BIJ><<<g1, BS_THREADS, bs_slot_smem_bytes(), st>>>(
+            x, n, rlo, rhi, w.h, mode, w.cursors, w.pool, w.bm, w.dup, w.bmask, vec);
+    } else if (shape.bmax <= BS_PAD_MAX && n < (1ll << 31)) {
         // runs padded to 16-byte chunks (at least 8 elements per bucket per tile on average)
         cudaFuncSetAttribute(bucket_scatter_kernel<T, BIJ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bs_smem_bytes(BS_PAD_MAX, true));

@@ -262,6 +262,33 @@ def test_inj_bucketed_skewed_overflow(ixp, dev, dtype):
 
 
 @pytest.mark.parametrize("dtype", [np.int32, np.int64])
+def test_inj_bucketed_pool_overflow_without_row_overflow(ixp, dev, dtype):
+    # 512 buckets of 2^15 values over [0, 2^24): every 8192-element tile holds 30
+    # values of bucket 0 and about 16 of each other bucket, so no tile overflows a
+    # bucket's slot row, but bucket 0 receives more entries in total than its pool
+    # region holds; the tiles that come last send them through the L2-atomic path
+    rng = np.random.default_rng(23)
+    n, tile, k0 = 1 << 20, 8192, 30
+    ntile = n // tile
+    b0 = rng.permutation(1 << 15)[: ntile * k0]
+    rest = (1 << 15) + rng.choice((1 << 24) - (1 << 15), size=n - ntile * k0, replace=False)
+    parts = []
+    for t in range(ntile):
+        chunk = np.concatenate([b0[t * k0:(t + 1) * k0], rest[t * (tile - k0):(t + 1) * (tile - k0)]])
+        parts.append(rng.permutation(chunk))
+    a = np.concatenate(parts).astype(dtype)
+    hi = (1 << 24) - 1
+    same(ixp.check_inj(T(a, dev), 0, hi), oracle.check_inj(a, 0, hi), "pool-overflow-ok")
+    same(ixp.check_inj(T(a, dev)), oracle.check_inj(a), "pool-overflow-ok-derived")
+    pos0 = np.flatnonzero(a < (1 << 15))  # bucket-0 positions, in index order
+    for p, q in [(pos0[0], pos0[-1]), (pos0[-2], pos0[-1]), (pos0[5], pos0[ntile * k0 // 2]), (0, n - 1)]:
+        b = a.copy()
+        b[q] = b[p]
+        same(ixp.check_inj(T(b, dev), 0, hi), oracle.check_inj(b, 0, hi), ("pool-overflow-dup", p, q))
+        same(ixp.check_bij(T(b, dev), 0, hi, 0, hi), oracle.check_bij(b, 0, hi, 0, hi), ("pool-overflow-bij", p, q))
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.int64])
 def test_inj_bij_bucketed_unaligned_sorted_and_witnesses(ixp, dev, dtype):
     # bucketed path on an unaligned view (scalar loads), on sorted values (each tile
     # lands in one or two buckets, so runs are thousands long), and repeats whose
