@@ -245,6 +245,10 @@ constexpr int BK_NB = 0, BK_CAP = 1, BK_LW = 2, BK_MODE = 3;
 constexpr unsigned long long BK_STAGED = 1, BK_WIDE = 2, BK_HASH = 3;
 // header slots of the hash-set path: the pair of the value -1, the smallest pair
 constexpr int HS_NEG1 = 4, HS_PAIR = 5;
+// header slots of the partitioned hash-set path: why it gave up (the single-table
+// path then decides), repeated values listed, elements whose hash is all ones
+constexpr int HP_FLAGS = 6, HP_NDUP = 7, HP_TOPH = 8;
+constexpr unsigned long long HP_F_POOL = 1, HP_F_DUPS = 2;
 
 // Min/max of the in-codomain values (needed when Rcd is unbounded). The bounds
 // come clamped to T, so every compare is in T; a vector that lies wholly inside
@@ -607,13 +611,18 @@ __device__ __forceinline__ void hash_keep(unsigned *first, unsigned *second, uns
     if (o) atomicMax(second, min(o, enc));  // o = 0: no earlier copy, min(o, enc) = 0 changes nothing
 }
 
+// gate = 1: only as the fallback of the partitioned path (which set HP_FLAGS).
+__device__ __forceinline__ bool hash_single_runs(const Hdr *h, int gate) {
+    return !h->status && h->spare[BK_MODE] == BK_HASH && (!gate || h->spare[HP_FLAGS]);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(STREAM_THREADS, 4) hash_insert_kernel(const T *__restrict__ x, int64_t n,
                                                                         int64_t rlo, int64_t rhi, Hdr *h,
                                                                         HashSlot *__restrict__ tab,
-                                                                        unsigned long long mask) {
+                                                                        unsigned long long mask, int gate) {
     IXP_KERNEL_ENTRY();
-    if (h->status || h->spare[BK_MODE] != BK_HASH) return;
+    if (!hash_single_runs(h, gate)) return;
     unsigned *nfirst = reinterpret_cast<unsigned *>(&h->spare[HS_NEG1]);  // the pair of v = -1
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -638,11 +647,17 @@ __global__ void __launch_bounds__(STREAM_THREADS, 4) hash_insert_kernel(const T 
     }
 }
 
-// The hash set starts empty: zeroed only when the setup kernel chose the hash path.
-__global__ void __launch_bounds__(STREAM_THREADS) hash_clear_kernel(const Hdr *h, HashSlot *__restrict__ tab,
-                                                                    unsigned long long slots) {
+// The hash set starts empty: zeroed only when the setup kernel chose the hash path
+// (as a fallback, after the partitioned path's repeat, witness and partner).
+__global__ void __launch_bounds__(STREAM_THREADS) hash_clear_kernel(Hdr *h, HashSlot *__restrict__ tab,
+                                                                    unsigned long long slots, int gate) {
     IXP_KERNEL_ENTRY();
-    if (h->status || h->spare[BK_MODE] != BK_HASH) return;
+    if (!hash_single_runs(h, gate)) return;
+    if (gate && blockIdx.x == 0 && threadIdx.x == 0) {
+        h->flag = 0u;
+        h->k_first = 0ull;
+        h->k_aux = 0ull;
+    }
     ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tab);
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < slots;
          k += (unsigned long long)gridDim.x * blockDim.x)
@@ -652,9 +667,9 @@ __global__ void __launch_bounds__(STREAM_THREADS) hash_clear_kernel(const Hdr *h
 // The smallest (first, second) pair over the slots with a second position, packed
 // as first << 32 | second and kept with one atomic maximum of its encoding.
 __global__ void __launch_bounds__(STREAM_THREADS) hash_witness_kernel(Hdr *h, const HashSlot *__restrict__ tab,
-                                                                      unsigned long long slots) {
+                                                                      unsigned long long slots, int gate) {
     IXP_KERNEL_ENTRY();
-    if (h->status || h->spare[BK_MODE] != BK_HASH) return;
+    if (!hash_single_runs(h, gate)) return;
     unsigned long long best = ~0ull;
     auto take = [&](unsigned f, unsigned sc) {
         if (!sc) return;
@@ -676,13 +691,317 @@ __global__ void __launch_bounds__(STREAM_THREADS) hash_witness_kernel(Hdr *h, co
 }
 
 // Hash mode's verdict fields: index = first, aux0 = second (the first repeat).
-__global__ void hash_result_kernel(Hdr *h) {
+__global__ void hash_result_kernel(Hdr *h, int gate) {
     IXP_KERNEL_ENTRY();
-    if (h->status || h->spare[BK_MODE] != BK_HASH || !h->spare[HS_PAIR]) return;
+    if (!hash_single_runs(h, gate) || !h->spare[HS_PAIR]) return;
     const unsigned long long pk = ~h->spare[HS_PAIR];
     h->flag = 1u;
     h->k_first = enc_first((int64_t)(pk >> 32));
     h->k_aux = enc_first((int64_t)(pk & 0xffffffffull));
+}
+
+// ---------------------------------------------- Inj, any value span: partitioned
+// For n above HP_MIN_N the hash set is split into P parts (P a power of two, about
+// 2^21 elements a part), so that the table one part needs fits in L2 and its
+// atomics are served there instead of in HBM. hv = mix64(v) is a bijection of the
+// 64-bit values, so v repeats exactly when hv does. Pass A groups the in-Rcd
+// elements' hv by the top log2 P bits into per-part pools (tiles of HP_TILE
+// elements, each entry stored at its part's slot row at the rank its counting
+// atomic returns, rows moved to the pools as 16-byte chunks; an entry past its row
+// reserves its own pool pair). Pass B, one launch per part, inserts the part's keys
+// (hv + 1, so that 0 marks an empty slot and a pad) into an open-addressing table
+// of 2^k >= 1.5 x the part's pool capacity, probing from the low bits of hv. All
+// parts share one table, zeroed once per call, so that it stays in L2: a slot that
+// holds a key of another part (its top bits name that part) is free for this one.
+// A key found in the table is a repeat: its hv goes once (a bit per slot, in one of
+// two bitmaps that alternate by part) into a list of repeated values. The witness pass scans x for the first element whose hv is in
+// that list (a set in shared memory), and the partner pass of the bitmap paths
+// finds the smallest later copy. The one value whose hv is all ones is counted in
+// the header. A part whose pool fills up (repeats, or values crafted to share a
+// part) or more than HP_DUPCAP repeated values set HP_FLAGS, and the single-table
+// path above then decides the call from scratch.
+constexpr int64_t HP_MIN_N = (int64_t)1 << 21;
+constexpr int HP_THREADS = 256, HP_PER = 16, HP_TILE = HP_THREADS * HP_PER;
+constexpr unsigned HP_DUPCAP = 2048, HP_SET = 4096;  // listed repeats; slots of the witness pass's set
+
+struct HpCfg {
+    unsigned logp;               // log2 of the part count P
+    unsigned rcap;               // slot-row capacity per part per tile (even)
+    unsigned rstride;            // row stride in entries (twice an odd number: 16-byte rows)
+    unsigned long long capp;     // pool entries per part (even)
+    unsigned long long tslots;   // table slots (a power of two)
+    unsigned *cursors;           // P pool cursors
+    unsigned long long *pool;    // P x capp keys
+    unsigned long long *tab;     // tslots keys
+    unsigned *rep[2];            // tslots bits each: the slot's key is listed as a repeat
+    unsigned long long *dups;    // HP_DUPCAP repeated hv
+};
+
+// Shared memory of pass A: per part a count and a pool reservation, then the rows.
+__host__ __device__ inline size_t hp_smem_bytes(const HpCfg &c) {
+    return 2 * (size_t)(((1u << c.logp) * 4u + 15u) & ~15u) + (size_t)(1u << c.logp) * c.rstride * 8u;
+}
+
+// Zeroes the pool cursors, the table, the first repeat bitmap and the header slots.
+__global__ void __launch_bounds__(STREAM_THREADS) hp_setup_kernel(Hdr *h, HpCfg c) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != BK_HASH) return;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    if (tid == 0) {
+        h->spare[HP_FLAGS] = 0ull;
+        h->spare[HP_NDUP] = 0ull;
+        h->spare[HP_TOPH] = 0ull;
+    }
+    for (unsigned long long k = tid; k < (1ull << c.logp); k += stride) c.cursors[k] = 0u;
+    ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(c.tab);
+    for (unsigned long long k = tid; k < c.tslots / 2; k += stride) __stcg(t2 + k, make_ulonglong2(0ull, 0ull));
+    for (unsigned long long k = tid; k < c.tslots / 32; k += stride) c.rep[0][k] = 0u;
+}
+
+// Pass A: per-part pools of hv + 1. Thread t of a tile holds the 16-byte vectors t,
+// t + HP_THREADS, ... of the tile (16 elements).
+template <typename T>
+__global__ void __launch_bounds__(HP_THREADS) hp_part_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
+                                                             int64_t rhi, Hdr *h, HpCfg c, int vec_ok) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != BK_HASH) return;
+    constexpr int V = Vec<T>::N;
+    constexpr int NV = HP_PER / V;
+    extern __shared__ __align__(16) unsigned char hp_raw[];
+    const unsigned P = 1u << c.logp;
+    const unsigned pb = (P * 4u + 15u) & ~15u;
+    unsigned *s_cnt = reinterpret_cast<unsigned *>(hp_raw);
+    unsigned *s_res = reinterpret_cast<unsigned *>(hp_raw + pb);  // pool slot of each part's run
+    unsigned long long *s_row = reinterpret_cast<unsigned long long *>(hp_raw + 2 * pb);
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned sh = 64u - c.logp;
+    for (unsigned p = tid; p < P; p += HP_THREADS) s_cnt[p] = 0u;
+    __syncthreads();
+    const int64_t ntiles = (n + HP_TILE - 1) / HP_TILE;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t t0 = tile * HP_TILE;
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+            const int64_t p0 = t0 + (int64_t)(j * HP_THREADS + tid) * V;
+            T e[V];
+            if (vec_ok && p0 + V <= n) {
+                if (V == 4) {
+                    const int4 v = __ldcs(reinterpret_cast<const int4 *>(x + p0));
+                    e[0] = (T)v.x;
+                    e[1 % V] = (T)v.y;
+                    e[2 % V] = (T)v.z;
+                    e[3 % V] = (T)v.w;
+                } else {
+                    const longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(x + p0));
+                    e[0] = (T)v.x;
+                    e[1 % V] = (T)v.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < V; q++) e[q] = p0 + q < n ? x[p0 + q] : (T)0;
+            }
+#pragma unroll
+            for (int q = 0; q < V; q++) {
+                const int64_t v = (int64_t)e[q];
+                if (p0 + q >= n || v < rlo || v > rhi) continue;
+                const unsigned long long hv = mix64((unsigned long long)v);
+                if (hv == ~0ull) {
+                    atomicAdd(&h->spare[HP_TOPH], 1ull);
+                    continue;
+                }
+                const unsigned part = (unsigned)(hv >> sh);
+                const unsigned rk = atomicAdd(&s_cnt[part], 1u);
+                if (rk < c.rcap) {
+                    s_row[(size_t)part * c.rstride + rk] = hv + 1ull;
+                } else {
+                    // past the row: a pool pair of its own (key, pad), keeping runs 16-byte aligned
+                    const unsigned g = atomicAdd(&c.cursors[part], 2u);
+                    if ((unsigned long long)g + 2ull <= c.capp) {
+                        c.pool[part * c.capp + g] = hv + 1ull;
+                        c.pool[part * c.capp + g + 1] = 0ull;
+                    } else {
+                        atomicOr(&h->spare[HP_FLAGS], HP_F_POOL);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // one pool reservation per part, all at once (thread p for part p), rounded up
+        // to whole 16-byte chunks (pad key 0)
+        for (unsigned p = tid; p < P; p += HP_THREADS) {
+            const unsigned cr = (min(s_cnt[p], c.rcap) + 1u) & ~1u;
+            const unsigned g = cr ? atomicAdd(&c.cursors[p], cr) : 0u;
+            s_res[p] = g;
+            if ((unsigned long long)g + cr > c.capp) atomicOr(&h->spare[HP_FLAGS], HP_F_POOL);
+        }
+        __syncthreads();
+        // rows to the pools: warp w moves parts w, w + 8, ...
+        for (unsigned p = wid; p < P; p += HP_THREADS / 32) {
+            const unsigned cnt = min(s_cnt[p], c.rcap);
+            const unsigned cr = (cnt + 1u) & ~1u;
+            const unsigned g = s_res[p];
+            if ((unsigned long long)g + cr > c.capp) continue;
+            const unsigned long long *row = s_row + (size_t)p * c.rstride;
+            unsigned long long *dst = c.pool + p * c.capp + g;
+            for (unsigned k = 2 * lane; k < cr; k += 64) {
+                const ulonglong2 d = *reinterpret_cast<const ulonglong2 *>(row + k);
+                __stcs(reinterpret_cast<ulonglong2 *>(dst + k), make_ulonglong2(d.x, k + 1 < cnt ? d.y : 0ull));
+            }
+        }
+        __syncthreads();  // rows and counts read
+        for (unsigned p = tid; p < P; p += HP_THREADS) s_cnt[p] = 0u;
+        __syncthreads();
+    }
+}
+
+// Pass B for part p: insert its keys into the table, list the repeats (repeat
+// bitmap p & 1), and clear the other repeat bitmap (the one part p + 1 uses).
+__global__ void __launch_bounds__(STREAM_THREADS) hp_insert_kernel(Hdr *h, HpCfg c, unsigned p) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != BK_HASH || h->spare[HP_FLAGS]) return;
+    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long *tab = c.tab;
+    unsigned *rep = (p & 1) ? c.rep[1] : c.rep[0];  // (no dynamic index into the parameter)
+    const unsigned long long mask = c.tslots - 1ull;
+    const unsigned sh = 64u - c.logp;
+    auto list = [&](unsigned long long hv) {
+        const unsigned long long k = atomicAdd(&h->spare[HP_NDUP], 1ull);
+        if (k < HP_DUPCAP) c.dups[k] = hv;
+        else atomicOr(&h->spare[HP_FLAGS], HP_F_DUPS);
+        atomicOr(&h->flag, 1u);
+    };
+    if (p == 0 && tid == 0 && h->spare[HP_TOPH] >= 2ull) list(~0ull);
+    if (p + 1 < (1u << c.logp)) {
+        unsigned *r2 = (p & 1) ? c.rep[0] : c.rep[1];
+        for (unsigned long long k = tid; k < c.tslots / 32; k += stride) r2[k] = 0u;
+    }
+    const unsigned long long cnt = min((unsigned long long)c.cursors[p], c.capp);
+    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(c.pool + p * c.capp);
+    for (unsigned long long q = tid; q < cnt / 2; q += stride) {
+        const ulonglong2 d = __ldcs(src + q);
+        const unsigned long long kk[2] = {d.x, d.y};
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const unsigned long long key = kk[j];
+            if (!key) continue;  // pad
+            unsigned long long s = (key - 1ull) & mask;
+            // the slot is read first, and the compare-and-swap expects what was read
+            // (after the first part most free slots hold another part's key). A slot
+            // goes from free (0 or another part's key) to this part's key once, so a
+            // slot takes at most two compare-and-swaps; the table always has free
+            // slots (this part's keys are fewer than its slots): ends
+            unsigned long long expect = ld_relaxed_u64(&tab[s]);
+            for (unsigned long long step = 0; step <= 3ull * mask; step++) {
+                if (expect == key) {  // a repeat, seen by the read
+                    const unsigned bit = 1u << (s & 31);
+                    if (!(atomicOr(&rep[s >> 5], bit) & bit)) list(key - 1ull);
+                    break;
+                }
+                if (expect != 0ull && ((expect - 1ull) >> sh) == p) {  // another key of this part
+                    s = (s + 1ull) & mask;
+                    expect = ld_relaxed_u64(&tab[s]);
+                    continue;
+                }
+                const unsigned long long old = atomicCAS(&tab[s], expect, key);
+                if (old == expect) break;  // claimed
+                if (old == key) {          // a repeat
+                    const unsigned bit = 1u << (s & 31);
+                    if (!(atomicOr(&rep[s >> 5], bit) & bit)) list(key - 1ull);
+                    break;
+                }
+                if (old != 0ull && ((old - 1ull) >> sh) == p) {  // another key of this part
+                    s = (s + 1ull) & mask;
+                    expect = ld_relaxed_u64(&tab[s]);
+                } else {
+                    expect = old;  // free: claim it as it is now
+                }
+            }
+        }
+    }
+}
+
+// Witness of the partitioned path: the smallest i whose hv is a listed repeat (the
+// first occurrence of the value whose first occurrence comes first), in index
+// order with the same early stop as first_dup_kernel.
+template <typename T>
+__global__ void __launch_bounds__(STREAM_THREADS, 4) hp_first_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
+                                                                     int64_t rhi, Hdr *h, HpCfg c) {
+    IXP_KERNEL_ENTRY();
+    if (h->status || h->spare[BK_MODE] != BK_HASH || h->spare[HP_FLAGS] || !h->flag) return;
+    __shared__ unsigned long long s_set[HP_SET];  // hv + 1 of the listed repeats, 0 = empty
+    __shared__ int s_top;                         // hv = all ones is a listed repeat
+    for (int k = threadIdx.x; k < (int)HP_SET; k += blockDim.x) s_set[k] = 0ull;
+    if (threadIdx.x == 0) s_top = 0;
+    __syncthreads();
+    const unsigned nd = (unsigned)min(h->spare[HP_NDUP], (unsigned long long)HP_DUPCAP);
+    for (unsigned k = threadIdx.x; k < nd; k += blockDim.x) {
+        const unsigned long long hv = c.dups[k];
+        if (hv == ~0ull) {
+            s_top = 1;
+            continue;
+        }
+        unsigned s = (unsigned)hv & (HP_SET - 1u);
+        for (unsigned probe = 0; probe < HP_SET; probe++) {  // at most HP_DUPCAP keys in HP_SET slots: ends
+            const unsigned long long old = atomicCAS(&s_set[s], 0ull, hv + 1ull);
+            if (old == 0ull || old == hv + 1ull) break;
+            s = (s + 1u) & (HP_SET - 1u);
+        }
+    }
+    __syncthreads();
+    auto listed = [&](int64_t v) -> bool {
+        if (v < rlo || v > rhi) return false;
+        const unsigned long long hv = mix64((unsigned long long)v);
+        if (hv == ~0ull) return s_top != 0;
+        unsigned s = (unsigned)hv & (HP_SET - 1u);
+        for (unsigned probe = 0; probe < HP_SET; probe++) {
+            const unsigned long long k = s_set[s];
+            if (k == hv + 1ull) return true;
+            if (k == 0ull) return false;
+            s = (s + 1u) & (HP_SET - 1u);
+        }
+        return false;
+    };
+    using VT = typename Vec<T>::type;
+    constexpr int V = Vec<T>::N;
+    Split<T> sp(x, n);
+    unsigned long long *slot = &h->k_first;
+    int64_t best = INT64_MAX;
+    if (blockIdx.x == 0) {
+        for (int64_t i = threadIdx.x; i < sp.head; i += blockDim.x)
+            if (listed((int64_t)x[i])) best = min(best, i);
+        for (int64_t i = sp.tail0 + threadIdx.x; i < n; i += blockDim.x)
+            if (listed((int64_t)x[i])) best = min(best, i);
+        if (best != INT64_MAX) atomic_max_u64(slot, enc_first(best));
+        best = INT64_MAX;
+    }
+    const VT *xv = reinterpret_cast<const VT *>(x + sp.head);
+    const int64_t ntiles = (sp.nvec + WT_VECS - 1) / WT_VECS;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const unsigned long long cur = ld_relaxed_u64(slot);
+        if (cur && sp.head + t * WT_VECS * V > dec_first(cur)) break;
+        VT a[WT_PER];
+#pragma unroll
+        for (int u = 0; u < WT_PER; u++) {
+            const int64_t v = t * WT_VECS + u * STREAM_THREADS + threadIdx.x;
+            if (v < sp.nvec) a[u] = ldv(xv + v);
+        }
+#pragma unroll
+        for (int u = 0; u < WT_PER; u++) {
+            const int64_t v = t * WT_VECS + u * STREAM_THREADS + threadIdx.x;
+            if (v >= sp.nvec) continue;
+            int64_t e[V];
+            unpack(a[u], e);
+#pragma unroll
+            for (int k = 0; k < V; k++)
+                if (listed((int64_t)(T)e[k])) best = min(best, sp.head + v * V + k);
+        }
+        if (best != INT64_MAX) {
+            atomic_max_u64(slot, enc_first(best));
+            best = INT64_MAX;
+        }
+    }
 }
 
 // Bij "missing" value: when nothing is out of image and nothing repeats but fewer
@@ -1571,6 +1890,47 @@ size_t inj_any_span_ws_bytes(int64_t n) {
            256;
 }
 
+// Layout of the partitioned hash-set path inside the hash-set region (2^k >= 2n
+// slots of 16 bytes): pool cursors | repeat list | two repeat bitmaps | table |
+// pools. P = 2^logp >= n / 2^21 (4 to 256 parts); rows of HP_TILE / P + 6
+// sqrt(HP_TILE / P) + 8 entries; a pool of 1.25 n / P + 64 entries a part and tables
+// of 2^k >= 1.5 x that. False (the single table decides) for n <= HP_MIN_N, whose
+// table already fits in L2, or when the layout does not fit the region.
+static bool hp_layout(const BitmapWs &w, int64_t n, HpCfg *c) {
+    if (!w.tab || n <= HP_MIN_N) return false;
+    unsigned logp = 2;
+    while (logp < 8 && (unsigned long long)n > (1ull << (21 + logp))) logp++;
+    const unsigned P = 1u << logp;
+    const unsigned m = (unsigned)HP_TILE / P;
+    unsigned sq = 1;
+    while (sq * sq < m) sq++;
+    const unsigned rcap = (m + 6 * sq + 8 + 1) & ~1u;
+    const unsigned rstride = ((rcap / 2) & 1u) ? rcap : rcap + 2;
+    const unsigned long long capp = ((5ull * (unsigned long long)n / 4ull) / P + 64ull + 1ull) & ~1ull;
+    unsigned long long ts = 64;
+    while (ts < capp + capp / 2) ts <<= 1;
+    size_t off = 0;
+    char *base = (char *)w.tab;
+    c->logp = logp;
+    c->rcap = rcap;
+    c->rstride = rstride;
+    c->capp = capp;
+    c->tslots = ts;
+    c->cursors = (unsigned *)(base + off);
+    off += round256((size_t)P * 4);
+    c->dups = (unsigned long long *)(base + off);
+    off += round256((size_t)HP_DUPCAP * 8);
+    for (int k = 0; k < 2; k++) {
+        c->rep[k] = (unsigned *)(base + off);
+        off += round256((size_t)(ts / 8));
+    }
+    c->tab = (unsigned long long *)(base + off);
+    off += round256((size_t)ts * 8);
+    c->pool = (unsigned long long *)(base + off);
+    off += round256((size_t)P * capp * 8);
+    return off <= (size_t)w.slots * sizeof(HashSlot) && hp_smem_bytes(*c) <= 200 * 1024;
+}
+
 // Bucket width: about two buckets per SM, between 2^14 and 2^19 values (a 64 KB
 // shared bitmap), widened to 2^20 if the bucket count would exceed BK_MAX.
 static bool bucket_config(unsigned long long span, unsigned long long pool, BucketCfg *cfg) {
@@ -1702,10 +2062,24 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
         partner_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, h, &h->k_first);
     }
     if (w.tab && n > 0) {  // spans wider than the bitmaps: the hash set decides (the kernels exit otherwise)
-        hash_clear_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, w.tab, w.slots);
-        hash_insert_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, w.tab, w.slots - 1);
-        hash_witness_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, w.tab, w.slots);
-        hash_result_kernel<<<1, 1, 0, st>>>(h);
+        HpCfg hc{};
+        const int gate = hp_layout(w, n, &hc) ? 1 : 0;
+        if (gate) {  // partitioned; the single table below runs only if it gives up
+            const size_t smem = hp_smem_bytes(hc);
+            const int64_t ptiles = (n + HP_TILE - 1) / HP_TILE;
+            hp_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, hc);
+            cudaFuncSetAttribute(hp_part_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            hp_part_kernel<T><<<(int)std::min<int64_t>(ptiles, (int64_t)num_sms() * 4), HP_THREADS, smem, st>>>(
+                x, n, rlo, rhi, h, hc, (reinterpret_cast<uintptr_t>(x) & 15u) == 0);
+            for (unsigned p = 0; p < (1u << hc.logp); p++)
+                hp_insert_kernel<<<num_sms() * 8, STREAM_THREADS, 0, st>>>(h, hc, p);
+            hp_first_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, hc);
+            partner_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, h, &h->k_first);
+        }
+        hash_clear_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, w.tab, w.slots, gate);
+        hash_insert_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, w.tab, w.slots - 1, gate);
+        hash_witness_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, w.tab, w.slots, gate);
+        hash_result_kernel<<<1, 1, 0, st>>>(h, gate);
     }
     inj_finalize<T><<<1, 1, 0, st>>>(x, h, out);
 }

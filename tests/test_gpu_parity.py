@@ -202,6 +202,60 @@ def test_inj_any_span_hash_set(ixp, dev, n):
     same(ixp.check_inj(T(e, dev)), oracle.check_inj(e), ("full-range-dup", n))
 
 
+def _mix64(z):
+    m = (1 << 64) - 1
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & m
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & m
+    return z ^ (z >> 31)
+
+
+def _unmix64(h):
+    """The value whose SplitMix64 finalizer is h (each step of the finalizer is a
+    bijection of the 64-bit words)."""
+    m = (1 << 64) - 1
+
+    def unxs(y, s):
+        x = y
+        for _ in range(64 // s + 1):
+            x = y ^ (x >> s)
+        return x
+
+    z = unxs(h, 31)
+    z = (z * pow(0x94D049BB133111EB, -1, 1 << 64)) & m
+    z = unxs(z, 27)
+    z = (z * pow(0xBF58476D1CE4E5B9, -1, 1 << 64)) & m
+    return unxs(z, 30)
+
+
+def test_inj_any_span_partitioned_paths(ixp, dev):
+    """Above 2^21 elements the any-span Inj splits the hash set into parts by the top
+    bits of the values' hash; these cases take each of its exits: a part whose pool
+    fills up (one value repeated 1.2 M times) and more repeated values than its list
+    holds (3000 pairs) both hand the call to the single table; 1500 pairs, and the
+    one value whose hash is all ones (counted apart), are decided by the parts."""
+    n = 3_000_001
+    x = spread_ids(n, 41)
+    rng = np.random.default_rng(41)
+    a = x.copy()
+    a[rng.choice(n, size=1_200_000, replace=False)] = x[12345]
+    same(ixp.check_inj(T(a, dev)), oracle.check_inj(a), "pool-full")
+    for pairs, what in [(3000, "many-repeats"), (1500, "listed-repeats")]:
+        b = x.copy()
+        pos = rng.choice(n, size=2 * pairs, replace=False)
+        b[pos[pairs:]] = b[pos[:pairs]]
+        same(ixp.check_inj(T(b, dev)), oracle.check_inj(b), what)
+    top = _unmix64((1 << 64) - 1)
+    assert _mix64(top) == (1 << 64) - 1
+    top = np.int64(top - (1 << 64) if top >= 1 << 63 else top)
+    c = x.copy()
+    c[777] = top
+    same(ixp.check_inj(T(c, dev)), oracle.check_inj(c), "top-hash-once")
+    c[2_500_000] = top
+    same(ixp.check_inj(T(c, dev)), oracle.check_inj(c), "top-hash-twice")
+    c[100] = c[2_900_000]  # an earlier repeat of another value wins
+    same(ixp.check_inj(T(c, dev)), oracle.check_inj(c), "top-hash-and-another")
+
+
 @pytest.mark.parametrize("dtype", [np.int32, np.int64])
 @pytest.mark.parametrize("n", [1, 2, 33, 4097, 65536, 100003])
 def test_bij(ixp, dev, n, dtype):
