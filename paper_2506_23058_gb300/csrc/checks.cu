@@ -15,6 +15,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include <type_traits>
 
 namespace ixp {
 
@@ -701,48 +702,54 @@ __global__ void hash_result_kernel(Hdr *h, int gate) {
 }
 
 // ---------------------------------------------- Inj, any value span: partitioned
-// For n above HP_MIN_N the hash set is split into P parts (P a power of two, about
-// 2^21 elements a part), so that the table one part needs fits in L2 and its
-// atomics are served there instead of in HBM. hv = mix64(v) is a bijection of the
-// 64-bit values, so v repeats exactly when hv does. Pass A groups the in-Rcd
-// elements' hv by the top log2 P bits into per-part pools (tiles of HP_TILE
-// elements, each entry stored at its part's slot row at the rank its counting
-// atomic returns, rows moved to the pools as 16-byte chunks; an entry past its row
-// reserves its own pool pair). Pass B, one launch per part, inserts the part's keys
-// (hv + 1, so that 0 marks an empty slot and a pad) into an open-addressing table
-// of 2^k >= 1.5 x the part's pool capacity, probing from the low bits of hv. All
-// parts share one table, zeroed once per call, so that it stays in L2: a slot that
-// holds a key of another part (its top bits name that part) is free for this one.
-// A key found in the table is a repeat: its hv goes once (a bit per slot, in one of
-// two bitmaps that alternate by part) into a list of repeated values. The witness pass scans x for the first element whose hv is in
-// that list (a set in shared memory), and the partner pass of the bitmap paths
-// finds the smallest later copy. The one value whose hv is all ones is counted in
-// the header. A part whose pool fills up (repeats, or values crafted to share a
-// part) or more than HP_DUPCAP repeated values set HP_FLAGS, and the single-table
-// path above then decides the call from scratch.
-constexpr int64_t HP_MIN_N = (int64_t)1 << 21;
+// For 2^21 < n <= 2^29 the hash set is split until each piece fits one SM's shared
+// memory. hv = mix64(v) is a bijection of the 64-bit values, so v repeats exactly
+// when hv does, and the keys hv + 1 (0 marks an empty slot and a pad) are grouped
+// twice by the top bits of hv: into P parts (P a power of two, about 2^21 keys a
+// part) and each part into HP_Q sub-parts (about 2^13 keys). Each grouping pass
+// (hp_group_kernel) takes tiles of HP_TILE entries, stores each entry at its
+// group's slot row at the rank its counting atomic returns (an entry past its row
+// reserves a pool pair of its own), then reserves one pool run per group with one
+// atomicAdd each and moves the rows there as 16-byte chunks. hp_set_kernel then
+// gives each sub-part one block with an open-addressing set of 2^k >= 1.5 x its pool
+// capacity in shared memory, probing from the low bits of hv; a key found in the set
+// is a repeat, and its hv goes once into a list of repeated values. The witness
+// pass scans x for the first element whose hv is listed (a set in shared memory),
+// and the partner pass of the bitmap paths finds the smallest later copy. The one
+// value whose hv is all ones is counted in the header. A group whose pool fills up
+// (one value repeated very often, or values crafted to share a group) or more than
+// HP_DUPCAP repeated values set HP_FLAGS, and the single-table path above then
+// decides the call from scratch.
+constexpr int64_t HP_MIN_N = (int64_t)1 << 21, HP_MAX_N = (int64_t)1 << 29;
 constexpr int HP_THREADS = 256, HP_PER = 16, HP_TILE = HP_THREADS * HP_PER;
-constexpr unsigned HP_DUPCAP = 2048, HP_SET = 4096;  // listed repeats; slots of the witness pass's set
+constexpr unsigned HP_LOGQ = 8, HP_Q = 1u << HP_LOGQ;  // sub-parts per part
+constexpr unsigned HP_DUPCAP = 2048, HP_SET = 4096;      // listed repeats; slots of the witness pass's set
+constexpr int HP_SET_THREADS = 1024;  // threads of a sub-part's block (one block a SM: its set is up to 128 KB)
 
-struct HpCfg {
-    unsigned logp;               // log2 of the part count P
-    unsigned rcap;               // slot-row capacity per part per tile (even)
-    unsigned rstride;            // row stride in entries (twice an odd number: 16-byte rows)
-    unsigned long long capp;     // pool entries per part (even)
-    unsigned long long tslots;   // table slots (a power of two)
-    unsigned *cursors;           // P pool cursors
-    unsigned long long *pool;    // P x capp keys
-    unsigned long long *tab;     // tslots keys
-    unsigned *rep[2];            // tslots bits each: the slot's key is listed as a repeat
-    unsigned long long *dups;    // HP_DUPCAP repeated hv
+// One grouping pass's shape: groups per tile, slot rows, pools.
+struct HpLevel {
+    unsigned logg;            // log2 of the groups an entry can go to (P, or HP_Q within its part)
+    unsigned rcap;            // slot-row capacity per group per tile (even)
+    unsigned rstride;         // row stride in entries (twice an odd number: 16-byte rows)
+    unsigned long long cap;   // pool entries per group (even)
+    unsigned *cursors;        // per group
+    unsigned long long *pool; // groups x cap keys
 };
 
-// Shared memory of pass A: per part a count and a pool reservation, then the rows.
-__host__ __device__ inline size_t hp_smem_bytes(const HpCfg &c) {
-    return 2 * (size_t)(((1u << c.logp) * 4u + 15u) & ~15u) + (size_t)(1u << c.logp) * c.rstride * 8u;
+struct HpCfg {
+    unsigned logp;             // log2 of the part count P
+    HpLevel l1, l2;            // P parts; P x HP_Q sub-parts
+    unsigned tslots;           // slots of a sub-part's set (a power of two)
+    unsigned long long *dups;  // HP_DUPCAP repeated hv
+};
+
+// Shared memory of a grouping pass: per group a count and a pool reservation, then
+// the rows.
+__host__ __device__ inline size_t hp_group_smem(const HpLevel &l) {
+    return 2 * (size_t)(((1u << l.logg) * 4u + 15u) & ~15u) + (size_t)(1u << l.logg) * l.rstride * 8u;
 }
 
-// Zeroes the pool cursors, the table, the first repeat bitmap and the header slots.
+// Zeroes both levels' pool cursors and the header slots.
 __global__ void __launch_bounds__(STREAM_THREADS) hp_setup_kernel(Hdr *h, HpCfg c) {
     IXP_KERNEL_ENTRY();
     if (h->status || h->spare[BK_MODE] != BK_HASH) return;
@@ -753,73 +760,113 @@ __global__ void __launch_bounds__(STREAM_THREADS) hp_setup_kernel(Hdr *h, HpCfg 
         h->spare[HP_NDUP] = 0ull;
         h->spare[HP_TOPH] = 0ull;
     }
-    for (unsigned long long k = tid; k < (1ull << c.logp); k += stride) c.cursors[k] = 0u;
-    ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(c.tab);
-    for (unsigned long long k = tid; k < c.tslots / 2; k += stride) __stcg(t2 + k, make_ulonglong2(0ull, 0ull));
-    for (unsigned long long k = tid; k < c.tslots / 32; k += stride) c.rep[0][k] = 0u;
+    for (unsigned long long k = tid; k < (1ull << c.logp); k += stride) c.l1.cursors[k] = 0u;
+    for (unsigned long long k = tid; k < ((unsigned long long)HP_Q << c.logp); k += stride) c.l2.cursors[k] = 0u;
 }
 
-// Pass A: per-part pools of hv + 1. Thread t of a tile holds the 16-byte vectors t,
-// t + HP_THREADS, ... of the tile (16 elements).
-template <typename T>
-__global__ void __launch_bounds__(HP_THREADS) hp_part_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
-                                                             int64_t rhi, Hdr *h, HpCfg c, int vec_ok) {
+// A grouping pass. SRC = 0: the entries are the in-Rcd elements of x (T), keyed by
+// hv + 1 and grouped into parts by the top logp bits of hv. SRC = 1: the entries are
+// the keys of the P part pools (tiles of one part each; pads skipped), grouped into
+// the part's sub-parts by the next HP_LOGQ bits. Thread t of a tile holds the
+// 16-byte vectors t, t + HP_THREADS, ... of the tile (16 entries).
+template <typename T, int SRC>
+__global__ void __launch_bounds__(HP_THREADS) hp_group_kernel(const T *__restrict__ x, int64_t n, int64_t rlo,
+                                                              int64_t rhi, Hdr *h, HpCfg c, int vec_ok) {
     IXP_KERNEL_ENTRY();
     if (h->status || h->spare[BK_MODE] != BK_HASH) return;
-    constexpr int V = Vec<T>::N;
+    if (SRC == 1 && h->spare[HP_FLAGS]) return;
+    constexpr int V = SRC == 0 ? Vec<T>::N : 2;
     constexpr int NV = HP_PER / V;
+    const HpLevel &L = SRC == 0 ? c.l1 : c.l2;
     extern __shared__ __align__(16) unsigned char hp_raw[];
-    const unsigned P = 1u << c.logp;
-    const unsigned pb = (P * 4u + 15u) & ~15u;
+    const unsigned G = 1u << L.logg;
+    const unsigned gb = (G * 4u + 15u) & ~15u;
     unsigned *s_cnt = reinterpret_cast<unsigned *>(hp_raw);
-    unsigned *s_res = reinterpret_cast<unsigned *>(hp_raw + pb);  // pool slot of each part's run
-    unsigned long long *s_row = reinterpret_cast<unsigned long long *>(hp_raw + 2 * pb);
+    unsigned *s_res = reinterpret_cast<unsigned *>(hp_raw + gb);  // pool slot of each group's run
+    unsigned long long *s_row = reinterpret_cast<unsigned long long *>(hp_raw + 2 * gb);
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned sh = 64u - c.logp;
-    for (unsigned p = tid; p < P; p += HP_THREADS) s_cnt[p] = 0u;
+    const unsigned sh1 = 64u - c.logp, sh2 = 64u - c.logp - HP_LOGQ;
+    for (unsigned g = tid; g < G; g += HP_THREADS) s_cnt[g] = 0u;
     __syncthreads();
-    const int64_t ntiles = (n + HP_TILE - 1) / HP_TILE;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t t0 = tile * HP_TILE;
+    // SRC = 0: tiles of x; SRC = 1: tiles (part, j) over each part's pool region
+    const int64_t per_part = SRC == 0 ? 0 : (int64_t)((c.l1.cap + HP_TILE - 1) / HP_TILE);
+    const int64_t ntiles = SRC == 0 ? (n + HP_TILE - 1) / HP_TILE : per_part << c.logp;
+    auto geom = [&](int64_t tile, unsigned &part, int64_t &t0, int64_t &m) {
+        part = SRC == 0 ? 0u : (unsigned)(tile / per_part);
+        t0 = SRC == 0 ? tile * HP_TILE : (tile - (int64_t)part * per_part) * HP_TILE;
+        m = SRC == 0 ? n : (int64_t)min((unsigned long long)c.l1.cursors[part], c.l1.cap);  // part's entries
+    };
+    // a tile's 16-byte vectors, when the whole tile can be read so (pool tiles always:
+    // regions and runs are 16-byte aligned and m is even); the next tile's are loaded
+    // while this one is placed
+    using RV = typename std::conditional<SRC == 0, typename Vec<T>::type, ulonglong2>::type;
+    auto load_vecs = [&](int64_t tile, RV (&r)[NV]) -> bool {
+        unsigned part;
+        int64_t t0, m;
+        geom(tile, part, t0, m);
+        if (SRC == 0 && !(vec_ok && t0 + HP_TILE <= m)) return false;
+        const RV *src = SRC == 0 ? reinterpret_cast<const RV *>(x)
+                                 : reinterpret_cast<const RV *>(c.l1.pool + (unsigned long long)part * c.l1.cap);
 #pragma unroll
         for (int j = 0; j < NV; j++) {
             const int64_t p0 = t0 + (int64_t)(j * HP_THREADS + tid) * V;
-            T e[V];
-            if (vec_ok && p0 + V <= n) {
-                if (V == 4) {
-                    const int4 v = __ldcs(reinterpret_cast<const int4 *>(x + p0));
-                    e[0] = (T)v.x;
-                    e[1 % V] = (T)v.y;
-                    e[2 % V] = (T)v.z;
-                    e[3 % V] = (T)v.w;
+            if (p0 < m) r[j] = __ldcs(src + p0 / V);
+            else r[j] = RV{};
+        }
+        return true;
+    };
+    RV nxt[NV];
+    bool have = blockIdx.x < ntiles ? load_vecs(blockIdx.x, nxt) : false;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        unsigned part;
+        int64_t t0, m;
+        geom(tile, part, t0, m);
+        RV cur[NV];
+#pragma unroll
+        for (int j = 0; j < NV; j++) cur[j] = nxt[j];
+        const bool cur_vec = have;
+        have = tile + gridDim.x < ntiles ? load_vecs(tile + gridDim.x, nxt) : false;
+        if (SRC == 1 && t0 >= m) continue;  // an empty tile of the part's region (uniform over the block)
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+            const int64_t p0 = t0 + (int64_t)(j * HP_THREADS + tid) * V;
+            unsigned long long key[V];  // hv + 1 of the entry, 0 for none
+            if constexpr (SRC == 0) {
+                int64_t e[V];
+                if (cur_vec) {
+                    unpack(cur[j], e);
                 } else {
-                    const longlong2 v = __ldcs(reinterpret_cast<const longlong2 *>(x + p0));
-                    e[0] = (T)v.x;
-                    e[1 % V] = (T)v.y;
+#pragma unroll
+                    for (int q = 0; q < V; q++) e[q] = p0 + q < m ? (int64_t)x[p0 + q] : 0;
+                }
+#pragma unroll
+                for (int q = 0; q < V; q++) {
+                    const int64_t v = (int64_t)(T)e[q];
+                    key[q] = 0ull;
+                    if (p0 + q >= m || v < rlo || v > rhi) continue;
+                    const unsigned long long hv = mix64((unsigned long long)v);
+                    if (hv == ~0ull) atomicAdd(&h->spare[HP_TOPH], 1ull);
+                    else key[q] = hv + 1ull;
                 }
             } else {
-#pragma unroll
-                for (int q = 0; q < V; q++) e[q] = p0 + q < n ? x[p0 + q] : (T)0;
+                key[0] = cur[j].x;  // zero past the part's entries
+                key[1 % V] = cur[j].y;
             }
 #pragma unroll
             for (int q = 0; q < V; q++) {
-                const int64_t v = (int64_t)e[q];
-                if (p0 + q >= n || v < rlo || v > rhi) continue;
-                const unsigned long long hv = mix64((unsigned long long)v);
-                if (hv == ~0ull) {
-                    atomicAdd(&h->spare[HP_TOPH], 1ull);
-                    continue;
-                }
-                const unsigned part = (unsigned)(hv >> sh);
-                const unsigned rk = atomicAdd(&s_cnt[part], 1u);
-                if (rk < c.rcap) {
-                    s_row[(size_t)part * c.rstride + rk] = hv + 1ull;
+                if (!key[q]) continue;
+                const unsigned long long hv = key[q] - 1ull;
+                const unsigned g = SRC == 0 ? (unsigned)(hv >> sh1) : (unsigned)(hv >> sh2) & (HP_Q - 1u);
+                const unsigned rk = atomicAdd(&s_cnt[g], 1u);
+                if (rk < L.rcap) {
+                    s_row[(size_t)g * L.rstride + rk] = key[q];
                 } else {
                     // past the row: a pool pair of its own (key, pad), keeping runs 16-byte aligned
-                    const unsigned g = atomicAdd(&c.cursors[part], 2u);
-                    if ((unsigned long long)g + 2ull <= c.capp) {
-                        c.pool[part * c.capp + g] = hv + 1ull;
-                        c.pool[part * c.capp + g + 1] = 0ull;
+                    const unsigned long long gg = (unsigned long long)part * G + g;
+                    const unsigned at = atomicAdd(&L.cursors[gg], 2u);
+                    if ((unsigned long long)at + 2ull <= L.cap) {
+                        L.pool[gg * L.cap + at] = key[q];
+                        L.pool[gg * L.cap + at + 1] = 0ull;
                     } else {
                         atomicOr(&h->spare[HP_FLAGS], HP_F_POOL);
                     }
@@ -827,96 +874,75 @@ __global__ void __launch_bounds__(HP_THREADS) hp_part_kernel(const T *__restrict
             }
         }
         __syncthreads();
-        // one pool reservation per part, all at once (thread p for part p), rounded up
+        // one pool reservation per group, all at once (thread g for group g), rounded up
         // to whole 16-byte chunks (pad key 0)
-        for (unsigned p = tid; p < P; p += HP_THREADS) {
-            const unsigned cr = (min(s_cnt[p], c.rcap) + 1u) & ~1u;
-            const unsigned g = cr ? atomicAdd(&c.cursors[p], cr) : 0u;
-            s_res[p] = g;
-            if ((unsigned long long)g + cr > c.capp) atomicOr(&h->spare[HP_FLAGS], HP_F_POOL);
+        for (unsigned g = tid; g < G; g += HP_THREADS) {
+            const unsigned cr = (min(s_cnt[g], L.rcap) + 1u) & ~1u;
+            const unsigned at = cr ? atomicAdd(&L.cursors[(unsigned long long)part * G + g], cr) : 0u;
+            s_res[g] = at;
+            if ((unsigned long long)at + cr > L.cap) atomicOr(&h->spare[HP_FLAGS], HP_F_POOL);
         }
         __syncthreads();
-        // rows to the pools: warp w moves parts w, w + 8, ...
-        for (unsigned p = wid; p < P; p += HP_THREADS / 32) {
-            const unsigned cnt = min(s_cnt[p], c.rcap);
+        // rows to the pools: warp w moves groups w, w + 8, ...
+        for (unsigned g = wid; g < G; g += HP_THREADS / 32) {
+            const unsigned cnt = min(s_cnt[g], L.rcap);
             const unsigned cr = (cnt + 1u) & ~1u;
-            const unsigned g = s_res[p];
-            if ((unsigned long long)g + cr > c.capp) continue;
-            const unsigned long long *row = s_row + (size_t)p * c.rstride;
-            unsigned long long *dst = c.pool + p * c.capp + g;
+            const unsigned at = s_res[g];
+            if ((unsigned long long)at + cr > L.cap) continue;
+            const unsigned long long *row = s_row + (size_t)g * L.rstride;
+            unsigned long long *dst = L.pool + ((unsigned long long)part * G + g) * L.cap + at;
             for (unsigned k = 2 * lane; k < cr; k += 64) {
                 const ulonglong2 d = *reinterpret_cast<const ulonglong2 *>(row + k);
                 __stcs(reinterpret_cast<ulonglong2 *>(dst + k), make_ulonglong2(d.x, k + 1 < cnt ? d.y : 0ull));
             }
         }
         __syncthreads();  // rows and counts read
-        for (unsigned p = tid; p < P; p += HP_THREADS) s_cnt[p] = 0u;
+        for (unsigned g = tid; g < G; g += HP_THREADS) s_cnt[g] = 0u;
         __syncthreads();
     }
 }
 
-// Pass B for part p: insert its keys into the table, list the repeats (repeat
-// bitmap p & 1), and clear the other repeat bitmap (the one part p + 1 uses).
-__global__ void __launch_bounds__(STREAM_THREADS) hp_insert_kernel(Hdr *h, HpCfg c, unsigned p) {
+// One block per sub-part: its keys into a set of c.tslots slots in shared memory
+// (plus one bit per slot: the slot's key is listed as a repeat). Block 0 also
+// lists the all-ones hv when it occurred twice or more.
+__global__ void __launch_bounds__(HP_SET_THREADS) hp_set_kernel(Hdr *h, HpCfg c) {
     IXP_KERNEL_ENTRY();
     if (h->status || h->spare[BK_MODE] != BK_HASH || h->spare[HP_FLAGS]) return;
-    const unsigned long long tid = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    unsigned long long *tab = c.tab;
-    unsigned *rep = (p & 1) ? c.rep[1] : c.rep[0];  // (no dynamic index into the parameter)
-    const unsigned long long mask = c.tslots - 1ull;
-    const unsigned sh = 64u - c.logp;
+    extern __shared__ __align__(16) unsigned char hs_raw[];
+    unsigned long long *s_set = reinterpret_cast<unsigned long long *>(hs_raw);
+    unsigned *s_rep = reinterpret_cast<unsigned *>(s_set + c.tslots);
+    const unsigned mask = c.tslots - 1u;
     auto list = [&](unsigned long long hv) {
         const unsigned long long k = atomicAdd(&h->spare[HP_NDUP], 1ull);
         if (k < HP_DUPCAP) c.dups[k] = hv;
         else atomicOr(&h->spare[HP_FLAGS], HP_F_DUPS);
         atomicOr(&h->flag, 1u);
     };
-    if (p == 0 && tid == 0 && h->spare[HP_TOPH] >= 2ull) list(~0ull);
-    if (p + 1 < (1u << c.logp)) {
-        unsigned *r2 = (p & 1) ? c.rep[0] : c.rep[1];
-        for (unsigned long long k = tid; k < c.tslots / 32; k += stride) r2[k] = 0u;
-    }
-    const unsigned long long cnt = min((unsigned long long)c.cursors[p], c.capp);
-    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(c.pool + p * c.capp);
-    for (unsigned long long q = tid; q < cnt / 2; q += stride) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && h->spare[HP_TOPH] >= 2ull) list(~0ull);
+    const unsigned long long sp = blockIdx.x;
+    const unsigned npair = (unsigned)min((unsigned long long)c.l2.cursors[sp], c.l2.cap) / 2;
+    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(c.l2.pool + sp * c.l2.cap);
+    ulonglong2 *z = reinterpret_cast<ulonglong2 *>(s_set);
+    for (unsigned k = threadIdx.x; k < c.tslots / 2; k += blockDim.x) z[k] = make_ulonglong2(0ull, 0ull);
+    for (unsigned k = threadIdx.x; k < c.tslots / 32; k += blockDim.x) s_rep[k] = 0u;
+    __syncthreads();
+    for (unsigned q = threadIdx.x; q < npair; q += blockDim.x) {
         const ulonglong2 d = __ldcs(src + q);
         const unsigned long long kk[2] = {d.x, d.y};
 #pragma unroll
         for (int j = 0; j < 2; j++) {
             const unsigned long long key = kk[j];
             if (!key) continue;  // pad
-            unsigned long long s = (key - 1ull) & mask;
-            // the slot is read first, and the compare-and-swap expects what was read
-            // (after the first part most free slots hold another part's key). A slot
-            // goes from free (0 or another part's key) to this part's key once, so a
-            // slot takes at most two compare-and-swaps; the table always has free
-            // slots (this part's keys are fewer than its slots): ends
-            unsigned long long expect = ld_relaxed_u64(&tab[s]);
-            for (unsigned long long step = 0; step <= 3ull * mask; step++) {
-                if (expect == key) {  // a repeat, seen by the read
+            unsigned s = (unsigned)(key - 1ull) & mask;
+            for (unsigned probe = 0; probe <= mask; probe++) {  // fewer keys than slots: ends
+                const unsigned long long old = atomicCAS(&s_set[s], 0ull, key);
+                if (old == 0ull) break;
+                if (old == key) {  // a repeat
                     const unsigned bit = 1u << (s & 31);
-                    if (!(atomicOr(&rep[s >> 5], bit) & bit)) list(key - 1ull);
+                    if (!(atomicOr(&s_rep[s >> 5], bit) & bit)) list(key - 1ull);
                     break;
                 }
-                if (expect != 0ull && ((expect - 1ull) >> sh) == p) {  // another key of this part
-                    s = (s + 1ull) & mask;
-                    expect = ld_relaxed_u64(&tab[s]);
-                    continue;
-                }
-                const unsigned long long old = atomicCAS(&tab[s], expect, key);
-                if (old == expect) break;  // claimed
-                if (old == key) {          // a repeat
-                    const unsigned bit = 1u << (s & 31);
-                    if (!(atomicOr(&rep[s >> 5], bit) & bit)) list(key - 1ull);
-                    break;
-                }
-                if (old != 0ull && ((old - 1ull) >> sh) == p) {  // another key of this part
-                    s = (s + 1ull) & mask;
-                    expect = ld_relaxed_u64(&tab[s]);
-                } else {
-                    expect = old;  // free: claim it as it is now
-                }
+                s = (s + 1u) & mask;
             }
         }
     }
@@ -1891,44 +1917,46 @@ size_t inj_any_span_ws_bytes(int64_t n) {
 }
 
 // Layout of the partitioned hash-set path inside the hash-set region (2^k >= 2n
-// slots of 16 bytes): pool cursors | repeat list | two repeat bitmaps | table |
-// pools. P = 2^logp >= n / 2^21 (4 to 256 parts); rows of HP_TILE / P + 6
-// sqrt(HP_TILE / P) + 8 entries; a pool of 1.25 n / P + 64 entries a part and tables
-// of 2^k >= 1.5 x that. False (the single table decides) for n <= HP_MIN_N, whose
-// table already fits in L2, or when the layout does not fit the region.
+// slots of 16 bytes): part cursors | sub-part cursors | repeat list | part pools |
+// sub-part pools. P = 2^logp >= n / 2^21 (4 to 256 parts) and HP_Q sub-parts a
+// part; a grouping pass's rows hold (entries per group per tile) + 6 x its square
+// root + 8; a pool holds 1.25 x the mean keys of its group + 64; a sub-part's set
+// 2^k >= 1.5 x its pool. False (the single table decides) for n <= HP_MIN_N, whose
+// table already fits in L2, for n > HP_MAX_N, or when the layout does not fit.
 static bool hp_layout(const BitmapWs &w, int64_t n, HpCfg *c) {
-    if (!w.tab || n <= HP_MIN_N) return false;
+    if (!w.tab || n <= HP_MIN_N || n > HP_MAX_N) return false;
     unsigned logp = 2;
     while (logp < 8 && (unsigned long long)n > (1ull << (21 + logp))) logp++;
-    const unsigned P = 1u << logp;
-    const unsigned m = (unsigned)HP_TILE / P;
-    unsigned sq = 1;
-    while (sq * sq < m) sq++;
-    const unsigned rcap = (m + 6 * sq + 8 + 1) & ~1u;
-    const unsigned rstride = ((rcap / 2) & 1u) ? rcap : rcap + 2;
-    const unsigned long long capp = ((5ull * (unsigned long long)n / 4ull) / P + 64ull + 1ull) & ~1ull;
-    unsigned long long ts = 64;
-    while (ts < capp + capp / 2) ts <<= 1;
-    size_t off = 0;
-    char *base = (char *)w.tab;
+    const unsigned long long P = 1ull << logp, PQ = P * HP_Q;
+    auto level = [](HpLevel &L, unsigned logg, unsigned long long mean) {
+        L.logg = logg;
+        const unsigned m = (unsigned)HP_TILE >> logg;
+        unsigned sq = 1;
+        while (sq * sq < m) sq++;
+        L.rcap = (m + 6 * sq + 8 + 1) & ~1u;
+        L.rstride = ((L.rcap / 2) & 1u) ? L.rcap : L.rcap + 2;
+        L.cap = (mean + mean / 4 + 64ull + 1ull) & ~1ull;
+    };
+    level(c->l1, logp, (unsigned long long)n / P);
+    level(c->l2, HP_LOGQ, (unsigned long long)n / PQ);
+    unsigned ts = 64;
+    while (ts < c->l2.cap + c->l2.cap / 2) ts <<= 1;
     c->logp = logp;
-    c->rcap = rcap;
-    c->rstride = rstride;
-    c->capp = capp;
     c->tslots = ts;
-    c->cursors = (unsigned *)(base + off);
+    char *base = (char *)w.tab;
+    size_t off = 0;
+    c->l1.cursors = (unsigned *)(base + off);
     off += round256((size_t)P * 4);
+    c->l2.cursors = (unsigned *)(base + off);
+    off += round256((size_t)PQ * 4);
     c->dups = (unsigned long long *)(base + off);
     off += round256((size_t)HP_DUPCAP * 8);
-    for (int k = 0; k < 2; k++) {
-        c->rep[k] = (unsigned *)(base + off);
-        off += round256((size_t)(ts / 8));
-    }
-    c->tab = (unsigned long long *)(base + off);
-    off += round256((size_t)ts * 8);
-    c->pool = (unsigned long long *)(base + off);
-    off += round256((size_t)P * capp * 8);
-    return off <= (size_t)w.slots * sizeof(HashSlot) && hp_smem_bytes(*c) <= 200 * 1024;
+    c->l1.pool = (unsigned long long *)(base + off);
+    off += round256((size_t)(P * c->l1.cap * 8));
+    c->l2.pool = (unsigned long long *)(base + off);
+    off += round256((size_t)(PQ * c->l2.cap * 8));
+    return off <= (size_t)w.slots * sizeof(HashSlot) && hp_group_smem(c->l1) <= 200 * 1024 &&
+           hp_group_smem(c->l2) <= 200 * 1024 && (size_t)ts * 8 + ts / 8 <= 200 * 1024;
 }
 
 // Bucket width: about two buckets per SM, between 2^14 and 2^19 values (a 64 KB
@@ -2065,14 +2093,20 @@ static void run_bitmap_check(const T *x, int64_t n, int64_t rlo, int64_t rhi, bo
         HpCfg hc{};
         const int gate = hp_layout(w, n, &hc) ? 1 : 0;
         if (gate) {  // partitioned; the single table below runs only if it gives up
-            const size_t smem = hp_smem_bytes(hc);
-            const int64_t ptiles = (n + HP_TILE - 1) / HP_TILE;
+            const size_t sm1 = hp_group_smem(hc.l1), sm2 = hp_group_smem(hc.l2);
+            const size_t sms = (size_t)hc.tslots * 8 + hc.tslots / 8;
+            const int64_t t1 = (n + HP_TILE - 1) / HP_TILE;
+            const int64_t t2 = (int64_t)((hc.l1.cap + HP_TILE - 1) / HP_TILE) << hc.logp;
+            const int64_t gcap = (int64_t)num_sms() * 4;
             hp_setup_kernel<<<sgrid, STREAM_THREADS, 0, st>>>(h, hc);
-            cudaFuncSetAttribute(hp_part_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            hp_part_kernel<T><<<(int)std::min<int64_t>(ptiles, (int64_t)num_sms() * 4), HP_THREADS, smem, st>>>(
+            cudaFuncSetAttribute(hp_group_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+            hp_group_kernel<T, 0><<<(int)std::min(t1, gcap), HP_THREADS, sm1, st>>>(
                 x, n, rlo, rhi, h, hc, (reinterpret_cast<uintptr_t>(x) & 15u) == 0);
-            for (unsigned p = 0; p < (1u << hc.logp); p++)
-                hp_insert_kernel<<<num_sms() * 8, STREAM_THREADS, 0, st>>>(h, hc, p);
+            cudaFuncSetAttribute(hp_group_kernel<int64_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+            hp_group_kernel<int64_t, 1><<<(int)std::min(t2, gcap), HP_THREADS, sm2, st>>>(nullptr, n, rlo, rhi, h,
+                                                                                          hc, 1);
+            cudaFuncSetAttribute(hp_set_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sms);
+            hp_set_kernel<<<(unsigned)(HP_Q << hc.logp), HP_SET_THREADS, sms, st>>>(h, hc);
             hp_first_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, rlo, rhi, h, hc);
             partner_kernel<T><<<grid, STREAM_THREADS, 0, st>>>(x, n, h, &h->k_first);
         }
