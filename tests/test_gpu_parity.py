@@ -254,6 +254,12 @@ def test_inj_any_span_partitioned_paths(ixp, dev):
     same(ixp.check_inj(T(c, dev)), oracle.check_inj(c), "top-hash-twice")
     c[100] = c[2_900_000]  # an earlier repeat of another value wins
     same(ixp.check_inj(T(c, dev)), oracle.check_inj(c), "top-hash-and-another")
+    # an 8-byte-aligned view (scalar loads in the first grouping pass), clean and with a repeat
+    buf = np.concatenate([np.zeros(1, np.int64), x])
+    same(ixp.check_inj(T(buf, dev)[1:]), oracle.check_inj(x), "unaligned")
+    buf[1 + n - 5] = x[17]
+    d = buf[1:].copy()
+    same(ixp.check_inj(T(buf, dev)[1:]), oracle.check_inj(d), "unaligned-dup")
 
 
 @pytest.mark.parametrize("dtype", [np.int32, np.int64])
